@@ -1,0 +1,194 @@
+"""FP64 CPU oracle for the MOL^T recursive-convolution wave solver.
+
+TEST INFRASTRUCTURE ONLY: the reference the CUDA library is checked against.
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` import this package.  The library never calls it and it shares no
+code with the library.
+
+The arithmetic lives in ``molt_oracle.c`` (plain C, double precision, the
+paper's operators in the paper's order); this module compiles it with gcc and
+wraps it for numpy arrays.  Fields are numpy arrays in C order with shape
+``(nz, ny, nx)`` (or ``(ny, nx)`` / ``(nx,)``), i.e. x varies fastest.
+
+Parity status of each function (see the pins in ``tests/test_oracle_*.py``):
+every function here is pinned; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "molt_oracle.c"
+_BUILD = _HERE / "_build"
+_LIB = _BUILD / "libmolt_oracle.so"
+
+PERIODIC = 0
+DIRICHLET = 1
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the C oracle (gcc, OpenMP over lines) into ``oracle/_build``."""
+    _BUILD.mkdir(exist_ok=True)
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
+        cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", str(tmp), str(_SRC), "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(str(build()))
+        dp = ctypes.POINTER(ctypes.c_double)
+        lp = ctypes.POINTER(ctypes.c_long)
+        L, I, D = ctypes.c_long, ctypes.c_int, ctypes.c_double
+        lib.orc_weights.argtypes = [D, I, dp]
+        lib.orc_linv_line.argtypes = [dp, L, dp, L, L, D, I, I]
+        lib.orc_linv_axis.argtypes = [dp, dp, I, lp, I, D, I, I]
+        lib.orc_D_axis.argtypes = [dp, dp, I, lp, I, D, I, I]
+        lib.orc_Ap.argtypes = [I, D, dp]
+        lib.orc_beta_max.argtypes = [I]
+        lib.orc_beta_max.restype = D
+        lib.orc_F.argtypes = [dp, dp, I, lp, dp, I, I, I, D, lp]
+        lib.orc_step.argtypes = [dp, dp, dp, I, lp, dp, I, I, I, D]
+        lib.orc_start.argtypes = [dp, dp, I, lp, dp, I, I, I, D]
+        lib.orc_run.argtypes = [dp, dp, L, I, lp, dp, I, I, I, D]
+        lib.orc_num_threads.restype = I
+        _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _shape(a: np.ndarray):
+    shp = (ctypes.c_long * 3)(*([1, 1, 1]))
+    for i, s in enumerate(reversed(a.shape)):
+        shp[i] = s
+    return a.ndim, shp
+
+
+def _nu_arr(nu, ndim):
+    nu = np.broadcast_to(np.asarray(nu, dtype=np.float64), (ndim,)).copy()
+    return np.concatenate([nu, np.ones(3 - ndim)])
+
+
+def _bc(bc) -> int:
+    if isinstance(bc, str):
+        return {"periodic": PERIODIC, "dirichlet": DIRICHLET}[bc]
+    return int(bc)
+
+
+def num_threads() -> int:
+    return _load().orc_num_threads()
+
+
+def weights(nu: float, quad: int = 2):
+    """(d, W0, W1, R) of one increment, Sec. 2 (R = 0 for the linear rule)."""
+    out = np.zeros(4)
+    _load().orc_weights(float(nu), int(quad), _dp(out))
+    return tuple(out)
+
+
+def linv_line(v, nu: float, bc="dirichlet", quad: int = 2) -> np.ndarray:
+    """L^{-1} of eq. (L_Inverse) on one line, with the boundary correction."""
+    v = _f64(v)
+    w = np.empty_like(v)
+    _load().orc_linv_line(_dp(v), 1, _dp(w), 1, v.size, float(nu), int(quad), _bc(bc))
+    return w
+
+
+def linv_axis(v, axis: int, nu: float, bc="dirichlet", quad: int = 2) -> np.ndarray:
+    """L_gamma^{-1} along ``axis`` (0 = x, the fastest index) of a field."""
+    v = _f64(v)
+    w = np.empty_like(v)
+    nd, shp = _shape(v)
+    _load().orc_linv_axis(_dp(v), _dp(w), nd, shp, int(axis), float(nu), int(quad), _bc(bc))
+    return w
+
+
+def D_axis(v, axis: int, nu: float, bc="dirichlet", quad: int = 2, power: int = 1) -> np.ndarray:
+    """D_gamma^power v with D_gamma = 1 - L_gamma^{-1} (eq. LD_gam)."""
+    out = _f64(v)
+    nd, shp = _shape(out)
+    for _ in range(power):
+        src = out
+        out = np.empty_like(src)
+        _load().orc_D_axis(_dp(src), _dp(out), nd, shp, int(axis), float(nu), int(quad), _bc(bc))
+    return out
+
+
+def Ap(P: int, beta: float) -> np.ndarray:
+    """A_p(beta), p = 1..P, of eq. (update_P)."""
+    out = np.zeros(P)
+    _load().orc_Ap(int(P), float(beta), _dp(out))
+    return out
+
+
+def beta_max(P: int) -> float:
+    """First positive root of -sum_p A_p(beta) = 4 (eq. Stab_cond, Table 1)."""
+    return _load().orc_beta_max(int(P))
+
+
+def F(u, nu, P: int, beta: float, bc="dirichlet", quad: int = 2, return_nops: bool = False):
+    """F[u] = sum_p sum_m c_pm C^m D^{p-m} u (eq. Full_2D; eq. update_P in 1D).
+
+    ``nu`` is alpha*h per axis (scalar or one value per axis, x first)."""
+    u = _f64(u)
+    out = np.empty_like(u)
+    nd, shp = _shape(u)
+    nus = _nu_arr(nu, nd)
+    nops = ctypes.c_long(0)
+    _load().orc_F(_dp(u), _dp(out), nd, shp, _dp(nus), int(quad), _bc(bc), int(P),
+                  float(beta), ctypes.byref(nops))
+    return (out, nops.value) if return_nops else out
+
+
+def step(uprev, ucur, nu, P: int, beta: float, bc="dirichlet", quad: int = 2) -> np.ndarray:
+    """u^{n+1} = 2u^n - u^{n-1} + F[u^n]."""
+    uprev, ucur = _f64(uprev), _f64(ucur)
+    out = np.empty_like(ucur)
+    nd, shp = _shape(ucur)
+    nus = _nu_arr(nu, nd)
+    _load().orc_step(_dp(uprev), _dp(ucur), _dp(out), nd, shp, _dp(nus), int(quad), _bc(bc),
+                     int(P), float(beta))
+    return out
+
+
+def start(u0, nu, P: int, beta: float, bc="dirichlet", quad: int = 2) -> np.ndarray:
+    """u^1 = u^0 + F[u^0]/2 (zero initial velocity, Sec. 3.2)."""
+    u0 = _f64(u0)
+    out = np.empty_like(u0)
+    nd, shp = _shape(u0)
+    nus = _nu_arr(nu, nd)
+    _load().orc_start(_dp(u0), _dp(out), nd, shp, _dp(nus), int(quad), _bc(bc), int(P), float(beta))
+    return out
+
+
+def run(uprev, ucur, nsteps: int, nu, P: int, beta: float, bc="dirichlet", quad: int = 2):
+    """Advance (u^{n-1}, u^n) by ``nsteps`` steps; returns new copies."""
+    up, uc = _f64(uprev).copy(), _f64(ucur).copy()
+    nd, shp = _shape(uc)
+    nus = _nu_arr(nu, nd)
+    _load().orc_run(_dp(up), _dp(uc), int(nsteps), nd, shp, _dp(nus), int(quad), _bc(bc),
+                    int(P), float(beta))
+    return up, uc
+
+
+def grid_spacing(n: int, length: float, bc) -> float:
+    """Dirichlet axes include both end nodes; periodic axes hold n points."""
+    return length / (n - 1) if _bc(bc) == DIRICHLET else length / n

@@ -1,0 +1,426 @@
+/*
+ * molt_oracle.c -- plain FP64 CPU oracle for the MOL^T recursive-convolution
+ * wave solver of Causley & Christlieb, "Higher order A-stable schemes for the
+ * wave equation using a recursive convolution approach" (arXiv:1308.3214).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference the CUDA library is
+ * checked against.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load it; the library itself never calls it and
+ * shares no code, header, table or constant generator with it.
+ *
+ * Everything is computed in double precision, in the order the paper states
+ * it, without blocking, fusion or algebraic re-arrangement:
+ *
+ *   - the convolution L^{-1} of eq. (L_Inverse), split into the left- and
+ *     right-going parts I^L, I^R and evaluated with the exponential
+ *     recurrences of Sec. 2, the increments integrated exactly against the
+ *     local quadratic (or linear) interpolant, plus the homogeneous boundary
+ *     terms A e^{-alpha(x-a)} + B e^{-alpha(b-x)} (Sec. 2, Sec. 3.2);
+ *   - D = 1 - L^{-1} (eq. D_def_1d);
+ *   - the 1D update of order 2P, eq. (update_P) with the coefficients A_p;
+ *   - the 2D/3D ADI operators C (eqs. C_def_ADI, C_def_ADI_3) and
+ *     D (eqs. D_def_ADI, D_def_ADI_3), combined as in eq. (Full_2D) with the
+ *     terms built in the order of Table 3 (Sec. 4.2);
+ *   - the time step u^{n+1} = 2u^n - u^{n-1} + F[u^n] and the start value
+ *     u^1 = u^0 + F[u^0]/2 for zero initial velocity (Sec. 3.2).
+ *
+ * Readings of points the paper leaves open (each is listed in the design
+ * notes of the repository):
+ *   - Local interpolant (Sec. 2 says only "O(1) operations"; the quadrature
+ *     is deferred to the authors' earlier paper).  quad = 2 (default): the
+ *     quadratic through the nodes j-1, j, j+1 of the destination node j,
+ *     integrated exactly over the cell next to x_j; in the cells touching a
+ *     Dirichlet end the three nodes nearest inside the domain are used.
+ *     quad = 1: the linear interpolant of the cell.  The quadratic rule
+ *     reproduces every error of Table 2.
+ *   - Dirichlet: the corrected L^{-1} returns w = v at both end nodes, so
+ *     D v = 0 there (Sec. 3.2: the boundary values of D^m u are the even
+ *     derivatives of the boundary data, zero for homogeneous data).
+ *   - Periodic: the left/right parts include every periodic image, which
+ *     fixes A = I^L(b)/(1-mu), B = I^R(a)/(1-mu) on the line closed by
+ *     x_n = x_0 (mu = e^{-alpha L}).
+ *
+ * Grid convention: a field of shape (nx, ny, nz) is stored with x fastest,
+ * index = x + nx*(y + ny*z).  A Dirichlet axis of n points includes both end
+ * nodes (spacing L/(n-1)); a periodic axis holds n distinct points (L/n).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PERIODIC 0
+#define ORC_DIRICHLET 1
+
+/* ------------------------------------------------------------------------ */
+/* Exponential moments M_k(nu) = int_0^nu t^k e^{-t} dt, k = 0, 1, 2.        */
+/* For small nu the closed forms cancel, so the power series is summed.      */
+/* ------------------------------------------------------------------------ */
+static double moment(int k, double nu)
+{
+    if (nu < 0.5) {
+        /* int_0^nu t^k sum_i (-t)^i / i! dt = sum_i (-1)^i nu^{k+i+1} / (i! (k+i+1)) */
+        double sum = 0.0, term_pow = pow(nu, k + 1), fact = 1.0;
+        for (int i = 0; i < 40; ++i) {
+            if (i > 0) { term_pow *= nu; fact *= i; }
+            double t = ((i & 1) ? -1.0 : 1.0) * term_pow / (fact * (k + i + 1));
+            sum += t;
+        }
+        return sum;
+    }
+    double e = exp(-nu);
+    if (k == 0) return 1.0 - e;
+    if (k == 1) return 1.0 - (1.0 + nu) * e;
+    return 2.0 - (2.0 + 2.0 * nu + nu * nu) * e;
+}
+
+/*
+ * Quadrature weights of one increment (Sec. 2):
+ *   J^L_j = (alpha/2) int_0^h e^{-alpha y} p(x_j - y) dy,
+ * with p the interpolant written in Newton form about x_j and s = -y/h:
+ *   p = v_j + s (v_j - v_{j-1}) + s (s+1)/2 * S,
+ * where S is the second difference of the three interpolation nodes.  With
+ * t = alpha y, s = -t/nu this integrates to
+ *   J^L_j = 1/2 [ W0 v_j + W1 v_{j-1} + R S ],
+ *   W0 = M0 - M1/nu,  W1 = M1/nu,  R = (M2/nu^2 - M1/nu)/2.
+ * The mirror image gives J^R_j with v_{j+1} in place of v_{j-1}.
+ * quad = 1 drops the S term (linear interpolant).
+ */
+void orc_weights(double nu, int quad, double out[4])
+{
+    double M0 = moment(0, nu), M1 = moment(1, nu), M2 = moment(2, nu);
+    out[0] = exp(-nu);                    /* d = e^{-alpha h} */
+    out[1] = M0 - M1 / nu;                /* W0 */
+    out[2] = M1 / nu;                     /* W1 */
+    out[3] = (quad >= 2) ? 0.5 * (M2 / (nu * nu) - M1 / nu) : 0.0; /* R */
+}
+
+/* ------------------------------------------------------------------------ */
+/* L^{-1} on one line (eq. L_Inverse with the boundary correction).          */
+/* v and w are read/written with stride sv / sw.                             */
+/* ------------------------------------------------------------------------ */
+static double vat(const double *v, long sv, long n, int bc, long j)
+{
+    if (bc == ORC_PERIODIC) { j %= n; if (j < 0) j += n; }
+    return v[j * sv];
+}
+
+/* second difference centred at node c */
+static double sdiff(const double *v, long sv, long n, int bc, long c)
+{
+    return vat(v, sv, n, bc, c + 1) - 2.0 * vat(v, sv, n, bc, c) + vat(v, sv, n, bc, c - 1);
+}
+
+void orc_linv_line(const double *v, long sv, double *w, long sw, long n,
+                   double nu, int quad, int bc)
+{
+    double c4[4];
+    orc_weights(nu, quad, c4);
+    double d = c4[0], W0 = c4[1], W1 = c4[2], R = c4[3];
+    /* Dirichlet: cells 1..n-1 between nodes 0..n-1.  Periodic: the line is
+     * closed by node n == node 0, giving n cells. */
+    long N = (bc == ORC_PERIODIC) ? n : n - 1;
+    int use_quad = (R != 0.0) && n >= 3;   /* a quadratic needs three nodes */
+    double *JL = calloc((size_t)(N + 1), sizeof(double));
+    double *JR = calloc((size_t)(N + 1), sizeof(double));
+    double *IL = calloc((size_t)(N + 1), sizeof(double));
+    double *IR = calloc((size_t)(N + 1), sizeof(double));
+
+    /* increments of the left-going part, cells [x_{j-1}, x_j] */
+    for (long j = 1; j <= N; ++j) {
+        double S = 0.0;
+        if (use_quad) {
+            long c = j;                                     /* nodes j-1, j, j+1 */
+            if (bc == ORC_DIRICHLET && c + 1 > n - 1) c = j - 1;  /* nodes j-2, j-1, j */
+            S = sdiff(v, sv, n, bc, c);
+        }
+        JL[j] = 0.5 * (W0 * vat(v, sv, n, bc, j) + W1 * vat(v, sv, n, bc, j - 1) + R * S);
+    }
+    /* increments of the right-going part, cells [x_j, x_{j+1}] */
+    for (long j = 0; j < N; ++j) {
+        double S = 0.0;
+        if (use_quad) {
+            long c = j;                                     /* nodes j-1, j, j+1 */
+            if (bc == ORC_DIRICHLET && c - 1 < 0) c = j + 1;      /* nodes j, j+1, j+2 */
+            S = sdiff(v, sv, n, bc, c);
+        }
+        JR[j] = 0.5 * (W0 * vat(v, sv, n, bc, j) + W1 * vat(v, sv, n, bc, j + 1) + R * S);
+    }
+    /* exponential recurrences: I^L(x) = e^{-alpha h} I^L(x - h) + J^L,
+     * I^R(x) = e^{-alpha h} I^R(x + h) + J^R, no inflow at the line ends */
+    IL[0] = 0.0;
+    for (long j = 1; j <= N; ++j) IL[j] = d * IL[j - 1] + JL[j];
+    IR[N] = 0.0;
+    for (long j = N - 1; j >= 0; --j) IR[j] = d * IR[j + 1] + JR[j];
+
+    /* homogeneous terms A e^{-alpha (x - a)} + B e^{-alpha (b - x)} */
+    double mu = pow(d, (double)N);     /* e^{-alpha (b - a)} */
+    double A, B;
+    if (bc == ORC_PERIODIC) {
+        /* contributions of all periodic images to the left / right */
+        A = IL[N] / (1.0 - mu);
+        B = IR[0] / (1.0 - mu);
+    } else {
+        /* w(a) = v(a), w(b) = v(b):
+         *   A + mu B = v_0 - I^R_0,   mu A + B = v_N - I^L_N  */
+        double r0 = vat(v, sv, n, bc, 0) - IR[0];
+        double r1 = vat(v, sv, n, bc, N) - IL[N];
+        A = (r0 - mu * r1) / (1.0 - mu * mu);
+        B = (r1 - mu * r0) / (1.0 - mu * mu);
+    }
+    for (long j = 0; j < n; ++j)
+        w[j * sw] = IL[j] + IR[j] + A * pow(d, (double)j) + B * pow(d, (double)(N - j));
+    free(JL); free(JR); free(IL); free(IR);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Axis operators on a whole field: L_gamma^{-1} and D_gamma (eq. LD_gam)     */
+/* ------------------------------------------------------------------------ */
+static long total_size(int ndim, const long *shape)
+{
+    long t = 1;
+    for (int a = 0; a < ndim; ++a) t *= shape[a];
+    return t;
+}
+
+void orc_linv_axis(const double *v, double *w, int ndim, const long *shape,
+                   int axis, double nu, int quad, int bc)
+{
+    long n = shape[axis];
+    long stride = 1;
+    for (int a = 0; a < axis; ++a) stride *= shape[a];
+    long total = total_size(ndim, shape);
+    long nlines = total / n;
+    #pragma omp parallel for schedule(static)
+    for (long line = 0; line < nlines; ++line) {
+        /* line = (inner index below the axis) + stride * (outer index) */
+        long inner = line % stride, outer = line / stride;
+        long base = inner + outer * stride * n;
+        orc_linv_line(v + base, stride, w + base, stride, n, nu, quad, bc);
+    }
+}
+
+void orc_D_axis(const double *v, double *out, int ndim, const long *shape,
+                int axis, double nu, int quad, int bc)
+{
+    long total = total_size(ndim, shape);
+    double *w = malloc(sizeof(double) * (size_t)total);
+    orc_linv_axis(v, w, ndim, shape, axis, nu, quad, bc);
+    for (long i = 0; i < total; ++i) out[i] = v[i] - w[i];
+    free(w);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coefficients of eq. (update_P):                                           */
+/*   A_p(beta) = 2 sum_{m=1}^{p} (-1)^m beta^{2m}/(2m)! binom(p-1, m-1)       */
+/* ------------------------------------------------------------------------ */
+static double binom(int n, int k)
+{
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+static double factorial(int n)
+{
+    double r = 1.0;
+    for (int i = 2; i <= n; ++i) r *= i;
+    return r;
+}
+
+/* c_{p,m} = (-1)^m 2 beta^{2m}/(2m)! binom(p-1, m-1), the weight of
+ * C^m D^{p-m} in eq. (Full_2D); in 1D C = D and sum_m c_{p,m} = A_p. */
+static double cpm(int p, int m, double beta)
+{
+    return ((m & 1) ? -1.0 : 1.0) * 2.0 * pow(beta, 2.0 * m) / factorial(2 * m) * binom(p - 1, m - 1);
+}
+
+void orc_Ap(int P, double beta, double *A)
+{
+    for (int p = 1; p <= P; ++p) {
+        double s = 0.0;
+        for (int m = 1; m <= p; ++m) s += cpm(p, m, beta);
+        A[p - 1] = s;
+    }
+}
+
+/* beta_max: the first positive root of -sum_{p=1}^P A_p(beta) = 4
+ * (eq. Stab_cond), found by a scan for the first sign change then bisection */
+double orc_beta_max(int P)
+{
+    double A[16];
+    double prev_b = 1e-6, prev_f;
+    orc_Ap(P, prev_b, A);
+    prev_f = -4.0;
+    for (int p = 0; p < P; ++p) prev_f -= A[p];
+    for (int i = 1; i <= 40000; ++i) {
+        double b = 1e-4 * i;
+        orc_Ap(P, b, A);
+        double f = -4.0;
+        for (int p = 0; p < P; ++p) f -= A[p];
+        if (prev_f < 0.0 && f >= 0.0) {
+            double lo = prev_b, hi = b;
+            for (int it = 0; it < 200; ++it) {
+                double mid = 0.5 * (lo + hi);
+                orc_Ap(P, mid, A);
+                double fm = -4.0;
+                for (int p = 0; p < P; ++p) fm -= A[p];
+                if (fm < 0.0) lo = mid; else hi = mid;
+            }
+            return 0.5 * (lo + hi);
+        }
+        prev_b = b; prev_f = f;
+    }
+    return -1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ADI operators of Sec. 4.                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int ndim; const long *shape; const double *nu; int quad; int bc; long total;
+    long napplied;            /* number of applications of C or D (Table 3) */
+} orc_ctx;
+
+static void Linv(orc_ctx *c, const double *v, double *w, int axis)
+{
+    orc_linv_axis(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
+}
+
+static void Dgam(orc_ctx *c, const double *v, double *w, int axis)
+{
+    orc_D_axis(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
+}
+
+/* C[v]: 1D: D_x v;  2D: L_y^{-1} D_x v + L_x^{-1} D_y v (eq. C_def_ADI);
+ * 3D: L_y^{-1}L_z^{-1} D_x v + L_z^{-1}L_x^{-1} D_y v + L_x^{-1}L_y^{-1} D_z v
+ * (eq. C_def_ADI_3). */
+static void applyC(orc_ctx *c, const double *v, double *out)
+{
+    long T = c->total;
+    double *t1 = malloc(sizeof(double) * (size_t)T);
+    double *t2 = malloc(sizeof(double) * (size_t)T);
+    c->napplied++;
+    if (c->ndim == 1) {
+        Dgam(c, v, out, 0);
+    } else if (c->ndim == 2) {
+        Dgam(c, v, t1, 0); Linv(c, t1, out, 1);          /* L_y^{-1} D_x v */
+        Dgam(c, v, t1, 1); Linv(c, t1, t2, 0);           /* L_x^{-1} D_y v */
+        for (long i = 0; i < T; ++i) out[i] += t2[i];
+    } else {
+        /* term g is L_outer^{-1} L_inner^{-1} D_g, applied right to left:
+         * (x: L_y L_z D_x), (y: L_z L_x D_y), (z: L_x L_y D_z) */
+        memset(out, 0, sizeof(double) * (size_t)T);
+        for (int g = 0; g < 3; ++g) {
+            int outer = (g + 1) % 3, inner = (g + 2) % 3;
+            Dgam(c, v, t1, g); Linv(c, t1, t2, inner); Linv(c, t2, t1, outer);
+            for (long i = 0; i < T; ++i) out[i] += t1[i];
+        }
+    }
+    free(t1); free(t2);
+}
+
+/* D[v]: 1D: D_x v;  2D: v - L_x^{-1}L_y^{-1} v (eq. D_def_ADI);
+ * 3D: v - L_x^{-1}L_y^{-1}L_z^{-1} v (eq. D_def_ADI_3). */
+static void applyD(orc_ctx *c, const double *v, double *out)
+{
+    long T = c->total;
+    double *t1 = malloc(sizeof(double) * (size_t)T);
+    double *t2 = malloc(sizeof(double) * (size_t)T);
+    c->napplied++;
+    if (c->ndim == 1) {
+        Dgam(c, v, out, 0);
+    } else {
+        const double *src = v;
+        double *bufs[2] = {t1, t2};
+        int k = 0;
+        for (int a = c->ndim - 1; a >= 0; --a) {   /* innermost operator first */
+            Linv(c, src, bufs[k], a);
+            src = bufs[k]; k ^= 1;
+        }
+        for (long i = 0; i < T; ++i) out[i] = v[i] - src[i];
+    }
+    free(t1); free(t2);
+}
+
+/*
+ * F[u] = sum_{p=1}^{P} sum_{m=1}^{p} c_{p,m} C^m D^{p-m} u   (eq. Full_2D;
+ * in 1D it is sum_p A_p D^p u, eq. update_P, since C = D there).
+ * The terms are built with the re-use scheme of Table 3: after stage p the
+ * auxiliaries hold v_k = C^{p-k+1} D^{k-1} u, k = 1..p, obtained from stage
+ * p-1 by v_p = D[v_{p-1}] and v_k = C[v_k] (k < p); stage p costs p
+ * applications.  *nops (if given) receives the number of applications.
+ */
+void orc_F(const double *u, double *F, int ndim, const long *shape,
+           const double *nu, int quad, int bc, int P, double beta, long *nops)
+{
+    orc_ctx c = {ndim, shape, nu, quad, bc, total_size(ndim, shape), 0};
+    long T = c.total;
+    double **v = calloc((size_t)P + 1, sizeof(double *));
+    for (int k = 1; k <= P; ++k) v[k] = malloc(sizeof(double) * (size_t)T);
+    double *tmp = malloc(sizeof(double) * (size_t)T);
+    memset(F, 0, sizeof(double) * (size_t)T);
+    for (int p = 1; p <= P; ++p) {
+        if (p == 1) {
+            applyC(&c, u, v[1]);
+        } else {
+            applyD(&c, v[p - 1], v[p]);
+            for (int k = 1; k < p; ++k) {
+                applyC(&c, v[k], tmp);
+                memcpy(v[k], tmp, sizeof(double) * (size_t)T);
+            }
+        }
+        for (int k = 1; k <= p; ++k) {
+            double w = cpm(p, p - k + 1, beta);
+            for (long i = 0; i < T; ++i) F[i] += w * v[k][i];
+        }
+    }
+    if (nops) *nops = c.napplied;
+    for (int k = 1; k <= P; ++k) free(v[k]);
+    free(v); free(tmp);
+}
+
+/* u^{n+1} = 2 u^n - u^{n-1} + F[u^n]   (eq. update_P / Full_2D) */
+void orc_step(const double *uprev, const double *ucur, double *unext, int ndim,
+              const long *shape, const double *nu, int quad, int bc, int P, double beta)
+{
+    long T = total_size(ndim, shape);
+    double *F = malloc(sizeof(double) * (size_t)T);
+    orc_F(ucur, F, ndim, shape, nu, quad, bc, P, beta, NULL);
+    for (long i = 0; i < T; ++i) unext[i] = 2.0 * ucur[i] - uprev[i] + F[i];
+    free(F);
+}
+
+/* u^1 = u^0 + F[u^0]/2: the Taylor series of Sec. 3.2 with zero initial
+ * velocity keeps only the even terms, each half the weight it has in F. */
+void orc_start(const double *u0, double *u1, int ndim, const long *shape,
+               const double *nu, int quad, int bc, int P, double beta)
+{
+    long T = total_size(ndim, shape);
+    double *F = malloc(sizeof(double) * (size_t)T);
+    orc_F(u0, F, ndim, shape, nu, quad, bc, P, beta, NULL);
+    for (long i = 0; i < T; ++i) u1[i] = u0[i] + 0.5 * F[i];
+    free(F);
+}
+
+/* Advance (uprev, ucur) = (u^{n-1}, u^n) by nsteps steps in place. */
+void orc_run(double *uprev, double *ucur, long nsteps, int ndim, const long *shape,
+             const double *nu, int quad, int bc, int P, double beta)
+{
+    long T = total_size(ndim, shape);
+    double *un = malloc(sizeof(double) * (size_t)T);
+    for (long s = 0; s < nsteps; ++s) {
+        orc_step(uprev, ucur, un, ndim, shape, nu, quad, bc, P, beta);
+        memcpy(uprev, ucur, sizeof(double) * (size_t)T);
+        memcpy(ucur, un, sizeof(double) * (size_t)T);
+    }
+    free(un);
+}
+
+/* Threads OpenMP would use (1 when built without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+int orc_num_threads(void) { return omp_get_max_threads(); }
+#else
+int orc_num_threads(void) { return 1; }
+#endif
