@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""Benchmark of the MOL^T wave solver on one or more GB300s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 2d|3d|1d]
+                    [--prec mixed|fp64] [--impl ours|reference]
+
+A "step" is one time step of the scheme of order 2P over the whole synthetic
+field: every pass of the hot path (per-axis line sweeps, the ADI combination
+and the level update u^{n+1} = 2u^n - u^{n-1} + F[u^n]).  The default workload
+is the 2D one: homogeneous Dirichlet unit square, 2048 x 2048 points, P = 3
+(6th order), CFL 2, beta = beta_max(3), a seeded Gaussian pulse; inputs are
+resident in HBM when the timed region starts.  Metric: point-updates/s
+(points x steps / second), summed over all GPUs.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
+problem (independent replicas, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_1308_3214_gb300 import workloads  # noqa: E402
+
+METRIC = "point-updates/s"
+PEAKS_FILE = ROOT / "MEASURED_PEAKS.json"
+TRAFFIC_FILE = ROOT / "profiles" / "ncu_traffic.json"
+KERNEL_SOURCES = [ROOT / "paper_1308_3214_gb300" / "csrc" / f for f in
+                  ("molt_kernels.cuh", "molt_passes.cu", "molt_api.cu")]
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_spec(name: str) -> dict:
+    if name == "2d":
+        n = 2048
+        return dict(name="2d-dirichlet-2048x2048-P3-cfl2-gaussian", shape=(n, n), P=3, cfl=2.0,
+                    bc="dirichlet", lo=(0.0, 0.0), hi=(1.0, 1.0), h=1.0 / (n - 1), steps_in_config=500,
+                    field=lambda: workloads.gaussian_2d(n, seed=1002))
+    if name == "3d":
+        n = 256
+        L = 2 * math.pi
+        return dict(name="3d-periodic-256^3-P2-cfl1.5-fourier16", shape=(n, n, n), P=2, cfl=1.5,
+                    bc="periodic", lo=(0.0,) * 3, hi=(L,) * 3, h=L / n, steps_in_config=200,
+                    field=lambda: workloads.fourier_3d(n, seed=1003)[0])
+    if name == "1d":
+        n = 256
+        L = 2 * math.pi
+        return dict(name="1d-periodic-256-P1-cfl1.5-fourier8", shape=(n,), P=1, cfl=1.5, bc="periodic",
+                    lo=(0.0,), hi=(L,), h=L / n, steps_in_config=200,
+                    field=lambda: workloads.fourier_1d(n, seed=1001))
+    raise SystemExit(f"unknown workload {name}")
+
+
+def bytes_per_point(spec: dict, prec: str) -> dict:
+    """Algorithmic HBM bytes per point and step of each pass:
+    every field read or written once per pass, levels as 8-byte pairs/doubles."""
+    P, nd = spec["P"], len(spec["shape"])
+    t = 4 if prec == "mixed" else 8
+    if nd == 1:
+        return {0: 24}
+    if nd == 2:
+        return {1: 8 + t * P, 0: t * P + 24}
+    return {2: 8 + t * P, 1: t * P + 8 + t * (P + 1), 0: t * (P + 1) + 24}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(p.read_bytes())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    QUERY = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        if shutil.which("nvidia-smi") is None:
+            return self
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.fh = open(self.path, "w")
+        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100"]
+        self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in Path(self.path).read_text().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            rows.append(f)
+        os.unlink(self.path)
+        if self.bus_id:
+            mine = [r for r in rows if r[1].lower().endswith(self.bus_id.lower()[-12:])]
+            rows = mine or rows
+        if not rows:
+            return None
+        idx0 = rows[0][0]
+        rows = [r for r in rows if r[0] == idx0]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = np.array([num(r[2]) for r in rows])
+        mx = np.array([num(r[3]) for r in rows])
+        pw = np.array([num(r[4]) for r in rows])
+        load = pw > np.nanmedian(pw) if len(pw) > 4 else np.ones_like(pw, dtype=bool)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[6 + k].lower().startswith("active"):
+                    reasons.add(name)
+        sm_load = sm[load] if load.any() else sm
+        return {"sm_mhz": float(np.nanmedian(sm_load)), "sm_max_mhz": float(np.nanmax(mx)),
+                "reasons": sorted(reasons), "samples": int(len(rows)),
+                "power_w_max": float(np.nanmax(pw)) if len(pw) else None}
+
+
+def read_peak():
+    try:
+        d = json.loads(PEAKS_FILE.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def read_traffic(kernel_axis: int, workload: str, prec: str):
+    """ncu DRAM bytes per launch of the dominant kernel, if taken on the
+    current kernel sources."""
+    try:
+        d = json.loads(TRAFFIC_FILE.read_text())
+    except Exception:
+        return None
+    if d.get("kernel_sha") != kernel_sha():
+        return None
+    for e in d.get("entries", []):
+        if e.get("workload") == workload and e.get("prec") == prec and int(e.get("axis", -1)) == kernel_axis:
+            return float(e["dram_bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(spec: dict, budget_s: float, max_steps: int | None = None, min_side: int = 64):
+    """Point-updates/s of the FP64 oracle on a bounded sample of the workload:
+    the full field when one step fits the budget, else a smaller grid with the
+    same CFL, P and boundary condition."""
+    import oracle
+    oracle.build()
+    nd = len(spec["shape"])
+    full = int(np.prod(spec["shape"]))
+    P, bc = spec["P"], spec["bc"]
+    beta = oracle.beta_max(P)
+    # probe: one step on a small grid
+    side = spec["shape"][0]
+    probe_side = min(side, 256 if nd < 3 else 48)
+    probe_shape = (probe_side,) * nd
+    u = sample_field(spec, probe_shape)
+    nu = beta / spec["cfl"]
+    t0 = time.perf_counter()
+    oracle.step(u, u, nu, P, beta, bc)
+    rate = np.prod(probe_shape) / max(time.perf_counter() - t0, 1e-6)
+    steps = max_steps or 3
+    pts = min(full, int(rate * budget_s / steps))
+    s = max(min_side, int(round(pts ** (1.0 / nd))))
+    s = min(s, side)
+    shape = (s,) * nd if pts < full else tuple(spec["shape"])
+    u0 = sample_field(spec, shape)
+    u1 = oracle.start(u0, nu, P, beta, bc)
+    t0 = time.perf_counter()
+    oracle.run(u0, u1, steps, nu, P, beta, bc)
+    dt = time.perf_counter() - t0
+    return float(np.prod(shape) * steps / dt), shape, steps, dt, oracle.num_threads()
+
+
+def sample_field(spec: dict, shape):
+    nd = len(shape)
+    if nd == 2:
+        return workloads.gaussian_2d(shape[1], seed=1002, ny=shape[0])
+    if nd == 3:
+        return workloads.fourier_3d(shape[0], seed=1003, shape=shape)[0]
+    return workloads.fourier_1d(shape[0], seed=1001)
+
+
+def run_reference(args, spec):
+    """The oracle as it stands on the host cores: each step is one oracle time
+    step on a bounded sample of the workload (same CFL, P, boundary)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    nd = len(spec["shape"])
+    P, bc = spec["P"], spec["bc"]
+    beta = oracle.beta_max(P)
+    nu = beta / spec["cfl"]
+    total_budget = 150.0
+    rate0, _, _, _, _ = cpu_oracle_rate(spec, budget_s=3.0, max_steps=1)
+    per_step_pts = rate0 * total_budget / max(args.steps + args.warmup, 1)
+    full = int(np.prod(spec["shape"]))
+    s = int(round(min(per_step_pts, full) ** (1.0 / nd)))
+    s = max(16, min(s, spec["shape"][0]))
+    shape = (s,) * nd
+    u0 = sample_field(spec, shape)
+    u1 = oracle.start(u0, nu, P, beta, bc)
+    up, uc = oracle.run(u0, u1, args.warmup, nu, P, beta, bc)
+    t0 = time.perf_counter()
+    up, uc = oracle.run(up, uc, args.steps, nu, P, beta, bc)
+    dt = time.perf_counter() - t0
+    pts = float(np.prod(shape))
+    value = pts * args.steps / dt
+    cores = oracle.num_threads()
+    sample = f"{'x'.join(map(str, shape))} grid per step (same CFL, P, bc), {args.steps} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": spec["name"], "sampled_shape": list(shape)},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    spec = workload_spec(args.workload)
+    if args.impl == "reference":
+        run_reference(args, spec)
+        return
+
+    import torch
+    from paper_1308_3214_gb300 import molt
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    shape, P = spec["shape"], spec["P"]
+    N = int(np.prod(shape))
+    dt = spec["cfl"] * spec["h"]
+
+    def make(prec):
+        return molt.Solver(shape, dt=dt, P=P, bc=spec["bc"], prec=prec, lo=spec["lo"], hi=spec["hi"])
+
+    u0_host = spec["field"]()
+    solver = make(args.prec)
+
+    def timed_steps(s, nsteps, warm):
+        up = torch.from_numpy(u0_host).cuda()
+        uc = s.start(up)
+        s.step(up, uc, warm)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        s.set_pass_timing(True)
+        l0 = s.launches
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        s.step(up, uc, nsteps)
+        ev1.record()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        launches = s.launches - l0
+        passes = s.pass_times()
+        s.set_pass_timing(False)
+        return ms, launches, passes, uc
+
+    try:
+        bus = torch.cuda.get_device_properties(dev_index).pci_bus_id
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus).start()
+    ms, launches, passes, _ = timed_steps(solver, args.steps, args.warmup)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ms)
+    value = world * N * args.steps / (ms * 1e-3)
+
+    # roofline of the dominant pass
+    bpp = bytes_per_point(spec, args.prec)
+    dom_axis = max(passes, key=lambda a: passes[a][0])
+    dom_ms = passes[dom_axis][0] / passes[dom_axis][1]
+    alg_bytes = bpp[dom_axis] * N
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    peak, peak_kind = read_peak()
+    kernel_name = {0: "k_horner<x>", 1: "k_powers<y>" if len(shape) == 2 else "k_horner<y>", 2: "k_powers<z>"}[dom_axis]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": read_traffic(dom_axis, spec["name"], args.prec),
+                "kernel": kernel_name, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                "alg_bytes_per_launch": alg_bytes,
+                "passes": {f"axis{a}": {"ms_per_launch": passes[a][0] / passes[a][1],
+                                         "alg_GBps": bpp[a] * N / (passes[a][0] / passes[a][1] * 1e-3) / 1e9,
+                                         "alg_bytes_per_point": bpp[a]} for a in passes},
+                "step_alg_GBps": sum(bpp.values()) * N * args.steps / (ms * 1e-3) / 1e9}
+
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": spec["name"], "shape": list(shape), "P": P, "cfl": spec["cfl"],
+                       "bc": spec["bc"], "beta": solver.beta, "prec": args.prec,
+                       "levels": "f32 hi+lo pairs" if args.prec == "mixed" else "f64",
+                       "l2": "no flush: per-step working set (3 levels + intermediate fields) exceeds the 129 MB L2",
+                       "parallelism": f"{world} independent replica(s)"},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+
+    if rank == 0 and not args.no_fp64_compare and args.prec == "mixed":
+        s64 = make("fp64")
+        k64 = max(3, args.steps // 8)
+        ms64, _, p64, _ = timed_steps(s64, k64, 3)
+        line["fp64_path"] = {"value": N * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
+                             "passes_ms_per_launch": {f"axis{a}": p64[a][0] / p64[a][1] for a in p64}}
+        s64.close()
+
+    if rank == 0 and not args.no_accuracy and len(shape) == 2:
+        line["accuracy"] = accuracy_check(spec, make, molt, torch)
+
+    if not args.no_e2e:
+        calls, per_call = 3, max(1, min(spec["steps_in_config"], args.steps))
+        pin_in = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        pin_out = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        pin_in.numpy()[...] = u0_host
+        solver.solve_host(pin_in.numpy(), per_call, out=pin_out.numpy())      # warm
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            solver.solve_host(pin_in.numpy(), per_call, out=pin_out.numpy())
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        line["e2e"] = {"value": world * N * per_call * calls / e2e_s, "unit": METRIC,
+                       "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
+                       "step": f"one mol_solve_host call: copy u0 in, start + {per_call - 1} steps, copy u out",
+                       "time_steps_per_step": per_call}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sshape, ssteps, sdt, cores = cpu_oracle_rate(spec, budget_s=20.0)
+        line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
+                                "sample": f"{ssteps} oracle steps on a {'x'.join(map(str, sshape))} grid "
+                                          f"({sdt:.1f} s), same CFL, P, boundary"}
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def accuracy_check(spec, make, molt, torch):
+    """Mixed vs FP64 at equal L2 error (2D): both paths run the workload's
+    step count; E_X = rel L2 against FP64 on the grid refined 2x in h and dt,
+    compared on the shared nodes."""
+    shape, P = spec["shape"], spec["P"]
+    nsteps = spec["steps_in_config"]
+    u0 = spec["field"]()
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = make(prec)
+        up = torch.from_numpy(u0).cuda()
+        uc = s.start(up)
+        s.step(up, uc, nsteps - 1)
+        out[prec] = uc.cpu().numpy()
+        s.close()
+    n = shape[0]
+    nf = 2 * n - 1
+    hf = 1.0 / (nf - 1)
+    sf = molt.Solver((nf, nf), dt=spec["cfl"] * spec["h"] / 2, P=P, bc=spec["bc"], prec="fp64",
+                     lo=spec["lo"], hi=spec["hi"])
+    del hf
+    xf = workloads.gaussian_2d(nf, seed=1002)
+    up = torch.from_numpy(xf).cuda()
+    uc = sf.start(up)
+    sf.step(up, uc, 2 * nsteps - 1)
+    ref = uc.cpu().numpy()[::2, ::2]
+    sf.close()
+    nr = np.linalg.norm(ref)
+    e_m = float(np.linalg.norm(out["mixed"] - ref) / nr)
+    e_d = float(np.linalg.norm(out["fp64"] - ref) / nr)
+    return {"steps": nsteps, "E_mixed": e_m, "E_fp64": e_d,
+            "equal_l2": bool(abs(e_m - e_d) <= 0.05 * e_d),
+            "rel_l2_mixed_vs_fp64": float(np.linalg.norm(out["mixed"] - out["fp64"]) / np.linalg.norm(out["fp64"])),
+            "reference": f"fp64 on {nf}x{nf}, dt/2, {2 * nsteps} steps, shared nodes"}
+
+
+if __name__ == "__main__":
+    main()

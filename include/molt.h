@@ -1,0 +1,175 @@
+/*
+ * molt.h -- C ABI of libmolt, a GB300 (sm_103a) implementation of the MOL^T
+ * recursive-convolution wave solver of Causley & Christlieb,
+ * "Higher order A-stable schemes for the wave equation using a recursive
+ * convolution approach" (arXiv:1308.3214).
+ *
+ * What it computes
+ *   The wave equation u_tt = c^2 Lap u on a rectangle / box (1D, 2D, 3D) with
+ *   homogeneous Dirichlet or periodic boundaries, advanced by the A-stable
+ *   scheme of order 2P (Sec. 3 eq. update_P in 1D; Sec. 4 eq. Full_2D with the
+ *   ADI operators C and D in 2D/3D):
+ *       u^{n+1} = 2 u^n - u^{n-1} + F[u^n],
+ *       F = sum_{p=1}^{P} sum_{m=1}^{p} (-1)^m 2 beta^{2m}/(2m)! binom(p-1,m-1) C^m D^{p-m}.
+ *   Every operator is built from the per-axis convolution
+ *       L_gamma^{-1} = (1 - d^2/dgamma^2 / alpha^2)^{-1},  alpha = beta/(c dt)
+ *   (eqs. L_def, L_Inverse), evaluated on each grid line by two exponential
+ *   recurrences (Sec. 2) plus the boundary terms A e^{-alpha(x-a)} +
+ *   B e^{-alpha(b-x)}, and D_gamma = 1 - L_gamma^{-1} (eq. LD_gam).  The local
+ *   increments integrate the quadratic interpolant exactly (the rule that
+ *   reproduces Table 2); the linear rule is available as an option.
+ *
+ * Conventions
+ *   - Fields are contiguous, x fastest: index = x + nx*(y + ny*z), with
+ *     grid.n[0] = nx, grid.n[1] = ny, grid.n[2] = nz.
+ *   - A Dirichlet axis of n points includes both end nodes (spacing
+ *     (hi-lo)/(n-1)); a periodic axis holds n distinct points ((hi-lo)/n).
+ *     Dirichlet data must vanish on the boundary (homogeneous condition).
+ *   - Field pointers are DEVICE pointers to float64 arrays owned by the caller
+ *     unless a function says "host".  The library never frees them.
+ *   - Every call is asynchronous on the given CUDA stream (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream) unless stated otherwise;
+ *     errors that the host can see are returned at once, device errors at the
+ *     next synchronising call (mol_sync, mol_solve_host).
+ *   - Nothing throws across the ABI.  On error a call returns a nonzero
+ *     mol_status and mol_last_error(handle) describes it.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef MOLT_H
+#define MOLT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MOL_OK = 0,
+    MOL_EINVAL = 1,     /* bad argument (sizes, pointers, P, axis, ...)        */
+    MOL_ENOMEM = 2,     /* device or host allocation failed                     */
+    MOL_ECUDA = 3,      /* a CUDA runtime call failed                            */
+    MOL_EUNSTABLE = 4,  /* beta above beta_max(P): the scheme is not A-stable    */
+    MOL_ETIMEOUT = 5    /* a bounded device wait gave up                         */
+} mol_status;
+
+typedef enum { MOL_BC_PERIODIC = 0, MOL_BC_DIRICHLET = 1 } mol_bc;
+
+/* Arithmetic of the line sweeps.
+ *   MOL_FP64:  everything in float64.
+ *   MOL_MIXED: sweeps and intermediate fields in float32; the time levels are
+ *              kept as float32 pairs (hi + lo, about 48 significant bits) and
+ *              the level update and the first second difference of u^n are
+ *              formed in that pair arithmetic. */
+typedef enum { MOL_FP64 = 0, MOL_MIXED = 1 } mol_prec;
+
+typedef struct {
+    int ndim;           /* 1, 2 or 3                                   */
+    int64_t n[3];       /* points per axis, x first                    */
+    double lo[3];       /* domain lower corner                         */
+    double hi[3];       /* domain upper corner                         */
+} mol_grid;
+
+typedef struct {
+    int quad_order;     /* 2 (default): quadratic local interpolant; 1: linear */
+    int lines_per_block;/* 0 = automatic; else 1, 2, 4, 8 or 16 lines per CTA    */
+    int use_graphs;     /* 1 (default): replay the time loop as a CUDA graph    */
+} mol_options;
+
+typedef struct mol_ctx *mol_handle;
+
+/* Defaults for mol_options (quad_order 2, automatic tiling, graphs on). */
+void mol_default_options(mol_options *opt);
+
+/*
+ * Create a solver.  Host-only work (constants, coefficient expansion) plus the
+ * device workspace allocation; no kernel runs.
+ *   grid  : domain and points; every axis needs n >= 3 and n <= mol_max_line().
+ *   c, dt : wave speed and time step (> 0); alpha = beta/(c dt) (eq. L_def).
+ *   beta  : 0 < beta <= beta_max(P) (Theorem of Sec. 3.1, Table 1); beta <= 0
+ *           selects beta_max(P).  beta > beta_max(P) -> MOL_EUNSTABLE.
+ *   P     : 1..5, the scheme has order 2P.
+ *   bc    : boundary condition of every axis.
+ *   prec  : sweep arithmetic (see mol_prec).
+ *   opt   : NULL for defaults.
+ *   out   : receives the handle (NULL on failure).
+ * The handle owns its device workspace until mol_destroy.
+ */
+mol_status mol_create(const mol_grid *grid, double c, double dt, double beta, int P,
+                      mol_bc bc, mol_prec prec, const mol_options *opt, mol_handle *out);
+
+/* Free the workspace and the handle (waits for the handle's work). */
+mol_status mol_destroy(mol_handle h);
+
+/* Message of the last failed call on h (static text if h is NULL). */
+const char *mol_last_error(mol_handle h);
+
+/* beta_max(P): the first positive root of -sum_{p<=P} A_p(beta) = 4
+ * (eq. Stab_cond; Table 1).  Returns -1 for P outside 1..5. */
+double mol_beta_max(int P);
+
+/* Longest line (points per axis) the on-chip sweep supports for prec. */
+int64_t mol_max_line(mol_prec prec);
+
+/* Scalars of the solver: out[0] = alpha, out[1] = beta, out[2..4] = nu per
+ * axis (alpha * h_gamma), out[5..7] = d = e^{-nu} per axis. */
+mol_status mol_get_params(mol_handle h, double out[8]);
+
+/*
+ * out = D_axis^power v  (eq. LD_gam: D_gamma = 1 - L_gamma^{-1}, Sec. 3:
+ * powers by repeated application).  v, out: device float64 fields of the
+ * grid's size; they may not overlap.  axis in [0, ndim), 1 <= power <= 8.
+ */
+mol_status mol_apply_D(mol_handle h, const double *v, double *out, int axis, int power,
+                       void *stream);
+
+/* F = F[u], the spatial operator of the update (eq. update_P / Full_2D). */
+mol_status mol_apply_F(mol_handle h, const double *u, double *F, void *stream);
+
+/* Start value for zero initial velocity: u1 = u0 + F[u0]/2 (Sec. 3.2). */
+mol_status mol_start(mol_handle h, const double *u0, double *u1, void *stream);
+
+/*
+ * Advance (u_prev, u_cur) = (u^{n-1}, u^n) by nsteps >= 0 steps in place:
+ * on return u_prev = u^{n+nsteps-1}, u_cur = u^{n+nsteps}.  The two buffers
+ * are device float64 fields and may not overlap.  The library keeps the
+ * levels in its own workspace during the call.
+ */
+mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps, void *stream);
+
+/*
+ * End-to-end solve from HOST memory: copies u0 (host float64, grid size) to
+ * the device, forms u1 = mol_start(u0), advances to u^{nsteps} and copies it
+ * back into u_out (host float64).  Synchronous.  nsteps >= 1.
+ */
+mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t nsteps,
+                          void *stream);
+
+/* Wait for the handle's work on the stream; reports device-side errors. */
+mol_status mol_sync(mol_handle h, void *stream);
+
+/* Number of kernel launches this handle issued so far (all entry points). */
+int64_t mol_launch_count(mol_handle h);
+
+/*
+ * Per-pass timing, for benchmarks.  While enabled, mol_step launches every
+ * pass directly (no graph) between two CUDA events on the caller's stream
+ * and accumulates the device time of each pass.  Enabling (or re-enabling)
+ * clears the totals.
+ */
+mol_status mol_set_pass_timing(mol_handle h, int enable);
+
+/*
+ * Device time of the passes timed since timing was enabled (synchronises
+ * the streams used).  Index = axis of the pass (0 = x, the last pass of a
+ * step; 1 = y; 2 = z): total_ms[a] = summed duration, launches[a] = count.
+ * Arrays of length 3.
+ */
+mol_status mol_pass_times(mol_handle h, double total_ms[3], int64_t launches[3]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOLT_H */

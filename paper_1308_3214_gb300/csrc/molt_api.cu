@@ -1,0 +1,797 @@
+// molt_api.cu -- the C ABI of libmolt: constants, workspace, pass plans,
+// CUDA-graph time loop.  See include/molt.h for the contract.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "molt.h"
+#include "molt_internal.h"
+
+using namespace molt;
+
+namespace {
+
+constexpr int kMaxP = 5;
+constexpr int64_t kMaxLine = 8192;
+
+struct Level {
+    void *hi = nullptr;   // float32 hi plane (mixed) or the float64 field
+    void *lo = nullptr;   // float32 lo plane (mixed)
+};
+
+}  // namespace
+
+struct mol_ctx {
+    int ndim = 0;
+    int64_t n[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    double c = 1, dt = 1, beta = 0, alpha = 0;
+    int P = 1, bc = 0, prec = 0;
+    mol_options opt{};
+    int tbytes = 8;
+    int64_t N = 0;
+    double h[3] = {0, 0, 0}, nu[3] = {0, 0, 0};
+    AxisDev ax[3]{};
+    double *dpow64[3] = {nullptr, nullptr, nullptr};
+    float *dpow32[3] = {nullptr, nullptr, nullptr};
+    std::vector<double> f;       // expanded coefficients, (P+1)^ndim, x degree fastest
+    Level lev[3];
+    std::vector<void *> inter;   // intermediate planes (T)
+    double *io[2] = {nullptr, nullptr};
+    std::vector<void *> allocs;
+    int device = 0;
+    int num_sms = 152;
+    size_t smem_optin = 227 * 1024;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t launches = 0;
+    bool timing = false;                       // per-pass events (benchmarks)
+    std::vector<cudaEvent_t> ev_pool;          // reusable events
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (axis, (start, stop))
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+mol_status fail(mol_ctx *h, mol_status st, const std::string &msg)
+{
+    if (h) h->err = msg; else g_err = msg;
+    return st;
+}
+
+mol_status cuda_fail(mol_ctx *h, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, MOL_ECUDA, m);
+}
+
+#define CK(expr, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Scheme coefficients (Sec. 3, eq. update_P; Sec. 4, eq. Full_2D)
+// ---------------------------------------------------------------------------
+double binomial(int n, int k)
+{
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 0; i < k; ++i) r = r * (double)(n - i) / (double)(i + 1);
+    return r;
+}
+
+// weight of C^m D^{p-m}: (-1)^m 2 beta^{2m}/(2m)! binom(p-1, m-1)
+double term_weight(int p, int m, double beta)
+{
+    double f = 1.0;
+    for (int i = 2; i <= 2 * m; ++i) f *= i;
+    double sgn = (m % 2) ? -1.0 : 1.0;
+    return sgn * 2.0 * std::pow(beta, 2.0 * m) / f * binomial(p - 1, m - 1);
+}
+
+double stability_sum(int P, double beta)   // S(beta, 1) = -sum_p A_p(beta)
+{
+    double s = 0.0;
+    for (int p = 1; p <= P; ++p)
+        for (int m = 1; m <= p; ++m) s -= term_weight(p, m, beta);
+    return s;
+}
+
+double beta_max_of(int P)
+{
+    if (P < 1 || P > kMaxP) return -1.0;
+    double prev = 0.0;
+    for (int i = 1; i <= 4000; ++i) {
+        double b = 1e-3 * i;
+        if (stability_sum(P, b) >= 4.0) {
+            double lo = prev, hi = b;
+            for (int it = 0; it < 100; ++it) {
+                double mid = 0.5 * (lo + hi);
+                (stability_sum(P, mid) >= 4.0 ? hi : lo) = mid;
+            }
+            return 0.5 * (lo + hi);
+        }
+        prev = b;
+    }
+    return -1.0;
+}
+
+// Dense polynomial in up to three commuting variables D_x, D_y, D_z with
+// degree <= deg in each.
+struct Poly {
+    int nv, deg;
+    std::vector<double> c;
+    Poly(int nv_, int deg_) : nv(nv_), deg(deg_), c((size_t)std::pow(deg_ + 1, nv_), 0.0) {}
+    int idx(int i, int j, int k) const { return i + (deg + 1) * (j + (deg + 1) * k); }
+    static Poly one(int nv, int deg) { Poly p(nv, deg); p.c[0] = 1.0; return p; }
+    static Poly var(int nv, int deg, int a)
+    {
+        Poly p(nv, deg);
+        int e[3] = {0, 0, 0};
+        e[a] = 1;
+        p.c[p.idx(e[0], e[1], e[2])] = 1.0;
+        return p;
+    }
+};
+
+Poly padd(const Poly &a, const Poly &b, double sb = 1.0)
+{
+    Poly r = a;
+    for (size_t i = 0; i < r.c.size(); ++i) r.c[i] += sb * b.c[i];
+    return r;
+}
+
+bool pmul(const Poly &a, const Poly &b, Poly &r)
+{
+    r = Poly(a.nv, a.deg);
+    const int D = a.deg, K = a.nv >= 3 ? D : 0, J = a.nv >= 2 ? D : 0;
+    for (int k1 = 0; k1 <= K; ++k1) for (int j1 = 0; j1 <= J; ++j1) for (int i1 = 0; i1 <= D; ++i1) {
+        double x = a.c[a.idx(i1, j1, k1)];
+        if (x == 0.0) continue;
+        for (int k2 = 0; k2 <= K; ++k2) for (int j2 = 0; j2 <= J; ++j2) for (int i2 = 0; i2 <= D; ++i2) {
+            double y = b.c[b.idx(i2, j2, k2)];
+            if (y == 0.0) continue;
+            if (i1 + i2 > D || j1 + j2 > D || k1 + k2 > D) return false;
+            r.c[r.idx(i1 + i2, j1 + j2, k1 + k2)] += x * y;
+        }
+    }
+    return true;
+}
+
+// F = sum_p sum_m w_pm C^m D^{p-m} with C, D expressed through the per-axis
+// D_gamma: L_gamma^{-1} = 1 - D_gamma (eq. LD_gam), so
+//   C = sum_g D_g prod_{g' != g} (1 - D_g')   (eqs. C_def_ADI, C_def_ADI_3)
+//   D = 1 - prod_g (1 - D_g)                  (eqs. D_def_ADI, D_def_ADI_3)
+// (1D: C = D = D_x).  The per-axis operators act on different indices of a
+// tensor grid and commute, so F is a polynomial of degree <= P in each D_g.
+bool expand_coefficients(int ndim, int P, double beta, std::vector<double> &out)
+{
+    const int nv = ndim;
+    Poly one = Poly::one(nv, P);
+    std::vector<Poly> Dg, Lg;
+    for (int a = 0; a < nv; ++a) {
+        Dg.push_back(Poly::var(nv, P, a));
+        Lg.push_back(padd(one, Dg.back(), -1.0));
+    }
+    Poly C(nv, P), Dop(nv, P), tmp(nv, P);
+    Poly prodL = one;
+    for (int a = 0; a < nv; ++a) { if (!pmul(prodL, Lg[a], tmp)) return false; prodL = tmp; }
+    Dop = padd(one, prodL, -1.0);
+    for (int g = 0; g < nv; ++g) {
+        Poly t = Dg[g];
+        for (int a = 0; a < nv; ++a) if (a != g) { if (!pmul(t, Lg[a], tmp)) return false; t = tmp; }
+        C = padd(C, t);
+    }
+    Poly F(nv, P);
+    std::vector<Poly> Cp(P + 1, one), Dp(P + 1, one);
+    for (int k = 1; k <= P; ++k) {
+        if (!pmul(Cp[k - 1], C, Cp[k])) return false;
+        if (!pmul(Dp[k - 1], Dop, Dp[k])) return false;
+    }
+    for (int p = 1; p <= P; ++p)
+        for (int m = 1; m <= p; ++m) {
+            if (!pmul(Cp[m], Dp[p - m], tmp)) return false;
+            F = padd(F, tmp, term_weight(p, m, beta));
+        }
+    out = F.c;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Per-axis constants of the difference form of D (see molt_kernels.cuh)
+// ---------------------------------------------------------------------------
+// R = (1 - d)/nu^2 - (1 + d)/(2 nu): weight of the second difference in an
+// increment of the quadratic rule.  Series for small nu, where the two terms
+// cancel: R = sum_{k>=3} (-1)^{k+1} (2 - k) nu^{k-2} / (2 k!).
+double quad_R(double nu)
+{
+    if (nu < 0.25) {
+        double s = 0.0, pw = nu, fact = 6.0;   // k = 3: nu^1, 3!
+        for (int k = 3; k < 28; ++k) {
+            double sign = ((k + 1) % 2 == 0) ? 1.0 : -1.0;
+            s += sign * (2.0 - k) * pw / (2.0 * fact);
+            pw *= nu;
+            fact *= (k + 1);
+        }
+        return s;
+    }
+    double om = -std::expm1(-nu);          // 1 - d
+    double d = std::exp(-nu);
+    return (om - 0.5 * nu * (1.0 + d)) / (nu * nu);
+}
+
+void axis_constants(double nu, int64_t n, int bc, int quad, AxisDev &A)
+{
+    A.n = (int)n;
+    A.m = (int)std::max<int64_t>(2, (n + 31) / 32);
+    A.ms = (A.m % 2 == 0) ? A.m + 1 : A.m;
+    A.mmagic = (unsigned)(((1ull << 32) + (unsigned long long)A.m - 1) / (unsigned long long)A.m);
+    A.ls = 0;
+    A.d = std::exp(-nu);
+    const double khalf = -std::expm1(-2.0 * nu) / (2.0 * nu);   // K/2 = (1 - d^2)/(2 nu)
+    const double R = (quad >= 2) ? quad_R(nu) : 0.0;
+    A.c1 = -(khalf + R);
+    A.c2 = 0.5 * R * A.d;
+    if (bc == BC_PERIODIC) {
+        A.mu = std::exp(-nu * (double)n);
+        A.inv = -1.0 / std::expm1(-nu * (double)n);
+    } else {
+        A.mu = std::exp(-nu * (double)(n - 1));
+        A.inv = -1.0 / std::expm1(-2.0 * nu * (double)(n - 1));
+    }
+    for (int k = 0; k < 5; ++k) A.dm[k] = std::exp(-nu * (double)A.m * (double)(1 << k));
+}
+
+int ilog2(int W)
+{
+    int s = 0;
+    while ((1 << s) < W) ++s;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+mol_status dev_alloc(mol_ctx *h, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, MOL_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                       " bytes failed: " + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(*p);
+    return MOL_OK;
+}
+
+void free_all(mol_ctx *h)
+{
+    for (auto &u : h->ev_used) { h->ev_pool.push_back(u.second.first); h->ev_pool.push_back(u.second.second); }
+    h->ev_used.clear();
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->ev_pool.clear();
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+// ---------------------------------------------------------------------------
+// Passes
+// ---------------------------------------------------------------------------
+PassGeom geom_of(const mol_ctx *h, int axis)
+{
+    PassGeom G{};
+    int64_t stride = 1;
+    for (int a = 0; a < axis; ++a) stride *= h->n[a];
+    G.stride = stride;
+    G.inner = stride;
+    G.nlines = h->N / h->n[axis];
+    return G;
+}
+
+int choose_W(const mol_ctx *h, int axis, bool horner)
+{
+    const PassGeom G = geom_of(h, axis);
+    const bool contig = (axis == 0);
+    int W;
+    if (h->opt.lines_per_block > 0) {
+        W = h->opt.lines_per_block;
+    } else if (contig) {
+        W = horner ? (h->tbytes == 4 ? 8 : 4) : 8;
+    } else {
+        W = h->tbytes == 4 ? 16 : 8;
+    }
+    const AxisDev &A = h->ax[axis];
+    while (W > 1 && pass_smem_bytes(horner, h->tbytes, W, line_stride(A.ms, W, h->tbytes), A.n) > h->smem_optin) W >>= 1;
+    if (h->opt.lines_per_block <= 0) {
+        // keep at least one CTA per SM; the strided axis keeps >= 8 lines per
+        // row access when it can
+        const int floorW = contig ? 1 : (h->tbytes == 4 ? 8 : 4);
+        while (W > floorW && (G.nlines + W - 1) / W < h->num_sms) W >>= 1;
+        while (W > 1 && W > G.nlines) W >>= 1;
+    }
+    return W;
+}
+
+cudaEvent_t take_event(mol_ctx *h)
+{
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+mol_status timing_begin(mol_ctx *h, cudaStream_t s, cudaEvent_t *e0, cudaEvent_t *e1)
+{
+    if (!h->timing) return MOL_OK;
+    *e0 = take_event(h);
+    *e1 = take_event(h);
+    if (!*e0 || !*e1) return fail(h, MOL_ECUDA, "event creation failed");
+    CK(cudaEventRecord(*e0, s), "event record");
+    return MOL_OK;
+}
+
+mol_status timing_end(mol_ctx *h, cudaStream_t s, int axis, cudaEvent_t e0, cudaEvent_t e1)
+{
+    if (!h->timing) return MOL_OK;
+    CK(cudaEventRecord(e1, s), "event record");
+    h->ev_used.push_back({axis, {e0, e1}});
+    return MOL_OK;
+}
+
+mol_status run_powers(mol_ctx *h, int axis, const Level &u, int P, void *const *outs, cudaStream_t s)
+{
+    PassGeom G = geom_of(h, axis);
+    G.W = choose_W(h, axis, false);
+    G.wshift = ilog2(G.W);
+    AxisDev A = h->ax[axis];
+    A.ls = line_stride(A.ms, G.W, h->tbytes);
+    PowersParams p{};
+    p.P = P;
+    p.u_hi = u.hi;
+    p.u_lo = u.lo;
+    for (int k = 0; k < P && k < MAXG; ++k) p.out[k] = outs[k];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    mol_status st = timing_begin(h, s, &e0, &e1);
+    if (st != MOL_OK) return st;
+    CK(launch_powers(h->tbytes, h->bc, axis == 0, A, G, p, s), "powers pass launch");
+    h->launches++;
+    return timing_end(h, s, axis, e0, e1);
+}
+
+mol_status run_horner(mol_ctx *h, int axis, HornerParams &p, cudaStream_t s)
+{
+    PassGeom G = geom_of(h, axis);
+    G.W = choose_W(h, axis, true);
+    G.wshift = ilog2(G.W);
+    AxisDev A = h->ax[axis];
+    A.ls = line_stride(A.ms, G.W, h->tbytes);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    mol_status st = timing_begin(h, s, &e0, &e1);
+    if (st != MOL_OK) return st;
+    CK(launch_horner(h->tbytes, h->bc, axis == 0, A, G, p, s), "horner pass launch");
+    h->launches++;
+    return timing_end(h, s, axis, e0, e1);
+}
+
+double fco(const mol_ctx *h, int i, int j, int k)
+{
+    const int D = h->P + 1;
+    return h->f[(size_t)i + D * ((size_t)j + D * (size_t)k)];
+}
+
+// un = ea*u + eb*up + ec*F[u]  (the full pass plan of one step)
+mol_status run_update(mol_ctx *h, const Level &u, const Level &up, const Level &un,
+                      double ea, double eb, double ec, cudaStream_t s)
+{
+    const int P = h->P;
+    HornerParams hp{};
+    hp.P = P;
+    hp.epi = 1;
+    hp.ea = ea; hp.eb = eb; hp.ec = ec;
+    hp.u_hi = u.hi; hp.u_lo = u.lo;
+    hp.up_hi = up.hi; hp.up_lo = up.lo;
+    hp.un_hi = un.hi; hp.un_lo = un.lo;
+    hp.nout = 1;
+    mol_status st;
+    if (h->ndim == 1) {
+        // F = sum_p A_p D_x^p u: Horner in D_x, u entering every step
+        hp.ng = 0;
+        for (int t = 1; t <= P; ++t) hp.cu[0][t] = fco(h, t, 0, 0);
+        return run_horner(h, 0, hp, s);
+    }
+    if (h->ndim == 2) {
+        // y pass: Y_j = D_y^j u;  x pass: F = sum_i D_x^i (sum_j f_ij Y_j)
+        if ((st = run_powers(h, 1, u, P, h->inter.data(), s)) != MOL_OK) return st;
+        hp.ng = P;
+        for (int k = 0; k < P; ++k) hp.g[k] = h->inter[k];
+        for (int t = 0; t <= P; ++t) {
+            for (int k = 0; k < P; ++k) hp.coef[0][t][k] = fco(h, t, k + 1, 0);
+            hp.cu[0][t] = fco(h, t, 0, 0);
+        }
+        return run_horner(h, 0, hp, s);
+    }
+    // 3D: z pass: Z_k = D_z^k u;  y pass: G_i = sum_{(j,k) != 0} f_ijk D_y^j Z_k;
+    //     x pass: F = sum_i D_x^i (f_i00 u + G_i)
+    if ((st = run_powers(h, 2, u, P, h->inter.data(), s)) != MOL_OK) return st;
+    HornerParams yp{};
+    yp.P = P;
+    yp.epi = 0;
+    yp.u_hi = u.hi; yp.u_lo = u.lo;
+    yp.ng = P;
+    yp.nout = P + 1;
+    for (int k = 0; k < P; ++k) yp.g[k] = h->inter[k];
+    for (int o = 0; o <= P; ++o) {
+        yp.out[o] = h->inter[P + o];
+        for (int t = 0; t <= P; ++t) {
+            for (int k = 0; k < P; ++k) yp.coef[o][t][k] = fco(h, o, t, k + 1);
+            yp.cu[o][t] = fco(h, o, t, 0);
+        }
+    }
+    if ((st = run_horner(h, 1, yp, s)) != MOL_OK) return st;
+    hp.ng = P + 1;
+    for (int k = 0; k <= P; ++k) hp.g[k] = h->inter[P + k];
+    for (int t = 0; t <= P; ++t) {
+        for (int k = 0; k <= P; ++k) hp.coef[0][t][k] = (k == t) ? 1.0 : 0.0;
+        hp.cu[0][t] = fco(h, t, 0, 0);
+    }
+    return run_horner(h, 0, hp, s);
+}
+
+mol_status load_level(mol_ctx *h, const double *x, const Level &L, cudaStream_t s)
+{
+    if (h->prec == MOL_MIXED) {
+        CK(launch_to_pair(x, (float *)L.hi, (float *)L.lo, h->N, s), "level conversion");
+        h->launches++;
+    } else {
+        CK(cudaMemcpyAsync(L.hi, x, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, s), "level copy");
+    }
+    return MOL_OK;
+}
+
+mol_status store_level(mol_ctx *h, const Level &L, double *x, cudaStream_t s)
+{
+    if (h->prec == MOL_MIXED) {
+        CK(launch_from_pair((const float *)L.hi, (const float *)L.lo, x, h->N, s), "level conversion");
+        h->launches++;
+    } else {
+        CK(cudaMemcpyAsync(x, L.hi, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, s), "level copy");
+    }
+    return MOL_OK;
+}
+
+int passes_per_step(const mol_ctx *h) { return h->ndim; }
+
+// Capture three steps (one full rotation of the three level buffers) as a graph.
+mol_status build_graph(mol_ctx *h)
+{
+    if (h->gexec) return MOL_OK;
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream create");
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+    const int64_t before = h->launches;
+    mol_status st = MOL_OK;
+    for (int k = 0; k < 3 && st == MOL_OK; ++k)
+        st = run_update(h, h->lev[(k + 1) % 3], h->lev[k % 3], h->lev[(k + 2) % 3], 2.0, -1.0, 1.0, h->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    h->launches = before;
+    if (st != MOL_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph capture end");
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "graph instantiate"); }
+    return MOL_OK;
+}
+
+mol_status check_ptr(mol_ctx *h, const void *p, const char *name)
+{
+    if (!p) return fail(h, MOL_EINVAL, std::string(name) + " is NULL");
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(h, MOL_EINVAL, std::string(name) + ": not a CUDA pointer"); }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(h, MOL_EINVAL, std::string(name) + " must be device memory");
+    return MOL_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void mol_default_options(mol_options *opt)
+{
+    if (!opt) return;
+    opt->quad_order = 2;
+    opt->lines_per_block = 0;
+    opt->use_graphs = 1;
+}
+
+double mol_beta_max(int P) { return beta_max_of(P); }
+
+int64_t mol_max_line(mol_prec) { return kMaxLine; }
+
+const char *mol_last_error(mol_handle h)
+{
+    if (!h) return g_err.c_str();
+    return h->err.c_str();
+}
+
+mol_status mol_create(const mol_grid *grid, double c, double dt, double beta, int P, mol_bc bc,
+                      mol_prec prec, const mol_options *opt, mol_handle *out)
+{
+    mol_ctx *h = nullptr;
+    if (!out) return fail(nullptr, MOL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid) return fail(nullptr, MOL_EINVAL, "grid is NULL");
+    if (grid->ndim < 1 || grid->ndim > 3) return fail(nullptr, MOL_EINVAL, "ndim must be 1, 2 or 3");
+    if (P < 1 || P > kMaxP) return fail(nullptr, MOL_EINVAL, "P must be in 1..5");
+    if (!(c > 0) || !(dt > 0) || !std::isfinite(c) || !std::isfinite(dt)) return fail(nullptr, MOL_EINVAL, "c and dt must be positive");
+    if (bc != MOL_BC_PERIODIC && bc != MOL_BC_DIRICHLET) return fail(nullptr, MOL_EINVAL, "unknown boundary condition");
+    if (prec != MOL_FP64 && prec != MOL_MIXED) return fail(nullptr, MOL_EINVAL, "unknown precision");
+    mol_options o;
+    mol_default_options(&o);
+    if (opt) o = *opt;
+    if (o.quad_order != 1 && o.quad_order != 2) return fail(nullptr, MOL_EINVAL, "quad_order must be 1 or 2");
+    if (o.lines_per_block != 0 && (o.lines_per_block < 1 || o.lines_per_block > 16 ||
+                                   (o.lines_per_block & (o.lines_per_block - 1))))
+        return fail(nullptr, MOL_EINVAL, "lines_per_block must be 0 or a power of two <= 16");
+    for (int a = 0; a < grid->ndim; ++a) {
+        if (grid->n[a] < 3 || grid->n[a] > kMaxLine)
+            return fail(nullptr, MOL_EINVAL, "every axis needs 3 <= n <= " + std::to_string(kMaxLine));
+        if (!(grid->hi[a] > grid->lo[a])) return fail(nullptr, MOL_EINVAL, "hi must exceed lo on every axis");
+    }
+    const double bmax = beta_max_of(P);
+    if (beta <= 0) beta = bmax;
+    if (beta > bmax * (1.0 + 1e-12))
+        return fail(nullptr, MOL_EUNSTABLE, "beta above beta_max(P): the scheme is not A-stable");
+
+    h = new mol_ctx();
+    h->ndim = grid->ndim;
+    h->N = 1;
+    for (int a = 0; a < 3; ++a) {
+        h->n[a] = a < grid->ndim ? grid->n[a] : 1;
+        h->lo[a] = grid->lo[a];
+        h->hi[a] = grid->hi[a];
+        h->N *= h->n[a];
+    }
+    h->c = c; h->dt = dt; h->beta = beta; h->P = P; h->bc = bc; h->prec = prec; h->opt = o;
+    h->alpha = beta / (c * dt);                        // eq. L_def
+    h->tbytes = (prec == MOL_MIXED) ? 4 : 8;
+    mol_status st;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { st = cuda_fail(h, e, "cudaGetDevice"); goto bad; }
+    {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, h->device) == cudaSuccess && v > 0) h->num_sms = v;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) == cudaSuccess && v > 0)
+            h->smem_optin = (size_t)v;
+    }
+    if ((e = configure_kernels()) != cudaSuccess) { st = cuda_fail(h, e, "kernel attributes"); goto bad; }
+    if (!expand_coefficients(h->ndim, P, beta, h->f)) { st = fail(h, MOL_EINVAL, "coefficient expansion failed"); goto bad; }
+
+    for (int a = 0; a < h->ndim; ++a) {
+        const int64_t n = h->n[a];
+        h->h[a] = (h->hi[a] - h->lo[a]) / (double)(bc == MOL_BC_DIRICHLET ? n - 1 : n);
+        h->nu[a] = h->alpha * h->h[a];
+        axis_constants(h->nu[a], n, bc, o.quad_order, h->ax[a]);
+        std::vector<double> t64(n + 1);
+        std::vector<float> t32(n + 1);
+        for (int64_t j = 0; j <= n; ++j) {
+            t64[j] = std::exp(-h->nu[a] * (double)j);
+            t32[j] = (float)t64[j];
+        }
+        if ((st = dev_alloc(h, (void **)&h->dpow64[a], sizeof(double) * (n + 1))) != MOL_OK) goto bad;
+        if ((st = dev_alloc(h, (void **)&h->dpow32[a], sizeof(float) * (n + 1))) != MOL_OK) goto bad;
+        if ((e = cudaMemcpy(h->dpow64[a], t64.data(), sizeof(double) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(h->dpow32[a], t32.data(), sizeof(float) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            st = cuda_fail(h, e, "constant upload");
+            goto bad;
+        }
+        h->ax[a].dpow64 = h->dpow64[a];
+        h->ax[a].dpow32 = h->dpow32[a];
+    }
+    // levels: three rotating buffers
+    for (int k = 0; k < 3; ++k) {
+        if (prec == MOL_MIXED) {
+            if ((st = dev_alloc(h, &h->lev[k].hi, sizeof(float) * h->N)) != MOL_OK) goto bad;
+            if ((st = dev_alloc(h, &h->lev[k].lo, sizeof(float) * h->N)) != MOL_OK) goto bad;
+        } else {
+            if ((st = dev_alloc(h, &h->lev[k].hi, sizeof(double) * h->N)) != MOL_OK) goto bad;
+        }
+    }
+    {
+        // intermediate planes: 2D P (powers of D_y), 3D P + (P+1); at least one
+        // for mol_apply_D
+        int ninter = h->ndim == 2 ? P : (h->ndim == 3 ? 2 * P + 1 : 0);
+        if (ninter < 1) ninter = 1;
+        h->inter.assign(MAXG * 2, nullptr);
+        for (int k = 0; k < ninter; ++k)
+            if ((st = dev_alloc(h, &h->inter[k], (size_t)h->tbytes * h->N)) != MOL_OK) goto bad;
+    }
+    *out = h;
+    return MOL_OK;
+bad:
+    g_err = h->err;
+    free_all(h);
+    delete h;
+    return st;
+}
+
+mol_status mol_destroy(mol_handle h)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    return MOL_OK;
+}
+
+mol_status mol_get_params(mol_handle h, double out[8])
+{
+    if (!h || !out) return fail(h, MOL_EINVAL, "NULL argument");
+    out[0] = h->alpha;
+    out[1] = h->beta;
+    for (int a = 0; a < 3; ++a) {
+        out[2 + a] = a < h->ndim ? h->nu[a] : 0.0;
+        out[5 + a] = a < h->ndim ? h->ax[a].d : 0.0;
+    }
+    return MOL_OK;
+}
+
+mol_status mol_apply_D(mol_handle h, const double *v, double *outp, int axis, int power, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (axis < 0 || axis >= h->ndim) return fail(h, MOL_EINVAL, "axis out of range");
+    if (power < 1 || power > MAXG) return fail(h, MOL_EINVAL, "power must be in 1..8");
+    mol_status st;
+    if ((st = check_ptr(h, v, "v")) != MOL_OK || (st = check_ptr(h, outp, "out")) != MOL_OK) return st;
+    if (v == outp) return fail(h, MOL_EINVAL, "v and out must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    void *outs[MAXG] = {nullptr};
+    if (h->prec == MOL_MIXED) {
+        if ((st = load_level(h, v, h->lev[0], s)) != MOL_OK) return st;
+        outs[power - 1] = h->inter[0];
+        if ((st = run_powers(h, axis, h->lev[0], power, outs, s)) != MOL_OK) return st;
+        CK(launch_from_f32((const float *)h->inter[0], outp, h->N, s), "output conversion");
+        h->launches++;
+    } else {
+        Level L;
+        L.hi = (void *)v;
+        outs[power - 1] = outp;
+        if ((st = run_powers(h, axis, L, power, outs, s)) != MOL_OK) return st;
+    }
+    return MOL_OK;
+}
+
+mol_status mol_apply_F(mol_handle h, const double *u, double *F, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_status st;
+    if ((st = check_ptr(h, u, "u")) != MOL_OK || (st = check_ptr(h, F, "F")) != MOL_OK) return st;
+    if (u == F) return fail(h, MOL_EINVAL, "u and F must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->prec == MOL_MIXED) {
+        if ((st = load_level(h, u, h->lev[0], s)) != MOL_OK) return st;
+        if ((st = run_update(h, h->lev[0], h->lev[0], h->lev[1], 0.0, 0.0, 1.0, s)) != MOL_OK) return st;
+        return store_level(h, h->lev[1], F, s);
+    }
+    Level U, O;
+    U.hi = (void *)u;
+    O.hi = F;
+    return run_update(h, U, U, O, 0.0, 0.0, 1.0, s);
+}
+
+mol_status mol_start(mol_handle h, const double *u0, double *u1, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_status st;
+    if ((st = check_ptr(h, u0, "u0")) != MOL_OK || (st = check_ptr(h, u1, "u1")) != MOL_OK) return st;
+    if (u0 == u1) return fail(h, MOL_EINVAL, "u0 and u1 must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->prec == MOL_MIXED) {
+        if ((st = load_level(h, u0, h->lev[0], s)) != MOL_OK) return st;
+        if ((st = run_update(h, h->lev[0], h->lev[0], h->lev[1], 1.0, 0.0, 0.5, s)) != MOL_OK) return st;
+        return store_level(h, h->lev[1], u1, s);
+    }
+    Level U, O;
+    U.hi = (void *)u0;
+    O.hi = u1;
+    return run_update(h, U, U, O, 1.0, 0.0, 0.5, s);
+}
+
+mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(h, MOL_EINVAL, "nsteps must be >= 0");
+    mol_status st;
+    if ((st = check_ptr(h, u_prev, "u_prev")) != MOL_OK || (st = check_ptr(h, u_cur, "u_cur")) != MOL_OK) return st;
+    if (u_prev == u_cur) return fail(h, MOL_EINVAL, "u_prev and u_cur must not overlap");
+    if (nsteps == 0) return MOL_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = load_level(h, u_prev, h->lev[0], s)) != MOL_OK) return st;
+    if ((st = load_level(h, u_cur, h->lev[1], s)) != MOL_OK) return st;
+    int64_t done = 0;
+    if (h->opt.use_graphs && !h->timing && nsteps >= 3) {
+        if ((st = build_graph(h)) != MOL_OK) return st;
+        for (; done + 3 <= nsteps; done += 3) {
+            CK(cudaGraphLaunch(h->gexec, s), "graph launch");
+            h->launches += 3 * passes_per_step(h);
+        }
+    }
+    for (; done < nsteps; ++done) {
+        const int k = (int)(done % 3);
+        if ((st = run_update(h, h->lev[(k + 1) % 3], h->lev[k], h->lev[(k + 2) % 3], 2.0, -1.0, 1.0, s)) != MOL_OK)
+            return st;
+    }
+    const int k = (int)(nsteps % 3);
+    if ((st = store_level(h, h->lev[k], u_prev, s)) != MOL_OK) return st;
+    return store_level(h, h->lev[(k + 1) % 3], u_cur, s);
+}
+
+mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t nsteps, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (!u0 || !u_out) return fail(h, MOL_EINVAL, "NULL host buffer");
+    if (nsteps < 1) return fail(h, MOL_EINVAL, "nsteps must be >= 1");
+    mol_status st;
+    for (int k = 0; k < 2; ++k)
+        if (!h->io[k] && (st = dev_alloc(h, (void **)&h->io[k], sizeof(double) * h->N)) != MOL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(h->io[0], u0, sizeof(double) * h->N, cudaMemcpyHostToDevice, s), "host to device copy");
+    if ((st = mol_start(h, h->io[0], h->io[1], stream)) != MOL_OK) return st;
+    if ((st = mol_step(h, h->io[0], h->io[1], nsteps - 1, stream)) != MOL_OK) return st;
+    CK(cudaMemcpyAsync(u_out, h->io[1], sizeof(double) * h->N, cudaMemcpyDeviceToHost, s), "device to host copy");
+    CK(cudaStreamSynchronize(s), "solve");
+    return MOL_OK;
+}
+
+mol_status mol_sync(mol_handle h, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+    CK(cudaGetLastError(), "device error");
+    return MOL_OK;
+}
+
+int64_t mol_launch_count(mol_handle h) { return h ? h->launches : 0; }
+
+mol_status mol_set_pass_timing(mol_handle h, int enable)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    for (auto &u : h->ev_used) { h->ev_pool.push_back(u.second.first); h->ev_pool.push_back(u.second.second); }
+    h->ev_used.clear();
+    h->timing = enable != 0;
+    return MOL_OK;
+}
+
+mol_status mol_pass_times(mol_handle h, double total_ms[3], int64_t launches[3])
+{
+    if (!h || !total_ms || !launches) return fail(h, MOL_EINVAL, "NULL argument");
+    for (int a = 0; a < 3; ++a) { total_ms[a] = 0.0; launches[a] = 0; }
+    for (auto &u : h->ev_used) {
+        CK(cudaEventSynchronize(u.second.second), "event synchronize");
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, u.second.first, u.second.second), "event elapsed time");
+        total_ms[u.first] += ms;
+        launches[u.first] += 1;
+    }
+    return MOL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,26 @@
+// molt_internal.h -- launchers shared by the C-ABI layer and the kernel unit.
+#pragma once
+#include <cuda_runtime.h>
+#include "molt_kernels.cuh"
+
+namespace molt {
+
+// tbytes: 4 -> float32 sweeps (pair levels), 8 -> float64 throughout.
+cudaError_t launch_powers(int tbytes, int bc, bool contig, const AxisDev &A, const PassGeom &G,
+                          const PowersParams &p, cudaStream_t s);
+cudaError_t launch_horner(int tbytes, int bc, bool contig, const AxisDev &A, const PassGeom &G,
+                          const HornerParams &p, cudaStream_t s);
+cudaError_t launch_to_pair(const double *x, float *hi, float *lo, int64_t N, cudaStream_t s);
+cudaError_t launch_from_pair(const float *hi, const float *lo, double *x, int64_t N, cudaStream_t s);
+cudaError_t launch_from_f32(const float *f, double *x, int64_t N, cudaStream_t s);
+
+// Allow every pass kernel the largest dynamic shared-memory carve-out.
+cudaError_t configure_kernels();
+
+// Bytes of dynamic shared memory a pass needs.
+size_t pass_smem_bytes(bool horner, int tbytes, int W, int ls, int n);
+
+// Line stride in shared memory for W lines of segment stride ms.
+int line_stride(int ms, int W, int tbytes);
+
+}  // namespace molt

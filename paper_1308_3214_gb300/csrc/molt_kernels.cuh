@@ -1,0 +1,505 @@
+// molt_kernels.cuh -- device code of libmolt (sm_103a).
+//
+// One warp owns one grid line at a time.  The line sits in shared memory in
+// 32 lane segments of m = ceil(n/32) points; segment s starts at s*ms with ms
+// odd, so the 32 lanes walking their segments hit 32 different banks.  A CTA
+// holds W lines (W warps) and moves them between HBM and shared memory in
+// cooperative, coalesced phases: rows of W neighbouring lines for an axis with
+// a stride (y, z), whole rows for the contiguous axis (x).
+//
+// The operator D = 1 - L^{-1} of one line (Sec. 2, eqs. L_Inverse, D_def_1d)
+// is evaluated without forming L^{-1} v and subtracting it.  With the local
+// increments of Sec. 2 (quadratic interpolant, weights W0, W1, R) the two
+// exponential recurrences and the boundary terms give, for e = D v,
+//     (1 + d^2) e_j - d (e_{j-1} + e_{j+1}) = q_j,
+//     q_j = c1 s_j + c2 (s_{j-1} + s_{j+1}),  s_j = v_{j+1} - 2 v_j + v_{j-1},
+//     c1 = -(K/2 + R),  c2 = R d / 2,  K = (1 - d^2)/nu,
+// at every interior node, with e = 0 at Dirichlet end nodes (the corrected
+// L^{-1} returns v there) and s_0 := s_1, s_{n-1} := s_{n-2} (the one-sided
+// interpolants of the end cells); periodic lines wrap.  So e is a causal
+// recurrence y_j = d y_{j-1} + q_j followed by an anti-causal one
+// e_j = d e_{j+1} + y_j, plus the homogeneous terms A' d^j + B' d^{n-1-j} that
+// zero the Dirichlet ends (or the sums over periodic images).  This is the
+// same operator; it never cancels v - L^{-1}v, which is what lets the
+// sweeps run in float32 (D v is much smaller than v for smooth fields).
+//
+// Each recurrence runs as a chunked scan: every lane reduces its segment,
+// the lane carries combine in a 5-step shuffle scan with multipliers
+// d^{m 2^k}, and every lane re-scans its segment from its carry.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace molt {
+
+enum : int { BC_PERIODIC = 0, BC_DIRICHLET = 1 };
+
+// Constants of one axis (host computes them in float64).
+struct AxisDev {
+    int n;          // points on a line
+    int m;          // points per lane segment, ceil(n/32)
+    int ms;         // segment stride in shared memory (odd)
+    int ls;         // line stride in shared memory (elements)
+    unsigned mmagic;// ceil(2^32 / m): j / m == __umulhi(j, mmagic) for j < 2^16
+    double d;       // e^{-nu}, nu = alpha h
+    double c1, c2;  // q_j = c1 s_j + c2 (s_{j-1} + s_{j+1})
+    double mu;      // d^n (periodic) or d^{n-1} (Dirichlet)
+    double inv;     // 1/(1-mu) (periodic) or 1/(1-mu^2) (Dirichlet)
+    double dm[5];   // d^{m 2^k}, k = 0..4
+    const double *dpow64;  // d^j, j = 0..n
+    const float *dpow32;
+};
+
+// Where the lines of one pass live in global memory.
+struct PassGeom {
+    int64_t stride;  // element stride along the axis
+    int64_t inner;   // product of the extents of the axes before this one
+    int64_t nlines;  // number of lines
+    int W;           // lines (warps) per CTA, a power of two <= 16
+    int wshift;      // log2(W)
+};
+
+constexpr int MAXP = 6;     // P <= 5, Horner steps 0..P
+constexpr int MAXG = 8;     // input fields of a Horner pass
+
+struct PowersParams {
+    int P;                   // powers 1..P
+    const void *u_hi;        // T == float: hi plane; T == double: the field
+    const void *u_lo;        // T == float: lo plane
+    void *out[MAXG];         // out[p-1] receives D^p u (nullptr: not stored)
+};
+
+struct HornerParams {
+    int P;                   // D applications per output
+    int ng;                  // number of input fields g
+    int nout;                // outputs
+    const void *g[MAXG];
+    void *out[MAXG];         // epi == 0: out[o] receives output o (type T)
+    double coef[MAXP][MAXP][MAXG];  // [o][step][k]: weight of g_k in step
+    double cu[MAXP][MAXP];          // [o][step]: weight of u in step (>= 1)
+    int epi;                 // 0: store outputs; 1: level combination
+    double ea, eb, ec;       // level: u_next = ea u + eb u_prev + ec F
+    const void *u_hi, *u_lo;
+    const void *up_hi, *up_lo;
+    void *un_hi, *un_lo;
+};
+
+// ---------------------------------------------------------------------------
+// float32 pair ("hi + lo") arithmetic for the time levels.  The __f*_rn
+// intrinsics keep the compiler from contracting or re-associating.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// second difference of a pair field: ((u+ - u0) - (u0 - u-)) for hi and lo
+__device__ __forceinline__ float sdiff_pair(float hm, float h0, float hp, float lm, float l0, float lp)
+{
+    float dh = __fsub_rn(__fsub_rn(hp, h0), __fsub_rn(h0, hm));
+    float dl = __fsub_rn(__fsub_rn(lp, l0), __fsub_rn(l0, lm));
+    return __fadd_rn(dh, dl);
+}
+
+// u_next = a u + b up + c F with a, b, c in {0, +-1, 2, 0.5} (exact scalings)
+__device__ __forceinline__ void level_pair(float uh, float ul, float ph, float pl, float F,
+                                           float a, float b, float c, float &nh, float &nl)
+{
+    float s1, e1, s2, e2;
+    two_sum(__fmul_rn(a, uh), __fmul_rn(b, ph), s1, e1);
+    two_sum(s1, __fmul_rn(c, F), s2, e2);
+    float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fmul_rn(a, ul), __fmul_rn(b, pl)));
+    two_sum(s2, lo, nh, nl);
+}
+
+template <class T> __device__ __forceinline__ const T *dpow_of(const AxisDev &A);
+template <> __device__ __forceinline__ const float *dpow_of<float>(const AxisDev &A) { return A.dpow32; }
+template <> __device__ __forceinline__ const double *dpow_of<double>(const AxisDev &A) { return A.dpow64; }
+
+// point j (0 <= j < n) of a line -> shared-memory position
+__device__ __forceinline__ int spos_raw(int j, int m, int ms, unsigned mmagic)
+{
+    int s = (int)__umulhi((unsigned)j, mmagic);
+    return s * ms + (j - s * m);
+}
+
+// any j -> position, wrapping (periodic) or clamping (Dirichlet) into the line
+template <int BC>
+__device__ __forceinline__ int spos(int j, const AxisDev &A)
+{
+    const int n = A.n;
+    if (BC == BC_PERIODIC) { j %= n; if (j < 0) j += n; }
+    else { j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j); }
+    return spos_raw(j, A.m, A.ms, A.mmagic);
+}
+
+// ---------------------------------------------------------------------------
+// The line sweep: buf <- D z (in place), one warp.
+//   MODE 0: buf holds s already (first power of u; ends pre-duplicated).
+//   MODE 1: s = second difference of buf.
+//   MODE 2: s = second difference of buf + cu * r, r from rbuf.
+// dp points to the d^j table in shared memory.
+// ---------------------------------------------------------------------------
+template <class T, int MODE, int BC>
+__device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
+                        const T *__restrict__ dp, int lane)
+{
+    const int n = A.n, m = A.m, ms = A.ms;
+    const T d = (T)A.d, c1 = (T)A.c1, c2 = (T)A.c2;
+    const int a = lane * m;
+    const int b = min(a + m, n);
+    const int cnt = b > a ? b - a : 0;
+    T *seg = buf + lane * ms;
+    const T *rseg = rbuf + lane * ms;
+
+    // ---- halo values from neighbouring segments, read before any write ----
+    T h_l2 = 0, h_l1 = 0, h_r0 = 0, h_r1 = 0;
+    if (cnt > 0) {
+        h_l1 = buf[spos<BC>(a - 1, A)];
+        h_r0 = buf[spos<BC>(b, A)];
+        if (MODE != 0) {
+            h_l2 = buf[spos<BC>(a - 2, A)];
+            h_r1 = buf[spos<BC>(b + 1, A)];
+        }
+    }
+    __syncwarp();
+
+    // ---- q_j and the causal reduction of this segment ----
+    T E = 0;
+    if (cnt > 0) {
+        // raw s at a-1 and a, and the z window (MODE 1/2)
+        T sm1, s0, z0 = 0, zp1 = 0;
+        if (MODE == 0) {
+            sm1 = h_l1;
+            s0 = seg[0];
+        } else {
+            T zm1 = h_l1;
+            z0 = seg[0];
+            zp1 = cnt > 1 ? seg[1] : h_r0;
+            sm1 = (z0 - zm1) - (zm1 - h_l2);
+            s0 = (zp1 - z0) - (z0 - zm1);
+            if (MODE == 2) {
+                sm1 += cu * rbuf[spos<BC>(a - 1, A)];
+                s0 += cu * rseg[0];
+            }
+        }
+        for (int k = 0; k < cnt; ++k) {
+            const int j = a + k;
+            T sp1;
+            if (MODE == 0) {
+                sp1 = (k + 1 < cnt) ? seg[k + 1] : h_r0;
+            } else {
+                T zp2 = (k + 2 < cnt) ? seg[k + 2] : (k + 2 == cnt ? h_r0 : h_r1);
+                sp1 = (zp2 - zp1) - (zp1 - z0);
+                if (MODE == 2) sp1 += cu * ((k + 1 < cnt) ? rseg[k + 1] : rbuf[spos<BC>(b, A)]);
+                z0 = zp1;
+                zp1 = zp2;
+            }
+            T q;
+            if (BC == BC_DIRICHLET) {
+                T sl = (j - 1 < 1) ? s0 : sm1;
+                T sr = (j + 1 > n - 2) ? s0 : sp1;
+                q = (j == 0 || j == n - 1) ? (T)0 : c1 * s0 + c2 * (sl + sr);
+            } else {
+                q = c1 * s0 + c2 * (sm1 + sp1);
+            }
+            seg[k] = q;
+            E = d * E + q;
+            sm1 = s0;
+            s0 = sp1;
+        }
+    }
+
+    // ---- causal carries: y at a-1 ----
+    T x = E;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        T y = __shfl_up_sync(0xffffffffu, x, 1 << k);
+        if (lane >= (1 << k)) x += (T)A.dm[k] * y;
+    }
+    T excl = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) excl = 0;
+    const int Ld = (n - 1) / m;        // last lane holding data
+    T y = excl;
+    if (BC == BC_PERIODIC) {
+        // zero-inflow y_{n-1}: the last lane may hold fewer than m points
+        T tot = __shfl_sync(0xffffffffu, cnt > 0 ? dp[cnt] * excl + E : (T)0, Ld);
+        T y_m1 = tot * (T)A.inv;                        // y_{-1} over all images
+        if (cnt > 0) y += dp[a] * y_m1;
+    }
+
+    // ---- causal scan of the segment; anti-causal reduction ----
+    T ER = 0, pw = 1;
+    for (int k = 0; k < cnt; ++k) {
+        y = d * y + seg[k];
+        seg[k] = y;
+        ER += pw * y;
+        pw *= d;
+    }
+
+    // ---- anti-causal carries ----
+    T xb = ER;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        T t = __shfl_down_sync(0xffffffffu, xb, 1 << k);
+        if (lane + (1 << k) < 32) xb += (T)A.dm[k] * t;
+    }
+    T exclb = __shfl_down_sync(0xffffffffu, xb, 1);
+    if (lane == 31) exclb = 0;
+    const T e00 = __shfl_sync(0xffffffffu, xb, 0);     // zero-inflow e_0
+    T Z, Acoef = 0;
+    if (BC == BC_DIRICHLET) {
+        const T ylast = __shfl_sync(0xffffffffu, y, Ld);  // y_{n-1} = zero-inflow e_{n-1}
+        const T mu = (T)A.mu, inv = (T)A.inv;
+        Acoef = (mu * ylast - e00) * inv;               // A'
+        Z = (mu * e00 - ylast) * inv;                   // B'
+    } else {
+        Z = d * e00 * (T)A.inv;                         // d * e_n, e_n = e_0 over all images
+    }
+    // c = d * e_b including the inflow from the right end
+    T acc = d * exclb + (cnt > 0 ? dp[n - b] * Z : (T)0);
+    for (int k = cnt - 1; k >= 0; --k) {
+        T e = acc + seg[k];
+        acc = d * e;
+        if (BC == BC_DIRICHLET) e += Acoef * dp[a + k];
+        seg[k] = e;
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// CTA helpers
+// ---------------------------------------------------------------------------
+// Shared-memory carve-out of a pass CTA: `arrays` line buffers of W lines,
+// the d^j table (n+1 values) and the W line base offsets.
+struct SmemLayout {
+    size_t lines, dpow, lbase, total;
+};
+__host__ __device__ inline size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline SmemLayout smem_layout(int arrays, int W, int ls, int n, size_t tsize)
+{
+    SmemLayout L;
+    L.lines = 0;
+    L.dpow = round16((size_t)arrays * W * ls * tsize);
+    L.lbase = L.dpow + round16((size_t)(n + 1) * tsize);
+    L.total = L.lbase + round16((size_t)W * sizeof(int64_t));
+    return L;
+}
+__device__ __forceinline__ int64_t line_base(const PassGeom &G, int64_t L, int n)
+{
+    return (L % G.inner) + (L / G.inner) * G.inner * (int64_t)n;
+}
+
+// centre of the second difference used at point j (Dirichlet clamps into [1, n-2])
+template <int BC>
+__device__ __forceinline__ int sd_centre(int j, int n)
+{
+    if (BC == BC_DIRICHLET) return j < 1 ? 1 : (j > n - 2 ? n - 2 : j);
+    return j;
+}
+
+template <int BC>
+__device__ __forceinline__ int wrap(int j, int n)
+{
+    if (BC == BC_PERIODIC) { if (j < 0) j += n; else if (j >= n) j -= n; }
+    return j;
+}
+
+// second difference of u along the axis at point j (accurate: from the pair
+// levels for T = float, float64 for T = double)
+template <class T, int BC>
+__device__ __forceinline__ T u_sdiff(const void *uh, const void *ul, int64_t base, int64_t stride, int j, int n);
+
+template <>
+__device__ __forceinline__ float u_sdiff<float, BC_PERIODIC>(const void *uh, const void *ul, int64_t base, int64_t stride, int j, int n)
+{
+    const float *H = (const float *)uh, *Lo = (const float *)ul;
+    int jm = wrap<BC_PERIODIC>(j - 1, n), jp = wrap<BC_PERIODIC>(j + 1, n);
+    return sdiff_pair(H[base + jm * stride], H[base + j * stride], H[base + jp * stride],
+                      Lo[base + jm * stride], Lo[base + j * stride], Lo[base + jp * stride]);
+}
+template <>
+__device__ __forceinline__ float u_sdiff<float, BC_DIRICHLET>(const void *uh, const void *ul, int64_t base, int64_t stride, int j, int n)
+{
+    const float *H = (const float *)uh, *Lo = (const float *)ul;
+    int c = sd_centre<BC_DIRICHLET>(j, n);
+    return sdiff_pair(H[base + (c - 1) * stride], H[base + c * stride], H[base + (c + 1) * stride],
+                      Lo[base + (c - 1) * stride], Lo[base + c * stride], Lo[base + (c + 1) * stride]);
+}
+template <>
+__device__ __forceinline__ double u_sdiff<double, BC_PERIODIC>(const void *uh, const void *, int64_t base, int64_t stride, int j, int n)
+{
+    const double *U = (const double *)uh;
+    int jm = wrap<BC_PERIODIC>(j - 1, n), jp = wrap<BC_PERIODIC>(j + 1, n);
+    double u0 = U[base + j * stride];
+    return (U[base + jp * stride] - u0) - (u0 - U[base + jm * stride]);
+}
+template <>
+__device__ __forceinline__ double u_sdiff<double, BC_DIRICHLET>(const void *uh, const void *, int64_t base, int64_t stride, int j, int n)
+{
+    const double *U = (const double *)uh;
+    int c = sd_centre<BC_DIRICHLET>(j, n);
+    double u0 = U[base + c * stride];
+    return (U[base + (c + 1) * stride] - u0) - (u0 - U[base + (c - 1) * stride]);
+}
+
+// Iterate over the (line, point) pairs of the CTA's block in a coalesced order:
+// contiguous axis: a warp walks consecutive points of one line;
+// strided axis: a warp walks W neighbouring lines of consecutive rows.
+template <bool CONTIG, class F>
+__device__ __forceinline__ void for_block(const PassGeom &G, int n, int nl, F &&f)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    if (CONTIG) {
+        for (int l = 0; l < nl; ++l)
+            for (int j = tid; j < n; j += nth) f(l, j);
+    } else {
+        const int W = G.W;
+        const int l = tid & (W - 1);
+        const int rstep = nth >> G.wshift;
+        if (l < nl)
+            for (int j = tid >> G.wshift; j < n; j += rstep) f(l, j);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Powers pass: out[p-1] = D^p u along the axis, p = 1..P.
+// ---------------------------------------------------------------------------
+template <class T, int BC, bool CONTIG>
+__global__ void __launch_bounds__(512) k_powers(AxisDev A, PassGeom G, PowersParams prm)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = A.n, W = G.W;
+    const SmemLayout SL = smem_layout(1, W, A.ls, n, sizeof(T));
+    T *lines = reinterpret_cast<T *>(smem_raw + SL.lines);
+    T *dp = reinterpret_cast<T *>(smem_raw + SL.dpow);
+    int64_t *lbase = reinterpret_cast<int64_t *>(smem_raw + SL.lbase);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t L0 = (int64_t)blockIdx.x * W;
+    const int64_t rem = G.nlines - L0;
+    const int nl = rem < W ? (int)rem : W;
+
+    const T *dpg = dpow_of<T>(A);
+    for (int j = threadIdx.x; j <= n; j += blockDim.x) dp[j] = dpg[j];
+    if (threadIdx.x < W) lbase[threadIdx.x] = line_base(G, L0 + ((int)threadIdx.x < nl ? (int)threadIdx.x : nl - 1), n);
+    __syncthreads();
+
+    // s = second difference of u (Dirichlet ends duplicated)
+    for_block<CONTIG>(G, n, nl, [&](int l, int j) {
+        lines[(size_t)l * A.ls + spos_raw(j, A.m, A.ms, A.mmagic)] =
+            u_sdiff<T, BC>(prm.u_hi, prm.u_lo, lbase[l], G.stride, j, n);
+    });
+    __syncthreads();
+
+    T *mine = lines + (size_t)warp * A.ls;
+    for (int p = 1; p <= prm.P; ++p) {
+        if (warp < nl) {
+            if (p == 1) sweep_D<T, 0, BC>(mine, mine, (T)0, A, dp, lane);
+            else sweep_D<T, 1, BC>(mine, mine, (T)0, A, dp, lane);
+        }
+        if (prm.out[p - 1] != nullptr) {
+            __syncthreads();
+            T *o = reinterpret_cast<T *>(prm.out[p - 1]);
+            for_block<CONTIG>(G, n, nl, [&](int l, int j) {
+                o[lbase[l] + (int64_t)j * G.stride] = lines[(size_t)l * A.ls + spos_raw(j, A.m, A.ms, A.mmagic)];
+            });
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Horner pass: for each output o,
+//   X = 0;  for t = P..1:  X = D( sum_k coef[o][t][k] g_k + cu[o][t] u + X )
+//   out_o = sum_k coef[o][0][k] g_k + X
+// The u term enters through its accurate second difference r (kept on chip).
+// epi == 1: the single output F is combined into the next time level.
+// ---------------------------------------------------------------------------
+template <class T> struct LevelIO;
+template <> struct LevelIO<float> {
+    __device__ static void combine(const HornerParams &p, int64_t i, float F)
+    {
+        const float *uh = (const float *)p.u_hi, *ul = (const float *)p.u_lo;
+        float ph = 0.f, pl = 0.f;
+        if (p.eb != 0.0) { ph = ((const float *)p.up_hi)[i]; pl = ((const float *)p.up_lo)[i]; }
+        float nh, nl;
+        level_pair(uh[i], ul[i], ph, pl, F, (float)p.ea, (float)p.eb, (float)p.ec, nh, nl);
+        ((float *)p.un_hi)[i] = nh;
+        ((float *)p.un_lo)[i] = nl;
+    }
+};
+template <> struct LevelIO<double> {
+    __device__ static void combine(const HornerParams &p, int64_t i, double F)
+    {
+        double v = p.ea * ((const double *)p.u_hi)[i] + p.ec * F;
+        if (p.eb != 0.0) v += p.eb * ((const double *)p.up_hi)[i];
+        ((double *)p.un_hi)[i] = v;
+    }
+};
+
+template <class T, int BC, bool CONTIG>
+__global__ void __launch_bounds__(512) k_horner(AxisDev A, PassGeom G, HornerParams prm)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = A.n, W = G.W;
+    const SmemLayout SL = smem_layout(2, W, A.ls, n, sizeof(T));
+    T *lines = reinterpret_cast<T *>(smem_raw + SL.lines);
+    T *rlines = lines + (size_t)W * A.ls;
+    T *dp = reinterpret_cast<T *>(smem_raw + SL.dpow);
+    int64_t *lbase = reinterpret_cast<int64_t *>(smem_raw + SL.lbase);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t L0 = (int64_t)blockIdx.x * W;
+    const int64_t rem = G.nlines - L0;
+    const int nl = rem < W ? (int)rem : W;
+
+    const T *dpg = dpow_of<T>(A);
+    for (int j = threadIdx.x; j <= n; j += blockDim.x) dp[j] = dpg[j];
+    if (threadIdx.x < W) lbase[threadIdx.x] = line_base(G, L0 + ((int)threadIdx.x < nl ? (int)threadIdx.x : nl - 1), n);
+    __syncthreads();
+
+    // r = accurate second difference of u along this axis
+    for_block<CONTIG>(G, n, nl, [&](int l, int j) {
+        rlines[(size_t)l * A.ls + spos_raw(j, A.m, A.ms, A.mmagic)] =
+            u_sdiff<T, BC>(prm.u_hi, prm.u_lo, lbase[l], G.stride, j, n);
+    });
+
+    T *mine = lines + (size_t)warp * A.ls;
+    const T *rmine = rlines + (size_t)warp * A.ls;
+    for (int o = 0; o < prm.nout; ++o) {
+        for (int t = prm.P; t >= 0; --t) {
+            // buf = (t == P ? 0 : buf) + sum_k coef g_k
+            const bool first = (t == prm.P);
+            for_block<CONTIG>(G, n, nl, [&](int l, int j) {
+                const int64_t gi = lbase[l] + (int64_t)j * G.stride;
+                const size_t si = (size_t)l * A.ls + spos_raw(j, A.m, A.ms, A.mmagic);
+                T acc = first ? (T)0 : lines[si];
+                for (int k = 0; k < prm.ng; ++k) {
+                    const double w = prm.coef[o][t][k];
+                    if (w != 0.0) acc += (T)w * reinterpret_cast<const T *>(prm.g[k])[gi];
+                }
+                if (t > 0) {
+                    lines[si] = acc;
+                } else if (prm.epi == 0) {
+                    reinterpret_cast<T *>(prm.out[o])[gi] = acc;
+                } else {
+                    LevelIO<T>::combine(prm, gi, acc);
+                }
+            });
+            __syncthreads();
+            if (t > 0 && warp < nl)
+                sweep_D<T, 2, BC>(mine, rmine, (T)prm.cu[o][t], A, dp, lane);
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Level conversions (float64 <-> pair) and plain copies
+// ---------------------------------------------------------------------------
+__global__ void k_to_pair(const double *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo, int64_t N);
+__global__ void k_from_pair(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ x, int64_t N);
+__global__ void k_from_f32(const float *__restrict__ f, double *__restrict__ x, int64_t N);
+
+}  // namespace molt

@@ -1,0 +1,128 @@
+// molt_passes.cu -- instantiation and launch of the pass kernels.
+#include "molt_internal.h"
+
+namespace molt {
+
+__global__ void k_to_pair(const double *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo, int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = x[i];
+        float h = __double2float_rn(v);
+        hi[i] = h;
+        lo[i] = __double2float_rn(v - (double)h);
+    }
+}
+
+__global__ void k_from_pair(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ x, int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (double)hi[i] + (double)lo[i];
+}
+
+__global__ void k_from_f32(const float *__restrict__ f, double *__restrict__ x, int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (double)f[i];
+}
+
+static int elementwise_grid(int64_t N)
+{
+    int64_t g = (N + 255) / 256;
+    return (int)(g < 152 * 16 ? (g < 1 ? 1 : g) : 152 * 16);
+}
+
+cudaError_t launch_to_pair(const double *x, float *hi, float *lo, int64_t N, cudaStream_t s)
+{
+    k_to_pair<<<elementwise_grid(N), 256, 0, s>>>(x, hi, lo, N);
+    return cudaGetLastError();
+}
+cudaError_t launch_from_pair(const float *hi, const float *lo, double *x, int64_t N, cudaStream_t s)
+{
+    k_from_pair<<<elementwise_grid(N), 256, 0, s>>>(hi, lo, x, N);
+    return cudaGetLastError();
+}
+cudaError_t launch_from_f32(const float *f, double *x, int64_t N, cudaStream_t s)
+{
+    k_from_f32<<<elementwise_grid(N), 256, 0, s>>>(f, x, N);
+    return cudaGetLastError();
+}
+
+int line_stride(int ms, int W, int tbytes)
+{
+    // bank-conflict-free transposing stores: ls == 32/W (mod 32) for 4-byte
+    // words, ls == 16/W (mod 16) in 8-byte words
+    int base = 32 * ms;
+    if (tbytes == 4) return base + (W <= 32 ? 32 / W : 1);
+    return base + (W <= 16 ? 16 / W : 1);
+}
+
+size_t pass_smem_bytes(bool horner, int tbytes, int W, int ls, int n)
+{
+    return smem_layout(horner ? 2 : 1, W, ls, n, (size_t)tbytes).total;
+}
+
+template <class T, int BC, bool CONTIG>
+static cudaError_t set_attr()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_powers<T, BC, CONTIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_horner<T, BC, CONTIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+cudaError_t configure_kernels()
+{
+    cudaError_t e;
+#define MOLT_SET(T, BC, C) if ((e = set_attr<T, BC, C>()) != cudaSuccess) return e;
+    MOLT_SET(float, BC_PERIODIC, true) MOLT_SET(float, BC_PERIODIC, false)
+    MOLT_SET(float, BC_DIRICHLET, true) MOLT_SET(float, BC_DIRICHLET, false)
+    MOLT_SET(double, BC_PERIODIC, true) MOLT_SET(double, BC_PERIODIC, false)
+    MOLT_SET(double, BC_DIRICHLET, true) MOLT_SET(double, BC_DIRICHLET, false)
+#undef MOLT_SET
+    return cudaSuccess;
+}
+
+template <class T, int BC, bool CONTIG>
+static cudaError_t run_powers(const AxisDev &A, const PassGeom &G, const PowersParams &p, cudaStream_t s)
+{
+    const size_t smem = pass_smem_bytes(false, sizeof(T), G.W, A.ls, A.n);
+    const int64_t grid = (G.nlines + G.W - 1) / G.W;
+    k_powers<T, BC, CONTIG><<<(unsigned)grid, 32 * G.W, smem, s>>>(A, G, p);
+    return cudaGetLastError();
+}
+
+template <class T, int BC, bool CONTIG>
+static cudaError_t run_horner(const AxisDev &A, const PassGeom &G, const HornerParams &p, cudaStream_t s)
+{
+    const size_t smem = pass_smem_bytes(true, sizeof(T), G.W, A.ls, A.n);
+    const int64_t grid = (G.nlines + G.W - 1) / G.W;
+    k_horner<T, BC, CONTIG><<<(unsigned)grid, 32 * G.W, smem, s>>>(A, G, p);
+    return cudaGetLastError();
+}
+
+#define MOLT_DISPATCH(FN, ...)                                                                   \
+    do {                                                                                         \
+        if (tbytes == 4) {                                                                       \
+            if (bc == BC_PERIODIC) return contig ? FN<float, BC_PERIODIC, true>(__VA_ARGS__)     \
+                                                 : FN<float, BC_PERIODIC, false>(__VA_ARGS__);   \
+            return contig ? FN<float, BC_DIRICHLET, true>(__VA_ARGS__)                           \
+                          : FN<float, BC_DIRICHLET, false>(__VA_ARGS__);                         \
+        }                                                                                        \
+        if (bc == BC_PERIODIC) return contig ? FN<double, BC_PERIODIC, true>(__VA_ARGS__)        \
+                                             : FN<double, BC_PERIODIC, false>(__VA_ARGS__);      \
+        return contig ? FN<double, BC_DIRICHLET, true>(__VA_ARGS__)                              \
+                      : FN<double, BC_DIRICHLET, false>(__VA_ARGS__);                            \
+    } while (0)
+
+cudaError_t launch_powers(int tbytes, int bc, bool contig, const AxisDev &A, const PassGeom &G,
+                          const PowersParams &p, cudaStream_t s)
+{
+    MOLT_DISPATCH(run_powers, A, G, p, s);
+}
+
+cudaError_t launch_horner(int tbytes, int bc, bool contig, const AxisDev &A, const PassGeom &G,
+                          const HornerParams &p, cudaStream_t s)
+{
+    MOLT_DISPATCH(run_horner, A, G, p, s);
+}
+
+}  // namespace molt

@@ -1,0 +1,233 @@
+"""ctypes binding of libmolt (include/molt.h): argument marshalling only.
+
+Every operation runs in the CUDA library; torch is used for device memory
+and streams.  Importing this module does not need a GPU; creating a
+``Solver`` does, and fails loudly if the library or the GPU is missing.
+
+Fields are torch float64 tensors on the GPU, C-contiguous with shape
+``(nx,)``, ``(ny, nx)`` or ``(nz, ny, nx)`` (x fastest), matching the
+library's ``index = x + nx*(y + ny*z)``.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+from typing import Sequence
+
+import numpy as np
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "_build" / "libmolt.so"
+
+MOL_OK, MOL_EINVAL, MOL_ENOMEM, MOL_ECUDA, MOL_EUNSTABLE, MOL_ETIMEOUT = range(6)
+STATUS_NAMES = {0: "MOL_OK", 1: "MOL_EINVAL", 2: "MOL_ENOMEM", 3: "MOL_ECUDA", 4: "MOL_EUNSTABLE",
+                5: "MOL_ETIMEOUT"}
+BC = {"periodic": 0, "dirichlet": 1}
+PREC = {"fp64": 0, "mixed": 1}
+
+# Every symbol include/molt.h declares.
+EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error", "mol_beta_max",
+           "mol_max_line", "mol_get_params", "mol_apply_D", "mol_apply_F", "mol_start", "mol_step",
+           "mol_solve_host", "mol_sync", "mol_launch_count", "mol_set_pass_timing", "mol_pass_times"]
+
+
+class MolError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mol_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3)]
+
+
+class mol_options(ctypes.Structure):
+    _fields_ = [("quad_order", ctypes.c_int), ("lines_per_block", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: Path | None = None):
+    """Load libmolt.so (building it first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        from . import build as _build
+        _build.build()
+    if not p.exists():
+        raise RuntimeError(f"libmolt.so not found at {p}; run `python -m paper_1308_3214_gb300.build`")
+    lib = ctypes.CDLL(str(p))
+    vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+    I, D = ctypes.c_int, ctypes.c_double
+    lib.mol_default_options.argtypes = [ctypes.POINTER(mol_options)]
+    lib.mol_create.argtypes = [ctypes.POINTER(mol_grid), D, D, D, I, I, I, ctypes.POINTER(mol_options),
+                               ctypes.POINTER(vp)]
+    lib.mol_destroy.argtypes = [vp]
+    lib.mol_last_error.argtypes = [vp]
+    lib.mol_last_error.restype = ctypes.c_char_p
+    lib.mol_beta_max.argtypes = [I]
+    lib.mol_beta_max.restype = D
+    lib.mol_max_line.argtypes = [I]
+    lib.mol_max_line.restype = i64
+    lib.mol_get_params.argtypes = [vp, dp]
+    lib.mol_apply_D.argtypes = [vp, vp, vp, I, I, vp]
+    lib.mol_apply_F.argtypes = [vp, vp, vp, vp]
+    lib.mol_start.argtypes = [vp, vp, vp, vp]
+    lib.mol_step.argtypes = [vp, vp, vp, i64, vp]
+    lib.mol_solve_host.argtypes = [vp, dp, dp, i64, vp]
+    lib.mol_sync.argtypes = [vp, vp]
+    lib.mol_set_pass_timing.argtypes = [vp, I]
+    lib.mol_pass_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
+    lib.mol_launch_count.argtypes = [vp]
+    lib.mol_launch_count.restype = i64
+    for name in EXPORTS:
+        if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
+                        "mol_launch_count"):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def beta_max(P: int) -> float:
+    return load_library().mol_beta_max(int(P))
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Solver:
+    """One MOL^T problem: grid, c, dt, beta, P, boundary condition, precision.
+
+    ``shape`` is given in array order (nz, ny, nx) like the fields; ``lo`` and
+    ``hi`` likewise.  ``beta <= 0`` selects beta_max(P)."""
+
+    def __init__(self, shape: Sequence[int], dt: float, P: int, bc: str = "dirichlet",
+                 prec: str = "mixed", c: float = 1.0, beta: float = 0.0,
+                 lo: Sequence[float] | None = None, hi: Sequence[float] | None = None,
+                 quad_order: int = 2, lines_per_block: int = 0, use_graphs: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libmolt needs a CUDA GPU")
+        self.lib = load_library()
+        self.shape = tuple(int(s) for s in shape)
+        nd = len(self.shape)
+        if lo is None:
+            lo = [0.0] * nd
+        if hi is None:
+            hi = [1.0] * nd
+        g = mol_grid()
+        g.ndim = nd
+        for a in range(3):
+            g.n[a] = self.shape[nd - 1 - a] if a < nd else 1
+            g.lo[a] = float(lo[nd - 1 - a]) if a < nd else 0.0
+            g.hi[a] = float(hi[nd - 1 - a]) if a < nd else 1.0
+        opt = mol_options(int(quad_order), int(lines_per_block), 1 if use_graphs else 0)
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        st = self.lib.mol_create(ctypes.byref(g), float(c), float(dt), float(beta), int(P), BC[bc],
+                                 PREC[prec], ctypes.byref(opt), ctypes.byref(h))
+        if st != MOL_OK:
+            raise MolError(st, self.lib.mol_last_error(None).decode())
+        self.h = h
+        self.P, self.bc, self.prec, self.dt, self.c = int(P), bc, prec, float(dt), float(c)
+        prm = (ctypes.c_double * 8)()
+        self._check(self.lib.mol_get_params(self.h, prm))
+        self.alpha, self.beta = prm[0], prm[1]
+        self.nu = tuple(prm[2 + a] for a in range(nd))      # x first
+        self.d = tuple(prm[5 + a] for a in range(nd))
+
+    # ------------------------------------------------------------------
+    def _check(self, st: int):
+        if st != MOL_OK:
+            raise MolError(st, self.lib.mol_last_error(self.h).decode())
+
+    def _field(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA float64 tensor")
+        if tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with shape {self.shape}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def empty(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+    # ------------------------------------------------------------------
+    def apply_D(self, v, axis: int, power: int = 1, out=None, stream=None):
+        """D_axis^power v; axis 0 is x (the last array dimension)."""
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_apply_D(self.h, self._field(v, "v"), self._field(out, "out"), int(axis),
+                                         int(power), ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def apply_F(self, u, out=None, stream=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_apply_F(self.h, self._field(u, "u"), self._field(out, "F"),
+                                         ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def start(self, u0, out=None, stream=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_start(self.h, self._field(u0, "u0"), self._field(out, "u1"),
+                                       ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def step(self, u_prev, u_cur, nsteps: int, stream=None):
+        """Advance (u_prev, u_cur) in place by nsteps."""
+        self._check(self.lib.mol_step(self.h, self._field(u_prev, "u_prev"), self._field(u_cur, "u_cur"),
+                                      int(nsteps), ctypes.c_void_p(_stream_ptr(stream))))
+        return u_prev, u_cur
+
+    def solve_host(self, u0: np.ndarray, nsteps: int, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """u^{nsteps} from host u0 (zero initial velocity), host result."""
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        if u0.shape != self.shape:
+            raise ValueError(f"u0 must have shape {self.shape}")
+        out = np.empty_like(u0) if out is None else out
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.mol_solve_host(self.h, u0.ctypes.data_as(dp), out.ctypes.data_as(dp), int(nsteps),
+                                            ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def sync(self, stream=None):
+        self._check(self.lib.mol_sync(self.h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def set_pass_timing(self, enable: bool = True):
+        self._check(self.lib.mol_set_pass_timing(self.h, 1 if enable else 0))
+
+    def pass_times(self):
+        """{axis: (total_ms, launches)} of the passes timed since enabling."""
+        ms = (ctypes.c_double * 3)()
+        cnt = (ctypes.c_int64 * 3)()
+        self._check(self.lib.mol_pass_times(self.h, ms, cnt))
+        return {a: (ms[a], int(cnt[a])) for a in range(3) if cnt[a] > 0}
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.mol_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mol_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

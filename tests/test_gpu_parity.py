@@ -1,0 +1,251 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2 over the whole field):
+  * FP64 path: 1e-12.
+  * Mixed path: float32 sweeps.  One application of D is a float32 scan whose
+    rounding error grows with the number of terms that matter,
+    ~1/(1 - d) = 1/(1 - e^{-nu}); a power D^p compounds p of them and F adds
+    P terms.  The bound used is 64 * eps32 * (1 + 1/(1 - d)) * p, eps32 = 2^-24
+    (measured errors sit 10-100x below it).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1308_3214_gb300 import molt, workloads
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def mixed_tol(d_min, p=1):
+    return 64 * EPS32 * (1.0 + 1.0 / (1.0 - d_min)) * p
+
+
+def tol_for(prec, solver, p=1):
+    if prec == "fp64":
+        return 1e-12
+    return mixed_tol(max(solver.d), p)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def field(shape, seed, bc):
+    u = workloads.random_field(shape, seed)
+    if bc == "dirichlet":
+        for ax in range(u.ndim):
+            sl = [slice(None)] * u.ndim
+            sl[ax] = 0
+            u[tuple(sl)] = 0
+            sl[ax] = -1
+            u[tuple(sl)] = 0
+    return u
+
+
+def smooth_field(shape, seed, bc):
+    """A band-limited field (a few low modes), so that D u << u."""
+    rng = np.random.default_rng(seed)
+    grids = np.meshgrid(*[np.linspace(0, 1, s) for s in shape], indexing="ij")
+    u = np.zeros(shape)
+    for _ in range(4):
+        k = rng.integers(1, 4, size=len(shape))
+        term = rng.normal()
+        for g, kk in zip(grids, k):
+            term = term * np.sin(np.pi * kk * g) if bc == "dirichlet" else term * np.cos(2 * np.pi * kk * g)
+        u += term
+    return u
+
+
+def make(shape, dt, P, bc, prec, quad=2, **kw):
+    lo = [0.0] * len(shape)
+    hi = [1.0] * len(shape)
+    return molt.Solver(shape, dt=dt, P=P, bc=bc, prec=prec, lo=lo, hi=hi, quad_order=quad, **kw)
+
+
+def spacing(n, bc):
+    return 1.0 / (n - 1) if bc == "dirichlet" else 1.0 / n
+
+
+# ---------------------------------------------------------------------------
+# one application of D_gamma^p
+# ---------------------------------------------------------------------------
+CASES_D = [
+    ((257,), 0.004), ((3,), 0.3), ((33,), 0.02), ((64,), 0.01), ((1000,), 0.0005),
+    ((37, 70), 0.01), ((130, 5), 0.02), ((9, 13, 21), 0.03), ((16, 3, 40), 0.05),
+]
+
+
+@pytest.mark.parametrize("shape, dt", CASES_D)
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("quad", [2, 1])
+def test_apply_D_matches_oracle(shape, dt, bc, prec, quad):
+    s = make(shape, dt, 2, bc, prec, quad)
+    v = field(shape, 11, bc)
+    vd = dev(v)
+    for axis in range(len(shape)):
+        for power in (1, 2, 3):
+            got = s.apply_D(vd, axis, power).cpu().numpy()
+            ref = oracle.D_axis(v, axis, s.nu[axis], bc, quad, power=power)
+            err = rel_l2(got, ref)
+            assert err <= tol_for(prec, s, power), (axis, power, err)
+
+
+@pytest.mark.parametrize("cfl", [0.05, 0.5, 2.0, 10.0, 100.0])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_apply_D_extreme_decay(cfl, bc):
+    """nu = beta/CFL from 24 (d ~ 1e-11) down to 0.012 (d ~ 0.99)."""
+    n = 300
+    h = spacing(n, bc)
+    dt = cfl * h
+    for prec in ("fp64", "mixed"):
+        s = make((n,), dt, 1, bc, prec)
+        v = smooth_field((n,), 3, bc) + 0.1 * field((n,), 4, bc)
+        got = s.apply_D(dev(v), 0, 1).cpu().numpy()
+        ref = oracle.D_axis(v, 0, s.nu[0], bc, 2)
+        assert rel_l2(got, ref) <= tol_for(prec, s), (prec, rel_l2(got, ref))
+
+
+def test_apply_D_longest_line():
+    n = int(molt.load_library().mol_max_line(0))
+    for prec in ("fp64", "mixed"):
+        s = make((n,), 0.5 / n, 1, "dirichlet", prec)
+        v = field((n,), 5, "dirichlet")
+        got = s.apply_D(dev(v), 0, 1).cpu().numpy()
+        ref = oracle.D_axis(v, 0, s.nu[0], "dirichlet", 2)
+        assert rel_l2(got, ref) <= tol_for(prec, s)
+
+
+# ---------------------------------------------------------------------------
+# the full spatial operator F, the start value and time stepping
+# ---------------------------------------------------------------------------
+CASES_F = [((301,), 1, 0.004), ((256,), 3, 0.01), ((70, 41), 1, 0.02), ((48, 66), 3, 0.015),
+           ((33, 35), 2, 0.05), ((11, 14, 17), 1, 0.06), ((12, 10, 19), 2, 0.04)]
+
+
+@pytest.mark.parametrize("shape, P, dt", CASES_F)
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_apply_F_matches_oracle(shape, P, dt, bc, prec):
+    s = make(shape, dt, P, bc, prec)
+    u = field(shape, 21, bc)
+    got = s.apply_F(dev(u)).cpu().numpy()
+    ref = oracle.F(u, s.nu, P, s.beta, bc)
+    assert rel_l2(got, ref) <= tol_for(prec, s, 2 * P), rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_start_matches_oracle(prec):
+    shape, P, bc = (40, 52), 2, "dirichlet"
+    s = make(shape, 0.03, P, bc, prec)
+    u0 = smooth_field(shape, 2, bc)
+    got = s.start(dev(u0)).cpu().numpy()
+    ref = oracle.start(u0, s.nu, P, s.beta, bc)
+    assert rel_l2(got, ref) <= (1e-12 if prec == "fp64" else 1e-9)
+
+
+STEP_CASES = [((256,), 1, "periodic", 200, 0.036816), ((130,), 5, "dirichlet", 60, 0.02),
+              ((96, 130), 3, "dirichlet", 30, 0.0157), ((64, 64), 2, "periodic", 25, 0.03),
+              ((20, 24, 28), 2, "periodic", 10, 0.05), ((18, 22, 15), 1, "dirichlet", 12, 0.07)]
+
+
+@pytest.mark.parametrize("shape, P, bc, nsteps, dt", STEP_CASES)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_time_stepping_matches_oracle(shape, P, bc, nsteps, dt, prec):
+    s = make(shape, dt, P, bc, prec)
+    u0 = smooth_field(shape, 7, bc) + 0.05 * field(shape, 8, bc)
+    u1 = oracle.start(u0, s.nu, P, s.beta, bc)
+    up, uc = dev(u0), dev(u1)
+    s.step(up, uc, nsteps)
+    rp, rc = oracle.run(u0, u1, nsteps, s.nu, P, s.beta, bc)
+    tol = 1e-12 if prec == "fp64" else 1e-7
+    assert rel_l2(uc.cpu().numpy(), rc) <= tol
+    assert rel_l2(up.cpu().numpy(), rp) <= tol
+
+
+def test_graph_and_direct_launches_agree_bitwise():
+    shape, P = (40, 50), 3
+    u0 = smooth_field(shape, 9, "dirichlet")
+    outs = []
+    for graphs in (True, False):
+        s = make(shape, 0.02, P, "dirichlet", "mixed", use_graphs=graphs)
+        up, uc = dev(u0), s.start(dev(u0))
+        s.step(up, uc, 17)
+        outs.append(uc.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_launch_count_reports_kernels():
+    s = make((32, 40), 0.02, 2, "dirichlet", "mixed")
+    u = dev(field((32, 40), 1, "dirichlet"))
+    before = s.launches
+    s.step(u.clone(), u.clone(), 6)
+    # 2 conversions in, 2 passes per step, 2 conversions out
+    assert s.launches - before == 2 + 2 * 6 + 2
+
+
+def test_solve_host_matches_device_path():
+    shape, P = (48, 40), 2
+    u0 = smooth_field(shape, 12, "dirichlet")
+    s = make(shape, 0.02, P, "dirichlet", "fp64")
+    host = s.solve_host(u0, 9)
+    up = dev(u0)
+    uc = s.start(up)
+    s.step(up, uc, 8)
+    assert np.array_equal(host, uc.cpu().numpy())
+
+
+def test_bad_pointer_rejected():
+    s = make((16, 16), 0.02, 1, "dirichlet", "fp64")
+    import ctypes
+    host = np.zeros((16, 16))
+    st = s.lib.mol_apply_F(s.h, ctypes.c_void_p(host.ctypes.data), ctypes.c_void_p(host.ctypes.data), None)
+    assert st == molt.MOL_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, in the launch configuration the benchmark times
+# ---------------------------------------------------------------------------
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_2d_gaussian_two_steps(prec):
+    n, P, cfl = 2048, 3, 2.0
+    h = 1.0 / (n - 1)
+    dt = cfl * h
+    s = make((n, n), dt, P, "dirichlet", prec)
+    u0 = workloads.gaussian_2d(n, seed=1002)
+    u1 = oracle.start(u0, s.nu, P, s.beta, "dirichlet")
+    up, uc = dev(u0), dev(u1)
+    s.step(up, uc, 2)
+    _, rc = oracle.run(u0, u1, 2, s.nu, P, s.beta, "dirichlet")
+    err = rel_l2(uc.cpu().numpy(), rc)
+    assert err <= (1e-12 if prec == "fp64" else 1e-8), err
+
+
+@pytest.mark.slow
+def test_full_size_3d_fourier_one_step():
+    n, P, cfl = 256, 2, 1.5
+    h = 2 * np.pi / n
+    dt = cfl * h
+    u0, _ = workloads.fourier_3d(n, seed=1003)
+    box = dict(lo=[0.0] * 3, hi=[2 * np.pi] * 3)
+    s64 = molt.Solver((n, n, n), dt=dt, P=P, bc="periodic", prec="fp64", **box)
+    ref = oracle.F(u0, s64.nu, P, s64.beta, "periodic")
+    got = s64.apply_F(dev(u0)).cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-12, rel_l2(got, ref)
+    s64.close()
+    smx = molt.Solver((n, n, n), dt=dt, P=P, bc="periodic", prec="mixed", **box)
+    got = smx.apply_F(dev(u0)).cpu().numpy()
+    assert rel_l2(got, ref) <= tol_for("mixed", smx, 2 * P), rel_l2(got, ref)
