@@ -1,12 +1,17 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances (relative L2 over the whole field):
-  * FP64 path: 1e-12.
-  * Mixed path: float32 sweeps.  One application of D is a float32 scan whose
-    rounding error grows with the number of terms that matter,
-    ~1/(1 - d) = 1/(1 - e^{-nu}); a power D^p compounds p of them and F adds
-    P terms.  The bound used is 64 * eps32 * (1 + 1/(1 - d)) * p, eps32 = 2^-24
-    (measured errors sit 10-100x below it).
+  * FP64 path: 1e-12, or the oracle's own cancellation floor where that is
+    larger: the oracle forms D v = v - L^{-1} v, which loses about
+    eps64 * |v| / |D v| (relevant only at extreme decay, nu > 20).
+  * Mixed path, one operator: float32 sweeps.  A recurrence with decay d sums
+    about 1/(1 - d) terms that matter, so one application of D carries a
+    relative error of order eps32 * (1 + 1/(1 - d)); a power D^p compounds p
+    of them and F (2P sweeps) 2P.  Bound: 16 * eps32 * (1 + 1/(1 - d)) * p
+    (measured ratios to the unscaled estimate stay below 1.1).
+  * Mixed path, n steps: every step adds the float32 error of F to the level,
+    so the bound is 8 * eps32 * (1 + 1/(1 - d)) * 2P * sum_k |F_k| / |u_n|,
+    with the F_k of the oracle's own run (measured ratios stay below 1.3).
 """
 import numpy as np
 import pytest
@@ -28,14 +33,22 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
 
 
-def mixed_tol(d_min, p=1):
-    return 64 * EPS32 * (1.0 + 1.0 / (1.0 - d_min)) * p
+EPS64 = 2.0 ** -52
 
 
-def tol_for(prec, solver, p=1):
+def mixed_tol(d_max, p=1):
+    return 16 * EPS32 * (1.0 + 1.0 / (1.0 - d_max)) * p
+
+
+def tol_for(prec, solver, p=1, cond=1.0):
+    """cond = |input| / |output| of the oracle's last cancellation."""
     if prec == "fp64":
-        return 1e-12
+        return max(1e-12, 64 * EPS64 * cond)
     return mixed_tol(max(solver.d), p)
+
+
+def cond_of(v, ref):
+    return float(np.linalg.norm(v) / max(np.linalg.norm(ref), 1e-300))
 
 
 def dev(x):
@@ -100,7 +113,7 @@ def test_apply_D_matches_oracle(shape, dt, bc, prec, quad):
             got = s.apply_D(vd, axis, power).cpu().numpy()
             ref = oracle.D_axis(v, axis, s.nu[axis], bc, quad, power=power)
             err = rel_l2(got, ref)
-            assert err <= tol_for(prec, s, power), (axis, power, err)
+            assert err <= tol_for(prec, s, power, cond_of(v, ref)), (axis, power, err)
 
 
 @pytest.mark.parametrize("cfl", [0.05, 0.5, 2.0, 10.0, 100.0])
@@ -115,7 +128,7 @@ def test_apply_D_extreme_decay(cfl, bc):
         v = smooth_field((n,), 3, bc) + 0.1 * field((n,), 4, bc)
         got = s.apply_D(dev(v), 0, 1).cpu().numpy()
         ref = oracle.D_axis(v, 0, s.nu[0], bc, 2)
-        assert rel_l2(got, ref) <= tol_for(prec, s), (prec, rel_l2(got, ref))
+        assert rel_l2(got, ref) <= tol_for(prec, s, cond=cond_of(v, ref)), (prec, rel_l2(got, ref))
 
 
 def test_apply_D_longest_line():
@@ -153,7 +166,9 @@ def test_start_matches_oracle(prec):
     u0 = smooth_field(shape, 2, bc)
     got = s.start(dev(u0)).cpu().numpy()
     ref = oracle.start(u0, s.nu, P, s.beta, bc)
-    assert rel_l2(got, ref) <= (1e-12 if prec == "fp64" else 1e-9)
+    F = oracle.F(u0, s.nu, P, s.beta, bc)
+    tol = 1e-12 if prec == "fp64" else tol_for(prec, s, 2 * P) * 0.5 * np.linalg.norm(F) / np.linalg.norm(ref)
+    assert rel_l2(got, ref) <= tol
 
 
 STEP_CASES = [((256,), 1, "periodic", 200, 0.036816), ((130,), 5, "dirichlet", 60, 0.02),
@@ -170,7 +185,14 @@ def test_time_stepping_matches_oracle(shape, P, bc, nsteps, dt, prec):
     up, uc = dev(u0), dev(u1)
     s.step(up, uc, nsteps)
     rp, rc = oracle.run(u0, u1, nsteps, s.nu, P, s.beta, bc)
-    tol = 1e-12 if prec == "fp64" else 1e-7
+    tol = 1e-12
+    if prec == "mixed":
+        Fsum, a, b = 0.0, u0, u1
+        for _ in range(nsteps):
+            F = oracle.F(b, s.nu, P, s.beta, bc)
+            Fsum += np.linalg.norm(F)
+            a, b = b, 2 * b - a + F
+        tol = 8 * EPS32 * (1 + 1 / (1 - max(s.d))) * 2 * P * Fsum / np.linalg.norm(rc)
     assert rel_l2(uc.cpu().numpy(), rc) <= tol
     assert rel_l2(up.cpu().numpy(), rp) <= tol
 
