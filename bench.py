@@ -40,7 +40,7 @@ METRIC = "point-updates/s"
 PEAKS_FILE = ROOT / "MEASURED_PEAKS.json"
 TRAFFIC_FILE = ROOT / "profiles" / "ncu_traffic.json"
 KERNEL_SOURCES = [ROOT / "paper_1308_3214_gb300" / "csrc" / f for f in
-                  ("molt_kernels.cuh", "molt_passes.cu", "molt_api.cu")]
+                  ("molt_kernels.cuh", "molt_regs.cuh", "molt_passes.cu", "molt_regs.cu", "molt_api.cu")]
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -357,7 +357,9 @@ def main():
     alg_bytes = bpp[dom_axis] * N
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
     peak, peak_kind = read_peak()
-    kernel_name = {0: "k_horner<x>", 1: "k_powers<y>" if len(shape) == 2 else "k_horner<y>", 2: "k_powers<z>"}[dom_axis]
+    kernel_name = {0: "k_contig (x: Horner + level update)",
+                   1: "k_strided (y: powers of D_y)" if len(shape) == 2 else "k_strided (y: Horner, P+1 outputs)",
+                   2: "k_strided (z: powers of D_z)"}[dom_axis]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": read_traffic(dom_axis, spec["name"], args.prec),
                 "kernel": kernel_name, "peak_kind": f"{peak_kind} hbm_gbs (copy)",

@@ -37,6 +37,11 @@ struct mol_ctx {
     double *dpow64[3] = {nullptr, nullptr, nullptr};
     float *dpow32[3] = {nullptr, nullptr, nullptr};
     std::vector<double> f;       // expanded coefficients, (P+1)^ndim, x degree fastest
+    HornerParams xtpl{}, ytpl{}; // coefficient templates of the Horner passes
+    double *coef_dev = nullptr;  // the same tables on the device: x coef, x cu, y coef, y cu
+    size_t off_xc = 0, off_xu = 0, off_yc = 0, off_yu = 0;
+    double dmr[4][5] = {};       // d^{R 2^k} for register segments R = 8, 16, 32, 64 (per axis below)
+    double dmr_ax[3][4][5] = {};
     Level lev[3];
     std::vector<void *> inter;   // intermediate planes (T)
     double *io[2] = {nullptr, nullptr};
@@ -352,39 +357,89 @@ mol_status timing_end(mol_ctx *h, cudaStream_t s, int axis, cudaEvent_t e0, cuda
     return MOL_OK;
 }
 
-mol_status run_powers(mol_ctx *h, int axis, const Level &u, int P, void *const *outs, cudaStream_t s)
+int rpt_index(int rpt) { return rpt == 8 ? 0 : rpt == 16 ? 1 : rpt == 32 ? 2 : 3; }
+
+AxisDev regs_axis(const mol_ctx *h, int axis, int rpt)
 {
-    PassGeom G = geom_of(h, axis);
-    G.W = choose_W(h, axis, false);
-    G.wshift = ilog2(G.W);
     AxisDev A = h->ax[axis];
-    A.ls = line_stride(A.ms, G.W, h->tbytes);
-    PowersParams p{};
-    p.P = P;
-    p.u_hi = u.hi;
-    p.u_lo = u.lo;
-    for (int k = 0; k < P && k < MAXG; ++k) p.out[k] = outs[k];
+    for (int k = 0; k < 5; ++k) A.dm[k] = h->dmr_ax[axis][rpt_index(rpt)][k];
+    return A;
+}
+
+LineSet lineset_of(const mol_ctx *h, int axis)
+{
+    const PassGeom G = geom_of(h, axis);
+    LineSet L{};
+    L.stride = G.stride;
+    L.inner = G.inner;
+    L.nlines = G.nlines;
+    L.S = L.K = 1;
+    return L;
+}
+
+// Launch one pass program: the register-resident kernel when the line length
+// and boundary condition allow it, else the shared-memory kernels.
+mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersParams *pp, const HornerParams *hp,
+                       cudaStream_t s)
+{
+    const int n = (int)h->n[axis];
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     mol_status st = timing_begin(h, s, &e0, &e1);
     if (st != MOL_OK) return st;
-    CK(launch_powers(h->tbytes, h->bc, axis == 0, A, G, p, s), "powers pass launch");
+    int rpt = 0, S = 0, K = 0;
+    cudaError_t e;
+    if (axis == 0 && regs_contig_plan(h->tbytes, h->bc, n, &rpt)) {
+        e = launch_contig(h->tbytes, h->bc, rpt, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
+    } else if (axis > 0 && regs_strided_plan(h->tbytes, h->bc, n, &rpt, &S, &K)) {
+        LineSet L = lineset_of(h, axis);
+        L.S = S;
+        L.K = K;
+        e = launch_strided(h->tbytes, h->bc, rpt, regs_axis(h, axis, rpt), L, pr, s);
+    } else {
+        PassGeom G = geom_of(h, axis);
+        G.W = choose_W(h, axis, hp != nullptr);
+        G.wshift = ilog2(G.W);
+        AxisDev A = h->ax[axis];
+        A.ls = line_stride(A.ms, G.W, h->tbytes);
+        e = hp ? launch_horner(h->tbytes, h->bc, axis == 0, A, G, *hp, s)
+               : launch_powers(h->tbytes, h->bc, axis == 0, A, G, *pp, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "pass launch");
     h->launches++;
     return timing_end(h, s, axis, e0, e1);
 }
 
-mol_status run_horner(mol_ctx *h, int axis, HornerParams &p, cudaStream_t s)
+mol_status run_powers(mol_ctx *h, int axis, const Level &u, int P, void *const *outs, cudaStream_t s)
 {
-    PassGeom G = geom_of(h, axis);
-    G.W = choose_W(h, axis, true);
-    G.wshift = ilog2(G.W);
-    AxisDev A = h->ax[axis];
-    A.ls = line_stride(A.ms, G.W, h->tbytes);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    mol_status st = timing_begin(h, s, &e0, &e1);
-    if (st != MOL_OK) return st;
-    CK(launch_horner(h->tbytes, h->bc, axis == 0, A, G, p, s), "horner pass launch");
-    h->launches++;
-    return timing_end(h, s, axis, e0, e1);
+    PowersParams p{};
+    p.P = P;
+    p.u_hi = u.hi;
+    p.u_lo = u.lo;
+    ProgParams pr{};
+    pr.mode = 0;
+    pr.P = P;
+    pr.u_hi = u.hi;
+    pr.u_lo = u.lo;
+    for (int k = 0; k < P && k < MAXG; ++k) p.out[k] = pr.out[k] = outs[k];
+    return run_program(h, axis, pr, &p, nullptr, s);
+}
+
+// hp carries the fields; dcoef / dcu are the device copies of its tables
+mol_status run_horner(mol_ctx *h, int axis, HornerParams &hp, const double *dcoef, const double *dcu, cudaStream_t s)
+{
+    ProgParams pr{};
+    pr.mode = 1;
+    pr.P = hp.P;
+    pr.ng = hp.ng;
+    pr.nout = hp.nout;
+    for (int k = 0; k < MAXG; ++k) { pr.g[k] = hp.g[k]; pr.out[k] = hp.out[k]; }
+    pr.coef = dcoef;
+    pr.cu = dcu;
+    pr.epi = hp.epi;
+    pr.ea = hp.ea; pr.eb = hp.eb; pr.ec = hp.ec;
+    pr.u_hi = hp.u_hi; pr.u_lo = hp.u_lo; pr.up_hi = hp.up_hi; pr.up_lo = hp.up_lo;
+    pr.un_hi = hp.un_hi; pr.un_lo = hp.un_lo;
+    return run_program(h, axis, pr, nullptr, &hp, s);
 }
 
 double fco(const mol_ctx *h, int i, int j, int k)
@@ -393,62 +448,87 @@ double fco(const mol_ctx *h, int i, int j, int k)
     return h->f[(size_t)i + D * ((size_t)j + D * (size_t)k)];
 }
 
+// Coefficient tables of the Horner passes (Sec. 4, eq. Full_2D expanded in
+// the per-axis D_gamma):
+//   1D x pass:  F = sum_t D_x^t (f_t u)                       (cu only)
+//   2D x pass:  F = sum_t D_x^t (sum_j f_tj D_y^j u)           g_k = D_y^{k+1} u
+//   3D y pass:  G_o = sum_t D_y^t (sum_k f_otk D_z^k u), (t,k) != (0,0)
+//   3D x pass:  F = sum_t D_x^t (f_t00 u + G_t)
+void build_tables(mol_ctx *h)
+{
+    const int P = h->P;
+    HornerParams &x = h->xtpl;
+    x = HornerParams{};
+    x.P = P;
+    x.nout = 1;
+    x.epi = 1;
+    if (h->ndim == 1) {
+        x.ng = 0;
+        for (int t = 1; t <= P; ++t) x.cu[0][t] = fco(h, t, 0, 0);
+    } else if (h->ndim == 2) {
+        x.ng = P;
+        for (int t = 0; t <= P; ++t) {
+            for (int k = 0; k < P; ++k) x.coef[0][t][k] = fco(h, t, k + 1, 0);
+            x.cu[0][t] = fco(h, t, 0, 0);
+        }
+    } else {
+        x.ng = P + 1;
+        for (int t = 0; t <= P; ++t) {
+            for (int k = 0; k <= P; ++k) x.coef[0][t][k] = (k == t) ? 1.0 : 0.0;
+            x.cu[0][t] = fco(h, t, 0, 0);
+        }
+        HornerParams &y = h->ytpl;
+        y = HornerParams{};
+        y.P = P;
+        y.epi = 0;
+        y.ng = P;
+        y.nout = P + 1;
+        for (int o = 0; o <= P; ++o)
+            for (int t = 0; t <= P; ++t) {
+                for (int k = 0; k < P; ++k) y.coef[o][t][k] = fco(h, o, t, k + 1);
+                y.cu[o][t] = fco(h, o, t, 0);
+            }
+    }
+}
+
+void flatten(const HornerParams &hp, std::vector<double> &coef, std::vector<double> &cu)
+{
+    coef.clear();
+    cu.clear();
+    for (int o = 0; o < std::max(hp.nout, 1); ++o)
+        for (int t = 0; t <= hp.P; ++t) {
+            for (int k = 0; k < hp.ng; ++k) coef.push_back(hp.coef[o][t][k]);
+            cu.push_back(hp.cu[o][t]);
+        }
+    if (coef.empty()) coef.push_back(0.0);
+}
+
 // un = ea*u + eb*up + ec*F[u]  (the full pass plan of one step)
 mol_status run_update(mol_ctx *h, const Level &u, const Level &up, const Level &un,
                       double ea, double eb, double ec, cudaStream_t s)
 {
     const int P = h->P;
-    HornerParams hp{};
-    hp.P = P;
-    hp.epi = 1;
+    HornerParams hp = h->xtpl;
     hp.ea = ea; hp.eb = eb; hp.ec = ec;
     hp.u_hi = u.hi; hp.u_lo = u.lo;
     hp.up_hi = up.hi; hp.up_lo = up.lo;
     hp.un_hi = un.hi; hp.un_lo = un.lo;
-    hp.nout = 1;
+    const double *xc = h->coef_dev + h->off_xc, *xu = h->coef_dev + h->off_xu;
     mol_status st;
-    if (h->ndim == 1) {
-        // F = sum_p A_p D_x^p u: Horner in D_x, u entering every step
-        hp.ng = 0;
-        for (int t = 1; t <= P; ++t) hp.cu[0][t] = fco(h, t, 0, 0);
-        return run_horner(h, 0, hp, s);
-    }
+    if (h->ndim == 1) return run_horner(h, 0, hp, xc, xu, s);
     if (h->ndim == 2) {
-        // y pass: Y_j = D_y^j u;  x pass: F = sum_i D_x^i (sum_j f_ij Y_j)
         if ((st = run_powers(h, 1, u, P, h->inter.data(), s)) != MOL_OK) return st;
-        hp.ng = P;
         for (int k = 0; k < P; ++k) hp.g[k] = h->inter[k];
-        for (int t = 0; t <= P; ++t) {
-            for (int k = 0; k < P; ++k) hp.coef[0][t][k] = fco(h, t, k + 1, 0);
-            hp.cu[0][t] = fco(h, t, 0, 0);
-        }
-        return run_horner(h, 0, hp, s);
+        return run_horner(h, 0, hp, xc, xu, s);
     }
-    // 3D: z pass: Z_k = D_z^k u;  y pass: G_i = sum_{(j,k) != 0} f_ijk D_y^j Z_k;
-    //     x pass: F = sum_i D_x^i (f_i00 u + G_i)
     if ((st = run_powers(h, 2, u, P, h->inter.data(), s)) != MOL_OK) return st;
-    HornerParams yp{};
-    yp.P = P;
-    yp.epi = 0;
+    HornerParams yp = h->ytpl;
     yp.u_hi = u.hi; yp.u_lo = u.lo;
-    yp.ng = P;
-    yp.nout = P + 1;
     for (int k = 0; k < P; ++k) yp.g[k] = h->inter[k];
-    for (int o = 0; o <= P; ++o) {
-        yp.out[o] = h->inter[P + o];
-        for (int t = 0; t <= P; ++t) {
-            for (int k = 0; k < P; ++k) yp.coef[o][t][k] = fco(h, o, t, k + 1);
-            yp.cu[o][t] = fco(h, o, t, 0);
-        }
-    }
-    if ((st = run_horner(h, 1, yp, s)) != MOL_OK) return st;
-    hp.ng = P + 1;
+    for (int o = 0; o <= P; ++o) yp.out[o] = h->inter[P + o];
+    if ((st = run_horner(h, 1, yp, h->coef_dev + h->off_yc, h->coef_dev + h->off_yu, s)) != MOL_OK) return st;
     for (int k = 0; k <= P; ++k) hp.g[k] = h->inter[P + k];
-    for (int t = 0; t <= P; ++t) {
-        for (int k = 0; k <= P; ++k) hp.coef[0][t][k] = (k == t) ? 1.0 : 0.0;
-        hp.cu[0][t] = fco(h, t, 0, 0);
-    }
-    return run_horner(h, 0, hp, s);
+    return run_horner(h, 0, hp, xc, xu, s);
 }
 
 mol_status load_level(mol_ctx *h, const double *x, const Level &L, cudaStream_t s)
@@ -583,6 +663,7 @@ mol_status mol_create(const mol_grid *grid, double c, double dt, double beta, in
             h->smem_optin = (size_t)v;
     }
     if ((e = configure_kernels()) != cudaSuccess) { st = cuda_fail(h, e, "kernel attributes"); goto bad; }
+    if ((e = configure_regs_kernels()) != cudaSuccess) { st = cuda_fail(h, e, "kernel attributes"); goto bad; }
     if (!expand_coefficients(h->ndim, P, beta, h->f)) { st = fail(h, MOL_EINVAL, "coefficient expansion failed"); goto bad; }
 
     for (int a = 0; a < h->ndim; ++a) {
@@ -605,6 +686,29 @@ mol_status mol_create(const mol_grid *grid, double c, double dt, double beta, in
         }
         h->ax[a].dpow64 = h->dpow64[a];
         h->ax[a].dpow32 = h->dpow32[a];
+        for (int r = 0; r < 4; ++r)
+            for (int k = 0; k < 5; ++k)
+                h->dmr_ax[a][r][k] = std::exp(-h->nu[a] * (double)(8 << r) * (double)(1 << k));
+    }
+    {
+        build_tables(h);
+        std::vector<double> xc, xu, yc, yu, all;
+        flatten(h->xtpl, xc, xu);
+        if (h->ndim == 3) flatten(h->ytpl, yc, yu);
+        else { yc.assign(1, 0.0); yu.assign(1, 0.0); }
+        h->off_xc = 0;
+        h->off_xu = xc.size();
+        h->off_yc = h->off_xu + xu.size();
+        h->off_yu = h->off_yc + yc.size();
+        all = xc;
+        all.insert(all.end(), xu.begin(), xu.end());
+        all.insert(all.end(), yc.begin(), yc.end());
+        all.insert(all.end(), yu.begin(), yu.end());
+        if ((st = dev_alloc(h, (void **)&h->coef_dev, sizeof(double) * all.size())) != MOL_OK) goto bad;
+        if ((e = cudaMemcpy(h->coef_dev, all.data(), sizeof(double) * all.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            st = cuda_fail(h, e, "coefficient upload");
+            goto bad;
+        }
     }
     // levels: three rotating buffers
     for (int k = 0; k < 3; ++k) {

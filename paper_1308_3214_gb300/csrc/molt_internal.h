@@ -23,4 +23,15 @@ size_t pass_smem_bytes(bool horner, int tbytes, int W, int ls, int n);
 // Line stride in shared memory for W lines of segment stride ms.
 int line_stride(int ms, int W, int tbytes);
 
+// Register-resident kernels (molt_regs.cu).  The *_plan functions say whether
+// a line of n points is supported and with which segment decomposition.
+bool regs_contig_plan(int tbytes, int bc, int n, int *rpt);
+bool regs_strided_plan(int tbytes, int bc, int n, int *rpt, int *S, int *K);
+size_t regs_strided_smem(int tbytes, int S, int rpt, bool horner);
+cudaError_t launch_contig(int tbytes, int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                          cudaStream_t s);
+cudaError_t launch_strided(int tbytes, int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                           cudaStream_t s);
+cudaError_t configure_regs_kernels();
+
 }  // namespace molt

@@ -84,6 +84,30 @@ struct HornerParams {
     void *un_hi, *un_lo;
 };
 
+// Coefficients and fields of a pass program.
+//   mode 0 (powers): out[p-1] = D^p u, p = 1..P
+//   mode 1 (Horner): for each output o:
+//       X = 0;  for t = P..1: X = D( sum_k coef[o][t][k] g_k + X + cu[o][t] u )
+//       out_o = sum_k coef[o][0][k] g_k + X     (or the level combination)
+struct ProgParams {
+    int mode, P, ng, nout;
+    const void *g[MAXG];
+    void *out[MAXG];
+    const double *coef;   // device, [nout][P+1][ng]
+    const double *cu;     // device, [nout][P+1]
+    int epi;              // 1: out_0 combined into the next level
+    double ea, eb, ec;    // u_next = ea u + eb u_prev + ec F
+    const void *u_hi, *u_lo, *up_hi, *up_lo;
+    void *un_hi, *un_lo;
+};
+
+struct LineSet {
+    int64_t stride;   // element stride along the axis
+    int64_t inner;    // product of the extents before the axis
+    int64_t nlines;
+    int S, K;         // strided: segments per CTA (warps) and CTAs per line
+};
+
 // ---------------------------------------------------------------------------
 // float32 pair ("hi + lo") arithmetic for the time levels.  The __f*_rn
 // intrinsics keep the compiler from contracting or re-associating.

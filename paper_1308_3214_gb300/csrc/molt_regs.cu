@@ -1,0 +1,154 @@
+// molt_regs.cu -- instantiation and launch of the register-resident pass kernels.
+#include "molt_internal.h"
+#include "molt_regs.cuh"
+
+namespace molt {
+
+namespace {
+
+constexpr int kContigWarps = 4;
+
+template <class T, int RPT>
+size_t contig_smem() { return (size_t)kContigWarps * 2 * ContigStage<T, RPT>::LINE * sizeof(T); }
+
+template <class T, int BC, int RPT>
+cudaError_t run_contig(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+{
+    const int64_t grid = (L.nlines + kContigWarps - 1) / kContigWarps;
+    k_contig<T, BC, RPT, kContigWarps><<<(unsigned)grid, 32 * kContigWarps, contig_smem<T, RPT>(), s>>>(A, L, p);
+    return cudaGetLastError();
+}
+
+template <class T, int BC, int RPT>
+cudaError_t run_strided(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+{
+    size_t smem = strided_slot_bytes(L.S, sizeof(T));
+    if (p.mode == 1) smem += (size_t)L.S * RPT * 32 * sizeof(T);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1);
+    cfg.blockDim = dim3(32 * L.S, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = (unsigned)L.K;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = L.K > 1 ? 1 : 0;
+    if (p.mode == 1) return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, true>, A, L, p);
+    return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, false>, A, L, p);
+}
+
+template <class T, int BC, int RPT>
+cudaError_t attr_contig()
+{
+    return cudaFuncSetAttribute(k_contig<T, BC, RPT, kContigWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)contig_smem<T, RPT>());
+}
+
+template <class T, int BC, int RPT>
+cudaError_t attr_strided()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_strided<T, BC, RPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_strided<T, BC, RPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+}  // namespace
+
+// Segment lengths: contiguous lines use the smallest RPT with 32*RPT >= n;
+// strided lines use 64 (float) / 32 (double) points per thread.
+constexpr int kStridedRptF = 64, kStridedRptD = 32;
+
+// Register kernels need whole segments: n a multiple of RPT (both boundary
+// conditions keep the line ends at fixed register positions).
+bool regs_contig_plan(int tbytes, int, int n, int *rpt)
+{
+    const int maxr = tbytes == 4 ? 64 : 32;
+    for (int r = 8; r <= maxr; r *= 2) {
+        if (32 * r < n) continue;
+        if (n % r != 0) return false;
+        *rpt = r;
+        return true;
+    }
+    return false;
+}
+
+bool regs_strided_plan(int tbytes, int, int n, int *rpt, int *S, int *K)
+{
+    const int r = tbytes == 4 ? kStridedRptF : kStridedRptD;
+    if (n % r != 0) return false;
+    const int G = n / r;
+    const int k = (G + 7) / 8;      // at most 8 warps per CTA
+    if (k > 8) return false;        // portable cluster size
+    *rpt = r;
+    *S = (G + k - 1) / k;
+    *K = k;
+    return true;
+}
+
+size_t regs_strided_smem(int tbytes, int S, int rpt, bool horner)
+{
+    size_t b = strided_slot_bytes(S, (size_t)tbytes);
+    if (horner) b += (size_t)S * rpt * 32 * tbytes;
+    return b;
+}
+
+#define MOLT_CONTIG_R(T, BC)                                                             \
+    switch (rpt) {                                                                       \
+    case 8: return run_contig<T, BC, 8>(A, L, p, s);                                     \
+    case 16: return run_contig<T, BC, 16>(A, L, p, s);                                   \
+    case 32: return run_contig<T, BC, 32>(A, L, p, s);                                   \
+    default: break;                                                                      \
+    }
+
+cudaError_t launch_contig(int tbytes, int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                          cudaStream_t s)
+{
+    if (tbytes == 4) {
+        if (bc == BC_PERIODIC) {
+            MOLT_CONTIG_R(float, BC_PERIODIC)
+            if (rpt == 64) return run_contig<float, BC_PERIODIC, 64>(A, L, p, s);
+        } else {
+            MOLT_CONTIG_R(float, BC_DIRICHLET)
+            if (rpt == 64) return run_contig<float, BC_DIRICHLET, 64>(A, L, p, s);
+        }
+    } else {
+        if (bc == BC_PERIODIC) { MOLT_CONTIG_R(double, BC_PERIODIC) }
+        else { MOLT_CONTIG_R(double, BC_DIRICHLET) }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_strided(int tbytes, int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                           cudaStream_t s)
+{
+    if (tbytes == 4 && rpt == kStridedRptF)
+        return bc == BC_PERIODIC ? run_strided<float, BC_PERIODIC, kStridedRptF>(A, L, p, s)
+                                 : run_strided<float, BC_DIRICHLET, kStridedRptF>(A, L, p, s);
+    if (tbytes == 8 && rpt == kStridedRptD)
+        return bc == BC_PERIODIC ? run_strided<double, BC_PERIODIC, kStridedRptD>(A, L, p, s)
+                                 : run_strided<double, BC_DIRICHLET, kStridedRptD>(A, L, p, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t configure_regs_kernels()
+{
+    cudaError_t e;
+#define MOLT_A(x) if ((e = (x)) != cudaSuccess) return e;
+    MOLT_A((attr_contig<float, BC_PERIODIC, 8>())) MOLT_A((attr_contig<float, BC_PERIODIC, 16>()))
+    MOLT_A((attr_contig<float, BC_PERIODIC, 32>())) MOLT_A((attr_contig<float, BC_PERIODIC, 64>()))
+    MOLT_A((attr_contig<float, BC_DIRICHLET, 8>())) MOLT_A((attr_contig<float, BC_DIRICHLET, 16>()))
+    MOLT_A((attr_contig<float, BC_DIRICHLET, 32>())) MOLT_A((attr_contig<float, BC_DIRICHLET, 64>()))
+    MOLT_A((attr_contig<double, BC_PERIODIC, 8>())) MOLT_A((attr_contig<double, BC_PERIODIC, 16>()))
+    MOLT_A((attr_contig<double, BC_PERIODIC, 32>()))
+    MOLT_A((attr_contig<double, BC_DIRICHLET, 8>())) MOLT_A((attr_contig<double, BC_DIRICHLET, 16>()))
+    MOLT_A((attr_contig<double, BC_DIRICHLET, 32>()))
+    MOLT_A((attr_strided<float, BC_PERIODIC, kStridedRptF>())) MOLT_A((attr_strided<float, BC_DIRICHLET, kStridedRptF>()))
+    MOLT_A((attr_strided<double, BC_PERIODIC, kStridedRptD>())) MOLT_A((attr_strided<double, BC_DIRICHLET, kStridedRptD>()))
+#undef MOLT_A
+    return cudaSuccess;
+}
+
+}  // namespace molt

@@ -1,0 +1,792 @@
+// molt_regs.cuh -- register-resident line sweeps (sm_103a).
+//
+// Every thread owns one segment of RPT consecutive points of one line in
+// registers.  The operator D (see molt_kernels.cuh for the difference form)
+// runs on the segment with a sliding 5-point window, a causal reduction, a
+// carry exchange, a causal scan fused with the anti-causal reduction, a
+// second exchange and the anti-causal scan; the Dirichlet term A' d^j is
+// added last.  Two layouts share these segment routines:
+//
+//  * k_contig  (contiguous axis x): one warp per line, lane s owns points
+//    [s*RPT, (s+1)*RPT).  Carries and halos travel by warp shuffles.  Global
+//    memory is read and written coalesced (lane = consecutive points) and
+//    turned into the segment layout through a per-warp shared staging buffer
+//    whose segment stride RPT + 16 B keeps both the coalesced side and the
+//    per-lane 16-byte side free of bank conflicts.
+//  * k_strided (axes y, z): lane = one of 32 neighbouring lines, so every
+//    global access is coalesced as it is; the segments of a line are spread
+//    over the warps of a CTA and, for long lines, over the CTAs of a thread
+//    block cluster.  Carries and halos travel through shared memory and, across
+//    the cluster, through distributed shared memory.
+#pragma once
+#include <cooperative_groups.h>
+#include <type_traits>
+#include "molt_kernels.cuh"
+
+namespace molt {
+
+namespace cg = cooperative_groups;
+
+// ---------------------------------------------------------------------------
+// per-segment arithmetic
+// ---------------------------------------------------------------------------
+template <class T> struct VecOf;
+template <> struct VecOf<float> { using type = float4; static constexpr int n = 4; };
+template <> struct VecOf<double> { using type = double2; static constexpr int n = 2; };
+
+// q_k = c1 s_k + c2 (s_{k-1} + s_{k+1}) from a sliding window.  MODE 0: z
+// already holds s; MODE 1: s = second difference of z; MODE 2: s = second
+// difference of z + cu r.  zl2, zl1 = z at a-2, a-1; zr0, zr1 = z at a+RPT,
+// a+RPT+1 (MODE 0: zl1 = s_{a-1}, zr0 = s_{a+RPT}).  r(k) supplies r at a+k
+// for k in [-1, RPT].  Dirichlet ends are handled by the caller: ghost values
+// in the halos (end_ghosts) and q = 0 at the end nodes (end_zero).
+template <class T, int RPT, int MODE, class RF>
+__device__ __forceinline__ void seg_make_q(T (&z)[RPT], T zl2, T zl1, T zr0, T zr1, RF r, T cu, T c1, T c2)
+{
+    T sm1, s0, zk, zp1;
+    if (MODE == 0) {
+        sm1 = zl1;
+        s0 = z[0];
+    } else {
+        zk = z[0];
+        zp1 = z[1];
+        sm1 = (zk - zl1) - (zl1 - zl2);
+        s0 = (zp1 - zk) - (zk - zl1);
+        if (MODE == 2) { sm1 += cu * r(-1); s0 += cu * r(0); }
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        T sp1;
+        if (MODE == 0) {
+            sp1 = (k + 1 < RPT) ? z[k + 1] : zr0;
+        } else {
+            const T zp2 = (k + 2 < RPT) ? z[k + 2] : (k + 2 == RPT ? zr0 : zr1);
+            sp1 = (zp2 - zp1) - (zp1 - zk);
+            if (MODE == 2) sp1 += cu * r(k + 1);
+            zk = zp1;
+            zp1 = zp2;
+        }
+        z[k] = c1 * s0 + c2 * (sm1 + sp1);
+        sm1 = s0;
+        s0 = sp1;
+    }
+}
+
+// Dirichlet: the one-sided interpolants of the end cells make s_0 = s_1 and
+// s_{n-1} = s_{n-2}; with the quadratic-extrapolation ghosts
+// z_{-1} = 3 z_0 - 3 z_1 + z_2 and z_n = 3 z_{n-1} - 3 z_{n-2} + z_{n-3}
+// the plain second difference gives exactly that.  MODE 0 (z = s, whose ends
+// were duplicated when formed) takes the ghost s_{-1} = s_0, s_n = s_{n-1}.
+template <class T, int RPT, int MODE>
+__device__ __forceinline__ void end_ghosts(const T (&z)[RPT], bool left, bool right, T &zl2, T &zl1, T &zr0, T &zr1)
+{
+    if (left) {
+        zl1 = (MODE == 0) ? z[0] : (T)3 * (z[0] - z[1]) + z[2];
+        zl2 = zl1;
+    }
+    if (right) {
+        zr0 = (MODE == 0) ? z[RPT - 1] : (T)3 * (z[RPT - 1] - z[RPT - 2]) + z[RPT - 3];
+        zr1 = zr0;
+    }
+}
+
+// Dirichlet: no interior equation at the end nodes (e = 0 there)
+template <class T, int RPT>
+__device__ __forceinline__ void end_zero(T (&z)[RPT], bool left, bool right)
+{
+    if (left) z[0] = 0;
+    if (right) z[RPT - 1] = 0;
+}
+
+template <class T, int RPT>
+__device__ __forceinline__ T seg_fwd_reduce(const T (&q)[RPT], T d)
+{
+    T E = 0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) E = d * E + q[k];
+    return E;
+}
+
+// y_k = d y_{k-1} + q_k from y = y_{a-1}; returns ER = sum_k d^k y_k
+template <class T, int RPT>
+__device__ __forceinline__ T seg_fwd_scan(T (&z)[RPT], T d, T y)
+{
+    T ER = 0, pw = 1;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        y = d * y + z[k];
+        z[k] = y;
+        ER += pw * y;
+        pw *= d;
+    }
+    return ER;
+}
+
+// e_k = d e_{k+1} + y_k with acc = d e_{a+RPT} on entry
+template <class T, int RPT>
+__device__ __forceinline__ void seg_bwd_scan(T (&z)[RPT], T d, T acc)
+{
+#pragma unroll
+    for (int k = RPT - 1; k >= 0; --k) {
+        const T e = acc + z[k];
+        acc = d * e;
+        z[k] = e;
+    }
+}
+
+// z_k += A' d^{a+k}, given w0 = A' d^a
+template <class T, int RPT>
+__device__ __forceinline__ void seg_add_left(T (&z)[RPT], T d, T w0)
+{
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        z[k] += w0;
+        w0 *= d;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// contiguous axis: one warp per line
+// ---------------------------------------------------------------------------
+template <class T, int RPT>
+struct ContigStage {
+    static constexpr int VN = VecOf<T>::n;
+    static constexpr int SST = RPT + VN;       // segment stride (elements)
+    static constexpr int LINE = 32 * SST;      // one line in the staging layout
+    __device__ static int pos(int g) { return (g / RPT) * SST + (g % RPT); }
+};
+
+// One application of D on a line held by a warp (lane = segment).  The line
+// has n = RPT * (Ld + 1) points; lanes past Ld hold zeros.
+template <class T, int BC, int RPT, int MODE>
+__device__ __forceinline__ void warp_sweep(T (&z)[RPT], const T *rline, T cu, const AxisDev &A, int lane)
+{
+    using St = ContigStage<T, RPT>;
+    const int n = A.n;
+    const T d = (T)A.d;
+    const int Ld = n / RPT - 1;
+    const bool full = lane <= Ld;
+    const int a = lane * RPT;
+
+    T zl1 = __shfl_up_sync(0xffffffffu, z[RPT - 1], 1);
+    T zl2 = __shfl_up_sync(0xffffffffu, z[RPT - 2], 1);
+    T zr0 = __shfl_down_sync(0xffffffffu, z[0], 1);
+    T zr1 = __shfl_down_sync(0xffffffffu, z[1], 1);
+    if (BC == BC_PERIODIC) {
+        const T w1 = __shfl_sync(0xffffffffu, z[RPT - 1], Ld), w2 = __shfl_sync(0xffffffffu, z[RPT - 2], Ld);
+        const T v0 = __shfl_sync(0xffffffffu, z[0], 0), v1 = __shfl_sync(0xffffffffu, z[1], 0);
+        if (lane == 0) { zl1 = w1; zl2 = w2; }
+        if (lane == Ld) { zr0 = v0; zr1 = v1; }
+    } else {
+        end_ghosts<T, RPT, MODE>(z, lane == 0, lane == Ld, zl2, zl1, zr0, zr1);
+    }
+    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    if (MODE == 2) {
+        const T *rs = rline + lane * St::SST;
+        const int jl = a == 0 ? (BC == BC_PERIODIC ? n - 1 : 0) : a - 1;
+        const int jr = a + RPT >= n ? (BC == BC_PERIODIC ? 0 : n - 1) : a + RPT;
+        const T rl = rline[St::pos(jl)], rr = rline[St::pos(jr)];
+        seg_make_q<T, RPT, 2>(z, zl2, zl1, zr0, zr1,
+                              [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : rs[k]); }, cu, c1, c2);
+    } else {
+        seg_make_q<T, RPT, MODE>(z, zl2, zl1, zr0, zr1, [&](int) { return (T)0; }, (T)0, c1, c2);
+    }
+    if (BC == BC_DIRICHLET) end_zero<T, RPT>(z, lane == 0, lane == Ld);
+    if (!full) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+    }
+
+    // causal carries: Kogge-Stone over lanes with multipliers d^{RPT 2^k}
+    const T E = seg_fwd_reduce<T, RPT>(z, d);
+    T x = E;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const T y = __shfl_up_sync(0xffffffffu, x, 1 << k);
+        if (lane >= (1 << k)) x += (T)A.dm[k] * y;
+    }
+    T yin = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) yin = 0;
+    const T *dpg = dpow_of<T>(A);
+    if (BC == BC_PERIODIC) {
+        const T tot = __shfl_sync(0xffffffffu, x, Ld);          // zero-inflow y_{n-1}
+        if (full) yin += dpg[a] * (tot * (T)A.inv);               // images to the left
+    }
+    if (!full) yin = 0;                                            // lanes past the line stay zero
+    const T ER = seg_fwd_scan<T, RPT>(z, d, yin);
+
+    // anti-causal carries
+    T xb = ER;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const T t = __shfl_down_sync(0xffffffffu, xb, 1 << k);
+        if (lane + (1 << k) < 32) xb += (T)A.dm[k] * t;
+    }
+    T exclb = __shfl_down_sync(0xffffffffu, xb, 1);
+    if (lane == 31) exclb = 0;
+    const T e00 = __shfl_sync(0xffffffffu, xb, 0);              // zero-inflow e_0
+    T Z, Acoef = 0;
+    if (BC == BC_DIRICHLET) {
+        const T yl = __shfl_sync(0xffffffffu, z[RPT - 1], Ld);  // y_{n-1}
+        const T mu = (T)A.mu, inv = (T)A.inv;
+        Acoef = (mu * yl - e00) * inv;
+        Z = (mu * e00 - yl) * inv;
+    } else {
+        Z = d * e00 * (T)A.inv;
+    }
+    const T acc = d * exclb + (full ? dpg[n - a - RPT] * Z : (T)0);
+    seg_bwd_scan<T, RPT>(z, d, acc);
+    if (BC == BC_DIRICHLET && full) seg_add_left<T, RPT>(z, d, Acoef * dpg[a]);
+}
+
+// stage (coalesced side) -> registers (segment side)
+template <class T, int RPT>
+__device__ __forceinline__ void stage_to_regs(const T *st, T (&z)[RPT], int lane, bool add)
+{
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n;
+    const V *p = reinterpret_cast<const V *>(st + lane * ContigStage<T, RPT>::SST);
+#pragma unroll
+    for (int q = 0; q < RPT / VN; ++q) {
+        V v = p[q];
+        const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+        for (int c = 0; c < VN; ++c) z[q * VN + c] = add ? z[q * VN + c] + e[c] : e[c];
+    }
+}
+
+template <class T, int RPT>
+__device__ __forceinline__ void regs_to_stage(T *st, const T (&z)[RPT], int lane)
+{
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n;
+    V *p = reinterpret_cast<V *>(st + lane * ContigStage<T, RPT>::SST);
+#pragma unroll
+    for (int q = 0; q < RPT / VN; ++q) {
+        V v;
+        T *e = reinterpret_cast<T *>(&v);
+#pragma unroll
+        for (int c = 0; c < VN; ++c) e[c] = z[q * VN + c];
+        p[q] = v;
+    }
+}
+
+// next time level of a vector of VN consecutive elements starting at i:
+// u_next = ea u + eb u_prev + ec F
+__device__ __forceinline__ void level_vec(const ProgParams &p, int64_t i, const float4 &F)
+{
+    const float4 uh = *reinterpret_cast<const float4 *>((const float *)p.u_hi + i);
+    const float4 ul = *reinterpret_cast<const float4 *>((const float *)p.u_lo + i);
+    float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
+    if (p.eb != 0.0) {
+        ph = *reinterpret_cast<const float4 *>((const float *)p.up_hi + i);
+        pl = *reinterpret_cast<const float4 *>((const float *)p.up_lo + i);
+    }
+    const float ea = (float)p.ea, eb = (float)p.eb, ec = (float)p.ec;
+    float4 nh, nl;
+    level_pair(uh.x, ul.x, ph.x, pl.x, F.x, ea, eb, ec, nh.x, nl.x);
+    level_pair(uh.y, ul.y, ph.y, pl.y, F.y, ea, eb, ec, nh.y, nl.y);
+    level_pair(uh.z, ul.z, ph.z, pl.z, F.z, ea, eb, ec, nh.z, nl.z);
+    level_pair(uh.w, ul.w, ph.w, pl.w, F.w, ea, eb, ec, nh.w, nl.w);
+    *reinterpret_cast<float4 *>((float *)p.un_hi + i) = nh;
+    *reinterpret_cast<float4 *>((float *)p.un_lo + i) = nl;
+}
+__device__ __forceinline__ void level_vec(const ProgParams &p, int64_t i, const double2 &F)
+{
+    const double2 u = *reinterpret_cast<const double2 *>((const double *)p.u_hi + i);
+    double2 v;
+    v.x = p.ea * u.x + p.ec * F.x;
+    v.y = p.ea * u.y + p.ec * F.y;
+    if (p.eb != 0.0) {
+        const double2 q = *reinterpret_cast<const double2 *>((const double *)p.up_hi + i);
+        v.x += p.eb * q.x;
+        v.y += p.eb * q.y;
+    }
+    *reinterpret_cast<double2 *>((double *)p.un_hi + i) = v;
+}
+
+template <class V> __device__ __forceinline__ V vfma(typename std::remove_reference<decltype(V().x)>::type c, const V &a, const V &b);
+template <> __device__ __forceinline__ float4 vfma<float4>(float c, const float4 &a, const float4 &b)
+{
+    return make_float4(b.x + c * a.x, b.y + c * a.y, b.z + c * a.z, b.w + c * a.w);
+}
+template <> __device__ __forceinline__ double2 vfma<double2>(double c, const double2 &a, const double2 &b)
+{
+    return make_double2(b.x + c * a.x, b.y + c * a.y);
+}
+
+// Coalesced side of the staging buffer: a lane covers vectors of VN
+// consecutive elements g = VN*(lane + 32 i).  Segment boundaries are
+// multiples of RPT (a multiple of VN), so a vector never straddles two
+// segments and sits 16-byte aligned at pos(g).
+template <class T, int RPT>
+struct CoalescedSide {
+    using V = typename VecOf<T>::type;
+    static constexpr int VN = VecOf<T>::n;
+    static constexpr int NV = RPT;                 // vectors per lane in a full line (32*RPT/(32*VN)*VN)
+    __device__ static V *at(T *st, int g) { return reinterpret_cast<V *>(st + ContigStage<T, RPT>::pos(g)); }
+};
+
+// stage <- stage + sum_k coef[k] g_k[base + .] over the line (coalesced),
+// one pass per field with a non-zero weight
+template <class T, int RPT>
+__device__ __forceinline__ void stage_accumulate(T *stage, const ProgParams &pr, const double *cf, int64_t base, int n,
+                                                 int lane)
+{
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n;
+    const int nvec = n / VN;                        // n is a multiple of RPT, hence of VN
+    for (int k = 0; k < pr.ng; ++k) {
+        const T ck = (T)__ldg(cf + k);
+        if (ck == (T)0) continue;
+        const V *src = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.g[k]) + base);
+#pragma unroll 4
+        for (int v = lane; v < nvec; v += 32) {
+            V *d = CoalescedSide<T, RPT>::at(stage, v * VN);
+            *d = vfma<V>(ck, src[v], *d);
+        }
+    }
+}
+
+// r = accurate second difference of u along the line, formed in the segment
+// layout from u staged in shared memory (hi plane in `stage`, lo in `rline`
+// for float32 pairs); result left in z and written to rline.
+template <class T, int BC, int RPT>
+__device__ __forceinline__ void contig_r(T (&z)[RPT], T *stage, T *rline, const ProgParams &pr, int64_t base, int n,
+                                         int lane)
+{
+    using St = ContigStage<T, RPT>;
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n;
+    const int nvec = n / VN;
+    const bool pair = sizeof(T) == 4;
+    const V *H = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.u_hi) + base);
+    const V *L = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.u_lo) + base);
+#pragma unroll 4
+    for (int v = lane; v < nvec; v += 32) {
+        *CoalescedSide<T, RPT>::at(stage, v * VN) = H[v];
+        if (pair) *CoalescedSide<T, RPT>::at(rline, v * VN) = L[v];
+    }
+    __syncwarp();
+    const int a = lane * RPT;
+    const int Ld = n / RPT - 1;
+    const bool full = lane <= Ld;
+    auto wrapc = [&](int j) { return BC == BC_PERIODIC ? (j < 0 ? j + n : (j >= n ? j - n : j)) : min(max(j, 0), n - 1); };
+    const int jl = wrapc(a - 1), jr = wrapc(a + RPT);
+    // hi part
+    stage_to_regs<T, RPT>(stage, z, lane, false);
+    {
+        T hm = stage[St::pos(jl)], hp = stage[St::pos(jr)];
+        T prev = hm, cur = z[0];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const T next = (k + 1 < RPT) ? z[k + 1] : hp;
+            const T sd = (next - cur) - (cur - prev);
+            prev = cur;
+            cur = next;
+            z[k] = sd;
+        }
+    }
+    if (pair) {
+        // lo part straight from shared memory (keeps register use at one line)
+        const T *ls = rline + lane * St::SST;
+        T prev = rline[St::pos(jl)], cur = ls[0];
+        const T lp = rline[St::pos(jr)];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const T next = (k + 1 < RPT) ? ls[k + 1] : lp;
+            const T sd = (next - cur) - (cur - prev);
+            prev = cur;
+            cur = next;
+            z[k] = z[k] + sd;
+        }
+    }
+    if (BC == BC_DIRICHLET) {          // end nodes take the neighbouring interior centre
+        if (lane == 0) z[0] = z[1];
+        if (lane == Ld) z[RPT - 1] = z[RPT - 2];
+    }
+    if (!full) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+    }
+    __syncwarp();
+    regs_to_stage<T, RPT>(rline, z, lane);
+    __syncwarp();
+}
+
+template <class T, int BC, int RPT, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, 3) k_contig(AxisDev A, LineSet LS, ProgParams pr)
+{
+    static_assert(RPT >= 4 && RPT % VecOf<T>::n == 0, "segment length");
+    using St = ContigStage<T, RPT>;
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *stage = reinterpret_cast<T *>(smem_raw) + (size_t)warp * 2 * St::LINE;
+    T *rline = stage + St::LINE;
+    const int n = A.n;
+    const int64_t L = (int64_t)blockIdx.x * WARPS + warp;
+    if (L >= LS.nlines) return;
+    const int64_t base = L * (int64_t)n;   // contiguous axis
+    const int nvec = n / VN;
+
+    T z[RPT];
+    contig_r<T, BC, RPT>(z, stage, rline, pr, base, n, lane);
+
+    if (pr.mode == 0) {
+        // powers: the first sweep starts from s = r
+        for (int p = 1; p <= pr.P; ++p) {
+            if (p == 1) warp_sweep<T, BC, RPT, 0>(z, rline, (T)0, A, lane);
+            else warp_sweep<T, BC, RPT, 1>(z, rline, (T)0, A, lane);
+            if (pr.out[p - 1] != nullptr) {
+                regs_to_stage<T, RPT>(stage, z, lane);
+                __syncwarp();
+                V *o = reinterpret_cast<V *>(reinterpret_cast<T *>(pr.out[p - 1]) + base);
+#pragma unroll 4
+                for (int v = lane; v < nvec; v += 32) o[v] = *CoalescedSide<T, RPT>::at(stage, v * VN);
+                __syncwarp();
+            }
+        }
+        return;
+    }
+    const int P = pr.P, ng = pr.ng;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) z[k] = 0;
+    for (int t = P; t >= 0; --t) {
+        if (ng > 0 || t == 0) {
+            regs_to_stage<T, RPT>(stage, z, lane);
+            __syncwarp();
+            if (ng > 0) stage_accumulate<T, RPT>(stage, pr, pr.coef + (size_t)t * ng, base, n, lane);
+            __syncwarp();
+            if (t == 0) break;
+            stage_to_regs<T, RPT>(stage, z, lane, false);
+            __syncwarp();
+        }
+        warp_sweep<T, BC, RPT, 2>(z, rline, (T)__ldg(pr.cu + t), A, lane);
+    }
+    // out = stage (coalesced side): level combination or plain store
+    if (pr.epi) {
+#pragma unroll 4
+        for (int v = lane; v < nvec; v += 32) level_vec(pr, base + (int64_t)v * VN, *CoalescedSide<T, RPT>::at(stage, v * VN));
+    } else {
+        V *o = reinterpret_cast<V *>(reinterpret_cast<T *>(pr.out[0]) + base);
+#pragma unroll 4
+        for (int v = lane; v < nvec; v += 32) o[v] = *CoalescedSide<T, RPT>::at(stage, v * VN);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// strided axes: lanes = 32 neighbouring lines, segments over warps and CTAs
+// ---------------------------------------------------------------------------
+template <class T>
+struct StridedSlots {
+    T *E;      // [S][32] causal segment reductions
+    T *ER;     // [S][32] anti-causal segment reductions
+    T *H;      // [S][4][32] first two / last two values of each segment
+    T *Tot;    // [2][32] CTA totals (causal, anti-causal)
+};
+
+__host__ __device__ inline size_t strided_slot_bytes(int S, size_t tsize) { return (6 * (size_t)S * 32 + 64) * tsize; }
+
+template <class T>
+struct StridedCtx {
+    cg::cluster_group cl;
+    StridedSlots<T> sl;
+    const T *dpg;
+    T d, dR;            // e^{-nu}, d^RPT
+    int n, S, K, w, lane, krank, seg, a, Gd;
+    bool full;
+};
+
+template <class T>
+__device__ __forceinline__ T *peer_of(const StridedCtx<T> &c, T *p, int r)
+{
+    return c.K > 1 ? c.cl.map_shared_rank(p, r) : p;
+}
+
+template <class T>
+__device__ __forceinline__ void csync(const StridedCtx<T> &c)
+{
+    if (c.K > 1) c.cl.sync();
+    else __syncthreads();
+}
+
+// number of data segments in CTA k, and its length multiplier d^{len}
+template <class T>
+__device__ __forceinline__ T cta_mult(const StridedCtx<T> &c, int k, int rpt)
+{
+    const int nf = max(0, min(c.S, c.Gd - k * c.S));
+    return c.dpg[nf * rpt];
+}
+
+// causal exchange: y at a-1 (zero inflow) and the line's y_{n-1}
+template <class T, int RPT>
+__device__ __forceinline__ void strided_causal(const StridedCtx<T> &c, T E, T &yin, T &ytot)
+{
+    c.sl.E[c.w * 32 + c.lane] = E;
+    __syncthreads();
+    if (c.w == 0) {
+        T acc = 0;
+        for (int v = 0; v < c.S; ++v) acc = ((c.krank * c.S + v) < c.Gd ? c.dR : (T)1) * acc + c.sl.E[v * 32 + c.lane];
+        c.sl.Tot[c.lane] = acc;
+    }
+    csync(c);
+    T cin = 0;
+    for (int k2 = 0; k2 < c.krank; ++k2) cin = cta_mult<T>(c, k2, RPT) * cin + peer_of(c, c.sl.Tot, k2)[c.lane];
+    T tot = cin;
+    for (int k2 = c.krank; k2 < c.K; ++k2) tot = cta_mult<T>(c, k2, RPT) * tot + peer_of(c, c.sl.Tot, k2)[c.lane];
+    T acc = cin;
+    for (int v = 0; v < c.w; ++v) acc = c.dR * acc + c.sl.E[v * 32 + c.lane];
+    yin = acc;
+    ytot = tot;
+}
+
+// anti-causal exchange: zero-inflow e just past the segment, and e_0
+template <class T, int RPT>
+__device__ __forceinline__ void strided_anticausal(const StridedCtx<T> &c, T ER, T &eout, T &e0)
+{
+    c.sl.ER[c.w * 32 + c.lane] = ER;
+    __syncthreads();
+    if (c.w == 0) {
+        T acc = 0;
+        for (int v = c.S - 1; v >= 0; --v) acc = ((c.krank * c.S + v) < c.Gd ? c.dR : (T)1) * acc + c.sl.ER[v * 32 + c.lane];
+        c.sl.Tot[32 + c.lane] = acc;
+    }
+    csync(c);
+    T cin = 0;
+    for (int k2 = c.K - 1; k2 > c.krank; --k2) cin = cta_mult<T>(c, k2, RPT) * cin + peer_of(c, c.sl.Tot, k2)[32 + c.lane];
+    T tot = cin;
+    for (int k2 = c.krank; k2 >= 0; --k2) tot = cta_mult<T>(c, k2, RPT) * tot + peer_of(c, c.sl.Tot, k2)[32 + c.lane];
+    T acc = cin;
+    for (int v = c.S - 1; v > c.w; --v) acc = ((c.krank * c.S + v) < c.Gd ? c.dR : (T)1) * acc + c.sl.ER[v * 32 + c.lane];
+    eout = acc;
+    e0 = tot;
+}
+
+// halo exchange: z at a-2, a-1 and a+RPT, a+RPT+1
+template <class T, int BC, int RPT>
+__device__ __forceinline__ void strided_halos(const StridedCtx<T> &c, const T (&z)[RPT], T &l2, T &l1, T &r0, T &r1)
+{
+    T *H = c.sl.H + c.w * 128;
+    H[c.lane] = z[0];
+    H[32 + c.lane] = z[1];
+    H[64 + c.lane] = z[RPT - 2];
+    H[96 + c.lane] = z[RPT - 1];
+    csync(c);
+    int gl = c.seg - 1, gr = c.seg + 1;
+    if (BC == BC_PERIODIC) {
+        if (gl < 0) gl = c.Gd - 1;
+        if (gr >= c.Gd) gr = 0;
+    }
+    l2 = l1 = r0 = r1 = 0;
+    if (gl >= 0) {
+        const T *Hl = peer_of(c, c.sl.H, gl / c.S) + (gl % c.S) * 128;
+        l2 = Hl[64 + c.lane];
+        l1 = Hl[96 + c.lane];
+    }
+    if (gr < c.Gd) {
+        const T *Hr = peer_of(c, c.sl.H, gr / c.S) + (gr % c.S) * 128;
+        r0 = Hr[c.lane];
+        r1 = Hr[32 + c.lane];
+    }
+    csync(c);   // the slots are rewritten only after everyone has read them
+}
+
+// One application of D on this thread's segment.  MODE as in seg_make_q;
+// halos l2, l1, r0, r1 as exchanged (MODE 0: l1 = s_{a-1}, r0 = s_{a+RPT}).
+template <class T, int BC, int RPT, int MODE>
+__device__ __forceinline__ void strided_sweep(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT], T cu,
+                                              T l2, T l1, T r0, T r1, const T *rs, T rl, T rr)
+{
+    const bool left = c.seg == 0, right = c.seg == c.Gd - 1;
+    if (BC == BC_DIRICHLET) end_ghosts<T, RPT, MODE>(z, left, right, l2, l1, r0, r1);
+    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    if (MODE == 2)
+        seg_make_q<T, RPT, 2>(z, l2, l1, r0, r1, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : rs[k * 32]); },
+                              cu, c1, c2);
+    else
+        seg_make_q<T, RPT, MODE>(z, l2, l1, r0, r1, [&](int) { return (T)0; }, (T)0, c1, c2);
+    if (BC == BC_DIRICHLET) end_zero<T, RPT>(z, left, right);
+    if (!c.full) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+    }
+    const T d = c.d;
+    const T E = seg_fwd_reduce<T, RPT>(z, d);
+    T yin, ytot;
+    strided_causal<T, RPT>(c, E, yin, ytot);
+    if (BC == BC_PERIODIC && c.full) yin += c.dpg[c.a] * (ytot * (T)A.inv);
+    if (!c.full) yin = 0;                                          // segments past the line stay zero
+    const T ER = seg_fwd_scan<T, RPT>(z, d, yin);
+    T eout, e00;
+    strided_anticausal<T, RPT>(c, ER, eout, e00);
+    T Z, Acoef = 0;
+    if (BC == BC_DIRICHLET) {
+        const T mu = (T)A.mu, inv = (T)A.inv;
+        Acoef = (mu * ytot - e00) * inv;     // ytot = zero-inflow y_{n-1}
+        Z = (mu * e00 - ytot) * inv;
+    } else {
+        Z = d * e00 * (T)A.inv;
+    }
+    const T acc = d * eout + (c.full ? c.dpg[c.n - c.a - RPT] * Z : (T)0);
+    seg_bwd_scan<T, RPT>(z, d, acc);
+    if (BC == BC_DIRICHLET && c.full) seg_add_left<T, RPT>(z, d, Acoef * c.dpg[c.a]);
+}
+
+// second differences r of u at points a-1 .. a+RPT of one strided line, from
+// one pass over rows a-2 .. a+RPT+1 (rows wrapped or clamped into the line;
+// the clamped Dirichlet end values are fixed by the caller)
+template <int BC>
+__device__ __forceinline__ int64_t wrap_or_clamp(int j, int n)
+{
+    if (BC == BC_PERIODIC) { if (j < 0) j += n; else if (j >= n) j -= n; }
+    else j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+    return (int64_t)j;
+}
+
+template <int BC, int RPT>
+__device__ __forceinline__ void strided_r_pair(const ProgParams &pr, int64_t lbase, int64_t st, int a, int n,
+                                               float (&r)[RPT], float &rl, float &rr)
+{
+    const float *H = (const float *)pr.u_hi + lbase, *L = (const float *)pr.u_lo + lbase;
+    const int64_t jm2 = wrap_or_clamp<BC>(a - 2, n) * st, jm1 = wrap_or_clamp<BC>(a - 1, n) * st;
+    float hm = H[jm2], lm = L[jm2], h0 = H[jm1], l0 = L[jm1];
+    const float *ph = H + (int64_t)a * st, *pl = L + (int64_t)a * st;
+#pragma unroll
+    for (int k = 0; k <= RPT + 1; ++k) {
+        float hp, lp;
+        if (k < RPT) {
+            hp = *ph; lp = *pl;
+            ph += st; pl += st;
+        } else {
+            const int64_t j = wrap_or_clamp<BC>(a + k, n) * st;
+            hp = H[j]; lp = L[j];
+        }
+        const float v = sdiff_pair(hm, h0, hp, lm, l0, lp);     // centre a + k - 1
+        if (k == 0) rl = v; else if (k == RPT + 1) rr = v; else r[k - 1] = v;
+        hm = h0; h0 = hp; lm = l0; l0 = lp;
+    }
+}
+
+template <int BC, int RPT>
+__device__ __forceinline__ void strided_r_pair(const ProgParams &pr, int64_t lbase, int64_t st, int a, int n,
+                                               double (&r)[RPT], double &rl, double &rr)
+{
+    const double *U = (const double *)pr.u_hi + lbase;
+    double um = U[wrap_or_clamp<BC>(a - 2, n) * st], u0 = U[wrap_or_clamp<BC>(a - 1, n) * st];
+    const double *pu = U + (int64_t)a * st;
+#pragma unroll
+    for (int k = 0; k <= RPT + 1; ++k) {
+        double up;
+        if (k < RPT) { up = *pu; pu += st; }
+        else up = U[wrap_or_clamp<BC>(a + k, n) * st];
+        const double v = (up - u0) - (u0 - um);
+        if (k == 0) rl = v; else if (k == RPT + 1) rr = v; else r[k - 1] = v;
+        um = u0; u0 = up;
+    }
+}
+
+template <class T, int BC, int RPT, bool HORNER>
+__global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgParams pr)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StridedCtx<T> c{cg::this_cluster()};
+    c.S = LS.S;
+    c.K = LS.K;
+    c.w = threadIdx.x >> 5;
+    c.lane = threadIdx.x & 31;
+    c.krank = LS.K > 1 ? (int)c.cl.block_rank() : 0;
+    c.n = A.n;
+    c.d = (T)A.d;
+    c.dR = (T)A.dm[0];
+    c.dpg = dpow_of<T>(A);
+    c.Gd = A.n / RPT;
+    c.seg = c.krank * c.S + c.w;
+    c.a = c.seg * RPT;
+    c.full = c.seg < c.Gd;
+    {
+        T *p = reinterpret_cast<T *>(smem_raw);
+        c.sl.E = p;
+        c.sl.ER = p + c.S * 32;
+        c.sl.H = p + 2 * c.S * 32;
+        c.sl.Tot = p + 6 * c.S * 32;
+    }
+    T *rbuf = reinterpret_cast<T *>(smem_raw + strided_slot_bytes(c.S, sizeof(T)));   // [S][RPT][32]
+    const int n = c.n, a = c.a;
+
+    const int64_t line = (int64_t)blockIdx.x * 32 + c.lane;
+    const bool valid = line < LS.nlines;
+    const bool io = valid && c.full;
+    const int64_t lbase = valid ? (line % LS.inner) + (line / LS.inner) * LS.inner * (int64_t)n : 0;
+    const int64_t st = LS.stride;
+
+    // r = accurate second difference of u along the line (Dirichlet end
+    // nodes use the neighbouring interior centre)
+    T z[RPT];
+    T rl = 0, rr = 0;
+    if (io) strided_r_pair<BC, RPT>(pr, lbase, st, a, n, z, rl, rr);
+    else {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+    }
+    if (BC == BC_DIRICHLET) {
+        if (c.seg == 0) z[0] = z[1];
+        if (c.seg == c.Gd - 1) z[RPT - 1] = z[RPT - 2];
+    }
+
+    if (!HORNER) {
+        // powers; the first sweep starts from s = r
+        for (int p = 1; p <= pr.P; ++p) {
+            if (p == 1) {
+                strided_sweep<T, BC, RPT, 0>(c, A, z, (T)0, (T)0, rl, rr, (T)0, nullptr, (T)0, (T)0);
+            } else {
+                T l2, l1, r0, r1;
+                strided_halos<T, BC, RPT>(c, z, l2, l1, r0, r1);
+                strided_sweep<T, BC, RPT, 1>(c, A, z, (T)0, l2, l1, r0, r1, nullptr, (T)0, (T)0);
+            }
+            T *o = reinterpret_cast<T *>(pr.out[p - 1]);
+            if (o != nullptr && io) {
+                T *po = o + lbase + (int64_t)a * st;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) { *po = z[k]; po += st; }
+            }
+        }
+        return;
+    }
+
+    // Horner: r kept on chip, lane-interleaved
+    T *rs = rbuf + (size_t)c.w * RPT * 32 + c.lane;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) rs[k * 32] = z[k];
+    const int P = pr.P, ng = pr.ng;
+    for (int o = 0; o < pr.nout; ++o) {
+        const double *cfo = pr.coef + (size_t)o * (P + 1) * ng;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+        for (int t = P; t >= 0; --t) {
+            const double *cf = cfo + (size_t)t * ng;
+            if (io) {
+                for (int q = 0; q < ng; ++q) {
+                    const T cq = (T)__ldg(cf + q);
+                    if (cq == (T)0) continue;
+                    const T *gq = reinterpret_cast<const T *>(pr.g[q]) + lbase + (int64_t)a * st;
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) { z[k] += cq * *gq; gq += st; }
+                }
+            }
+            if (t == 0) break;
+            T l2, l1, r0, r1;
+            strided_halos<T, BC, RPT>(c, z, l2, l1, r0, r1);
+            strided_sweep<T, BC, RPT, 2>(c, A, z, (T)__ldg(pr.cu + (size_t)o * (P + 1) + t), l2, l1, r0, r1, rs, rl, rr);
+        }
+        T *ob = reinterpret_cast<T *>(pr.out[o]);
+        if (io) {
+            T *po = ob + lbase + (int64_t)a * st;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) { *po = z[k]; po += st; }
+        }
+    }
+}
+
+}  // namespace molt

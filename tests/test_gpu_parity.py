@@ -271,3 +271,60 @@ def test_full_size_3d_fourier_one_step():
     smx = molt.Solver((n, n, n), dt=dt, P=P, bc="periodic", prec="mixed", **box)
     got = smx.apply_F(dev(u0)).cpu().numpy()
     assert rel_l2(got, ref) <= tol_for("mixed", smx, 2 * P), rel_l2(got, ref)
+
+
+# ---------------------------------------------------------------------------
+# shapes whose lines are whole multiples of the register segment length, so
+# the register-resident kernels run (x: 32*RPT >= n with RPT | n; strided
+# axes: 64 | n for float32, 32 | n for float64; 2048-point strided lines are
+# split over a 4-CTA (float32) or 8-CTA (float64) cluster)
+# ---------------------------------------------------------------------------
+REG_SHAPES = [(64,), (512,), (2048,), (128, 256), (2048, 64), (256, 512), (64, 64, 128), (128, 64, 32)]
+
+
+@pytest.mark.parametrize("shape", REG_SHAPES)
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_register_kernels_apply_D(shape, bc, prec):
+    if prec == "fp64" and shape[-1] > 1024:
+        pytest.skip("float64 contiguous lines longer than 1024 use the shared-memory kernels")
+    dt = 1.5 / max(shape)
+    s = make(shape, dt, 3, bc, prec)
+    v = field(shape, 31, bc)
+    vd = dev(v)
+    for axis in range(len(shape)):
+        for power in (1, 3):
+            got = s.apply_D(vd, axis, power).cpu().numpy()
+            ref = oracle.D_axis(v, axis, s.nu[axis], bc, 2, power=power)
+            err = rel_l2(got, ref)
+            assert err <= tol_for(prec, s, power, cond_of(v, ref)), (axis, power, err)
+
+
+@pytest.mark.parametrize("shape, P", [((2048,), 3), ((128, 256), 3), ((2048, 64), 2), ((256, 512), 1),
+                                      ((64, 64, 128), 2), ((128, 64, 32), 3)])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_register_kernels_F_and_steps(shape, P, bc, prec):
+    if prec == "fp64" and shape[-1] > 1024:
+        pytest.skip("float64 contiguous lines longer than 1024 use the shared-memory kernels")
+    dt = 2.0 / max(shape)
+    s = make(shape, dt, P, bc, prec)
+    u = field(shape, 41, bc)
+    got = s.apply_F(dev(u)).cpu().numpy()
+    ref = oracle.F(u, s.nu, P, s.beta, bc)
+    assert rel_l2(got, ref) <= tol_for(prec, s, 2 * P), rel_l2(got, ref)
+    u0 = smooth_field(shape, 42, bc)
+    u1 = oracle.start(u0, s.nu, P, s.beta, bc)
+    up, uc = dev(u0), dev(u1)
+    nsteps = 6
+    s.step(up, uc, nsteps)
+    rp, rc = oracle.run(u0, u1, nsteps, s.nu, P, s.beta, bc)
+    tol = 1e-12
+    if prec == "mixed":
+        Fsum, a, b = 0.0, u0, u1
+        for _ in range(nsteps):
+            F = oracle.F(b, s.nu, P, s.beta, bc)
+            Fsum += np.linalg.norm(F)
+            a, b = b, 2 * b - a + F
+        tol = 8 * EPS32 * (1 + 1 / (1 - max(s.d))) * 2 * P * Fsum / np.linalg.norm(rc)
+    assert rel_l2(uc.cpu().numpy(), rc) <= tol
