@@ -305,6 +305,80 @@ __device__ __forceinline__ void level_vec(const ProgParams &p, int64_t i, const 
     *reinterpret_cast<double2 *>((double *)p.un_hi + i) = v;
 }
 
+// level combination of CH vectors per lane (v = lane + 32*(i0+i)), all
+// loads issued before any store
+template <class T, int CH> struct LevelBatch;
+template <int CH> struct LevelBatch<float, CH> {
+    __device__ static void run(const ProgParams &p, int64_t base, int lane, int i0, int nvec, const float4 (&F)[CH])
+    {
+        const float4 *__restrict__ UH = reinterpret_cast<const float4 *>((const float *)p.u_hi + base);
+        const float4 *__restrict__ UL = reinterpret_cast<const float4 *>((const float *)p.u_lo + base);
+        const float4 *__restrict__ PH = reinterpret_cast<const float4 *>((const float *)p.up_hi + base);
+        const float4 *__restrict__ PL = reinterpret_cast<const float4 *>((const float *)p.up_lo + base);
+        float4 uh[CH], ul[CH], ph[CH], pl[CH];
+        const bool prev = p.eb != 0.0;
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int v = lane + 32 * (i0 + i);
+            if (v < nvec) {
+                uh[i] = __ldg(UH + v);
+                ul[i] = __ldg(UL + v);
+                ph[i] = prev ? __ldg(PH + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                pl[i] = prev ? __ldg(PL + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        const float ea = (float)p.ea, eb = (float)p.eb, ec = (float)p.ec;
+        float4 *NH = reinterpret_cast<float4 *>((float *)p.un_hi + base);
+        float4 *NL = reinterpret_cast<float4 *>((float *)p.un_lo + base);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int v = lane + 32 * (i0 + i);
+            if (v < nvec) {
+                float4 nh, nl;
+                level_pair(uh[i].x, ul[i].x, ph[i].x, pl[i].x, F[i].x, ea, eb, ec, nh.x, nl.x);
+                level_pair(uh[i].y, ul[i].y, ph[i].y, pl[i].y, F[i].y, ea, eb, ec, nh.y, nl.y);
+                level_pair(uh[i].z, ul[i].z, ph[i].z, pl[i].z, F[i].z, ea, eb, ec, nh.z, nl.z);
+                level_pair(uh[i].w, ul[i].w, ph[i].w, pl[i].w, F[i].w, ea, eb, ec, nh.w, nl.w);
+                NH[v] = nh;
+                NL[v] = nl;
+            }
+        }
+    }
+};
+template <int CH> struct LevelBatch<double, CH> {
+    __device__ static void run(const ProgParams &p, int64_t base, int lane, int i0, int nvec, const double2 (&F)[CH])
+    {
+        const double2 *__restrict__ U = reinterpret_cast<const double2 *>((const double *)p.u_hi + base);
+        const double2 *__restrict__ Q = reinterpret_cast<const double2 *>((const double *)p.up_hi + base);
+        double2 u[CH], q[CH];
+        const bool prev = p.eb != 0.0;
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int v = lane + 32 * (i0 + i);
+            if (v < nvec) {
+                u[i] = __ldg(U + v);
+                q[i] = prev ? __ldg(Q + v) : make_double2(0.0, 0.0);
+            }
+        }
+        double2 *N = reinterpret_cast<double2 *>((double *)p.un_hi + base);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int v = lane + 32 * (i0 + i);
+            if (v < nvec) {
+                double2 r;
+                r.x = p.ea * u[i].x + p.ec * F[i].x + p.eb * q[i].x;
+                r.y = p.ea * u[i].y + p.ec * F[i].y + p.eb * q[i].y;
+                N[v] = r;
+            }
+        }
+    }
+};
+template <class T, int CH, class V>
+__device__ __forceinline__ void level_batch(const ProgParams &p, int64_t base, int lane, int i0, int nvec, const V (&F)[CH])
+{
+    LevelBatch<T, CH>::run(p, base, lane, i0, nvec, F);
+}
+
 template <class V> __device__ __forceinline__ V vfma(typename std::remove_reference<decltype(V().x)>::type c, const V &a, const V &b);
 template <> __device__ __forceinline__ float4 vfma<float4>(float c, const float4 &a, const float4 &b)
 {
@@ -328,22 +402,34 @@ struct CoalescedSide {
 };
 
 // stage <- stage + sum_k coef[k] g_k[base + .] over the line (coalesced),
-// one pass per field with a non-zero weight
+// one pass per field with a non-zero weight; every lane first issues all the
+// loads of its share of the row (up to RPT/VN vectors) so that they are in
+// flight together, then accumulates.
 template <class T, int RPT>
 __device__ __forceinline__ void stage_accumulate(T *stage, const ProgParams &pr, const double *cf, int64_t base, int n,
                                                  int lane)
 {
     using V = typename VecOf<T>::type;
     constexpr int VN = VecOf<T>::n;
+    constexpr int NV = RPT / VN;                    // vectors per lane (n <= 32*RPT)
     const int nvec = n / VN;                        // n is a multiple of RPT, hence of VN
     for (int k = 0; k < pr.ng; ++k) {
         const T ck = (T)__ldg(cf + k);
         if (ck == (T)0) continue;
-        const V *src = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.g[k]) + base);
-#pragma unroll 4
-        for (int v = lane; v < nvec; v += 32) {
-            V *d = CoalescedSide<T, RPT>::at(stage, v * VN);
-            *d = vfma<V>(ck, src[v], *d);
+        const V *__restrict__ src = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.g[k]) + base);
+        V buf[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int v = lane + 32 * i;
+            if (v < nvec) buf[i] = __ldg(src + v);
+        }
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int v = lane + 32 * i;
+            if (v < nvec) {
+                V *d = CoalescedSide<T, RPT>::at(stage, v * VN);
+                *d = vfma<V>(ck, buf[i], *d);
+            }
         }
     }
 }
@@ -360,12 +446,22 @@ __device__ __forceinline__ void contig_r(T (&z)[RPT], T *stage, T *rline, const 
     constexpr int VN = VecOf<T>::n;
     const int nvec = n / VN;
     const bool pair = sizeof(T) == 4;
-    const V *H = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.u_hi) + base);
-    const V *L = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.u_lo) + base);
-#pragma unroll 4
-    for (int v = lane; v < nvec; v += 32) {
-        *CoalescedSide<T, RPT>::at(stage, v * VN) = H[v];
-        if (pair) *CoalescedSide<T, RPT>::at(rline, v * VN) = L[v];
+    constexpr int NV = RPT / VN;
+    {
+        const V *__restrict__ H = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.u_hi) + base);
+        V buf[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) if (lane + 32 * i < nvec) buf[i] = __ldg(H + lane + 32 * i);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) if (lane + 32 * i < nvec) *CoalescedSide<T, RPT>::at(stage, (lane + 32 * i) * VN) = buf[i];
+    }
+    if (pair) {
+        const V *__restrict__ Lo = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.u_lo) + base);
+        V buf[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) if (lane + 32 * i < nvec) buf[i] = __ldg(Lo + lane + 32 * i);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) if (lane + 32 * i < nvec) *CoalescedSide<T, RPT>::at(rline, (lane + 32 * i) * VN) = buf[i];
     }
     __syncwarp();
     const int a = lane * RPT;
@@ -467,8 +563,18 @@ __global__ void __launch_bounds__(32 * WARPS, 3) k_contig(AxisDev A, LineSet LS,
     }
     // out = stage (coalesced side): level combination or plain store
     if (pr.epi) {
-#pragma unroll 4
-        for (int v = lane; v < nvec; v += 32) level_vec(pr, base + (int64_t)v * VN, *CoalescedSide<T, RPT>::at(stage, v * VN));
+        constexpr int NV = RPT / VN;
+        constexpr int CH = NV > 4 ? 4 : NV;          // vectors per lane per batch
+#pragma unroll
+        for (int i0 = 0; i0 < NV; i0 += CH) {
+            V F[CH];
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
+                const int v = lane + 32 * (i0 + i);
+                if (v < nvec) F[i] = *CoalescedSide<T, RPT>::at(stage, v * VN);
+            }
+            level_batch<T, CH>(pr, base, lane, i0, nvec, F);
+        }
     } else {
         V *o = reinterpret_cast<V *>(reinterpret_cast<T *>(pr.out[0]) + base);
 #pragma unroll 4
@@ -483,11 +589,11 @@ template <class T>
 struct StridedSlots {
     T *E;      // [S][32] causal segment reductions
     T *ER;     // [S][32] anti-causal segment reductions
-    T *H;      // [S][4][32] first two / last two values of each segment
+    T *H;      // [2][S][4][32] first two / last two values of each segment, two sets
     T *Tot;    // [2][32] CTA totals (causal, anti-causal)
 };
 
-__host__ __device__ inline size_t strided_slot_bytes(int S, size_t tsize) { return (6 * (size_t)S * 32 + 64) * tsize; }
+__host__ __device__ inline size_t strided_slot_bytes(int S, size_t tsize) { return (10 * (size_t)S * 32 + 64) * tsize; }
 
 template <class T>
 struct StridedCtx {
@@ -566,9 +672,11 @@ __device__ __forceinline__ void strided_anticausal(const StridedCtx<T> &c, T ER,
 
 // halo exchange: z at a-2, a-1 and a+RPT, a+RPT+1
 template <class T, int BC, int RPT>
-__device__ __forceinline__ void strided_halos(const StridedCtx<T> &c, const T (&z)[RPT], T &l2, T &l1, T &r0, T &r1)
+__device__ __forceinline__ void strided_halos(const StridedCtx<T> &c, const T (&z)[RPT], T &l2, T &l1, T &r0, T &r1,
+                                              int buf)
 {
-    T *H = c.sl.H + c.w * 128;
+    T *Hb = c.sl.H + buf * c.S * 128;
+    T *H = Hb + c.w * 128;
     H[c.lane] = z[0];
     H[32 + c.lane] = z[1];
     H[64 + c.lane] = z[RPT - 2];
@@ -581,16 +689,18 @@ __device__ __forceinline__ void strided_halos(const StridedCtx<T> &c, const T (&
     }
     l2 = l1 = r0 = r1 = 0;
     if (gl >= 0) {
-        const T *Hl = peer_of(c, c.sl.H, gl / c.S) + (gl % c.S) * 128;
+        const T *Hl = peer_of(c, Hb, gl / c.S) + (gl % c.S) * 128;
         l2 = Hl[64 + c.lane];
         l1 = Hl[96 + c.lane];
     }
     if (gr < c.Gd) {
-        const T *Hr = peer_of(c, c.sl.H, gr / c.S) + (gr % c.S) * 128;
+        const T *Hr = peer_of(c, Hb, gr / c.S) + (gr % c.S) * 128;
         r0 = Hr[c.lane];
         r1 = Hr[32 + c.lane];
     }
-    csync(c);   // the slots are rewritten only after everyone has read them
+    // two alternating slot sets: a set is written again only after two more
+    // cluster barriers (the causal and anti-causal exchanges of the sweep),
+    // by which time every reader is done with it
 }
 
 // One application of D on this thread's segment.  MODE as in seg_make_q;
@@ -710,7 +820,7 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
         c.sl.E = p;
         c.sl.ER = p + c.S * 32;
         c.sl.H = p + 2 * c.S * 32;
-        c.sl.Tot = p + 6 * c.S * 32;
+        c.sl.Tot = p + 10 * c.S * 32;
     }
     T *rbuf = reinterpret_cast<T *>(smem_raw + strided_slot_bytes(c.S, sizeof(T)));   // [S][RPT][32]
     const int n = c.n, a = c.a;
@@ -742,7 +852,7 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
                 strided_sweep<T, BC, RPT, 0>(c, A, z, (T)0, (T)0, rl, rr, (T)0, nullptr, (T)0, (T)0);
             } else {
                 T l2, l1, r0, r1;
-                strided_halos<T, BC, RPT>(c, z, l2, l1, r0, r1);
+                strided_halos<T, BC, RPT>(c, z, l2, l1, r0, r1, p & 1);
                 strided_sweep<T, BC, RPT, 1>(c, A, z, (T)0, l2, l1, r0, r1, nullptr, (T)0, (T)0);
             }
             T *o = reinterpret_cast<T *>(pr.out[p - 1]);
@@ -760,6 +870,7 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
 #pragma unroll
     for (int k = 0; k < RPT; ++k) rs[k * 32] = z[k];
     const int P = pr.P, ng = pr.ng;
+    int hpar = 0;
     for (int o = 0; o < pr.nout; ++o) {
         const double *cfo = pr.coef + (size_t)o * (P + 1) * ng;
 #pragma unroll
@@ -777,7 +888,8 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
             }
             if (t == 0) break;
             T l2, l1, r0, r1;
-            strided_halos<T, BC, RPT>(c, z, l2, l1, r0, r1);
+            strided_halos<T, BC, RPT>(c, z, l2, l1, r0, r1, hpar);
+            hpar ^= 1;
             strided_sweep<T, BC, RPT, 2>(c, A, z, (T)__ldg(pr.cu + (size_t)o * (P + 1) + t), l2, l1, r0, r1, rs, rl, rr);
         }
         T *ob = reinterpret_cast<T *>(pr.out[o]);
