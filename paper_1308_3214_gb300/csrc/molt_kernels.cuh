@@ -237,6 +237,9 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
     }
 
     // ---- causal carries: y at a-1 ----
+    // reconverge the warp before the shuffles (lanes ran loops of different
+    // lengths; __shfl_sync pairs lanes by mask, not by call site)
+    __syncwarp();
     T x = E;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -264,6 +267,7 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
     }
 
     // ---- anti-causal carries ----
+    __syncwarp();
     T xb = ER;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {

@@ -168,6 +168,10 @@ __device__ __forceinline__ void warp_sweep(T (&z)[RPT], const T *rline, T cu, co
     const bool full = lane <= Ld;
     const int a = lane * RPT;
 
+    // Lanes diverge in the predicated per-lane code; __shfl_sync pairs lanes by
+    // mask, not by call site, so the warp is reconverged before every group of
+    // shuffles (consecutive sweeps otherwise exchanged values across sweeps).
+    __syncwarp();
     T zl1 = __shfl_up_sync(0xffffffffu, z[RPT - 1], 1);
     T zl2 = __shfl_up_sync(0xffffffffu, z[RPT - 2], 1);
     T zr0 = __shfl_down_sync(0xffffffffu, z[0], 1);
@@ -175,8 +179,10 @@ __device__ __forceinline__ void warp_sweep(T (&z)[RPT], const T *rline, T cu, co
     if (BC == BC_PERIODIC) {
         const T w1 = __shfl_sync(0xffffffffu, z[RPT - 1], Ld), w2 = __shfl_sync(0xffffffffu, z[RPT - 2], Ld);
         const T v0 = __shfl_sync(0xffffffffu, z[0], 0), v1 = __shfl_sync(0xffffffffu, z[1], 0);
-        if (lane == 0) { zl1 = w1; zl2 = w2; }
-        if (lane == Ld) { zr0 = v0; zr1 = v1; }
+        zl1 = (lane == 0) ? w1 : zl1;
+        zl2 = (lane == 0) ? w2 : zl2;
+        zr0 = (lane == Ld) ? v0 : zr0;
+        zr1 = (lane == Ld) ? v1 : zr1;
     } else {
         end_ghosts<T, RPT, MODE>(z, lane == 0, lane == Ld, zl2, zl1, zr0, zr1);
     }
@@ -192,51 +198,53 @@ __device__ __forceinline__ void warp_sweep(T (&z)[RPT], const T *rline, T cu, co
         seg_make_q<T, RPT, MODE>(z, zl2, zl1, zr0, zr1, [&](int) { return (T)0; }, (T)0, c1, c2);
     }
     if (BC == BC_DIRICHLET) end_zero<T, RPT>(z, lane == 0, lane == Ld);
-    if (!full) {
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) z[k] = 0;
-    }
+    for (int k = 0; k < RPT; ++k) z[k] = full ? z[k] : (T)0;
 
-    // causal carries: Kogge-Stone over lanes with multipliers d^{RPT 2^k}
+    // causal carries: Kogge-Stone over lanes with multipliers d^{RPT 2^k};
+    // all shuffles of a group run before any lane-dependent branch
     const T E = seg_fwd_reduce<T, RPT>(z, d);
+    __syncwarp();
     T x = E;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const T y = __shfl_up_sync(0xffffffffu, x, 1 << k);
-        if (lane >= (1 << k)) x += (T)A.dm[k] * y;
+        x = (lane >= (1 << k)) ? x + (T)A.dm[k] * y : x;
     }
     T yin = __shfl_up_sync(0xffffffffu, x, 1);
-    if (lane == 0) yin = 0;
+    const T tot = __shfl_sync(0xffffffffu, x, Ld);              // zero-inflow y_{n-1}
+    yin = (lane == 0) ? (T)0 : yin;
     const T *dpg = dpow_of<T>(A);
-    if (BC == BC_PERIODIC) {
-        const T tot = __shfl_sync(0xffffffffu, x, Ld);          // zero-inflow y_{n-1}
-        if (full) yin += dpg[a] * (tot * (T)A.inv);               // images to the left
-    }
-    if (!full) yin = 0;                                            // lanes past the line stay zero
+    if (BC == BC_PERIODIC)
+        yin += full ? dpg[a] * (tot * (T)A.inv) : (T)0;          // images to the left
+    yin = full ? yin : (T)0;                                     // lanes past the line stay zero
     const T ER = seg_fwd_scan<T, RPT>(z, d, yin);
 
     // anti-causal carries
+    __syncwarp();
     T xb = ER;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const T t = __shfl_down_sync(0xffffffffu, xb, 1 << k);
-        if (lane + (1 << k) < 32) xb += (T)A.dm[k] * t;
+        xb = (lane + (1 << k) < 32) ? xb + (T)A.dm[k] * t : xb;
     }
     T exclb = __shfl_down_sync(0xffffffffu, xb, 1);
-    if (lane == 31) exclb = 0;
     const T e00 = __shfl_sync(0xffffffffu, xb, 0);              // zero-inflow e_0
+    const T yl = __shfl_sync(0xffffffffu, z[RPT - 1], Ld);      // y_{n-1}
+    exclb = (lane == 31) ? (T)0 : exclb;
     T Z, Acoef = 0;
     if (BC == BC_DIRICHLET) {
-        const T yl = __shfl_sync(0xffffffffu, z[RPT - 1], Ld);  // y_{n-1}
         const T mu = (T)A.mu, inv = (T)A.inv;
         Acoef = (mu * yl - e00) * inv;
         Z = (mu * e00 - yl) * inv;
     } else {
         Z = d * e00 * (T)A.inv;
     }
-    const T acc = d * exclb + (full ? dpg[n - a - RPT] * Z : (T)0);
+    const int ia = full ? a : 0, ib = full ? n - a - RPT : 0;   // table indices in [0, n]
+    const T acc = d * exclb + (full ? dpg[ib] * Z : (T)0);
     seg_bwd_scan<T, RPT>(z, d, acc);
-    if (BC == BC_DIRICHLET && full) seg_add_left<T, RPT>(z, d, Acoef * dpg[a]);
+    if (BC == BC_DIRICHLET && full) seg_add_left<T, RPT>(z, d, Acoef * dpg[ia]);
+    __syncwarp();
 }
 
 // stage (coalesced side) -> registers (segment side)
