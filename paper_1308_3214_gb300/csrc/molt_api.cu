@@ -388,7 +388,9 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
     if (st != MOL_OK) return st;
     int rpt = 0, S = 0, K = 0;
     cudaError_t e;
-    if (axis == 0 && regs_contig_plan(h->tbytes, h->bc, n, &rpt)) {
+    if (axis == 0 && pr.mode == 1 && pr.nout == 1 && regs_res_plan(h->tbytes, n, pr.ng, &rpt)) {
+        e = launch_res(h->bc, rpt, pr.ng, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
+    } else if (axis == 0 && regs_contig_plan(h->tbytes, h->bc, n, &rpt)) {
         e = launch_contig(h->tbytes, h->bc, rpt, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
     } else if (axis > 0 && regs_strided_plan(h->tbytes, h->bc, n, &rpt, &S, &K)) {
         LineSet L = lineset_of(h, axis);

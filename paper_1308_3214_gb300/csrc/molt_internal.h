@@ -33,5 +33,7 @@ cudaError_t launch_contig(int tbytes, int bc, int rpt, const AxisDev &A, const L
 cudaError_t launch_strided(int tbytes, int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
                            cudaStream_t s);
 cudaError_t configure_regs_kernels();
+bool regs_res_plan(int tbytes, int n, int ng, int *rpt);
+cudaError_t launch_res(int bc, int rpt, int ng, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s);
 
 }  // namespace molt

@@ -7,6 +7,25 @@ namespace molt {
 namespace {
 
 constexpr int kContigWarps = 4;
+constexpr int kResWarps = 2;
+
+template <int RPT, int NB>
+size_t res_smem() { return (size_t)kResWarps * (NB + 1) * ContigStage<float, RPT>::LINE * sizeof(float); }
+
+template <int BC, int RPT, int NB>
+cudaError_t run_res(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+{
+    const int64_t grid = (L.nlines + kResWarps - 1) / kResWarps;
+    k_contig_res<BC, RPT, NB, kResWarps><<<(unsigned)grid, 32 * kResWarps, res_smem<RPT, NB>(), s>>>(A, L, p);
+    return cudaGetLastError();
+}
+
+template <int BC, int RPT, int NB>
+cudaError_t attr_res()
+{
+    return cudaFuncSetAttribute(k_contig_res<BC, RPT, NB, kResWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)res_smem<RPT, NB>());
+}
 
 template <class T, int RPT>
 size_t contig_smem() { return (size_t)kContigWarps * 2 * ContigStage<T, RPT>::LINE * sizeof(T); }
@@ -133,10 +152,53 @@ cudaError_t launch_strided(int tbytes, int bc, int rpt, const AxisDev &A, const 
     return cudaErrorInvalidValue;
 }
 
+// float32 Horner pass with the fields resident: up to 3 fields
+bool regs_res_plan(int tbytes, int n, int ng, int *rpt)
+{
+    if (tbytes != 4 || ng > 3) return false;
+    for (int r = 8; r <= 64; r *= 2) {
+        if (32 * r < n) continue;
+        if (n % r != 0) return false;
+        *rpt = r;
+        return true;
+    }
+    return false;
+}
+
+cudaError_t launch_res(int bc, int rpt, int ng, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+{
+#define MOLT_RES(BC)                                                                      \
+    switch (rpt * 10 + (ng < 1 ? 1 : ng)) {                                               \
+    case 81: return run_res<BC, 8, 1>(A, L, p, s);                                        \
+    case 82: return run_res<BC, 8, 2>(A, L, p, s);                                        \
+    case 83: return run_res<BC, 8, 3>(A, L, p, s);                                        \
+    case 161: return run_res<BC, 16, 1>(A, L, p, s);                                      \
+    case 162: return run_res<BC, 16, 2>(A, L, p, s);                                      \
+    case 163: return run_res<BC, 16, 3>(A, L, p, s);                                      \
+    case 321: return run_res<BC, 32, 1>(A, L, p, s);                                      \
+    case 322: return run_res<BC, 32, 2>(A, L, p, s);                                      \
+    case 323: return run_res<BC, 32, 3>(A, L, p, s);                                      \
+    case 641: return run_res<BC, 64, 1>(A, L, p, s);                                      \
+    case 642: return run_res<BC, 64, 2>(A, L, p, s);                                      \
+    case 643: return run_res<BC, 64, 3>(A, L, p, s);                                      \
+    default: break;                                                                       \
+    }
+    if (bc == BC_PERIODIC) { MOLT_RES(BC_PERIODIC) }
+    else { MOLT_RES(BC_DIRICHLET) }
+#undef MOLT_RES
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t configure_regs_kernels()
 {
     cudaError_t e;
 #define MOLT_A(x) if ((e = (x)) != cudaSuccess) return e;
+#define MOLT_RA(BC) MOLT_A((attr_res<BC, 8, 1>())) MOLT_A((attr_res<BC, 8, 2>())) MOLT_A((attr_res<BC, 8, 3>())) \
+    MOLT_A((attr_res<BC, 16, 1>())) MOLT_A((attr_res<BC, 16, 2>())) MOLT_A((attr_res<BC, 16, 3>()))             \
+    MOLT_A((attr_res<BC, 32, 1>())) MOLT_A((attr_res<BC, 32, 2>())) MOLT_A((attr_res<BC, 32, 3>()))             \
+    MOLT_A((attr_res<BC, 64, 1>())) MOLT_A((attr_res<BC, 64, 2>())) MOLT_A((attr_res<BC, 64, 3>()))
+    MOLT_RA(BC_PERIODIC) MOLT_RA(BC_DIRICHLET)
+#undef MOLT_RA
     MOLT_A((attr_contig<float, BC_PERIODIC, 8>())) MOLT_A((attr_contig<float, BC_PERIODIC, 16>()))
     MOLT_A((attr_contig<float, BC_PERIODIC, 32>())) MOLT_A((attr_contig<float, BC_PERIODIC, 64>()))
     MOLT_A((attr_contig<float, BC_DIRICHLET, 8>())) MOLT_A((attr_contig<float, BC_DIRICHLET, 16>()))

@@ -591,6 +591,159 @@ __global__ void __launch_bounds__(32 * WARPS, 3) k_contig(AxisDev A, LineSet LS,
 }
 
 // ---------------------------------------------------------------------------
+// contiguous axis, float32 Horner pass with the input fields resident
+// ---------------------------------------------------------------------------
+// Each warp copies the NG input rows of its line into shared memory once,
+// with cp.async (16-byte pieces, coalesced global side, padded segment
+// layout in shared memory), while it forms r = second difference of u in
+// registers from coalesced 16-byte loads.  All Horner steps then read the
+// fields from shared memory: a row costs a handful of memory round trips
+// instead of one per field and step.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// second difference of a pair field at 4 consecutive points, given the
+// points left (before .x) and right (after .w)
+__device__ __forceinline__ float4 sdiff4(const float4 &h, const float4 &l, float hl, float ll, float hr, float lr)
+{
+    float4 r;
+    r.x = sdiff_pair(hl, h.x, h.y, ll, l.x, l.y);
+    r.y = sdiff_pair(h.x, h.y, h.z, l.x, l.y, l.z);
+    r.z = sdiff_pair(h.y, h.z, h.w, l.y, l.z, l.w);
+    r.w = sdiff_pair(h.z, h.w, hr, l.z, l.w, lr);
+    return r;
+}
+
+template <int BC, int RPT, int NB, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_contig_res(AxisDev A, LineSet LS, ProgParams pr)
+{
+    static_assert(RPT % 4 == 0 && RPT >= 8, "segment length");
+    using T = float;
+    using St = ContigStage<T, RPT>;
+    constexpr int NVL = RPT / 4;                 // vectors per lane when n = 32*RPT
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *R = reinterpret_cast<T *>(smem_raw) + (size_t)warp * (NB + 1) * St::LINE;
+    T *B = R + St::LINE;                        // NB field buffers, St::LINE apart
+    const int n = A.n;
+    const int64_t L = (int64_t)blockIdx.x * WARPS + warp;
+    if (L >= LS.nlines) return;
+    const int64_t base = L * (int64_t)n;
+    const int nvec = n / 4;
+    const int ng = pr.ng;
+
+    // 1. fields -> shared memory (asynchronous)
+    for (int k = 0; k < ng; ++k) {
+        const float4 *src = reinterpret_cast<const float4 *>(reinterpret_cast<const T *>(pr.g[k]) + base);
+        T *dst = B + k * St::LINE;
+#pragma unroll
+        for (int i = 0; i < NVL; ++i) {
+            const int v = lane + 32 * i;
+            if (v < nvec) cp_async16(dst + St::pos(4 * v), src + v);
+        }
+    }
+    cp_async_commit();
+
+    // 2. r = second difference of u (pair levels), coalesced, into R; every
+    //    load of the row (and of the points just past each 128-point chunk)
+    //    is issued before any is used
+    {
+        const T *H = reinterpret_cast<const T *>(pr.u_hi) + base, *Lo = reinterpret_cast<const T *>(pr.u_lo) + base;
+        const float4 *H4 = reinterpret_cast<const float4 *>(H), *L4 = reinterpret_cast<const float4 *>(Lo);
+        float4 h[NVL], l[NVL];
+        float hx[NVL], lx[NVL];        // lane 0: point before the chunk; lane 31: point after it
+#pragma unroll
+        for (int i = 0; i < NVL; ++i) {
+            const int v = lane + 32 * i;
+            if (v < nvec) { h[i] = __ldg(H4 + v); l[i] = __ldg(L4 + v); }
+            else { h[i] = make_float4(0.f, 0.f, 0.f, 0.f); l[i] = h[i]; }
+            int j = (lane == 0) ? 4 * v - 1 : 4 * v + 4;
+            if (BC == BC_PERIODIC) j = j < 0 ? j + n : (j >= n ? j - n : j);
+            else j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+            hx[i] = 0.f; lx[i] = 0.f;
+            if ((lane == 0 || lane == 31) && v < nvec) { hx[i] = __ldg(H + j); lx[i] = __ldg(Lo + j); }
+        }
+#pragma unroll
+        for (int i = 0; i < NVL; ++i) {
+            const int v = lane + 32 * i;
+            float hl = __shfl_up_sync(0xffffffffu, h[i].w, 1), ll = __shfl_up_sync(0xffffffffu, l[i].w, 1);
+            float hr = __shfl_down_sync(0xffffffffu, h[i].x, 1), lr = __shfl_down_sync(0xffffffffu, l[i].x, 1);
+            const int g0 = 4 * v;
+            // the last vector of the line may sit in any lane: its right neighbour is past the line
+            const bool last = (g0 + 4 == n);
+            if (lane == 0) { hl = hx[i]; ll = lx[i]; }
+            if (lane == 31) { hr = hx[i]; lr = lx[i]; }
+            if (last && lane != 31) {
+                const int j = (BC == BC_PERIODIC) ? 0 : n - 1;
+                hr = H[j]; lr = Lo[j];
+            }
+            if (v < nvec) {
+                float4 r = sdiff4(h[i], l[i], hl, ll, hr, lr);
+                if (BC == BC_DIRICHLET) {            // end nodes take the neighbouring interior centre
+                    if (g0 == 0) r.x = r.y;
+                    if (last) r.w = r.z;
+                }
+                *reinterpret_cast<float4 *>(R + St::pos(g0)) = r;
+            }
+        }
+        __syncwarp();
+    }
+    cp_async_wait_all();
+    __syncwarp();
+
+    // 3. Horner in D_x with the fields from shared memory
+    const int P = pr.P;
+    T z[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) z[k] = 0;
+    for (int t = P; t >= 0; --t) {
+        for (int k = 0; k < ng; ++k) {
+            const T c = (T)__ldg(pr.coef + (size_t)t * ng + k);
+            if (c == (T)0) continue;
+            const float4 *seg = reinterpret_cast<const float4 *>(B + k * St::LINE + lane * St::SST);
+#pragma unroll
+            for (int q = 0; q < RPT / 4; ++q) {
+                const float4 y = seg[q];
+                z[4 * q] += c * y.x;
+                z[4 * q + 1] += c * y.y;
+                z[4 * q + 2] += c * y.z;
+                z[4 * q + 3] += c * y.w;
+            }
+        }
+        if (t == 0) break;
+        warp_sweep<T, BC, RPT, 2>(z, R, (T)__ldg(pr.cu + t), A, lane);
+    }
+
+    // 4. F (segment layout) -> coalesced side -> next level
+    T *S0 = B;                                   // the first buffer is free now
+    __syncwarp();
+    regs_to_stage<T, RPT>(S0, z, lane);
+    __syncwarp();
+    if (pr.epi) {
+        constexpr int CH = NVL > 8 ? 8 : NVL;
+#pragma unroll
+        for (int i0 = 0; i0 < NVL; i0 += CH) {
+            float4 F[CH];
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
+                const int v = lane + 32 * (i0 + i);
+                if (v < nvec) F[i] = *CoalescedSide<T, RPT>::at(S0, v * 4);
+            }
+            level_batch<T, CH>(pr, base, lane, i0, nvec, F);
+        }
+    } else {
+        float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<T *>(pr.out[0]) + base);
+#pragma unroll 4
+        for (int v = lane; v < nvec; v += 32) o[v] = *CoalescedSide<T, RPT>::at(S0, v * 4);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // strided axes: lanes = 32 neighbouring lines, segments over warps and CTAs
 // ---------------------------------------------------------------------------
 template <class T>
