@@ -10,7 +10,7 @@ constexpr int kContigWarps = 4;
 constexpr int kResWarps = 2;
 
 template <int RPT, int NB>
-size_t res_smem() { return (size_t)kResWarps * (NB + 1) * ContigStage<float, RPT>::LINE * sizeof(float); }
+size_t res_smem() { return (size_t)kResWarps * NB * ContigStage<float, RPT>::LINE * sizeof(float); }
 
 template <int BC, int RPT, int NB>
 cudaError_t run_res(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)

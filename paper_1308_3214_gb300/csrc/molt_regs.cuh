@@ -158,10 +158,9 @@ struct ContigStage {
 
 // One application of D on a line held by a warp (lane = segment).  The line
 // has n = RPT * (Ld + 1) points; lanes past Ld hold zeros.
-template <class T, int BC, int RPT, int MODE>
-__device__ __forceinline__ void warp_sweep(T (&z)[RPT], const T *rline, T cu, const AxisDev &A, int lane)
+template <class T, int BC, int RPT, int MODE, class RF>
+__device__ __forceinline__ void warp_sweep_core(T (&z)[RPT], RF rfun, T cu, const AxisDev &A, int lane)
 {
-    using St = ContigStage<T, RPT>;
     const int n = A.n;
     const T d = (T)A.d;
     const int Ld = n / RPT - 1;
@@ -187,16 +186,7 @@ __device__ __forceinline__ void warp_sweep(T (&z)[RPT], const T *rline, T cu, co
         end_ghosts<T, RPT, MODE>(z, lane == 0, lane == Ld, zl2, zl1, zr0, zr1);
     }
     const T c1 = (T)A.c1, c2 = (T)A.c2;
-    if (MODE == 2) {
-        const T *rs = rline + lane * St::SST;
-        const int jl = a == 0 ? (BC == BC_PERIODIC ? n - 1 : 0) : a - 1;
-        const int jr = a + RPT >= n ? (BC == BC_PERIODIC ? 0 : n - 1) : a + RPT;
-        const T rl = rline[St::pos(jl)], rr = rline[St::pos(jr)];
-        seg_make_q<T, RPT, 2>(z, zl2, zl1, zr0, zr1,
-                              [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : rs[k]); }, cu, c1, c2);
-    } else {
-        seg_make_q<T, RPT, MODE>(z, zl2, zl1, zr0, zr1, [&](int) { return (T)0; }, (T)0, c1, c2);
-    }
+    seg_make_q<T, RPT, MODE>(z, zl2, zl1, zr0, zr1, rfun, cu, c1, c2);
     if (BC == BC_DIRICHLET) end_zero<T, RPT>(z, lane == 0, lane == Ld);
 #pragma unroll
     for (int k = 0; k < RPT; ++k) z[k] = full ? z[k] : (T)0;
@@ -245,6 +235,40 @@ __device__ __forceinline__ void warp_sweep(T (&z)[RPT], const T *rline, T cu, co
     seg_bwd_scan<T, RPT>(z, d, acc);
     if (BC == BC_DIRICHLET && full) seg_add_left<T, RPT>(z, d, Acoef * dpg[ia]);
     __syncwarp();
+}
+
+// D on the warp's line; MODE 2 takes r from the staging layout in shared memory
+template <class T, int BC, int RPT, int MODE>
+__device__ __forceinline__ void warp_sweep(T (&z)[RPT], const T *rline, T cu, const AxisDev &A, int lane)
+{
+    using St = ContigStage<T, RPT>;
+    if (MODE == 2) {
+        const int n = A.n, a = lane * RPT;
+        const T *rs = rline + lane * St::SST;
+        const int jl = a == 0 ? (BC == BC_PERIODIC ? n - 1 : 0) : a - 1;
+        const int jr = a + RPT >= n ? (BC == BC_PERIODIC ? 0 : n - 1) : a + RPT;
+        const T rl = rline[St::pos(min(jl, n - 1))], rr = rline[St::pos(min(jr, n - 1))];
+        warp_sweep_core<T, BC, RPT, 2>(z, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : rs[k]); }, cu, A, lane);
+    } else {
+        warp_sweep_core<T, BC, RPT, MODE>(z, [&](int) { return (T)0; }, (T)0, A, lane);
+    }
+}
+
+// D on the warp's line, MODE 2 with r held in registers (segment layout)
+template <class T, int BC, int RPT>
+__device__ __forceinline__ void warp_sweep_rreg(T (&z)[RPT], const T (&r)[RPT], T cu, const AxisDev &A, int lane)
+{
+    const int n = A.n;
+    const int Ld = n / RPT - 1;
+    __syncwarp();
+    T rl = __shfl_up_sync(0xffffffffu, r[RPT - 1], 1);
+    T rr = __shfl_down_sync(0xffffffffu, r[0], 1);
+    const T wl = __shfl_sync(0xffffffffu, r[RPT - 1], Ld), wr = __shfl_sync(0xffffffffu, r[0], 0);
+    if (BC == BC_PERIODIC) {
+        rl = (lane == 0) ? wl : rl;
+        rr = (lane == Ld) ? wr : rr;
+    }
+    warp_sweep_core<T, BC, RPT, 2>(z, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : r[k]); }, cu, A, lane);
 }
 
 // stage (coalesced side) -> registers (segment side)
@@ -628,8 +652,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_contig_res(AxisDev A, LineSet LS
     constexpr int NVL = RPT / 4;                 // vectors per lane when n = 32*RPT
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T *R = reinterpret_cast<T *>(smem_raw) + (size_t)warp * (NB + 1) * St::LINE;
-    T *B = R + St::LINE;                        // NB field buffers, St::LINE apart
+    T *B = reinterpret_cast<T *>(smem_raw) + (size_t)warp * NB * St::LINE;   // NB field buffers
+    T *R = B;                                    // staging for r before field 0 lands there
     const int n = A.n;
     const int64_t L = (int64_t)blockIdx.x * WARPS + warp;
     if (L >= LS.nlines) return;
@@ -637,8 +661,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_contig_res(AxisDev A, LineSet LS
     const int nvec = n / 4;
     const int ng = pr.ng;
 
-    // 1. fields -> shared memory (asynchronous)
-    for (int k = 0; k < ng; ++k) {
+    // 1. fields 1..ng-1 -> shared memory (asynchronous); field 0 after r
+    auto copy_field = [&](int k) {
         const float4 *src = reinterpret_cast<const float4 *>(reinterpret_cast<const T *>(pr.g[k]) + base);
         T *dst = B + k * St::LINE;
 #pragma unroll
@@ -646,7 +670,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_contig_res(AxisDev A, LineSet LS
             const int v = lane + 32 * i;
             if (v < nvec) cp_async16(dst + St::pos(4 * v), src + v);
         }
-    }
+    };
+    for (int k = 1; k < ng; ++k) copy_field(k);
     cp_async_commit();
 
     // 2. r = second difference of u (pair levels), coalesced, into R; every
@@ -693,6 +718,12 @@ __global__ void __launch_bounds__(32 * WARPS) k_contig_res(AxisDev A, LineSet LS
         }
         __syncwarp();
     }
+    // r to registers (segment layout); then field 0 may overwrite the staging
+    T r[RPT];
+    stage_to_regs<T, RPT>(R, r, lane, false);
+    __syncwarp();
+    if (ng > 0) copy_field(0);
+    cp_async_commit();
     cp_async_wait_all();
     __syncwarp();
 
@@ -716,7 +747,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_contig_res(AxisDev A, LineSet LS
             }
         }
         if (t == 0) break;
-        warp_sweep<T, BC, RPT, 2>(z, R, (T)__ldg(pr.cu + t), A, lane);
+        warp_sweep_rreg<T, BC, RPT>(z, r, (T)__ldg(pr.cu + t), A, lane);
     }
 
     // 4. F (segment layout) -> coalesced side -> next level
