@@ -168,6 +168,41 @@ mol_status mol_set_pass_timing(mol_handle h, int enable);
  */
 mol_status mol_pass_times(mol_handle h, double total_ms[3], int64_t launches[3]);
 
+/*
+ * F = F[u] in float64 (the operator of eq. update_P / Full_2D, as
+ * mol_apply_F on a MOL_FP64 handle) WITHOUT ALLOCATING: no handle, no
+ * cudaMalloc / cudaFree or any other allocating routine.  The paper has no
+ * counterpart; this serves callers that cannot allocate device memory where
+ * they need F -- a process whose caching allocator already holds nearly all
+ * of the device, or a loop that cannot afford cudaFree's device-wide
+ * synchronisation.
+ *
+ * Scratch: the intermediate planes, the tables d^j and the Horner
+ * coefficients live in one static device array of 32 MiB (32 << 20 bytes)
+ * inside libmolt.  A call needs 512 + sum_a roundup32(n_a + 1) +
+ * planes * roundup32(N) doubles, planes = 0 (1D), P (2D), 2P + 1 (3D),
+ * N = the number of grid points; larger grids are rejected with MOL_EINVAL
+ * and a message giving both sizes (2D, P = 3: up to about 1.39 M points).
+ * Nothing in the array needs to start at zero: every word a call reads was
+ * written earlier in the same call.
+ *
+ * Set-up: the first call on each device (with that device current) looks
+ * up the array's address and sets the kernels' shared-memory limits; make
+ * that first call before any stream capture.
+ *
+ * Concurrency: the array is shared by all calls on a device.  Calls that
+ * overlap in time on one device (different streams, or threads without
+ * ordering) race on it and give wrong results; order them on one stream.
+ *
+ * grid, c, dt, beta (<= 0 selects beta_max(P)), P, bc and quad_order (1 or
+ * 2) mean what they mean for mol_create; u, F: device float64 fields of the
+ * grid's size that may not overlap; stream: the CUDA stream (NULL = legacy
+ * default).  Errors: MOL_EINVAL (arguments, size), MOL_EUNSTABLE (beta),
+ * MOL_ECUDA (launch); text via mol_last_error(NULL).
+ */
+mol_status mol_apply_F_noalloc(const mol_grid *grid, double c, double dt, double beta, int P, mol_bc bc,
+                               int quad_order, const double *u, double *F, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,5 +1,7 @@
 // molt_api.cu -- the C ABI of libmolt: constants, workspace, pass plans,
 // CUDA-graph time loop.  See include/molt.h for the contract.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +17,7 @@ namespace {
 
 constexpr int kMaxP = 5;
 constexpr int64_t kMaxLine = 8192;
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // static scratch of mol_apply_F_noalloc
 
 struct Level {
     void *hi = nullptr;   // float32 hi plane (mixed) or the float64 field
@@ -456,30 +459,28 @@ double fco(const mol_ctx *h, int i, int j, int k)
 //   2D x pass:  F = sum_t D_x^t (sum_j f_tj D_y^j u)           g_k = D_y^{k+1} u
 //   3D y pass:  G_o = sum_t D_y^t (sum_k f_otk D_z^k u), (t,k) != (0,0)
 //   3D x pass:  F = sum_t D_x^t (f_t00 u + G_t)
-void build_tables(mol_ctx *h)
+template <class Fco>
+void fill_tables(int ndim, int P, Fco fco, HornerParams &x, HornerParams &y)
 {
-    const int P = h->P;
-    HornerParams &x = h->xtpl;
     x = HornerParams{};
     x.P = P;
     x.nout = 1;
     x.epi = 1;
-    if (h->ndim == 1) {
+    if (ndim == 1) {
         x.ng = 0;
-        for (int t = 1; t <= P; ++t) x.cu[0][t] = fco(h, t, 0, 0);
-    } else if (h->ndim == 2) {
+        for (int t = 1; t <= P; ++t) x.cu[0][t] = fco(t, 0, 0);
+    } else if (ndim == 2) {
         x.ng = P;
         for (int t = 0; t <= P; ++t) {
-            for (int k = 0; k < P; ++k) x.coef[0][t][k] = fco(h, t, k + 1, 0);
-            x.cu[0][t] = fco(h, t, 0, 0);
+            for (int k = 0; k < P; ++k) x.coef[0][t][k] = fco(t, k + 1, 0);
+            x.cu[0][t] = fco(t, 0, 0);
         }
     } else {
         x.ng = P + 1;
         for (int t = 0; t <= P; ++t) {
             for (int k = 0; k <= P; ++k) x.coef[0][t][k] = (k == t) ? 1.0 : 0.0;
-            x.cu[0][t] = fco(h, t, 0, 0);
+            x.cu[0][t] = fco(t, 0, 0);
         }
-        HornerParams &y = h->ytpl;
         y = HornerParams{};
         y.P = P;
         y.epi = 0;
@@ -487,10 +488,15 @@ void build_tables(mol_ctx *h)
         y.nout = P + 1;
         for (int o = 0; o <= P; ++o)
             for (int t = 0; t <= P; ++t) {
-                for (int k = 0; k < P; ++k) y.coef[o][t][k] = fco(h, o, t, k + 1);
-                y.cu[o][t] = fco(h, o, t, 0);
+                for (int k = 0; k < P; ++k) y.coef[o][t][k] = fco(o, t, k + 1);
+                y.cu[o][t] = fco(o, t, 0);
             }
     }
+}
+
+void build_tables(mol_ctx *h)
+{
+    fill_tables(h->ndim, h->P, [h](int i, int j, int k) { return fco(h, i, j, k); }, h->xtpl, h->ytpl);
 }
 
 void flatten(const HornerParams &hp, std::vector<double> &coef, std::vector<double> &cu)
@@ -505,9 +511,11 @@ void flatten(const HornerParams &hp, std::vector<double> &coef, std::vector<doub
     if (coef.empty()) coef.push_back(0.0);
 }
 
-// un = ea*u + eb*up + ec*F[u]  (the full pass plan of one step)
-mol_status run_update(mol_ctx *h, const Level &u, const Level &up, const Level &un,
-                      double ea, double eb, double ec, cudaStream_t s)
+// un = ea*u + eb*up + ec*F[u]  (the full pass plan of one step).  inter:
+// the intermediate planes; xc/xu/yc/yu: device copies of the Horner tables.
+mol_status run_update_with(mol_ctx *h, void *const *inter, const double *xc, const double *xu, const double *yc,
+                           const double *yu, const Level &u, const Level &up, const Level &un, double ea, double eb,
+                           double ec, cudaStream_t s)
 {
     const int P = h->P;
     HornerParams hp = h->xtpl;
@@ -515,22 +523,29 @@ mol_status run_update(mol_ctx *h, const Level &u, const Level &up, const Level &
     hp.u_hi = u.hi; hp.u_lo = u.lo;
     hp.up_hi = up.hi; hp.up_lo = up.lo;
     hp.un_hi = un.hi; hp.un_lo = un.lo;
-    const double *xc = h->coef_dev + h->off_xc, *xu = h->coef_dev + h->off_xu;
     mol_status st;
     if (h->ndim == 1) return run_horner(h, 0, hp, xc, xu, s);
     if (h->ndim == 2) {
-        if ((st = run_powers(h, 1, u, P, h->inter.data(), s)) != MOL_OK) return st;
-        for (int k = 0; k < P; ++k) hp.g[k] = h->inter[k];
+        if ((st = run_powers(h, 1, u, P, inter, s)) != MOL_OK) return st;
+        for (int k = 0; k < P; ++k) hp.g[k] = inter[k];
         return run_horner(h, 0, hp, xc, xu, s);
     }
-    if ((st = run_powers(h, 2, u, P, h->inter.data(), s)) != MOL_OK) return st;
+    if ((st = run_powers(h, 2, u, P, inter, s)) != MOL_OK) return st;
     HornerParams yp = h->ytpl;
     yp.u_hi = u.hi; yp.u_lo = u.lo;
-    for (int k = 0; k < P; ++k) yp.g[k] = h->inter[k];
-    for (int o = 0; o <= P; ++o) yp.out[o] = h->inter[P + o];
-    if ((st = run_horner(h, 1, yp, h->coef_dev + h->off_yc, h->coef_dev + h->off_yu, s)) != MOL_OK) return st;
-    for (int k = 0; k <= P; ++k) hp.g[k] = h->inter[P + k];
+    for (int k = 0; k < P; ++k) yp.g[k] = inter[k];
+    for (int o = 0; o <= P; ++o) yp.out[o] = inter[P + o];
+    if ((st = run_horner(h, 1, yp, yc, yu, s)) != MOL_OK) return st;
+    for (int k = 0; k <= P; ++k) hp.g[k] = inter[P + k];
     return run_horner(h, 0, hp, xc, xu, s);
+}
+
+mol_status run_update(mol_ctx *h, const Level &u, const Level &up, const Level &un,
+                      double ea, double eb, double ec, cudaStream_t s)
+{
+    const double *b = h->coef_dev;
+    return run_update_with(h, h->inter.data(), b + h->off_xc, b + h->off_xu, b + h->off_yc, b + h->off_yu, u, up,
+                           un, ea, eb, ec, s);
 }
 
 mol_status load_level(mol_ctx *h, const double *x, const Level &L, cudaStream_t s)
@@ -901,3 +916,263 @@ mol_status mol_pass_times(mol_handle h, double total_ms[3], int64_t launches[3])
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// F[u] without allocation (float64)
+// ===========================================================================
+// Callers that cannot allocate device memory at the point where they need
+// F[u]: a process whose caching allocator (PyTorch's, for one) already holds
+// nearly all of the device, so that cudaMalloc fails or forces the cache to
+// be emptied; and loops that cannot afford cudaFree, which synchronises the
+// whole device.  mol_apply_F_noalloc serves them.  Every buffer it needs
+// besides u and F -- the intermediate planes of the pass plan, the tables
+// d^j and the Horner coefficients -- lives in the fixed array below, so the
+// array's size bounds the grids it accepts.
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchBytes / sizeof(double)];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+constexpr int kNoallocCoefCap = 512;   // doubles reserved for the Horner tables
+constexpr int kNoallocCoefMax = 288;   // >= the 258 table entries of 3D, P = 5; keeps the
+                                       // parameter block of k_noalloc_tables under 4 KB
+std::atomic<double *> g_noalloc_ptr[kNoallocMaxDevices];
+int g_noalloc_sms[kNoallocMaxDevices];
+int g_noalloc_smem[kNoallocMaxDevices];
+
+// Resolve the array's device address once per device (with that device
+// current) and give the pass kernels their shared-memory limits.
+mol_status noalloc_setup(int dev, double **out)
+{
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(nullptr, MOL_EINVAL, "device ordinal out of range");
+    double *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *q = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress of the static scratch");
+        if ((e = configure_kernels()) != cudaSuccess) return cuda_fail(nullptr, e, "kernel attributes");
+        if ((e = configure_regs_kernels()) != cudaSuccess) return cuda_fail(nullptr, e, "kernel attributes");
+        int v = 0;
+        g_noalloc_sms[dev] = (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+                                 ? v : 152;
+        g_noalloc_smem[dev] = (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+                               v > 0) ? v : 227 * 1024;
+        p = (double *)q;
+        g_noalloc_ptr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return MOL_OK;
+}
+
+// Coefficient expansion of F with fixed-capacity polynomials: the same
+// products, in the same order, as expand_coefficients (index i + 6 (j + 6 k)).
+constexpr int kFS = kMaxP + 1;
+struct FPoly {
+    double c[kFS * kFS * kFS];
+};
+
+int fidx(int i, int j, int k) { return i + kFS * (j + kFS * k); }
+
+void fset(FPoly &r, const FPoly &a, const FPoly &b, double sb)   // r = a + sb b
+{
+    for (int i = 0; i < kFS * kFS * kFS; ++i) r.c[i] = a.c[i] + sb * b.c[i];
+}
+
+bool fmul(const FPoly &a, const FPoly &b, int P, FPoly &r)
+{
+    for (double &x : r.c) x = 0.0;
+    for (int k1 = 0; k1 <= P; ++k1) for (int j1 = 0; j1 <= P; ++j1) for (int i1 = 0; i1 <= P; ++i1) {
+        const double x = a.c[fidx(i1, j1, k1)];
+        if (x == 0.0) continue;
+        for (int k2 = 0; k2 <= P; ++k2) for (int j2 = 0; j2 <= P; ++j2) for (int i2 = 0; i2 <= P; ++i2) {
+            const double y = b.c[fidx(i2, j2, k2)];
+            if (y == 0.0) continue;
+            if (i1 + i2 > P || j1 + j2 > P || k1 + k2 > P) return false;
+            r.c[fidx(i1 + i2, j1 + j2, k1 + k2)] += x * y;
+        }
+    }
+    return true;
+}
+
+bool expand_fixed(int ndim, int P, double beta, FPoly &F)
+{
+    FPoly one{}, zero{}, Dg[3]{}, Lg[3]{}, prodL{}, Dop{}, C{}, t{}, tmp{}, Cp[kFS]{}, Dp[kFS]{};
+    one.c[0] = 1.0;
+    for (int a = 0; a < ndim; ++a) {
+        int e[3] = {0, 0, 0};
+        e[a] = 1;
+        Dg[a].c[fidx(e[0], e[1], e[2])] = 1.0;
+        fset(Lg[a], one, Dg[a], -1.0);
+    }
+    prodL = one;
+    for (int a = 0; a < ndim; ++a) { if (!fmul(prodL, Lg[a], P, tmp)) return false; prodL = tmp; }
+    fset(Dop, one, prodL, -1.0);
+    for (int g = 0; g < ndim; ++g) {
+        t = Dg[g];
+        for (int a = 0; a < ndim; ++a) if (a != g) { if (!fmul(t, Lg[a], P, tmp)) return false; t = tmp; }
+        fset(C, C, t, 1.0);
+    }
+    Cp[0] = Dp[0] = one;
+    for (int k = 1; k <= P; ++k) {
+        if (!fmul(Cp[k - 1], C, P, Cp[k])) return false;
+        if (!fmul(Dp[k - 1], Dop, P, Dp[k])) return false;
+    }
+    F = zero;
+    for (int p = 1; p <= P; ++p)
+        for (int m = 1; m <= p; ++m) {
+            if (!fmul(Cp[m], Dp[p - m], P, tmp)) return false;
+            fset(F, F, tmp, term_weight(p, m, beta));
+        }
+    return true;
+}
+
+// Constants written into the scratch by one small kernel at the start of
+// every call (they travel as the kernel's parameters, so no host copy).
+struct NoallocTables {
+    double *coef_dst;
+    int ncoef;
+    double coef[kNoallocCoefMax];
+    double *dpow[3];
+    int n[3];
+    double nu[3];
+};
+
+__global__ void k_noalloc_tables(const NoallocTables t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < t.ncoef) t.coef_dst[i] = t.coef[i];
+    for (int a = 0; a < 3; ++a)
+        if (t.dpow[a] && i <= t.n[a]) t.dpow[a][i] = exp(-t.nu[a] * (double)i);
+}
+
+size_t round_up32(size_t x) { return (x + 31) & ~(size_t)31; }   // doubles -> 256-byte alignment
+
+}  // namespace
+
+extern "C" mol_status mol_apply_F_noalloc(const mol_grid *grid, double c, double dt, double beta, int P, mol_bc bc,
+                                          int quad_order, const double *u, double *F, void *stream)
+{
+    if (!grid) return fail(nullptr, MOL_EINVAL, "grid is NULL");
+    if (grid->ndim < 1 || grid->ndim > 3) return fail(nullptr, MOL_EINVAL, "ndim must be 1, 2 or 3");
+    if (P < 1 || P > kMaxP) return fail(nullptr, MOL_EINVAL, "P must be in 1..5");
+    if (!(c > 0) || !(dt > 0) || !std::isfinite(c) || !std::isfinite(dt))
+        return fail(nullptr, MOL_EINVAL, "c and dt must be positive");
+    if (bc != MOL_BC_PERIODIC && bc != MOL_BC_DIRICHLET) return fail(nullptr, MOL_EINVAL, "unknown boundary condition");
+    if (quad_order != 1 && quad_order != 2) return fail(nullptr, MOL_EINVAL, "quad_order must be 1 or 2");
+    int64_t N = 1;
+    for (int a = 0; a < grid->ndim; ++a) {
+        if (grid->n[a] < 3 || grid->n[a] > kMaxLine)
+            return fail(nullptr, MOL_EINVAL, "every axis needs 3 <= n <= " + std::to_string(kMaxLine));
+        if (!(grid->hi[a] > grid->lo[a])) return fail(nullptr, MOL_EINVAL, "hi must exceed lo on every axis");
+        N *= grid->n[a];
+    }
+    const double bmax = beta_max_of(P);
+    if (beta <= 0) beta = bmax;
+    if (beta > bmax * (1.0 + 1e-12))
+        return fail(nullptr, MOL_EUNSTABLE, "beta above beta_max(P): the scheme is not A-stable");
+
+    // scratch layout (doubles, every part 256-byte aligned): Horner tables,
+    // d^j per axis, intermediate planes (2D: D_y^k u; 3D: D_z^k u and the
+    // P + 1 outputs of the y pass)
+    const int ndim = grid->ndim;
+    const int nplanes = ndim == 2 ? P : (ndim == 3 ? 2 * P + 1 : 0);
+    size_t off_dpow[3] = {0, 0, 0};
+    size_t need = kNoallocCoefCap;
+    for (int a = 0; a < ndim; ++a) { off_dpow[a] = need; need += round_up32((size_t)grid->n[a] + 1); }
+    const size_t off_planes = need;
+    need += (size_t)nplanes * round_up32((size_t)N);
+    if (need * sizeof(double) > kNoallocScratchBytes)
+        return fail(nullptr, MOL_EINVAL, "the grid needs " + std::to_string(need * sizeof(double)) +
+                                             " bytes of static scratch; the maximum is " +
+                                             std::to_string(kNoallocScratchBytes));
+    mol_status st;
+    if ((st = check_ptr(nullptr, u, "u")) != MOL_OK || (st = check_ptr(nullptr, F, "F")) != MOL_OK) return st;
+    if (u == F) return fail(nullptr, MOL_EINVAL, "u and F must not overlap");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    double *scratch = nullptr;
+    if ((st = noalloc_setup(dev, &scratch)) != MOL_OK) return st;
+
+    // a context on the stack: the pass launchers read only its scalars
+    mol_ctx h;
+    h.ndim = ndim;
+    h.N = N;
+    for (int a = 0; a < 3; ++a) {
+        h.n[a] = a < ndim ? grid->n[a] : 1;
+        h.lo[a] = grid->lo[a];
+        h.hi[a] = grid->hi[a];
+    }
+    h.c = c; h.dt = dt; h.beta = beta; h.P = P; h.bc = bc; h.prec = MOL_FP64;
+    mol_default_options(&h.opt);
+    h.opt.quad_order = quad_order;
+    h.opt.use_graphs = 0;
+    h.alpha = beta / (c * dt);                        // eq. L_def
+    h.tbytes = 8;
+    h.device = dev;
+    h.num_sms = g_noalloc_sms[dev];
+    h.smem_optin = (size_t)g_noalloc_smem[dev];
+
+    NoallocTables tb{};
+    int nmax = 0;
+    for (int a = 0; a < ndim; ++a) {
+        const int64_t n = h.n[a];
+        h.h[a] = (h.hi[a] - h.lo[a]) / (double)(bc == MOL_BC_DIRICHLET ? n - 1 : n);
+        h.nu[a] = h.alpha * h.h[a];
+        axis_constants(h.nu[a], n, bc, quad_order, h.ax[a]);
+        h.ax[a].dpow64 = scratch + off_dpow[a];
+        h.ax[a].dpow32 = nullptr;                      // float64 kernels read only dpow64
+        for (int r = 0; r < 4; ++r)
+            for (int k = 0; k < 5; ++k)
+                h.dmr_ax[a][r][k] = std::exp(-h.nu[a] * (double)(8 << r) * (double)(1 << k));
+        tb.dpow[a] = scratch + off_dpow[a];
+        tb.n[a] = (int)n;
+        tb.nu[a] = h.nu[a];
+        nmax = std::max(nmax, (int)n + 1);
+    }
+
+    FPoly f;
+    if (!expand_fixed(ndim, P, beta, f)) return fail(nullptr, MOL_EINVAL, "coefficient expansion failed");
+    fill_tables(ndim, P, [&f](int i, int j, int k) { return f.c[fidx(i, j, k)]; }, h.xtpl, h.ytpl);
+    // flattened like flatten(): per output o and Horner term t, the ng field
+    // weights, then the weights of u
+    double flat[2 * kNoallocCoefMax];
+    size_t off[4];
+    int nc = 0;
+    const HornerParams *tp[2] = {&h.xtpl, &h.ytpl};
+    for (int q = 0; q < 2; ++q) {
+        const HornerParams &hp = *tp[q];
+        const bool used = q == 0 || ndim == 3;
+        off[2 * q] = nc;
+        if (used)
+            for (int o = 0; o < std::max(hp.nout, 1); ++o)
+                for (int t = 0; t <= hp.P; ++t)
+                    for (int k = 0; k < hp.ng; ++k) flat[nc++] = hp.coef[o][t][k];
+        if (nc == (int)off[2 * q]) flat[nc++] = 0.0;
+        off[2 * q + 1] = nc;
+        if (used)
+            for (int o = 0; o < std::max(hp.nout, 1); ++o)
+                for (int t = 0; t <= hp.P; ++t) flat[nc++] = hp.cu[o][t];
+        if (nc == (int)off[2 * q + 1]) flat[nc++] = 0.0;
+    }
+    if (nc > kNoallocCoefMax) return fail(nullptr, MOL_EINVAL, "coefficient tables exceed their reserved space");
+    for (int i = 0; i < nc; ++i) tb.coef[i] = flat[i];
+    tb.coef_dst = scratch;
+    tb.ncoef = nc;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nthr = 256, nblk = (std::max(nmax, nc) + nthr - 1) / nthr;
+    k_noalloc_tables<<<nblk, nthr, 0, s>>>(tb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "table kernel launch");
+
+    void *inter[2 * MAXG] = {nullptr};
+    for (int k = 0; k < nplanes; ++k) inter[k] = scratch + off_planes + (size_t)k * round_up32((size_t)N);
+    Level U, O;
+    U.hi = (void *)u;
+    O.hi = F;
+    st = run_update_with(&h, inter, scratch + off[0], scratch + off[1], scratch + off[2], scratch + off[3], U, U, O,
+                         0.0, 0.0, 1.0, s);
+    if (st != MOL_OK) g_err = h.err;
+    return st;
+}

@@ -28,7 +28,8 @@ PREC = {"fp64": 0, "mixed": 1}
 # Every symbol include/molt.h declares.
 EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error", "mol_beta_max",
            "mol_max_line", "mol_get_params", "mol_apply_D", "mol_apply_F", "mol_start", "mol_step",
-           "mol_solve_host", "mol_sync", "mol_launch_count", "mol_set_pass_timing", "mol_pass_times"]
+           "mol_solve_host", "mol_sync", "mol_launch_count", "mol_set_pass_timing", "mol_pass_times",
+           "mol_apply_F_noalloc"]
 
 
 class MolError(RuntimeError):
@@ -83,6 +84,7 @@ def load_library(path: Path | None = None):
     lib.mol_set_pass_timing.argtypes = [vp, I]
     lib.mol_pass_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
     lib.mol_launch_count.argtypes = [vp]
+    lib.mol_apply_F_noalloc.argtypes = [ctypes.POINTER(mol_grid), D, D, D, I, I, I, vp, vp, vp]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
@@ -94,6 +96,45 @@ def load_library(path: Path | None = None):
 
 def beta_max(P: int) -> float:
     return load_library().mol_beta_max(int(P))
+
+
+def make_grid(shape: Sequence[int], lo: Sequence[float] | None = None,
+              hi: Sequence[float] | None = None) -> mol_grid:
+    """mol_grid of an array shape (nz, ny, nx); lo / hi in the same order
+    (default [0, 1] on every axis)."""
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    lo = [0.0] * nd if lo is None else lo
+    hi = [1.0] * nd if hi is None else hi
+    g = mol_grid()
+    g.ndim = nd
+    for a in range(3):
+        g.n[a] = shape[nd - 1 - a] if a < nd else 1
+        g.lo[a] = float(lo[nd - 1 - a]) if a < nd else 0.0
+        g.hi[a] = float(hi[nd - 1 - a]) if a < nd else 1.0
+    return g
+
+
+def apply_F_noalloc(u, out, dt: float, P: int, bc: str = "dirichlet", c: float = 1.0, beta: float = 0.0,
+                    lo: Sequence[float] | None = None, hi: Sequence[float] | None = None,
+                    quad_order: int = 2, stream=None):
+    """F[u] in float64 through mol_apply_F_noalloc: no handle and no device
+    allocation.  u and out: contiguous CUDA float64 tensors of one shape
+    (nz, ny, nx); the library's static scratch bounds the grid size."""
+    import torch
+    lib = load_library()
+    for t, name in ((u, "u"), (out, "out")):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
+    if tuple(u.shape) != tuple(out.shape):
+        raise ValueError("u and out must have the same shape")
+    g = make_grid(u.shape, lo, hi)
+    st = lib.mol_apply_F_noalloc(ctypes.byref(g), float(c), float(dt), float(beta), int(P), BC[bc],
+                                 int(quad_order), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(_stream_ptr(stream)))
+    if st != MOL_OK:
+        raise MolError(st, lib.mol_last_error(None).decode())
+    return out
 
 
 def _stream_ptr(stream) -> int:
@@ -119,16 +160,7 @@ class Solver:
         self.lib = load_library()
         self.shape = tuple(int(s) for s in shape)
         nd = len(self.shape)
-        if lo is None:
-            lo = [0.0] * nd
-        if hi is None:
-            hi = [1.0] * nd
-        g = mol_grid()
-        g.ndim = nd
-        for a in range(3):
-            g.n[a] = self.shape[nd - 1 - a] if a < nd else 1
-            g.lo[a] = float(lo[nd - 1 - a]) if a < nd else 0.0
-            g.hi[a] = float(hi[nd - 1 - a]) if a < nd else 1.0
+        g = make_grid(self.shape, lo, hi)
         opt = mol_options(int(quad_order), int(lines_per_block), 1 if use_graphs else 0)
         h = ctypes.c_void_p()
         torch.cuda.init()
