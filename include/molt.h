@@ -168,6 +168,56 @@ mol_status mol_set_pass_timing(mol_handle h, int enable);
  */
 mol_status mol_pass_times(mol_handle h, double total_ms[3], int64_t launches[3]);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent 2D problems
+ *
+ * Many Dirichlet problems of uneven size stepped together: every pass runs
+ * all problems in one persistent launch over a flat work list (rows for
+ * the x pass, groups of 32 columns for the y pass), and mol_batch_step
+ * captures its time loop in a CUDA graph.  Problem i has its own grid
+ * (ndim = 2, 3 <= n <= 1024 per axis), c, dt, beta and P; all share the
+ * boundary condition (homogeneous Dirichlet only) and the precision.  Each
+ * problem follows the same scheme as a single mol_create handle (eq.
+ * update_P; Sec. 4, eq. Full_2D).
+ *
+ * Fields are PACKED float64 device arrays: problem after problem, each
+ * C-contiguous (ny, nx) with x fastest; mol_batch_offsets gives where each
+ * starts.  The library keeps the levels in its own padded layout.
+ * ------------------------------------------------------------------------ */
+typedef struct mol_batch_ctx *mol_batch;
+
+/* grids, c, dt, P: arrays of nprob entries; beta may be NULL (beta_max(P_i)
+ * for every problem) or hold entries <= 0 with the same meaning.  bc must
+ * be MOL_BC_DIRICHLET.  opt as for mol_create (lines_per_block ignored). */
+mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, const double *dt,
+                            const double *beta, const int *P, mol_bc bc, mol_prec prec,
+                            const mol_options *opt, mol_batch *out);
+mol_status mol_batch_destroy(mol_batch b);
+
+/* Message of the last failed call on b (that of mol_last_error(NULL) if b is NULL). */
+const char *mol_batch_last_error(mol_batch b);
+
+/* offsets[0..nprob]: element offset of every problem in a packed field;
+ * offsets[nprob] = the packed field's length. */
+mol_status mol_batch_offsets(mol_batch b, int64_t *offsets);
+
+/* F = F[u] for every problem (packed fields, may not overlap). */
+mol_status mol_batch_apply_F(mol_batch b, const double *u, double *F, void *stream);
+
+/* u1 = u0 + F[u0]/2 for every problem (zero initial velocity, Sec. 3.2). */
+mol_status mol_batch_start(mol_batch b, const double *u0, double *u1, void *stream);
+
+/* Advance every problem by nsteps in place; as mol_step. */
+mol_status mol_batch_step(mol_batch b, double *u_prev, double *u_cur, int64_t nsteps, void *stream);
+
+mol_status mol_batch_sync(mol_batch b, void *stream);
+int64_t mol_batch_launch_count(mol_batch b);
+
+/* Per-pass CUDA-event timing as mol_set_pass_timing / mol_pass_times
+ * (index 0 = x pass, 1 = y pass). */
+mol_status mol_batch_set_pass_timing(mol_batch b, int enable);
+mol_status mol_batch_pass_times(mol_batch b, double total_ms[3], int64_t launches[3]);
+
 /*
  * F = F[u] in float64 (the operator of eq. update_P / Full_2D, as
  * mol_apply_F on a MOL_FP64 handle) WITHOUT ALLOCATING: no handle, no

@@ -1,0 +1,575 @@
+// molt_batch.cu -- the batched C ABI (mol_batch_* in include/molt.h): many
+// independent 2D Dirichlet problems of uneven size stepped together, one
+// persistent launch per pass, the time loop captured in a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "molt.h"
+#include "molt_internal.h"
+#include "molt_batch.cuh"
+
+using namespace molt;
+
+namespace {
+
+struct BLevel {
+    void *hi = nullptr;
+    void *lo = nullptr;
+};
+
+}  // namespace
+
+struct mol_batch_ctx {
+    int nprob = 0, prec = 0, tbytes = 8, Pmax = 1, quad = 2, use_graphs = 1;
+    int64_t nrows = 0, total_int = 0;
+    int64_t rows_small = 0;             // rows of the problems with x segments <= 16 come first
+    int nitems_y = 0;
+    std::vector<int64_t> uoff;          // packed user layout: nprob + 1 prefix sums
+    std::vector<BatchProb> hp;          // host copy of the problem table
+    BatchProb *probs = nullptr;
+    int *row_prob = nullptr;
+    int2 *items = nullptr;
+    long long *uoff_dev = nullptr;
+    double *dp64 = nullptr;
+    float *dp32 = nullptr;
+    BLevel lev[3];
+    void *inter[BMAXP] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int xW[2] = {8, 8}, xgrid[2] = {1, 1}, ygrid = 1, nbuf = 1, cgrid = 1;
+    size_t xsmem[2] = {0, 0}, ysmem = 0;
+    int num_sms = 152;
+    std::vector<void *> allocs;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t launches = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    std::string err;
+    int x_launches() const { return (rows_small > 0 ? 1 : 0) + (nrows > rows_small ? 1 : 0); }
+};
+
+namespace {
+
+mol_status bfail(mol_batch_ctx *b, mol_status st, const std::string &msg)
+{
+    if (b) b->err = msg;
+    else set_global_error(msg);
+    return st;
+}
+
+mol_status bcuda(mol_batch_ctx *b, cudaError_t e, const char *what)
+{
+    return bfail(b, MOL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define BCK(expr, what)                                      \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return bcuda(b, e_, what);    \
+    } while (0)
+
+mol_status balloc(mol_batch_ctx *b, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, MOL_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+                                        cudaGetErrorString(e));
+    }
+    b->allocs.push_back(*p);
+    return MOL_OK;
+}
+
+void bfree_all(mol_batch_ctx *b)
+{
+    for (auto &u : b->ev_used) { b->ev_pool.push_back(u.second.first); b->ev_pool.push_back(u.second.second); }
+    b->ev_used.clear();
+    for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+    b->ev_pool.clear();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    b->cap_stream = nullptr;
+    for (void *p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+}
+
+// segment lengths: x pass 32 lanes x rpt >= nx; y pass 16 warps x rpt >= ny
+int pick_rpt_x(int n)
+{
+    int r = 4;
+    while (32 * r < n) r *= 2;
+    return r;
+}
+int pick_rpt_y(int n)
+{
+    int r = 4;
+    while (kBatchYWarps * r < n) r *= 2;
+    return r;
+}
+
+cudaEvent_t btake_event(mol_batch_ctx *b)
+{
+    if (!b->ev_pool.empty()) {
+        cudaEvent_t e = b->ev_pool.back();
+        b->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+template <class T>
+cudaError_t launch_pass_y(const mol_batch_ctx *b, const BatchPass &bp, cudaStream_t s)
+{
+    k_batch_y<T><<<b->ygrid, 32 * kBatchYWarps, b->ysmem, s>>>(bp);
+    return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_pass_x(const mol_batch_ctx *b, BatchPass bp, cudaStream_t s)
+{
+    // rows of short lines, then rows of long lines (each a persistent launch)
+    bp.row_begin = 0;
+    bp.nitems = (int)b->rows_small;
+    if (bp.nitems > 0) k_batch_x<T, false><<<b->xgrid[0], 32 * b->xW[0], b->xsmem[0], s>>>(bp, b->nbuf);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bp.row_begin = (int)b->rows_small;
+    bp.nitems = (int)b->nrows;
+    if (bp.nitems > bp.row_begin) k_batch_x<T, true><<<b->xgrid[1], 32 * b->xW[1], b->xsmem[1], s>>>(bp, b->nbuf);
+    return cudaGetLastError();
+}
+
+// one pass, timed when pass timing is on (axis 0 = x, 1 = y)
+mol_status run_pass(mol_batch_ctx *b, int axis, const BatchPass &bp, cudaStream_t s)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (b->timing) {
+        e0 = btake_event(b);
+        e1 = btake_event(b);
+        if (!e0 || !e1) return bfail(b, MOL_ECUDA, "event creation failed");
+        BCK(cudaEventRecord(e0, s), "event record");
+    }
+    cudaError_t e;
+    if (axis == 1) e = b->tbytes == 4 ? launch_pass_y<float>(b, bp, s) : launch_pass_y<double>(b, bp, s);
+    else e = b->tbytes == 4 ? launch_pass_x<float>(b, bp, s) : launch_pass_x<double>(b, bp, s);
+    if (e != cudaSuccess) return bcuda(b, e, "batched pass launch");
+    b->launches += (axis == 1) ? 1 : b->x_launches();
+    if (b->timing) {
+        BCK(cudaEventRecord(e1, s), "event record");
+        b->ev_used.push_back({axis, {e0, e1}});
+    }
+    return MOL_OK;
+}
+
+// un = ea u + eb up + ec F[u] for every problem: y pass, then x pass
+mol_status run_update(mol_batch_ctx *b, const BLevel &u, const BLevel &up, const BLevel &un, double ea, double eb,
+                      double ec, cudaStream_t s)
+{
+    BatchPass y{};
+    y.probs = b->probs;
+    y.row_prob = b->row_prob;
+    y.items = b->items;
+    y.nitems = b->nitems_y;
+    y.pr.u_hi = u.hi;
+    y.pr.u_lo = u.lo;
+    for (int k = 0; k < b->Pmax; ++k) y.pr.out[k] = b->inter[k];
+    mol_status st = run_pass(b, 1, y, s);
+    if (st != MOL_OK) return st;
+    BatchPass x = y;
+    x.nitems = (int)b->nrows;
+    for (int k = 0; k < b->Pmax; ++k) { x.pr.g[k] = b->inter[k]; x.pr.out[k] = nullptr; }
+    x.pr.up_hi = up.hi;
+    x.pr.up_lo = up.lo;
+    x.pr.un_hi = un.hi;
+    x.pr.un_lo = un.lo;
+    x.pr.ea = ea;
+    x.pr.eb = eb;
+    x.pr.ec = ec;
+    return run_pass(b, 0, x, s);
+}
+
+mol_status pack(mol_batch_ctx *b, const double *x, const BLevel &L, cudaStream_t s)
+{
+    if (b->tbytes == 4)
+        k_batch_pack<float><<<b->cgrid, 256, 0, s>>>(b->probs, b->row_prob, b->uoff_dev, (int)b->nrows, x,
+                                                     (float *)L.hi, (float *)L.lo);
+    else
+        k_batch_pack<double><<<b->cgrid, 256, 0, s>>>(b->probs, b->row_prob, b->uoff_dev, (int)b->nrows, x,
+                                                      (double *)L.hi, nullptr);
+    BCK(cudaGetLastError(), "batched level conversion");
+    b->launches++;
+    return MOL_OK;
+}
+
+mol_status unpack(mol_batch_ctx *b, const BLevel &L, double *x, cudaStream_t s)
+{
+    if (b->tbytes == 4)
+        k_batch_unpack<float><<<b->cgrid, 256, 0, s>>>(b->probs, b->row_prob, b->uoff_dev, (int)b->nrows,
+                                                       (const float *)L.hi, (const float *)L.lo, x);
+    else
+        k_batch_unpack<double><<<b->cgrid, 256, 0, s>>>(b->probs, b->row_prob, b->uoff_dev, (int)b->nrows,
+                                                        (const double *)L.hi, nullptr, x);
+    BCK(cudaGetLastError(), "batched level conversion");
+    b->launches++;
+    return MOL_OK;
+}
+
+mol_status build_graph(mol_batch_ctx *b)
+{
+    if (b->gexec) return MOL_OK;
+    if (!b->cap_stream) BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream create");
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+    const int64_t before = b->launches;
+    mol_status st = MOL_OK;
+    for (int k = 0; k < 3 && st == MOL_OK; ++k)
+        st = run_update(b, b->lev[(k + 1) % 3], b->lev[k % 3], b->lev[(k + 2) % 3], 2.0, -1.0, 1.0, b->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    b->launches = before;
+    if (st != MOL_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return bcuda(b, e, "graph capture end");
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->gexec = nullptr; return bcuda(b, e, "graph instantiate"); }
+    return MOL_OK;
+}
+
+mol_status bcheck_ptr(mol_batch_ctx *b, const void *p, const char *name)
+{
+    if (!p) return bfail(b, MOL_EINVAL, std::string(name) + " is NULL");
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return bfail(b, MOL_EINVAL, std::string(name) + ": not a CUDA pointer"); }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return bfail(b, MOL_EINVAL, std::string(name) + " must be device memory");
+    return MOL_OK;
+}
+
+// host-side validation and constants of every problem (no device work)
+mol_status plan_batch(mol_batch_ctx *b, int nprob, const mol_grid *grids, const double *c, const double *dt,
+                      const double *beta, const int *P, int quad)
+{
+    b->hp.assign(nprob, BatchProb{});
+    b->uoff.assign(nprob + 1, 0);
+    int64_t off = 0, rows = 0, items = 0;
+    b->rows_small = 0;
+    for (int i = 0; i < nprob; ++i) {
+        const mol_grid &g = grids[i];
+        const std::string who = "problem " + std::to_string(i) + ": ";
+        if (g.ndim != 2) return bfail(nullptr, MOL_EINVAL, who + "batched problems are 2D (ndim = 2)");
+        for (int a = 0; a < 2; ++a) {
+            if (g.n[a] < 3 || g.n[a] > kBatchMaxN)
+                return bfail(nullptr, MOL_EINVAL, who + "every axis needs 3 <= n <= " + std::to_string(kBatchMaxN));
+            if (!(g.hi[a] > g.lo[a])) return bfail(nullptr, MOL_EINVAL, who + "hi must exceed lo on every axis");
+        }
+        if (P[i] < 1 || P[i] > BMAXP) return bfail(nullptr, MOL_EINVAL, who + "P must be in 1..5");
+        if (!(c[i] > 0) || !(dt[i] > 0) || !std::isfinite(c[i]) || !std::isfinite(dt[i]))
+            return bfail(nullptr, MOL_EINVAL, who + "c and dt must be positive");
+        const double bmax = beta_max_of(P[i]);
+        double bt = beta ? beta[i] : 0.0;
+        if (bt <= 0) bt = bmax;
+        if (bt > bmax * (1.0 + 1e-12))
+            return bfail(nullptr, MOL_EUNSTABLE, who + "beta above beta_max(P): the scheme is not A-stable");
+
+        BatchProb &pb = b->hp[i];
+        const int nx = (int)g.n[0], ny = (int)g.n[1];
+        const double alpha = bt / (c[i] * dt[i]);                       // eq. L_def
+        const double nux = alpha * (g.hi[0] - g.lo[0]) / (double)(nx - 1);
+        const double nuy = alpha * (g.hi[1] - g.lo[1]) / (double)(ny - 1);
+        axis_constants(nux, nx, BC_DIRICHLET, quad, pb.ax);
+        axis_constants(nuy, ny, BC_DIRICHLET, quad, pb.ay);
+        pb.rpt_x = pick_rpt_x(nx);
+        pb.rpt_y = pick_rpt_y(ny);
+        for (int k = 0; k < 5; ++k) {
+            pb.ax.dm[k] = std::exp(-nux * (double)pb.rpt_x * (double)(1 << k));
+            pb.ay.dm[k] = std::exp(-nuy * (double)pb.rpt_y * (double)(1 << k));
+        }
+        pb.P = P[i];
+        pb.pitch = (nx + 3) & ~3;
+        items += (nx + 31) / 32;
+        std::vector<double> f;
+        if (!expand_coefficients(2, P[i], bt, f)) return bfail(nullptr, MOL_EINVAL, who + "coefficient expansion failed");
+        const int D = P[i] + 1;
+        for (int t = 0; t <= P[i]; ++t) {
+            pb.cu[t] = f[t];
+            for (int k = 0; k < P[i]; ++k) pb.coef[t][k] = f[t + D * (k + 1)];
+        }
+        b->Pmax = std::max(b->Pmax, P[i]);
+        b->uoff[i + 1] = b->uoff[i] + (int64_t)nx * ny;
+    }
+    // internal order: problems with x segments <= 16 first, so that each
+    // x-pass kernel takes one contiguous range of rows
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < nprob; ++i) {
+            BatchProb &pb = b->hp[i];
+            if ((pb.rpt_x == 32) != (pass == 1)) continue;
+            pb.off = off;
+            pb.row0 = (int)rows;
+            off += ((int64_t)pb.ay.n * pb.pitch + 63) & ~(int64_t)63;
+            rows += pb.ay.n;
+            if (pass == 0) b->rows_small = rows;
+        }
+    if (rows > (1ll << 30) || items > (1ll << 30)) return bfail(nullptr, MOL_EINVAL, "batch too large");
+    b->total_int = off;
+    b->nrows = rows;
+    b->nitems_y = (int)items;
+    return MOL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, const double *dt, const double *beta,
+                            const int *P, mol_bc bc, mol_prec prec, const mol_options *opt, mol_batch *out)
+{
+    if (!out) return bfail(nullptr, MOL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1) return bfail(nullptr, MOL_EINVAL, "nprob must be >= 1");
+    if (!grids || !c || !dt || !P) return bfail(nullptr, MOL_EINVAL, "grids, c, dt and P must not be NULL");
+    if (bc != MOL_BC_DIRICHLET) return bfail(nullptr, MOL_EINVAL, "batched problems take homogeneous Dirichlet conditions");
+    if (prec != MOL_FP64 && prec != MOL_MIXED) return bfail(nullptr, MOL_EINVAL, "unknown precision");
+    mol_options o;
+    mol_default_options(&o);
+    if (opt) o = *opt;
+    if (o.quad_order != 1 && o.quad_order != 2) return bfail(nullptr, MOL_EINVAL, "quad_order must be 1 or 2");
+
+    mol_batch_ctx *b = new mol_batch_ctx();
+    b->nprob = nprob;
+    b->prec = prec;
+    b->tbytes = prec == MOL_MIXED ? 4 : 8;
+    b->quad = o.quad_order;
+    b->use_graphs = o.use_graphs;
+    mol_status st = plan_batch(b, nprob, grids, c, dt, beta, P, o.quad_order);
+    if (st != MOL_OK) { delete b; return st; }
+
+    int dev = 0, smem_sm = 228 * 1024, smem_blk = 227 * 1024, v = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { st = bcuda(b, e, "cudaGetDevice"); goto bad; }
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) b->num_sms = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess && v > 0) smem_sm = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && v > 0) smem_blk = v;
+    {
+        // tables d^j per problem and axis (n + 1 + kBatchDpowPad entries)
+        std::vector<int64_t> tofs(2 * nprob + 1, 0);
+        for (int i = 0; i < nprob; ++i) {
+            tofs[2 * i + 1] = tofs[2 * i] + b->hp[i].ax.n + 1 + kBatchDpowPad;
+            tofs[2 * i + 2] = tofs[2 * i + 1] + b->hp[i].ay.n + 1 + kBatchDpowPad;
+        }
+        const int64_t nt = tofs[2 * nprob];
+        std::vector<double> t64(nt);
+        std::vector<float> t32(nt);
+        for (int i = 0; i < nprob; ++i)
+            for (int a = 0; a < 2; ++a) {
+                const AxisDev &A = a == 0 ? b->hp[i].ax : b->hp[i].ay;
+                const double nu = -std::log(A.d);
+                for (int64_t j = 0; j < tofs[2 * i + a + 1] - tofs[2 * i + a]; ++j) {
+                    t64[tofs[2 * i + a] + j] = std::exp(-nu * (double)j);
+                    t32[tofs[2 * i + a] + j] = (float)t64[tofs[2 * i + a] + j];
+                }
+            }
+        if ((st = balloc(b, (void **)&b->dp64, sizeof(double) * nt)) != MOL_OK) goto bad;
+        if ((st = balloc(b, (void **)&b->dp32, sizeof(float) * nt)) != MOL_OK) goto bad;
+        if ((e = cudaMemcpy(b->dp64, t64.data(), sizeof(double) * nt, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(b->dp32, t32.data(), sizeof(float) * nt, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            st = bcuda(b, e, "constant upload");
+            goto bad;
+        }
+        for (int i = 0; i < nprob; ++i) {
+            b->hp[i].ax.dpow64 = b->dp64 + tofs[2 * i];
+            b->hp[i].ax.dpow32 = b->dp32 + tofs[2 * i];
+            b->hp[i].ay.dpow64 = b->dp64 + tofs[2 * i + 1];
+            b->hp[i].ay.dpow32 = b->dp32 + tofs[2 * i + 1];
+        }
+    }
+    {
+        std::vector<int> rp(b->nrows);
+        std::vector<int2> it;
+        it.reserve(b->nitems_y);
+        std::vector<long long> uo(nprob + 1);
+        for (int i = 0; i < nprob; ++i) {
+            const BatchProb &pb = b->hp[i];
+            for (int r = 0; r < pb.ay.n; ++r) rp[pb.row0 + r] = i;
+            for (int c0 = 0; c0 < pb.ax.n; c0 += 32) it.push_back(make_int2(i, c0));
+        }
+        for (int i = 0; i <= nprob; ++i) uo[i] = b->uoff[i];
+        if ((st = balloc(b, (void **)&b->probs, sizeof(BatchProb) * nprob)) != MOL_OK) goto bad;
+        if ((st = balloc(b, (void **)&b->row_prob, sizeof(int) * rp.size())) != MOL_OK) goto bad;
+        if ((st = balloc(b, (void **)&b->items, sizeof(int2) * it.size())) != MOL_OK) goto bad;
+        if ((st = balloc(b, (void **)&b->uoff_dev, sizeof(long long) * uo.size())) != MOL_OK) goto bad;
+        if ((e = cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(b->row_prob, rp.data(), sizeof(int) * rp.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(b->items, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(b->uoff_dev, uo.data(), sizeof(long long) * uo.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+            st = bcuda(b, e, "work list upload");
+            goto bad;
+        }
+    }
+    {
+        const size_t plane = (size_t)b->tbytes * b->total_int;
+        for (int k = 0; k < 3; ++k) {
+            if ((st = balloc(b, &b->lev[k].hi, plane)) != MOL_OK) goto bad;
+            if ((e = cudaMemset(b->lev[k].hi, 0, plane)) != cudaSuccess) { st = bcuda(b, e, "memset"); goto bad; }
+            if (b->tbytes == 4) {
+                if ((st = balloc(b, &b->lev[k].lo, plane)) != MOL_OK) goto bad;
+                if ((e = cudaMemset(b->lev[k].lo, 0, plane)) != cudaSuccess) { st = bcuda(b, e, "memset"); goto bad; }
+            }
+        }
+        for (int k = 0; k < b->Pmax; ++k) {
+            if ((st = balloc(b, &b->inter[k], plane)) != MOL_OK) goto bad;
+            if ((e = cudaMemset(b->inter[k], 0, plane)) != cudaSuccess) { st = bcuda(b, e, "memset"); goto bad; }
+        }
+    }
+    {
+        // launch shapes: x pass W warps per CTA with two CTAs per SM when the
+        // field buffers allow it; y pass one 16-warp CTA per SM
+        b->nbuf = b->Pmax;
+        const size_t per_warp = batch_x_smem((size_t)b->tbytes, 1, b->nbuf);
+        for (int L = 0; L < 2; ++L) {
+            const int ctas = L == 0 ? 2 : 1;       // CTAs per SM the register budget allows
+            int W = 8;
+            while (W > 1 && ctas * (W * per_warp + 1024) > (size_t)smem_sm) --W;
+            b->xW[L] = W;
+            b->xsmem[L] = batch_x_smem((size_t)b->tbytes, W, b->nbuf);
+            if (b->xsmem[L] > (size_t)smem_blk) { st = bfail(b, MOL_EINVAL, "x-pass buffers exceed shared memory"); goto bad; }
+            const int64_t nr = L == 0 ? b->rows_small : b->nrows - b->rows_small;
+            b->xgrid[L] = (int)std::max<int64_t>(1, std::min<int64_t>((nr + W - 1) / W, ctas * (int64_t)b->num_sms));
+        }
+        b->ygrid = std::min(b->nitems_y, b->num_sms);
+        b->ysmem = batch_y_smem((size_t)b->tbytes);
+        b->cgrid = (int)std::min<int64_t>((b->nrows + 7) / 8, 8 * (int64_t)b->num_sms);
+        if (b->tbytes == 4) {
+            e = cudaFuncSetAttribute(k_batch_x<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[0]);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_batch_x<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[1]);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_batch_y<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->ysmem);
+        } else {
+            e = cudaFuncSetAttribute(k_batch_x<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[0]);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_batch_x<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[1]);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_batch_y<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->ysmem);
+        }
+        if (e != cudaSuccess) { st = bcuda(b, e, "kernel attributes"); goto bad; }
+    }
+    *out = b;
+    return MOL_OK;
+bad:
+    set_global_error(b->err);
+    bfree_all(b);
+    delete b;
+    return st;
+}
+
+mol_status mol_batch_destroy(mol_batch b)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    cudaDeviceSynchronize();
+    bfree_all(b);
+    delete b;
+    return MOL_OK;
+}
+
+const char *mol_batch_last_error(mol_batch b) { return b ? b->err.c_str() : mol_last_error(nullptr); }
+
+mol_status mol_batch_offsets(mol_batch b, int64_t *offsets)
+{
+    if (!b || !offsets) return bfail(b, MOL_EINVAL, "NULL argument");
+    for (int i = 0; i <= b->nprob; ++i) offsets[i] = b->uoff[i];
+    return MOL_OK;
+}
+
+mol_status mol_batch_apply_F(mol_batch b, const double *u, double *F, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_status st;
+    if ((st = bcheck_ptr(b, u, "u")) != MOL_OK || (st = bcheck_ptr(b, F, "F")) != MOL_OK) return st;
+    if (u == F) return bfail(b, MOL_EINVAL, "u and F must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = pack(b, u, b->lev[0], s)) != MOL_OK) return st;
+    if ((st = run_update(b, b->lev[0], b->lev[0], b->lev[1], 0.0, 0.0, 1.0, s)) != MOL_OK) return st;
+    return unpack(b, b->lev[1], F, s);
+}
+
+mol_status mol_batch_start(mol_batch b, const double *u0, double *u1, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_status st;
+    if ((st = bcheck_ptr(b, u0, "u0")) != MOL_OK || (st = bcheck_ptr(b, u1, "u1")) != MOL_OK) return st;
+    if (u0 == u1) return bfail(b, MOL_EINVAL, "u0 and u1 must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = pack(b, u0, b->lev[0], s)) != MOL_OK) return st;
+    if ((st = run_update(b, b->lev[0], b->lev[0], b->lev[1], 1.0, 0.0, 0.5, s)) != MOL_OK) return st;
+    return unpack(b, b->lev[1], u1, s);
+}
+
+mol_status mol_batch_step(mol_batch b, double *u_prev, double *u_cur, int64_t nsteps, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (nsteps < 0) return bfail(b, MOL_EINVAL, "nsteps must be >= 0");
+    mol_status st;
+    if ((st = bcheck_ptr(b, u_prev, "u_prev")) != MOL_OK || (st = bcheck_ptr(b, u_cur, "u_cur")) != MOL_OK) return st;
+    if (u_prev == u_cur) return bfail(b, MOL_EINVAL, "u_prev and u_cur must not overlap");
+    if (nsteps == 0) return MOL_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = pack(b, u_prev, b->lev[0], s)) != MOL_OK) return st;
+    if ((st = pack(b, u_cur, b->lev[1], s)) != MOL_OK) return st;
+    int64_t done = 0;
+    if (b->use_graphs && !b->timing && nsteps >= 3) {
+        if ((st = build_graph(b)) != MOL_OK) return st;
+        for (; done + 3 <= nsteps; done += 3) {
+            BCK(cudaGraphLaunch(b->gexec, s), "graph launch");
+            b->launches += 3 * (1 + b->x_launches());
+        }
+    }
+    for (; done < nsteps; ++done) {
+        const int k = (int)(done % 3);
+        if ((st = run_update(b, b->lev[(k + 1) % 3], b->lev[k], b->lev[(k + 2) % 3], 2.0, -1.0, 1.0, s)) != MOL_OK)
+            return st;
+    }
+    const int k = (int)(nsteps % 3);
+    if ((st = unpack(b, b->lev[k], u_prev, s)) != MOL_OK) return st;
+    return unpack(b, b->lev[(k + 1) % 3], u_cur, s);
+}
+
+mol_status mol_batch_sync(mol_batch b, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    BCK(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+    BCK(cudaGetLastError(), "device error");
+    return MOL_OK;
+}
+
+int64_t mol_batch_launch_count(mol_batch b) { return b ? b->launches : 0; }
+
+mol_status mol_batch_set_pass_timing(mol_batch b, int enable)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    for (auto &u : b->ev_used) { b->ev_pool.push_back(u.second.first); b->ev_pool.push_back(u.second.second); }
+    b->ev_used.clear();
+    b->timing = enable != 0;
+    return MOL_OK;
+}
+
+mol_status mol_batch_pass_times(mol_batch b, double total_ms[3], int64_t launches[3])
+{
+    if (!b || !total_ms || !launches) return bfail(b, MOL_EINVAL, "NULL argument");
+    for (int a = 0; a < 3; ++a) { total_ms[a] = 0.0; launches[a] = 0; }
+    for (auto &u : b->ev_used) {
+        BCK(cudaEventSynchronize(u.second.second), "event synchronize");
+        float ms = 0.f;
+        BCK(cudaEventElapsedTime(&ms, u.second.first, u.second.second), "event elapsed time");
+        total_ms[u.first] += ms;
+        launches[u.first] += 1;
+    }
+    return MOL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,476 @@
+// molt_batch.cuh -- many independent 2D Dirichlet problems of uneven size in
+// one launch per pass.
+//
+// A step of problem i is the 2D pass plan of Sec. 4 (eq. Full_2D expanded in
+// the per-axis D_gamma): a y pass forming g_k = D_y^{k+1} u (k < P_i), then an
+// x pass evaluating F = sum_t D_x^t (f_t0 u + sum_k f_t,k+1 g_k) by Horner's
+// rule with the level combination u^{n+1} = ea u^n + eb u^{n-1} + ec F fused
+// in (eq. update_P).  Each pass runs every problem in ONE persistent launch
+// over a flat work list:
+//
+//  * x pass: one warp per row; the rows of all problems form the list (the
+//    problem of a row is looked up, its constants copied to shared memory).
+//    A lane owns a segment of RPT_i points, RPT_i the smallest of 4..32 with
+//    32 RPT_i >= nx_i, so short rows keep most lanes busy; the row's input
+//    fields are copied once into shared memory with cp.async.
+//  * y pass: one CTA of 16 warps per group of 32 neighbouring columns (lane =
+//    column, warp = segment of RPT_i rows, RPT_i the smallest of 4..64 with
+//    16 RPT_i >= ny_i); carries cross the segments through shared memory.
+//
+// Line lengths are arbitrary: the segment routines' RAG variants handle the
+// last point anywhere in a segment.  Fields live in an internal layout whose
+// rows are padded to a multiple of 4 points (16-byte aligned vectors); the
+// padding carries zeros and is never read as data.
+#pragma once
+#include "molt_regs.cuh"
+
+namespace molt {
+
+constexpr int BMAXP = 5;            // highest P of a batched problem
+constexpr int kBatchYWarps = 16;    // segments per column group in the y pass
+constexpr int kBatchDpowPad = 64;   // table entries past d^n (read, multiplied by zero, by the exchange)
+constexpr int kBatchMaxN = 1024;    // longest line of a batched problem
+
+struct BatchProb {
+    AxisDev ax, ay;                  // per-axis constants (dm[] for rpt_x / rpt_y)
+    long long off;                   // first element in the internal layout (multiple of 64)
+    int pitch;                       // row pitch of the internal layout (multiple of 4, >= nx)
+    int P;
+    int rpt_x, rpt_y;                // segment lengths of the x and y passes
+    int row0;                        // first global row of the problem in the x-pass list
+    int pad_;
+    double cu[BMAXP + 1];            // x Horner weights of u, t = 0..P
+    double coef[BMAXP + 1][BMAXP];   // x Horner weights of g_k, t = 0..P, k < P
+};
+static_assert(sizeof(BatchProb) % 16 == 0, "BatchProb is copied in 8-byte words into 16-byte aligned slots");
+
+struct BatchPass {
+    const BatchProb *probs;
+    const int *row_prob;     // x pass: problem of every global row
+    const int2 *items;       // y pass: (problem, first column)
+    int row_begin;           // x pass: first row of the list
+    int nitems;              // x pass: end of the rows; y pass: column groups
+    ProgParams pr;           // levels, ea / eb / ec, g[k] planes (internal layout)
+};
+
+template <class T>
+struct BatchX {
+    static constexpr int VN = VecOf<T>::n;
+    static constexpr int RMAX = 32;                  // largest x segment
+    static constexpr int LINE = 32 * (RMAX + VN);    // elements of one field buffer
+};
+
+// copy a struct of 8-byte words with the lanes of one warp
+template <class S>
+__device__ __forceinline__ void warp_copy(S *dst, const S *src, int lane)
+{
+    static_assert(sizeof(S) % 8 == 0, "word copy");
+    const unsigned long long *s = reinterpret_cast<const unsigned long long *>(src);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+    for (int i = lane; i < (int)(sizeof(S) / 8); i += 32) d[i] = __ldg(s + i);
+}
+
+__device__ __forceinline__ float vfirst(const float4 &v) { return v.x; }
+__device__ __forceinline__ float vlast(const float4 &v) { return v.w; }
+__device__ __forceinline__ double vfirst(const double2 &v) { return v.x; }
+__device__ __forceinline__ double vlast(const double2 &v) { return v.y; }
+
+// second difference of 2 consecutive points given their outer neighbours
+__device__ __forceinline__ double2 sdiff2(const double2 &h, double hl, double hr)
+{
+    return make_double2((h.y - h.x) - (h.x - hl), (hr - h.y) - (h.y - h.x));
+}
+
+// ---------------------------------------------------------------------------
+// x pass: one row
+// ---------------------------------------------------------------------------
+template <class T, int RPT>
+__device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams &pr, int row, int lane, T *B)
+{
+    using St = ContigStage<T, RPT>;
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n;
+    constexpr int NVL = RPT / VN;                    // vectors per lane of a full segment row
+    constexpr bool pair = sizeof(T) == 4;
+    constexpr int LB = BatchX<T>::LINE;
+    static_assert(RPT % VN == 0 && RPT >= 4 && RPT <= BatchX<T>::RMAX, "segment length");
+    const AxisDev &A = pb.ax;
+    const int n = A.n;
+    const int64_t base = pb.off + (int64_t)row * pb.pitch;
+    const int nvec = (n + VN - 1) / VN;              // within the padded pitch
+    const int ng = pb.P;
+
+    // 1. fields 1..ng-1 -> shared memory (asynchronous); field 0 after r
+    auto copy_field = [&](int k) {
+        const V *src = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.g[k]) + base);
+        T *dst = B + k * LB;
+#pragma unroll
+        for (int i = 0; i < NVL; ++i) {
+            const int v = lane + 32 * i;
+            if (v < nvec) cp_async16(dst + St::pos(VN * v), src + v);
+        }
+    };
+    for (int k = 1; k < ng; ++k) copy_field(k);
+    cp_async_commit();
+
+    // 2. r = accurate second difference of u, coalesced, in chunks of up to
+    //    4 vectors per lane (all loads of a chunk in flight together);
+    //    buffer 0 stages it
+    T *R = B;
+    {
+        const T *H = reinterpret_cast<const T *>(pr.u_hi) + base;
+        const T *Lo = pair ? reinterpret_cast<const T *>(pr.u_lo) + base : H;
+        const V *H4 = reinterpret_cast<const V *>(H), *L4 = reinterpret_cast<const V *>(Lo);
+        constexpr int CR = NVL < 4 ? NVL : 4;
+#pragma unroll
+        for (int i0 = 0; i0 < NVL; i0 += CR) {
+            V h[CR], l[CR];
+            T hx[CR], lx[CR];        // lane 0: the point before the chunk; lane 31: the point after it
+#pragma unroll
+            for (int i = 0; i < CR; ++i) {
+                const int v = lane + 32 * (i0 + i);
+                if (v < nvec) {
+                    h[i] = __ldg(H4 + v);
+                    if (pair) l[i] = __ldg(L4 + v);
+                } else {
+                    h[i] = V{};
+                    l[i] = V{};
+                }
+                int j = (lane == 0) ? VN * v - 1 : VN * v + VN;
+                j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+                hx[i] = 0;
+                lx[i] = 0;
+                if ((lane == 0 || lane == 31) && v < nvec) {
+                    hx[i] = __ldg(H + j);
+                    if (pair) lx[i] = __ldg(Lo + j);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < CR; ++i) {
+                const int v = lane + 32 * (i0 + i);
+                T hl = __shfl_up_sync(0xffffffffu, vlast(h[i]), 1), hr = __shfl_down_sync(0xffffffffu, vfirst(h[i]), 1);
+                T ll = 0, lr = 0;
+                if (pair) {
+                    ll = __shfl_up_sync(0xffffffffu, vlast(l[i]), 1);
+                    lr = __shfl_down_sync(0xffffffffu, vfirst(l[i]), 1);
+                }
+                hl = (lane == 0) ? hx[i] : hl;
+                ll = (lane == 0) ? lx[i] : ll;
+                hr = (lane == 31) ? hx[i] : hr;
+                lr = (lane == 31) ? lx[i] : lr;
+                if (v < nvec) {
+                    V r;
+                    if constexpr (pair) r = sdiff4(h[i], l[i], hl, ll, hr, lr);
+                    else r = sdiff2(h[i], hl, hr);
+                    if (v == 0) r.x = r.y;             // Dirichlet: the end node takes the interior centre
+                    *reinterpret_cast<V *>(R + St::pos(VN * v)) = r;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    T r[RPT];
+    stage_to_regs<T, RPT>(R, r, lane, false);
+    __syncwarp();
+    copy_field(0);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncwarp();
+
+    // 3. Horner in D_x with the fields from shared memory
+    T z[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) z[k] = 0;
+    for (int t = pb.P; t >= 0; --t) {
+        for (int k = 0; k < ng; ++k) {
+            const T c = (T)pb.coef[t][k];
+            if (c == (T)0) continue;
+            const V *seg = reinterpret_cast<const V *>(B + k * LB + lane * St::SST);
+#pragma unroll
+            for (int q = 0; q < RPT / VN; ++q) {
+                const V y = seg[q];
+                const T *e = reinterpret_cast<const T *>(&y);
+#pragma unroll
+                for (int cc = 0; cc < VN; ++cc) z[VN * q + cc] += c * e[cc];
+            }
+        }
+        if (t == 0) break;
+        warp_sweep_rreg<T, BC_DIRICHLET, RPT, true>(z, r, (T)pb.cu[t], A, lane);
+    }
+
+    // 4. F -> coalesced side -> next level; padding points get F = 0
+    __syncwarp();
+    regs_to_stage<T, RPT>(B, z, lane);
+    __syncwarp();
+    constexpr int CH = NVL > 4 ? 4 : NVL;
+#pragma unroll
+    for (int i0 = 0; i0 < NVL; i0 += CH) {
+        V F[CH];
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int v = lane + 32 * (i0 + i);
+            F[i] = V{};
+            if (v < nvec) {
+                F[i] = *CoalescedSide<T, RPT>::at(B, v * VN);
+                T *e = reinterpret_cast<T *>(&F[i]);
+#pragma unroll
+                for (int cc = 0; cc < VN; ++cc) e[cc] = (VN * v + cc < n) ? e[cc] : (T)0;
+            }
+        }
+        level_batch<T, CH>(pr, base, lane, i0, nvec, F);
+    }
+}
+
+// LARGE: rows of 513..1024 points (32-point segments; the segment, its r and
+// the sweep temporaries need more than 128 registers); else rows of up to
+// 512 points at two CTAs per SM.  Rows [row_begin, nitems) of the list.
+template <class T, bool LARGE>
+__global__ void __launch_bounds__(256, LARGE ? 1 : 2) k_batch_x(BatchPass bp, int nbuf)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, W = blockDim.x >> 5;
+    BatchProb *pbs = reinterpret_cast<BatchProb *>(smem_raw) + warp;
+    T *B = reinterpret_cast<T *>(smem_raw + (size_t)W * sizeof(BatchProb)) + (size_t)warp * nbuf * BatchX<T>::LINE;
+    int cur = -1;
+    for (int r = bp.row_begin + blockIdx.x * W + warp; r < bp.nitems; r += gridDim.x * W) {
+        const int p = __ldg(bp.row_prob + r);
+        if (p != cur) {
+            __syncwarp();
+            warp_copy(pbs, bp.probs + p, lane);
+            __syncwarp();
+            cur = p;
+        }
+        const BatchProb &pb = *pbs;
+        const int row = r - pb.row0;
+        if (LARGE) {
+            batch_row<T, 32>(pb, bp.pr, row, lane, B);
+        } else {
+            switch (pb.rpt_x) {
+            case 4: batch_row<T, 4>(pb, bp.pr, row, lane, B); break;
+            case 8: batch_row<T, 8>(pb, bp.pr, row, lane, B); break;
+            default: batch_row<T, 16>(pb, bp.pr, row, lane, B); break;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// y pass: one group of 32 columns
+// ---------------------------------------------------------------------------
+// r = accurate second difference of u at rows a-1 .. a+RPT of one column,
+// every row index clamped into the problem (the last segment may be partial)
+template <int RPT>
+__device__ __forceinline__ void bcol_r_rag(const ProgParams &pr, int64_t lbase, int64_t st, int a, int n,
+                                           float (&r)[RPT], float &rl, float &rr)
+{
+    const float *H = (const float *)pr.u_hi + lbase, *L = (const float *)pr.u_lo + lbase;
+    auto row = [&](int j) { return (int64_t)(j < 0 ? 0 : (j > n - 1 ? n - 1 : j)) * st; };
+    float hm = H[row(a - 2)], lm = L[row(a - 2)], h0 = H[row(a - 1)], l0 = L[row(a - 1)];
+#pragma unroll
+    for (int k = 0; k <= RPT + 1; ++k) {
+        const int64_t j = row(a + k);
+        const float hp = H[j], lp = L[j];
+        const float v = sdiff_pair(hm, h0, hp, lm, l0, lp);
+        if (k == 0) rl = v; else if (k == RPT + 1) rr = v; else r[k - 1] = v;
+        hm = h0; h0 = hp; lm = l0; l0 = lp;
+    }
+}
+
+template <int RPT>
+__device__ __forceinline__ void bcol_r_rag(const ProgParams &pr, int64_t lbase, int64_t st, int a, int n,
+                                           double (&r)[RPT], double &rl, double &rr)
+{
+    const double *U = (const double *)pr.u_hi + lbase;
+    auto row = [&](int j) { return (int64_t)(j < 0 ? 0 : (j > n - 1 ? n - 1 : j)) * st; };
+    double um = U[row(a - 2)], u0 = U[row(a - 1)];
+#pragma unroll
+    for (int k = 0; k <= RPT + 1; ++k) {
+        const double up = U[row(a + k)];
+        const double v = (up - u0) - (u0 - um);
+        if (k == 0) rl = v; else if (k == RPT + 1) rr = v; else r[k - 1] = v;
+        um = u0; u0 = up;
+    }
+}
+
+// One application of D on this thread's segment of a Dirichlet column of any
+// length.  rag: the segment holds the last point (0 <= kl < RPT) or the one
+// before it (kl == RPT); YL carries y_{n-1} of every lane from the segment
+// that holds the last point to all segments.
+template <class T, int RPT, int MODE>
+__device__ __forceinline__ void bsweep(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT], T l2, T l1, T r0,
+                                       T r1, int kl, bool rag, T *YL)
+{
+    const bool left = c.seg == 0;
+    end_ghosts<T, RPT, MODE>(z, left, false, l2, l1, r0, r1);
+    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    auto rz = [&](int) { return (T)0; };
+    if (rag) seg_make_q<T, RPT, MODE, true>(z, l2, l1, r0, r1, rz, (T)0, c1, c2, kl);
+    else seg_make_q<T, RPT, MODE, false>(z, l2, l1, r0, r1, rz, (T)0, c1, c2);
+    end_zero<T, RPT>(z, left, false);
+    if (!c.full) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+    }
+    const T d = c.d;
+    const T E = seg_fwd_reduce<T, RPT>(z, d);
+    T yin, ytot;
+    strided_causal<T, RPT>(c, E, yin, ytot);
+    if (!c.full) yin = 0;
+    T ylast = 0;
+    const T ER = rag ? seg_fwd_scan<T, RPT, true>(z, d, yin, kl, &ylast) : seg_fwd_scan<T, RPT>(z, d, yin);
+    if (rag && kl < RPT) YL[c.lane] = ylast;
+    T eout, e00;
+    strided_anticausal<T, RPT>(c, ER, eout, e00);      // its barrier publishes YL
+    const T yl = YL[c.lane];
+    const T mu = (T)A.mu, inv = (T)A.inv;
+    const T Acoef = (mu * yl - e00) * inv;
+    const T Z = (mu * e00 - yl) * inv;
+    const T acc = d * eout + ((c.full && kl >= RPT) ? c.dpg[kl + 1 - RPT] * Z : (T)0);
+    if (rag) seg_bwd_scan<T, RPT, true>(z, d, acc, kl, Z);
+    else seg_bwd_scan<T, RPT>(z, d, acc);
+    if (c.full) seg_add_left<T, RPT>(z, d, Acoef * c.dpg[c.a]);
+}
+
+template <class T, int RPT>
+__device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams &pr, int col0, StridedCtx<T> &c, T *YL)
+{
+    const AxisDev &A = pb.ay;
+    const int n = A.n;
+    c.n = n;
+    c.d = (T)A.d;
+    c.dR = (T)A.dm[0];
+    c.dpg = dpow_of<T>(A);
+    c.Gd = (n + RPT - 1) / RPT;
+    c.a = c.seg * RPT;
+    c.full = c.seg < c.Gd;
+    const int kl = n - 1 - c.a;
+    const bool rag = c.full && kl <= RPT;
+    const int col = col0 + c.lane;
+    const bool io = c.full && col < pb.ax.n;
+    const int64_t lbase = pb.off + (io ? col : 0);
+    const int64_t st = pb.pitch;
+
+    T z[RPT];
+    T rl = 0, rr = 0;
+    if (io) {
+        if (rag) bcol_r_rag<RPT>(pr, lbase, st, c.a, n, z, rl, rr);
+        else strided_r_pair<BC_DIRICHLET, RPT>(pr, lbase, st, c.a, n, z, rl, rr);
+    } else {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+    }
+    if (c.seg == 0) z[0] = z[1];                   // Dirichlet: the end node takes the interior centre
+
+    for (int p = 1; p <= pb.P; ++p) {
+        if (p == 1) {
+            bsweep<T, RPT, 0>(c, A, z, (T)0, rl, rr, (T)0, kl, rag, YL);
+        } else {
+            T l2, l1, r0, r1;
+            strided_halos<T, BC_DIRICHLET, RPT>(c, z, l2, l1, r0, r1, p & 1);
+            bsweep<T, RPT, 1>(c, A, z, l2, l1, r0, r1, kl, rag, YL);
+        }
+        if (io) {
+            T *po = reinterpret_cast<T *>(pr.out[p - 1]) + lbase + (int64_t)c.a * st;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (k <= kl) *po = z[k];
+                po += st;
+            }
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) BatchProb pbs;
+    StridedCtx<T> c{cg::this_cluster()};
+    c.S = kBatchYWarps;
+    c.K = 1;
+    c.krank = 0;
+    c.w = threadIdx.x >> 5;
+    c.lane = threadIdx.x & 31;
+    c.seg = c.w;
+    {
+        T *p = reinterpret_cast<T *>(smem_raw);
+        c.sl.E = p;
+        c.sl.ER = p + c.S * 32;
+        c.sl.H = p + 2 * c.S * 32;
+        c.sl.Tot = p + 10 * c.S * 32;
+    }
+    T *YL = reinterpret_cast<T *>(smem_raw + strided_slot_bytes(kBatchYWarps, sizeof(T)));
+    for (int it = blockIdx.x; it < bp.nitems; it += gridDim.x) {
+        const int2 item = bp.items[it];
+        __syncthreads();                               // the previous item is done with pbs and the slots
+        if (threadIdx.x < 32) warp_copy(&pbs, bp.probs + item.x, threadIdx.x);
+        __syncthreads();
+        switch (pbs.rpt_y) {
+        case 4: batch_cols<T, 4>(pbs, bp.pr, item.y, c, YL); break;
+        case 8: batch_cols<T, 8>(pbs, bp.pr, item.y, c, YL); break;
+        case 16: batch_cols<T, 16>(pbs, bp.pr, item.y, c, YL); break;
+        case 32: batch_cols<T, 32>(pbs, bp.pr, item.y, c, YL); break;
+        default: batch_cols<T, 64>(pbs, bp.pr, item.y, c, YL); break;
+        }
+    }
+}
+
+inline size_t batch_y_smem(size_t tsize) { return strided_slot_bytes(kBatchYWarps, tsize) + 32 * tsize; }
+inline size_t batch_x_smem(size_t tsize, int W, int nbuf)
+{
+    return (size_t)W * (sizeof(BatchProb) + (size_t)nbuf * 32 * (BatchX<float>::RMAX + 16 / tsize) * tsize);
+}
+
+// ---------------------------------------------------------------------------
+// packed float64 fields (problem after problem, rows of nx points) <->
+// internal layout (padded rows; float32 pairs or float64)
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_batch_pack(const BatchProb *probs, const int *row_prob, const long long *uoff, int nrows,
+                             const double *__restrict__ x, T *hi, T *lo)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = gw; r < nrows; r += nw) {
+        const int p = __ldg(row_prob + r);
+        const BatchProb *pb = probs + p;
+        const int nx = __ldg(&pb->ax.n), pitch = __ldg(&pb->pitch);
+        const int row = r - __ldg(&pb->row0);
+        const double *src = x + __ldg(uoff + p) + (int64_t)row * nx;
+        const int64_t dst = __ldg(&pb->off) + (int64_t)row * pitch;
+        for (int j = lane; j < pitch; j += 32) {
+            const double v = j < nx ? src[j] : 0.0;
+            if constexpr (sizeof(T) == 4) {
+                const float h = __double2float_rn(v);
+                hi[dst + j] = h;
+                lo[dst + j] = __double2float_rn(v - (double)h);
+            } else {
+                hi[dst + j] = v;
+            }
+        }
+    }
+}
+
+template <class T>
+__global__ void k_batch_unpack(const BatchProb *probs, const int *row_prob, const long long *uoff, int nrows,
+                               const T *hi, const T *lo, double *__restrict__ x)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = gw; r < nrows; r += nw) {
+        const int p = __ldg(row_prob + r);
+        const BatchProb *pb = probs + p;
+        const int nx = __ldg(&pb->ax.n), pitch = __ldg(&pb->pitch);
+        const int row = r - __ldg(&pb->row0);
+        double *dstp = x + __ldg(uoff + p) + (int64_t)row * nx;
+        const int64_t src = __ldg(&pb->off) + (int64_t)row * pitch;
+        for (int j = lane; j < nx; j += 32) {
+            if constexpr (sizeof(T) == 4) dstp[j] = (double)hi[src + j] + (double)lo[src + j];
+            else dstp[j] = hi[src + j];
+        }
+    }
+}
+
+}  // namespace molt

@@ -1,9 +1,25 @@
 // molt_internal.h -- launchers shared by the C-ABI layer and the kernel unit.
 #pragma once
 #include <cuda_runtime.h>
+#include <string>
+#include <vector>
 #include "molt_kernels.cuh"
 
 namespace molt {
+
+constexpr int kMaxP = 5;            // highest order parameter P (order 2P)
+constexpr int64_t kMaxLine = 8192;  // longest line of the single-problem sweeps
+
+// Host constants of the scheme (molt_host.cu).
+double term_weight(int p, int m, double beta);     // weight of C^m D^{p-m} in the update
+double beta_max_of(int P);                         // Table 1; -1 outside 1..5
+// F = sum f_ijk D_x^i D_y^j D_z^k, degree <= P per axis, index i + (P+1)(j + (P+1)k)
+bool expand_coefficients(int ndim, int P, double beta, std::vector<double> &out);
+double quad_R(double nu);                          // second-difference weight of the quadratic rule
+void axis_constants(double nu, int64_t n, int bc, int quad, AxisDev &A);
+
+// Message for mol_last_error(NULL) (molt_api.cu).
+void set_global_error(const std::string &msg);
 
 // tbytes: 4 -> float32 sweeps (pair levels), 8 -> float64 throughout.
 cudaError_t launch_powers(int tbytes, int bc, bool contig, const AxisDev &A, const PassGeom &G,

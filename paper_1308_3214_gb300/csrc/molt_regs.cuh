@@ -40,8 +40,12 @@ template <> struct VecOf<double> { using type = double2; static constexpr int n 
 // a+RPT+1 (MODE 0: zl1 = s_{a-1}, zr0 = s_{a+RPT}).  r(k) supplies r at a+k
 // for k in [-1, RPT].  Dirichlet ends are handled by the caller: ghost values
 // in the halos (end_ghosts) and q = 0 at the end nodes (end_zero).
-template <class T, int RPT, int MODE, class RF>
-__device__ __forceinline__ void seg_make_q(T (&z)[RPT], T zl2, T zl1, T zr0, T zr1, RF r, T cu, T c1, T c2)
+// RAG (Dirichlet lines whose last point n-1 may sit anywhere): kl = n-1-a is
+// the local index of the last point; s_{n-1} is replaced by s_{n-2} in
+// q_{n-2} (the one-sided end interpolant) and q = 0 from the last point on.
+template <class T, int RPT, int MODE, bool RAG = false, class RF>
+__device__ __forceinline__ void seg_make_q(T (&z)[RPT], T zl2, T zl1, T zr0, T zr1, RF r, T cu, T c1, T c2,
+                                           int kl = 0)
 {
     T sm1, s0, zk, zp1;
     if (MODE == 0) {
@@ -66,7 +70,9 @@ __device__ __forceinline__ void seg_make_q(T (&z)[RPT], T zl2, T zl1, T zr0, T z
             zk = zp1;
             zp1 = zp2;
         }
+        if (RAG) sp1 = (k == kl - 1) ? s0 : sp1;
         z[k] = c1 * s0 + c2 * (sm1 + sp1);
+        if (RAG) z[k] = (k < kl) ? z[k] : (T)0;
         sm1 = s0;
         s0 = sp1;
     }
@@ -107,28 +113,35 @@ __device__ __forceinline__ T seg_fwd_reduce(const T (&q)[RPT], T d)
     return E;
 }
 
-// y_k = d y_{k-1} + q_k from y = y_{a-1}; returns ER = sum_k d^k y_k
-template <class T, int RPT>
-__device__ __forceinline__ T seg_fwd_scan(T (&z)[RPT], T d, T y)
+// y_k = d y_{k-1} + q_k from y = y_{a-1}; returns ER = sum_k d^k y_k.
+// RAG: y = 0 past the last point kl (so that the zero-inflow anti-causal
+// value at n-1 is y_{n-1} itself), and ylast = y_{n-1} when kl is local.
+template <class T, int RPT, bool RAG = false>
+__device__ __forceinline__ T seg_fwd_scan(T (&z)[RPT], T d, T y, int kl = 0, T *ylast = nullptr)
 {
-    T ER = 0, pw = 1;
+    T ER = 0, pw = 1, yl = 0;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
         y = d * y + z[k];
-        z[k] = y;
-        ER += pw * y;
+        const T yo = (!RAG || k <= kl) ? y : (T)0;
+        if (RAG) yl = (k == kl) ? y : yl;
+        z[k] = yo;
+        ER += pw * yo;
         pw *= d;
     }
+    if (RAG) *ylast = yl;
     return ER;
 }
 
-// e_k = d e_{k+1} + y_k with acc = d e_{a+RPT} on entry
-template <class T, int RPT>
-__device__ __forceinline__ void seg_bwd_scan(T (&z)[RPT], T d, T acc)
+// e_k = d e_{k+1} + y_k with acc = d e_{a+RPT} on entry.  RAG: the right
+// boundary term B' d^{n-1-j} enters at the last point kl as Zr.
+template <class T, int RPT, bool RAG = false>
+__device__ __forceinline__ void seg_bwd_scan(T (&z)[RPT], T d, T acc, int kl = 0, T Zr = 0)
 {
 #pragma unroll
     for (int k = RPT - 1; k >= 0; --k) {
-        const T e = acc + z[k];
+        T e = acc + z[k];
+        if (RAG) e += (k == kl) ? Zr : (T)0;
         acc = d * e;
         z[k] = e;
     }
@@ -157,15 +170,18 @@ struct ContigStage {
 };
 
 // One application of D on a line held by a warp (lane = segment).  The line
-// has n = RPT * (Ld + 1) points; lanes past Ld hold zeros.
-template <class T, int BC, int RPT, int MODE, class RF>
+// has n = RPT * (Ld + 1) points; lanes past Ld hold zeros.  RAG (Dirichlet
+// only): any n <= 32 RPT; lane Ld = (n-1)/RPT holds the last point.
+template <class T, int BC, int RPT, int MODE, bool RAG = false, class RF>
 __device__ __forceinline__ void warp_sweep_core(T (&z)[RPT], RF rfun, T cu, const AxisDev &A, int lane)
 {
+    static_assert(!RAG || BC == BC_DIRICHLET, "ragged lines are Dirichlet lines");
     const int n = A.n;
     const T d = (T)A.d;
-    const int Ld = n / RPT - 1;
+    const int Ld = RAG ? (n - 1) / RPT : n / RPT - 1;
     const bool full = lane <= Ld;
     const int a = lane * RPT;
+    const int kl = n - 1 - a;
 
     // Lanes diverge in the predicated per-lane code; __shfl_sync pairs lanes by
     // mask, not by call site, so the warp is reconverged before every group of
@@ -183,11 +199,11 @@ __device__ __forceinline__ void warp_sweep_core(T (&z)[RPT], RF rfun, T cu, cons
         zr0 = (lane == Ld) ? v0 : zr0;
         zr1 = (lane == Ld) ? v1 : zr1;
     } else {
-        end_ghosts<T, RPT, MODE>(z, lane == 0, lane == Ld, zl2, zl1, zr0, zr1);
+        end_ghosts<T, RPT, MODE>(z, lane == 0, !RAG && lane == Ld, zl2, zl1, zr0, zr1);
     }
     const T c1 = (T)A.c1, c2 = (T)A.c2;
-    seg_make_q<T, RPT, MODE>(z, zl2, zl1, zr0, zr1, rfun, cu, c1, c2);
-    if (BC == BC_DIRICHLET) end_zero<T, RPT>(z, lane == 0, lane == Ld);
+    seg_make_q<T, RPT, MODE, RAG>(z, zl2, zl1, zr0, zr1, rfun, cu, c1, c2, kl);
+    if (BC == BC_DIRICHLET) end_zero<T, RPT>(z, lane == 0, !RAG && lane == Ld);
 #pragma unroll
     for (int k = 0; k < RPT; ++k) z[k] = full ? z[k] : (T)0;
 
@@ -208,7 +224,8 @@ __device__ __forceinline__ void warp_sweep_core(T (&z)[RPT], RF rfun, T cu, cons
     if (BC == BC_PERIODIC)
         yin += full ? dpg[a] * (tot * (T)A.inv) : (T)0;          // images to the left
     yin = full ? yin : (T)0;                                     // lanes past the line stay zero
-    const T ER = seg_fwd_scan<T, RPT>(z, d, yin);
+    T ylast = 0;
+    const T ER = seg_fwd_scan<T, RPT, RAG>(z, d, yin, kl, &ylast);
 
     // anti-causal carries
     __syncwarp();
@@ -220,7 +237,7 @@ __device__ __forceinline__ void warp_sweep_core(T (&z)[RPT], RF rfun, T cu, cons
     }
     T exclb = __shfl_down_sync(0xffffffffu, xb, 1);
     const T e00 = __shfl_sync(0xffffffffu, xb, 0);              // zero-inflow e_0
-    const T yl = __shfl_sync(0xffffffffu, z[RPT - 1], Ld);      // y_{n-1}
+    const T yl = __shfl_sync(0xffffffffu, RAG ? ylast : z[RPT - 1], Ld);   // y_{n-1}
     exclb = (lane == 31) ? (T)0 : exclb;
     T Z, Acoef = 0;
     if (BC == BC_DIRICHLET) {
@@ -230,9 +247,12 @@ __device__ __forceinline__ void warp_sweep_core(T (&z)[RPT], RF rfun, T cu, cons
     } else {
         Z = d * e00 * (T)A.inv;
     }
-    const int ia = full ? a : 0, ib = full ? n - a - RPT : 0;   // table indices in [0, n]
-    const T acc = d * exclb + (full ? dpg[ib] * Z : (T)0);
-    seg_bwd_scan<T, RPT>(z, d, acc);
+    // B' d^{n-1-j}: through the inflow of every segment that ends before the
+    // last point; RAG injects it at the last point itself
+    const bool before = RAG ? lane < Ld : full;
+    const int ia = full ? a : 0, ib = before ? n - a - RPT : 0;   // table indices in [0, n]
+    const T acc = d * exclb + (before ? dpg[ib] * Z : (T)0);
+    seg_bwd_scan<T, RPT, RAG>(z, d, acc, kl, Z);
     if (BC == BC_DIRICHLET && full) seg_add_left<T, RPT>(z, d, Acoef * dpg[ia]);
     __syncwarp();
 }
@@ -255,11 +275,11 @@ __device__ __forceinline__ void warp_sweep(T (&z)[RPT], const T *rline, T cu, co
 }
 
 // D on the warp's line, MODE 2 with r held in registers (segment layout)
-template <class T, int BC, int RPT>
+template <class T, int BC, int RPT, bool RAG = false>
 __device__ __forceinline__ void warp_sweep_rreg(T (&z)[RPT], const T (&r)[RPT], T cu, const AxisDev &A, int lane)
 {
     const int n = A.n;
-    const int Ld = n / RPT - 1;
+    const int Ld = RAG ? (n - 1) / RPT : n / RPT - 1;
     __syncwarp();
     T rl = __shfl_up_sync(0xffffffffu, r[RPT - 1], 1);
     T rr = __shfl_down_sync(0xffffffffu, r[0], 1);
@@ -268,7 +288,7 @@ __device__ __forceinline__ void warp_sweep_rreg(T (&z)[RPT], const T (&r)[RPT], 
         rl = (lane == 0) ? wl : rl;
         rr = (lane == Ld) ? wr : rr;
     }
-    warp_sweep_core<T, BC, RPT, 2>(z, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : r[k]); }, cu, A, lane);
+    warp_sweep_core<T, BC, RPT, 2, RAG>(z, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : r[k]); }, cu, A, lane);
 }
 
 // stage (coalesced side) -> registers (segment side)

@@ -29,7 +29,9 @@ PREC = {"fp64": 0, "mixed": 1}
 EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error", "mol_beta_max",
            "mol_max_line", "mol_get_params", "mol_apply_D", "mol_apply_F", "mol_start", "mol_step",
            "mol_solve_host", "mol_sync", "mol_launch_count", "mol_set_pass_timing", "mol_pass_times",
-           "mol_apply_F_noalloc"]
+           "mol_apply_F_noalloc", "mol_batch_create", "mol_batch_destroy", "mol_batch_last_error",
+           "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_sync",
+           "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times"]
 
 
 class MolError(RuntimeError):
@@ -85,10 +87,24 @@ def load_library(path: Path | None = None):
     lib.mol_pass_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
     lib.mol_launch_count.argtypes = [vp]
     lib.mol_apply_F_noalloc.argtypes = [ctypes.POINTER(mol_grid), D, D, D, I, I, I, vp, vp, vp]
+    lib.mol_batch_create.argtypes = [I, ctypes.POINTER(mol_grid), dp, dp, dp, ctypes.POINTER(I), I, I,
+                                     ctypes.POINTER(mol_options), ctypes.POINTER(vp)]
+    lib.mol_batch_destroy.argtypes = [vp]
+    lib.mol_batch_last_error.argtypes = [vp]
+    lib.mol_batch_last_error.restype = ctypes.c_char_p
+    lib.mol_batch_offsets.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.mol_batch_apply_F.argtypes = [vp, vp, vp, vp]
+    lib.mol_batch_start.argtypes = [vp, vp, vp, vp]
+    lib.mol_batch_step.argtypes = [vp, vp, vp, i64, vp]
+    lib.mol_batch_sync.argtypes = [vp, vp]
+    lib.mol_batch_launch_count.argtypes = [vp]
+    lib.mol_batch_launch_count.restype = i64
+    lib.mol_batch_set_pass_timing.argtypes = [vp, I]
+    lib.mol_batch_pass_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
-                        "mol_launch_count"):
+                        "mol_launch_count", "mol_batch_last_error", "mol_batch_launch_count"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -250,6 +266,133 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.mol_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class BatchSolver:
+    """Many independent 2D Dirichlet problems stepped together (one launch
+    per pass for all of them).
+
+    ``shapes``: one (ny, nx) per problem; ``dt``, ``P``, ``c``, ``beta``: one
+    value per problem or a scalar for all; ``lo`` / ``hi``: per-problem
+    (y, x) pairs or None for the unit square.  Fields are PACKED: one flat
+    CUDA float64 tensor holding every problem's (ny, nx) array in turn;
+    ``pack`` / ``unpack`` convert."""
+
+    def __init__(self, shapes, dt, P, c=1.0, beta=0.0, prec: str = "mixed", lo=None, hi=None,
+                 quad_order: int = 2, use_graphs: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libmolt needs a CUDA GPU")
+        self.lib = load_library()
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        n = len(self.shapes)
+
+        def per(v, cast):
+            arr = np.broadcast_to(np.asarray(v), (n,)) if np.ndim(v) == 0 else np.asarray(v)
+            if len(arr) != n:
+                raise ValueError("per-problem arrays need one entry per shape")
+            return [cast(x) for x in arr]
+
+        grids = (mol_grid * n)()
+        for i, shp in enumerate(self.shapes):
+            if len(shp) != 2:
+                raise ValueError("batched problems are 2D")
+            grids[i] = make_grid(shp, None if lo is None else lo[i], None if hi is None else hi[i])
+        self.dt, self.P, self.c = per(dt, float), per(P, int), per(c, float)
+        betas = per(beta, float)
+        dts = (ctypes.c_double * n)(*self.dt)
+        cs = (ctypes.c_double * n)(*self.c)
+        bs = (ctypes.c_double * n)(*betas)
+        Ps = (ctypes.c_int * n)(*self.P)
+        opt = mol_options(int(quad_order), 0, 1 if use_graphs else 0)
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        st = self.lib.mol_batch_create(n, grids, cs, dts, bs, Ps, BC["dirichlet"], PREC[prec], ctypes.byref(opt),
+                                       ctypes.byref(h))
+        if st != MOL_OK:
+            raise MolError(st, self.lib.mol_last_error(None).decode())
+        self.h = h
+        self.prec = prec
+        offs = (ctypes.c_int64 * (n + 1))()
+        self._check(self.lib.mol_batch_offsets(self.h, offs))
+        self.offsets = [int(v) for v in offs]
+        self.size = self.offsets[-1]
+
+    def _check(self, st: int):
+        if st != MOL_OK:
+            raise MolError(st, self.lib.mol_batch_last_error(self.h).decode())
+
+    def _flat(self, t, name):
+        import torch
+        if (not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or t.dim() != 1
+                or t.numel() != self.size or not t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous CUDA float64 tensor of {self.size} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def empty(self):
+        import torch
+        return torch.empty(self.size, dtype=torch.float64, device="cuda")
+
+    def pack(self, fields):
+        """Packed device tensor from one (ny, nx) array per problem."""
+        import torch
+        parts = [torch.as_tensor(np.ascontiguousarray(f) if isinstance(f, np.ndarray) else f,
+                                 dtype=torch.float64).reshape(-1) for f in fields]
+        return torch.cat([p.cpu() for p in parts]).cuda()
+
+    def unpack(self, flat):
+        """Per-problem (ny, nx) views of a packed tensor."""
+        return [flat[self.offsets[i]:self.offsets[i + 1]].view(*self.shapes[i]) for i in range(len(self.shapes))]
+
+    def apply_F(self, u, out=None, stream=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_batch_apply_F(self.h, self._flat(u, "u"), self._flat(out, "F"),
+                                               ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def start(self, u0, out=None, stream=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_batch_start(self.h, self._flat(u0, "u0"), self._flat(out, "u1"),
+                                             ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def step(self, u_prev, u_cur, nsteps: int, stream=None):
+        self._check(self.lib.mol_batch_step(self.h, self._flat(u_prev, "u_prev"), self._flat(u_cur, "u_cur"),
+                                            int(nsteps), ctypes.c_void_p(_stream_ptr(stream))))
+        return u_prev, u_cur
+
+    def sync(self, stream=None):
+        self._check(self.lib.mol_batch_sync(self.h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def set_pass_timing(self, enable: bool = True):
+        self._check(self.lib.mol_batch_set_pass_timing(self.h, 1 if enable else 0))
+
+    def pass_times(self):
+        ms = (ctypes.c_double * 3)()
+        cnt = (ctypes.c_int64 * 3)()
+        self._check(self.lib.mol_batch_pass_times(self.h, ms, cnt))
+        return {a: (ms[a], int(cnt[a])) for a in range(3) if cnt[a] > 0}
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.mol_batch_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mol_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

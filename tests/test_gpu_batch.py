@@ -1,0 +1,192 @@
+"""Batches of 2D Dirichlet problems of uneven size (mol_batch_*), problem by
+problem against the float64 oracle.
+
+The shapes cover every segment length of both passes (x: 4..32 points per
+lane; y: 4..64 rows per warp), lines whose last point falls anywhere in a
+segment (n = 3 .. 1024, odd and even, one past and one short of a power of
+two), rectangles in both orientations, and P = 1..3 with CFL 0.5..4.
+Tolerances as in test_gpu_parity: float64 1e-12 (or the oracle's own
+cancellation floor); mixed 16 eps32 (1 + 1/(1 - d)) 2P for F and the
+accumulated model 8 eps32 (1 + 1/(1 - d)) 2P sum|F_k| / |u_n| for steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1308_3214_gb300 import molt, workloads
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+EPS64 = 2.0 ** -52
+
+SHAPES = [(64, 64), (65, 67), (3, 3), (5, 130), (100, 129), (250, 257), (17, 300), (300, 17), (511, 513),
+          (700, 1000), (1024, 1024), (33, 1021), (129, 4), (40, 512), (512, 40), (1023, 7)]
+CFLS = [0.5, 4.0, 1.3, 2.0, 0.8, 3.3, 1.0]
+
+
+def spec(i, shape):
+    P = 1 + i % 3
+    cfl = CFLS[i % len(CFLS)]
+    ny, nx = shape
+    hx, hy = 1.0 / (nx - 1), 1.0 / (ny - 1)
+    dt = cfl * min(hx, hy)
+    beta = oracle.beta_max(P)
+    alpha = beta / dt
+    nu = (alpha * hx, alpha * hy)           # x first, as the oracle takes it
+    return P, dt, beta, nu
+
+
+def rough_field(shape, seed):
+    u = workloads.random_field(shape, seed)
+    u[0, :] = u[-1, :] = 0.0
+    u[:, 0] = u[:, -1] = 0.0
+    return u
+
+
+def smooth_field(shape, seed):
+    rng = np.random.default_rng(seed)
+    y = np.linspace(0, 1, shape[0])[:, None]
+    x = np.linspace(0, 1, shape[1])[None, :]
+    u = np.zeros(shape)
+    for _ in range(3):
+        kx, ky = rng.integers(1, 4, size=2)
+        u += rng.normal() * np.sin(np.pi * kx * x) * np.sin(np.pi * ky * y)
+    return u
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def make_batch(shapes, prec, **kw):
+    specs = [spec(i, s) for i, s in enumerate(shapes)]
+    b = molt.BatchSolver(shapes, dt=[s[1] for s in specs], P=[s[0] for s in specs], prec=prec, **kw)
+    return b, specs
+
+
+def mixed_tol(nu, p):
+    dmax = max(math.exp(-v) for v in nu)
+    return 16 * EPS32 * (1.0 + 1.0 / (1.0 - dmax)) * p
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_F_matches_oracle(prec):
+    b, specs = make_batch(SHAPES, prec)
+    us = [rough_field(s, 300 + i) for i, s in enumerate(SHAPES)]
+    got = b.unpack(b.apply_F(b.pack(us)))
+    torch.cuda.synchronize()
+    for i, (u, g, (P, dt, beta, nu)) in enumerate(zip(us, got, specs)):
+        ref = oracle.F(u, nu, P, beta, "dirichlet")
+        cond = np.linalg.norm(u) / max(np.linalg.norm(ref), 1e-300)
+        tol = max(1e-12, 64 * EPS64 * cond) if prec == "fp64" else mixed_tol(nu, 2 * P)
+        err = rel_l2(g.cpu().numpy(), ref)
+        assert err <= tol, (i, SHAPES[i], P, err, tol)
+
+
+STEP_SHAPES = [(64, 64), (65, 67), (5, 130), (100, 129), (250, 257), (300, 17), (129, 4), (40, 512), (33, 1021)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_start_and_steps_match_oracle(prec):
+    nsteps = 7
+    b, specs = make_batch(STEP_SHAPES, prec)
+    u0s = [smooth_field(s, 400 + i) + 0.05 * rough_field(s, 500 + i) for i, s in enumerate(STEP_SHAPES)]
+    u1 = b.start(b.pack(u0s))
+    up, uc = b.pack(u0s), u1.clone()
+    b.step(up, uc, nsteps)
+    torch.cuda.synchronize()
+    g1, gp, gc = b.unpack(u1), b.unpack(up), b.unpack(uc)
+    for i, (u0, (P, dt, beta, nu)) in enumerate(zip(u0s, specs)):
+        r1 = oracle.start(u0, nu, P, beta, "dirichlet")
+        rp, rc = oracle.run(u0, r1, nsteps, nu, P, beta, "dirichlet")
+        if prec == "fp64":
+            tol1 = tol = 1e-12
+        else:
+            F0 = oracle.F(u0, nu, P, beta, "dirichlet")
+            tol1 = mixed_tol(nu, 2 * P) * 0.5 * np.linalg.norm(F0) / np.linalg.norm(r1)
+            Fsum, a, c = 0.0, u0, r1
+            for _ in range(nsteps):
+                F = oracle.F(c, nu, P, beta, "dirichlet")
+                Fsum += np.linalg.norm(F)
+                a, c = c, 2 * c - a + F
+            dmax = max(math.exp(-v) for v in nu)
+            tol = 8 * EPS32 * (1 + 1 / (1 - dmax)) * 2 * P * Fsum / np.linalg.norm(rc)
+        assert rel_l2(g1[i].cpu().numpy(), r1) <= tol1, (i, "start")
+        assert rel_l2(gc[i].cpu().numpy(), rc) <= tol, (i, "u_cur")
+        assert rel_l2(gp[i].cpu().numpy(), rp) <= tol, (i, "u_prev")
+
+
+def test_batch_graph_and_direct_agree_bitwise():
+    shapes = SHAPES[:8]
+    outs = []
+    for graphs in (True, False):
+        b, _ = make_batch(shapes, "mixed", use_graphs=graphs)
+        u0s = [smooth_field(s, 600 + i) for i, s in enumerate(shapes)]
+        up = b.pack(u0s)
+        uc = b.start(up)
+        b.step(up, uc, 6)
+        torch.cuda.synchronize()
+        outs.append(uc.cpu().numpy())
+        b.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_batch_launches_and_pass_times():
+    b, _ = make_batch(SHAPES, "mixed")
+    u = b.pack([smooth_field(s, 700 + i) for i, s in enumerate(SHAPES)])
+    v = b.start(u)
+    n0 = b.launches
+    b.step(u, v, 3)
+    b.sync()
+    # two level conversions in, two out; per step one y pass and the x pass
+    # (one launch for rows of <= 512 points, one for longer rows)
+    x_launches = int(any(s[1] <= 512 for s in SHAPES)) + int(any(s[1] > 512 for s in SHAPES))
+    assert b.launches - n0 == 4 + 3 * (1 + x_launches)
+    b.set_pass_timing(True)
+    b.step(u, v, 2)
+    t = b.pass_times()
+    assert set(t) == {0, 1} and t[0][1] == 2 and t[1][1] == 2 and t[0][0] > 0 and t[1][0] > 0
+
+
+def test_batch_rejects_bad_pointers():
+    b, _ = make_batch(SHAPES[:3], "fp64")
+    u = b.empty()
+    with pytest.raises(molt.MolError):
+        b.apply_F(u, u)
+    host = np.zeros(b.size)
+    st = b.lib.mol_batch_apply_F(b.h, host.ctypes.data_as(molt.ctypes.c_void_p), molt.ctypes.c_void_p(u.data_ptr()),
+                                 None)
+    assert st == molt.MOL_EINVAL
+
+
+@pytest.mark.slow
+def test_batch_full_size_512_problems_sampled():
+    """The 512-problem workload (n log-uniform in [64, 1024], P in 1..3, CFL
+    in [0.5, 4]): float64 F of every problem against mixed F, and 10
+    sampled problems against the oracle."""
+    probs = workloads.batch_problems()
+    shapes = [(p.n, p.n) for p in probs]
+    dts = [p.cfl / (p.n - 1) for p in probs]
+    Ps = [p.P for p in probs]
+    us = [p.u0 for p in probs]
+    res = {}
+    for prec in ("fp64", "mixed"):
+        b = molt.BatchSolver(shapes, dt=dts, P=Ps, prec=prec)
+        res[prec] = [t.cpu().numpy() for t in b.unpack(b.apply_F(b.pack(us)))]
+        b.close()
+    rng = np.random.default_rng(11)
+    for i in rng.choice(len(probs), size=10, replace=False):
+        p = probs[i]
+        beta = oracle.beta_max(p.P)
+        nu = beta / dts[i] / (p.n - 1)
+        ref = oracle.F(us[i], (nu, nu), p.P, beta, "dirichlet")
+        assert rel_l2(res["fp64"][i], ref) <= 1e-12, i
+    for i, p in enumerate(probs):
+        nu = oracle.beta_max(p.P) / dts[i] / (p.n - 1)
+        assert rel_l2(res["mixed"][i], res["fp64"][i]) <= mixed_tol((nu, nu), 2 * p.P), i
