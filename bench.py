@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark of the MOL^T wave solver on one or more GB300s.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 2d|3d|1d]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 2d|3d|1d|batch]
                     [--prec mixed|fp64] [--impl ours|reference]
 
 A "step" is one time step of the scheme of order 2P over the whole synthetic
@@ -10,7 +10,10 @@ and the level update u^{n+1} = 2u^n - u^{n-1} + F[u^n]).  The default workload
 is the 2D one: homogeneous Dirichlet unit square, 2048 x 2048 points, P = 3
 (6th order), CFL 2, beta = beta_max(3), a seeded Gaussian pulse; inputs are
 resident in HBM when the timed region starts.  Metric: point-updates/s
-(points x steps / second), summed over all GPUs.
+(points x steps / second), summed over all GPUs.  ``--workload batch``: 512
+independent Dirichlet squares, n log-uniform in [64, 1024], P in {1, 2, 3},
+CFL in [0.5, 4], seeded Gaussians, stepped together through mol_batch_step
+(every rank its own 512 problems).
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
 problem (independent replicas, weak scaling, no collective on the data path).
@@ -39,8 +42,11 @@ from paper_1308_3214_gb300 import workloads  # noqa: E402
 METRIC = "point-updates/s"
 PEAKS_FILE = ROOT / "MEASURED_PEAKS.json"
 TRAFFIC_FILE = ROOT / "profiles" / "ncu_traffic.json"
-KERNEL_SOURCES = [ROOT / "paper_1308_3214_gb300" / "csrc" / f for f in
-                  ("molt_kernels.cuh", "molt_regs.cuh", "molt_passes.cu", "molt_regs.cu", "molt_api.cu")]
+CSRC = ROOT / "paper_1308_3214_gb300" / "csrc"
+KERNEL_SOURCES = {
+    "single": [CSRC / f for f in ("molt_kernels.cuh", "molt_regs.cuh", "molt_passes.cu", "molt_regs.cu", "molt_api.cu")],
+    "batch": [CSRC / f for f in ("molt_kernels.cuh", "molt_regs.cuh", "molt_batch.cuh", "molt_batch.cu")],
+}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -56,6 +62,9 @@ def workload_spec(name: str) -> dict:
         return dict(name="3d-periodic-256^3-P2-cfl1.5-fourier16", shape=(n, n, n), P=2, cfl=1.5,
                     bc="periodic", lo=(0.0,) * 3, hi=(L,) * 3, h=L / n, steps_in_config=200,
                     field=lambda: workloads.fourier_3d(n, seed=1003)[0])
+    if name == "batch":
+        return dict(name="batch-512-dirichlet-n64..1024-P1..3-cfl0.5..4-gaussian", count=512, seed=1004,
+                    steps_in_config=200, bc="dirichlet")
     if name == "1d":
         n = 256
         L = 2 * math.pi
@@ -77,9 +86,12 @@ def bytes_per_point(spec: dict, prec: str) -> dict:
     return {2: 8 + t * P, 1: t * P + 8 + t * (P + 1), 0: t * (P + 1) + 24}
 
 
-def kernel_sha() -> str:
+def kernel_sha(family: str = "single") -> str:
+    """Hash of the sources the kernels of one family (single-problem or
+    batched passes) are compiled from; traffic figures taken on other
+    sources are not reported."""
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_SOURCES[family]:
         h.update(p.read_bytes())
     return h.hexdigest()[:16]
 
@@ -159,17 +171,16 @@ def read_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def read_traffic(kernel_axis: int, workload: str, prec: str):
-    """ncu DRAM bytes per launch of the dominant kernel, if taken on the
+def read_traffic(kernel_axis: int, workload: str, prec: str, family: str = "single"):
+    """ncu DRAM bytes per launch of the dominant pass, if taken on the
     current kernel sources."""
     try:
         d = json.loads(TRAFFIC_FILE.read_text())
     except Exception:
         return None
-    if d.get("kernel_sha") != kernel_sha():
-        return None
     for e in d.get("entries", []):
-        if e.get("workload") == workload and e.get("prec") == prec and int(e.get("axis", -1)) == kernel_axis:
+        if (e.get("workload") == workload and e.get("prec") == prec and int(e.get("axis", -1)) == kernel_axis
+                and e.get("kernel_sha") == kernel_sha(family)):
             return float(e["dram_bytes_per_launch"])
     return None
 
@@ -267,7 +278,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batch"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -278,6 +289,9 @@ def main():
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     spec = workload_spec(args.workload)
+    if args.workload == "batch":
+        main_batch(args, spec)
+        return
     if args.impl == "reference":
         run_reference(args, spec)
         return
@@ -432,6 +446,242 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched workload
+# ---------------------------------------------------------------------------
+def batch_set(spec, rank: int = 0):
+    """The 512 problems of one rank: (n, P, cfl, u0) each, dt = CFL h."""
+    probs = workloads.batch_problems(count=spec["count"], seed=spec["seed"] + 7919 * rank)
+    shapes = [(p.n, p.n) for p in probs]
+    dts = [p.cfl / (p.n - 1) for p in probs]
+    return probs, shapes, dts, [p.P for p in probs]
+
+
+def batch_oracle_rate(probs, dts, budget_s: float, steps: int = 2):
+    """Point-updates/s of the FP64 oracle on the first problems of the list
+    (in their seeded order) that fit the budget, `steps` steps each."""
+    import oracle
+    oracle.build()
+    pts = 0.0
+    used = 0
+    t_all = 0.0
+    for p, dt in zip(probs, dts):
+        beta = oracle.beta_max(p.P)
+        nu = beta / dt / (p.n - 1)
+        u1 = oracle.start(p.u0, nu, p.P, beta, "dirichlet")
+        t0 = time.perf_counter()
+        oracle.run(p.u0, u1, steps, nu, p.P, beta, "dirichlet")
+        t_all += time.perf_counter() - t0
+        pts += p.n * p.n * steps
+        used += 1
+        if t_all >= budget_s:
+            break
+    return pts / t_all, used, steps, t_all, oracle.num_threads()
+
+
+def main_batch(args, spec):
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        probs, shapes, dts, Ps = batch_set(spec)
+        # warm-up and timed steps, each step a bounded sample of problems
+        budget = 150.0 / max(args.steps + args.warmup, 1)
+        batch_oracle_rate(probs, dts, budget * args.warmup, steps=1)
+        rates = []
+        used = 0
+        for _ in range(args.steps):
+            r, used, _, _, cores = batch_oracle_rate(probs, dts, budget, steps=1)
+            rates.append(r)
+        value = float(np.mean(rates))
+        npts = sum(n * n for n, _ in shapes)
+        sample = f"each step: the first {used} of the 512 problems (seeded order), one oracle step each"
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * npts / value,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": spec["name"], "points_per_step": npts},
+                "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_1308_3214_gb300 import molt
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    probs, shapes, dts, Ps = batch_set(spec, rank)
+    npts = sum(n * n for n, _ in shapes)
+    t = 4 if args.prec == "mixed" else 8
+    bpp_tot = {1: sum(n * n * (8 + t * P) for (n, _), P in zip(shapes, Ps)),
+               0: sum(n * n * (t * P + 24) for (n, _), P in zip(shapes, Ps))}
+
+    def make(prec, **kw):
+        return molt.BatchSolver(shapes, dt=dts, P=Ps, prec=prec, **kw)
+
+    b = make(args.prec)
+    u0 = b.pack([p.u0 for p in probs])
+
+    def timed(bs, nsteps, warm):
+        up = u0.clone()
+        uc = bs.start(up)
+        bs.step(up, uc, warm)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        l0 = bs.launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bs.step(up, uc, nsteps)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = bs.launches - l0
+        bs.set_pass_timing(True)
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record()
+        bs.step(up, uc, nsteps)
+        e3.record()
+        torch.cuda.synchronize()
+        passes = bs.pass_times()
+        bs.set_pass_timing(False)
+        return ms, launches, passes, e2.elapsed_time(e3), uc
+
+    try:
+        bus = torch.cuda.get_device_properties(dev_index).pci_bus_id
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus).start()
+    ms, launches, passes, ms_b, _ = timed(b, args.steps, args.warmup)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ms)
+    value = world * npts * args.steps / (ms * 1e-3)
+    peak, peak_kind = read_peak()
+    dom_axis = max(passes, key=lambda a: passes[a][0])
+    dom_ms = passes[dom_axis][0] / passes[dom_axis][1]
+    achieved = bpp_tot[dom_axis] / (dom_ms * 1e-3) / 1e9
+    kernel_name = {0: "k_batch_x (x pass: Horner + level update; rows <= 512 and longer rows, two launches)",
+                   1: "k_batch_y (y pass: powers of D_y)"}[dom_axis]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": read_traffic(dom_axis, spec["name"], args.prec, "batch"),
+                "kernel": kernel_name, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                "alg_bytes_per_launch": bpp_tot[dom_axis],
+                "passes": {f"axis{a}": {"ms_per_launch": passes[a][0] / passes[a][1],
+                                         "alg_GBps": bpp_tot[a] / (passes[a][0] / passes[a][1] * 1e-3) / 1e9,
+                                         "alg_bytes": bpp_tot[a]} for a in passes},
+                "step_alg_GBps": sum(bpp_tot.values()) * args.steps / (ms * 1e-3) / 1e9,
+                "kernel_timing": (f"per-pass CUDA events over a second region of {args.steps} steps "
+                                  f"(graphs off, {ms_b / args.steps:.4f} ms/step)")}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": spec["name"], "problems": len(shapes), "points_per_step": npts,
+                       "n_range": [min(n for n, _ in shapes), max(n for n, _ in shapes)],
+                       "P_counts": {str(k): Ps.count(k) for k in (1, 2, 3)}, "prec": args.prec,
+                       "levels": "f32 hi+lo pairs" if args.prec == "mixed" else "f64",
+                       "l2": "no flush: per-step working set (3 levels + intermediate fields) exceeds the 129 MB L2",
+                       "parallelism": f"{world} rank(s), each its own 512 problems"},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+
+    if rank == 0 and not args.no_fp64_compare and args.prec == "mixed":
+        b64 = make("fp64")
+        k64 = max(3, args.steps // 8)
+        ms64, _, p64, _, _ = timed(b64, k64, 3)
+        line["fp64_path"] = {"value": npts * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
+                             "passes_ms_per_launch": {f"axis{a}": p64[a][0] / p64[a][1] for a in p64}}
+        b64.close()
+
+    if rank == 0 and not args.no_accuracy and args.prec == "mixed":
+        line["accuracy"] = batch_accuracy(spec, probs, shapes, dts, Ps, make, molt, torch)
+
+    if not args.no_e2e:
+        calls, per_call = 3, max(1, min(spec["steps_in_config"], args.steps))
+        pin_in = torch.empty(npts, dtype=torch.float64, pin_memory=True)
+        pin_out = torch.empty(npts, dtype=torch.float64, pin_memory=True)
+        pin_in.numpy()[...] = np.concatenate([p.u0.reshape(-1) for p in probs])
+        b.solve_host(pin_in.numpy(), per_call, out=pin_out.numpy())
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            b.solve_host(pin_in.numpy(), per_call, out=pin_out.numpy())
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        line["e2e"] = {"value": world * npts * per_call * calls / e2e_s, "unit": METRIC,
+                       "h2d_bytes_per_step": 8 * npts, "d2h_bytes_per_step": 8 * npts,
+                       "step": f"one mol_batch_solve_host call: copy u0 in, start + {per_call - 1} steps, copy u out",
+                       "time_steps_per_step": per_call}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, used, ssteps, sdt, cores = batch_oracle_rate(probs, dts, budget_s=20.0)
+        line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
+                                "sample": f"{ssteps} oracle steps on each of the first {used} problems "
+                                          f"(seeded order; {sdt:.1f} s)"}
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def batch_accuracy(spec, probs, shapes, dts, Ps, make, molt, torch, sample: int = 6):
+    """Mixed vs FP64 on the batch after the workload's step count: rel L2 of
+    mixed against FP64 for every problem, and on `sample` seeded problems the
+    error of each path against FP64 on the grid refined 2x in h and dt."""
+    nsteps = spec["steps_in_config"]
+    res = {}
+    for prec in ("mixed", "fp64"):
+        bs = make(prec)
+        u = bs.solve_host(np.concatenate([p.u0.reshape(-1) for p in probs]), nsteps)
+        res[prec] = [u[o:o + n * n].reshape(n, n) for o, (n, _) in zip(bs.offsets, shapes)]
+        bs.close()
+    rel = [float(np.linalg.norm(m - d) / max(np.linalg.norm(d), 1e-300)) for m, d in zip(res["mixed"], res["fp64"])]
+    rng = np.random.default_rng(17)
+    picks = sorted(int(i) for i in rng.choice(len(probs), size=sample, replace=False))
+    E = []
+    for i in picks:
+        n = shapes[i][0]
+        nf = 2 * n - 1
+        sf = molt.Solver((nf, nf), dt=dts[i] / 2, P=Ps[i], bc="dirichlet", prec="fp64")
+        # the same Gaussian on the refined grid: evaluate the generator's recipe at the fine nodes
+        uf = workloads.gaussian_2d(nf, seed=spec["seed"] * 7919 + i)
+        up = torch.from_numpy(uf).cuda()
+        uc = sf.start(up)
+        sf.step(up, uc, 2 * nsteps - 1)
+        ref = uc.cpu().numpy()[::2, ::2]
+        sf.close()
+        nr = np.linalg.norm(ref)
+        e_m = float(np.linalg.norm(res["mixed"][i] - ref) / nr)
+        e_d = float(np.linalg.norm(res["fp64"][i] - ref) / nr)
+        E.append({"problem": i, "n": n, "P": Ps[i], "E_mixed": e_m, "E_fp64": e_d,
+                  "equal_l2": bool(abs(e_m - e_d) <= 0.05 * e_d)})
+    return {"steps": nsteps, "rel_l2_mixed_vs_fp64_max": max(rel), "rel_l2_mixed_vs_fp64_median": float(np.median(rel)),
+            "sampled": E, "equal_l2_all_sampled": all(e["equal_l2"] for e in E),
+            "reference": "fp64 single-problem solver on (2n-1)^2, dt/2, 2x steps, shared nodes"}
 
 
 def accuracy_check(spec, make, molt, torch):

@@ -210,6 +210,10 @@ mol_status mol_batch_start(mol_batch b, const double *u0, double *u1, void *stre
 /* Advance every problem by nsteps in place; as mol_step. */
 mol_status mol_batch_step(mol_batch b, double *u_prev, double *u_cur, int64_t nsteps, void *stream);
 
+/* End-to-end from HOST memory, as mol_solve_host: packed u0 (host float64)
+ * in, u^{nsteps} of every problem out (host float64, packed).  Synchronous. */
+mol_status mol_batch_solve_host(mol_batch b, const double *u0, double *u_out, int64_t nsteps, void *stream);
+
 mol_status mol_batch_sync(mol_batch b, void *stream);
 int64_t mol_batch_launch_count(mol_batch b);
 

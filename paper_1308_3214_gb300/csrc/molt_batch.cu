@@ -36,6 +36,7 @@ struct mol_batch_ctx {
     double *dp64 = nullptr;
     float *dp32 = nullptr;
     BLevel lev[3];
+    double *io[2] = {nullptr, nullptr};  // packed float64 fields of mol_batch_solve_host
     void *inter[BMAXP] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int xW[2] = {8, 8}, xgrid[2] = {1, 1}, ygrid = 1, nbuf = 1, cgrid = 1;
     size_t xsmem[2] = {0, 0}, ysmem = 0;
@@ -537,6 +538,24 @@ mol_status mol_batch_step(mol_batch b, double *u_prev, double *u_cur, int64_t ns
     const int k = (int)(nsteps % 3);
     if ((st = unpack(b, b->lev[k], u_prev, s)) != MOL_OK) return st;
     return unpack(b, b->lev[(k + 1) % 3], u_cur, s);
+}
+
+mol_status mol_batch_solve_host(mol_batch b, const double *u0, double *u_out, int64_t nsteps, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (!u0 || !u_out) return bfail(b, MOL_EINVAL, "NULL host buffer");
+    if (nsteps < 1) return bfail(b, MOL_EINVAL, "nsteps must be >= 1");
+    mol_status st;
+    const size_t bytes = sizeof(double) * (size_t)b->uoff[b->nprob];
+    for (int k = 0; k < 2; ++k)
+        if (!b->io[k] && (st = balloc(b, (void **)&b->io[k], bytes)) != MOL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    BCK(cudaMemcpyAsync(b->io[0], u0, bytes, cudaMemcpyHostToDevice, s), "host to device copy");
+    if ((st = mol_batch_start(b, b->io[0], b->io[1], stream)) != MOL_OK) return st;
+    if ((st = mol_batch_step(b, b->io[0], b->io[1], nsteps - 1, stream)) != MOL_OK) return st;
+    BCK(cudaMemcpyAsync(u_out, b->io[1], bytes, cudaMemcpyDeviceToHost, s), "device to host copy");
+    BCK(cudaStreamSynchronize(s), "solve");
+    return MOL_OK;
 }
 
 mol_status mol_batch_sync(mol_batch b, void *stream)

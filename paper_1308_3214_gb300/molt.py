@@ -30,7 +30,7 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_max_line", "mol_get_params", "mol_apply_D", "mol_apply_F", "mol_start", "mol_step",
            "mol_solve_host", "mol_sync", "mol_launch_count", "mol_set_pass_timing", "mol_pass_times",
            "mol_apply_F_noalloc", "mol_batch_create", "mol_batch_destroy", "mol_batch_last_error",
-           "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_sync",
+           "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
            "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times"]
 
 
@@ -96,6 +96,7 @@ def load_library(path: Path | None = None):
     lib.mol_batch_apply_F.argtypes = [vp, vp, vp, vp]
     lib.mol_batch_start.argtypes = [vp, vp, vp, vp]
     lib.mol_batch_step.argtypes = [vp, vp, vp, i64, vp]
+    lib.mol_batch_solve_host.argtypes = [vp, dp, dp, i64, vp]
     lib.mol_batch_sync.argtypes = [vp, vp]
     lib.mol_batch_launch_count.argtypes = [vp]
     lib.mol_batch_launch_count.restype = i64
@@ -373,6 +374,17 @@ class BatchSolver:
         self._check(self.lib.mol_batch_step(self.h, self._flat(u_prev, "u_prev"), self._flat(u_cur, "u_cur"),
                                             int(nsteps), ctypes.c_void_p(_stream_ptr(stream))))
         return u_prev, u_cur
+
+    def solve_host(self, u0: np.ndarray, nsteps: int, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """Packed host u0 -> packed host u^{nsteps} (zero initial velocity)."""
+        u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
+        if u0.size != self.size:
+            raise ValueError(f"u0 must hold {self.size} values")
+        out = np.empty_like(u0) if out is None else out
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.mol_batch_solve_host(self.h, u0.ctypes.data_as(dp), out.ctypes.data_as(dp), int(nsteps),
+                                                  ctypes.c_void_p(_stream_ptr(stream))))
+        return out
 
     def sync(self, stream=None):
         self._check(self.lib.mol_batch_sync(self.h, ctypes.c_void_p(_stream_ptr(stream))))
