@@ -62,6 +62,12 @@ def _load():
         lib.orc_step.argtypes = [dp, dp, dp, I, lp, dp, I, I, I, D]
         lib.orc_start.argtypes = [dp, dp, I, lp, dp, I, I, I, D]
         lib.orc_run.argtypes = [dp, dp, L, I, lp, dp, I, I, I, D]
+        lib.orc_linv_line_T.argtypes = [dp, L, dp, L, L, D, I, I]
+        lib.orc_linv_axis_T.argtypes = [dp, dp, I, lp, I, D, I, I]
+        lib.orc_D_axis_T.argtypes = [dp, dp, I, lp, I, D, I, I]
+        lib.orc_FT.argtypes = [dp, dp, I, lp, dp, I, I, I, D]
+        lib.orc_traces.argtypes = [dp, L, I, lp, dp, I, lp, dp, I, I, I, D]
+        lib.orc_adjoint.argtypes = [dp, L, I, lp, dp, I, lp, dp, I, I, I, D]
         lib.orc_num_threads.restype = I
         _lib = lib
     return _lib
@@ -130,6 +136,65 @@ def D_axis(v, axis: int, nu: float, bc="dirichlet", quad: int = 2, power: int = 
         out = np.empty_like(src)
         _load().orc_D_axis(_dp(src), _dp(out), nd, shp, int(axis), float(nu), int(quad), _bc(bc))
     return out
+
+
+def linv_line_T(w, nu: float, bc="dirichlet", quad: int = 2) -> np.ndarray:
+    """(L^{-1})^T on one line: the program of linv_line transposed."""
+    w = _f64(w)
+    v = np.empty_like(w)
+    _load().orc_linv_line_T(_dp(w), 1, _dp(v), 1, w.size, float(nu), int(quad), _bc(bc))
+    return v
+
+
+def D_axis_T(v, axis: int, nu: float, bc="dirichlet", quad: int = 2, power: int = 1) -> np.ndarray:
+    """(D_gamma^T)^power v, D_gamma^T = 1 - (L_gamma^{-1})^T."""
+    out = _f64(v)
+    nd, shp = _shape(out)
+    for _ in range(power):
+        src = out
+        out = np.empty_like(src)
+        _load().orc_D_axis_T(_dp(src), _dp(out), nd, shp, int(axis), float(nu), int(quad), _bc(bc))
+    return out
+
+
+def FT(u, nu, P: int, beta: float, bc="dirichlet", quad: int = 2) -> np.ndarray:
+    """F^T: the transpose of F (every per-axis operator transposed)."""
+    u = _f64(u)
+    out = np.empty_like(u)
+    nd, shp = _shape(u)
+    _load().orc_FT(_dp(u), _dp(out), nd, shp, _dp(_nu_arr(nu, nd)), int(quad), _bc(bc), int(P), float(beta))
+    return out
+
+
+def _rec_arr(rec, size):
+    rec = np.ascontiguousarray(rec, dtype=np.int64).reshape(-1)
+    if rec.size and (rec.min() < 0 or rec.max() >= size):
+        raise ValueError("receiver index out of range")
+    return rec
+
+
+def traces(u0, nsteps: int, rec, nu, P: int, beta: float, bc="dirichlet", quad: int = 2) -> np.ndarray:
+    """t[n-1, r] = u^n at flat index rec[r] (C order), n = 1..nsteps, from
+    u^1 = u^0 + F[u^0]/2 and the time steps."""
+    u0 = _f64(u0)
+    nd, shp = _shape(u0)
+    rec = _rec_arr(rec, u0.size)
+    out = np.zeros((int(nsteps), rec.size))
+    _load().orc_traces(_dp(u0), int(nsteps), rec.size, rec.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                       _dp(out), nd, shp, _dp(_nu_arr(nu, nd)), int(quad), _bc(bc), int(P), float(beta))
+    return out
+
+
+def adjoint(tgrad, shape, rec, nu, P: int, beta: float, bc="dirichlet", quad: int = 2) -> np.ndarray:
+    """dJ/du^0 for a loss J of the traces, given tgrad[n-1, r] = dJ/dt^n_r."""
+    tgrad = _f64(np.asarray(tgrad, dtype=np.float64))
+    nsteps = tgrad.shape[0]
+    grad = np.zeros(tuple(shape))
+    nd, shp = _shape(grad)
+    rec = _rec_arr(rec, grad.size)
+    _load().orc_adjoint(_dp(tgrad), int(nsteps), rec.size, rec.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                        _dp(grad), nd, shp, _dp(_nu_arr(nu, nd)), int(quad), _bc(bc), int(P), float(beta))
+    return grad
 
 
 def Ap(P: int, beta: float) -> np.ndarray:

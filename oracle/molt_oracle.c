@@ -173,6 +173,95 @@ void orc_linv_line(const double *v, long sv, double *w, long sw, long n,
 }
 
 /* ------------------------------------------------------------------------ */
+/* (L^{-1})^T on one line: the statements of orc_linv_line transposed and     */
+/* executed in reverse order (each read x = v_j becomes vbar_j += xbar, each  */
+/* recurrence runs backwards).  Used by the adjoint of the time stepping; the */
+/* paper itself has no adjoint.                                               */
+/* ------------------------------------------------------------------------ */
+static void vadd(double *v, long sv, long n, int bc, long j, double x)
+{
+    if (bc == ORC_PERIODIC) { j %= n; if (j < 0) j += n; }
+    v[j * sv] += x;
+}
+
+static void sdiff_T(double *v, long sv, long n, int bc, long c, double x)
+{
+    vadd(v, sv, n, bc, c + 1, x);
+    vadd(v, sv, n, bc, c, -2.0 * x);
+    vadd(v, sv, n, bc, c - 1, x);
+}
+
+void orc_linv_line_T(const double *w, long sw, double *v, long sv, long n,
+                     double nu, int quad, int bc)
+{
+    double c4[4];
+    orc_weights(nu, quad, c4);
+    double d = c4[0], W0 = c4[1], W1 = c4[2], R = c4[3];
+    long N = (bc == ORC_PERIODIC) ? n : n - 1;
+    int use_quad = (R != 0.0) && n >= 3;
+    double *gJL = calloc((size_t)(N + 1), sizeof(double));
+    double *gJR = calloc((size_t)(N + 1), sizeof(double));
+    double *gIL = calloc((size_t)(N + 1), sizeof(double));
+    double *gIR = calloc((size_t)(N + 1), sizeof(double));
+    for (long j = 0; j < n; ++j) v[j * sv] = 0.0;
+
+    /* w_j = IL_j + IR_j + A d^j + B d^{N-j} */
+    double gA = 0.0, gB = 0.0;
+    for (long j = 0; j < n; ++j) {
+        double x = w[j * sw];
+        gIL[j] += x;
+        gIR[j] += x;
+        gA += x * pow(d, (double)j);
+        gB += x * pow(d, (double)(N - j));
+    }
+    double mu = pow(d, (double)N);
+    if (bc == ORC_PERIODIC) {
+        gIL[N] += gA / (1.0 - mu);              /* A = IL_N / (1 - mu) */
+        gIR[0] += gB / (1.0 - mu);              /* B = IR_0 / (1 - mu) */
+    } else {
+        double gr0 = (gA - mu * gB) / (1.0 - mu * mu);
+        double gr1 = (gB - mu * gA) / (1.0 - mu * mu);
+        vadd(v, sv, n, bc, 0, gr0);             /* r0 = v_0 - IR_0 */
+        gIR[0] -= gr0;
+        vadd(v, sv, n, bc, N, gr1);             /* r1 = v_N - IL_N */
+        gIL[N] -= gr1;
+    }
+    /* IR_j = d IR_{j+1} + JR_j, computed for j = N-1 down to 0 */
+    for (long j = 0; j < N; ++j) {
+        gJR[j] += gIR[j];
+        gIR[j + 1] += d * gIR[j];
+    }
+    /* IL_j = d IL_{j-1} + JL_j, computed for j = 1 up to N */
+    for (long j = N; j >= 1; --j) {
+        gJL[j] += gIL[j];
+        gIL[j - 1] += d * gIL[j];
+    }
+    /* JR_j = (W0 v_j + W1 v_{j+1} + R S)/2 */
+    for (long j = 0; j < N; ++j) {
+        double g = 0.5 * gJR[j];
+        vadd(v, sv, n, bc, j, W0 * g);
+        vadd(v, sv, n, bc, j + 1, W1 * g);
+        if (use_quad) {
+            long c = j;
+            if (bc == ORC_DIRICHLET && c - 1 < 0) c = j + 1;
+            sdiff_T(v, sv, n, bc, c, R * g);
+        }
+    }
+    /* JL_j = (W0 v_j + W1 v_{j-1} + R S)/2 */
+    for (long j = 1; j <= N; ++j) {
+        double g = 0.5 * gJL[j];
+        vadd(v, sv, n, bc, j, W0 * g);
+        vadd(v, sv, n, bc, j - 1, W1 * g);
+        if (use_quad) {
+            long c = j;
+            if (bc == ORC_DIRICHLET && c + 1 > n - 1) c = j - 1;
+            sdiff_T(v, sv, n, bc, c, R * g);
+        }
+    }
+    free(gJL); free(gJR); free(gIL); free(gIR);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Axis operators on a whole field: L_gamma^{-1} and D_gamma (eq. LD_gam)     */
 /* ------------------------------------------------------------------------ */
 static long total_size(int ndim, const long *shape)
@@ -205,6 +294,33 @@ void orc_D_axis(const double *v, double *out, int ndim, const long *shape,
     long total = total_size(ndim, shape);
     double *w = malloc(sizeof(double) * (size_t)total);
     orc_linv_axis(v, w, ndim, shape, axis, nu, quad, bc);
+    for (long i = 0; i < total; ++i) out[i] = v[i] - w[i];
+    free(w);
+}
+
+void orc_linv_axis_T(const double *v, double *w, int ndim, const long *shape,
+                     int axis, double nu, int quad, int bc)
+{
+    long n = shape[axis];
+    long stride = 1;
+    for (int a = 0; a < axis; ++a) stride *= shape[a];
+    long total = total_size(ndim, shape);
+    long nlines = total / n;
+#pragma omp parallel for schedule(static)
+    for (long line = 0; line < nlines; ++line) {
+        long inner = line % stride, outer = line / stride;
+        long base = inner + outer * stride * n;
+        orc_linv_line_T(v + base, stride, w + base, stride, n, nu, quad, bc);
+    }
+}
+
+/* D^T = 1 - (L^{-1})^T along one axis */
+void orc_D_axis_T(const double *v, double *out, int ndim, const long *shape,
+                  int axis, double nu, int quad, int bc)
+{
+    long total = total_size(ndim, shape);
+    double *w = malloc(sizeof(double) * (size_t)total);
+    orc_linv_axis_T(v, w, ndim, shape, axis, nu, quad, bc);
     for (long i = 0; i < total; ++i) out[i] = v[i] - w[i];
     free(w);
 }
@@ -280,16 +396,19 @@ double orc_beta_max(int P)
 typedef struct {
     int ndim; const long *shape; const double *nu; int quad; int bc; long total;
     long napplied;            /* number of applications of C or D (Table 3) */
+    int transpose;            /* 1: every per-axis operator replaced by its transpose */
 } orc_ctx;
 
 static void Linv(orc_ctx *c, const double *v, double *w, int axis)
 {
-    orc_linv_axis(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
+    if (c->transpose) orc_linv_axis_T(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
+    else orc_linv_axis(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
 }
 
 static void Dgam(orc_ctx *c, const double *v, double *w, int axis)
 {
-    orc_D_axis(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
+    if (c->transpose) orc_D_axis_T(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
+    else orc_D_axis(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
 }
 
 /* C[v]: 1D: D_x v;  2D: L_y^{-1} D_x v + L_x^{-1} D_y v (eq. C_def_ADI);
@@ -351,10 +470,10 @@ static void applyD(orc_ctx *c, const double *v, double *out)
  * p-1 by v_p = D[v_{p-1}] and v_k = C[v_k] (k < p); stage p costs p
  * applications.  *nops (if given) receives the number of applications.
  */
-void orc_F(const double *u, double *F, int ndim, const long *shape,
-           const double *nu, int quad, int bc, int P, double beta, long *nops)
+static void F_impl(const double *u, double *F, int ndim, const long *shape, const double *nu, int quad,
+                   int bc, int P, double beta, long *nops, int transpose)
 {
-    orc_ctx c = {ndim, shape, nu, quad, bc, total_size(ndim, shape), 0};
+    orc_ctx c = {ndim, shape, nu, quad, bc, total_size(ndim, shape), 0, transpose};
     long T = c.total;
     double **v = calloc((size_t)P + 1, sizeof(double *));
     for (int k = 1; k <= P; ++k) v[k] = malloc(sizeof(double) * (size_t)T);
@@ -378,6 +497,22 @@ void orc_F(const double *u, double *F, int ndim, const long *shape,
     if (nops) *nops = c.napplied;
     for (int k = 1; k <= P; ++k) free(v[k]);
     free(v); free(tmp);
+}
+
+void orc_F(const double *u, double *F, int ndim, const long *shape,
+           const double *nu, int quad, int bc, int P, double beta, long *nops)
+{
+    F_impl(u, F, ndim, shape, nu, quad, bc, P, beta, nops, 0);
+}
+
+/* F^T: every per-axis operator transposed.  The per-axis operators act on
+ * different indices and commute, so (C^m D^{p-m})^T = (C^T)^m (D^T)^{p-m}
+ * with C^T, D^T the expressions of C, D in the transposed per-axis
+ * operators: the same sum with the same weights. */
+void orc_FT(const double *u, double *F, int ndim, const long *shape,
+            const double *nu, int quad, int bc, int P, double beta)
+{
+    F_impl(u, F, ndim, shape, nu, quad, bc, P, beta, NULL, 1);
 }
 
 /* u^{n+1} = 2 u^n - u^{n-1} + F[u^n]   (eq. update_P / Full_2D) */
@@ -415,6 +550,55 @@ void orc_run(double *uprev, double *ucur, long nsteps, int ndim, const long *sha
         memcpy(ucur, un, sizeof(double) * (size_t)T);
     }
     free(un);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Receiver traces and the adjoint of the time stepping (no counterpart in    */
+/* the paper).  The forward map u^0 -> (u^1, ..., u^N) is                     */
+/*   u^1 = u^0 + F u^0 / 2,  u^{n+1} = 2 u^n - u^{n-1} + F u^n,               */
+/* and the traces are t^n_r = u^n[rec_r].  For a loss J of the traces with    */
+/* g^n = R^T dJ/dt^n (scatter of the trace gradients to the receiver nodes),   */
+/* the adjoint states mu^n = dJ/du^n satisfy, from mu^{N+1} = 0, mu^N = g^N,  */
+/*   mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n,   n = N-1 .. 1,        */
+/* and dJ/du^0 = mu^1 + F^T mu^1 / 2 - mu^2.                                  */
+/* ------------------------------------------------------------------------ */
+void orc_traces(const double *u0, long nsteps, int nrec, const long *rec, double *traces,
+                int ndim, const long *shape, const double *nu, int quad, int bc, int P, double beta)
+{
+    long T = total_size(ndim, shape);
+    double *a = malloc(sizeof(double) * (size_t)T);
+    double *b = malloc(sizeof(double) * (size_t)T);
+    double *c = malloc(sizeof(double) * (size_t)T);
+    memcpy(a, u0, sizeof(double) * (size_t)T);
+    orc_start(u0, b, ndim, shape, nu, quad, bc, P, beta);
+    for (long n = 1; n <= nsteps; ++n) {
+        for (int r = 0; r < nrec; ++r) traces[(n - 1) * nrec + r] = b[rec[r]];
+        if (n == nsteps) break;
+        orc_step(a, b, c, ndim, shape, nu, quad, bc, P, beta);
+        double *t = a; a = b; b = c; c = t;
+    }
+    free(a); free(b); free(c);
+}
+
+void orc_adjoint(const double *tgrad, long nsteps, int nrec, const long *rec, double *grad,
+                 int ndim, const long *shape, const double *nu, int quad, int bc, int P, double beta)
+{
+    long T = total_size(ndim, shape);
+    double *m2 = calloc((size_t)T, sizeof(double));   /* mu^{n+2} */
+    double *m1 = calloc((size_t)T, sizeof(double));   /* mu^{n+1} */
+    double *m0 = malloc(sizeof(double) * (size_t)T);  /* mu^n */
+    double *F = malloc(sizeof(double) * (size_t)T);
+    for (int r = 0; r < nrec; ++r) m1[rec[r]] += tgrad[(nsteps - 1) * nrec + r];   /* mu^N = g^N */
+    for (long n = nsteps - 1; n >= 1; --n) {
+        orc_FT(m1, F, ndim, shape, nu, quad, bc, P, beta);
+        for (long i = 0; i < T; ++i) m0[i] = 2.0 * m1[i] - m2[i] + F[i];
+        for (int r = 0; r < nrec; ++r) m0[rec[r]] += tgrad[(n - 1) * nrec + r];
+        double *t = m2; m2 = m1; m1 = m0; m0 = t;
+    }
+    /* now m1 = mu^1, m2 = mu^2 (zero when nsteps == 1) */
+    orc_FT(m1, F, ndim, shape, nu, quad, bc, P, beta);
+    for (long i = 0; i < T; ++i) grad[i] = m1[i] + 0.5 * F[i] - m2[i];
+    free(m0); free(m1); free(m2); free(F);
 }
 
 /* Threads OpenMP would use (1 when built without OpenMP). */
