@@ -210,6 +210,32 @@ mol_status mol_batch_start(mol_batch b, const double *u0, double *u1, void *stre
 /* Advance every problem by nsteps in place; as mol_step. */
 mol_status mol_batch_step(mol_batch b, double *u_prev, double *u_cur, int64_t nsteps, void *stream);
 
+/* ---- adjoint (the paper has none): receivers and the gradient of a loss
+ * of the receiver traces with respect to the initial field.
+ *
+ * Receivers are HOST arrays of packed-field indices (problem offset + y nx
+ * + x).  The forward map is u^1 = u^0 + F u^0 / 2, u^{n+1} = 2 u^n - u^{n-1}
+ * + F u^n; the traces are t[(n-1) nrec + r] = u^n[rec_r], n = 1..nsteps.
+ * For a loss J(t) with tgrad[(n-1) nrec + r] = dJ/dt^n_r, the adjoint states
+ * mu^n = dJ/du^n satisfy mu^N = g^N, mu^n = 2 mu^{n+1} - mu^{n+2} + F^T
+ * mu^{n+1} + g^n (g^n = the trace gradients of step n added at the
+ * receivers), and dJ/du^0 = mu^1 + F^T mu^1 / 2 - mu^2.  The scheme is
+ * linear with fixed coefficients, so the adjoint needs no stored forward
+ * level: only tgrad.  F^T = sum f_ij (D_x^T)^i (D_y^T)^j with the transposed
+ * per-axis operators. */
+
+/* out = F^T w for every problem (packed fields, may not overlap). */
+mol_status mol_batch_apply_FT(mol_batch b, const double *w, double *out, void *stream);
+
+/* traces (device, nsteps * nrec float64) of the forward run from u0 (packed,
+ * device) with zero initial velocity. */
+mol_status mol_batch_traces(mol_batch b, const double *u0, int nrec, const int64_t *rec, int64_t nsteps,
+                            double *traces, void *stream);
+
+/* grad (device, packed) = dJ/du^0 given tgrad (device, nsteps * nrec). */
+mol_status mol_batch_adjoint(mol_batch b, int nrec, const int64_t *rec, int64_t nsteps, const double *tgrad,
+                             double *grad, void *stream);
+
 /* End-to-end from HOST memory, as mol_solve_host: packed u0 (host float64)
  * in, u^{nsteps} of every problem out (host float64, packed).  Synchronous. */
 mol_status mol_batch_solve_host(mol_batch b, const double *u0, double *u_out, int64_t nsteps, void *stream);

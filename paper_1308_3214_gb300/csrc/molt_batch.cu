@@ -37,6 +37,8 @@ struct mol_batch_ctx {
     float *dp32 = nullptr;
     BLevel lev[3];
     double *io[2] = {nullptr, nullptr};  // packed float64 fields of mol_batch_solve_host
+    long long *irec = nullptr;           // receivers in the internal layout
+    int nrec = 0, irec_cap = 0;
     void *inter[BMAXP] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int xW[2] = {8, 8}, xgrid[2] = {1, 1}, ygrid = 1, nbuf = 1, cgrid = 1;
     size_t xsmem[2] = {0, 0}, ysmem = 0;
@@ -124,29 +126,45 @@ cudaEvent_t btake_event(mol_batch_ctx *b)
     return e;
 }
 
-template <class T>
+template <class T, bool ADJ>
 cudaError_t launch_pass_y(const mol_batch_ctx *b, const BatchPass &bp, cudaStream_t s)
 {
-    k_batch_y<T><<<b->ygrid, 32 * kBatchYWarps, b->ysmem, s>>>(bp);
+    k_batch_y<T, ADJ><<<b->ygrid, 32 * kBatchYWarps, b->ysmem, s>>>(bp);
     return cudaGetLastError();
 }
-template <class T>
+template <class T, bool ADJ>
 cudaError_t launch_pass_x(const mol_batch_ctx *b, BatchPass bp, cudaStream_t s)
 {
     // rows of short lines, then rows of long lines (each a persistent launch)
     bp.row_begin = 0;
     bp.nitems = (int)b->rows_small;
-    if (bp.nitems > 0) k_batch_x<T, false><<<b->xgrid[0], 32 * b->xW[0], b->xsmem[0], s>>>(bp, b->nbuf);
+    if (bp.nitems > 0) k_batch_x<T, false, ADJ><<<b->xgrid[0], 32 * b->xW[0], b->xsmem[0], s>>>(bp, b->nbuf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     bp.row_begin = (int)b->rows_small;
     bp.nitems = (int)b->nrows;
-    if (bp.nitems > bp.row_begin) k_batch_x<T, true><<<b->xgrid[1], 32 * b->xW[1], b->xsmem[1], s>>>(bp, b->nbuf);
+    if (bp.nitems > bp.row_begin) k_batch_x<T, true, ADJ><<<b->xgrid[1], 32 * b->xW[1], b->xsmem[1], s>>>(bp, b->nbuf);
     return cudaGetLastError();
 }
 
-// one pass, timed when pass timing is on (axis 0 = x, 1 = y)
-mol_status run_pass(mol_batch_ctx *b, int axis, const BatchPass &bp, cudaStream_t s)
+template <class T>
+cudaError_t set_kernel_smem(const mol_batch_ctx *b)
+{
+    cudaError_t e = cudaSuccess;
+    const void *xk[2][2] = {{(const void *)k_batch_x<T, false, false>, (const void *)k_batch_x<T, true, false>},
+                            {(const void *)k_batch_x<T, false, true>, (const void *)k_batch_x<T, true, true>}};
+    const void *yk[2] = {(const void *)k_batch_y<T, false>, (const void *)k_batch_y<T, true>};
+    for (int adj = 0; adj < 2 && e == cudaSuccess; ++adj) {
+        for (int L = 0; L < 2 && e == cudaSuccess; ++L)
+            e = cudaFuncSetAttribute(xk[adj][L], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[L]);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(yk[adj], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->ysmem);
+    }
+    return e;
+}
+
+// one pass, timed when pass timing is on (axis 0 = x, 1 = y); adj: the
+// transposed operators
+mol_status run_pass(mol_batch_ctx *b, int axis, const BatchPass &bp, cudaStream_t s, bool adj = false)
 {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (b->timing) {
@@ -156,8 +174,13 @@ mol_status run_pass(mol_batch_ctx *b, int axis, const BatchPass &bp, cudaStream_
         BCK(cudaEventRecord(e0, s), "event record");
     }
     cudaError_t e;
-    if (axis == 1) e = b->tbytes == 4 ? launch_pass_y<float>(b, bp, s) : launch_pass_y<double>(b, bp, s);
-    else e = b->tbytes == 4 ? launch_pass_x<float>(b, bp, s) : launch_pass_x<double>(b, bp, s);
+    if (axis == 1) {
+        if (adj) e = b->tbytes == 4 ? launch_pass_y<float, true>(b, bp, s) : launch_pass_y<double, true>(b, bp, s);
+        else e = b->tbytes == 4 ? launch_pass_y<float, false>(b, bp, s) : launch_pass_y<double, false>(b, bp, s);
+    } else {
+        if (adj) e = b->tbytes == 4 ? launch_pass_x<float, true>(b, bp, s) : launch_pass_x<double, true>(b, bp, s);
+        else e = b->tbytes == 4 ? launch_pass_x<float, false>(b, bp, s) : launch_pass_x<double, false>(b, bp, s);
+    }
     if (e != cudaSuccess) return bcuda(b, e, "batched pass launch");
     b->launches += (axis == 1) ? 1 : b->x_launches();
     if (b->timing) {
@@ -167,9 +190,9 @@ mol_status run_pass(mol_batch_ctx *b, int axis, const BatchPass &bp, cudaStream_
     return MOL_OK;
 }
 
-// un = ea u + eb up + ec F[u] for every problem: y pass, then x pass
+// un = ea u + eb up + ec F[u] (adj: F^T[u]) for every problem: y pass, then x pass
 mol_status run_update(mol_batch_ctx *b, const BLevel &u, const BLevel &up, const BLevel &un, double ea, double eb,
-                      double ec, cudaStream_t s)
+                      double ec, cudaStream_t s, bool adj = false)
 {
     BatchPass y{};
     y.probs = b->probs;
@@ -179,7 +202,7 @@ mol_status run_update(mol_batch_ctx *b, const BLevel &u, const BLevel &up, const
     y.pr.u_hi = u.hi;
     y.pr.u_lo = u.lo;
     for (int k = 0; k < b->Pmax; ++k) y.pr.out[k] = b->inter[k];
-    mol_status st = run_pass(b, 1, y, s);
+    mol_status st = run_pass(b, 1, y, s, adj);
     if (st != MOL_OK) return st;
     BatchPass x = y;
     x.nitems = (int)b->nrows;
@@ -191,7 +214,7 @@ mol_status run_update(mol_batch_ctx *b, const BLevel &u, const BLevel &up, const
     x.pr.ea = ea;
     x.pr.eb = eb;
     x.pr.ec = ec;
-    return run_pass(b, 0, x, s);
+    return run_pass(b, 0, x, s, adj);
 }
 
 mol_status pack(mol_batch_ctx *b, const double *x, const BLevel &L, cudaStream_t s)
@@ -217,6 +240,65 @@ mol_status unpack(mol_batch_ctx *b, const BLevel &L, double *x, cudaStream_t s)
                                                         (const double *)L.hi, nullptr, x);
     BCK(cudaGetLastError(), "batched level conversion");
     b->launches++;
+    return MOL_OK;
+}
+
+// receivers: packed user indices (host) -> internal-layout indices (device).
+// Waits for the stream first: kernels of an earlier call may still read them.
+mol_status set_receivers(mol_batch_ctx *b, int nrec, const int64_t *rec, cudaStream_t s)
+{
+    if (nrec < 1 || !rec) return bfail(b, MOL_EINVAL, "need nrec >= 1 receiver indices");
+    std::vector<long long> ir(nrec);
+    const int64_t total = b->uoff[b->nprob];
+    for (int r = 0; r < nrec; ++r) {
+        const int64_t g = rec[r];
+        if (g < 0 || g >= total) return bfail(b, MOL_EINVAL, "receiver index out of range");
+        const int p = (int)(std::upper_bound(b->uoff.begin(), b->uoff.end(), g) - b->uoff.begin()) - 1;
+        const BatchProb &pb = b->hp[p];
+        const int64_t loc = g - b->uoff[p];
+        ir[r] = pb.off + (loc / pb.ax.n) * pb.pitch + loc % pb.ax.n;
+    }
+    BCK(cudaStreamSynchronize(s), "stream synchronize");
+    if (nrec > b->irec_cap) {
+        if (b->irec) {
+            cudaFree(b->irec);
+            b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), (void *)b->irec));
+            b->irec = nullptr;
+            b->irec_cap = 0;
+        }
+        mol_status st = balloc(b, (void **)&b->irec, sizeof(long long) * nrec);
+        if (st != MOL_OK) return st;
+        b->irec_cap = nrec;
+    }
+    BCK(cudaMemcpy(b->irec, ir.data(), sizeof(long long) * nrec, cudaMemcpyHostToDevice), "receiver upload");
+    b->nrec = nrec;
+    return MOL_OK;
+}
+
+mol_status gather(mol_batch_ctx *b, const BLevel &L, double *out, cudaStream_t s)
+{
+    const int blocks = (b->nrec + 255) / 256;
+    if (b->tbytes == 4) k_batch_gather<float><<<blocks, 256, 0, s>>>((const float *)L.hi, (const float *)L.lo, b->irec, b->nrec, out);
+    else k_batch_gather<double><<<blocks, 256, 0, s>>>((const double *)L.hi, nullptr, b->irec, b->nrec, out);
+    BCK(cudaGetLastError(), "receiver gather");
+    b->launches++;
+    return MOL_OK;
+}
+
+mol_status inject(mol_batch_ctx *b, const BLevel &L, const double *vals, cudaStream_t s)
+{
+    if (b->tbytes == 4) k_batch_inject<float><<<1, 32, 0, s>>>((float *)L.hi, (float *)L.lo, b->irec, b->nrec, vals);
+    else k_batch_inject<double><<<1, 32, 0, s>>>((double *)L.hi, nullptr, b->irec, b->nrec, vals);
+    BCK(cudaGetLastError(), "receiver injection");
+    b->launches++;
+    return MOL_OK;
+}
+
+mol_status zero_level(mol_batch_ctx *b, const BLevel &L, cudaStream_t s)
+{
+    const size_t plane = (size_t)b->tbytes * b->total_int;
+    BCK(cudaMemsetAsync(L.hi, 0, plane, s), "level clear");
+    if (L.lo) BCK(cudaMemsetAsync(L.lo, 0, plane, s), "level clear");
     return MOL_OK;
 }
 
@@ -445,19 +527,7 @@ mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, c
         b->ygrid = std::min(b->nitems_y, b->num_sms);
         b->ysmem = batch_y_smem((size_t)b->tbytes);
         b->cgrid = (int)std::min<int64_t>((b->nrows + 7) / 8, 8 * (int64_t)b->num_sms);
-        if (b->tbytes == 4) {
-            e = cudaFuncSetAttribute(k_batch_x<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[0]);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_batch_x<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[1]);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_batch_y<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->ysmem);
-        } else {
-            e = cudaFuncSetAttribute(k_batch_x<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[0]);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_batch_x<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[1]);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_batch_y<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->ysmem);
-        }
+        e = b->tbytes == 4 ? set_kernel_smem<float>(b) : set_kernel_smem<double>(b);
         if (e != cudaSuccess) { st = bcuda(b, e, "kernel attributes"); goto bad; }
     }
     *out = b;
@@ -556,6 +626,64 @@ mol_status mol_batch_solve_host(mol_batch b, const double *u0, double *u_out, in
     BCK(cudaMemcpyAsync(u_out, b->io[1], bytes, cudaMemcpyDeviceToHost, s), "device to host copy");
     BCK(cudaStreamSynchronize(s), "solve");
     return MOL_OK;
+}
+
+mol_status mol_batch_apply_FT(mol_batch b, const double *w, double *out, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_status st;
+    if ((st = bcheck_ptr(b, w, "w")) != MOL_OK || (st = bcheck_ptr(b, out, "out")) != MOL_OK) return st;
+    if (w == out) return bfail(b, MOL_EINVAL, "w and out must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = pack(b, w, b->lev[0], s)) != MOL_OK) return st;
+    if ((st = run_update(b, b->lev[0], b->lev[0], b->lev[1], 0.0, 0.0, 1.0, s, true)) != MOL_OK) return st;
+    return unpack(b, b->lev[1], out, s);
+}
+
+mol_status mol_batch_traces(mol_batch b, const double *u0, int nrec, const int64_t *rec, int64_t nsteps,
+                            double *traces, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (nsteps < 1) return bfail(b, MOL_EINVAL, "nsteps must be >= 1");
+    mol_status st;
+    if ((st = bcheck_ptr(b, u0, "u0")) != MOL_OK || (st = bcheck_ptr(b, traces, "traces")) != MOL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = set_receivers(b, nrec, rec, s)) != MOL_OK) return st;
+    int ip = 0, ic = 1, in = 2;
+    if ((st = pack(b, u0, b->lev[ip], s)) != MOL_OK) return st;
+    if ((st = run_update(b, b->lev[ip], b->lev[ip], b->lev[ic], 1.0, 0.0, 0.5, s)) != MOL_OK) return st;
+    if ((st = gather(b, b->lev[ic], traces, s)) != MOL_OK) return st;
+    for (int64_t n = 1; n < nsteps; ++n) {
+        if ((st = run_update(b, b->lev[ic], b->lev[ip], b->lev[in], 2.0, -1.0, 1.0, s)) != MOL_OK) return st;
+        if ((st = gather(b, b->lev[in], traces + n * nrec, s)) != MOL_OK) return st;
+        const int t = ip; ip = ic; ic = in; in = t;
+    }
+    return MOL_OK;
+}
+
+mol_status mol_batch_adjoint(mol_batch b, int nrec, const int64_t *rec, int64_t nsteps, const double *tgrad,
+                             double *grad, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (nsteps < 1) return bfail(b, MOL_EINVAL, "nsteps must be >= 1");
+    mol_status st;
+    if ((st = bcheck_ptr(b, tgrad, "tgrad")) != MOL_OK || (st = bcheck_ptr(b, grad, "grad")) != MOL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = set_receivers(b, nrec, rec, s)) != MOL_OK) return st;
+    // mu^{N+1} = 0 in ia, mu^N = g^N in ib
+    int ia = 0, ib = 1, ic = 2;
+    if ((st = zero_level(b, b->lev[ia], s)) != MOL_OK) return st;
+    if ((st = zero_level(b, b->lev[ib], s)) != MOL_OK) return st;
+    if ((st = inject(b, b->lev[ib], tgrad + (nsteps - 1) * nrec, s)) != MOL_OK) return st;
+    for (int64_t n = nsteps - 1; n >= 1; --n) {
+        // mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n
+        if ((st = run_update(b, b->lev[ib], b->lev[ia], b->lev[ic], 2.0, -1.0, 1.0, s, true)) != MOL_OK) return st;
+        if ((st = inject(b, b->lev[ic], tgrad + (n - 1) * nrec, s)) != MOL_OK) return st;
+        const int t = ia; ia = ib; ib = ic; ic = t;
+    }
+    // dJ/du^0 = mu^1 + F^T mu^1 / 2 - mu^2
+    if ((st = run_update(b, b->lev[ib], b->lev[ia], b->lev[ic], 1.0, -1.0, 0.5, s, true)) != MOL_OK) return st;
+    return unpack(b, b->lev[ic], grad, s);
 }
 
 mol_status mol_batch_sync(mol_batch b, void *stream)

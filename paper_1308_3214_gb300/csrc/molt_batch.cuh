@@ -84,7 +84,10 @@ __device__ __forceinline__ double2 sdiff2(const double2 &h, double hl, double hr
 // ---------------------------------------------------------------------------
 // x pass: one row
 // ---------------------------------------------------------------------------
-template <class T, int RPT>
+// ADJ: the transposed Horner pass, F^T = sum_t (D_x^T)^t (f_t0 u + sum_k f_tk g_k)
+// with g_k = (D_y^T)^{k+1} u; u itself (not its second difference) is kept
+// in registers.
+template <class T, int RPT, bool ADJ>
 __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams &pr, int row, int lane, T *B)
 {
     using St = ContigStage<T, RPT>;
@@ -161,9 +164,19 @@ __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams 
                 lr = (lane == 31) ? lx[i] : lr;
                 if (v < nvec) {
                     V r;
-                    if constexpr (pair) r = sdiff4(h[i], l[i], hl, ll, hr, lr);
-                    else r = sdiff2(h[i], hl, hr);
-                    if (v == 0) r.x = r.y;             // Dirichlet: the end node takes the interior centre
+                    if constexpr (ADJ) {
+                        r = h[i];
+                        if constexpr (pair) {
+                            T *e = reinterpret_cast<T *>(&r);
+                            const T *lo4 = reinterpret_cast<const T *>(&l[i]);
+#pragma unroll
+                            for (int cc = 0; cc < VN; ++cc) e[cc] += lo4[cc];
+                        }
+                    } else {
+                        if constexpr (pair) r = sdiff4(h[i], l[i], hl, ll, hr, lr);
+                        else r = sdiff2(h[i], hl, hr);
+                        if (v == 0) r.x = r.y;         // Dirichlet: the end node takes the interior centre
+                    }
                     *reinterpret_cast<V *>(R + St::pos(VN * v)) = r;
                 }
             }
@@ -196,7 +209,8 @@ __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams 
             }
         }
         if (t == 0) break;
-        warp_sweep_rreg<T, BC_DIRICHLET, RPT, true>(z, r, (T)pb.cu[t], A, lane);
+        if (ADJ) warp_sweep_T<T, RPT>(z, r, (T)pb.cu[t], A, lane);
+        else warp_sweep_rreg<T, BC_DIRICHLET, RPT, true>(z, r, (T)pb.cu[t], A, lane);
     }
 
     // 4. F -> coalesced side -> next level; padding points get F = 0
@@ -225,7 +239,7 @@ __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams 
 // LARGE: rows of 513..1024 points (32-point segments; the segment, its r and
 // the sweep temporaries need more than 128 registers); else rows of up to
 // 512 points at two CTAs per SM.  Rows [row_begin, nitems) of the list.
-template <class T, bool LARGE>
+template <class T, bool LARGE, bool ADJ>
 __global__ void __launch_bounds__(256, LARGE ? 1 : 2) k_batch_x(BatchPass bp, int nbuf)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -244,12 +258,12 @@ __global__ void __launch_bounds__(256, LARGE ? 1 : 2) k_batch_x(BatchPass bp, in
         const BatchProb &pb = *pbs;
         const int row = r - pb.row0;
         if (LARGE) {
-            batch_row<T, 32>(pb, bp.pr, row, lane, B);
+            batch_row<T, 32, ADJ>(pb, bp.pr, row, lane, B);
         } else {
             switch (pb.rpt_x) {
-            case 4: batch_row<T, 4>(pb, bp.pr, row, lane, B); break;
-            case 8: batch_row<T, 8>(pb, bp.pr, row, lane, B); break;
-            default: batch_row<T, 16>(pb, bp.pr, row, lane, B); break;
+            case 4: batch_row<T, 4, ADJ>(pb, bp.pr, row, lane, B); break;
+            case 8: batch_row<T, 8, ADJ>(pb, bp.pr, row, lane, B); break;
+            default: batch_row<T, 16, ADJ>(pb, bp.pr, row, lane, B); break;
             }
         }
         __syncwarp();
@@ -294,25 +308,14 @@ __device__ __forceinline__ void bcol_r_rag(const ProgParams &pr, int64_t lbase, 
     }
 }
 
-// One application of D on this thread's segment of a Dirichlet column of any
-// length.  rag: the segment holds the last point (0 <= kl < RPT) or the one
-// before it (kl == RPT); YL carries y_{n-1} of every lane from the segment
-// that holds the last point to all segments.
-template <class T, int RPT, int MODE>
-__device__ __forceinline__ void bsweep(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT], T l2, T l1, T r0,
-                                       T r1, int kl, bool rag, T *YL)
+// The solve of the difference form on this thread's segment of a Dirichlet
+// column of any length: z holds q on entry (zero past the line and at the
+// end nodes), e on exit.  rag: the segment holds the last point (0 <= kl <
+// RPT) or the one before it (kl == RPT); YL carries y_{n-1} of every lane
+// from the segment that holds the last point to all segments.
+template <class T, int RPT>
+__device__ __forceinline__ void bsolve(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT], int kl, bool rag, T *YL)
 {
-    const bool left = c.seg == 0;
-    end_ghosts<T, RPT, MODE>(z, left, false, l2, l1, r0, r1);
-    const T c1 = (T)A.c1, c2 = (T)A.c2;
-    auto rz = [&](int) { return (T)0; };
-    if (rag) seg_make_q<T, RPT, MODE, true>(z, l2, l1, r0, r1, rz, (T)0, c1, c2, kl);
-    else seg_make_q<T, RPT, MODE, false>(z, l2, l1, r0, r1, rz, (T)0, c1, c2);
-    end_zero<T, RPT>(z, left, false);
-    if (!c.full) {
-#pragma unroll
-        for (int k = 0; k < RPT; ++k) z[k] = 0;
-    }
     const T d = c.d;
     const T E = seg_fwd_reduce<T, RPT>(z, d);
     T yin, ytot;
@@ -333,7 +336,73 @@ __device__ __forceinline__ void bsweep(const StridedCtx<T> &c, const AxisDev &A,
     if (c.full) seg_add_left<T, RPT>(z, d, Acoef * c.dpg[c.a]);
 }
 
+// One application of D on this thread's segment (MODE as in seg_make_q)
+template <class T, int RPT, int MODE>
+__device__ __forceinline__ void bsweep(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT], T l2, T l1, T r0,
+                                       T r1, int kl, bool rag, T *YL)
+{
+    const bool left = c.seg == 0;
+    end_ghosts<T, RPT, MODE>(z, left, false, l2, l1, r0, r1);
+    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    auto rz = [&](int) { return (T)0; };
+    if (rag) seg_make_q<T, RPT, MODE, true>(z, l2, l1, r0, r1, rz, (T)0, c1, c2, kl);
+    else seg_make_q<T, RPT, MODE, false>(z, l2, l1, r0, r1, rz, (T)0, c1, c2);
+    end_zero<T, RPT>(z, left, false);
+    if (!c.full) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+    }
+    bsolve<T, RPT>(c, A, z, kl, rag, YL);
+}
+
+// zero at the end nodes and past the line (interior rows only)
 template <class T, int RPT>
+__device__ __forceinline__ void interior_only(const StridedCtx<T> &c, T (&z)[RPT], int kl, bool rag)
+{
+    if (c.seg == 0) z[0] = 0;
+    if (rag) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = (k < kl) ? z[k] : (T)0;
+    }
+    if (!c.full) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+    }
+}
+
+// One application of D^T on this thread's segment (see post_T)
+template <class T, int RPT>
+__device__ __forceinline__ void bsweep_T(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT], int kl, bool rag,
+                                         T *YL, int hbuf)
+{
+    interior_only<T, RPT>(c, z, kl, rag);
+    bsolve<T, RPT>(c, A, z, kl, rag, YL);
+    interior_only<T, RPT>(c, z, kl, rag);
+    T l2, l1, r0, r1;
+    strided_halos<T, BC_DIRICHLET, RPT>(c, z, l2, l1, r0, r1, hbuf);
+    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    if (c.seg == 0 || rag) post_T<T, RPT, true>(z, l2, l1, r0, r1, c1, c2, c.a, c.n);
+    else post_T<T, RPT, false>(z, l2, l1, r0, r1, c1, c2, c.a, c.n);
+}
+
+// level value at rows a .. a+RPT-1 of one column (pairs summed in T), rows
+// past the line read as zero
+template <class T, int RPT>
+__device__ __forceinline__ void bcol_level(const ProgParams &pr, int64_t lbase, int64_t st, int a, int n, T (&z)[RPT])
+{
+    const T *H = (const T *)pr.u_hi + lbase;
+    const T *L = (const T *)pr.u_lo + lbase;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int j = a + k;
+        const int64_t o = (int64_t)(j < n ? j : n - 1) * st;
+        T v = H[o];
+        if constexpr (sizeof(T) == 4) v += L[o];
+        z[k] = (j < n) ? v : (T)0;
+    }
+}
+
+template <class T, int RPT, bool ADJ>
 __device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams &pr, int col0, StridedCtx<T> &c, T *YL)
 {
     const AxisDev &A = pb.ay;
@@ -353,6 +422,26 @@ __device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams
     const int64_t st = pb.pitch;
 
     T z[RPT];
+    if (ADJ) {
+        // powers of D_y^T applied to the level
+        if (io) bcol_level<T, RPT>(pr, lbase, st, c.a, n, z);
+        else {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) z[k] = 0;
+        }
+        for (int p = 1; p <= pb.P; ++p) {
+            bsweep_T<T, RPT>(c, A, z, kl, rag, YL, p & 1);
+            if (io) {
+                T *po = reinterpret_cast<T *>(pr.out[p - 1]) + lbase + (int64_t)c.a * st;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    if (k <= kl) *po = z[k];
+                    po += st;
+                }
+            }
+        }
+        return;
+    }
     T rl = 0, rr = 0;
     if (io) {
         if (rag) bcol_r_rag<RPT>(pr, lbase, st, c.a, n, z, rl, rr);
@@ -382,7 +471,8 @@ __device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams
     }
 }
 
-template <class T>
+// ADJ: powers of D_y^T (the adjoint step) instead of D_y
+template <class T, bool ADJ>
 __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -408,11 +498,11 @@ __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
         if (threadIdx.x < 32) warp_copy(&pbs, bp.probs + item.x, threadIdx.x);
         __syncthreads();
         switch (pbs.rpt_y) {
-        case 4: batch_cols<T, 4>(pbs, bp.pr, item.y, c, YL); break;
-        case 8: batch_cols<T, 8>(pbs, bp.pr, item.y, c, YL); break;
-        case 16: batch_cols<T, 16>(pbs, bp.pr, item.y, c, YL); break;
-        case 32: batch_cols<T, 32>(pbs, bp.pr, item.y, c, YL); break;
-        default: batch_cols<T, 64>(pbs, bp.pr, item.y, c, YL); break;
+        case 4: batch_cols<T, 4, ADJ>(pbs, bp.pr, item.y, c, YL); break;
+        case 8: batch_cols<T, 8, ADJ>(pbs, bp.pr, item.y, c, YL); break;
+        case 16: batch_cols<T, 16, ADJ>(pbs, bp.pr, item.y, c, YL); break;
+        case 32: batch_cols<T, 32, ADJ>(pbs, bp.pr, item.y, c, YL); break;
+        default: batch_cols<T, 64, ADJ>(pbs, bp.pr, item.y, c, YL); break;
         }
     }
 }
@@ -469,6 +559,40 @@ __global__ void k_batch_unpack(const BatchProb *probs, const int *row_prob, cons
         for (int j = lane; j < nx; j += 32) {
             if constexpr (sizeof(T) == 4) dstp[j] = (double)hi[src + j] + (double)lo[src + j];
             else dstp[j] = hi[src + j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// receivers (internal-layout indices): traces and adjoint sources
+// ---------------------------------------------------------------------------
+// out[r] = level value at irec[r]
+template <class T>
+__global__ void k_batch_gather(const T *hi, const T *lo, const long long *irec, int nrec, double *out)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
+        const long long i = irec[r];
+        double v = (double)hi[i];
+        if constexpr (sizeof(T) == 4) v += (double)lo[i];
+        out[r] = v;
+    }
+}
+
+// level[irec[r]] += vals[r], one thread in receiver order (receivers may
+// share a node)
+template <class T>
+__global__ void k_batch_inject(T *hi, T *lo, const long long *irec, int nrec, const double *vals)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int r = 0; r < nrec; ++r) {
+        const long long i = irec[r];
+        if constexpr (sizeof(T) == 4) {
+            const double x = (double)hi[i] + (double)lo[i] + vals[r];
+            const float h = __double2float_rn(x);
+            hi[i] = h;
+            lo[i] = __double2float_rn(x - (double)h);
+        } else {
+            hi[i] += vals[r];
         }
     }
 }

@@ -169,6 +169,9 @@ struct ContigStage {
     __device__ static int pos(int g) { return (g / RPT) * SST + (g % RPT); }
 };
 
+template <class T, int BC, int RPT, bool RAG>
+__device__ __forceinline__ void warp_solve(T (&z)[RPT], const AxisDev &A, int lane);
+
 // One application of D on a line held by a warp (lane = segment).  The line
 // has n = RPT * (Ld + 1) points; lanes past Ld hold zeros.  RAG (Dirichlet
 // only): any n <= 32 RPT; lane Ld = (n-1)/RPT holds the last point.
@@ -206,6 +209,22 @@ __device__ __forceinline__ void warp_sweep_core(T (&z)[RPT], RF rfun, T cu, cons
     if (BC == BC_DIRICHLET) end_zero<T, RPT>(z, lane == 0, !RAG && lane == Ld);
 #pragma unroll
     for (int k = 0; k < RPT; ++k) z[k] = full ? z[k] : (T)0;
+    warp_solve<T, BC, RPT, RAG>(z, A, lane);
+}
+
+// The solve of the difference form on a warp's line: z holds q on entry
+// (zero past the line) and e on exit, (1 + d^2) e_j - d (e_{j-1} + e_{j+1})
+// = q_j with the homogeneous boundary terms (Dirichlet: e = 0 at both end
+// nodes; periodic: all images).
+template <class T, int BC, int RPT, bool RAG>
+__device__ __forceinline__ void warp_solve(T (&z)[RPT], const AxisDev &A, int lane)
+{
+    const int n = A.n;
+    const T d = (T)A.d;
+    const int Ld = RAG ? (n - 1) / RPT : n / RPT - 1;
+    const bool full = lane <= Ld;
+    const int a = lane * RPT;
+    const int kl = n - 1 - a;
 
     // causal carries: Kogge-Stone over lanes with multipliers d^{RPT 2^k};
     // all shuffles of a group run before any lane-dependent branch
@@ -289,6 +308,71 @@ __device__ __forceinline__ void warp_sweep_rreg(T (&z)[RPT], const T (&r)[RPT], 
         rr = (lane == Ld) ? wr : rr;
     }
     warp_sweep_core<T, BC, RPT, 2, RAG>(z, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : r[k]); }, cu, A, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Transpose of D (Dirichlet).  In the difference form D = S C Delta: Delta the
+// second difference with the end rows duplicated (s_0 = s_1, s_{n-1} =
+// s_{n-2}), C the stencil q_j = c1 s_j + c2 (s_{j-1} + s_{j+1}) on the interior
+// rows, S the solve with e = 0 at both end nodes.  S is symmetric (the
+// interior system is symmetric Toeplitz and the end rows and columns are
+// dropped), so D^T w = Delta^T C^T S w: the same solve on w with its end values
+// dropped, then t = c1 e + c2 (e_{j-1} + e_{j+1}) (e zero outside the interior),
+// the end rows folded in (t'_1 = t_1 + t_0, t'_{n-2} = t_{n-2} + t_{n-1} with
+// t_0 = c2 e_1, t_{n-1} = c2 e_{n-2}; t' = 0 at and past the ends), and the
+// second difference of t'.
+// ---------------------------------------------------------------------------
+// z <- second difference of t' on a segment [a, a + RPT), given e there and
+// its halos e_{a-2}, e_{a-1}, e_{a+RPT}, e_{a+RPT+1}.  EDGE: the segment may
+// touch an end of the line (else t' = t throughout).
+template <class T, int RPT, bool EDGE>
+__device__ __forceinline__ void post_T(T (&z)[RPT], T el2, T el1, T er0, T er1, T c1, T c2, int a, int n)
+{
+    auto E = [&](int k) -> T {
+        return k < 0 ? (k == -1 ? el1 : el2) : (k >= RPT ? (k == RPT ? er0 : er1) : z[(k >= 0 && k < RPT) ? k : 0]);
+    };
+    auto tp = [&](int k) -> T {
+        const T ek = E(k);
+        T t = c1 * ek + c2 * (E(k - 1) + E(k + 1));
+        if (EDGE) {
+            const int j = a + k;
+            t += ((j == 1) ? c2 * ek : (T)0) + ((j == n - 2) ? c2 * ek : (T)0);
+            t = (j >= 1 && j <= n - 2) ? t : (T)0;
+        }
+        return t;
+    };
+    T tm = tp(-1), t0 = tp(0);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const T tn = tp(k + 1);          // reads e at k .. k+2: z[k] is still e here
+        z[k] = (tn - t0) - (t0 - tm);
+        tm = t0;
+        t0 = tn;
+    }
+}
+
+// D^T (z + cu u) on the warp's line (any n <= 32 RPT; lane = segment)
+template <class T, int RPT>
+__device__ __forceinline__ void warp_sweep_T(T (&z)[RPT], const T (&u)[RPT], T cu, const AxisDev &A, int lane)
+{
+    const int n = A.n, a = lane * RPT, kl = n - 1 - a;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const T q = z[k] + cu * u[k];
+        z[k] = (k < kl && (lane > 0 || k > 0)) ? q : (T)0;     // interior rows only
+    }
+    warp_solve<T, BC_DIRICHLET, RPT, true>(z, A, lane);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) z[k] = (k < kl && (lane > 0 || k > 0)) ? z[k] : (T)0;
+    __syncwarp();
+    T el2 = __shfl_up_sync(0xffffffffu, z[RPT - 2], 1), el1 = __shfl_up_sync(0xffffffffu, z[RPT - 1], 1);
+    T er0 = __shfl_down_sync(0xffffffffu, z[0], 1), er1 = __shfl_down_sync(0xffffffffu, z[1], 1);
+    el2 = (lane == 0) ? (T)0 : el2;
+    el1 = (lane == 0) ? (T)0 : el1;
+    er0 = (lane == 31) ? (T)0 : er0;
+    er1 = (lane == 31) ? (T)0 : er1;
+    post_T<T, RPT, true>(z, el2, el1, er0, er1, (T)A.c1, (T)A.c2, a, n);
+    __syncwarp();
 }
 
 // stage (coalesced side) -> registers (segment side)

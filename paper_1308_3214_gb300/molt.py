@@ -31,7 +31,8 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_solve_host", "mol_sync", "mol_launch_count", "mol_set_pass_timing", "mol_pass_times",
            "mol_apply_F_noalloc", "mol_batch_create", "mol_batch_destroy", "mol_batch_last_error",
            "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
-           "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times"]
+           "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times", "mol_batch_apply_FT",
+           "mol_batch_traces", "mol_batch_adjoint"]
 
 
 class MolError(RuntimeError):
@@ -102,6 +103,9 @@ def load_library(path: Path | None = None):
     lib.mol_batch_launch_count.restype = i64
     lib.mol_batch_set_pass_timing.argtypes = [vp, I]
     lib.mol_batch_pass_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
+    lib.mol_batch_apply_FT.argtypes = [vp, vp, vp, vp]
+    lib.mol_batch_traces.argtypes = [vp, vp, I, ctypes.POINTER(i64), i64, vp, vp]
+    lib.mol_batch_adjoint.argtypes = [vp, I, ctypes.POINTER(i64), i64, vp, vp, vp]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
@@ -375,6 +379,38 @@ class BatchSolver:
                                             int(nsteps), ctypes.c_void_p(_stream_ptr(stream))))
         return u_prev, u_cur
 
+    def apply_FT(self, w, out=None, stream=None):
+        """F^T w for every problem (packed)."""
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_batch_apply_FT(self.h, self._flat(w, "w"), self._flat(out, "out"),
+                                                ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def _rec(self, rec):
+        rec = np.ascontiguousarray(np.asarray(rec, dtype=np.int64).reshape(-1))
+        return rec, rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+    def traces(self, u0, rec, nsteps: int, stream=None):
+        """(nsteps, nrec) CUDA float64: u^n at the packed indices rec, n = 1..nsteps."""
+        import torch
+        rec, rp = self._rec(rec)
+        out = torch.empty((int(nsteps), rec.size), dtype=torch.float64, device="cuda")
+        self._check(self.lib.mol_batch_traces(self.h, self._flat(u0, "u0"), rec.size, rp, int(nsteps),
+                                              ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def adjoint(self, rec, tgrad, stream=None):
+        """dJ/du^0 (packed) from tgrad[n-1, r] = dJ/d(u^n at rec[r])."""
+        import torch
+        rec, rp = self._rec(rec)
+        tg = tgrad.to(dtype=torch.float64, device="cuda").contiguous()
+        if tg.dim() != 2 or tg.shape[1] != rec.size:
+            raise ValueError("tgrad must be (nsteps, nrec)")
+        out = self.empty()
+        self._check(self.lib.mol_batch_adjoint(self.h, rec.size, rp, int(tg.shape[0]), ctypes.c_void_p(tg.data_ptr()),
+                                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
     def solve_host(self, u0: np.ndarray, nsteps: int, out: np.ndarray | None = None, stream=None) -> np.ndarray:
         """Packed host u0 -> packed host u^{nsteps} (zero initial velocity)."""
         u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
@@ -418,3 +454,35 @@ class BatchSolver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _traces_function():
+    import torch
+
+    class ReceiverTraces(torch.autograd.Function):
+        """traces = T(u0): the receiver values u^n[rec], n = 1..nsteps, of the
+        forward run from u0 (zero initial velocity).  T is linear, so the
+        backward pass is the adjoint run on the trace gradients alone."""
+
+        @staticmethod
+        def forward(ctx, u0, solver, rec, nsteps):
+            ctx.solver, ctx.rec = solver, np.asarray(rec, dtype=np.int64)
+            return solver.traces(u0.detach().contiguous(), ctx.rec, int(nsteps))
+
+        @staticmethod
+        def backward(ctx, grad_traces):
+            return ctx.solver.adjoint(ctx.rec, grad_traces), None, None, None
+
+    return ReceiverTraces
+
+
+_RT = None
+
+
+def receiver_traces(u0, solver: "BatchSolver", rec, nsteps: int):
+    """Differentiable receiver traces: a (nsteps, nrec) tensor whose gradient
+    with respect to the packed initial field u0 runs the adjoint kernels."""
+    global _RT
+    if _RT is None:
+        _RT = _traces_function()
+    return _RT.apply(u0, solver, rec, nsteps)

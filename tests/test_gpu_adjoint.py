@@ -1,0 +1,228 @@
+"""Adjoint path (mol_batch_apply_FT / mol_batch_traces / mol_batch_adjoint and
+the autograd function) against the float64 oracle.
+
+Tolerances: float64 1e-12 (relative L2; traces and gradients of a 2-level
+recursion accumulate no more than the forward steps do).  Mixed: every step
+adds the float32 error of one F (or F^T) application, 16 eps32 (1 + 1/(1-d))
+2P relative to that application, and the recursion neither amplifies nor
+damps it (A-stability), so the error of step N is at most
+8 eps32 (1 + 1/(1-d)) 2P sum_n |F v^n| (the forward-stepping model of
+test_gpu_parity) with v^n the oracle's own states; a trace value's error is
+bounded by the field error in L2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1308_3214_gb300 import molt
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+EPS64 = 2.0 ** -52
+
+SHAPES = [(64, 64), (65, 67), (5, 130), (100, 129), (250, 257), (33, 1021), (1024, 40)]
+CFLS = [0.5, 2.0, 4.0, 1.3, 0.8, 3.3, 1.0]
+
+
+def spec(i, shape):
+    P = 1 + i % 3
+    ny, nx = shape
+    hx, hy = 1.0 / (nx - 1), 1.0 / (ny - 1)
+    dt = CFLS[i % len(CFLS)] * min(hx, hy)
+    beta = oracle.beta_max(P)
+    return P, dt, beta, (beta / dt * hx, beta / dt * hy)
+
+
+def model(nu, P):
+    dmax = max(math.exp(-v) for v in nu)
+    return 8 * EPS32 * (1.0 + 1.0 / (1.0 - dmax)) * 2 * P
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def make(shapes, prec):
+    specs = [spec(i, s) for i, s in enumerate(shapes)]
+    return molt.BatchSolver(shapes, dt=[s[1] for s in specs], P=[s[0] for s in specs], prec=prec), specs
+
+
+def receivers(shapes, offsets, per, seed):
+    rng = np.random.default_rng(seed)
+    rec, local = [], []
+    for i, (ny, nx) in enumerate(shapes):
+        iy = rng.integers(1, ny - 1, size=per)
+        ix = rng.integers(1, nx - 1, size=per)
+        loc = iy * nx + ix
+        local.append(loc)
+        rec.extend(offsets[i] + loc)
+    return np.array(rec, dtype=np.int64), local
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_FT_matches_oracle(prec):
+    b, specs = make(SHAPES, prec)
+    rng = np.random.default_rng(1)
+    ws = [rng.normal(size=s) for s in SHAPES]
+    got = b.unpack(b.apply_FT(b.pack(ws)))
+    torch.cuda.synchronize()
+    for i, (w, g, (P, dt, beta, nu)) in enumerate(zip(ws, got, specs)):
+        ref = oracle.FT(w, nu, P, beta, "dirichlet")
+        cond = np.linalg.norm(w) / max(np.linalg.norm(ref), 1e-300)
+        tol = max(1e-12, 64 * EPS64 * cond) if prec == "fp64" else 2 * model(nu, P) * max(cond, 1.0)
+        assert rel_l2(g.cpu().numpy(), ref) <= tol, (i, SHAPES[i])
+
+
+def test_FT_is_the_transpose_of_F_on_the_gpu():
+    """<F u, w> = <u, F^T w> with both sides from the GPU (float64), at the
+    size of the adjoint workload."""
+    shapes = [(1024, 1024), (77, 300)]
+    b, _ = make(shapes, "fp64")
+    rng = np.random.default_rng(2)
+    u = b.pack([rng.normal(size=s) for s in shapes])
+    w = b.pack([rng.normal(size=s) for s in shapes])
+    Fu, FTw = b.apply_F(u), b.apply_FT(w)
+    for i in range(len(shapes)):
+        sl = slice(b.offsets[i], b.offsets[i + 1])
+        lhs = float(torch.dot(Fu[sl], w[sl]))
+        rhs = float(torch.dot(u[sl], FTw[sl]))
+        scale = float(torch.linalg.norm(u[sl]) * torch.linalg.norm(w[sl]))
+        assert abs(lhs - rhs) <= 1e-13 * scale
+
+
+STEP_SHAPES = [(64, 64), (65, 67), (100, 129), (40, 250), (130, 9)]
+
+
+def oracle_states(u0, nsteps, nu, P, beta):
+    """Forward states u^1..u^N of the oracle and sum_n |F u^n|."""
+    a, c = u0, oracle.start(u0, nu, P, beta, "dirichlet")
+    Fsum = np.linalg.norm(oracle.F(u0, nu, P, beta, "dirichlet")) * 0.5
+    for _ in range(nsteps - 1):
+        F = oracle.F(c, nu, P, beta, "dirichlet")
+        Fsum += np.linalg.norm(F)
+        a, c = c, 2 * c - a + F
+    return Fsum
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_traces_match_oracle(prec):
+    nsteps = 9
+    b, specs = make(STEP_SHAPES, prec)
+    rng = np.random.default_rng(3)
+    u0s = []
+    for s in STEP_SHAPES:
+        u = rng.normal(size=s)
+        u[0, :] = u[-1, :] = 0
+        u[:, 0] = u[:, -1] = 0
+        u0s.append(u)
+    rec, local = receivers(STEP_SHAPES, b.offsets, 4, 4)
+    t = b.traces(b.pack(u0s), rec, nsteps).cpu().numpy()
+    for i, (P, dt, beta, nu) in enumerate(specs):
+        ref = oracle.traces(u0s[i], nsteps, local[i], nu, P, beta, "dirichlet")
+        got = t[:, 4 * i:4 * (i + 1)]
+        if prec == "fp64":
+            assert rel_l2(got, ref) <= 1e-12, i
+        else:
+            bound = model(nu, P) * oracle_states(u0s[i], nsteps, nu, P, beta)
+            assert np.abs(got - ref).max() <= bound, i
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_adjoint_matches_oracle(prec):
+    nsteps = 9
+    b, specs = make(STEP_SHAPES, prec)
+    rec, local = receivers(STEP_SHAPES, b.offsets, 4, 5)
+    tg = np.random.default_rng(6).normal(size=(nsteps, rec.size))
+    grad = b.unpack(b.adjoint(rec, torch.from_numpy(tg)))
+    for i, (P, dt, beta, nu) in enumerate(specs):
+        shape = STEP_SHAPES[i]
+        tgi = tg[:, 4 * i:4 * (i + 1)]
+        ref = oracle.adjoint(tgi, shape, local[i], nu, P, beta, "dirichlet")
+        got = grad[i].cpu().numpy()
+        if prec == "fp64":
+            assert rel_l2(got, ref) <= 1e-12, i
+        else:
+            # sum_n |F^T mu^n| along the oracle's adjoint recursion
+            size = int(np.prod(shape))
+            g = np.zeros((nsteps, size))
+            for n in range(nsteps):
+                np.add.at(g[n], local[i], tgi[n])
+            m2, m1 = np.zeros(shape), g[-1].reshape(shape)
+            Fsum = 0.0
+            for n in range(nsteps - 1, 0, -1):
+                F = oracle.FT(m1, nu, P, beta, "dirichlet")
+                Fsum += np.linalg.norm(F)
+                m2, m1 = m1, 2 * m1 - m2 + F + g[n - 1].reshape(shape)
+            Fsum += 0.5 * np.linalg.norm(oracle.FT(m1, nu, P, beta, "dirichlet"))
+            assert np.linalg.norm(got - ref) <= model(nu, P) * Fsum, i
+
+
+def test_gradient_matches_central_difference_on_gpu():
+    """J(u0) = |T u0 - d|^2 / 2 is quadratic: the central difference along s
+    equals <grad J, s> up to rounding (float64 path)."""
+    shapes = [(96, 80), (51, 130)]
+    nsteps = 12
+    b, _ = make(shapes, "fp64")
+    rng = np.random.default_rng(7)
+    u0 = b.pack([rng.normal(size=s) for s in shapes])
+    rec, _ = receivers(shapes, b.offsets, 6, 8)
+    d = torch.from_numpy(rng.normal(size=(nsteps, rec.size))).cuda()
+
+    def J(u):
+        return 0.5 * float(((b.traces(u, rec, nsteps) - d) ** 2).sum())
+
+    grad = b.adjoint(rec, b.traces(u0, rec, nsteps) - d)
+    for _ in range(3):
+        s = b.pack([rng.normal(size=sh) for sh in shapes])
+        eps = 1e-3
+        fd = (J(u0 + eps * s) - J(u0 - eps * s)) / (2 * eps)
+        an = float(torch.dot(grad, s))
+        assert abs(fd - an) <= 1e-9 * max(abs(fd), float(torch.linalg.norm(grad) * torch.linalg.norm(s)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_autograd_function_runs_the_adjoint(prec):
+    shapes = [(70, 90)]
+    nsteps = 10
+    b, _ = make(shapes, prec)
+    rng = np.random.default_rng(9)
+    u0 = b.pack([rng.normal(size=shapes[0])]).requires_grad_(True)
+    rec, _ = receivers(shapes, b.offsets, 8, 10)
+    d = torch.from_numpy(rng.normal(size=(nsteps, rec.size))).cuda()
+    tr = molt.receiver_traces(u0, b, rec, nsteps)
+    loss = 0.5 * ((tr - d) ** 2).sum()
+    loss.backward()
+    expect = b.adjoint(rec, (tr - d).detach())
+    assert torch.equal(u0.grad, expect)
+
+
+@pytest.mark.slow
+def test_adjoint_workload_dot_product_and_mixed_error():
+    """The adjoint workload: 1024^2 Dirichlet, P = 2, CFL 2, 400 steps, 64
+    receivers.  Float64: <T s, r> = <s, T^T r>; mixed gradient within the
+    accumulated float32 bound of the float64 one."""
+    from paper_1308_3214_gb300 import workloads
+    n, P, nsteps = 1024, 2, 400
+    dt = 2.0 / (n - 1)
+    rec = np.array([iy * n + ix for iy, ix in workloads.receivers_2d(n, 64, seed=1005)], dtype=np.int64)
+    rng = np.random.default_rng(11)
+    grads = {}
+    for prec in ("fp64", "mixed"):
+        b = molt.BatchSolver([(n, n)], dt=dt, P=P, prec=prec)
+        s = b.pack([rng.normal(size=(n, n))]) if prec == "fp64" else s
+        r = torch.from_numpy(np.random.default_rng(12).normal(size=(nsteps, rec.size))).cuda()
+        grads[prec] = b.adjoint(rec, r)
+        if prec == "fp64":
+            Ts = b.traces(s, rec, nsteps)
+            lhs, rhs = float((Ts * r).sum()), float(torch.dot(s, grads[prec]))
+            assert abs(lhs - rhs) <= 1e-10 * float(torch.linalg.norm(Ts) * torch.linalg.norm(r))
+        b.close()
+    nu = oracle.beta_max(P) / 2.0
+    err = float(torch.linalg.norm(grads["mixed"] - grads["fp64"]) / torch.linalg.norm(grads["fp64"]))
+    assert err <= model((nu, nu), P) * nsteps * 4
