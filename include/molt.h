@@ -227,6 +227,14 @@ mol_status mol_batch_step(mol_batch b, double *u_prev, double *u_cur, int64_t ns
 /* out = F^T w for every problem (packed fields, may not overlap). */
 mol_status mol_batch_apply_FT(mol_batch b, const double *w, double *out, void *stream);
 
+/* One update on packed fields: un = ea u + eb up + ec Op(u) + add, Op = F
+ * (transpose = 0) or F^T (transpose = 1); up is read only when eb != 0, add
+ * may be NULL.  The building block of adjoints of general history losses
+ * (one adjoint step: u = mu^{n+1}, up = mu^{n+2}, ea = 2, eb = -1, ec = 1,
+ * F^T, add = dJ/du^n). */
+mol_status mol_batch_update(mol_batch b, const double *u, const double *up, double *un, double ea, double eb,
+                            double ec, int transpose, const double *add, void *stream);
+
 /* traces (device, nsteps * nrec float64) of the forward run from u0 (packed,
  * device) with zero initial velocity. */
 mol_status mol_batch_traces(mol_batch b, const double *u0, int nrec, const int64_t *rec, int64_t nsteps,

@@ -230,14 +230,14 @@ mol_status pack(mol_batch_ctx *b, const double *x, const BLevel &L, cudaStream_t
     return MOL_OK;
 }
 
-mol_status unpack(mol_batch_ctx *b, const BLevel &L, double *x, cudaStream_t s)
+mol_status unpack(mol_batch_ctx *b, const BLevel &L, double *x, cudaStream_t s, const double *add = nullptr)
 {
     if (b->tbytes == 4)
         k_batch_unpack<float><<<b->cgrid, 256, 0, s>>>(b->probs, b->row_prob, b->uoff_dev, (int)b->nrows,
-                                                       (const float *)L.hi, (const float *)L.lo, x);
+                                                       (const float *)L.hi, (const float *)L.lo, x, add);
     else
         k_batch_unpack<double><<<b->cgrid, 256, 0, s>>>(b->probs, b->row_prob, b->uoff_dev, (int)b->nrows,
-                                                        (const double *)L.hi, nullptr, x);
+                                                        (const double *)L.hi, nullptr, x, add);
     BCK(cudaGetLastError(), "batched level conversion");
     b->launches++;
     return MOL_OK;
@@ -638,6 +638,24 @@ mol_status mol_batch_apply_FT(mol_batch b, const double *w, double *out, void *s
     if ((st = pack(b, w, b->lev[0], s)) != MOL_OK) return st;
     if ((st = run_update(b, b->lev[0], b->lev[0], b->lev[1], 0.0, 0.0, 1.0, s, true)) != MOL_OK) return st;
     return unpack(b, b->lev[1], out, s);
+}
+
+mol_status mol_batch_update(mol_batch b, const double *u, const double *up, double *un, double ea, double eb,
+                            double ec, int transpose, const double *add, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_status st;
+    if ((st = bcheck_ptr(b, u, "u")) != MOL_OK || (st = bcheck_ptr(b, un, "un")) != MOL_OK) return st;
+    if (eb != 0.0 && (st = bcheck_ptr(b, up, "up")) != MOL_OK) return st;
+    if (add && (st = bcheck_ptr(b, add, "add")) != MOL_OK) return st;
+    if (un == u || (eb != 0.0 && un == up)) return bfail(b, MOL_EINVAL, "un must not overlap u or up");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = pack(b, u, b->lev[0], s)) != MOL_OK) return st;
+    if (eb != 0.0 && (st = pack(b, up, b->lev[1], s)) != MOL_OK) return st;
+    if ((st = run_update(b, b->lev[0], eb != 0.0 ? b->lev[1] : b->lev[0], b->lev[2], ea, eb, ec, s, transpose != 0)) !=
+        MOL_OK)
+        return st;
+    return unpack(b, b->lev[2], un, s, add);
 }
 
 mol_status mol_batch_traces(mol_batch b, const double *u0, int nrec, const int64_t *rec, int64_t nsteps,

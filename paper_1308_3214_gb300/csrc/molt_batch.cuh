@@ -543,9 +543,10 @@ __global__ void k_batch_pack(const BatchProb *probs, const int *row_prob, const 
     }
 }
 
+// x = level (+ add, a packed field, when given)
 template <class T>
 __global__ void k_batch_unpack(const BatchProb *probs, const int *row_prob, const long long *uoff, int nrows,
-                               const T *hi, const T *lo, double *__restrict__ x)
+                               const T *hi, const T *lo, double *__restrict__ x, const double *__restrict__ add)
 {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -554,11 +555,15 @@ __global__ void k_batch_unpack(const BatchProb *probs, const int *row_prob, cons
         const BatchProb *pb = probs + p;
         const int nx = __ldg(&pb->ax.n), pitch = __ldg(&pb->pitch);
         const int row = r - __ldg(&pb->row0);
-        double *dstp = x + __ldg(uoff + p) + (int64_t)row * nx;
+        const int64_t u0 = __ldg(uoff + p) + (int64_t)row * nx;
+        double *dstp = x + u0;
         const int64_t src = __ldg(&pb->off) + (int64_t)row * pitch;
         for (int j = lane; j < nx; j += 32) {
-            if constexpr (sizeof(T) == 4) dstp[j] = (double)hi[src + j] + (double)lo[src + j];
-            else dstp[j] = hi[src + j];
+            double v;
+            if constexpr (sizeof(T) == 4) v = (double)hi[src + j] + (double)lo[src + j];
+            else v = hi[src + j];
+            if (add) v += add[u0 + j];
+            dstp[j] = v;
         }
     }
 }

@@ -32,7 +32,7 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_apply_F_noalloc", "mol_batch_create", "mol_batch_destroy", "mol_batch_last_error",
            "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
            "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times", "mol_batch_apply_FT",
-           "mol_batch_traces", "mol_batch_adjoint"]
+           "mol_batch_traces", "mol_batch_adjoint", "mol_batch_update"]
 
 
 class MolError(RuntimeError):
@@ -106,6 +106,7 @@ def load_library(path: Path | None = None):
     lib.mol_batch_apply_FT.argtypes = [vp, vp, vp, vp]
     lib.mol_batch_traces.argtypes = [vp, vp, I, ctypes.POINTER(i64), i64, vp, vp]
     lib.mol_batch_adjoint.argtypes = [vp, I, ctypes.POINTER(i64), i64, vp, vp, vp]
+    lib.mol_batch_update.argtypes = [vp, vp, vp, vp, D, D, D, I, vp, vp]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
@@ -386,6 +387,17 @@ class BatchSolver:
                                                 ctypes.c_void_p(_stream_ptr(stream))))
         return out
 
+    def update(self, u, up, ea: float, eb: float, ec: float, transpose: bool = False, add=None, out=None,
+               stream=None):
+        """ea u + eb up + ec Op(u) + add with Op = F or F^T (packed fields)."""
+        out = self.empty() if out is None else out
+        upp = self._flat(up, "up") if eb != 0.0 else None
+        addp = self._flat(add, "add") if add is not None else None
+        self._check(self.lib.mol_batch_update(self.h, self._flat(u, "u"), upp, self._flat(out, "out"), float(ea),
+                                              float(eb), float(ec), 1 if transpose else 0, addp,
+                                              ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
     def _rec(self, rec):
         rec = np.ascontiguousarray(np.asarray(rec, dtype=np.int64).reshape(-1))
         return rec, rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
@@ -486,3 +498,44 @@ def receiver_traces(u0, solver: "BatchSolver", rec, nsteps: int):
     if _RT is None:
         _RT = _traces_function()
     return _RT.apply(u0, solver, rec, nsteps)
+
+
+def history_gradient(solver: "BatchSolver", u0, nsteps: int, grad_fn, checkpoint_every: int = 40):
+    """dJ/du^0 for J = sum_{n=0}^{nsteps} phi_n(u^n) over the forward run from
+    u0 (zero initial velocity), given grad_fn(n, u_n) -> dphi_n/du^n (a packed
+    tensor, or None where phi_n is absent).
+
+    The adjoint states obey mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n
+    (n = N..1, mu^{N+1} = mu^{N+2} = 0) and dJ/du^0 = mu^1 + F^T mu^1 / 2 -
+    mu^2 + g^0, with g^n = grad_fn(n, u^n).  g^n needs the forward state u^n
+    in reverse order: the forward pass keeps (u^{c-1}, u^c) at c = 1, 1+K,
+    1+2K, ... (K = checkpoint_every) and the backward pass recomputes one
+    segment of K states at a time from its checkpoint, holding about
+    2 N/K + K fields instead of N."""
+    K = max(1, int(checkpoint_every))
+    N = int(nsteps)
+    up = u0.detach().clone()
+    uc = solver.start(up)
+    ckpt = {}                                  # c -> (u^{c-1}, u^c)
+    c = 1
+    while True:
+        ckpt[c] = (up.clone(), uc.clone())
+        if c + K > N:
+            break
+        solver.step(up, uc, K)
+        c += K
+    mu1, mu2 = solver.empty().zero_(), solver.empty().zero_()   # mu^{n+1}, mu^{n+2}
+    for c in sorted(ckpt, reverse=True):
+        a, bb = ckpt[c][0].clone(), ckpt[c][1].clone()
+        states = [bb.clone()]                  # u^c .. u^{min(c+K-1, N)}
+        for _ in range(min(c + K - 1, N) - c):
+            solver.step(a, bb, 1)
+            states.append(bb.clone())
+        for j in range(len(states) - 1, -1, -1):
+            n = c + j
+            g = grad_fn(n, states[j])
+            mu0 = solver.update(mu1, mu2, 2.0, -1.0, 1.0, transpose=True, add=g)
+            mu1, mu2 = mu0, mu1
+        del states
+    g0 = grad_fn(0, u0.detach())
+    return solver.update(mu1, mu2, 1.0, -1.0, 0.5, transpose=True, add=g0)
