@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark of the MOL^T wave solver on one or more GB300s.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 2d|3d|1d|batch]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 2d|3d|1d|batch|adjoint]
                     [--prec mixed|fp64] [--impl ours|reference]
 
 A "step" is one time step of the scheme of order 2P over the whole synthetic
@@ -13,7 +13,9 @@ resident in HBM when the timed region starts.  Metric: point-updates/s
 (points x steps / second), summed over all GPUs.  ``--workload batch``: 512
 independent Dirichlet squares, n log-uniform in [64, 1024], P in {1, 2, 3},
 CFL in [0.5, 4], seeded Gaussians, stepped together through mol_batch_step
-(every rank its own 512 problems).
+(every rank its own 512 problems).  ``--workload adjoint``: gradient of a
+receiver misfit (64 receivers, 400 steps) with respect to the initial field of
+a 1024^2 Dirichlet problem, P = 2, CFL 2; a step is one adjoint time step.
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
 problem (independent replicas, weak scaling, no collective on the data path).
@@ -62,6 +64,10 @@ def workload_spec(name: str) -> dict:
         return dict(name="3d-periodic-256^3-P2-cfl1.5-fourier16", shape=(n, n, n), P=2, cfl=1.5,
                     bc="periodic", lo=(0.0,) * 3, hi=(L,) * 3, h=L / n, steps_in_config=200,
                     field=lambda: workloads.fourier_3d(n, seed=1003)[0])
+    if name == "adjoint":
+        n = 1024
+        return dict(name="adjoint-2d-dirichlet-1024x1024-P2-cfl2-400steps-64rec", n=n, P=2, cfl=2.0, nsteps=400,
+                    nrec=64, bc="dirichlet")
     if name == "batch":
         return dict(name="batch-512-dirichlet-n64..1024-P1..3-cfl0.5..4-gaussian", count=512, seed=1004,
                     steps_in_config=200, bc="dirichlet")
@@ -278,19 +284,26 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batch"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batch", "adjoint"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512, help="problems of the batch workload (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     spec = workload_spec(args.workload)
+    if args.workload == "batch" and args.batch_count != spec["count"]:
+        spec["count"] = args.batch_count
+        spec["name"] = spec["name"].replace("batch-512", f"batch-{args.batch_count}")
     if args.workload == "batch":
         main_batch(args, spec)
+        return
+    if args.workload == "adjoint":
+        main_adjoint(args, spec)
         return
     if args.impl == "reference":
         run_reference(args, spec)
@@ -640,6 +653,200 @@ def main_batch(args, spec):
         line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
                                 "sample": f"{ssteps} oracle steps on each of the first {used} problems "
                                           f"(seeded order; {sdt:.1f} s)"}
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# adjoint workload
+# ---------------------------------------------------------------------------
+def adjoint_problem(spec, seed_offset: int = 0):
+    """u0: seeded Gaussian; targets: traces of a forward run from a second
+    seeded Gaussian; receivers: seeded interior nodes."""
+    n = spec["n"]
+    u0 = workloads.gaussian_2d(n, seed=1005 + seed_offset)
+    u_true = workloads.gaussian_2d(n, seed=2005 + seed_offset)
+    rec = np.array([iy * n + ix for iy, ix in workloads.receivers_2d(n, spec["nrec"], seed=1005 + seed_offset)],
+                   dtype=np.int64)
+    return u0, u_true, rec
+
+
+def main_adjoint(args, spec):
+    world, rank, local = dist_setup()
+    n, P, nsteps = spec["n"], spec["P"], spec["nsteps"]
+    dt = spec["cfl"] / (n - 1)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        beta = oracle.beta_max(P)
+        # each step: one oracle adjoint step (F^T on the field + injection) on
+        # a grid sized so that the whole run stays within a few minutes
+        budget = 150.0 / max(args.steps + args.warmup, 1)
+        m = 64
+        t0 = time.perf_counter()
+        oracle.FT(np.zeros((m, m)), beta / spec["cfl"], P, beta, "dirichlet")
+        per_pt = (time.perf_counter() - t0) / (m * m)
+        m = int(max(32, min(n, math.sqrt(budget / max(per_pt, 1e-12)))))
+        rng = np.random.default_rng(1)
+        rec = rng.choice(m * m, size=spec["nrec"], replace=False)
+        tg = rng.normal(size=(args.warmup + args.steps, rec.size))
+        nu = beta / spec["cfl"]
+        oracle.adjoint(tg[:args.warmup], (m, m), rec, nu, P, beta, "dirichlet")
+        t0 = time.perf_counter()
+        oracle.adjoint(tg[:args.steps], (m, m), rec, nu, P, beta, "dirichlet")
+        el = time.perf_counter() - t0
+        value = m * m * args.steps / el
+        cores = oracle.num_threads()
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": spec["name"], "sampled_shape": [m, m]},
+                "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                                 "sample": f"{m}x{m} grid, {args.steps} adjoint steps (same CFL, P, 64 receivers)"},
+                "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_1308_3214_gb300 import molt
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    u0h, uth, rec = adjoint_problem(spec, 7919 * rank)
+    N = args.steps                                   # adjoint steps timed
+    b = molt.BatchSolver([(n, n)], dt=dt, P=P, prec=args.prec)
+    u0 = b.pack([u0h])
+    d = b.traces(b.pack([uth]), rec, max(N, nsteps))
+    res = b.traces(u0, rec, max(N, nsteps)) - d
+    # warm-up, then the timed adjoint run of N steps (ms = one mol_batch_adjoint call)
+    b.adjoint(rec, res[:args.warmup])
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = b.launches
+    sampler = None
+    try:
+        bus = torch.cuda.get_device_properties(dev_index).pci_bus_id
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus).start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    grad = b.adjoint(rec, res[:N])
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    launches = b.launches - l0
+    # per-pass device times of the adjoint passes
+    b.set_pass_timing(True)
+    b.adjoint(rec, res[:min(N, 100)])
+    passes = b.pass_times()
+    b.set_pass_timing(False)
+    pts = n * n
+    value = world * pts * N / (ms * 1e-3)
+    t = 4 if args.prec == "mixed" else 8
+    bpp = {1: 8 + t * P, 0: t * P + 24}
+    dom_axis = max(passes, key=lambda a: passes[a][0])
+    dom_ms = passes[dom_axis][0] / passes[dom_axis][1]
+    achieved = bpp[dom_axis] * pts / (dom_ms * 1e-3) / 1e9
+    peak, peak_kind = read_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": read_traffic(dom_axis, spec["name"], args.prec, "batch"),
+                "kernel": {0: "k_batch_x<ADJ> (x pass: transposed Horner + level update)",
+                           1: "k_batch_y<ADJ> (y pass: powers of D_y^T)"}[dom_axis],
+                "peak_kind": f"{peak_kind} hbm_gbs (copy)", "alg_bytes_per_launch": bpp[dom_axis] * pts,
+                "passes": {f"axis{a}": {"ms_per_launch": passes[a][0] / passes[a][1],
+                                         "alg_GBps": bpp[a] * pts / (passes[a][0] / passes[a][1] * 1e-3) / 1e9,
+                                         "alg_bytes_per_point": bpp[a]} for a in passes},
+                "kernel_timing": "per-pass CUDA events over a second adjoint run of min(steps, 100) steps"}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": N, "warmup": args.warmup,
+            "ms_per_step": ms / N, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": spec["name"], "shape": [n, n], "P": P, "cfl": spec["cfl"], "receivers": int(rec.size),
+                       "prec": args.prec, "step": "one adjoint step: mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n",
+                       "l2": "no flush: per-step working set exceeds the 129 MB L2",
+                       "parallelism": f"{world} rank(s), each its own problem"},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+    # gradient check and mixed-vs-fp64 comparison of the full workload gradient
+    if rank == 0 and not args.no_accuracy:
+        other = "fp64" if args.prec == "mixed" else "mixed"
+        b2 = molt.BatchSolver([(n, n)], dt=dt, P=P, prec=other)
+        r2 = b2.traces(b2.pack([u0h]), rec, nsteps) - b2.traces(b2.pack([uth]), rec, nsteps)
+        g2 = b2.adjoint(rec, r2)
+        g1 = b.adjoint(rec, res[:nsteps])
+        line["accuracy"] = {"steps": nsteps, f"rel_l2_grad_{args.prec}_vs_{other}":
+                            float(torch.linalg.norm(g1 - g2) / torch.linalg.norm(g2))}
+        b2.close()
+    if not args.no_e2e:
+        # the user's whole job through the public API: host u0 in, traces,
+        # loss, backward (adjoint), host gradient out
+        pin = torch.empty(pts, dtype=torch.float64, pin_memory=True)
+        pin.numpy()[...] = u0h.reshape(-1)
+        gout = torch.empty(pts, dtype=torch.float64, pin_memory=True)
+        dd = d[:nsteps]
+
+        def job():
+            u = pin.cuda(non_blocking=True).requires_grad_(True)
+            tr = molt.receiver_traces(u, b, rec, nsteps)
+            loss = 0.5 * ((tr - dd) ** 2).sum()
+            loss.backward()
+            gout.copy_(u.grad)
+            return float(loss)
+
+        job()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        calls = 3
+        for _ in range(calls):
+            job()
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0)
+        line["e2e"] = {"value": world * pts * nsteps * calls / el, "unit": METRIC,
+                       "h2d_bytes_per_step": 8 * pts, "d2h_bytes_per_step": 8 * pts + 8,
+                       "step": f"one gradient: copy u0 in, {nsteps} forward steps with traces, loss, "
+                               f"{nsteps} adjoint steps, copy the gradient out (counted as {nsteps} point-updates)",
+                       "time_steps_per_step": nsteps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        m = 256
+        beta = oracle.beta_max(P)
+        rng = np.random.default_rng(1)
+        rr = rng.choice(m * m, size=spec["nrec"], replace=False)
+        ksteps = 20
+        t0 = time.perf_counter()
+        oracle.adjoint(rng.normal(size=(ksteps, rr.size)), (m, m), rr, beta / spec["cfl"], P, beta, "dirichlet")
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": m * m * ksteps / el, "unit": METRIC, "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": f"{ksteps} oracle adjoint steps on a {m}x{m} grid "
+                                                            f"({el:.1f} s), same CFL and P, 64 receivers"}
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -1158,6 +1158,9 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
                 for (int k = 0; k < RPT; ++k) { *po = z[k]; po += st; }
             }
         }
+        // peers read this CTA's shared memory after the last exchange: no CTA
+        // of the cluster exits before all of them are past those reads
+        if (c.K > 1) c.cl.sync();
         return;
     }
 
@@ -1195,6 +1198,7 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
             for (int k = 0; k < RPT; ++k) { *po = z[k]; po += st; }
         }
     }
+    if (c.K > 1) c.cl.sync();       // see the powers path: peers may still read this CTA's slots
 }
 
 }  // namespace molt
