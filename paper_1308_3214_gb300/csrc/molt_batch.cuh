@@ -102,6 +102,15 @@ __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams 
     const int64_t base = pb.off + (int64_t)row * pb.pitch;
     const int nvec = (n + VN - 1) / VN;              // within the padded pitch
     const int ng = pb.P;
+    if (lane == 0) {
+        const unsigned bytes = (unsigned)(nvec * 16);    // whole 16-byte vectors inside the pitch
+        prefetch_l2(reinterpret_cast<const T *>(pr.u_hi) + base, bytes);
+        if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.u_lo) + base, bytes);
+        if (pr.eb != 0.0) {
+            prefetch_l2(reinterpret_cast<const T *>(pr.up_hi) + base, bytes);
+            if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.up_lo) + base, bytes);
+        }
+    }
 
     // 1. fields 1..ng-1 -> shared memory (asynchronous); field 0 after r
     auto copy_field = [&](int k) {

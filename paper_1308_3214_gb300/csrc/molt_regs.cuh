@@ -733,6 +733,14 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, bytes a multiple
+// of 16): the level rows the epilogue reads long after the row starts are
+// fetched while the row is being swept, at no register or shared-memory cost.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // second difference of a pair field at 4 consecutive points, given the
@@ -764,6 +772,15 @@ __global__ void __launch_bounds__(32 * WARPS) k_contig_res(AxisDev A, LineSet LS
     const int64_t base = L * (int64_t)n;
     const int nvec = n / 4;
     const int ng = pr.ng;
+    if (lane == 0) {
+        const unsigned bytes = (unsigned)n * 4u;          // n is a multiple of RPT >= 8
+        prefetch_l2((const float *)pr.u_hi + base, bytes);
+        prefetch_l2((const float *)pr.u_lo + base, bytes);
+        if (pr.eb != 0.0) {
+            prefetch_l2((const float *)pr.up_hi + base, bytes);
+            prefetch_l2((const float *)pr.up_lo + base, bytes);
+        }
+    }
 
     // 1. fields 1..ng-1 -> shared memory (asynchronous); field 0 after r
     auto copy_field = [&](int k) {
