@@ -343,6 +343,7 @@ def main():
 
     u0_host = spec["field"]()
     solver = make(args.prec)
+    tuning = solver.autotune()              # once per problem, as a user would
 
     def timed_steps(s, nsteps, warm):
         """Region A: nsteps through mol_step as a user runs it (CUDA-graph time
@@ -416,11 +417,12 @@ def main():
                        "bc": spec["bc"], "beta": solver.beta, "prec": args.prec,
                        "levels": "f32 hi+lo pairs" if args.prec == "mixed" else "f64",
                        "l2": "no flush: per-step working set (3 levels + intermediate fields) exceeds the 129 MB L2",
-                       "parallelism": f"{world} independent replica(s)"},
+                       "parallelism": f"{world} independent replica(s)", "tuning": tuning},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
 
     if rank == 0 and not args.no_fp64_compare and args.prec == "mixed":
         s64 = make("fp64")
+        s64.autotune()
         k64 = max(3, args.steps // 8)
         ms64, _, p64, _ = timed_steps(s64, k64, 3)
         line["fp64_path"] = {"value": N * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
@@ -553,6 +555,7 @@ def main_batch(args, spec):
         return molt.BatchSolver(shapes, dt=dts, P=Ps, prec=prec, **kw)
 
     b = make(args.prec)
+    tuning = b.autotune()
     u0 = b.pack([p.u0 for p in probs])
 
     def timed(bs, nsteps, warm):
@@ -616,11 +619,12 @@ def main_batch(args, spec):
                        "P_counts": {str(k): Ps.count(k) for k in (1, 2, 3)}, "prec": args.prec,
                        "levels": "f32 hi+lo pairs" if args.prec == "mixed" else "f64",
                        "l2": "no flush: per-step working set (3 levels + intermediate fields) exceeds the 129 MB L2",
-                       "parallelism": f"{world} rank(s), each its own 512 problems"},
+                       "parallelism": f"{world} rank(s), each its own {len(shapes)} problems", "tuning": tuning},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
 
     if rank == 0 and not args.no_fp64_compare and args.prec == "mixed":
         b64 = make("fp64")
+        b64.autotune()
         k64 = max(3, args.steps // 8)
         ms64, _, p64, _, _ = timed(b64, k64, 3)
         line["fp64_path"] = {"value": npts * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
@@ -739,6 +743,7 @@ def main_adjoint(args, spec):
     u0h, uth, rec = adjoint_problem(spec, 7919 * rank)
     N = args.steps                                   # adjoint steps timed
     b = molt.BatchSolver([(n, n)], dt=dt, P=P, prec=args.prec)
+    b.autotune()
     u0 = b.pack([u0h])
     d = b.traces(b.pack([uth]), rec, max(N, nsteps))
     res = b.traces(u0, rec, max(N, nsteps)) - d

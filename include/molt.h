@@ -146,6 +146,27 @@ mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps,
 mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t nsteps,
                           void *stream);
 
+/*
+ * Autotuner: times the launch variants that change something for this grid
+ * -- warps per CTA of the resident x pass (1, 2, 4), the strided segment
+ * length (64 or 32 points per thread for float32 sweeps) and the segments
+ * per CTA at most (8 or 4, hence the cluster size) -- on the handle's own
+ * workspace (a few steps each, CUDA events, minimum of 3 timings) and keeps
+ * the fastest for every later call.  Synchronous on the stream; the caller's
+ * fields are not touched.  The paper has no counterpart.
+ */
+mol_status mol_autotune(mol_handle h, void *stream);
+
+/* Force launch choices (e.g. a tuning result kept from an earlier run):
+ * res_warps 1, 2 or 4; strided_rpt 0 (default) or 32; strided_warps 1..8.
+ * MOL_EINVAL if a choice is out of range or does not fit an axis. */
+mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int strided_warps);
+
+/* The launch choices in use: out[0] = warps per CTA of the resident x pass,
+ * out[1] = strided segment length (0 = default), out[2] = segments per CTA at
+ * most; *ms_per_step (may be NULL) = the tuned step time (0 before tuning). */
+mol_status mol_get_tuning(mol_handle h, int out[3], double *ms_per_step);
+
 /* Wait for the handle's work on the stream; reports device-side errors. */
 mol_status mol_sync(mol_handle h, void *stream);
 
@@ -250,6 +271,17 @@ mol_status mol_batch_solve_host(mol_batch b, const double *u0, double *u_out, in
 
 mol_status mol_batch_sync(mol_batch b, void *stream);
 int64_t mol_batch_launch_count(mol_batch b);
+
+/* Autotuner of a batch: times the x pass with 2, 4 and 8 warps per CTA for
+ * each of its two launches (rows of <= 512 points; longer rows), then the y
+ * pass with each problem's segment length at the smallest RPT covering the
+ * column with 16 warps or at twice that, on the batch's own workspace, and
+ * keeps the fastest.  Synchronous; the caller's fields are not touched.
+ * mol_batch_get_tuning: out[0], out[1] = warps per CTA of the two x launches,
+ * out[2] = y segment rule (0 smallest, 1 doubled); ms (may be NULL) = the
+ * tuned x and y pass times. */
+mol_status mol_batch_autotune(mol_batch b, void *stream);
+mol_status mol_batch_get_tuning(mol_batch b, int out[3], double ms[2]);
 
 /* Per-pass CUDA-event timing as mol_set_pass_timing / mol_pass_times
  * (index 0 = x pass, 1 = y pass). */

@@ -53,6 +53,10 @@ struct mol_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t launches = 0;
+    // launch choices (mol_autotune): warps per CTA of the resident x pass,
+    // strided segment length (0 = default) and segments per CTA at most
+    int tune_res_warps = 2, tune_strided_rpt = 0, tune_strided_warps = 8;
+    double tune_ms = 0.0;                      // step time of the chosen configuration
     bool timing = false;                       // per-pass events (benchmarks)
     std::vector<cudaEvent_t> ev_pool;          // reusable events
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (axis, (start, stop))
@@ -217,10 +221,11 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
     int rpt = 0, S = 0, K = 0;
     cudaError_t e;
     if (axis == 0 && pr.mode == 1 && pr.nout == 1 && regs_res_plan(h->tbytes, n, pr.ng, &rpt)) {
-        e = launch_res(h->bc, rpt, pr.ng, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
+        e = launch_res(h->bc, rpt, pr.ng, h->tune_res_warps, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
     } else if (axis == 0 && regs_contig_plan(h->tbytes, h->bc, n, &rpt)) {
         e = launch_contig(h->tbytes, h->bc, rpt, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
-    } else if (axis > 0 && regs_strided_plan(h->tbytes, h->bc, n, &rpt, &S, &K)) {
+    } else if (axis > 0 && regs_strided_plan(h->tbytes, h->bc, n, &rpt, &S, &K, h->tune_strided_rpt,
+                                             h->tune_strided_warps)) {
         LineSet L = lineset_of(h, axis);
         L.S = S;
         L.K = K;
@@ -706,6 +711,110 @@ mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t
     if ((st = mol_step(h, h->io[0], h->io[1], nsteps - 1, stream)) != MOL_OK) return st;
     CK(cudaMemcpyAsync(u_out, h->io[1], sizeof(double) * h->N, cudaMemcpyDeviceToHost, s), "device to host copy");
     CK(cudaStreamSynchronize(s), "solve");
+    return MOL_OK;
+}
+
+mol_status mol_autotune(mol_handle h, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    // candidates that change something for this grid
+    int dummy = 0, r0 = 0, S0 = 0, K0 = 0;
+    const bool res = h->ndim >= 2 && regs_res_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, &dummy);
+    bool strided = false;
+    for (int a = 1; a < h->ndim; ++a) strided |= regs_strided_plan(h->tbytes, h->bc, (int)h->n[a], &r0, &S0, &K0);
+    std::vector<int> warps_c = res ? std::vector<int>{1, 2, 4} : std::vector<int>{h->tune_res_warps};
+    std::vector<std::pair<int, int>> str_c = {{h->tune_strided_rpt, h->tune_strided_warps}};
+    if (strided) {
+        str_c = {{0, 8}, {0, 4}};
+        if (h->tbytes == 4) { str_c.push_back({32, 8}); str_c.push_back({32, 4}); }
+    }
+    for (int k = 0; k < 3; ++k) {
+        const size_t bytes = (size_t)h->tbytes * h->N;
+        if (h->lev[k].hi) CK(cudaMemsetAsync(h->lev[k].hi, 0, bytes, s), "memset");
+        if (h->lev[k].lo) CK(cudaMemsetAsync(h->lev[k].lo, 0, bytes, s), "memset");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "event create");
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(h, MOL_ECUDA, "event create"); }
+    const bool was_timing = h->timing;
+    h->timing = false;
+    const int64_t launches0 = h->launches;
+    double best = 1e30;
+    int bw = h->tune_res_warps, br = h->tune_strided_rpt, bsw = h->tune_strided_warps;
+    mol_status st = MOL_OK;
+    for (int w : warps_c) {
+        for (auto &sc : str_c) {
+            int rr = 0, SS = 0, KK = 0;
+            bool ok = true;
+            for (int a = 1; a < h->ndim && strided; ++a)
+                ok &= regs_strided_plan(h->tbytes, h->bc, (int)h->n[a], &rr, &SS, &KK, sc.first, sc.second);
+            if (!ok) continue;
+            h->tune_res_warps = w;
+            h->tune_strided_rpt = sc.first;
+            h->tune_strided_warps = sc.second;
+            // 2 warm-up steps, then the minimum of 3 timings of 3 steps
+            double t = 1e30;
+            for (int rep = 0; rep < 4 && st == MOL_OK; ++rep) {
+                if (rep > 0 && cudaEventRecord(e0, s) != cudaSuccess) { st = fail(h, MOL_ECUDA, "event record"); break; }
+                for (int k = 0; k < (rep == 0 ? 2 : 3) && st == MOL_OK; ++k)
+                    st = run_update(h, h->lev[(k + 1) % 3], h->lev[k % 3], h->lev[(k + 2) % 3], 2.0, -1.0, 1.0, s);
+                if (st != MOL_OK) break;
+                if (rep > 0) {
+                    float ms = 0.f;
+                    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        st = fail(h, MOL_ECUDA, "tuning timer");
+                        break;
+                    }
+                    t = std::min(t, (double)ms / 3.0);
+                }
+            }
+            if (st != MOL_OK) break;
+            if (t < best) { best = t; bw = w; br = sc.first; bsw = sc.second; }
+        }
+        if (st != MOL_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->timing = was_timing;
+    h->launches = launches0;
+    h->tune_res_warps = bw;
+    h->tune_strided_rpt = br;
+    h->tune_strided_warps = bsw;
+    h->tune_ms = best < 1e30 ? best : 0.0;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // rebuilt with the choice
+    return st;
+}
+
+mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int strided_warps)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (res_warps != 1 && res_warps != 2 && res_warps != 4) return fail(h, MOL_EINVAL, "res_warps must be 1, 2 or 4");
+    if (strided_rpt != 0 && strided_rpt != 32) return fail(h, MOL_EINVAL, "strided_rpt must be 0 or 32");
+    if (strided_warps < 1 || strided_warps > 8) return fail(h, MOL_EINVAL, "strided_warps must be in 1..8");
+    for (int a = 1; a < h->ndim; ++a) {
+        int r = 0, S = 0, K = 0;
+        const int n = (int)h->n[a];
+        // a choice must keep every strided axis that has a register plan on one
+        if (regs_strided_plan(h->tbytes, h->bc, n, &r, &S, &K) &&
+            !regs_strided_plan(h->tbytes, h->bc, n, &r, &S, &K, strided_rpt, strided_warps))
+            return fail(h, MOL_EINVAL, "the strided choice does not fit an axis of this grid");
+    }
+    h->tune_res_warps = res_warps;
+    h->tune_strided_rpt = strided_rpt;
+    h->tune_strided_warps = strided_warps;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    return MOL_OK;
+}
+
+mol_status mol_get_tuning(mol_handle h, int out[3], double *ms_per_step)
+{
+    if (!h || !out) return fail(h, MOL_EINVAL, "NULL argument");
+    out[0] = h->tune_res_warps;
+    out[1] = h->tune_strided_rpt;
+    out[2] = h->tune_strided_warps;
+    if (ms_per_step) *ms_per_step = h->tune_ms;
     return MOL_OK;
 }
 

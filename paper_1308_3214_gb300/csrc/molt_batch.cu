@@ -52,6 +52,9 @@ struct mol_batch_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     std::string err;
     int x_launches() const { return (rows_small > 0 ? 1 : 0) + (nrows > rows_small ? 1 : 0); }
+    int smem_sm = 228 * 1024, smem_blk = 227 * 1024;
+    int ymode = 0;                      // y segment rule: 0 smallest covering RPT, 1 twice that (<= 64)
+    double tune_ms[2] = {0.0, 0.0};     // tuned x / y pass times
 };
 
 namespace {
@@ -107,11 +110,35 @@ int pick_rpt_x(int n)
     while (32 * r < n) r *= 2;
     return r;
 }
-int pick_rpt_y(int n)
+int pick_rpt_y(int n, int mode = 0)
 {
     int r = 4;
     while (kBatchYWarps * r < n) r *= 2;
+    if (mode == 1 && r < 64) r *= 2;
     return r;
+}
+
+// per-problem y-pass segment constants for the current rule
+void set_y_segments(mol_batch_ctx *b)
+{
+    for (BatchProb &pb : b->hp) {
+        pb.rpt_y = pick_rpt_y(pb.ay.n, b->ymode);
+        const double nuy = -std::log(pb.ay.d);
+        for (int k = 0; k < 5; ++k) pb.ay.dm[k] = std::exp(-nuy * (double)pb.rpt_y * (double)(1 << k));
+    }
+}
+
+// x-pass launch shape L (0: rows of <= 512 points, 1: longer rows) for W warps per CTA
+bool set_x_shape(mol_batch_ctx *b, int L, int W)
+{
+    const int ctas = L == 0 ? 2 : 1;
+    const size_t bytes = batch_x_smem((size_t)b->tbytes, W, b->nbuf);
+    if (W < 1 || W > 8 || bytes > (size_t)b->smem_blk || ctas * (bytes + 1024) > (size_t)b->smem_sm) return false;
+    b->xW[L] = W;
+    b->xsmem[L] = bytes;
+    const int64_t nr = L == 0 ? b->rows_small : b->nrows - b->rows_small;
+    b->xgrid[L] = (int)std::max<int64_t>(1, std::min<int64_t>((nr + W - 1) / W, ctas * (int64_t)b->num_sms));
+    return true;
 }
 
 cudaEvent_t btake_event(mol_batch_ctx *b)
@@ -513,16 +540,12 @@ mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, c
         // launch shapes: x pass W warps per CTA with two CTAs per SM when the
         // field buffers allow it; y pass one 16-warp CTA per SM
         b->nbuf = b->Pmax;
-        const size_t per_warp = batch_x_smem((size_t)b->tbytes, 1, b->nbuf);
+        b->smem_sm = smem_sm;
+        b->smem_blk = smem_blk;
         for (int L = 0; L < 2; ++L) {
-            const int ctas = L == 0 ? 2 : 1;       // CTAs per SM the register budget allows
-            int W = 8;
-            while (W > 1 && ctas * (W * per_warp + 1024) > (size_t)smem_sm) --W;
-            b->xW[L] = W;
-            b->xsmem[L] = batch_x_smem((size_t)b->tbytes, W, b->nbuf);
-            if (b->xsmem[L] > (size_t)smem_blk) { st = bfail(b, MOL_EINVAL, "x-pass buffers exceed shared memory"); goto bad; }
-            const int64_t nr = L == 0 ? b->rows_small : b->nrows - b->rows_small;
-            b->xgrid[L] = (int)std::max<int64_t>(1, std::min<int64_t>((nr + W - 1) / W, ctas * (int64_t)b->num_sms));
+            int W = 8;                             // the most warps per CTA that fit
+            while (W > 1 && !set_x_shape(b, L, W)) --W;
+            if (!set_x_shape(b, L, W)) { st = bfail(b, MOL_EINVAL, "x-pass buffers exceed shared memory"); goto bad; }
         }
         b->ygrid = std::min(b->nitems_y, b->num_sms);
         b->ysmem = batch_y_smem((size_t)b->tbytes);
@@ -713,6 +736,85 @@ mol_status mol_batch_sync(mol_batch b, void *stream)
 }
 
 int64_t mol_batch_launch_count(mol_batch b) { return b ? b->launches : 0; }
+
+// x and y pass times (ms per launch, minimum over 3 steps) with the current choices
+static mol_status batch_pass_ms(mol_batch b, cudaStream_t s, double out[2])
+{
+    const bool was = b->timing;
+    for (auto &u : b->ev_used) { b->ev_pool.push_back(u.second.first); b->ev_pool.push_back(u.second.second); }
+    b->ev_used.clear();
+    b->timing = true;
+    mol_status st = MOL_OK;
+    for (int k = 0; k < 4 && st == MOL_OK; ++k)
+        st = run_update(b, b->lev[(k + 1) % 3], b->lev[k % 3], b->lev[(k + 2) % 3], 2.0, -1.0, 1.0, s);
+    out[0] = out[1] = 1e30;
+    if (st == MOL_OK) {
+        int idx = 0;
+        for (auto &u : b->ev_used) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(u.second.second) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, u.second.first, u.second.second) != cudaSuccess) {
+                st = bfail(b, MOL_ECUDA, "tuning timer");
+                break;
+            }
+            if (idx++ >= 2) out[u.first] = std::min(out[u.first], (double)ms);   // the first step warms up
+        }
+    }
+    for (auto &u : b->ev_used) { b->ev_pool.push_back(u.second.first); b->ev_pool.push_back(u.second.second); }
+    b->ev_used.clear();
+    b->timing = was;
+    return st;
+}
+
+mol_status mol_batch_autotune(mol_batch b, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    mol_status st;
+    for (int k = 0; k < 3; ++k)
+        if ((st = zero_level(b, b->lev[k], s)) != MOL_OK) return st;
+    const int64_t launches0 = b->launches;
+    double t[2];
+    // warps per CTA of each x launch (the other held), then the y segment rule
+    for (int L = 0; L < 2; ++L) {
+        if ((L == 0 && b->rows_small == 0) || (L == 1 && b->nrows == b->rows_small)) continue;
+        int bestW = b->xW[L];
+        double best = 1e30;
+        for (int W : {2, 4, 8}) {
+            if (!set_x_shape(b, L, W)) continue;
+            if ((st = batch_pass_ms(b, s, t)) != MOL_OK) return st;
+            if (t[0] < best) { best = t[0]; bestW = W; }
+        }
+        set_x_shape(b, L, bestW);
+        b->tune_ms[0] = best;
+    }
+    int bestY = b->ymode;
+    double besty = 1e30;
+    for (int mode : {0, 1}) {
+        b->ymode = mode;
+        set_y_segments(b);
+        BCK(cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice), "table upload");
+        if ((st = batch_pass_ms(b, s, t)) != MOL_OK) return st;
+        if (t[1] < besty) { besty = t[1]; bestY = mode; }
+    }
+    b->ymode = bestY;
+    set_y_segments(b);
+    BCK(cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice), "table upload");
+    b->tune_ms[1] = besty;
+    b->launches = launches0;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    return MOL_OK;
+}
+
+mol_status mol_batch_get_tuning(mol_batch b, int out[3], double ms[2])
+{
+    if (!b || !out) return bfail(b, MOL_EINVAL, "NULL argument");
+    out[0] = b->xW[0];
+    out[1] = b->xW[1];
+    out[2] = b->ymode;
+    if (ms) { ms[0] = b->tune_ms[0]; ms[1] = b->tune_ms[1]; }
+    return MOL_OK;
+}
 
 mol_status mol_batch_set_pass_timing(mol_batch b, int enable)
 {

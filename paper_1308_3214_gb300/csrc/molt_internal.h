@@ -42,7 +42,9 @@ int line_stride(int ms, int W, int tbytes);
 // Register-resident kernels (molt_regs.cu).  The *_plan functions say whether
 // a line of n points is supported and with which segment decomposition.
 bool regs_contig_plan(int tbytes, int bc, int n, int *rpt);
-bool regs_strided_plan(int tbytes, int bc, int n, int *rpt, int *S, int *K);
+// pref_rpt: 0 = default segment length (or 32 for float lines, a tuner
+// choice); max_warps: segments per CTA at most (1..8)
+bool regs_strided_plan(int tbytes, int bc, int n, int *rpt, int *S, int *K, int pref_rpt = 0, int max_warps = 8);
 size_t regs_strided_smem(int tbytes, int S, int rpt, bool horner);
 cudaError_t launch_contig(int tbytes, int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
                           cudaStream_t s);
@@ -50,6 +52,7 @@ cudaError_t launch_strided(int tbytes, int bc, int rpt, const AxisDev &A, const 
                            cudaStream_t s);
 cudaError_t configure_regs_kernels();
 bool regs_res_plan(int tbytes, int n, int ng, int *rpt);
-cudaError_t launch_res(int bc, int rpt, int ng, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s);
+cudaError_t launch_res(int bc, int rpt, int ng, int warps, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                       cudaStream_t s);
 
 }  // namespace molt

@@ -7,24 +7,24 @@ namespace molt {
 namespace {
 
 constexpr int kContigWarps = 4;
-constexpr int kResWarps = 2;
+constexpr int kResWarpsMax = 4;
 
 template <int RPT, int NB>
-size_t res_smem() { return (size_t)kResWarps * NB * ContigStage<float, RPT>::LINE * sizeof(float); }
+size_t res_smem(int warps) { return (size_t)warps * NB * ContigStage<float, RPT>::LINE * sizeof(float); }
 
 template <int BC, int RPT, int NB>
-cudaError_t run_res(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+cudaError_t run_res(int warps, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
 {
-    const int64_t grid = (L.nlines + kResWarps - 1) / kResWarps;
-    k_contig_res<BC, RPT, NB, kResWarps><<<(unsigned)grid, 32 * kResWarps, res_smem<RPT, NB>(), s>>>(A, L, p);
+    const int64_t grid = (L.nlines + warps - 1) / warps;
+    k_contig_res<BC, RPT, NB><<<(unsigned)grid, 32 * warps, res_smem<RPT, NB>(warps), s>>>(A, L, p);
     return cudaGetLastError();
 }
 
 template <int BC, int RPT, int NB>
 cudaError_t attr_res()
 {
-    return cudaFuncSetAttribute(k_contig_res<BC, RPT, NB, kResWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)res_smem<RPT, NB>());
+    return cudaFuncSetAttribute(k_contig_res<BC, RPT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)res_smem<RPT, NB>(kResWarpsMax));
 }
 
 template <class T, int RPT>
@@ -77,8 +77,9 @@ cudaError_t attr_strided()
 }  // namespace
 
 // Segment lengths: contiguous lines use the smallest RPT with 32*RPT >= n;
-// strided lines use 64 (float) / 32 (double) points per thread.
-constexpr int kStridedRptF = 64, kStridedRptD = 32;
+// strided lines use 64 (float) / 32 (double) points per thread by default,
+// or 32 (float) as an alternative the tuner may pick.
+constexpr int kStridedRptF = 64, kStridedRptF2 = 32, kStridedRptD = 32;
 
 // Register kernels need whole segments: n a multiple of RPT (both boundary
 // conditions keep the line ends at fixed register positions).
@@ -94,13 +95,15 @@ bool regs_contig_plan(int tbytes, int, int n, int *rpt)
     return false;
 }
 
-bool regs_strided_plan(int tbytes, int, int n, int *rpt, int *S, int *K)
+bool regs_strided_plan(int tbytes, int, int n, int *rpt, int *S, int *K, int pref_rpt, int max_warps)
 {
-    const int r = tbytes == 4 ? kStridedRptF : kStridedRptD;
+    int r = tbytes == 4 ? kStridedRptF : kStridedRptD;
+    if (tbytes == 4 && pref_rpt == kStridedRptF2) r = kStridedRptF2;
     if (n % r != 0) return false;
+    const int mw = (max_warps >= 1 && max_warps <= 8) ? max_warps : 8;
     const int G = n / r;
-    const int k = (G + 7) / 8;      // at most 8 warps per CTA
-    if (k > 8) return false;        // portable cluster size
+    const int k = (G + mw - 1) / mw;  // at most mw warps per CTA
+    if (k > 8) return false;          // portable cluster size
     *rpt = r;
     *S = (G + k - 1) / k;
     *K = k;
@@ -146,6 +149,9 @@ cudaError_t launch_strided(int tbytes, int bc, int rpt, const AxisDev &A, const 
     if (tbytes == 4 && rpt == kStridedRptF)
         return bc == BC_PERIODIC ? run_strided<float, BC_PERIODIC, kStridedRptF>(A, L, p, s)
                                  : run_strided<float, BC_DIRICHLET, kStridedRptF>(A, L, p, s);
+    if (tbytes == 4 && rpt == kStridedRptF2)
+        return bc == BC_PERIODIC ? run_strided<float, BC_PERIODIC, kStridedRptF2>(A, L, p, s)
+                                 : run_strided<float, BC_DIRICHLET, kStridedRptF2>(A, L, p, s);
     if (tbytes == 8 && rpt == kStridedRptD)
         return bc == BC_PERIODIC ? run_strided<double, BC_PERIODIC, kStridedRptD>(A, L, p, s)
                                  : run_strided<double, BC_DIRICHLET, kStridedRptD>(A, L, p, s);
@@ -165,22 +171,24 @@ bool regs_res_plan(int tbytes, int n, int ng, int *rpt)
     return false;
 }
 
-cudaError_t launch_res(int bc, int rpt, int ng, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+cudaError_t launch_res(int bc, int rpt, int ng, int warps, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                       cudaStream_t s)
 {
+    if (warps < 1 || warps > kResWarpsMax) warps = 2;
 #define MOLT_RES(BC)                                                                      \
     switch (rpt * 10 + (ng < 1 ? 1 : ng)) {                                               \
-    case 81: return run_res<BC, 8, 1>(A, L, p, s);                                        \
-    case 82: return run_res<BC, 8, 2>(A, L, p, s);                                        \
-    case 83: return run_res<BC, 8, 3>(A, L, p, s);                                        \
-    case 161: return run_res<BC, 16, 1>(A, L, p, s);                                      \
-    case 162: return run_res<BC, 16, 2>(A, L, p, s);                                      \
-    case 163: return run_res<BC, 16, 3>(A, L, p, s);                                      \
-    case 321: return run_res<BC, 32, 1>(A, L, p, s);                                      \
-    case 322: return run_res<BC, 32, 2>(A, L, p, s);                                      \
-    case 323: return run_res<BC, 32, 3>(A, L, p, s);                                      \
-    case 641: return run_res<BC, 64, 1>(A, L, p, s);                                      \
-    case 642: return run_res<BC, 64, 2>(A, L, p, s);                                      \
-    case 643: return run_res<BC, 64, 3>(A, L, p, s);                                      \
+    case 81: return run_res<BC, 8, 1>(warps, A, L, p, s);                                 \
+    case 82: return run_res<BC, 8, 2>(warps, A, L, p, s);                                 \
+    case 83: return run_res<BC, 8, 3>(warps, A, L, p, s);                                 \
+    case 161: return run_res<BC, 16, 1>(warps, A, L, p, s);                               \
+    case 162: return run_res<BC, 16, 2>(warps, A, L, p, s);                               \
+    case 163: return run_res<BC, 16, 3>(warps, A, L, p, s);                               \
+    case 321: return run_res<BC, 32, 1>(warps, A, L, p, s);                               \
+    case 322: return run_res<BC, 32, 2>(warps, A, L, p, s);                               \
+    case 323: return run_res<BC, 32, 3>(warps, A, L, p, s);                               \
+    case 641: return run_res<BC, 64, 1>(warps, A, L, p, s);                               \
+    case 642: return run_res<BC, 64, 2>(warps, A, L, p, s);                               \
+    case 643: return run_res<BC, 64, 3>(warps, A, L, p, s);                               \
     default: break;                                                                       \
     }
     if (bc == BC_PERIODIC) { MOLT_RES(BC_PERIODIC) }
@@ -208,6 +216,7 @@ cudaError_t configure_regs_kernels()
     MOLT_A((attr_contig<double, BC_DIRICHLET, 8>())) MOLT_A((attr_contig<double, BC_DIRICHLET, 16>()))
     MOLT_A((attr_contig<double, BC_DIRICHLET, 32>()))
     MOLT_A((attr_strided<float, BC_PERIODIC, kStridedRptF>())) MOLT_A((attr_strided<float, BC_DIRICHLET, kStridedRptF>()))
+    MOLT_A((attr_strided<float, BC_PERIODIC, kStridedRptF2>())) MOLT_A((attr_strided<float, BC_DIRICHLET, kStridedRptF2>()))
     MOLT_A((attr_strided<double, BC_PERIODIC, kStridedRptD>())) MOLT_A((attr_strided<double, BC_DIRICHLET, kStridedRptD>()))
 #undef MOLT_A
     return cudaSuccess;

@@ -755,8 +755,9 @@ __device__ __forceinline__ float4 sdiff4(const float4 &h, const float4 &l, float
     return r;
 }
 
-template <int BC, int RPT, int NB, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_contig_res(AxisDev A, LineSet LS, ProgParams pr)
+// Up to 4 warps per CTA (the warps per CTA are a launch choice: blockDim.x / 32)
+template <int BC, int RPT, int NB>
+__global__ void __launch_bounds__(128) k_contig_res(AxisDev A, LineSet LS, ProgParams pr)
 {
     static_assert(RPT % 4 == 0 && RPT >= 8, "segment length");
     using T = float;
@@ -767,7 +768,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_contig_res(AxisDev A, LineSet LS
     T *B = reinterpret_cast<T *>(smem_raw) + (size_t)warp * NB * St::LINE;   // NB field buffers
     T *R = B;                                    // staging for r before field 0 lands there
     const int n = A.n;
-    const int64_t L = (int64_t)blockIdx.x * WARPS + warp;
+    const int64_t L = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (L >= LS.nlines) return;
     const int64_t base = L * (int64_t)n;
     const int nvec = n / 4;

@@ -32,7 +32,8 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_apply_F_noalloc", "mol_batch_create", "mol_batch_destroy", "mol_batch_last_error",
            "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
            "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times", "mol_batch_apply_FT",
-           "mol_batch_traces", "mol_batch_adjoint", "mol_batch_update"]
+           "mol_batch_traces", "mol_batch_adjoint", "mol_batch_update", "mol_autotune", "mol_get_tuning", "mol_set_tuning",
+           "mol_batch_autotune", "mol_batch_get_tuning"]
 
 
 class MolError(RuntimeError):
@@ -107,6 +108,11 @@ def load_library(path: Path | None = None):
     lib.mol_batch_traces.argtypes = [vp, vp, I, ctypes.POINTER(i64), i64, vp, vp]
     lib.mol_batch_adjoint.argtypes = [vp, I, ctypes.POINTER(i64), i64, vp, vp, vp]
     lib.mol_batch_update.argtypes = [vp, vp, vp, vp, D, D, D, I, vp, vp]
+    lib.mol_autotune.argtypes = [vp, vp]
+    lib.mol_get_tuning.argtypes = [vp, ctypes.POINTER(I), dp]
+    lib.mol_set_tuning.argtypes = [vp, I, I, I]
+    lib.mol_batch_autotune.argtypes = [vp, vp]
+    lib.mol_batch_get_tuning.argtypes = [vp, ctypes.POINTER(I), dp]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
@@ -251,6 +257,20 @@ class Solver:
         self._check(self.lib.mol_solve_host(self.h, u0.ctypes.data_as(dp), out.ctypes.data_as(dp), int(nsteps),
                                             ctypes.c_void_p(_stream_ptr(stream))))
         return out
+
+    def autotune(self, stream=None) -> dict:
+        """Time the launch variants on this grid and keep the fastest."""
+        self._check(self.lib.mol_autotune(self.h, ctypes.c_void_p(_stream_ptr(stream))))
+        return self.tuning()
+
+    def set_tuning(self, res_warps: int = 2, strided_rpt: int = 0, strided_warps: int = 8):
+        self._check(self.lib.mol_set_tuning(self.h, int(res_warps), int(strided_rpt), int(strided_warps)))
+
+    def tuning(self) -> dict:
+        out = (ctypes.c_int * 3)()
+        ms = ctypes.c_double()
+        self._check(self.lib.mol_get_tuning(self.h, out, ctypes.byref(ms)))
+        return {"res_warps": out[0], "strided_rpt": out[1], "strided_warps": out[2], "ms_per_step": ms.value}
 
     def sync(self, stream=None):
         self._check(self.lib.mol_sync(self.h, ctypes.c_void_p(_stream_ptr(stream))))
@@ -433,6 +453,17 @@ class BatchSolver:
         self._check(self.lib.mol_batch_solve_host(self.h, u0.ctypes.data_as(dp), out.ctypes.data_as(dp), int(nsteps),
                                                   ctypes.c_void_p(_stream_ptr(stream))))
         return out
+
+    def autotune(self, stream=None) -> dict:
+        """Time the launch variants on this batch and keep the fastest."""
+        self._check(self.lib.mol_batch_autotune(self.h, ctypes.c_void_p(_stream_ptr(stream))))
+        return self.tuning()
+
+    def tuning(self) -> dict:
+        out = (ctypes.c_int * 3)()
+        ms = (ctypes.c_double * 2)()
+        self._check(self.lib.mol_batch_get_tuning(self.h, out, ms))
+        return {"x_warps": [out[0], out[1]], "y_rule": out[2], "x_ms": ms[0], "y_ms": ms[1]}
 
     def sync(self, stream=None):
         self._check(self.lib.mol_batch_sync(self.h, ctypes.c_void_p(_stream_ptr(stream))))

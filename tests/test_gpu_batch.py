@@ -190,3 +190,15 @@ def test_batch_full_size_512_problems_sampled():
     for i, p in enumerate(probs):
         nu = oracle.beta_max(p.P) / dts[i] / (p.n - 1)
         assert rel_l2(res["mixed"][i], res["fp64"][i]) <= mixed_tol((nu, nu), 2 * p.P), i
+
+
+def test_batch_autotune_choice_keeps_parity():
+    b, specs = make_batch(SHAPES, "mixed")
+    tun = b.autotune()
+    assert all(w in (2, 4, 8) for w in tun["x_warps"]) and tun["y_rule"] in (0, 1)
+    assert tun["x_ms"] > 0 and tun["y_ms"] > 0
+    us = [rough_field(s, 900 + i) for i, s in enumerate(SHAPES)]
+    got = b.unpack(b.apply_F(b.pack(us)))
+    for i, (u, g, (P, dt, beta, nu)) in enumerate(zip(us, got, specs)):
+        ref = oracle.F(u, nu, P, beta, "dirichlet")
+        assert rel_l2(g.cpu().numpy(), ref) <= mixed_tol(nu, 2 * P), i

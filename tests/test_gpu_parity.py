@@ -328,3 +328,42 @@ def test_register_kernels_F_and_steps(shape, P, bc, prec):
             a, b = b, 2 * b - a + F
         tol = 8 * EPS32 * (1 + 1 / (1 - max(s.d))) * 2 * P * Fsum / np.linalg.norm(rc)
     assert rel_l2(uc.cpu().numpy(), rc) <= tol
+
+
+# ---------------------------------------------------------------------------
+# autotuner
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_autotune_choice_keeps_parity(prec):
+    shape, P, bc, nsteps, dt = (256, 512), 3, "dirichlet", 6, 0.004
+    s = make(shape, dt, P, bc, prec)
+    tun = s.autotune()
+    assert tun["res_warps"] in (1, 2, 4) and tun["strided_warps"] in (4, 8) and tun["strided_rpt"] in (0, 32)
+    assert tun["ms_per_step"] > 0
+    u0 = smooth_field(shape, 7, bc) + 0.05 * field(shape, 8, bc)
+    u1 = oracle.start(u0, s.nu, P, s.beta, bc)
+    up, uc = dev(u0), dev(u1)
+    s.step(up, uc, nsteps)
+    rp, rc = oracle.run(u0, u1, nsteps, s.nu, P, s.beta, bc)
+    tol = 1e-12
+    if prec == "mixed":
+        Fsum, a, b = 0.0, u0, u1
+        for _ in range(nsteps):
+            F = oracle.F(b, s.nu, P, s.beta, bc)
+            Fsum += np.linalg.norm(F)
+            a, b = b, 2 * b - a + F
+        tol = 8 * EPS32 * (1 + 1 / (1 - max(s.d))) * 2 * P * Fsum / np.linalg.norm(rc)
+    assert rel_l2(uc.cpu().numpy(), rc) <= tol
+
+
+@pytest.mark.parametrize("rpt,warps", [(0, 8), (0, 4), (32, 8), (32, 4)])
+def test_every_strided_choice_matches_oracle(rpt, warps):
+    """Each strided segmenting the tuner may pick (segment length, segments
+    per CTA, hence the cluster size) applies D_y^2 correctly."""
+    shape, bc = (1024, 96), "dirichlet"
+    s = make(shape, 0.002, 2, bc, "mixed")
+    s.set_tuning(res_warps=2, strided_rpt=rpt, strided_warps=warps)
+    v = field(shape, 40, bc)
+    ref = oracle.D_axis(v, 1, s.nu[1], bc, 2, power=2)
+    got = s.apply_D(dev(v), 1, 2).cpu().numpy()
+    assert rel_l2(got, ref) <= tol_for("mixed", s, 2)
