@@ -99,6 +99,10 @@ void mol_default_options(mol_options *opt);
 mol_status mol_create(const mol_grid *grid, double c, double dt, double beta, int P,
                       mol_bc bc, mol_prec prec, const mol_options *opt, mol_handle *out);
 
+/* (2D Dirichlet grids with at most 1024 points per axis whose lines do not
+ * split into whole register segments run mol_apply_F, mol_start, mol_step
+ * and mol_solve_host on the batched kernels, as a batch of one problem.) */
+
 /* Free the workspace and the handle (waits for the handle's work). */
 mol_status mol_destroy(mol_handle h);
 

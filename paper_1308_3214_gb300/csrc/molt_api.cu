@@ -57,6 +57,10 @@ struct mol_ctx {
     // strided segment length (0 = default) and segments per CTA at most
     int tune_res_warps = 2, tune_strided_rpt = 0, tune_strided_warps = 8;
     double tune_ms = 0.0;                      // step time of the chosen configuration
+    // 2D Dirichlet grids (n <= 1024 per axis) whose lines the register
+    // kernels cannot split into whole segments run on the batched kernels
+    // (ragged lines) as a batch of one problem
+    mol_batch batch = nullptr;
     bool timing = false;                       // per-pass events (benchmarks)
     std::vector<cudaEvent_t> ev_pool;          // reusable events
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (axis, (start, stop))
@@ -109,6 +113,7 @@ mol_status dev_alloc(mol_ctx *h, void **p, size_t bytes)
 
 void free_all(mol_ctx *h)
 {
+    if (h->batch) { mol_batch_destroy(h->batch); h->batch = nullptr; }
     for (auto &u : h->ev_used) { h->ev_pool.push_back(u.second.first); h->ev_pool.push_back(u.second.second); }
     h->ev_used.clear();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -577,6 +582,18 @@ mol_status mol_create(const mol_grid *grid, double c, double dt, double beta, in
         for (int k = 0; k < ninter; ++k)
             if ((st = dev_alloc(h, &h->inter[k], (size_t)h->tbytes * h->N)) != MOL_OK) goto bad;
     }
+    if (h->ndim == 2 && bc == MOL_BC_DIRICHLET && h->n[0] <= 1024 && h->n[1] <= 1024) {
+        int r = 0, S = 0, K = 0;
+        const bool xreg = regs_res_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, &r) ||
+                          regs_contig_plan(h->tbytes, h->bc, (int)h->n[0], &r);
+        const bool yreg = regs_strided_plan(h->tbytes, h->bc, (int)h->n[1], &r, &S, &K);
+        if (!xreg || !yreg) {
+            if ((st = mol_batch_create(1, grid, &c, &dt, &beta, &P, bc, prec, &o, &h->batch)) != MOL_OK) {
+                h->err = mol_last_error(nullptr);
+                goto bad;
+            }
+        }
+    }
     *out = h;
     return MOL_OK;
 bad:
@@ -635,6 +652,11 @@ mol_status mol_apply_D(mol_handle h, const double *v, double *outp, int axis, in
 mol_status mol_apply_F(mol_handle h, const double *u, double *F, void *stream)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (h->batch) {
+        const mol_status st0 = mol_batch_apply_F(h->batch, u, F, stream);
+        if (st0 != MOL_OK) h->err = mol_batch_last_error(h->batch);
+        return st0;
+    }
     mol_status st;
     if ((st = check_ptr(h, u, "u")) != MOL_OK || (st = check_ptr(h, F, "F")) != MOL_OK) return st;
     if (u == F) return fail(h, MOL_EINVAL, "u and F must not overlap");
@@ -653,6 +675,11 @@ mol_status mol_apply_F(mol_handle h, const double *u, double *F, void *stream)
 mol_status mol_start(mol_handle h, const double *u0, double *u1, void *stream)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (h->batch) {
+        const mol_status st0 = mol_batch_start(h->batch, u0, u1, stream);
+        if (st0 != MOL_OK) h->err = mol_batch_last_error(h->batch);
+        return st0;
+    }
     mol_status st;
     if ((st = check_ptr(h, u0, "u0")) != MOL_OK || (st = check_ptr(h, u1, "u1")) != MOL_OK) return st;
     if (u0 == u1) return fail(h, MOL_EINVAL, "u0 and u1 must not overlap");
@@ -671,6 +698,11 @@ mol_status mol_start(mol_handle h, const double *u0, double *u1, void *stream)
 mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps, void *stream)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (h->batch) {
+        const mol_status st0 = mol_batch_step(h->batch, u_prev, u_cur, nsteps, stream);
+        if (st0 != MOL_OK) h->err = mol_batch_last_error(h->batch);
+        return st0;
+    }
     if (nsteps < 0) return fail(h, MOL_EINVAL, "nsteps must be >= 0");
     mol_status st;
     if ((st = check_ptr(h, u_prev, "u_prev")) != MOL_OK || (st = check_ptr(h, u_cur, "u_cur")) != MOL_OK) return st;
@@ -700,6 +732,11 @@ mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps,
 mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t nsteps, void *stream)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (h->batch) {
+        const mol_status st0 = mol_batch_solve_host(h->batch, u0, u_out, nsteps, stream);
+        if (st0 != MOL_OK) h->err = mol_batch_last_error(h->batch);
+        return st0;
+    }
     if (!u0 || !u_out) return fail(h, MOL_EINVAL, "NULL host buffer");
     if (nsteps < 1) return fail(h, MOL_EINVAL, "nsteps must be >= 1");
     mol_status st;
@@ -717,6 +754,16 @@ mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t
 mol_status mol_autotune(mol_handle h, void *stream)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (h->batch) {
+        const mol_status st0 = mol_batch_autotune(h->batch, stream);
+        double ms[2] = {0.0, 0.0};
+        if (st0 == MOL_OK) {
+            int out[3];
+            mol_batch_get_tuning(h->batch, out, ms);
+            h->tune_ms = ms[0] + ms[1];
+        }
+        return st0;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     // candidates that change something for this grid
     int dummy = 0, r0 = 0, S0 = 0, K0 = 0;
@@ -826,11 +873,12 @@ mol_status mol_sync(mol_handle h, void *stream)
     return MOL_OK;
 }
 
-int64_t mol_launch_count(mol_handle h) { return h ? h->launches : 0; }
+int64_t mol_launch_count(mol_handle h) { return h ? h->launches + (h->batch ? mol_batch_launch_count(h->batch) : 0) : 0; }
 
 mol_status mol_set_pass_timing(mol_handle h, int enable)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (h->batch) return mol_batch_set_pass_timing(h->batch, enable);
     for (auto &u : h->ev_used) { h->ev_pool.push_back(u.second.first); h->ev_pool.push_back(u.second.second); }
     h->ev_used.clear();
     h->timing = enable != 0;
@@ -840,6 +888,7 @@ mol_status mol_set_pass_timing(mol_handle h, int enable)
 mol_status mol_pass_times(mol_handle h, double total_ms[3], int64_t launches[3])
 {
     if (!h || !total_ms || !launches) return fail(h, MOL_EINVAL, "NULL argument");
+    if (h->batch) return mol_batch_pass_times(h->batch, total_ms, launches);
     for (int a = 0; a < 3; ++a) { total_ms[a] = 0.0; launches[a] = 0; }
     for (auto &u : h->ev_used) {
         CK(cudaEventSynchronize(u.second.second), "event synchronize");
