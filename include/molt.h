@@ -171,6 +171,19 @@ mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int stri
  * most; *ms_per_step (may be NULL) = the tuned step time (0 before tuning). */
 mol_status mol_get_tuning(mol_handle h, int out[3], double *ms_per_step);
 
+/*
+ * Adjoint on a single-problem handle (2D Dirichlet, at most 1024 points per
+ * axis; MOL_EINVAL otherwise): F^T, receiver traces and the gradient of a
+ * trace loss with respect to the initial field, as mol_batch_apply_FT /
+ * mol_batch_traces / mol_batch_adjoint for a batch of this one problem
+ * (receivers: flat indices y nx + x; host arrays).  The paper has no adjoint.
+ */
+mol_status mol_apply_FT(mol_handle h, const double *w, double *out, void *stream);
+mol_status mol_traces(mol_handle h, const double *u0, int nrec, const int64_t *rec, int64_t nsteps, double *traces,
+                      void *stream);
+mol_status mol_adjoint(mol_handle h, int nrec, const int64_t *rec, int64_t nsteps, const double *tgrad, double *grad,
+                       void *stream);
+
 /* Wait for the handle's work on the stream; reports device-side errors. */
 mol_status mol_sync(mol_handle h, void *stream);
 

@@ -61,6 +61,7 @@ struct mol_ctx {
     // kernels cannot split into whole segments run on the batched kernels
     // (ragged lines) as a batch of one problem
     mol_batch batch = nullptr;
+    mol_batch adj = nullptr;                   // one-problem batch for the adjoint entry points
     bool timing = false;                       // per-pass events (benchmarks)
     std::vector<cudaEvent_t> ev_pool;          // reusable events
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (axis, (start, stop))
@@ -114,6 +115,7 @@ mol_status dev_alloc(mol_ctx *h, void **p, size_t bytes)
 void free_all(mol_ctx *h)
 {
     if (h->batch) { mol_batch_destroy(h->batch); h->batch = nullptr; }
+    if (h->adj) { mol_batch_destroy(h->adj); h->adj = nullptr; }
     for (auto &u : h->ev_used) { h->ev_pool.push_back(u.second.first); h->ev_pool.push_back(u.second.second); }
     h->ev_used.clear();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -863,6 +865,57 @@ mol_status mol_get_tuning(mol_handle h, int out[3], double *ms_per_step)
     out[2] = h->tune_strided_warps;
     if (ms_per_step) *ms_per_step = h->tune_ms;
     return MOL_OK;
+}
+
+// The adjoint runs on the batched kernels (ragged lines, transposed sweeps):
+// the handle's own one-problem batch, or one made on first use.
+static mol_status adjoint_batch(mol_ctx *h, mol_batch *out)
+{
+    if (h->batch) { *out = h->batch; return MOL_OK; }
+    if (!h->adj) {
+        if (h->ndim != 2 || h->bc != MOL_BC_DIRICHLET || h->n[0] > 1024 || h->n[1] > 1024)
+            return fail(h, MOL_EINVAL, "the adjoint entry points take 2D Dirichlet grids of at most 1024 points per axis");
+        mol_grid g{};
+        g.ndim = 2;
+        for (int a = 0; a < 2; ++a) { g.n[a] = h->n[a]; g.lo[a] = h->lo[a]; g.hi[a] = h->hi[a]; }
+        mol_status st = mol_batch_create(1, &g, &h->c, &h->dt, &h->beta, &h->P, MOL_BC_DIRICHLET, (mol_prec)h->prec,
+                                         &h->opt, &h->adj);
+        if (st != MOL_OK) return fail(h, st, mol_last_error(nullptr));
+    }
+    *out = h->adj;
+    return MOL_OK;
+}
+
+mol_status mol_apply_FT(mol_handle h, const double *w, double *out, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_batch b = nullptr;
+    mol_status st = adjoint_batch(h, &b);
+    if (st != MOL_OK) return st;
+    if ((st = mol_batch_apply_FT(b, w, out, stream)) != MOL_OK) h->err = mol_batch_last_error(b);
+    return st;
+}
+
+mol_status mol_traces(mol_handle h, const double *u0, int nrec, const int64_t *rec, int64_t nsteps, double *traces,
+                      void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_batch b = nullptr;
+    mol_status st = adjoint_batch(h, &b);
+    if (st != MOL_OK) return st;
+    if ((st = mol_batch_traces(b, u0, nrec, rec, nsteps, traces, stream)) != MOL_OK) h->err = mol_batch_last_error(b);
+    return st;
+}
+
+mol_status mol_adjoint(mol_handle h, int nrec, const int64_t *rec, int64_t nsteps, const double *tgrad, double *grad,
+                       void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_batch b = nullptr;
+    mol_status st = adjoint_batch(h, &b);
+    if (st != MOL_OK) return st;
+    if ((st = mol_batch_adjoint(b, nrec, rec, nsteps, tgrad, grad, stream)) != MOL_OK) h->err = mol_batch_last_error(b);
+    return st;
 }
 
 mol_status mol_sync(mol_handle h, void *stream)

@@ -33,7 +33,7 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
            "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times", "mol_batch_apply_FT",
            "mol_batch_traces", "mol_batch_adjoint", "mol_batch_update", "mol_autotune", "mol_get_tuning", "mol_set_tuning",
-           "mol_batch_autotune", "mol_batch_get_tuning"]
+           "mol_batch_autotune", "mol_batch_get_tuning", "mol_apply_FT", "mol_traces", "mol_adjoint"]
 
 
 class MolError(RuntimeError):
@@ -112,6 +112,9 @@ def load_library(path: Path | None = None):
     lib.mol_get_tuning.argtypes = [vp, ctypes.POINTER(I), dp]
     lib.mol_set_tuning.argtypes = [vp, I, I, I]
     lib.mol_batch_autotune.argtypes = [vp, vp]
+    lib.mol_apply_FT.argtypes = [vp, vp, vp, vp]
+    lib.mol_traces.argtypes = [vp, vp, I, ctypes.POINTER(i64), i64, vp, vp]
+    lib.mol_adjoint.argtypes = [vp, I, ctypes.POINTER(i64), i64, vp, vp, vp]
     lib.mol_batch_get_tuning.argtypes = [vp, ctypes.POINTER(I), dp]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
@@ -256,6 +259,36 @@ class Solver:
         dp = ctypes.POINTER(ctypes.c_double)
         self._check(self.lib.mol_solve_host(self.h, u0.ctypes.data_as(dp), out.ctypes.data_as(dp), int(nsteps),
                                             ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def apply_FT(self, w, out=None, stream=None):
+        """F^T w (2D Dirichlet grids of at most 1024 points per axis)."""
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_apply_FT(self.h, self._field(w, "w"), self._field(out, "out"),
+                                          ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def traces(self, u0, rec, nsteps: int, stream=None):
+        """(nsteps, nrec): u^n at the flat indices rec (y nx + x), n = 1..nsteps."""
+        import torch
+        rec = np.ascontiguousarray(np.asarray(rec, dtype=np.int64).reshape(-1))
+        out = torch.empty((int(nsteps), rec.size), dtype=torch.float64, device="cuda")
+        self._check(self.lib.mol_traces(self.h, self._field(u0, "u0"), rec.size,
+                                        rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(nsteps),
+                                        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def adjoint(self, rec, tgrad, stream=None):
+        """dJ/du^0 from tgrad[n-1, r] = dJ/d(u^n at rec[r])."""
+        import torch
+        rec = np.ascontiguousarray(np.asarray(rec, dtype=np.int64).reshape(-1))
+        tg = tgrad.to(dtype=torch.float64, device="cuda").contiguous()
+        if tg.dim() != 2 or tg.shape[1] != rec.size:
+            raise ValueError("tgrad must be (nsteps, nrec)")
+        out = self.empty()
+        self._check(self.lib.mol_adjoint(self.h, rec.size, rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         int(tg.shape[0]), ctypes.c_void_p(tg.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
         return out
 
     def autotune(self, stream=None) -> dict:
