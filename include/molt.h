@@ -152,24 +152,28 @@ mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t
 
 /*
  * Autotuner: times the launch variants that change something for this grid
- * -- warps per CTA of the resident x pass (1, 2, 4), the strided segment
- * length (64 or 32 points per thread for float32 sweeps) and the segments
- * per CTA at most (8 or 4, hence the cluster size) -- on the handle's own
- * workspace (a few steps each, CUDA events, minimum of 3 timings) and keeps
- * the fastest for every later call.  Synchronous on the stream; the caller's
- * fields are not touched.  The paper has no counterpart.
+ * -- the float32 x pass with one warp per row (1, 2 or 4 warps per CTA) or
+ * each row split over 2 or 4 warps (rows of 32 W RPT points, RPT 16 or 32),
+ * the strided segment length (64 or 32 points per thread for float32 sweeps)
+ * and the segments per CTA at most (8 or 4, hence the cluster size) -- on the
+ * handle's own workspace (a few steps each, CUDA events, minimum of 3
+ * timings) and keeps the fastest for every later call.  Synchronous on the
+ * stream; the caller's fields are not touched.  The paper has no counterpart.
  */
 mol_status mol_autotune(mol_handle h, void *stream);
 
 /* Force launch choices (e.g. a tuning result kept from an earlier run):
- * res_warps 1, 2 or 4; strided_rpt 0 (default) or 32; strided_warps 1..8.
- * MOL_EINVAL if a choice is out of range or does not fit an axis. */
-mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int strided_warps);
+ * res_warps 1, 2 or 4; strided_rpt 0 (default) or 32; strided_warps 1..8;
+ * rows_warps 0 (one warp per row) or 2, 4 (each row split over that many
+ * warps, where the row length allows it).  MOL_EINVAL if a choice is out of
+ * range or does not fit an axis. */
+mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int strided_warps, int rows_warps);
 
 /* The launch choices in use: out[0] = warps per CTA of the resident x pass,
  * out[1] = strided segment length (0 = default), out[2] = segments per CTA at
- * most; *ms_per_step (may be NULL) = the tuned step time (0 before tuning). */
-mol_status mol_get_tuning(mol_handle h, int out[3], double *ms_per_step);
+ * most, out[3] = warps per row (0 = one); *ms_per_step (may be NULL) = the
+ * tuned step time (0 before tuning). */
+mol_status mol_get_tuning(mol_handle h, int out[4], double *ms_per_step);
 
 /*
  * Adjoint on a single-problem handle (2D Dirichlet, at most 1024 points per

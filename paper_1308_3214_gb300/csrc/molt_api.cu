@@ -56,6 +56,7 @@ struct mol_ctx {
     // launch choices (mol_autotune): warps per CTA of the resident x pass,
     // strided segment length (0 = default) and segments per CTA at most
     int tune_res_warps = 2, tune_strided_rpt = 0, tune_strided_warps = 8;
+    int tune_rows_warps = 0;                   // > 0: the x pass splits each row over this many warps
     double tune_ms = 0.0;                      // step time of the chosen configuration
     // 2D Dirichlet grids (n <= 1024 per axis) whose lines the register
     // kernels cannot split into whole segments run on the batched kernels
@@ -227,7 +228,10 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
     if (st != MOL_OK) return st;
     int rpt = 0, S = 0, K = 0;
     cudaError_t e;
-    if (axis == 0 && pr.mode == 1 && pr.nout == 1 && regs_res_plan(h->tbytes, n, pr.ng, &rpt)) {
+    if (axis == 0 && pr.mode == 1 && pr.nout == 1 && h->tune_rows_warps > 0 &&
+        regs_rows_plan(h->tbytes, n, pr.ng, h->tune_rows_warps, &rpt)) {
+        e = launch_rows(h->bc, rpt, pr.ng, h->tune_rows_warps, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
+    } else if (axis == 0 && pr.mode == 1 && pr.nout == 1 && regs_res_plan(h->tbytes, n, pr.ng, &rpt)) {
         e = launch_res(h->bc, rpt, pr.ng, h->tune_res_warps, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
     } else if (axis == 0 && regs_contig_plan(h->tbytes, h->bc, n, &rpt)) {
         e = launch_contig(h->tbytes, h->bc, rpt, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
@@ -584,6 +588,13 @@ mol_status mol_create(const mol_grid *grid, double c, double dt, double beta, in
         for (int k = 0; k < ninter; ++k)
             if ((st = dev_alloc(h, &h->inter[k], (size_t)h->tbytes * h->N)) != MOL_OK) goto bad;
     }
+    {
+        // rows split over two warps where the row length allows it (faster
+        // than one warp per row on every measured grid; mol_autotune may
+        // still choose otherwise)
+        int r = 0;
+        if (h->ndim >= 2 && regs_rows_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, 2, &r)) h->tune_rows_warps = 2;
+    }
     if (h->ndim == 2 && bc == MOL_BC_DIRICHLET && h->n[0] <= 1024 && h->n[1] <= 1024) {
         int r = 0, S = 0, K = 0;
         const bool xreg = regs_res_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, &r) ||
@@ -772,7 +783,13 @@ mol_status mol_autotune(mol_handle h, void *stream)
     const bool res = h->ndim >= 2 && regs_res_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, &dummy);
     bool strided = false;
     for (int a = 1; a < h->ndim; ++a) strided |= regs_strided_plan(h->tbytes, h->bc, (int)h->n[a], &r0, &S0, &K0);
+    // x variants: one warp per row with 1, 2 or 4 warps per CTA (code 1, 2, 4),
+    // or each row split over 2 or 4 warps (code -2, -4)
     std::vector<int> warps_c = res ? std::vector<int>{1, 2, 4} : std::vector<int>{h->tune_res_warps};
+    if (h->ndim >= 2) {
+        for (int W : {2, 4})
+            if (regs_rows_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, W, &dummy)) warps_c.push_back(-W);
+    }
     std::vector<std::pair<int, int>> str_c = {{h->tune_strided_rpt, h->tune_strided_warps}};
     if (strided) {
         str_c = {{0, 8}, {0, 4}};
@@ -790,7 +807,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
     h->timing = false;
     const int64_t launches0 = h->launches;
     double best = 1e30;
-    int bw = h->tune_res_warps, br = h->tune_strided_rpt, bsw = h->tune_strided_warps;
+    int bw = h->tune_res_warps, br = h->tune_strided_rpt, bsw = h->tune_strided_warps, brw = h->tune_rows_warps;
     mol_status st = MOL_OK;
     for (int w : warps_c) {
         for (auto &sc : str_c) {
@@ -799,7 +816,8 @@ mol_status mol_autotune(mol_handle h, void *stream)
             for (int a = 1; a < h->ndim && strided; ++a)
                 ok &= regs_strided_plan(h->tbytes, h->bc, (int)h->n[a], &rr, &SS, &KK, sc.first, sc.second);
             if (!ok) continue;
-            h->tune_res_warps = w;
+            h->tune_res_warps = w > 0 ? w : h->tune_res_warps;
+            h->tune_rows_warps = w < 0 ? -w : 0;
             h->tune_strided_rpt = sc.first;
             h->tune_strided_warps = sc.second;
             // 2 warm-up steps, then the minimum of 3 timings of 3 steps
@@ -820,7 +838,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
                 }
             }
             if (st != MOL_OK) break;
-            if (t < best) { best = t; bw = w; br = sc.first; bsw = sc.second; }
+            if (t < best) { best = t; bw = h->tune_res_warps; brw = h->tune_rows_warps; br = sc.first; bsw = sc.second; }
         }
         if (st != MOL_OK) break;
     }
@@ -829,6 +847,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
     h->timing = was_timing;
     h->launches = launches0;
     h->tune_res_warps = bw;
+    h->tune_rows_warps = brw;
     h->tune_strided_rpt = br;
     h->tune_strided_warps = bsw;
     h->tune_ms = best < 1e30 ? best : 0.0;
@@ -836,10 +855,11 @@ mol_status mol_autotune(mol_handle h, void *stream)
     return st;
 }
 
-mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int strided_warps)
+mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int strided_warps, int rows_warps)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
     if (res_warps != 1 && res_warps != 2 && res_warps != 4) return fail(h, MOL_EINVAL, "res_warps must be 1, 2 or 4");
+    if (rows_warps != 0 && rows_warps != 2 && rows_warps != 4) return fail(h, MOL_EINVAL, "rows_warps must be 0, 2 or 4");
     if (strided_rpt != 0 && strided_rpt != 32) return fail(h, MOL_EINVAL, "strided_rpt must be 0 or 32");
     if (strided_warps < 1 || strided_warps > 8) return fail(h, MOL_EINVAL, "strided_warps must be in 1..8");
     for (int a = 1; a < h->ndim; ++a) {
@@ -851,18 +871,20 @@ mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int stri
             return fail(h, MOL_EINVAL, "the strided choice does not fit an axis of this grid");
     }
     h->tune_res_warps = res_warps;
+    h->tune_rows_warps = rows_warps;
     h->tune_strided_rpt = strided_rpt;
     h->tune_strided_warps = strided_warps;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     return MOL_OK;
 }
 
-mol_status mol_get_tuning(mol_handle h, int out[3], double *ms_per_step)
+mol_status mol_get_tuning(mol_handle h, int out[4], double *ms_per_step)
 {
     if (!h || !out) return fail(h, MOL_EINVAL, "NULL argument");
     out[0] = h->tune_res_warps;
     out[1] = h->tune_strided_rpt;
     out[2] = h->tune_strided_warps;
+    out[3] = h->tune_rows_warps;
     if (ms_per_step) *ms_per_step = h->tune_ms;
     return MOL_OK;
 }

@@ -52,6 +52,9 @@ cudaError_t launch_strided(int tbytes, int bc, int rpt, const AxisDev &A, const 
                            cudaStream_t s);
 cudaError_t configure_regs_kernels();
 bool regs_res_plan(int tbytes, int n, int ng, int *rpt);
+bool regs_rows_plan(int tbytes, int n, int ng, int W, int *rpt);
+cudaError_t launch_rows(int bc, int rpt, int ng, int W, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                        cudaStream_t s);
 cudaError_t launch_res(int bc, int rpt, int ng, int warps, const AxisDev &A, const LineSet &L, const ProgParams &p,
                        cudaStream_t s);
 

@@ -27,6 +27,23 @@ cudaError_t attr_res()
                                 (int)res_smem<RPT, NB>(kResWarpsMax));
 }
 
+template <int RPT, int NB, int W>
+size_t rows_smem() { return row_slots_bytes<W>() + (size_t)NB * 32 * W * ContigStage<float, RPT>::SST * sizeof(float); }
+
+template <int BC, int RPT, int NB, int W>
+cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+{
+    k_contig_rows<BC, RPT, NB, W><<<(unsigned)L.nlines, 32 * W, rows_smem<RPT, NB, W>(), s>>>(A, L, p);
+    return cudaGetLastError();
+}
+
+template <int BC, int RPT, int NB, int W>
+cudaError_t attr_rows()
+{
+    return cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rows_smem<RPT, NB, W>());
+}
+
 template <class T, int RPT>
 size_t contig_smem() { return (size_t)kContigWarps * 2 * ContigStage<T, RPT>::LINE * sizeof(T); }
 
@@ -197,10 +214,47 @@ cudaError_t launch_res(int bc, int rpt, int ng, int warps, const AxisDev &A, con
     return cudaErrorInvalidValue;
 }
 
+// float32 Horner pass with W warps per row: n = 32 W RPT exactly, RPT 16 or 32
+bool regs_rows_plan(int tbytes, int n, int ng, int W, int *rpt)
+{
+    if (tbytes != 4 || ng > 3 || (W != 2 && W != 4) || n % (32 * W) != 0) return false;
+    const int r = n / (32 * W);
+    if (r != 16 && r != 32) return false;
+    *rpt = r;
+    return true;
+}
+
+cudaError_t launch_rows(int bc, int rpt, int ng, int W, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                        cudaStream_t s)
+{
+#define MOLT_ROWS(BC, WW)                                                                 \
+    switch (rpt * 10 + (ng < 1 ? 1 : ng)) {                                               \
+    case 161: return run_rows<BC, 16, 1, WW>(A, L, p, s);                                 \
+    case 162: return run_rows<BC, 16, 2, WW>(A, L, p, s);                                 \
+    case 163: return run_rows<BC, 16, 3, WW>(A, L, p, s);                                 \
+    case 321: return run_rows<BC, 32, 1, WW>(A, L, p, s);                                 \
+    case 322: return run_rows<BC, 32, 2, WW>(A, L, p, s);                                 \
+    case 323: return run_rows<BC, 32, 3, WW>(A, L, p, s);                                 \
+    default: break;                                                                       \
+    }
+    if (W == 2) {
+        if (bc == BC_PERIODIC) { MOLT_ROWS(BC_PERIODIC, 2) } else { MOLT_ROWS(BC_DIRICHLET, 2) }
+    } else if (W == 4) {
+        if (bc == BC_PERIODIC) { MOLT_ROWS(BC_PERIODIC, 4) } else { MOLT_ROWS(BC_DIRICHLET, 4) }
+    }
+#undef MOLT_ROWS
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t configure_regs_kernels()
 {
     cudaError_t e;
 #define MOLT_A(x) if ((e = (x)) != cudaSuccess) return e;
+#define MOLT_ROWA(BC, WW) MOLT_A((attr_rows<BC, 16, 1, WW>())) MOLT_A((attr_rows<BC, 16, 2, WW>())) \
+    MOLT_A((attr_rows<BC, 16, 3, WW>())) MOLT_A((attr_rows<BC, 32, 1, WW>())) MOLT_A((attr_rows<BC, 32, 2, WW>())) \
+    MOLT_A((attr_rows<BC, 32, 3, WW>()))
+    MOLT_ROWA(BC_PERIODIC, 2) MOLT_ROWA(BC_DIRICHLET, 2) MOLT_ROWA(BC_PERIODIC, 4) MOLT_ROWA(BC_DIRICHLET, 4)
+#undef MOLT_ROWA
 #define MOLT_RA(BC) MOLT_A((attr_res<BC, 8, 1>())) MOLT_A((attr_res<BC, 8, 2>())) MOLT_A((attr_res<BC, 8, 3>())) \
     MOLT_A((attr_res<BC, 16, 1>())) MOLT_A((attr_res<BC, 16, 2>())) MOLT_A((attr_res<BC, 16, 3>()))             \
     MOLT_A((attr_res<BC, 32, 1>())) MOLT_A((attr_res<BC, 32, 2>())) MOLT_A((attr_res<BC, 32, 3>()))             \

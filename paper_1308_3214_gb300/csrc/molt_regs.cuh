@@ -897,6 +897,270 @@ __global__ void __launch_bounds__(128) k_contig_res(AxisDev A, LineSet LS, ProgP
 }
 
 // ---------------------------------------------------------------------------
+// contiguous axis, float32 Horner pass, one row per CTA of W warps
+// ---------------------------------------------------------------------------
+// A row of n = 32 W RPT points is split over the W warps of a CTA: warp w holds
+// points [32 w RPT, 32 (w+1) RPT), lane = segment of RPT points.  Each warp
+// runs the single-warp sweep on its part; halos and the causal and anti-causal
+// carries between the warps of the row pass through a few shared-memory slots
+// (three CTA barriers per sweep).  A row then costs about 1/W of the
+// single-warp latency, and the shorter segments need fewer registers, so more
+// rows are in flight per SM.
+template <int W>
+struct RowSlots {
+    float halo[W][4];    // per warp: z at its first two and last two points
+    float rhalo[W][2];   // per warp: r at its first and last point
+    float tc[W];         // per warp: zero-inflow causal total (y at its last point)
+    float ta[W];         // per warp: zero-inflow anti-causal total (e at its first point)
+    float yl;            // y_{n-1} of the row with zero inflow
+};
+
+template <int BC, int RPT, int W>
+__device__ __forceinline__ void row_sweep(float (&z)[RPT], const float (&r)[RPT], float rl, float rr, float cu,
+                                          const AxisDev &A, int lane, int warp, RowSlots<W> &sl)
+{
+    const int n = A.n;
+    const float d = (float)A.d;
+    const int seg = warp * 32 + lane, a = seg * RPT;
+    constexpr int Ld = 32 * W - 1;                   // n = 32 W RPT: every segment is full
+    const float *dpg = A.dpow32;
+    const float c1 = (float)A.c1, c2 = (float)A.c2;
+
+    // halos: by shuffles inside the warp, through shared memory across warps
+    __syncwarp();
+    float zl1 = __shfl_up_sync(0xffffffffu, z[RPT - 1], 1), zl2 = __shfl_up_sync(0xffffffffu, z[RPT - 2], 1);
+    float zr0 = __shfl_down_sync(0xffffffffu, z[0], 1), zr1 = __shfl_down_sync(0xffffffffu, z[1], 1);
+    if (lane == 0) { sl.halo[warp][0] = z[0]; sl.halo[warp][1] = z[1]; }
+    if (lane == 31) { sl.halo[warp][2] = z[RPT - 2]; sl.halo[warp][3] = z[RPT - 1]; }
+    __syncthreads();
+    if (lane == 0 && (warp > 0 || BC == BC_PERIODIC)) {
+        const int wl = warp > 0 ? warp - 1 : W - 1;
+        zl2 = sl.halo[wl][2];
+        zl1 = sl.halo[wl][3];
+    }
+    if (lane == 31 && (warp < W - 1 || BC == BC_PERIODIC)) {
+        const int wr = warp < W - 1 ? warp + 1 : 0;
+        zr0 = sl.halo[wr][0];
+        zr1 = sl.halo[wr][1];
+    }
+    if (BC == BC_DIRICHLET) end_ghosts<float, RPT, 2>(z, seg == 0, seg == Ld, zl2, zl1, zr0, zr1);
+    seg_make_q<float, RPT, 2>(z, zl2, zl1, zr0, zr1, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : r[k]); }, cu,
+                              c1, c2);
+    if (BC == BC_DIRICHLET) end_zero<float, RPT>(z, seg == 0, seg == Ld);
+
+    // causal carries: Kogge-Stone inside the warp, then across the warps
+    const float E = seg_fwd_reduce<float, RPT>(z, d);
+    __syncwarp();
+    float x = E;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float y = __shfl_up_sync(0xffffffffu, x, 1 << k);
+        x = (lane >= (1 << k)) ? x + (float)A.dm[k] * y : x;
+    }
+    float yin = __shfl_up_sync(0xffffffffu, x, 1);
+    yin = (lane == 0) ? 0.f : yin;
+    if (lane == 31) sl.tc[warp] = x;
+    __syncthreads();
+    const float DW = dpg[32 * RPT];                  // decay over one warp's points
+    float cin = 0.f, tot = 0.f;
+#pragma unroll
+    for (int w2 = 0; w2 < W; ++w2) {
+        cin = (w2 == warp) ? tot : cin;
+        tot = DW * tot + sl.tc[w2];
+    }
+    yin += dpg[lane * RPT] * cin;
+    if (BC == BC_PERIODIC) yin += dpg[a] * (tot * (float)A.inv);   // images to the left
+    const float ER = seg_fwd_scan<float, RPT>(z, d, yin);
+
+    // anti-causal carries
+    __syncwarp();
+    float xb = ER;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float t = __shfl_down_sync(0xffffffffu, xb, 1 << k);
+        xb = (lane + (1 << k) < 32) ? xb + (float)A.dm[k] * t : xb;
+    }
+    float exclb = __shfl_down_sync(0xffffffffu, xb, 1);
+    exclb = (lane == 31) ? 0.f : exclb;
+    if (lane == 0) sl.ta[warp] = xb;
+    if (warp == W - 1 && lane == 31) sl.yl = z[RPT - 1];
+    __syncthreads();
+    float cinb = 0.f, e00 = 0.f;
+#pragma unroll
+    for (int w2 = W - 1; w2 >= 0; --w2) {
+        cinb = (w2 == warp) ? e00 : cinb;
+        e00 = DW * e00 + sl.ta[w2];
+    }
+    exclb += dpg[(31 - lane) * RPT] * cinb;
+    float Z, Acoef = 0.f;
+    if (BC == BC_DIRICHLET) {
+        const float mu = (float)A.mu, inv = (float)A.inv, yl = sl.yl;
+        Acoef = (mu * yl - e00) * inv;
+        Z = (mu * e00 - yl) * inv;
+    } else {
+        Z = d * e00 * (float)A.inv;
+    }
+    seg_bwd_scan<float, RPT>(z, d, d * exclb + dpg[n - a - RPT] * Z);
+    if (BC == BC_DIRICHLET) seg_add_left<float, RPT>(z, d, Acoef * dpg[a]);
+    __syncwarp();
+}
+
+template <int W>
+__host__ __device__ constexpr size_t row_slots_bytes() { return (sizeof(RowSlots<W>) + 15) & ~(size_t)15; }
+
+template <int BC, int RPT, int NB, int W>
+__global__ void __launch_bounds__(32 * W, W == 2 ? 8 : 6) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr)
+{
+    static_assert(RPT % 4 == 0 && RPT >= 8, "segment length");
+    using T = float;
+    using St = ContigStage<T, RPT>;
+    constexpr int NT = 32 * W;                        // threads (segments) of one row
+    constexpr int LINE = NT * St::SST;                // one field of the row in the segment layout
+    constexpr int NVL = RPT / 4;                      // 16-byte vectors per thread
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RowSlots<W> &sl = *reinterpret_cast<RowSlots<W> *>(smem_raw);
+    T *B = reinterpret_cast<T *>(smem_raw + row_slots_bytes<W>());
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int n = A.n;                                // == NT * RPT
+    const int64_t row = blockIdx.x;
+    if (row >= LS.nlines) return;
+    const int64_t base = row * (int64_t)n;
+    const int ng = pr.ng;
+    if (t == 0) {
+        const unsigned bytes = (unsigned)n * 4u;
+        prefetch_l2((const float *)pr.u_hi + base, bytes);
+        prefetch_l2((const float *)pr.u_lo + base, bytes);
+        if (pr.eb != 0.0) {
+            prefetch_l2((const float *)pr.up_hi + base, bytes);
+            prefetch_l2((const float *)pr.up_lo + base, bytes);
+        }
+    }
+    auto copy_field = [&](int k) {
+        const float4 *src = reinterpret_cast<const float4 *>(reinterpret_cast<const T *>(pr.g[k]) + base);
+        T *dst = B + k * LINE;
+#pragma unroll
+        for (int i = 0; i < NVL; ++i) {
+            const int v = t + NT * i;
+            cp_async16(dst + St::pos(4 * v), src + v);
+        }
+    };
+    for (int k = 1; k < ng; ++k) copy_field(k);
+    cp_async_commit();
+
+    // r = accurate second difference of u (pairs), coalesced over the CTA;
+    // buffer 0 stages it in the segment layout
+    T *R = B;
+    {
+        const T *H = reinterpret_cast<const T *>(pr.u_hi) + base, *Lo = reinterpret_cast<const T *>(pr.u_lo) + base;
+        const float4 *H4 = reinterpret_cast<const float4 *>(H), *L4 = reinterpret_cast<const float4 *>(Lo);
+        float4 h[NVL], l[NVL];
+        float hx[NVL], lx[NVL];      // lane 0: the point before its vector; lane 31: the point after it
+#pragma unroll
+        for (int i = 0; i < NVL; ++i) {
+            const int v = t + NT * i;
+            h[i] = __ldg(H4 + v);
+            l[i] = __ldg(L4 + v);
+            int j = (lane == 0) ? 4 * v - 1 : 4 * v + 4;
+            if (BC == BC_PERIODIC) j = j < 0 ? j + n : (j >= n ? j - n : j);
+            else j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+            hx[i] = 0.f;
+            lx[i] = 0.f;
+            if (lane == 0 || lane == 31) { hx[i] = __ldg(H + j); lx[i] = __ldg(Lo + j); }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < NVL; ++i) {
+            const int v = t + NT * i;
+            float hl = __shfl_up_sync(0xffffffffu, h[i].w, 1), ll = __shfl_up_sync(0xffffffffu, l[i].w, 1);
+            float hr = __shfl_down_sync(0xffffffffu, h[i].x, 1), lr = __shfl_down_sync(0xffffffffu, l[i].x, 1);
+            hl = (lane == 0) ? hx[i] : hl;
+            ll = (lane == 0) ? lx[i] : ll;
+            hr = (lane == 31) ? hx[i] : hr;
+            lr = (lane == 31) ? lx[i] : lr;
+            float4 rv = sdiff4(h[i], l[i], hl, ll, hr, lr);
+            if (BC == BC_DIRICHLET) {                // end nodes take the neighbouring interior centre
+                if (v == 0) rv.x = rv.y;
+                if (4 * v + 4 == n) rv.w = rv.z;
+            }
+            *reinterpret_cast<float4 *>(R + St::pos(4 * v)) = rv;
+        }
+    }
+    __syncthreads();
+    T r[RPT];
+    stage_to_regs<T, RPT>(R, r, t, false);
+    if (lane == 0) sl.rhalo[warp][0] = r[0];
+    if (lane == 31) sl.rhalo[warp][1] = r[RPT - 1];
+    __syncthreads();                                  // every thread is done with R
+    if (ng > 0) copy_field(0);
+    cp_async_commit();
+    float rl = __shfl_up_sync(0xffffffffu, r[RPT - 1], 1), rr = __shfl_down_sync(0xffffffffu, r[0], 1);
+    if (lane == 0) rl = (warp > 0) ? sl.rhalo[warp - 1][1] : (BC == BC_PERIODIC ? sl.rhalo[W - 1][1] : r[0]);
+    if (lane == 31) rr = (warp < W - 1) ? sl.rhalo[warp + 1][0] : (BC == BC_PERIODIC ? sl.rhalo[0][0] : r[RPT - 1]);
+    cp_async_wait_all();
+    __syncthreads();
+
+    // Horner in D_x with the fields from shared memory
+    T z[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) z[k] = 0;
+    for (int tt = pr.P; tt >= 0; --tt) {
+        for (int k = 0; k < ng; ++k) {
+            const T c = (T)__ldg(pr.coef + (size_t)tt * ng + k);
+            if (c == (T)0) continue;
+            const float4 *sg = reinterpret_cast<const float4 *>(B + k * LINE + t * St::SST);
+#pragma unroll
+            for (int q = 0; q < RPT / 4; ++q) {
+                const float4 y = sg[q];
+                z[4 * q] += c * y.x;
+                z[4 * q + 1] += c * y.y;
+                z[4 * q + 2] += c * y.z;
+                z[4 * q + 3] += c * y.w;
+            }
+        }
+        if (tt == 0) break;
+        row_sweep<BC, RPT, W>(z, r, rl, rr, (T)__ldg(pr.cu + tt), A, lane, warp, sl);
+    }
+
+    // F -> coalesced side -> next level
+    __syncthreads();                                  // every thread is done reading the fields
+    regs_to_stage<T, RPT>(B, z, t);
+    __syncthreads();
+    const float4 *UH = reinterpret_cast<const float4 *>((const float *)pr.u_hi + base);
+    const float4 *UL = reinterpret_cast<const float4 *>((const float *)pr.u_lo + base);
+    const float4 *PH = reinterpret_cast<const float4 *>((const float *)pr.up_hi + base);
+    const float4 *PL = reinterpret_cast<const float4 *>((const float *)pr.up_lo + base);
+    float4 *NH = reinterpret_cast<float4 *>((float *)pr.un_hi + base);
+    float4 *NL = reinterpret_cast<float4 *>((float *)pr.un_lo + base);
+    const bool prev = pr.eb != 0.0;
+    const float ea = (float)pr.ea, eb = (float)pr.eb, ec = (float)pr.ec;
+    constexpr int CH = NVL > 4 ? 4 : NVL;
+#pragma unroll
+    for (int i0 = 0; i0 < NVL; i0 += CH) {
+        float4 uh[CH], ul[CH], ph[CH], pl[CH];
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int v = t + NT * (i0 + i);
+            uh[i] = __ldg(UH + v);
+            ul[i] = __ldg(UL + v);
+            ph[i] = prev ? __ldg(PH + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+            pl[i] = prev ? __ldg(PL + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int v = t + NT * (i0 + i);
+            const float4 F = *CoalescedSide<T, RPT>::at(B, 4 * v);
+            float4 nh, nl;
+            level_pair(uh[i].x, ul[i].x, ph[i].x, pl[i].x, F.x, ea, eb, ec, nh.x, nl.x);
+            level_pair(uh[i].y, ul[i].y, ph[i].y, pl[i].y, F.y, ea, eb, ec, nh.y, nl.y);
+            level_pair(uh[i].z, ul[i].z, ph[i].z, pl[i].z, F.z, ea, eb, ec, nh.z, nl.z);
+            level_pair(uh[i].w, ul[i].w, ph[i].w, pl[i].w, F.w, ea, eb, ec, nh.w, nl.w);
+            NH[v] = nh;
+            NL[v] = nl;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // strided axes: lanes = 32 neighbouring lines, segments over warps and CTAs
 // ---------------------------------------------------------------------------
 template <class T>

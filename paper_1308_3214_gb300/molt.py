@@ -110,7 +110,7 @@ def load_library(path: Path | None = None):
     lib.mol_batch_update.argtypes = [vp, vp, vp, vp, D, D, D, I, vp, vp]
     lib.mol_autotune.argtypes = [vp, vp]
     lib.mol_get_tuning.argtypes = [vp, ctypes.POINTER(I), dp]
-    lib.mol_set_tuning.argtypes = [vp, I, I, I]
+    lib.mol_set_tuning.argtypes = [vp, I, I, I, I]
     lib.mol_batch_autotune.argtypes = [vp, vp]
     lib.mol_apply_FT.argtypes = [vp, vp, vp, vp]
     lib.mol_traces.argtypes = [vp, vp, I, ctypes.POINTER(i64), i64, vp, vp]
@@ -296,14 +296,16 @@ class Solver:
         self._check(self.lib.mol_autotune(self.h, ctypes.c_void_p(_stream_ptr(stream))))
         return self.tuning()
 
-    def set_tuning(self, res_warps: int = 2, strided_rpt: int = 0, strided_warps: int = 8):
-        self._check(self.lib.mol_set_tuning(self.h, int(res_warps), int(strided_rpt), int(strided_warps)))
+    def set_tuning(self, res_warps: int = 2, strided_rpt: int = 0, strided_warps: int = 8, rows_warps: int = 0):
+        self._check(self.lib.mol_set_tuning(self.h, int(res_warps), int(strided_rpt), int(strided_warps),
+                                            int(rows_warps)))
 
     def tuning(self) -> dict:
-        out = (ctypes.c_int * 3)()
+        out = (ctypes.c_int * 4)()
         ms = ctypes.c_double()
         self._check(self.lib.mol_get_tuning(self.h, out, ctypes.byref(ms)))
-        return {"res_warps": out[0], "strided_rpt": out[1], "strided_warps": out[2], "ms_per_step": ms.value}
+        return {"res_warps": out[0], "strided_rpt": out[1], "strided_warps": out[2], "rows_warps": out[3],
+                "ms_per_step": ms.value}
 
     def sync(self, stream=None):
         self._check(self.lib.mol_sync(self.h, ctypes.c_void_p(_stream_ptr(stream))))

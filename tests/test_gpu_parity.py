@@ -339,6 +339,7 @@ def test_autotune_choice_keeps_parity(prec):
     s = make(shape, dt, P, bc, prec)
     tun = s.autotune()
     assert tun["res_warps"] in (1, 2, 4) and tun["strided_warps"] in (4, 8) and tun["strided_rpt"] in (0, 32)
+    assert tun["rows_warps"] in (0, 2, 4)
     assert tun["ms_per_step"] > 0
     u0 = smooth_field(shape, 7, bc) + 0.05 * field(shape, 8, bc)
     u1 = oracle.start(u0, s.nu, P, s.beta, bc)
@@ -367,3 +368,32 @@ def test_every_strided_choice_matches_oracle(rpt, warps):
     ref = oracle.D_axis(v, 1, s.nu[1], bc, 2, power=2)
     got = s.apply_D(dev(v), 1, 2).cpu().numpy()
     assert rel_l2(got, ref) <= tol_for("mixed", s, 2)
+
+
+
+@pytest.mark.parametrize("shape, W", [((48, 2048), 2), ((40, 2048), 4), ((64, 1024), 2)])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("P", [1, 3])
+def test_rows_split_over_warps_match_oracle(shape, W, bc, P):
+    """The x pass with each row split over W warps (carries and halos through
+    shared memory): F and a few steps against the oracle."""
+    dt = 2.0 / max(shape)
+    s = make(shape, dt, P, bc, "mixed")
+    s.set_tuning(rows_warps=W)
+    assert s.tuning()["rows_warps"] == W
+    u = field(shape, 50 + W, bc)
+    ref = oracle.F(u, s.nu, P, s.beta, bc)
+    assert rel_l2(s.apply_F(dev(u)).cpu().numpy(), ref) <= tol_for("mixed", s, 2 * P)
+    u0 = smooth_field(shape, 51, bc) + 0.05 * field(shape, 52, bc)
+    u1 = oracle.start(u0, s.nu, P, s.beta, bc)
+    up, uc = dev(u0), dev(u1)
+    nsteps = 5
+    s.step(up, uc, nsteps)
+    rp, rc = oracle.run(u0, u1, nsteps, s.nu, P, s.beta, bc)
+    Fsum, a, b = 0.0, u0, u1
+    for _ in range(nsteps):
+        F = oracle.F(b, s.nu, P, s.beta, bc)
+        Fsum += np.linalg.norm(F)
+        a, b = b, 2 * b - a + F
+    tol = 8 * EPS32 * (1 + 1 / (1 - max(s.d))) * 2 * P * Fsum / np.linalg.norm(rc)
+    assert rel_l2(uc.cpu().numpy(), rc) <= tol
