@@ -294,15 +294,22 @@ mol_status mol_batch_sync(mol_batch b, void *stream);
 int64_t mol_batch_launch_count(mol_batch b);
 
 /* Autotuner of a batch: times the x pass with 2, 4 and 8 warps per CTA for
- * each of its two launches (rows of <= 512 points; longer rows), then the y
- * pass with each problem's segment length at the smallest RPT covering the
- * column with 16 warps or at twice that, on the batch's own workspace, and
- * keeps the fastest.  Synchronous; the caller's fields are not touched.
- * mol_batch_get_tuning: out[0], out[1] = warps per CTA of the two x launches,
+ * each of its two launches (rows of <= 512 points; longer rows, which are
+ * also timed split over the two warps of one CTA per row), then the y pass
+ * with each problem's segment length at the smallest RPT covering the column
+ * with 16 warps or at twice that, on the batch's own workspace, and keeps
+ * the fastest.  Synchronous; the caller's fields are not touched.
+ * mol_batch_get_tuning: out[0], out[1] = warps per CTA of the two x launches
+ * (out[1] = 0: the long rows run split, one CTA of two warps per row),
  * out[2] = y segment rule (0 smallest, 1 doubled); ms (may be NULL) = the
  * tuned x and y pass times. */
 mol_status mol_batch_autotune(mol_batch b, void *stream);
 mol_status mol_batch_get_tuning(mol_batch b, int out[3], double ms[2]);
+/* Sets the launch variants by hand, in the encoding of mol_batch_get_tuning:
+ * x_warps_short, x_warps_long in {2, 4, 8} (x_warps_long 0: split long
+ * rows), y_rule in {0, 1}.  MOL_EINVAL (nothing changed) for a value outside
+ * those sets or one whose buffers exceed shared memory.  Synchronous. */
+mol_status mol_batch_set_tuning(mol_batch b, int x_warps_short, int x_warps_long, int y_rule);
 
 /* Per-pass CUDA-event timing as mol_set_pass_timing / mol_pass_times
  * (index 0 = x pass, 1 = y pass). */

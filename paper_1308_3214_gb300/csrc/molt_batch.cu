@@ -25,7 +25,7 @@ struct BLevel {
 struct mol_batch_ctx {
     int nprob = 0, prec = 0, tbytes = 8, Pmax = 1, quad = 2, use_graphs = 1;
     int64_t nrows = 0, total_int = 0;
-    int64_t rows_small = 0;             // rows of the problems with x segments <= 16 come first
+    int64_t rows_small = 0;             // rows of the problems with rows of <= 512 points come first
     int nitems_y = 0;
     std::vector<int64_t> uoff;          // packed user layout: nprob + 1 prefix sums
     std::vector<BatchProb> hp;          // host copy of the problem table
@@ -54,6 +54,8 @@ struct mol_batch_ctx {
     int x_launches() const { return (rows_small > 0 ? 1 : 0) + (nrows > rows_small ? 1 : 0); }
     int smem_sm = 228 * 1024, smem_blk = 227 * 1024;
     int ymode = 0;                      // y segment rule: 0 smallest covering RPT, 1 twice that (<= 64)
+    int xsplit = 1;                     // rows of > 512 points: 1 one CTA of two warps per row, 0 one warp
+    size_t xs_smem = 0;                 // shared memory of the split-row kernel
     double tune_ms[2] = {0.0, 0.0};     // tuned x / y pass times
 };
 
@@ -118,6 +120,21 @@ int pick_rpt_y(int n, int mode = 0)
     return r;
 }
 
+bool long_row(int nx) { return nx > 16 * 32; }
+
+// per-problem x-pass segment constants of the long rows for the current
+// choice: 16-point segments over two warps (split) or 32-point segments
+// over one warp
+void set_x_segments(mol_batch_ctx *b)
+{
+    for (BatchProb &pb : b->hp) {
+        if (!long_row(pb.ax.n)) continue;
+        pb.rpt_x = b->xsplit ? 16 : 32;
+        const double nux = -std::log(pb.ax.d);
+        for (int k = 0; k < 5; ++k) pb.ax.dm[k] = std::exp(-nux * (double)pb.rpt_x * (double)(1 << k));
+    }
+}
+
 // per-problem y-pass segment constants for the current rule
 void set_y_segments(mol_batch_ctx *b)
 {
@@ -170,7 +187,12 @@ cudaError_t launch_pass_x(const mol_batch_ctx *b, BatchPass bp, cudaStream_t s)
     if (e != cudaSuccess) return e;
     bp.row_begin = (int)b->rows_small;
     bp.nitems = (int)b->nrows;
-    if (bp.nitems > bp.row_begin) k_batch_x<T, true, ADJ><<<b->xgrid[1], 32 * b->xW[1], b->xsmem[1], s>>>(bp, b->nbuf);
+    if (bp.nitems > bp.row_begin) {
+        if (b->xsplit)
+            k_batch_xs<T, 16, 2, ADJ><<<(unsigned)(b->nrows - b->rows_small), 64, b->xs_smem, s>>>(bp);
+        else
+            k_batch_x<T, true, ADJ><<<b->xgrid[1], 32 * b->xW[1], b->xsmem[1], s>>>(bp, b->nbuf);
+    }
     return cudaGetLastError();
 }
 
@@ -186,6 +208,9 @@ cudaError_t set_kernel_smem(const mol_batch_ctx *b)
             e = cudaFuncSetAttribute(xk[adj][L], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xsmem[L]);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(yk[adj], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->ysmem);
     }
+    const void *sk[2] = {(const void *)k_batch_xs<T, 16, 2, false>, (const void *)k_batch_xs<T, 16, 2, true>};
+    for (int adj = 0; adj < 2 && e == cudaSuccess; ++adj)
+        e = cudaFuncSetAttribute(sk[adj], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xs_smem);
     return e;
 }
 
@@ -412,12 +437,12 @@ mol_status plan_batch(mol_batch_ctx *b, int nprob, const mol_grid *grids, const 
         b->Pmax = std::max(b->Pmax, P[i]);
         b->uoff[i + 1] = b->uoff[i] + (int64_t)nx * ny;
     }
-    // internal order: problems with x segments <= 16 first, so that each
+    // internal order: problems with rows of <= 512 points first, so that each
     // x-pass kernel takes one contiguous range of rows
     for (int pass = 0; pass < 2; ++pass)
         for (int i = 0; i < nprob; ++i) {
             BatchProb &pb = b->hp[i];
-            if ((pb.rpt_x == 32) != (pass == 1)) continue;
+            if (long_row(pb.ax.n) != (pass == 1)) continue;
             pb.off = off;
             pb.row0 = (int)rows;
             off += ((int64_t)pb.ay.n * pb.pitch + 63) & ~(int64_t)63;
@@ -428,6 +453,9 @@ mol_status plan_batch(mol_batch_ctx *b, int nprob, const mol_grid *grids, const 
     b->total_int = off;
     b->nrows = rows;
     b->nitems_y = (int)items;
+    b->xs_smem = batch_xs_smem((size_t)b->tbytes, 16, 2, b->Pmax);
+    b->xsplit = b->xs_smem <= (size_t)b->smem_blk ? 1 : 0;
+    set_x_segments(b);
     return MOL_OK;
 }
 
@@ -775,15 +803,30 @@ mol_status mol_batch_autotune(mol_batch b, void *stream)
         if ((st = zero_level(b, b->lev[k], s)) != MOL_OK) return st;
     const int64_t launches0 = b->launches;
     double t[2];
-    // warps per CTA of each x launch (the other held), then the y segment rule
+    // warps per CTA of each x launch (the other held; long rows also split
+    // over two warps, W = 0 below), then the y segment rule
+    auto upload = [&]() {
+        return cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice);
+    };
     for (int L = 0; L < 2; ++L) {
         if ((L == 0 && b->rows_small == 0) || (L == 1 && b->nrows == b->rows_small)) continue;
-        int bestW = b->xW[L];
+        int bestW = b->xW[L], bestSplit = b->xsplit;
         double best = 1e30;
-        for (int W : {2, 4, 8}) {
-            if (!set_x_shape(b, L, W)) continue;
+        for (int W : {0, 2, 4, 8}) {
+            if (W == 0 && (L == 0 || b->xs_smem > (size_t)b->smem_blk)) continue;
+            if (L == 1) {
+                b->xsplit = W == 0 ? 1 : 0;
+                set_x_segments(b);
+                BCK(upload(), "table upload");
+            }
+            if (W > 0 && !set_x_shape(b, L, W)) continue;
             if ((st = batch_pass_ms(b, s, t)) != MOL_OK) return st;
-            if (t[0] < best) { best = t[0]; bestW = W; }
+            if (t[0] < best) { best = t[0]; bestW = W > 0 ? W : bestW; bestSplit = W == 0; }
+        }
+        if (L == 1) {
+            b->xsplit = bestSplit;
+            set_x_segments(b);
+            BCK(upload(), "table upload");
         }
         set_x_shape(b, L, bestW);
         b->tune_ms[0] = best;
@@ -793,15 +836,39 @@ mol_status mol_batch_autotune(mol_batch b, void *stream)
     for (int mode : {0, 1}) {
         b->ymode = mode;
         set_y_segments(b);
-        BCK(cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice), "table upload");
+        BCK(upload(), "table upload");
         if ((st = batch_pass_ms(b, s, t)) != MOL_OK) return st;
         if (t[1] < besty) { besty = t[1]; bestY = mode; }
     }
     b->ymode = bestY;
     set_y_segments(b);
-    BCK(cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice), "table upload");
+    BCK(upload(), "table upload");
     b->tune_ms[1] = besty;
     b->launches = launches0;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    return MOL_OK;
+}
+
+mol_status mol_batch_set_tuning(mol_batch b, int x_warps_short, int x_warps_long, int y_rule)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    auto okW = [](int W) { return W == 2 || W == 4 || W == 8; };
+    if (!okW(x_warps_short) || !(okW(x_warps_long) || x_warps_long == 0) || (y_rule != 0 && y_rule != 1))
+        return bfail(b, MOL_EINVAL, "x warps must be 2, 4 or 8 (0: split long rows) and the y rule 0 or 1");
+    if (x_warps_long == 0 && b->xs_smem > (size_t)b->smem_blk)
+        return bfail(b, MOL_EINVAL, "split-row buffers exceed shared memory");
+    const int oldW[2] = {b->xW[0], b->xW[1]};
+    if (!set_x_shape(b, 0, x_warps_short) || (x_warps_long > 0 && !set_x_shape(b, 1, x_warps_long))) {
+        set_x_shape(b, 0, oldW[0]);
+        set_x_shape(b, 1, oldW[1]);
+        return bfail(b, MOL_EINVAL, "x-pass buffers exceed shared memory");
+    }
+    b->xsplit = x_warps_long == 0 ? 1 : 0;
+    b->ymode = y_rule;
+    set_x_segments(b);
+    set_y_segments(b);
+    BCK(cudaDeviceSynchronize(), "synchronise before the table upload");
+    BCK(cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice), "table upload");
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
     return MOL_OK;
 }
@@ -810,7 +877,7 @@ mol_status mol_batch_get_tuning(mol_batch b, int out[3], double ms[2])
 {
     if (!b || !out) return bfail(b, MOL_EINVAL, "NULL argument");
     out[0] = b->xW[0];
-    out[1] = b->xW[1];
+    out[1] = b->xsplit ? 0 : b->xW[1];
     out[2] = b->ymode;
     if (ms) { ms[0] = b->tune_ms[0]; ms[1] = b->tune_ms[1]; }
     return MOL_OK;

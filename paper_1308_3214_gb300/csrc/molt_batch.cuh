@@ -280,6 +280,207 @@ __global__ void __launch_bounds__(256, LARGE ? 1 : 2) k_batch_x(BatchPass bp, in
 }
 
 // ---------------------------------------------------------------------------
+// x pass: long rows split over the W warps of one CTA
+// ---------------------------------------------------------------------------
+// A row of 32 (W-1) RPT < n <= 32 W RPT points: thread t = 32 warp + lane
+// owns segment t (points t RPT .. t RPT + RPT - 1); the last point falls in
+// the last warp.  The steps are those of batch_row with the thread index in
+// place of the lane and the halos and carries between the warps through
+// shared memory (row_sweep / row_sweep_T).
+template <class T, int RPT, int W, bool ADJ>
+__device__ __forceinline__ void batch_row_split(const BatchProb &pb, const ProgParams &pr, int row, int t, T *B,
+                                                RowSlots<T, W> &sl)
+{
+    using St = ContigStage<T, RPT>;
+    using V = typename VecOf<T>::type;
+    constexpr int VN = VecOf<T>::n;
+    constexpr int NT = 32 * W;
+    constexpr int NVL = RPT / VN;                    // vectors per thread of a full row
+    constexpr bool pair = sizeof(T) == 4;
+    constexpr int LB = NT * St::SST;                 // one field buffer
+    static_assert(RPT % VN == 0 && RPT >= 4, "segment length");
+    const int warp = t >> 5, lane = t & 31;
+    const AxisDev &A = pb.ax;
+    const int n = A.n;
+    const int64_t base = pb.off + (int64_t)row * pb.pitch;
+    const int nvec = (n + VN - 1) / VN;              // within the padded pitch
+    const int ng = pb.P;
+    if (t == 0) {
+        const unsigned bytes = (unsigned)(nvec * 16);
+        prefetch_l2(reinterpret_cast<const T *>(pr.u_hi) + base, bytes);
+        if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.u_lo) + base, bytes);
+        if (pr.eb != 0.0) {
+            prefetch_l2(reinterpret_cast<const T *>(pr.up_hi) + base, bytes);
+            if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.up_lo) + base, bytes);
+        }
+    }
+
+    // 1. fields 1..ng-1 -> shared memory (asynchronous); field 0 after r
+    auto copy_field = [&](int k) {
+        const V *src = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.g[k]) + base);
+        T *dst = B + k * LB;
+#pragma unroll
+        for (int i = 0; i < NVL; ++i) {
+            const int v = t + NT * i;
+            if (v < nvec) cp_async16(dst + St::pos(VN * v), src + v);
+        }
+    };
+    for (int k = 1; k < ng; ++k) copy_field(k);
+    cp_async_commit();
+
+    // 2. r (ADJ: u) coalesced over the CTA, staged in buffer 0
+    T *R = B;
+    {
+        const T *H = reinterpret_cast<const T *>(pr.u_hi) + base;
+        const T *Lo = pair ? reinterpret_cast<const T *>(pr.u_lo) + base : H;
+        const V *H4 = reinterpret_cast<const V *>(H), *L4 = reinterpret_cast<const V *>(Lo);
+        constexpr int CR = NVL < 4 ? NVL : 4;
+#pragma unroll
+        for (int i0 = 0; i0 < NVL; i0 += CR) {
+            V h[CR], l[CR];
+            T hx[CR], lx[CR];        // lane 0: the point before its vector; lane 31: the point after it
+#pragma unroll
+            for (int i = 0; i < CR; ++i) {
+                const int v = t + NT * (i0 + i);
+                if (v < nvec) {
+                    h[i] = __ldg(H4 + v);
+                    if (pair) l[i] = __ldg(L4 + v);
+                } else {
+                    h[i] = V{};
+                    l[i] = V{};
+                }
+                int j = (lane == 0) ? VN * v - 1 : VN * v + VN;
+                j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+                hx[i] = 0;
+                lx[i] = 0;
+                if (!ADJ && (lane == 0 || lane == 31) && v < nvec) {
+                    hx[i] = __ldg(H + j);
+                    if (pair) lx[i] = __ldg(Lo + j);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < CR; ++i) {
+                const int v = t + NT * (i0 + i);
+                T hl = __shfl_up_sync(0xffffffffu, vlast(h[i]), 1), hr = __shfl_down_sync(0xffffffffu, vfirst(h[i]), 1);
+                T ll = 0, lr = 0;
+                if (pair) {
+                    ll = __shfl_up_sync(0xffffffffu, vlast(l[i]), 1);
+                    lr = __shfl_down_sync(0xffffffffu, vfirst(l[i]), 1);
+                }
+                hl = (lane == 0) ? hx[i] : hl;
+                ll = (lane == 0) ? lx[i] : ll;
+                hr = (lane == 31) ? hx[i] : hr;
+                lr = (lane == 31) ? lx[i] : lr;
+                if (v < nvec) {
+                    V r;
+                    if constexpr (ADJ) {
+                        r = h[i];
+                        if constexpr (pair) {
+                            T *e = reinterpret_cast<T *>(&r);
+                            const T *lo4 = reinterpret_cast<const T *>(&l[i]);
+#pragma unroll
+                            for (int cc = 0; cc < VN; ++cc) e[cc] += lo4[cc];
+                        }
+                    } else {
+                        if constexpr (pair) r = sdiff4(h[i], l[i], hl, ll, hr, lr);
+                        else r = sdiff2(h[i], hl, hr);
+                        if (v == 0) r.x = r.y;         // Dirichlet: the end node takes the interior centre
+                    }
+                    *reinterpret_cast<V *>(R + St::pos(VN * v)) = r;
+                } else {
+                    *reinterpret_cast<V *>(R + St::pos(VN * v)) = V{};
+                }
+            }
+        }
+    }
+    __syncthreads();
+    T r[RPT];
+    stage_to_regs<T, RPT>(R, r, t, false);
+    if (!ADJ) {
+        if (lane == 0) sl.rhalo[warp][0] = r[0];
+        if (lane == 31) sl.rhalo[warp][1] = r[RPT - 1];
+    }
+    __syncthreads();                                 // every thread is done with R
+    copy_field(0);
+    cp_async_commit();
+    T rl = 0, rr = 0;
+    if (!ADJ) {
+        rl = __shfl_up_sync(0xffffffffu, r[RPT - 1], 1);
+        rr = __shfl_down_sync(0xffffffffu, r[0], 1);
+        if (lane == 0) rl = (warp > 0) ? sl.rhalo[warp - 1][1] : r[0];
+        if (lane == 31) rr = (warp < W - 1) ? sl.rhalo[warp + 1][0] : r[RPT - 1];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    // 3. Horner in D_x with the fields from shared memory
+    T z[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) z[k] = 0;
+    for (int tt = pb.P; tt >= 0; --tt) {
+        for (int k = 0; k < ng; ++k) {
+            const T c = (T)pb.coef[tt][k];
+            if (c == (T)0) continue;
+            const V *seg = reinterpret_cast<const V *>(B + k * LB + t * St::SST);
+#pragma unroll
+            for (int q = 0; q < NVL; ++q) {
+                const V y = seg[q];
+                const T *e = reinterpret_cast<const T *>(&y);
+#pragma unroll
+                for (int cc = 0; cc < VN; ++cc) z[VN * q + cc] += c * e[cc];
+            }
+        }
+        if (tt == 0) break;
+        if (ADJ) row_sweep_T<T, RPT, W>(z, r, (T)pb.cu[tt], A, lane, warp, sl);
+        else row_sweep<T, BC_DIRICHLET, RPT, W, true>(z, r, rl, rr, (T)pb.cu[tt], A, lane, warp, sl);
+    }
+
+    // 4. F -> coalesced side -> next level; padding points get F = 0
+    __syncthreads();                                 // every thread is done reading the fields
+    regs_to_stage<T, RPT>(B, z, t);
+    __syncthreads();
+    constexpr int CH = NVL > 4 ? 4 : NVL;
+#pragma unroll
+    for (int i0 = 0; i0 < NVL; i0 += CH) {
+        V F[CH];
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int v = t + NT * (i0 + i);
+            F[i] = V{};
+            if (v < nvec) {
+                F[i] = *CoalescedSide<T, RPT>::at(B, v * VN);
+                T *e = reinterpret_cast<T *>(&F[i]);
+#pragma unroll
+                for (int cc = 0; cc < VN; ++cc) e[cc] = (VN * v + cc < n) ? e[cc] : (T)0;
+            }
+        }
+        level_batch<T, CH, NT>(pr, base, t, i0, nvec, F);
+    }
+}
+
+// Rows [row_begin, nitems) of the list, one CTA of W warps per row (rows of
+// 32 (W-1) RPT < n <= 32 W RPT points)
+template <class T, int RPT, int W, bool ADJ>
+__global__ void __launch_bounds__(32 * W, sizeof(T) == 4 ? 8 : 4) k_batch_xs(BatchPass bp)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BatchProb &pb = *reinterpret_cast<BatchProb *>(smem_raw);
+    RowSlots<T, W> &sl = *reinterpret_cast<RowSlots<T, W> *>(smem_raw + sizeof(BatchProb));
+    T *B = reinterpret_cast<T *>(smem_raw + sizeof(BatchProb) + row_slots_bytes<T, W>());
+    const int r = bp.row_begin + (int)blockIdx.x;
+    if (r >= bp.nitems) return;
+    const int p = __ldg(bp.row_prob + r);
+    {
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(bp.probs + p);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&pb);
+        for (int i = threadIdx.x; i < (int)(sizeof(BatchProb) / 8); i += 32 * W) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    batch_row_split<T, RPT, W, ADJ>(pb, bp.pr, r - pb.row0, threadIdx.x, B, sl);
+}
+
+// ---------------------------------------------------------------------------
 // y pass: one group of 32 columns
 // ---------------------------------------------------------------------------
 // r = accurate second difference of u at rows a-1 .. a+RPT of one column,
@@ -326,12 +527,18 @@ template <class T, int RPT>
 __device__ __forceinline__ void bsolve(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT], int kl, bool rag, T *YL)
 {
     const T d = c.d;
-    const T E = seg_fwd_reduce<T, RPT>(z, d);
+    constexpr bool TWO = RPT >= 16;              // two-chain recurrences on the segments without the line's end
+    const T dH = TWO ? c.dpg[RPT / 2] : (T)0;
+    T E1 = 0, ER2 = 0;
+    const T E = (TWO && !rag) ? seg_fwd_reduce2<T, RPT>(z, d, dH, E1) : seg_fwd_reduce<T, RPT>(z, d);
     T yin, ytot;
     strided_causal<T, RPT>(c, E, yin, ytot);
     if (!c.full) yin = 0;
     T ylast = 0;
-    const T ER = rag ? seg_fwd_scan<T, RPT, true>(z, d, yin, kl, &ylast) : seg_fwd_scan<T, RPT>(z, d, yin);
+    T ER;
+    if (rag) ER = seg_fwd_scan<T, RPT, true>(z, d, yin, kl, &ylast);
+    else if (TWO) ER = seg_fwd_scan2<T, RPT>(z, d, dH, yin, E1, ER2);
+    else ER = seg_fwd_scan<T, RPT>(z, d, yin);
     if (rag && kl < RPT) YL[c.lane] = ylast;
     T eout, e00;
     strided_anticausal<T, RPT>(c, ER, eout, e00);      // its barrier publishes YL
@@ -341,8 +548,12 @@ __device__ __forceinline__ void bsolve(const StridedCtx<T> &c, const AxisDev &A,
     const T Z = (mu * e00 - yl) * inv;
     const T acc = d * eout + ((c.full && kl >= RPT) ? c.dpg[kl + 1 - RPT] * Z : (T)0);
     if (rag) seg_bwd_scan<T, RPT, true>(z, d, acc, kl, Z);
+    else if (TWO) seg_bwd_scan2<T, RPT>(z, d, dH, acc, ER2);
     else seg_bwd_scan<T, RPT>(z, d, acc);
-    if (c.full) seg_add_left<T, RPT>(z, d, Acoef * c.dpg[c.a]);
+    if (c.full) {
+        if (TWO && !rag) seg_add_left2<T, RPT>(z, d, dH, Acoef * c.dpg[c.a]);
+        else seg_add_left<T, RPT>(z, d, Acoef * c.dpg[c.a]);
+    }
 }
 
 // One application of D on this thread's segment (MODE as in seg_make_q)
@@ -520,6 +731,13 @@ inline size_t batch_y_smem(size_t tsize) { return strided_slot_bytes(kBatchYWarp
 inline size_t batch_x_smem(size_t tsize, int W, int nbuf)
 {
     return (size_t)W * (sizeof(BatchProb) + (size_t)nbuf * 32 * (BatchX<float>::RMAX + 16 / tsize) * tsize);
+}
+// k_batch_xs: the problem, the exchange slots and nbuf fields of one row
+// (32 W segments of RPT + 16 / tsize elements)
+inline size_t batch_xs_smem(size_t tsize, int RPT, int W, int nbuf)
+{
+    const size_t slots = tsize == 4 ? row_slots_bytes<float, 8>() : row_slots_bytes<double, 8>();
+    return sizeof(BatchProb) + slots + (size_t)nbuf * 32 * W * (RPT + 16 / tsize) * tsize;
 }
 
 // ---------------------------------------------------------------------------

@@ -28,7 +28,7 @@ cudaError_t attr_res()
 }
 
 template <int RPT, int NB, int W>
-size_t rows_smem() { return row_slots_bytes<W>() + (size_t)NB * 32 * W * ContigStage<float, RPT>::SST * sizeof(float); }
+size_t rows_smem() { return row_slots_bytes<float, W>() + (size_t)NB * 32 * W * ContigStage<float, RPT>::SST * sizeof(float); }
 
 template <int BC, int RPT, int NB, int W>
 cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)

@@ -147,6 +147,76 @@ __device__ __forceinline__ void seg_bwd_scan(T (&z)[RPT], T d, T acc, int kl = 0
     }
 }
 
+// Two-chain forms of the three recurrences (segments of RPT >= 16, no
+// ragged end): the halves [0, H) and [H, RPT) advance together, which halves
+// the length of the dependent chains.  The second half of the causal scan
+// starts from y_{H-1} = d^H yin + E1 (E1 = the first half's zero-inflow total
+// from the reduction); the first half of the anti-causal scan starts from
+// d e_H = d ER2 + d^{RPT-H} acc (ER2 = sum_j d^j y_{H+j} from the causal scan).
+template <class T, int RPT>
+__device__ __forceinline__ T seg_fwd_reduce2(const T (&q)[RPT], T d, T dH, T &E1)
+{
+    constexpr int H = RPT / 2;
+    T a = 0, b = 0;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        a = d * a + q[k];
+        b = d * b + q[H + k];
+    }
+    E1 = a;
+    return dH * a + b;
+}
+
+template <class T, int RPT>
+__device__ __forceinline__ T seg_fwd_scan2(T (&z)[RPT], T d, T dH, T y, T E1, T &ER2)
+{
+    constexpr int H = RPT / 2;
+    T ya = y, yb = dH * y + E1, ra = 0, rb = 0, pw = 1;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        ya = d * ya + z[k];
+        yb = d * yb + z[H + k];
+        z[k] = ya;
+        z[H + k] = yb;
+        ra += pw * ya;
+        rb += pw * yb;
+        pw *= d;
+    }
+    ER2 = rb;
+    return ra + dH * rb;
+}
+
+// dHc = d^{RPT-H}
+template <class T, int RPT>
+__device__ __forceinline__ void seg_bwd_scan2(T (&z)[RPT], T d, T dHc, T acc, T ER2)
+{
+    constexpr int H = RPT / 2;
+    T accb = acc, acca = d * ER2 + dHc * acc;
+#pragma unroll
+    for (int k = H - 1; k >= 0; --k) {
+        const T eb = accb + z[H + k];
+        const T ea = acca + z[k];
+        accb = d * eb;
+        acca = d * ea;
+        z[H + k] = eb;
+        z[k] = ea;
+    }
+}
+
+template <class T, int RPT>
+__device__ __forceinline__ void seg_add_left2(T (&z)[RPT], T d, T dH, T w0)
+{
+    constexpr int H = RPT / 2;
+    T wa = w0, wb = w0 * dH;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        z[k] += wa;
+        z[H + k] += wb;
+        wa *= d;
+        wb *= d;
+    }
+}
+
 // z_k += A' d^{a+k}, given w0 = A' d^a
 template <class T, int RPT>
 __device__ __forceinline__ void seg_add_left(T (&z)[RPT], T d, T w0)
@@ -228,7 +298,11 @@ __device__ __forceinline__ void warp_solve(T (&z)[RPT], const AxisDev &A, int la
 
     // causal carries: Kogge-Stone over lanes with multipliers d^{RPT 2^k};
     // all shuffles of a group run before any lane-dependent branch
-    const T E = seg_fwd_reduce<T, RPT>(z, d);
+    constexpr bool TWO = !RAG && RPT >= 16;
+    const T *dpg = dpow_of<T>(A);
+    const T dH = TWO ? dpg[RPT / 2] : (T)0;
+    T E1 = 0, ER2 = 0;
+    const T E = TWO ? seg_fwd_reduce2<T, RPT>(z, d, dH, E1) : seg_fwd_reduce<T, RPT>(z, d);
     __syncwarp();
     T x = E;
 #pragma unroll
@@ -239,12 +313,11 @@ __device__ __forceinline__ void warp_solve(T (&z)[RPT], const AxisDev &A, int la
     T yin = __shfl_up_sync(0xffffffffu, x, 1);
     const T tot = __shfl_sync(0xffffffffu, x, Ld);              // zero-inflow y_{n-1}
     yin = (lane == 0) ? (T)0 : yin;
-    const T *dpg = dpow_of<T>(A);
     if (BC == BC_PERIODIC)
         yin += full ? dpg[a] * (tot * (T)A.inv) : (T)0;          // images to the left
     yin = full ? yin : (T)0;                                     // lanes past the line stay zero
     T ylast = 0;
-    const T ER = seg_fwd_scan<T, RPT, RAG>(z, d, yin, kl, &ylast);
+    const T ER = TWO ? seg_fwd_scan2<T, RPT>(z, d, dH, yin, E1, ER2) : seg_fwd_scan<T, RPT, RAG>(z, d, yin, kl, &ylast);
 
     // anti-causal carries
     __syncwarp();
@@ -271,8 +344,12 @@ __device__ __forceinline__ void warp_solve(T (&z)[RPT], const AxisDev &A, int la
     const bool before = RAG ? lane < Ld : full;
     const int ia = full ? a : 0, ib = before ? n - a - RPT : 0;   // table indices in [0, n]
     const T acc = d * exclb + (before ? dpg[ib] * Z : (T)0);
-    seg_bwd_scan<T, RPT, RAG>(z, d, acc, kl, Z);
-    if (BC == BC_DIRICHLET && full) seg_add_left<T, RPT>(z, d, Acoef * dpg[ia]);
+    if constexpr (TWO) seg_bwd_scan2<T, RPT>(z, d, dH, acc, ER2);
+    else seg_bwd_scan<T, RPT, RAG>(z, d, acc, kl, Z);
+    if (BC == BC_DIRICHLET && full) {
+        if constexpr (TWO) seg_add_left2<T, RPT>(z, d, dH, Acoef * dpg[ia]);
+        else seg_add_left<T, RPT>(z, d, Acoef * dpg[ia]);
+    }
     __syncwarp();
 }
 
@@ -441,10 +518,10 @@ __device__ __forceinline__ void level_vec(const ProgParams &p, int64_t i, const 
     *reinterpret_cast<double2 *>((double *)p.un_hi + i) = v;
 }
 
-// level combination of CH vectors per lane (v = lane + 32*(i0+i)), all
-// loads issued before any store
-template <class T, int CH> struct LevelBatch;
-template <int CH> struct LevelBatch<float, CH> {
+// level combination of CH vectors per thread (v = lane + NT (i0 + i) with NT
+// threads over the row), all loads issued before any store
+template <class T, int CH, int NT = 32> struct LevelBatch;
+template <int CH, int NT> struct LevelBatch<float, CH, NT> {
     __device__ static void run(const ProgParams &p, int64_t base, int lane, int i0, int nvec, const float4 (&F)[CH])
     {
         const float4 *__restrict__ UH = reinterpret_cast<const float4 *>((const float *)p.u_hi + base);
@@ -455,7 +532,7 @@ template <int CH> struct LevelBatch<float, CH> {
         const bool prev = p.eb != 0.0;
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
-            const int v = lane + 32 * (i0 + i);
+            const int v = lane + NT * (i0 + i);
             if (v < nvec) {
                 uh[i] = __ldg(UH + v);
                 ul[i] = __ldg(UL + v);
@@ -468,7 +545,7 @@ template <int CH> struct LevelBatch<float, CH> {
         float4 *NL = reinterpret_cast<float4 *>((float *)p.un_lo + base);
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
-            const int v = lane + 32 * (i0 + i);
+            const int v = lane + NT * (i0 + i);
             if (v < nvec) {
                 float4 nh, nl;
                 level_pair(uh[i].x, ul[i].x, ph[i].x, pl[i].x, F[i].x, ea, eb, ec, nh.x, nl.x);
@@ -481,7 +558,7 @@ template <int CH> struct LevelBatch<float, CH> {
         }
     }
 };
-template <int CH> struct LevelBatch<double, CH> {
+template <int CH, int NT> struct LevelBatch<double, CH, NT> {
     __device__ static void run(const ProgParams &p, int64_t base, int lane, int i0, int nvec, const double2 (&F)[CH])
     {
         const double2 *__restrict__ U = reinterpret_cast<const double2 *>((const double *)p.u_hi + base);
@@ -490,7 +567,7 @@ template <int CH> struct LevelBatch<double, CH> {
         const bool prev = p.eb != 0.0;
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
-            const int v = lane + 32 * (i0 + i);
+            const int v = lane + NT * (i0 + i);
             if (v < nvec) {
                 u[i] = __ldg(U + v);
                 q[i] = prev ? __ldg(Q + v) : make_double2(0.0, 0.0);
@@ -499,7 +576,7 @@ template <int CH> struct LevelBatch<double, CH> {
         double2 *N = reinterpret_cast<double2 *>((double *)p.un_hi + base);
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
-            const int v = lane + 32 * (i0 + i);
+            const int v = lane + NT * (i0 + i);
             if (v < nvec) {
                 double2 r;
                 r.x = p.ea * u[i].x + p.ec * F[i].x + p.eb * q[i].x;
@@ -509,10 +586,10 @@ template <int CH> struct LevelBatch<double, CH> {
         }
     }
 };
-template <class T, int CH, class V>
+template <class T, int CH, int NT = 32, class V>
 __device__ __forceinline__ void level_batch(const ProgParams &p, int64_t base, int lane, int i0, int nvec, const V (&F)[CH])
 {
-    LevelBatch<T, CH>::run(p, base, lane, i0, nvec, F);
+    LevelBatch<T, CH, NT>::run(p, base, lane, i0, nvec, F);
 }
 
 template <class V> __device__ __forceinline__ V vfma(typename std::remove_reference<decltype(V().x)>::type c, const V &a, const V &b);
@@ -906,107 +983,187 @@ __global__ void __launch_bounds__(128) k_contig_res(AxisDev A, LineSet LS, ProgP
 // (three CTA barriers per sweep).  A row then costs about 1/W of the
 // single-warp latency, and the shorter segments need fewer registers, so more
 // rows are in flight per SM.
-template <int W>
+template <class T, int W>
 struct RowSlots {
-    float halo[W][4];    // per warp: z at its first two and last two points
-    float rhalo[W][2];   // per warp: r at its first and last point
-    float tc[W];         // per warp: zero-inflow causal total (y at its last point)
-    float ta[W];         // per warp: zero-inflow anti-causal total (e at its first point)
-    float yl;            // y_{n-1} of the row with zero inflow
+    T halo[W][4];    // per warp: z at its first two and last two points
+    T rhalo[W][2];   // per warp: r at its first and last point
+    T tc[W];         // per warp: zero-inflow causal total (y at its last point)
+    T ta[W];         // per warp: zero-inflow anti-causal total (e at its first point)
+    T yl;            // y_{n-1} of the row with zero inflow
 };
 
-template <int BC, int RPT, int W>
-__device__ __forceinline__ void row_sweep(float (&z)[RPT], const float (&r)[RPT], float rl, float rr, float cu,
-                                          const AxisDev &A, int lane, int warp, RowSlots<W> &sl)
+// Neighbours of the thread's segment: z at a-2, a-1 (left) and a+RPT,
+// a+RPT+1 (right), by shuffles inside the warp and through shared memory
+// across warps.  WRAP: the row's ends see each other (periodic); else the
+// outer halos of the row are left as the shuffles give them (the caller
+// replaces them).
+template <class T, int RPT, int W, bool WRAP>
+__device__ __forceinline__ void row_halos(const T (&z)[RPT], int lane, int warp, RowSlots<T, W> &sl, T &zl2, T &zl1,
+                                          T &zr0, T &zr1)
 {
-    const int n = A.n;
-    const float d = (float)A.d;
-    const int seg = warp * 32 + lane, a = seg * RPT;
-    constexpr int Ld = 32 * W - 1;                   // n = 32 W RPT: every segment is full
-    const float *dpg = A.dpow32;
-    const float c1 = (float)A.c1, c2 = (float)A.c2;
-
-    // halos: by shuffles inside the warp, through shared memory across warps
     __syncwarp();
-    float zl1 = __shfl_up_sync(0xffffffffu, z[RPT - 1], 1), zl2 = __shfl_up_sync(0xffffffffu, z[RPT - 2], 1);
-    float zr0 = __shfl_down_sync(0xffffffffu, z[0], 1), zr1 = __shfl_down_sync(0xffffffffu, z[1], 1);
+    zl1 = __shfl_up_sync(0xffffffffu, z[RPT - 1], 1);
+    zl2 = __shfl_up_sync(0xffffffffu, z[RPT - 2], 1);
+    zr0 = __shfl_down_sync(0xffffffffu, z[0], 1);
+    zr1 = __shfl_down_sync(0xffffffffu, z[1], 1);
     if (lane == 0) { sl.halo[warp][0] = z[0]; sl.halo[warp][1] = z[1]; }
     if (lane == 31) { sl.halo[warp][2] = z[RPT - 2]; sl.halo[warp][3] = z[RPT - 1]; }
     __syncthreads();
-    if (lane == 0 && (warp > 0 || BC == BC_PERIODIC)) {
+    if (lane == 0 && (warp > 0 || WRAP)) {
         const int wl = warp > 0 ? warp - 1 : W - 1;
         zl2 = sl.halo[wl][2];
         zl1 = sl.halo[wl][3];
     }
-    if (lane == 31 && (warp < W - 1 || BC == BC_PERIODIC)) {
+    if (lane == 31 && (warp < W - 1 || WRAP)) {
         const int wr = warp < W - 1 ? warp + 1 : 0;
         zr0 = sl.halo[wr][0];
         zr1 = sl.halo[wr][1];
     }
-    if (BC == BC_DIRICHLET) end_ghosts<float, RPT, 2>(z, seg == 0, seg == Ld, zl2, zl1, zr0, zr1);
-    seg_make_q<float, RPT, 2>(z, zl2, zl1, zr0, zr1, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : r[k]); }, cu,
-                              c1, c2);
-    if (BC == BC_DIRICHLET) end_zero<float, RPT>(z, seg == 0, seg == Ld);
+}
 
-    // causal carries: Kogge-Stone inside the warp, then across the warps
-    const float E = seg_fwd_reduce<float, RPT>(z, d);
+// The solve of the difference form on a row held by the W warps of a CTA
+// (thread 32 warp + lane owns segment a = (32 warp + lane) RPT): z holds q on
+// entry (zero past the row) and e on exit.  Carries: Kogge-Stone inside each
+// warp, then a short serial pass over the W warp totals in shared memory.
+// RAG (Dirichlet): the row's last point n-1 may sit anywhere in the last warp
+// (n > 32 (W-1) RPT); the segment routines' ragged variants handle it.
+template <class T, int BC, int RPT, int W, bool RAG>
+__device__ __forceinline__ void row_solve(T (&z)[RPT], const AxisDev &A, int lane, int warp, RowSlots<T, W> &sl)
+{
+    static_assert(!RAG || BC == BC_DIRICHLET, "ragged rows are Dirichlet rows");
+    const int n = A.n;
+    const T d = (T)A.d;
+    const int seg = warp * 32 + lane, a = seg * RPT;
+    const int Ld = RAG ? (n - 1) / RPT : 32 * W - 1;  // segment holding the last point
+    const int kl = n - 1 - a;
+    const bool full = seg <= Ld;
+    const T *dpg = dpow_of<T>(A);
+
+    constexpr bool TWO = !RAG && RPT >= 16;
+    const T dH = TWO ? dpg[RPT / 2] : (T)0;
+    T E1 = 0, ER2 = 0;
+    const T E = TWO ? seg_fwd_reduce2<T, RPT>(z, d, dH, E1) : seg_fwd_reduce<T, RPT>(z, d);
     __syncwarp();
-    float x = E;
+    T x = E;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        const float y = __shfl_up_sync(0xffffffffu, x, 1 << k);
-        x = (lane >= (1 << k)) ? x + (float)A.dm[k] * y : x;
+        const T y = __shfl_up_sync(0xffffffffu, x, 1 << k);
+        x = (lane >= (1 << k)) ? x + (T)A.dm[k] * y : x;
     }
-    float yin = __shfl_up_sync(0xffffffffu, x, 1);
-    yin = (lane == 0) ? 0.f : yin;
+    T yin = __shfl_up_sync(0xffffffffu, x, 1);
+    yin = (lane == 0) ? (T)0 : yin;
     if (lane == 31) sl.tc[warp] = x;
     __syncthreads();
-    const float DW = dpg[32 * RPT];                  // decay over one warp's points
-    float cin = 0.f, tot = 0.f;
+    const T DW = dpg[32 * RPT];                      // decay over one warp's points
+    T cin = 0, tot = 0;
 #pragma unroll
     for (int w2 = 0; w2 < W; ++w2) {
         cin = (w2 == warp) ? tot : cin;
         tot = DW * tot + sl.tc[w2];
     }
     yin += dpg[lane * RPT] * cin;
-    if (BC == BC_PERIODIC) yin += dpg[a] * (tot * (float)A.inv);   // images to the left
-    const float ER = seg_fwd_scan<float, RPT>(z, d, yin);
+    if (BC == BC_PERIODIC) yin += dpg[a] * (tot * (T)A.inv);       // images to the left
+    if (RAG) yin = full ? yin : (T)0;
+    T ylast = 0;
+    const T ER = TWO ? seg_fwd_scan2<T, RPT>(z, d, dH, yin, E1, ER2) : seg_fwd_scan<T, RPT, RAG>(z, d, yin, kl, &ylast);
 
     // anti-causal carries
     __syncwarp();
-    float xb = ER;
+    T xb = ER;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        const float t = __shfl_down_sync(0xffffffffu, xb, 1 << k);
-        xb = (lane + (1 << k) < 32) ? xb + (float)A.dm[k] * t : xb;
+        const T t = __shfl_down_sync(0xffffffffu, xb, 1 << k);
+        xb = (lane + (1 << k) < 32) ? xb + (T)A.dm[k] * t : xb;
     }
-    float exclb = __shfl_down_sync(0xffffffffu, xb, 1);
-    exclb = (lane == 31) ? 0.f : exclb;
+    T exclb = __shfl_down_sync(0xffffffffu, xb, 1);
+    exclb = (lane == 31) ? (T)0 : exclb;
     if (lane == 0) sl.ta[warp] = xb;
-    if (warp == W - 1 && lane == 31) sl.yl = z[RPT - 1];
+    if (RAG) {
+        if (kl >= 0 && kl < RPT) sl.yl = ylast;
+    } else if (warp == W - 1 && lane == 31) {
+        sl.yl = z[RPT - 1];
+    }
     __syncthreads();
-    float cinb = 0.f, e00 = 0.f;
+    T cinb = 0, e00 = 0;
 #pragma unroll
     for (int w2 = W - 1; w2 >= 0; --w2) {
         cinb = (w2 == warp) ? e00 : cinb;
         e00 = DW * e00 + sl.ta[w2];
     }
     exclb += dpg[(31 - lane) * RPT] * cinb;
-    float Z, Acoef = 0.f;
+    T Z, Acoef = 0;
     if (BC == BC_DIRICHLET) {
-        const float mu = (float)A.mu, inv = (float)A.inv, yl = sl.yl;
+        const T mu = (T)A.mu, inv = (T)A.inv, yl = sl.yl;
         Acoef = (mu * yl - e00) * inv;
         Z = (mu * e00 - yl) * inv;
     } else {
-        Z = d * e00 * (float)A.inv;
+        Z = d * e00 * (T)A.inv;
     }
-    seg_bwd_scan<float, RPT>(z, d, d * exclb + dpg[n - a - RPT] * Z);
-    if (BC == BC_DIRICHLET) seg_add_left<float, RPT>(z, d, Acoef * dpg[a]);
+    // B' d^{n-1-j}: through the inflow of every segment that ends before the
+    // last point; RAG injects it at the last point itself
+    const bool before = RAG ? seg < Ld : true;
+    const T acc = d * exclb + (before ? dpg[before ? n - a - RPT : 0] * Z : (T)0);
+    if constexpr (TWO) seg_bwd_scan2<T, RPT>(z, d, dH, acc, ER2);
+    else seg_bwd_scan<T, RPT, RAG>(z, d, acc, kl, Z);
+    if (BC == BC_DIRICHLET && full) {
+        if constexpr (TWO) seg_add_left2<T, RPT>(z, d, dH, Acoef * dpg[a]);
+        else seg_add_left<T, RPT>(z, d, Acoef * dpg[a]);
+    }
     __syncwarp();
 }
 
-template <int W>
-__host__ __device__ constexpr size_t row_slots_bytes() { return (sizeof(RowSlots<W>) + 15) & ~(size_t)15; }
+// One application of D (MODE 2: z + cu r, r the second difference of u in
+// registers with its row neighbours rl, rr) on a row split over W warps
+template <class T, int BC, int RPT, int W, bool RAG = false>
+__device__ __forceinline__ void row_sweep(T (&z)[RPT], const T (&r)[RPT], T rl, T rr, T cu, const AxisDev &A, int lane,
+                                          int warp, RowSlots<T, W> &sl)
+{
+    const int n = A.n;
+    const int seg = warp * 32 + lane, a = seg * RPT;
+    const int Ld = RAG ? (n - 1) / RPT : 32 * W - 1;
+    const int kl = n - 1 - a;
+    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    T zl2, zl1, zr0, zr1;
+    row_halos<T, RPT, W, BC == BC_PERIODIC>(z, lane, warp, sl, zl2, zl1, zr0, zr1);
+    if (BC == BC_DIRICHLET) end_ghosts<T, RPT, 2>(z, seg == 0, !RAG && seg == Ld, zl2, zl1, zr0, zr1);
+    seg_make_q<T, RPT, 2, RAG>(z, zl2, zl1, zr0, zr1, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : r[k]); }, cu,
+                               c1, c2, kl);
+    if (BC == BC_DIRICHLET) end_zero<T, RPT>(z, seg == 0, !RAG && seg == Ld);
+    if (RAG && seg > Ld) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0;
+    }
+    row_solve<T, BC, RPT, W, RAG>(z, A, lane, warp, sl);
+}
+
+// D^T (z + cu u) on a Dirichlet row split over W warps (the transposed
+// difference form of post_T; any n with 32 (W-1) RPT < n <= 32 W RPT)
+template <class T, int RPT, int W>
+__device__ __forceinline__ void row_sweep_T(T (&z)[RPT], const T (&u)[RPT], T cu, const AxisDev &A, int lane, int warp,
+                                            RowSlots<T, W> &sl)
+{
+    const int n = A.n, seg = warp * 32 + lane, a = seg * RPT, kl = n - 1 - a;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const T q = z[k] + cu * u[k];
+        z[k] = (k < kl && (seg > 0 || k > 0)) ? q : (T)0;      // interior rows only
+    }
+    row_solve<T, BC_DIRICHLET, RPT, W, true>(z, A, lane, warp, sl);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) z[k] = (k < kl && (seg > 0 || k > 0)) ? z[k] : (T)0;
+    T el2, el1, er0, er1;
+    row_halos<T, RPT, W, false>(z, lane, warp, sl, el2, el1, er0, er1);
+    const bool first = seg == 0, last = seg == 32 * W - 1;
+    el2 = first ? (T)0 : el2;
+    el1 = first ? (T)0 : el1;
+    er0 = last ? (T)0 : er0;
+    er1 = last ? (T)0 : er1;
+    post_T<T, RPT, true>(z, el2, el1, er0, er1, (T)A.c1, (T)A.c2, a, n);
+    __syncwarp();
+}
+
+template <class T, int W>
+__host__ __device__ constexpr size_t row_slots_bytes() { return (sizeof(RowSlots<T, W>) + 15) & ~(size_t)15; }
 
 template <int BC, int RPT, int NB, int W>
 __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : 6) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr)
@@ -1018,8 +1175,8 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : 6) k_contig_rows(AxisDev 
     constexpr int LINE = NT * St::SST;                // one field of the row in the segment layout
     constexpr int NVL = RPT / 4;                      // 16-byte vectors per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    RowSlots<W> &sl = *reinterpret_cast<RowSlots<W> *>(smem_raw);
-    T *B = reinterpret_cast<T *>(smem_raw + row_slots_bytes<W>());
+    RowSlots<T, W> &sl = *reinterpret_cast<RowSlots<T, W> *>(smem_raw);
+    T *B = reinterpret_cast<T *>(smem_raw + row_slots_bytes<T, W>());
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int n = A.n;                                // == NT * RPT
     const int64_t row = blockIdx.x;
@@ -1118,7 +1275,7 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : 6) k_contig_rows(AxisDev 
             }
         }
         if (tt == 0) break;
-        row_sweep<BC, RPT, W>(z, r, rl, rr, (T)__ldg(pr.cu + tt), A, lane, warp, sl);
+        row_sweep<T, BC, RPT, W>(z, r, rl, rr, (T)__ldg(pr.cu + tt), A, lane, warp, sl);
     }
 
     // F -> coalesced side -> next level
@@ -1301,12 +1458,14 @@ __device__ __forceinline__ void strided_sweep(const StridedCtx<T> &c, const Axis
         for (int k = 0; k < RPT; ++k) z[k] = 0;
     }
     const T d = c.d;
-    const T E = seg_fwd_reduce<T, RPT>(z, d);
+    const T dH = c.dpg[RPT / 2];
+    T E1, ER2;
+    const T E = seg_fwd_reduce2<T, RPT>(z, d, dH, E1);
     T yin, ytot;
     strided_causal<T, RPT>(c, E, yin, ytot);
     if (BC == BC_PERIODIC && c.full) yin += c.dpg[c.a] * (ytot * (T)A.inv);
     if (!c.full) yin = 0;                                          // segments past the line stay zero
-    const T ER = seg_fwd_scan<T, RPT>(z, d, yin);
+    const T ER = seg_fwd_scan2<T, RPT>(z, d, dH, yin, E1, ER2);
     T eout, e00;
     strided_anticausal<T, RPT>(c, ER, eout, e00);
     T Z, Acoef = 0;
@@ -1318,8 +1477,8 @@ __device__ __forceinline__ void strided_sweep(const StridedCtx<T> &c, const Axis
         Z = d * e00 * (T)A.inv;
     }
     const T acc = d * eout + (c.full ? c.dpg[c.n - c.a - RPT] * Z : (T)0);
-    seg_bwd_scan<T, RPT>(z, d, acc);
-    if (BC == BC_DIRICHLET && c.full) seg_add_left<T, RPT>(z, d, Acoef * c.dpg[c.a]);
+    seg_bwd_scan2<T, RPT>(z, d, dH, acc, ER2);
+    if (BC == BC_DIRICHLET && c.full) seg_add_left2<T, RPT>(z, d, dH, Acoef * c.dpg[c.a]);
 }
 
 // second differences r of u at points a-1 .. a+RPT of one strided line, from

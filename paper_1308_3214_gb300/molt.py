@@ -33,7 +33,7 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
            "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times", "mol_batch_apply_FT",
            "mol_batch_traces", "mol_batch_adjoint", "mol_batch_update", "mol_autotune", "mol_get_tuning", "mol_set_tuning",
-           "mol_batch_autotune", "mol_batch_get_tuning", "mol_apply_FT", "mol_traces", "mol_adjoint"]
+           "mol_batch_autotune", "mol_batch_get_tuning", "mol_batch_set_tuning", "mol_apply_FT", "mol_traces", "mol_adjoint"]
 
 
 class MolError(RuntimeError):
@@ -116,6 +116,7 @@ def load_library(path: Path | None = None):
     lib.mol_traces.argtypes = [vp, vp, I, ctypes.POINTER(i64), i64, vp, vp]
     lib.mol_adjoint.argtypes = [vp, I, ctypes.POINTER(i64), i64, vp, vp, vp]
     lib.mol_batch_get_tuning.argtypes = [vp, ctypes.POINTER(I), dp]
+    lib.mol_batch_set_tuning.argtypes = [vp, I, I, I]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
@@ -493,6 +494,11 @@ class BatchSolver:
         """Time the launch variants on this batch and keep the fastest."""
         self._check(self.lib.mol_batch_autotune(self.h, ctypes.c_void_p(_stream_ptr(stream))))
         return self.tuning()
+
+    def set_tuning(self, x_warps=(8, 8), y_rule: int = 0):
+        """Launch variants by hand: x_warps = (short rows, long rows; 0 = long
+        rows split over two warps of one CTA), y_rule 0 or 1."""
+        self._check(self.lib.mol_batch_set_tuning(self.h, int(x_warps[0]), int(x_warps[1]), int(y_rule)))
 
     def tuning(self) -> dict:
         out = (ctypes.c_int * 3)()

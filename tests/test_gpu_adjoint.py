@@ -66,17 +66,20 @@ def receivers(shapes, offsets, per, seed):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_FT_matches_oracle(prec):
-    b, specs = make(SHAPES, prec)
+@pytest.mark.parametrize("long_rows", ["split", "warp"])
+def test_FT_matches_oracle(prec, long_rows):
+    shapes = SHAPES + [(6, 513), (4, 529), (5, 1024), (7, 800)]
+    b, specs = make(shapes, prec)
+    b.set_tuning((4, 0 if long_rows == "split" else 4), 0)
     rng = np.random.default_rng(1)
-    ws = [rng.normal(size=s) for s in SHAPES]
+    ws = [rng.normal(size=s) for s in shapes]
     got = b.unpack(b.apply_FT(b.pack(ws)))
     torch.cuda.synchronize()
     for i, (w, g, (P, dt, beta, nu)) in enumerate(zip(ws, got, specs)):
         ref = oracle.FT(w, nu, P, beta, "dirichlet")
         cond = np.linalg.norm(w) / max(np.linalg.norm(ref), 1e-300)
         tol = max(1e-12, 64 * EPS64 * cond) if prec == "fp64" else 2 * model(nu, P) * max(cond, 1.0)
-        assert rel_l2(g.cpu().numpy(), ref) <= tol, (i, SHAPES[i])
+        assert rel_l2(g.cpu().numpy(), ref) <= tol, (i, shapes[i])
 
 
 def test_FT_is_the_transpose_of_F_on_the_gpu():

@@ -75,10 +75,19 @@ def mixed_tol(nu, p):
     return 16 * EPS32 * (1.0 + 1.0 / (1.0 - dmax)) * p
 
 
+# rows of 513..1024 points with the last point at the first, a middle and the
+# last point of a 16-point segment of the split x pass, and in either warp
+LONG_SHAPES = [(6, 513), (5, 528), (4, 529), (7, 545), (3, 1023), (8, 1024), (9, 777)]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batch_F_matches_oracle(prec):
-    b, specs = make_batch(SHAPES, prec)
-    us = [rough_field(s, 300 + i) for i, s in enumerate(SHAPES)]
+@pytest.mark.parametrize("long_rows", ["split", "warp"])
+def test_batch_F_matches_oracle(prec, long_rows):
+    shapes = SHAPES + LONG_SHAPES
+    b, specs = make_batch(shapes, prec)
+    b.set_tuning((4, 0 if long_rows == "split" else 4), 0)
+    assert b.tuning()["x_warps"][1] == (0 if long_rows == "split" else 4)
+    us = [rough_field(s, 300 + i) for i, s in enumerate(shapes)]
     got = b.unpack(b.apply_F(b.pack(us)))
     torch.cuda.synchronize()
     for i, (u, g, (P, dt, beta, nu)) in enumerate(zip(us, got, specs)):
@@ -86,7 +95,7 @@ def test_batch_F_matches_oracle(prec):
         cond = np.linalg.norm(u) / max(np.linalg.norm(ref), 1e-300)
         tol = max(1e-12, 64 * EPS64 * cond) if prec == "fp64" else mixed_tol(nu, 2 * P)
         err = rel_l2(g.cpu().numpy(), ref)
-        assert err <= tol, (i, SHAPES[i], P, err, tol)
+        assert err <= tol, (i, shapes[i], P, err, tol)
 
 
 STEP_SHAPES = [(64, 64), (65, 67), (5, 130), (100, 129), (250, 257), (300, 17), (129, 4), (40, 512), (33, 1021)]
@@ -192,10 +201,17 @@ def test_batch_full_size_512_problems_sampled():
         assert rel_l2(res["mixed"][i], res["fp64"][i]) <= mixed_tol((nu, nu), 2 * p.P), i
 
 
+def test_batch_set_tuning_rejects_bad_choices():
+    b, _ = make_batch(SHAPES[:3], "mixed")
+    for bad in (((3, 8), 0), ((8, 1), 0), ((8, 8), 2), ((0, 8), 0)):
+        with pytest.raises(molt.MolError):
+            b.set_tuning(*bad)
+
+
 def test_batch_autotune_choice_keeps_parity():
     b, specs = make_batch(SHAPES, "mixed")
     tun = b.autotune()
-    assert all(w in (2, 4, 8) for w in tun["x_warps"]) and tun["y_rule"] in (0, 1)
+    assert tun["x_warps"][0] in (2, 4, 8) and tun["x_warps"][1] in (0, 2, 4, 8) and tun["y_rule"] in (0, 1)
     assert tun["x_ms"] > 0 and tun["y_ms"] > 0
     us = [rough_field(s, 900 + i) for i, s in enumerate(SHAPES)]
     got = b.unpack(b.apply_F(b.pack(us)))
