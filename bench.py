@@ -292,6 +292,10 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512, help="problems of the batch workload (profiling)")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed launch variants instead of the autotuner (profiling): res_warps,strided_rpt,"
+                         "strided_warps,rows_warps for a single problem; x_warps_short,x_warps_long,y_rule for "
+                         "the batch")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -343,7 +347,11 @@ def main():
 
     u0_host = spec["field"]()
     solver = make(args.prec)
-    tuning = solver.autotune()              # once per problem, as a user would
+    if args.tuning:
+        solver.set_tuning(*[int(v) for v in args.tuning.split(",")])
+        tuning = solver.tuning()
+    else:
+        tuning = solver.autotune()          # once per problem, as a user would
 
     def timed_steps(s, nsteps, warm):
         """Region A: nsteps through mol_step as a user runs it (CUDA-graph time
@@ -395,7 +403,11 @@ def main():
     alg_bytes = bpp[dom_axis] * N
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
     peak, peak_kind = read_peak()
-    kernel_name = {0: "k_contig (x: Horner + level update)",
+    if tuning.get("rows_warps", 0) > 0:
+        xk = f"k_contig_rows (x: one row per CTA of {tuning['rows_warps']} warps; Horner + level update)"
+    else:
+        xk = "k_contig_res / k_contig (x: one row per warp; Horner + level update)"
+    kernel_name = {0: xk,
                    1: "k_strided (y: powers of D_y)" if len(shape) == 2 else "k_strided (y: Horner, P+1 outputs)",
                    2: "k_strided (z: powers of D_z)"}[dom_axis]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -555,7 +567,12 @@ def main_batch(args, spec):
         return molt.BatchSolver(shapes, dt=dts, P=Ps, prec=prec, **kw)
 
     b = make(args.prec)
-    tuning = b.autotune()
+    if args.tuning:
+        xs, xl, yr = [int(v) for v in args.tuning.split(",")]
+        b.set_tuning((xs, xl), yr)
+        tuning = b.tuning()
+    else:
+        tuning = b.autotune()
     u0 = b.pack([p.u0 for p in probs])
 
     def timed(bs, nsteps, warm):
@@ -598,7 +615,9 @@ def main_batch(args, spec):
     dom_axis = max(passes, key=lambda a: passes[a][0])
     dom_ms = passes[dom_axis][0] / passes[dom_axis][1]
     achieved = bpp_tot[dom_axis] / (dom_ms * 1e-3) / 1e9
-    kernel_name = {0: "k_batch_x (x pass: Horner + level update; rows <= 512 and longer rows, two launches)",
+    long_x = ("k_batch_xs (one CTA of two warps per row)" if tuning["x_warps"][1] == 0
+              else "k_batch_x<LARGE> (one warp per row)")
+    kernel_name = {0: f"k_batch_x (x pass: Horner + level update; rows <= 512) + {long_x} for longer rows",
                    1: "k_batch_y (y pass: powers of D_y)"}[dom_axis]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": read_traffic(dom_axis, spec["name"], args.prec, "batch"),

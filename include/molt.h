@@ -164,7 +164,7 @@ mol_status mol_autotune(mol_handle h, void *stream);
 
 /* Force launch choices (e.g. a tuning result kept from an earlier run):
  * res_warps 1, 2 or 4; strided_rpt 0 (default) or 32; strided_warps 1..8;
- * rows_warps 0 (one warp per row) or 2, 4 (each row split over that many
+ * rows_warps 0 (one warp per row) or 2, 4, 8 (each row split over that many
  * warps, where the row length allows it).  MOL_EINVAL if a choice is out of
  * range or does not fit an axis. */
 mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int strided_warps, int rows_warps);

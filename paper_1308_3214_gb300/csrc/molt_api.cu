@@ -203,6 +203,7 @@ AxisDev regs_axis(const mol_ctx *h, int axis, int rpt)
 {
     AxisDev A = h->ax[axis];
     for (int k = 0; k < 5; ++k) A.dm[k] = h->dmr_ax[axis][rpt_index(rpt)][k];
+    axis_mirror(A);
     return A;
 }
 
@@ -283,6 +284,7 @@ mol_status run_horner(mol_ctx *h, int axis, HornerParams &hp, const double *dcoe
     pr.cu = dcu;
     pr.epi = hp.epi;
     pr.ea = hp.ea; pr.eb = hp.eb; pr.ec = hp.ec;
+    prog_mirror(pr, hp);
     pr.u_hi = hp.u_hi; pr.u_lo = hp.u_lo; pr.up_hi = hp.up_hi; pr.up_lo = hp.up_lo;
     pr.un_hi = hp.un_hi; pr.un_lo = hp.un_lo;
     return run_program(h, axis, pr, nullptr, &hp, s);
@@ -787,7 +789,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
     // or each row split over 2 or 4 warps (code -2, -4)
     std::vector<int> warps_c = res ? std::vector<int>{1, 2, 4} : std::vector<int>{h->tune_res_warps};
     if (h->ndim >= 2) {
-        for (int W : {2, 4})
+        for (int W : {2, 4, 8})
             if (regs_rows_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, W, &dummy)) warps_c.push_back(-W);
     }
     std::vector<std::pair<int, int>> str_c = {{h->tune_strided_rpt, h->tune_strided_warps}};
@@ -859,7 +861,8 @@ mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int stri
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
     if (res_warps != 1 && res_warps != 2 && res_warps != 4) return fail(h, MOL_EINVAL, "res_warps must be 1, 2 or 4");
-    if (rows_warps != 0 && rows_warps != 2 && rows_warps != 4) return fail(h, MOL_EINVAL, "rows_warps must be 0, 2 or 4");
+    if (rows_warps != 0 && rows_warps != 2 && rows_warps != 4 && rows_warps != 8)
+        return fail(h, MOL_EINVAL, "rows_warps must be 0, 2, 4 or 8");
     if (strided_rpt != 0 && strided_rpt != 32) return fail(h, MOL_EINVAL, "strided_rpt must be 0 or 32");
     if (strided_warps < 1 || strided_warps > 8) return fail(h, MOL_EINVAL, "strided_warps must be in 1..8");
     for (int a = 1; a < h->ndim; ++a) {

@@ -37,8 +37,9 @@ struct mol_batch_ctx {
     float *dp32 = nullptr;
     BLevel lev[3];
     double *io[2] = {nullptr, nullptr};  // packed float64 fields of mol_batch_solve_host
-    long long *irec = nullptr;           // receivers in the internal layout
-    int nrec = 0, irec_cap = 0;
+    long long *irec = nullptr;           // receivers in the internal layout, then their distinct
+    int nrec = 0, irec_cap = 0;          //   nodes, the node groups' starts and the receivers by node
+    int nnode = 0;
     void *inter[BMAXP] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int xW[2] = {8, 8}, xgrid[2] = {1, 1}, ygrid = 1, nbuf = 1, cgrid = 1;
     size_t xsmem[2] = {0, 0}, ysmem = 0;
@@ -121,6 +122,13 @@ int pick_rpt_y(int n, int mode = 0)
 }
 
 bool long_row(int nx) { return nx > 16 * 32; }
+
+// the problem table to the device, with its float32 copies refreshed
+cudaError_t upload_table(mol_batch_ctx *b)
+{
+    for (BatchProb &pb : b->hp) batch_mirror(pb);
+    return cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice);
+}
 
 // per-problem x-pass segment constants of the long rows for the current
 // choice: 16-point segments over two warps (split) or 32-point segments
@@ -266,6 +274,9 @@ mol_status run_update(mol_batch_ctx *b, const BLevel &u, const BLevel &up, const
     x.pr.ea = ea;
     x.pr.eb = eb;
     x.pr.ec = ec;
+    x.pr.fea = (float)ea;
+    x.pr.feb = (float)eb;
+    x.pr.fec = (float)ec;
     return run_pass(b, 0, x, s, adj);
 }
 
@@ -310,6 +321,23 @@ mol_status set_receivers(mol_batch_ctx *b, int nrec, const int64_t *rec, cudaStr
         const int64_t loc = g - b->uoff[p];
         ir[r] = pb.off + (loc / pb.ax.n) * pb.pitch + loc % pb.ax.n;
     }
+    // receivers grouped by node (stable: each group in receiver order), so
+    // that the injection runs one thread per distinct node
+    std::vector<int> ord(nrec);
+    for (int r = 0; r < nrec; ++r) ord[r] = r;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return ir[x] < ir[y]; });
+    std::vector<long long> buf(4 * (size_t)nrec + 1, 0);
+    long long *node = buf.data() + nrec, *start = node + nrec, *order = start + nrec + 1;
+    int nn = 0;
+    for (int j = 0; j < nrec; ++j) {
+        if (j == 0 || ir[ord[j]] != ir[ord[j - 1]]) {
+            node[nn] = ir[ord[j]];
+            start[nn++] = j;
+        }
+        order[j] = ord[j];
+    }
+    start[nn] = nrec;
+    for (int r = 0; r < nrec; ++r) buf[r] = ir[r];
     BCK(cudaStreamSynchronize(s), "stream synchronize");
     if (nrec > b->irec_cap) {
         if (b->irec) {
@@ -318,12 +346,13 @@ mol_status set_receivers(mol_batch_ctx *b, int nrec, const int64_t *rec, cudaStr
             b->irec = nullptr;
             b->irec_cap = 0;
         }
-        mol_status st = balloc(b, (void **)&b->irec, sizeof(long long) * nrec);
+        mol_status st = balloc(b, (void **)&b->irec, sizeof(long long) * (4 * (size_t)nrec + 1));
         if (st != MOL_OK) return st;
         b->irec_cap = nrec;
     }
-    BCK(cudaMemcpy(b->irec, ir.data(), sizeof(long long) * nrec, cudaMemcpyHostToDevice), "receiver upload");
+    BCK(cudaMemcpy(b->irec, buf.data(), sizeof(long long) * buf.size(), cudaMemcpyHostToDevice), "receiver upload");
     b->nrec = nrec;
+    b->nnode = nn;
     return MOL_OK;
 }
 
@@ -339,8 +368,13 @@ mol_status gather(mol_batch_ctx *b, const BLevel &L, double *out, cudaStream_t s
 
 mol_status inject(mol_batch_ctx *b, const BLevel &L, const double *vals, cudaStream_t s)
 {
-    if (b->tbytes == 4) k_batch_inject<float><<<1, 32, 0, s>>>((float *)L.hi, (float *)L.lo, b->irec, b->nrec, vals);
-    else k_batch_inject<double><<<1, 32, 0, s>>>((double *)L.hi, nullptr, b->irec, b->nrec, vals);
+    // layout of the receiver buffer: see set_receivers
+    const long long *node = b->irec + b->nrec, *start = node + b->nrec, *order = start + b->nrec + 1;
+    const int blocks = (b->nnode + 127) / 128;
+    if (b->tbytes == 4)
+        k_batch_inject<float><<<blocks, 128, 0, s>>>((float *)L.hi, (float *)L.lo, node, start, order, b->nnode, vals);
+    else
+        k_batch_inject<double><<<blocks, 128, 0, s>>>((double *)L.hi, nullptr, node, start, order, b->nnode, vals);
     BCK(cudaGetLastError(), "receiver injection");
     b->launches++;
     return MOL_OK;
@@ -540,7 +574,7 @@ mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, c
         if ((st = balloc(b, (void **)&b->row_prob, sizeof(int) * rp.size())) != MOL_OK) goto bad;
         if ((st = balloc(b, (void **)&b->items, sizeof(int2) * it.size())) != MOL_OK) goto bad;
         if ((st = balloc(b, (void **)&b->uoff_dev, sizeof(long long) * uo.size())) != MOL_OK) goto bad;
-        if ((e = cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        if ((e = upload_table(b)) != cudaSuccess ||
             (e = cudaMemcpy(b->row_prob, rp.data(), sizeof(int) * rp.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMemcpy(b->items, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMemcpy(b->uoff_dev, uo.data(), sizeof(long long) * uo.size(), cudaMemcpyHostToDevice)) !=
@@ -806,7 +840,7 @@ mol_status mol_batch_autotune(mol_batch b, void *stream)
     // warps per CTA of each x launch (the other held; long rows also split
     // over two warps, W = 0 below), then the y segment rule
     auto upload = [&]() {
-        return cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice);
+        return upload_table(b);
     };
     for (int L = 0; L < 2; ++L) {
         if ((L == 0 && b->rows_small == 0) || (L == 1 && b->nrows == b->rows_small)) continue;
@@ -868,7 +902,7 @@ mol_status mol_batch_set_tuning(mol_batch b, int x_warps_short, int x_warps_long
     set_x_segments(b);
     set_y_segments(b);
     BCK(cudaDeviceSynchronize(), "synchronise before the table upload");
-    BCK(cudaMemcpy(b->probs, b->hp.data(), sizeof(BatchProb) * b->nprob, cudaMemcpyHostToDevice), "table upload");
+    BCK(upload_table(b), "table upload");
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
     return MOL_OK;
 }

@@ -41,7 +41,31 @@ struct BatchProb {
     int pad_;
     double cu[BMAXP + 1];            // x Horner weights of u, t = 0..P
     double coef[BMAXP + 1][BMAXP];   // x Horner weights of g_k, t = 0..P, k < P
+    float cu32[BMAXP + 1];           // float32 copies (batch_mirror)
+    float coef32[BMAXP + 1][BMAXP];
+
+    template <class T> __device__ T ccu(int t) const
+    {
+        if constexpr (sizeof(T) == 4) return cu32[t];
+        else return cu[t];
+    }
+    template <class T> __device__ T ccoef(int t, int k) const
+    {
+        if constexpr (sizeof(T) == 4) return coef32[t][k];
+        else return coef[t][k];
+    }
 };
+
+// fills a problem's float32 copies (after any change to its constants)
+inline void batch_mirror(BatchProb &pb)
+{
+    axis_mirror(pb.ax);
+    axis_mirror(pb.ay);
+    for (int t = 0; t <= BMAXP; ++t) {
+        pb.cu32[t] = (float)pb.cu[t];
+        for (int k = 0; k < BMAXP; ++k) pb.coef32[t][k] = (float)pb.coef[t][k];
+    }
+}
 static_assert(sizeof(BatchProb) % 16 == 0, "BatchProb is copied in 8-byte words into 16-byte aligned slots");
 
 struct BatchPass {
@@ -106,7 +130,7 @@ __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams 
         const unsigned bytes = (unsigned)(nvec * 16);    // whole 16-byte vectors inside the pitch
         prefetch_l2(reinterpret_cast<const T *>(pr.u_hi) + base, bytes);
         if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.u_lo) + base, bytes);
-        if (pr.eb != 0.0) {
+        if (pr.feb != 0.f) {
             prefetch_l2(reinterpret_cast<const T *>(pr.up_hi) + base, bytes);
             if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.up_lo) + base, bytes);
         }
@@ -206,7 +230,7 @@ __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams 
     for (int k = 0; k < RPT; ++k) z[k] = 0;
     for (int t = pb.P; t >= 0; --t) {
         for (int k = 0; k < ng; ++k) {
-            const T c = (T)pb.coef[t][k];
+            const T c = pb.ccoef<T>(t, k);
             if (c == (T)0) continue;
             const V *seg = reinterpret_cast<const V *>(B + k * LB + lane * St::SST);
 #pragma unroll
@@ -218,8 +242,8 @@ __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams 
             }
         }
         if (t == 0) break;
-        if (ADJ) warp_sweep_T<T, RPT>(z, r, (T)pb.cu[t], A, lane);
-        else warp_sweep_rreg<T, BC_DIRICHLET, RPT, true>(z, r, (T)pb.cu[t], A, lane);
+        if (ADJ) warp_sweep_T<T, RPT>(z, r, pb.ccu<T>(t), A, lane);
+        else warp_sweep_rreg<T, BC_DIRICHLET, RPT, true>(z, r, pb.ccu<T>(t), A, lane);
     }
 
     // 4. F -> coalesced side -> next level; padding points get F = 0
@@ -309,7 +333,7 @@ __device__ __forceinline__ void batch_row_split(const BatchProb &pb, const ProgP
         const unsigned bytes = (unsigned)(nvec * 16);
         prefetch_l2(reinterpret_cast<const T *>(pr.u_hi) + base, bytes);
         if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.u_lo) + base, bytes);
-        if (pr.eb != 0.0) {
+        if (pr.feb != 0.f) {
             prefetch_l2(reinterpret_cast<const T *>(pr.up_hi) + base, bytes);
             if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.up_lo) + base, bytes);
         }
@@ -420,7 +444,7 @@ __device__ __forceinline__ void batch_row_split(const BatchProb &pb, const ProgP
     for (int k = 0; k < RPT; ++k) z[k] = 0;
     for (int tt = pb.P; tt >= 0; --tt) {
         for (int k = 0; k < ng; ++k) {
-            const T c = (T)pb.coef[tt][k];
+            const T c = pb.ccoef<T>(tt, k);
             if (c == (T)0) continue;
             const V *seg = reinterpret_cast<const V *>(B + k * LB + t * St::SST);
 #pragma unroll
@@ -432,8 +456,8 @@ __device__ __forceinline__ void batch_row_split(const BatchProb &pb, const ProgP
             }
         }
         if (tt == 0) break;
-        if (ADJ) row_sweep_T<T, RPT, W>(z, r, (T)pb.cu[tt], A, lane, warp, sl);
-        else row_sweep<T, BC_DIRICHLET, RPT, W, true>(z, r, rl, rr, (T)pb.cu[tt], A, lane, warp, sl);
+        if (ADJ) row_sweep_T<T, RPT, W>(z, r, pb.ccu<T>(tt), A, lane, warp, sl);
+        else row_sweep<T, BC_DIRICHLET, RPT, W, true>(z, r, rl, rr, pb.ccu<T>(tt), A, lane, warp, sl);
     }
 
     // 4. F -> coalesced side -> next level; padding points get F = 0
@@ -543,7 +567,7 @@ __device__ __forceinline__ void bsolve(const StridedCtx<T> &c, const AxisDev &A,
     T eout, e00;
     strided_anticausal<T, RPT>(c, ER, eout, e00);      // its barrier publishes YL
     const T yl = YL[c.lane];
-    const T mu = (T)A.mu, inv = (T)A.inv;
+    const T mu = A.cmu<T>(), inv = A.cinv<T>();
     const T Acoef = (mu * yl - e00) * inv;
     const T Z = (mu * e00 - yl) * inv;
     const T acc = d * eout + ((c.full && kl >= RPT) ? c.dpg[kl + 1 - RPT] * Z : (T)0);
@@ -563,7 +587,7 @@ __device__ __forceinline__ void bsweep(const StridedCtx<T> &c, const AxisDev &A,
 {
     const bool left = c.seg == 0;
     end_ghosts<T, RPT, MODE>(z, left, false, l2, l1, r0, r1);
-    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    const T c1 = A.cc1<T>(), c2 = A.cc2<T>();
     auto rz = [&](int) { return (T)0; };
     if (rag) seg_make_q<T, RPT, MODE, true>(z, l2, l1, r0, r1, rz, (T)0, c1, c2, kl);
     else seg_make_q<T, RPT, MODE, false>(z, l2, l1, r0, r1, rz, (T)0, c1, c2);
@@ -600,7 +624,7 @@ __device__ __forceinline__ void bsweep_T(const StridedCtx<T> &c, const AxisDev &
     interior_only<T, RPT>(c, z, kl, rag);
     T l2, l1, r0, r1;
     strided_halos<T, BC_DIRICHLET, RPT>(c, z, l2, l1, r0, r1, hbuf);
-    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    const T c1 = A.cc1<T>(), c2 = A.cc2<T>();
     if (c.seg == 0 || rag) post_T<T, RPT, true>(z, l2, l1, r0, r1, c1, c2, c.a, c.n);
     else post_T<T, RPT, false>(z, l2, l1, r0, r1, c1, c2, c.a, c.n);
 }
@@ -628,8 +652,8 @@ __device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams
     const AxisDev &A = pb.ay;
     const int n = A.n;
     c.n = n;
-    c.d = (T)A.d;
-    c.dR = (T)A.dm[0];
+    c.d = A.cd<T>();
+    c.dR = A.cdm<T>(0);
     c.dpg = dpow_of<T>(A);
     c.Gd = (n + RPT - 1) / RPT;
     c.a = c.seg * RPT;
@@ -746,8 +770,11 @@ inline size_t batch_xs_smem(size_t tsize, int RPT, int W, int nbuf)
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_batch_pack(const BatchProb *probs, const int *row_prob, const long long *uoff, int nrows,
-                             const double *__restrict__ x, T *hi, T *lo)
+                             const double *__restrict__ x, T *__restrict__ hi, T *__restrict__ lo)
 {
+    // a lane converts 4 consecutive points (the internal row starts 16-byte
+    // aligned and its pitch is a multiple of 4): 4 loads in flight, 16-byte
+    // stores
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int r = gw; r < nrows; r += nw) {
@@ -757,14 +784,26 @@ __global__ void k_batch_pack(const BatchProb *probs, const int *row_prob, const 
         const int row = r - __ldg(&pb->row0);
         const double *src = x + __ldg(uoff + p) + (int64_t)row * nx;
         const int64_t dst = __ldg(&pb->off) + (int64_t)row * pitch;
-        for (int j = lane; j < pitch; j += 32) {
-            const double v = j < nx ? src[j] : 0.0;
+#pragma unroll 2
+        for (int j = 4 * lane; j < pitch; j += 128) {
+            double v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = (j + c < nx) ? __ldg(src + j + c) : 0.0;
             if constexpr (sizeof(T) == 4) {
-                const float h = __double2float_rn(v);
-                hi[dst + j] = h;
-                lo[dst + j] = __double2float_rn(v - (double)h);
+                float4 h, l;
+                h.x = __double2float_rn(v[0]);
+                h.y = __double2float_rn(v[1]);
+                h.z = __double2float_rn(v[2]);
+                h.w = __double2float_rn(v[3]);
+                l.x = __double2float_rn(v[0] - (double)h.x);
+                l.y = __double2float_rn(v[1] - (double)h.y);
+                l.z = __double2float_rn(v[2] - (double)h.z);
+                l.w = __double2float_rn(v[3] - (double)h.w);
+                *reinterpret_cast<float4 *>(hi + dst + j) = h;
+                *reinterpret_cast<float4 *>(lo + dst + j) = l;
             } else {
-                hi[dst + j] = v;
+                *reinterpret_cast<double2 *>(hi + dst + j) = make_double2(v[0], v[1]);
+                *reinterpret_cast<double2 *>(hi + dst + j + 2) = make_double2(v[2], v[3]);
             }
         }
     }
@@ -773,7 +812,8 @@ __global__ void k_batch_pack(const BatchProb *probs, const int *row_prob, const 
 // x = level (+ add, a packed field, when given)
 template <class T>
 __global__ void k_batch_unpack(const BatchProb *probs, const int *row_prob, const long long *uoff, int nrows,
-                               const T *hi, const T *lo, double *__restrict__ x, const double *__restrict__ add)
+                               const T *__restrict__ hi, const T *__restrict__ lo, double *__restrict__ x,
+                               const double *__restrict__ add)
 {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -785,12 +825,31 @@ __global__ void k_batch_unpack(const BatchProb *probs, const int *row_prob, cons
         const int64_t u0 = __ldg(uoff + p) + (int64_t)row * nx;
         double *dstp = x + u0;
         const int64_t src = __ldg(&pb->off) + (int64_t)row * pitch;
-        for (int j = lane; j < nx; j += 32) {
-            double v;
-            if constexpr (sizeof(T) == 4) v = (double)hi[src + j] + (double)lo[src + j];
-            else v = hi[src + j];
-            if (add) v += add[u0 + j];
-            dstp[j] = v;
+#pragma unroll 2
+        for (int j = 4 * lane; j < nx; j += 128) {
+            double v[4];
+            if constexpr (sizeof(T) == 4) {
+                const float4 h = __ldg(reinterpret_cast<const float4 *>(hi + src + j));
+                const float4 l = __ldg(reinterpret_cast<const float4 *>(lo + src + j));
+                v[0] = (double)h.x + (double)l.x;
+                v[1] = (double)h.y + (double)l.y;
+                v[2] = (double)h.z + (double)l.z;
+                v[3] = (double)h.w + (double)l.w;
+            } else {
+                const double2 a = __ldg(reinterpret_cast<const double2 *>(hi + src + j));
+                const double2 b = __ldg(reinterpret_cast<const double2 *>(hi + src + j + 2));
+                v[0] = a.x;
+                v[1] = a.y;
+                v[2] = b.x;
+                v[3] = b.y;
+            }
+            if (add) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[c] += (j + c < nx) ? __ldg(add + u0 + j + c) : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (j + c < nx) dstp[j + c] = v[c];
         }
     }
 }
@@ -810,21 +869,25 @@ __global__ void k_batch_gather(const T *hi, const T *lo, const long long *irec, 
     }
 }
 
-// level[irec[r]] += vals[r], one thread in receiver order (receivers may
-// share a node)
+// level[node[u]] += the values of the node's receivers, added in receiver
+// order (order[start[u]] .. order[start[u+1] - 1]); one thread per distinct
+// node, so receivers that share a node need no atomics and the sum is the
+// same on every run
 template <class T>
-__global__ void k_batch_inject(T *hi, T *lo, const long long *irec, int nrec, const double *vals)
+__global__ void k_batch_inject(T *hi, T *lo, const long long *node, const long long *start, const long long *order,
+                               int nnode, const double *vals)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    for (int r = 0; r < nrec; ++r) {
-        const long long i = irec[r];
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nnode; u += gridDim.x * blockDim.x) {
+        const long long i = node[u];
+        double x = (double)hi[i];
+        if constexpr (sizeof(T) == 4) x += (double)lo[i];
+        for (long long j = start[u]; j < start[u + 1]; ++j) x += vals[order[j]];
         if constexpr (sizeof(T) == 4) {
-            const double x = (double)hi[i] + (double)lo[i] + vals[r];
             const float h = __double2float_rn(x);
             hi[i] = h;
             lo[i] = __double2float_rn(x - (double)h);
         } else {
-            hi[i] += vals[r];
+            hi[i] = x;
         }
     }
 }

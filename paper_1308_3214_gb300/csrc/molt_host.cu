@@ -180,6 +180,7 @@ void axis_constants(double nu, int64_t n, int bc, int quad, AxisDev &A)
         A.inv = -1.0 / std::expm1(-2.0 * nu * (double)(n - 1));
     }
     for (int k = 0; k < 5; ++k) A.dm[k] = std::exp(-nu * (double)A.m * (double)(1 << k));
+    axis_mirror(A);
 }
 
 }  // namespace molt

@@ -48,7 +48,32 @@ struct AxisDev {
     double dm[5];   // d^{m 2^k}, k = 0..4
     const double *dpow64;  // d^j, j = 0..n
     const float *dpow32;
+    // float32 copies of the constants above (axis_mirror): float kernels read
+    // these and so do no float64 arithmetic, which runs on a narrow pipe
+    float fd, fc1, fc2, fmu, finv, fdm[5];
+
+    template <class T> __host__ __device__ T cd() const { if constexpr (sizeof(T) == 4) return fd; else return d; }
+    template <class T> __host__ __device__ T cc1() const { if constexpr (sizeof(T) == 4) return fc1; else return c1; }
+    template <class T> __host__ __device__ T cc2() const { if constexpr (sizeof(T) == 4) return fc2; else return c2; }
+    template <class T> __host__ __device__ T cmu() const { if constexpr (sizeof(T) == 4) return fmu; else return mu; }
+    template <class T> __host__ __device__ T cinv() const { if constexpr (sizeof(T) == 4) return finv; else return inv; }
+    template <class T> __host__ __device__ T cdm(int k) const
+    {
+        if constexpr (sizeof(T) == 4) return fdm[k];
+        else return dm[k];
+    }
 };
+
+// fills the float32 copies of an axis' constants (after any change to them)
+inline void axis_mirror(AxisDev &A)
+{
+    A.fd = (float)A.d;
+    A.fc1 = (float)A.c1;
+    A.fc2 = (float)A.c2;
+    A.fmu = (float)A.mu;
+    A.finv = (float)A.inv;
+    for (int k = 0; k < 5; ++k) A.fdm[k] = (float)A.dm[k];
+}
 
 // Where the lines of one pass live in global memory.
 struct PassGeom {
@@ -99,7 +124,40 @@ struct ProgParams {
     double ea, eb, ec;    // u_next = ea u + eb u_prev + ec F
     const void *u_hi, *u_lo, *up_hi, *up_lo;
     void *un_hi, *un_lo;
+    // float32 copies for the float kernels (no float64 arithmetic on their
+    // paths): the tables in the kernel's parameter space, the level weights
+    float coef32[MAXP * MAXP * MAXG];
+    float cu32[MAXP * MAXP];
+    float fea, feb, fec;
 };
+
+// Horner weights in the kernel's precision: float kernels read the copies in
+// the parameter space, float64 kernels the device tables
+template <class T> __device__ __forceinline__ T prog_coef(const ProgParams &p, size_t i)
+{
+    if constexpr (sizeof(T) == 4) return p.coef32[i];
+    else return __ldg(p.coef + i);
+}
+template <class T> __device__ __forceinline__ T prog_cu(const ProgParams &p, size_t i)
+{
+    if constexpr (sizeof(T) == 4) return p.cu32[i];
+    else return __ldg(p.cu + i);
+}
+
+// fills the float32 copies of a program's level weights and Horner weights
+// (flattened as the device tables: [o][t][k] and [o][t])
+inline void prog_mirror(ProgParams &p, const HornerParams &hp)
+{
+    int nc = 0, nu = 0;
+    for (int o = 0; o < (hp.nout > 1 ? hp.nout : 1); ++o)
+        for (int t = 0; t <= hp.P; ++t) {
+            for (int k = 0; k < hp.ng; ++k) p.coef32[nc++] = (float)hp.coef[o][t][k];
+            p.cu32[nu++] = (float)hp.cu[o][t];
+        }
+    p.fea = (float)p.ea;
+    p.feb = (float)p.eb;
+    p.fec = (float)p.ec;
+}
 
 struct LineSet {
     int64_t stride;   // element stride along the axis
@@ -171,7 +229,7 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
                         const T *__restrict__ dp, int lane)
 {
     const int n = A.n, m = A.m, ms = A.ms;
-    const T d = (T)A.d, c1 = (T)A.c1, c2 = (T)A.c2;
+    const T d = A.cd<T>(), c1 = A.cc1<T>(), c2 = A.cc2<T>();
     const int a = lane * m;
     const int b = min(a + m, n);
     const int cnt = b > a ? b - a : 0;
@@ -244,7 +302,7 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         T y = __shfl_up_sync(0xffffffffu, x, 1 << k);
-        if (lane >= (1 << k)) x += (T)A.dm[k] * y;
+        if (lane >= (1 << k)) x += A.cdm<T>(k) * y;
     }
     T excl = __shfl_up_sync(0xffffffffu, x, 1);
     if (lane == 0) excl = 0;
@@ -253,7 +311,7 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
     if (BC == BC_PERIODIC) {
         // zero-inflow y_{n-1}: the last lane may hold fewer than m points
         T tot = __shfl_sync(0xffffffffu, cnt > 0 ? dp[cnt] * excl + E : (T)0, Ld);
-        T y_m1 = tot * (T)A.inv;                        // y_{-1} over all images
+        T y_m1 = tot * A.cinv<T>();                        // y_{-1} over all images
         if (cnt > 0) y += dp[a] * y_m1;
     }
 
@@ -272,7 +330,7 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         T t = __shfl_down_sync(0xffffffffu, xb, 1 << k);
-        if (lane + (1 << k) < 32) xb += (T)A.dm[k] * t;
+        if (lane + (1 << k) < 32) xb += A.cdm<T>(k) * t;
     }
     T exclb = __shfl_down_sync(0xffffffffu, xb, 1);
     if (lane == 31) exclb = 0;
@@ -280,11 +338,11 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
     T Z, Acoef = 0;
     if (BC == BC_DIRICHLET) {
         const T ylast = __shfl_sync(0xffffffffu, y, Ld);  // y_{n-1} = zero-inflow e_{n-1}
-        const T mu = (T)A.mu, inv = (T)A.inv;
+        const T mu = A.cmu<T>(), inv = A.cinv<T>();
         Acoef = (mu * ylast - e00) * inv;               // A'
         Z = (mu * e00 - ylast) * inv;                   // B'
     } else {
-        Z = d * e00 * (T)A.inv;                         // d * e_n, e_n = e_0 over all images
+        Z = d * e00 * A.cinv<T>();                         // d * e_n, e_n = e_0 over all images
     }
     // c = d * e_b including the inflow from the right end
     T acc = d * exclb + (cnt > 0 ? dp[n - b] * Z : (T)0);

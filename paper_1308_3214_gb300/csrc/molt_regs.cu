@@ -217,9 +217,9 @@ cudaError_t launch_res(int bc, int rpt, int ng, int warps, const AxisDev &A, con
 // float32 Horner pass with W warps per row: n = 32 W RPT exactly, RPT 16 or 32
 bool regs_rows_plan(int tbytes, int n, int ng, int W, int *rpt)
 {
-    if (tbytes != 4 || ng > 3 || (W != 2 && W != 4) || n % (32 * W) != 0) return false;
+    if (tbytes != 4 || ng > 3 || (W != 2 && W != 4 && W != 8) || n % (32 * W) != 0) return false;
     const int r = n / (32 * W);
-    if (r != 16 && r != 32) return false;
+    if (W == 8 ? (r != 8 && r != 16) : (r != 16 && r != 32)) return false;
     *rpt = r;
     return true;
 }
@@ -227,20 +227,22 @@ bool regs_rows_plan(int tbytes, int n, int ng, int W, int *rpt)
 cudaError_t launch_rows(int bc, int rpt, int ng, int W, const AxisDev &A, const LineSet &L, const ProgParams &p,
                         cudaStream_t s)
 {
-#define MOLT_ROWS(BC, WW)                                                                 \
+#define MOLT_ROWS(BC, WW, R1, R2)                                                         \
     switch (rpt * 10 + (ng < 1 ? 1 : ng)) {                                               \
-    case 161: return run_rows<BC, 16, 1, WW>(A, L, p, s);                                 \
-    case 162: return run_rows<BC, 16, 2, WW>(A, L, p, s);                                 \
-    case 163: return run_rows<BC, 16, 3, WW>(A, L, p, s);                                 \
-    case 321: return run_rows<BC, 32, 1, WW>(A, L, p, s);                                 \
-    case 322: return run_rows<BC, 32, 2, WW>(A, L, p, s);                                 \
-    case 323: return run_rows<BC, 32, 3, WW>(A, L, p, s);                                 \
+    case R1 * 10 + 1: return run_rows<BC, R1, 1, WW>(A, L, p, s);                         \
+    case R1 * 10 + 2: return run_rows<BC, R1, 2, WW>(A, L, p, s);                         \
+    case R1 * 10 + 3: return run_rows<BC, R1, 3, WW>(A, L, p, s);                         \
+    case R2 * 10 + 1: return run_rows<BC, R2, 1, WW>(A, L, p, s);                         \
+    case R2 * 10 + 2: return run_rows<BC, R2, 2, WW>(A, L, p, s);                         \
+    case R2 * 10 + 3: return run_rows<BC, R2, 3, WW>(A, L, p, s);                         \
     default: break;                                                                       \
     }
     if (W == 2) {
-        if (bc == BC_PERIODIC) { MOLT_ROWS(BC_PERIODIC, 2) } else { MOLT_ROWS(BC_DIRICHLET, 2) }
+        if (bc == BC_PERIODIC) { MOLT_ROWS(BC_PERIODIC, 2, 16, 32) } else { MOLT_ROWS(BC_DIRICHLET, 2, 16, 32) }
     } else if (W == 4) {
-        if (bc == BC_PERIODIC) { MOLT_ROWS(BC_PERIODIC, 4) } else { MOLT_ROWS(BC_DIRICHLET, 4) }
+        if (bc == BC_PERIODIC) { MOLT_ROWS(BC_PERIODIC, 4, 16, 32) } else { MOLT_ROWS(BC_DIRICHLET, 4, 16, 32) }
+    } else if (W == 8) {
+        if (bc == BC_PERIODIC) { MOLT_ROWS(BC_PERIODIC, 8, 8, 16) } else { MOLT_ROWS(BC_DIRICHLET, 8, 8, 16) }
     }
 #undef MOLT_ROWS
     return cudaErrorInvalidValue;
@@ -250,10 +252,11 @@ cudaError_t configure_regs_kernels()
 {
     cudaError_t e;
 #define MOLT_A(x) if ((e = (x)) != cudaSuccess) return e;
-#define MOLT_ROWA(BC, WW) MOLT_A((attr_rows<BC, 16, 1, WW>())) MOLT_A((attr_rows<BC, 16, 2, WW>())) \
-    MOLT_A((attr_rows<BC, 16, 3, WW>())) MOLT_A((attr_rows<BC, 32, 1, WW>())) MOLT_A((attr_rows<BC, 32, 2, WW>())) \
-    MOLT_A((attr_rows<BC, 32, 3, WW>()))
-    MOLT_ROWA(BC_PERIODIC, 2) MOLT_ROWA(BC_DIRICHLET, 2) MOLT_ROWA(BC_PERIODIC, 4) MOLT_ROWA(BC_DIRICHLET, 4)
+#define MOLT_ROWA(BC, WW, R1, R2) MOLT_A((attr_rows<BC, R1, 1, WW>())) MOLT_A((attr_rows<BC, R1, 2, WW>())) \
+    MOLT_A((attr_rows<BC, R1, 3, WW>())) MOLT_A((attr_rows<BC, R2, 1, WW>())) MOLT_A((attr_rows<BC, R2, 2, WW>())) \
+    MOLT_A((attr_rows<BC, R2, 3, WW>()))
+    MOLT_ROWA(BC_PERIODIC, 2, 16, 32) MOLT_ROWA(BC_DIRICHLET, 2, 16, 32) MOLT_ROWA(BC_PERIODIC, 4, 16, 32)
+    MOLT_ROWA(BC_DIRICHLET, 4, 16, 32) MOLT_ROWA(BC_PERIODIC, 8, 8, 16) MOLT_ROWA(BC_DIRICHLET, 8, 8, 16)
 #undef MOLT_ROWA
 #define MOLT_RA(BC) MOLT_A((attr_res<BC, 8, 1>())) MOLT_A((attr_res<BC, 8, 2>())) MOLT_A((attr_res<BC, 8, 3>())) \
     MOLT_A((attr_res<BC, 16, 1>())) MOLT_A((attr_res<BC, 16, 2>())) MOLT_A((attr_res<BC, 16, 3>()))             \

@@ -250,7 +250,7 @@ __device__ __forceinline__ void warp_sweep_core(T (&z)[RPT], RF rfun, T cu, cons
 {
     static_assert(!RAG || BC == BC_DIRICHLET, "ragged lines are Dirichlet lines");
     const int n = A.n;
-    const T d = (T)A.d;
+    const T d = A.cd<T>();
     const int Ld = RAG ? (n - 1) / RPT : n / RPT - 1;
     const bool full = lane <= Ld;
     const int a = lane * RPT;
@@ -274,7 +274,7 @@ __device__ __forceinline__ void warp_sweep_core(T (&z)[RPT], RF rfun, T cu, cons
     } else {
         end_ghosts<T, RPT, MODE>(z, lane == 0, !RAG && lane == Ld, zl2, zl1, zr0, zr1);
     }
-    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    const T c1 = A.cc1<T>(), c2 = A.cc2<T>();
     seg_make_q<T, RPT, MODE, RAG>(z, zl2, zl1, zr0, zr1, rfun, cu, c1, c2, kl);
     if (BC == BC_DIRICHLET) end_zero<T, RPT>(z, lane == 0, !RAG && lane == Ld);
 #pragma unroll
@@ -290,7 +290,7 @@ template <class T, int BC, int RPT, bool RAG>
 __device__ __forceinline__ void warp_solve(T (&z)[RPT], const AxisDev &A, int lane)
 {
     const int n = A.n;
-    const T d = (T)A.d;
+    const T d = A.cd<T>();
     const int Ld = RAG ? (n - 1) / RPT : n / RPT - 1;
     const bool full = lane <= Ld;
     const int a = lane * RPT;
@@ -308,13 +308,13 @@ __device__ __forceinline__ void warp_solve(T (&z)[RPT], const AxisDev &A, int la
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const T y = __shfl_up_sync(0xffffffffu, x, 1 << k);
-        x = (lane >= (1 << k)) ? x + (T)A.dm[k] * y : x;
+        x = (lane >= (1 << k)) ? x + A.cdm<T>(k) * y : x;
     }
     T yin = __shfl_up_sync(0xffffffffu, x, 1);
     const T tot = __shfl_sync(0xffffffffu, x, Ld);              // zero-inflow y_{n-1}
     yin = (lane == 0) ? (T)0 : yin;
     if (BC == BC_PERIODIC)
-        yin += full ? dpg[a] * (tot * (T)A.inv) : (T)0;          // images to the left
+        yin += full ? dpg[a] * (tot * A.cinv<T>()) : (T)0;          // images to the left
     yin = full ? yin : (T)0;                                     // lanes past the line stay zero
     T ylast = 0;
     const T ER = TWO ? seg_fwd_scan2<T, RPT>(z, d, dH, yin, E1, ER2) : seg_fwd_scan<T, RPT, RAG>(z, d, yin, kl, &ylast);
@@ -325,7 +325,7 @@ __device__ __forceinline__ void warp_solve(T (&z)[RPT], const AxisDev &A, int la
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const T t = __shfl_down_sync(0xffffffffu, xb, 1 << k);
-        xb = (lane + (1 << k) < 32) ? xb + (T)A.dm[k] * t : xb;
+        xb = (lane + (1 << k) < 32) ? xb + A.cdm<T>(k) * t : xb;
     }
     T exclb = __shfl_down_sync(0xffffffffu, xb, 1);
     const T e00 = __shfl_sync(0xffffffffu, xb, 0);              // zero-inflow e_0
@@ -333,11 +333,11 @@ __device__ __forceinline__ void warp_solve(T (&z)[RPT], const AxisDev &A, int la
     exclb = (lane == 31) ? (T)0 : exclb;
     T Z, Acoef = 0;
     if (BC == BC_DIRICHLET) {
-        const T mu = (T)A.mu, inv = (T)A.inv;
+        const T mu = A.cmu<T>(), inv = A.cinv<T>();
         Acoef = (mu * yl - e00) * inv;
         Z = (mu * e00 - yl) * inv;
     } else {
-        Z = d * e00 * (T)A.inv;
+        Z = d * e00 * A.cinv<T>();
     }
     // B' d^{n-1-j}: through the inflow of every segment that ends before the
     // last point; RAG injects it at the last point itself
@@ -448,7 +448,7 @@ __device__ __forceinline__ void warp_sweep_T(T (&z)[RPT], const T (&u)[RPT], T c
     el1 = (lane == 0) ? (T)0 : el1;
     er0 = (lane == 31) ? (T)0 : er0;
     er1 = (lane == 31) ? (T)0 : er1;
-    post_T<T, RPT, true>(z, el2, el1, er0, er1, (T)A.c1, (T)A.c2, a, n);
+    post_T<T, RPT, true>(z, el2, el1, er0, er1, A.cc1<T>(), A.cc2<T>(), a, n);
     __syncwarp();
 }
 
@@ -491,11 +491,11 @@ __device__ __forceinline__ void level_vec(const ProgParams &p, int64_t i, const 
     const float4 uh = *reinterpret_cast<const float4 *>((const float *)p.u_hi + i);
     const float4 ul = *reinterpret_cast<const float4 *>((const float *)p.u_lo + i);
     float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
-    if (p.eb != 0.0) {
+    if (p.feb != 0.f) {
         ph = *reinterpret_cast<const float4 *>((const float *)p.up_hi + i);
         pl = *reinterpret_cast<const float4 *>((const float *)p.up_lo + i);
     }
-    const float ea = (float)p.ea, eb = (float)p.eb, ec = (float)p.ec;
+    const float ea = p.fea, eb = p.feb, ec = p.fec;
     float4 nh, nl;
     level_pair(uh.x, ul.x, ph.x, pl.x, F.x, ea, eb, ec, nh.x, nl.x);
     level_pair(uh.y, ul.y, ph.y, pl.y, F.y, ea, eb, ec, nh.y, nl.y);
@@ -510,7 +510,7 @@ __device__ __forceinline__ void level_vec(const ProgParams &p, int64_t i, const 
     double2 v;
     v.x = p.ea * u.x + p.ec * F.x;
     v.y = p.ea * u.y + p.ec * F.y;
-    if (p.eb != 0.0) {
+    if (p.feb != 0.f) {
         const double2 q = *reinterpret_cast<const double2 *>((const double *)p.up_hi + i);
         v.x += p.eb * q.x;
         v.y += p.eb * q.y;
@@ -529,7 +529,7 @@ template <int CH, int NT> struct LevelBatch<float, CH, NT> {
         const float4 *__restrict__ PH = reinterpret_cast<const float4 *>((const float *)p.up_hi + base);
         const float4 *__restrict__ PL = reinterpret_cast<const float4 *>((const float *)p.up_lo + base);
         float4 uh[CH], ul[CH], ph[CH], pl[CH];
-        const bool prev = p.eb != 0.0;
+        const bool prev = p.feb != 0.f;
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
             const int v = lane + NT * (i0 + i);
@@ -540,7 +540,7 @@ template <int CH, int NT> struct LevelBatch<float, CH, NT> {
                 pl[i] = prev ? __ldg(PL + v) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
-        const float ea = (float)p.ea, eb = (float)p.eb, ec = (float)p.ec;
+        const float ea = p.fea, eb = p.feb, ec = p.fec;
         float4 *NH = reinterpret_cast<float4 *>((float *)p.un_hi + base);
         float4 *NL = reinterpret_cast<float4 *>((float *)p.un_lo + base);
 #pragma unroll
@@ -619,7 +619,7 @@ struct CoalescedSide {
 // loads of its share of the row (up to RPT/VN vectors) so that they are in
 // flight together, then accumulates.
 template <class T, int RPT>
-__device__ __forceinline__ void stage_accumulate(T *stage, const ProgParams &pr, const double *cf, int64_t base, int n,
+__device__ __forceinline__ void stage_accumulate(T *stage, const ProgParams &pr, size_t cf, int64_t base, int n,
                                                  int lane)
 {
     using V = typename VecOf<T>::type;
@@ -627,7 +627,7 @@ __device__ __forceinline__ void stage_accumulate(T *stage, const ProgParams &pr,
     constexpr int NV = RPT / VN;                    // vectors per lane (n <= 32*RPT)
     const int nvec = n / VN;                        // n is a multiple of RPT, hence of VN
     for (int k = 0; k < pr.ng; ++k) {
-        const T ck = (T)__ldg(cf + k);
+        const T ck = prog_coef<T>(pr, cf + k);
         if (ck == (T)0) continue;
         const V *__restrict__ src = reinterpret_cast<const V *>(reinterpret_cast<const T *>(pr.g[k]) + base);
         V buf[NV];
@@ -766,13 +766,13 @@ __global__ void __launch_bounds__(32 * WARPS, 3) k_contig(AxisDev A, LineSet LS,
         if (ng > 0 || t == 0) {
             regs_to_stage<T, RPT>(stage, z, lane);
             __syncwarp();
-            if (ng > 0) stage_accumulate<T, RPT>(stage, pr, pr.coef + (size_t)t * ng, base, n, lane);
+            if (ng > 0) stage_accumulate<T, RPT>(stage, pr, (size_t)t * ng, base, n, lane);
             __syncwarp();
             if (t == 0) break;
             stage_to_regs<T, RPT>(stage, z, lane, false);
             __syncwarp();
         }
-        warp_sweep<T, BC, RPT, 2>(z, rline, (T)__ldg(pr.cu + t), A, lane);
+        warp_sweep<T, BC, RPT, 2>(z, rline, prog_cu<T>(pr, t), A, lane);
     }
     // out = stage (coalesced side): level combination or plain store
     if (pr.epi) {
@@ -854,7 +854,7 @@ __global__ void __launch_bounds__(128) k_contig_res(AxisDev A, LineSet LS, ProgP
         const unsigned bytes = (unsigned)n * 4u;          // n is a multiple of RPT >= 8
         prefetch_l2((const float *)pr.u_hi + base, bytes);
         prefetch_l2((const float *)pr.u_lo + base, bytes);
-        if (pr.eb != 0.0) {
+        if (pr.feb != 0.f) {
             prefetch_l2((const float *)pr.up_hi + base, bytes);
             prefetch_l2((const float *)pr.up_lo + base, bytes);
         }
@@ -933,7 +933,7 @@ __global__ void __launch_bounds__(128) k_contig_res(AxisDev A, LineSet LS, ProgP
     for (int k = 0; k < RPT; ++k) z[k] = 0;
     for (int t = P; t >= 0; --t) {
         for (int k = 0; k < ng; ++k) {
-            const T c = (T)__ldg(pr.coef + (size_t)t * ng + k);
+            const T c = prog_coef<T>(pr, (size_t)t * ng + k);
             if (c == (T)0) continue;
             const float4 *seg = reinterpret_cast<const float4 *>(B + k * St::LINE + lane * St::SST);
 #pragma unroll
@@ -946,7 +946,7 @@ __global__ void __launch_bounds__(128) k_contig_res(AxisDev A, LineSet LS, ProgP
             }
         }
         if (t == 0) break;
-        warp_sweep_rreg<T, BC, RPT>(z, r, (T)__ldg(pr.cu + t), A, lane);
+        warp_sweep_rreg<T, BC, RPT>(z, r, prog_cu<T>(pr, t), A, lane);
     }
 
     // 4. F (segment layout) -> coalesced side -> next level
@@ -1032,7 +1032,7 @@ __device__ __forceinline__ void row_solve(T (&z)[RPT], const AxisDev &A, int lan
 {
     static_assert(!RAG || BC == BC_DIRICHLET, "ragged rows are Dirichlet rows");
     const int n = A.n;
-    const T d = (T)A.d;
+    const T d = A.cd<T>();
     const int seg = warp * 32 + lane, a = seg * RPT;
     const int Ld = RAG ? (n - 1) / RPT : 32 * W - 1;  // segment holding the last point
     const int kl = n - 1 - a;
@@ -1048,7 +1048,7 @@ __device__ __forceinline__ void row_solve(T (&z)[RPT], const AxisDev &A, int lan
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const T y = __shfl_up_sync(0xffffffffu, x, 1 << k);
-        x = (lane >= (1 << k)) ? x + (T)A.dm[k] * y : x;
+        x = (lane >= (1 << k)) ? x + A.cdm<T>(k) * y : x;
     }
     T yin = __shfl_up_sync(0xffffffffu, x, 1);
     yin = (lane == 0) ? (T)0 : yin;
@@ -1062,7 +1062,7 @@ __device__ __forceinline__ void row_solve(T (&z)[RPT], const AxisDev &A, int lan
         tot = DW * tot + sl.tc[w2];
     }
     yin += dpg[lane * RPT] * cin;
-    if (BC == BC_PERIODIC) yin += dpg[a] * (tot * (T)A.inv);       // images to the left
+    if (BC == BC_PERIODIC) yin += dpg[a] * (tot * A.cinv<T>());       // images to the left
     if (RAG) yin = full ? yin : (T)0;
     T ylast = 0;
     const T ER = TWO ? seg_fwd_scan2<T, RPT>(z, d, dH, yin, E1, ER2) : seg_fwd_scan<T, RPT, RAG>(z, d, yin, kl, &ylast);
@@ -1073,7 +1073,7 @@ __device__ __forceinline__ void row_solve(T (&z)[RPT], const AxisDev &A, int lan
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const T t = __shfl_down_sync(0xffffffffu, xb, 1 << k);
-        xb = (lane + (1 << k) < 32) ? xb + (T)A.dm[k] * t : xb;
+        xb = (lane + (1 << k) < 32) ? xb + A.cdm<T>(k) * t : xb;
     }
     T exclb = __shfl_down_sync(0xffffffffu, xb, 1);
     exclb = (lane == 31) ? (T)0 : exclb;
@@ -1093,11 +1093,11 @@ __device__ __forceinline__ void row_solve(T (&z)[RPT], const AxisDev &A, int lan
     exclb += dpg[(31 - lane) * RPT] * cinb;
     T Z, Acoef = 0;
     if (BC == BC_DIRICHLET) {
-        const T mu = (T)A.mu, inv = (T)A.inv, yl = sl.yl;
+        const T mu = A.cmu<T>(), inv = A.cinv<T>(), yl = sl.yl;
         Acoef = (mu * yl - e00) * inv;
         Z = (mu * e00 - yl) * inv;
     } else {
-        Z = d * e00 * (T)A.inv;
+        Z = d * e00 * A.cinv<T>();
     }
     // B' d^{n-1-j}: through the inflow of every segment that ends before the
     // last point; RAG injects it at the last point itself
@@ -1122,7 +1122,7 @@ __device__ __forceinline__ void row_sweep(T (&z)[RPT], const T (&r)[RPT], T rl, 
     const int seg = warp * 32 + lane, a = seg * RPT;
     const int Ld = RAG ? (n - 1) / RPT : 32 * W - 1;
     const int kl = n - 1 - a;
-    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    const T c1 = A.cc1<T>(), c2 = A.cc2<T>();
     T zl2, zl1, zr0, zr1;
     row_halos<T, RPT, W, BC == BC_PERIODIC>(z, lane, warp, sl, zl2, zl1, zr0, zr1);
     if (BC == BC_DIRICHLET) end_ghosts<T, RPT, 2>(z, seg == 0, !RAG && seg == Ld, zl2, zl1, zr0, zr1);
@@ -1158,7 +1158,7 @@ __device__ __forceinline__ void row_sweep_T(T (&z)[RPT], const T (&u)[RPT], T cu
     el1 = first ? (T)0 : el1;
     er0 = last ? (T)0 : er0;
     er1 = last ? (T)0 : er1;
-    post_T<T, RPT, true>(z, el2, el1, er0, er1, (T)A.c1, (T)A.c2, a, n);
+    post_T<T, RPT, true>(z, el2, el1, er0, er1, A.cc1<T>(), A.cc2<T>(), a, n);
     __syncwarp();
 }
 
@@ -1166,7 +1166,7 @@ template <class T, int W>
 __host__ __device__ constexpr size_t row_slots_bytes() { return (sizeof(RowSlots<T, W>) + 15) & ~(size_t)15; }
 
 template <int BC, int RPT, int NB, int W>
-__global__ void __launch_bounds__(32 * W, W == 2 ? 8 : 6) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr)
+__global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 6 : 4)) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr)
 {
     static_assert(RPT % 4 == 0 && RPT >= 8, "segment length");
     using T = float;
@@ -1187,7 +1187,7 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : 6) k_contig_rows(AxisDev 
         const unsigned bytes = (unsigned)n * 4u;
         prefetch_l2((const float *)pr.u_hi + base, bytes);
         prefetch_l2((const float *)pr.u_lo + base, bytes);
-        if (pr.eb != 0.0) {
+        if (pr.feb != 0.f) {
             prefetch_l2((const float *)pr.up_hi + base, bytes);
             prefetch_l2((const float *)pr.up_lo + base, bytes);
         }
@@ -1262,7 +1262,7 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : 6) k_contig_rows(AxisDev 
     for (int k = 0; k < RPT; ++k) z[k] = 0;
     for (int tt = pr.P; tt >= 0; --tt) {
         for (int k = 0; k < ng; ++k) {
-            const T c = (T)__ldg(pr.coef + (size_t)tt * ng + k);
+            const T c = prog_coef<T>(pr, (size_t)tt * ng + k);
             if (c == (T)0) continue;
             const float4 *sg = reinterpret_cast<const float4 *>(B + k * LINE + t * St::SST);
 #pragma unroll
@@ -1275,7 +1275,7 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : 6) k_contig_rows(AxisDev 
             }
         }
         if (tt == 0) break;
-        row_sweep<T, BC, RPT, W>(z, r, rl, rr, (T)__ldg(pr.cu + tt), A, lane, warp, sl);
+        row_sweep<T, BC, RPT, W>(z, r, rl, rr, prog_cu<T>(pr, tt), A, lane, warp, sl);
     }
 
     // F -> coalesced side -> next level
@@ -1288,8 +1288,8 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : 6) k_contig_rows(AxisDev 
     const float4 *PL = reinterpret_cast<const float4 *>((const float *)pr.up_lo + base);
     float4 *NH = reinterpret_cast<float4 *>((float *)pr.un_hi + base);
     float4 *NL = reinterpret_cast<float4 *>((float *)pr.un_lo + base);
-    const bool prev = pr.eb != 0.0;
-    const float ea = (float)pr.ea, eb = (float)pr.eb, ec = (float)pr.ec;
+    const bool prev = pr.feb != 0.f;
+    const float ea = pr.fea, eb = pr.feb, ec = pr.fec;
     constexpr int CH = NVL > 4 ? 4 : NVL;
 #pragma unroll
     for (int i0 = 0; i0 < NVL; i0 += CH) {
@@ -1446,7 +1446,7 @@ __device__ __forceinline__ void strided_sweep(const StridedCtx<T> &c, const Axis
 {
     const bool left = c.seg == 0, right = c.seg == c.Gd - 1;
     if (BC == BC_DIRICHLET) end_ghosts<T, RPT, MODE>(z, left, right, l2, l1, r0, r1);
-    const T c1 = (T)A.c1, c2 = (T)A.c2;
+    const T c1 = A.cc1<T>(), c2 = A.cc2<T>();
     if (MODE == 2)
         seg_make_q<T, RPT, 2>(z, l2, l1, r0, r1, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : rs[k * 32]); },
                               cu, c1, c2);
@@ -1463,18 +1463,18 @@ __device__ __forceinline__ void strided_sweep(const StridedCtx<T> &c, const Axis
     const T E = seg_fwd_reduce2<T, RPT>(z, d, dH, E1);
     T yin, ytot;
     strided_causal<T, RPT>(c, E, yin, ytot);
-    if (BC == BC_PERIODIC && c.full) yin += c.dpg[c.a] * (ytot * (T)A.inv);
+    if (BC == BC_PERIODIC && c.full) yin += c.dpg[c.a] * (ytot * A.cinv<T>());
     if (!c.full) yin = 0;                                          // segments past the line stay zero
     const T ER = seg_fwd_scan2<T, RPT>(z, d, dH, yin, E1, ER2);
     T eout, e00;
     strided_anticausal<T, RPT>(c, ER, eout, e00);
     T Z, Acoef = 0;
     if (BC == BC_DIRICHLET) {
-        const T mu = (T)A.mu, inv = (T)A.inv;
+        const T mu = A.cmu<T>(), inv = A.cinv<T>();
         Acoef = (mu * ytot - e00) * inv;     // ytot = zero-inflow y_{n-1}
         Z = (mu * e00 - ytot) * inv;
     } else {
-        Z = d * e00 * (T)A.inv;
+        Z = d * e00 * A.cinv<T>();
     }
     const T acc = d * eout + (c.full ? c.dpg[c.n - c.a - RPT] * Z : (T)0);
     seg_bwd_scan2<T, RPT>(z, d, dH, acc, ER2);
@@ -1545,8 +1545,8 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
     c.lane = threadIdx.x & 31;
     c.krank = LS.K > 1 ? (int)c.cl.block_rank() : 0;
     c.n = A.n;
-    c.d = (T)A.d;
-    c.dR = (T)A.dm[0];
+    c.d = A.cd<T>();
+    c.dR = A.cdm<T>(0);
     c.dpg = dpow_of<T>(A);
     c.Gd = A.n / RPT;
     c.seg = c.krank * c.S + c.w;
@@ -1612,14 +1612,14 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
     const int P = pr.P, ng = pr.ng;
     int hpar = 0;
     for (int o = 0; o < pr.nout; ++o) {
-        const double *cfo = pr.coef + (size_t)o * (P + 1) * ng;
+        const size_t cfo = (size_t)o * (P + 1) * ng;
 #pragma unroll
         for (int k = 0; k < RPT; ++k) z[k] = 0;
         for (int t = P; t >= 0; --t) {
-            const double *cf = cfo + (size_t)t * ng;
+            const size_t cf = cfo + (size_t)t * ng;
             if (io) {
                 for (int q = 0; q < ng; ++q) {
-                    const T cq = (T)__ldg(cf + q);
+                    const T cq = prog_coef<T>(pr, cf + q);
                     if (cq == (T)0) continue;
                     const T *gq = reinterpret_cast<const T *>(pr.g[q]) + lbase + (int64_t)a * st;
 #pragma unroll
@@ -1630,7 +1630,7 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
             T l2, l1, r0, r1;
             strided_halos<T, BC, RPT>(c, z, l2, l1, r0, r1, hpar);
             hpar ^= 1;
-            strided_sweep<T, BC, RPT, 2>(c, A, z, (T)__ldg(pr.cu + (size_t)o * (P + 1) + t), l2, l1, r0, r1, rs, rl, rr);
+            strided_sweep<T, BC, RPT, 2>(c, A, z, prog_cu<T>(pr, (size_t)o * (P + 1) + t), l2, l1, r0, r1, rs, rl, rr);
         }
         T *ob = reinterpret_cast<T *>(pr.out[o]);
         if (io) {

@@ -166,6 +166,29 @@ def test_adjoint_matches_oracle(prec):
             assert np.linalg.norm(got - ref) <= model(nu, P) * Fsum, i
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_adjoint_with_receivers_sharing_nodes(prec):
+    """Receivers listed in no particular order, several on one node (within
+    a problem), some nodes once: the injection sums each node's receivers."""
+    nsteps = 7
+    shapes = STEP_SHAPES[:3]
+    b, specs = make(shapes, prec)
+    rng = np.random.default_rng(17)
+    rec, local = [], []
+    for i, (ny, nx) in enumerate(shapes):
+        nodes = (rng.integers(1, ny - 1, size=3) * nx + rng.integers(1, nx - 1, size=3)).tolist()
+        loc = np.array(nodes + [nodes[0], nodes[0], nodes[2]])[rng.permutation(6)]
+        local.append(loc)
+        rec.extend(b.offsets[i] + loc)
+    rec = np.array(rec, dtype=np.int64)
+    tg = rng.normal(size=(nsteps, rec.size))
+    grad = b.unpack(b.adjoint(rec, torch.from_numpy(tg)))
+    for i, (P, dt, beta, nu) in enumerate(specs):
+        ref = oracle.adjoint(tg[:, 6 * i:6 * (i + 1)], shapes[i], local[i], nu, P, beta, "dirichlet")
+        tol = 1e-12 if prec == "fp64" else 1e-4
+        assert rel_l2(grad[i].cpu().numpy(), ref) <= tol, i
+
+
 def test_gradient_matches_central_difference_on_gpu():
     """J(u0) = |T u0 - d|^2 / 2 is quadratic: the central difference along s
     equals <grad J, s> up to rounding (float64 path)."""

@@ -339,7 +339,7 @@ def test_autotune_choice_keeps_parity(prec):
     s = make(shape, dt, P, bc, prec)
     tun = s.autotune()
     assert tun["res_warps"] in (1, 2, 4) and tun["strided_warps"] in (4, 8) and tun["strided_rpt"] in (0, 32)
-    assert tun["rows_warps"] in (0, 2, 4)
+    assert tun["rows_warps"] in (0, 2, 4, 8)
     assert tun["ms_per_step"] > 0
     u0 = smooth_field(shape, 7, bc) + 0.05 * field(shape, 8, bc)
     u1 = oracle.start(u0, s.nu, P, s.beta, bc)
@@ -371,7 +371,8 @@ def test_every_strided_choice_matches_oracle(rpt, warps):
 
 
 
-@pytest.mark.parametrize("shape, W", [((48, 2048), 2), ((40, 2048), 4), ((64, 1024), 2)])
+@pytest.mark.parametrize("shape, W", [((48, 2048), 2), ((40, 2048), 4), ((64, 1024), 2), ((36, 2048), 8),
+                                      ((20, 4096), 8)])
 @pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
 @pytest.mark.parametrize("P", [1, 3])
 def test_rows_split_over_warps_match_oracle(shape, W, bc, P):
