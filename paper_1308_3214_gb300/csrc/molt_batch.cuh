@@ -656,6 +656,7 @@ __device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams
     c.dR = A.cdm<T>(0);
     c.dpg = dpow_of<T>(A);
     c.Gd = (n + RPT - 1) / RPT;
+    strided_cta_consts<T, RPT>(c);
     c.a = c.seg * RPT;
     c.full = c.seg < c.Gd;
     const int kl = n - 1 - c.a;

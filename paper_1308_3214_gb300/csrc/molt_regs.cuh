@@ -1336,7 +1336,8 @@ struct StridedCtx {
     StridedSlots<T> sl;
     const T *dpg;
     T d, dR;            // e^{-nu}, d^RPT
-    int n, S, K, w, lane, krank, seg, a, Gd;
+    T dS, dL;           // cta_mult: decay across a full CTA and across the last CTA with data
+    int n, S, K, w, lane, krank, seg, a, Gd, kL;
     bool full;
 };
 
@@ -1353,13 +1354,30 @@ __device__ __forceinline__ void csync(const StridedCtx<T> &c)
     else __syncthreads();
 }
 
-// number of data segments in CTA k, and its length multiplier d^{len}
+// decay across the data segments of CTA k of the line: d^{S RPT} for the
+// CTAs before the last one holding data (kL), d^{len} for that one (dL),
+// 1 past it
 template <class T>
-__device__ __forceinline__ T cta_mult(const StridedCtx<T> &c, int k, int rpt)
+__device__ __forceinline__ T cta_mult(const StridedCtx<T> &c, int k)
 {
-    const int nf = max(0, min(c.S, c.Gd - k * c.S));
-    return c.dpg[nf * rpt];
+    return k < c.kL ? c.dS : (k == c.kL ? c.dL : (T)1);
 }
+
+// per-kernel constants of cta_mult
+template <class T, int RPT>
+__device__ __forceinline__ void strided_cta_consts(StridedCtx<T> &c)
+{
+    c.kL = c.Gd > 0 ? (c.Gd - 1) / c.S : 0;
+    c.dS = c.kL > 0 ? c.dpg[c.S * RPT] : (T)1;          // read only when a full CTA precedes the last
+    c.dL = c.dpg[(c.Gd - c.kL * c.S) * RPT];           // <= n + RPT - 1 (tables padded past d^n)
+}
+
+// Exchanges across the segments of a line.  The totals of the warps of this
+// CTA (shared memory) and of the cluster's CTAs (distributed shared memory)
+// are combined by short recurrences; the loads of a group of them are issued
+// together (KMAX = 8 CTAs, SMAX = 16 warps at most), so that their latencies
+// overlap instead of adding up.
+constexpr int kXchKMax = 8, kXchSMax = 16;
 
 // causal exchange: y at a-1 (zero inflow) and the line's y_{n-1}
 template <class T, int RPT>
@@ -1369,16 +1387,38 @@ __device__ __forceinline__ void strided_causal(const StridedCtx<T> &c, T E, T &y
     __syncthreads();
     if (c.w == 0) {
         T acc = 0;
-        for (int v = 0; v < c.S; ++v) acc = ((c.krank * c.S + v) < c.Gd ? c.dR : (T)1) * acc + c.sl.E[v * 32 + c.lane];
+#pragma unroll
+        for (int v0 = 0; v0 < kXchSMax; v0 += 4) {
+            T ev[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ev[i] = v0 + i < c.S ? c.sl.E[(v0 + i) * 32 + c.lane] : (T)0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (v0 + i < c.S) acc = ((c.krank * c.S + v0 + i) < c.Gd ? c.dR : (T)1) * acc + ev[i];
+        }
         c.sl.Tot[c.lane] = acc;
     }
     csync(c);
-    T cin = 0;
-    for (int k2 = 0; k2 < c.krank; ++k2) cin = cta_mult<T>(c, k2, RPT) * cin + peer_of(c, c.sl.Tot, k2)[c.lane];
-    T tot = cin;
-    for (int k2 = c.krank; k2 < c.K; ++k2) tot = cta_mult<T>(c, k2, RPT) * tot + peer_of(c, c.sl.Tot, k2)[c.lane];
+    T tv[kXchKMax];
+#pragma unroll
+    for (int k2 = 0; k2 < kXchKMax; ++k2) tv[k2] = k2 < c.K ? peer_of(c, c.sl.Tot, k2)[c.lane] : (T)0;
+    T cin = 0, tot = 0;
+#pragma unroll
+    for (int k2 = 0; k2 < kXchKMax; ++k2)
+        if (k2 < c.K) {
+            cin = (k2 == c.krank) ? tot : cin;
+            tot = cta_mult<T>(c, k2) * tot + tv[k2];
+        }
     T acc = cin;
-    for (int v = 0; v < c.w; ++v) acc = c.dR * acc + c.sl.E[v * 32 + c.lane];
+#pragma unroll
+    for (int v0 = 0; v0 < kXchSMax; v0 += 4) {
+        T ev[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ev[i] = v0 + i < c.w ? c.sl.E[(v0 + i) * 32 + c.lane] : (T)0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (v0 + i < c.w) acc = c.dR * acc + ev[i];
+    }
     yin = acc;
     ytot = tot;
 }
@@ -1391,16 +1431,39 @@ __device__ __forceinline__ void strided_anticausal(const StridedCtx<T> &c, T ER,
     __syncthreads();
     if (c.w == 0) {
         T acc = 0;
-        for (int v = c.S - 1; v >= 0; --v) acc = ((c.krank * c.S + v) < c.Gd ? c.dR : (T)1) * acc + c.sl.ER[v * 32 + c.lane];
+#pragma unroll
+        for (int v0 = kXchSMax - 1; v0 >= 0; v0 -= 4) {
+            T ev[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ev[i] = v0 - i < c.S ? c.sl.ER[(v0 - i) * 32 + c.lane] : (T)0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (v0 - i < c.S) acc = ((c.krank * c.S + v0 - i) < c.Gd ? c.dR : (T)1) * acc + ev[i];
+        }
         c.sl.Tot[32 + c.lane] = acc;
     }
     csync(c);
-    T cin = 0;
-    for (int k2 = c.K - 1; k2 > c.krank; --k2) cin = cta_mult<T>(c, k2, RPT) * cin + peer_of(c, c.sl.Tot, k2)[32 + c.lane];
-    T tot = cin;
-    for (int k2 = c.krank; k2 >= 0; --k2) tot = cta_mult<T>(c, k2, RPT) * tot + peer_of(c, c.sl.Tot, k2)[32 + c.lane];
+    T tv[kXchKMax];
+#pragma unroll
+    for (int k2 = 0; k2 < kXchKMax; ++k2) tv[k2] = k2 < c.K ? peer_of(c, c.sl.Tot, k2)[32 + c.lane] : (T)0;
+    T cin = 0, tot = 0;
+#pragma unroll
+    for (int k2 = kXchKMax - 1; k2 >= 0; --k2)
+        if (k2 < c.K) {
+            cin = (k2 == c.krank) ? tot : cin;
+            tot = cta_mult<T>(c, k2) * tot + tv[k2];
+        }
     T acc = cin;
-    for (int v = c.S - 1; v > c.w; --v) acc = ((c.krank * c.S + v) < c.Gd ? c.dR : (T)1) * acc + c.sl.ER[v * 32 + c.lane];
+#pragma unroll
+    for (int v0 = kXchSMax - 1; v0 >= 0; v0 -= 4) {
+        T ev[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ev[i] = (v0 - i > c.w && v0 - i < c.S) ? c.sl.ER[(v0 - i) * 32 + c.lane] : (T)0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (v0 - i > c.w && v0 - i < c.S)
+                acc = ((c.krank * c.S + v0 - i) < c.Gd ? c.dR : (T)1) * acc + ev[i];
+    }
     eout = acc;
     e0 = tot;
 }
@@ -1549,6 +1612,7 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
     c.dR = A.cdm<T>(0);
     c.dpg = dpow_of<T>(A);
     c.Gd = A.n / RPT;
+    strided_cta_consts<T, RPT>(c);
     c.seg = c.krank * c.S + c.w;
     c.a = c.seg * RPT;
     c.full = c.seg < c.Gd;
