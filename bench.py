@@ -761,12 +761,12 @@ def main_adjoint(args, spec):
 
     u0h, uth, rec = adjoint_problem(spec, 7919 * rank)
     N = args.steps                                   # adjoint steps timed
-    b = molt.BatchSolver([(n, n)], dt=dt, P=P, prec=args.prec)
+    b = molt.Solver((n, n), dt=dt, P=P, bc="dirichlet", prec=args.prec)
     b.autotune()
-    u0 = b.pack([u0h])
-    d = b.traces(b.pack([uth]), rec, max(N, nsteps))
+    u0 = torch.from_numpy(u0h).cuda()
+    d = b.traces(torch.from_numpy(uth).cuda(), rec, max(N, nsteps))
     res = b.traces(u0, rec, max(N, nsteps)) - d
-    # warm-up, then the timed adjoint run of N steps (ms = one mol_batch_adjoint call)
+    # warm-up, then the timed adjoint run of N steps (ms = one mol_adjoint call)
     b.adjoint(rec, res[:args.warmup])
     torch.cuda.synchronize()
     barrier()
@@ -801,9 +801,9 @@ def main_adjoint(args, spec):
     achieved = bpp[dom_axis] * pts / (dom_ms * 1e-3) / 1e9
     peak, peak_kind = read_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": read_traffic(dom_axis, spec["name"], args.prec, "batch"),
-                "kernel": {0: "k_batch_x<ADJ> (x pass: transposed Horner + level update)",
-                           1: "k_batch_y<ADJ> (y pass: powers of D_y^T)"}[dom_axis],
+                "traffic": read_traffic(dom_axis, spec["name"], args.prec, "single"),
+                "kernel": {0: "k_contig_rows<ADJ> (x pass: transposed Horner + level update, rows split over warps)",
+                           1: "k_strided<KM = 2> (y pass: powers of D_y^T, clusters)"}[dom_axis],
                 "peak_kind": f"{peak_kind} hbm_gbs (copy)", "alg_bytes_per_launch": bpp[dom_axis] * pts,
                 "passes": {f"axis{a}": {"ms_per_launch": passes[a][0] / passes[a][1],
                                          "alg_GBps": bpp[a] * pts / (passes[a][0] / passes[a][1] * 1e-3) / 1e9,
@@ -820,8 +820,9 @@ def main_adjoint(args, spec):
     # gradient check and mixed-vs-fp64 comparison of the full workload gradient
     if rank == 0 and not args.no_accuracy:
         other = "fp64" if args.prec == "mixed" else "mixed"
-        b2 = molt.BatchSolver([(n, n)], dt=dt, P=P, prec=other)
-        r2 = b2.traces(b2.pack([u0h]), rec, nsteps) - b2.traces(b2.pack([uth]), rec, nsteps)
+        b2 = molt.Solver((n, n), dt=dt, P=P, bc="dirichlet", prec=other)
+        r2 = (b2.traces(torch.from_numpy(u0h).cuda(), rec, nsteps)
+              - b2.traces(torch.from_numpy(uth).cuda(), rec, nsteps))
         g2 = b2.adjoint(rec, r2)
         g1 = b.adjoint(rec, res[:nsteps])
         line["accuracy"] = {"steps": nsteps, f"rel_l2_grad_{args.prec}_vs_{other}":
@@ -836,11 +837,11 @@ def main_adjoint(args, spec):
         dd = d[:nsteps]
 
         def job():
-            u = pin.cuda(non_blocking=True).requires_grad_(True)
+            u = pin.view(n, n).cuda(non_blocking=True).requires_grad_(True)
             tr = molt.receiver_traces(u, b, rec, nsteps)
             loss = 0.5 * ((tr - dd) ** 2).sum()
             loss.backward()
-            gout.copy_(u.grad)
+            gout.copy_(u.grad.view(-1))
             return float(loss)
 
         job()

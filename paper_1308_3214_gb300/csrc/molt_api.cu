@@ -10,6 +10,7 @@
 
 #include "molt.h"
 #include "molt_internal.h"
+#include "molt_recv.cuh"
 
 using namespace molt;
 
@@ -63,6 +64,8 @@ struct mol_ctx {
     // (ragged lines) as a batch of one problem
     mol_batch batch = nullptr;
     mol_batch adj = nullptr;                   // one-problem batch for the adjoint entry points
+    long long *irec = nullptr;                 // receivers (molt_recv.cuh layout), capacity irec_cap
+    int nrec = 0, irec_cap = 0, nnode = 0;
     bool timing = false;                       // per-pass events (benchmarks)
     std::vector<cudaEvent_t> ev_pool;          // reusable events
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (axis, (start, stop))
@@ -229,7 +232,24 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
     if (st != MOL_OK) return st;
     int rpt = 0, S = 0, K = 0;
     cudaError_t e;
-    if (axis == 0 && pr.mode == 1 && pr.nout == 1 && h->tune_rows_warps > 0 &&
+    if (pr.mode == 2 || pr.mode == 3) {
+        // the transposed passes of the adjoint step (register kernels only;
+        // single_adjoint checks that the grid has both plans)
+        int W = 0;
+        if (pr.mode == 3) {
+            for (int w : {h->tune_rows_warps, 4, 2, 8})
+                if (w > 0 && regs_rows_plan(h->tbytes, n, pr.ng, w, &rpt)) { W = w; break; }
+            if (W == 0) return fail(h, MOL_EINVAL, "no register plan for the transposed x pass");
+            e = launch_rows(h->bc, rpt, pr.ng, W, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
+        } else {
+            if (!regs_strided_plan(h->tbytes, h->bc, n, &rpt, &S, &K, h->tune_strided_rpt, h->tune_strided_warps))
+                return fail(h, MOL_EINVAL, "no register plan for the transposed y pass");
+            LineSet L = lineset_of(h, axis);
+            L.S = S;
+            L.K = K;
+            e = launch_strided(h->tbytes, h->bc, rpt, regs_axis(h, axis, rpt), L, pr, s);
+        }
+    } else if (axis == 0 && pr.mode == 1 && pr.nout == 1 && h->tune_rows_warps > 0 &&
         regs_rows_plan(h->tbytes, n, pr.ng, h->tune_rows_warps, &rpt)) {
         e = launch_rows(h->bc, rpt, pr.ng, h->tune_rows_warps, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
     } else if (axis == 0 && pr.mode == 1 && pr.nout == 1 && regs_res_plan(h->tbytes, n, pr.ng, &rpt)) {
@@ -389,6 +409,110 @@ mol_status run_update(mol_ctx *h, const Level &u, const Level &up, const Level &
     const double *b = h->coef_dev;
     return run_update_with(h, h->inter.data(), b + h->off_xc, b + h->off_xu, b + h->off_yc, b + h->off_yu, u, up,
                            un, ea, eb, ec, s);
+}
+
+// 2D Dirichlet handles of float32-pair levels whose x rows split over warps
+// and whose y lines split into strided segments run the adjoint step on the
+// register kernels (transposed modes); others go through a one-problem batch
+bool single_adjoint(const mol_ctx *h)
+{
+    if (h->batch || h->ndim != 2 || h->bc != MOL_BC_DIRICHLET || h->prec != MOL_MIXED) return false;
+    int r = 0, S = 0, K = 0;
+    bool rows = false;
+    for (int w : {2, 4, 8}) rows = rows || regs_rows_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, w, &r);
+    return rows && regs_strided_plan(h->tbytes, h->bc, (int)h->n[1], &r, &S, &K, h->tune_strided_rpt,
+                                     h->tune_strided_warps);
+}
+
+// un = ea u + eb up + ec F^T[u]: powers of D_y^T into the intermediate
+// planes, then the Horner pass in D_x^T with the same coefficients (F^T is
+// the same polynomial in the transposed one-axis operators, which commute)
+mol_status run_update_T(mol_ctx *h, const Level &u, const Level &up, const Level &un, double ea, double eb,
+                        double ec, cudaStream_t s)
+{
+    const int P = h->P;
+    ProgParams y{};
+    y.mode = 2;
+    y.P = P;
+    y.u_hi = u.hi;
+    y.u_lo = u.lo;
+    for (int k = 0; k < P && k < MAXG; ++k) y.out[k] = h->inter[k];
+    mol_status st = run_program(h, 1, y, nullptr, nullptr, s);
+    if (st != MOL_OK) return st;
+    HornerParams hp = h->xtpl;
+    hp.ea = ea; hp.eb = eb; hp.ec = ec;
+    hp.u_hi = u.hi; hp.u_lo = u.lo;
+    hp.up_hi = up.hi; hp.up_lo = up.lo;
+    hp.un_hi = un.hi; hp.un_lo = un.lo;
+    for (int k = 0; k < P; ++k) hp.g[k] = h->inter[k];
+    ProgParams x{};
+    x.mode = 3;
+    x.P = hp.P;
+    x.ng = hp.ng;
+    x.nout = hp.nout;
+    for (int k = 0; k < MAXG; ++k) { x.g[k] = hp.g[k]; x.out[k] = hp.out[k]; }
+    x.coef = h->coef_dev + h->off_xc;
+    x.cu = h->coef_dev + h->off_xu;
+    x.epi = hp.epi;
+    x.ea = ea; x.eb = eb; x.ec = ec;
+    x.u_hi = u.hi; x.u_lo = u.lo; x.up_hi = up.hi; x.up_lo = up.lo; x.un_hi = un.hi; x.un_lo = un.lo;
+    prog_mirror(x, hp);
+    return run_program(h, 0, x, nullptr, &hp, s);
+}
+
+// receivers: flat indices of the field (the levels' own layout)
+mol_status set_receivers(mol_ctx *h, int nrec, const int64_t *rec, cudaStream_t s)
+{
+    if (nrec < 1 || !rec) return fail(h, MOL_EINVAL, "need nrec >= 1 receiver indices");
+    std::vector<long long> ir(nrec);
+    for (int r = 0; r < nrec; ++r) {
+        if (rec[r] < 0 || rec[r] >= h->N) return fail(h, MOL_EINVAL, "receiver index out of range");
+        ir[r] = rec[r];
+    }
+    std::vector<long long> buf;
+    const int nn = receiver_layout(ir, buf);
+    CK(cudaStreamSynchronize(s), "stream synchronize");         // earlier calls may still read the buffer
+    if (nrec > h->irec_cap) {
+        if (h->irec) {
+            cudaFree(h->irec);
+            h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->irec));
+            h->irec = nullptr;
+            h->irec_cap = 0;
+        }
+        mol_status st = dev_alloc(h, (void **)&h->irec, sizeof(long long) * buf.size());
+        if (st != MOL_OK) return st;
+        h->irec_cap = nrec;
+    }
+    CK(cudaMemcpy(h->irec, buf.data(), sizeof(long long) * buf.size(), cudaMemcpyHostToDevice), "receiver upload");
+    h->nrec = nrec;
+    h->nnode = nn;
+    return MOL_OK;
+}
+
+mol_status gather(mol_ctx *h, const Level &L, double *out, cudaStream_t s)
+{
+    const int blocks = (h->nrec + 255) / 256;
+    k_recv_gather<float><<<blocks, 256, 0, s>>>((const float *)L.hi, (const float *)L.lo, h->irec, h->nrec, out);
+    CK(cudaGetLastError(), "receiver gather");
+    h->launches++;
+    return MOL_OK;
+}
+
+mol_status inject(mol_ctx *h, const Level &L, const double *vals, cudaStream_t s)
+{
+    const long long *node = h->irec + h->nrec, *start = node + h->nrec, *order = start + h->nrec + 1;
+    k_recv_inject<float><<<(h->nnode + 127) / 128, 128, 0, s>>>((float *)L.hi, (float *)L.lo, node, start, order,
+                                                                h->nnode, vals);
+    CK(cudaGetLastError(), "receiver injection");
+    h->launches++;
+    return MOL_OK;
+}
+
+mol_status zero_level(mol_ctx *h, const Level &L, cudaStream_t s)
+{
+    CK(cudaMemsetAsync(L.hi, 0, (size_t)h->tbytes * h->N, s), "level clear");
+    if (L.lo) CK(cudaMemsetAsync(L.lo, 0, (size_t)h->tbytes * h->N, s), "level clear");
+    return MOL_OK;
 }
 
 mol_status load_level(mol_ctx *h, const double *x, const Level &L, cudaStream_t s)
@@ -914,6 +1038,15 @@ static mol_status adjoint_batch(mol_ctx *h, mol_batch *out)
 mol_status mol_apply_FT(mol_handle h, const double *w, double *out, void *stream)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (single_adjoint(h)) {
+        mol_status st;
+        if ((st = check_ptr(h, w, "w")) != MOL_OK || (st = check_ptr(h, out, "out")) != MOL_OK) return st;
+        if (w == out) return fail(h, MOL_EINVAL, "w and out must not overlap");
+        cudaStream_t s = (cudaStream_t)stream;
+        if ((st = load_level(h, w, h->lev[0], s)) != MOL_OK) return st;
+        if ((st = run_update_T(h, h->lev[0], h->lev[0], h->lev[1], 0.0, 0.0, 1.0, s)) != MOL_OK) return st;
+        return store_level(h, h->lev[1], out, s);
+    }
     mol_batch b = nullptr;
     mol_status st = adjoint_batch(h, &b);
     if (st != MOL_OK) return st;
@@ -925,6 +1058,24 @@ mol_status mol_traces(mol_handle h, const double *u0, int nrec, const int64_t *r
                       void *stream)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (single_adjoint(h)) {
+        if (nsteps < 1) return fail(h, MOL_EINVAL, "nsteps must be >= 1");
+        mol_status st;
+        if ((st = check_ptr(h, u0, "u0")) != MOL_OK || (st = check_ptr(h, traces, "traces")) != MOL_OK) return st;
+        cudaStream_t s = (cudaStream_t)stream;
+        if ((st = set_receivers(h, nrec, rec, s)) != MOL_OK) return st;
+        // traces[n-1] = u^n at the receivers, n = 1..nsteps
+        int ip = 0, ic = 1, in = 2;
+        if ((st = load_level(h, u0, h->lev[ip], s)) != MOL_OK) return st;
+        if ((st = run_update(h, h->lev[ip], h->lev[ip], h->lev[ic], 1.0, 0.0, 0.5, s)) != MOL_OK) return st;
+        if ((st = gather(h, h->lev[ic], traces, s)) != MOL_OK) return st;
+        for (int64_t n = 1; n < nsteps; ++n) {
+            if ((st = run_update(h, h->lev[ic], h->lev[ip], h->lev[in], 2.0, -1.0, 1.0, s)) != MOL_OK) return st;
+            if ((st = gather(h, h->lev[in], traces + n * nrec, s)) != MOL_OK) return st;
+            const int t = ip; ip = ic; ic = in; in = t;
+        }
+        return MOL_OK;
+    }
     mol_batch b = nullptr;
     mol_status st = adjoint_batch(h, &b);
     if (st != MOL_OK) return st;
@@ -936,6 +1087,27 @@ mol_status mol_adjoint(mol_handle h, int nrec, const int64_t *rec, int64_t nstep
                        void *stream)
 {
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (single_adjoint(h)) {
+        if (nsteps < 1) return fail(h, MOL_EINVAL, "nsteps must be >= 1");
+        mol_status st;
+        if ((st = check_ptr(h, tgrad, "tgrad")) != MOL_OK || (st = check_ptr(h, grad, "grad")) != MOL_OK) return st;
+        cudaStream_t s = (cudaStream_t)stream;
+        if ((st = set_receivers(h, nrec, rec, s)) != MOL_OK) return st;
+        // the reverse recursion of the trace map: mu^N = g^N,
+        // mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n,
+        // dJ/du^0 = mu^1 + F^T mu^1 / 2 - mu^2
+        int ia = 0, ib = 1, ic = 2;
+        if ((st = zero_level(h, h->lev[ia], s)) != MOL_OK) return st;
+        if ((st = zero_level(h, h->lev[ib], s)) != MOL_OK) return st;
+        if ((st = inject(h, h->lev[ib], tgrad + (nsteps - 1) * nrec, s)) != MOL_OK) return st;
+        for (int64_t n = nsteps - 1; n >= 1; --n) {
+            if ((st = run_update_T(h, h->lev[ib], h->lev[ia], h->lev[ic], 2.0, -1.0, 1.0, s)) != MOL_OK) return st;
+            if ((st = inject(h, h->lev[ic], tgrad + (n - 1) * nrec, s)) != MOL_OK) return st;
+            const int t = ia; ia = ib; ib = ic; ic = t;
+        }
+        if ((st = run_update_T(h, h->lev[ib], h->lev[ia], h->lev[ic], 1.0, -1.0, 0.5, s)) != MOL_OK) return st;
+        return store_level(h, h->lev[ic], grad, s);
+    }
     mol_batch b = nullptr;
     mol_status st = adjoint_batch(h, &b);
     if (st != MOL_OK) return st;

@@ -321,23 +321,10 @@ mol_status set_receivers(mol_batch_ctx *b, int nrec, const int64_t *rec, cudaStr
         const int64_t loc = g - b->uoff[p];
         ir[r] = pb.off + (loc / pb.ax.n) * pb.pitch + loc % pb.ax.n;
     }
-    // receivers grouped by node (stable: each group in receiver order), so
-    // that the injection runs one thread per distinct node
-    std::vector<int> ord(nrec);
-    for (int r = 0; r < nrec; ++r) ord[r] = r;
-    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return ir[x] < ir[y]; });
-    std::vector<long long> buf(4 * (size_t)nrec + 1, 0);
-    long long *node = buf.data() + nrec, *start = node + nrec, *order = start + nrec + 1;
-    int nn = 0;
-    for (int j = 0; j < nrec; ++j) {
-        if (j == 0 || ir[ord[j]] != ir[ord[j - 1]]) {
-            node[nn] = ir[ord[j]];
-            start[nn++] = j;
-        }
-        order[j] = ord[j];
-    }
-    start[nn] = nrec;
-    for (int r = 0; r < nrec; ++r) buf[r] = ir[r];
+    // receivers grouped by node, so that the injection runs one thread per
+    // distinct node (molt_recv.cuh)
+    std::vector<long long> buf;
+    const int nn = receiver_layout(ir, buf);
     BCK(cudaStreamSynchronize(s), "stream synchronize");
     if (nrec > b->irec_cap) {
         if (b->irec) {
@@ -359,8 +346,8 @@ mol_status set_receivers(mol_batch_ctx *b, int nrec, const int64_t *rec, cudaStr
 mol_status gather(mol_batch_ctx *b, const BLevel &L, double *out, cudaStream_t s)
 {
     const int blocks = (b->nrec + 255) / 256;
-    if (b->tbytes == 4) k_batch_gather<float><<<blocks, 256, 0, s>>>((const float *)L.hi, (const float *)L.lo, b->irec, b->nrec, out);
-    else k_batch_gather<double><<<blocks, 256, 0, s>>>((const double *)L.hi, nullptr, b->irec, b->nrec, out);
+    if (b->tbytes == 4) k_recv_gather<float><<<blocks, 256, 0, s>>>((const float *)L.hi, (const float *)L.lo, b->irec, b->nrec, out);
+    else k_recv_gather<double><<<blocks, 256, 0, s>>>((const double *)L.hi, nullptr, b->irec, b->nrec, out);
     BCK(cudaGetLastError(), "receiver gather");
     b->launches++;
     return MOL_OK;
@@ -372,9 +359,9 @@ mol_status inject(mol_batch_ctx *b, const BLevel &L, const double *vals, cudaStr
     const long long *node = b->irec + b->nrec, *start = node + b->nrec, *order = start + b->nrec + 1;
     const int blocks = (b->nnode + 127) / 128;
     if (b->tbytes == 4)
-        k_batch_inject<float><<<blocks, 128, 0, s>>>((float *)L.hi, (float *)L.lo, node, start, order, b->nnode, vals);
+        k_recv_inject<float><<<blocks, 128, 0, s>>>((float *)L.hi, (float *)L.lo, node, start, order, b->nnode, vals);
     else
-        k_batch_inject<double><<<blocks, 128, 0, s>>>((double *)L.hi, nullptr, node, start, order, b->nnode, vals);
+        k_recv_inject<double><<<blocks, 128, 0, s>>>((double *)L.hi, nullptr, node, start, order, b->nnode, vals);
     BCK(cudaGetLastError(), "receiver injection");
     b->launches++;
     return MOL_OK;

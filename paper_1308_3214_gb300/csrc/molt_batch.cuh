@@ -23,6 +23,7 @@
 // padding carries zeros and is never read as data.
 #pragma once
 #include "molt_regs.cuh"
+#include "molt_recv.cuh"
 
 namespace molt {
 
@@ -851,44 +852,6 @@ __global__ void k_batch_unpack(const BatchProb *probs, const int *row_prob, cons
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 if (j + c < nx) dstp[j + c] = v[c];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// receivers (internal-layout indices): traces and adjoint sources
-// ---------------------------------------------------------------------------
-// out[r] = level value at irec[r]
-template <class T>
-__global__ void k_batch_gather(const T *hi, const T *lo, const long long *irec, int nrec, double *out)
-{
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
-        const long long i = irec[r];
-        double v = (double)hi[i];
-        if constexpr (sizeof(T) == 4) v += (double)lo[i];
-        out[r] = v;
-    }
-}
-
-// level[node[u]] += the values of the node's receivers, added in receiver
-// order (order[start[u]] .. order[start[u+1] - 1]); one thread per distinct
-// node, so receivers that share a node need no atomics and the sum is the
-// same on every run
-template <class T>
-__global__ void k_batch_inject(T *hi, T *lo, const long long *node, const long long *start, const long long *order,
-                               int nnode, const double *vals)
-{
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nnode; u += gridDim.x * blockDim.x) {
-        const long long i = node[u];
-        double x = (double)hi[i];
-        if constexpr (sizeof(T) == 4) x += (double)lo[i];
-        for (long long j = start[u]; j < start[u + 1]; ++j) x += vals[order[j]];
-        if constexpr (sizeof(T) == 4) {
-            const float h = __double2float_rn(x);
-            hi[i] = h;
-            lo[i] = __double2float_rn(x - (double)h);
-        } else {
-            hi[i] = x;
         }
     }
 }

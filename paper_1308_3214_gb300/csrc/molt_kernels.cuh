@@ -115,7 +115,8 @@ struct HornerParams {
 //       X = 0;  for t = P..1: X = D( sum_k coef[o][t][k] g_k + X + cu[o][t] u )
 //       out_o = sum_k coef[o][0][k] g_k + X     (or the level combination)
 struct ProgParams {
-    int mode, P, ng, nout;
+    int mode;             // 0 powers, 1 Horner, 2 powers of D^T, 3 Horner in D^T (adjoint step)
+    int P, ng, nout;
     const void *g[MAXG];
     void *out[MAXG];
     const double *coef;   // device, [nout][P+1][ng]

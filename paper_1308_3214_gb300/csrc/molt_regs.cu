@@ -33,6 +33,12 @@ size_t rows_smem() { return row_slots_bytes<float, W>() + (size_t)NB * 32 * W * 
 template <int BC, int RPT, int NB, int W>
 cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
 {
+    if constexpr (BC == BC_DIRICHLET) {
+        if (p.mode == 3) {                            // the transposed Horner pass
+            k_contig_rows<BC, RPT, NB, W, true><<<(unsigned)L.nlines, 32 * W, rows_smem<RPT, NB, W>(), s>>>(A, L, p);
+            return cudaGetLastError();
+        }
+    }
     k_contig_rows<BC, RPT, NB, W><<<(unsigned)L.nlines, 32 * W, rows_smem<RPT, NB, W>(), s>>>(A, L, p);
     return cudaGetLastError();
 }
@@ -40,8 +46,22 @@ cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cu
 template <int BC, int RPT, int NB, int W>
 cudaError_t attr_rows()
 {
-    return cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)rows_smem<RPT, NB, W>());
+    // the largest shared-memory carveout: the CTAs per SM are then limited
+    // by registers and the row's buffers, not by the default split with L1
+    cudaError_t e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rows_smem<RPT, NB, W>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if constexpr (BC == BC_DIRICHLET) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)rows_smem<RPT, NB, W>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W, true>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    }
+    return e;
 }
 
 template <class T, int RPT>
@@ -72,8 +92,10 @@ cudaError_t run_strided(const AxisDev &A, const LineSet &L, const ProgParams &p,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = L.K > 1 ? 1 : 0;
-    if (p.mode == 1) return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, true>, A, L, p);
-    return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, false>, A, L, p);
+    if (p.mode == 1) return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, 1>, A, L, p);
+    if constexpr (BC == BC_DIRICHLET)
+        if (p.mode == 2) return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, 2>, A, L, p);
+    return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, 0>, A, L, p);
 }
 
 template <class T, int BC, int RPT>
@@ -86,9 +108,13 @@ cudaError_t attr_contig()
 template <class T, int BC, int RPT>
 cudaError_t attr_strided()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_strided<T, BC, RPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_strided<T, BC, RPT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_strided<T, BC, RPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if constexpr (BC == BC_DIRICHLET) {
+        e = cudaFuncSetAttribute(k_strided<T, BC, RPT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaFuncSetAttribute(k_strided<T, BC, RPT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace

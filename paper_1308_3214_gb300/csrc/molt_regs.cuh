@@ -1165,10 +1165,14 @@ __device__ __forceinline__ void row_sweep_T(T (&z)[RPT], const T (&u)[RPT], T cu
 template <class T, int W>
 __host__ __device__ constexpr size_t row_slots_bytes() { return (sizeof(RowSlots<T, W>) + 15) & ~(size_t)15; }
 
-template <int BC, int RPT, int NB, int W>
+// ADJ (Dirichlet): the transposed Horner pass of the adjoint step,
+// F^T = sum_t (D_x^T)^t (f_t0 u + sum_k f_tk g_k) with g_k = (D_y^T)^{k+1} u;
+// u itself (pairs summed) takes the place of its second difference.
+template <int BC, int RPT, int NB, int W, bool ADJ = false>
 __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 6 : 4)) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr)
 {
     static_assert(RPT % 4 == 0 && RPT >= 8, "segment length");
+    static_assert(!ADJ || BC == BC_DIRICHLET, "the transposed pass is for Dirichlet rows");
     using T = float;
     using St = ContigStage<T, RPT>;
     constexpr int NT = 32 * W;                        // threads (segments) of one row
@@ -1234,10 +1238,15 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 6 : 4)) k_conti
             ll = (lane == 0) ? lx[i] : ll;
             hr = (lane == 31) ? hx[i] : hr;
             lr = (lane == 31) ? lx[i] : lr;
-            float4 rv = sdiff4(h[i], l[i], hl, ll, hr, lr);
-            if (BC == BC_DIRICHLET) {                // end nodes take the neighbouring interior centre
-                if (v == 0) rv.x = rv.y;
-                if (4 * v + 4 == n) rv.w = rv.z;
+            float4 rv;
+            if constexpr (ADJ) {
+                rv = make_float4(h[i].x + l[i].x, h[i].y + l[i].y, h[i].z + l[i].z, h[i].w + l[i].w);
+            } else {
+                rv = sdiff4(h[i], l[i], hl, ll, hr, lr);
+                if (BC == BC_DIRICHLET) {            // end nodes take the neighbouring interior centre
+                    if (v == 0) rv.x = rv.y;
+                    if (4 * v + 4 == n) rv.w = rv.z;
+                }
             }
             *reinterpret_cast<float4 *>(R + St::pos(4 * v)) = rv;
         }
@@ -1275,7 +1284,8 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 6 : 4)) k_conti
             }
         }
         if (tt == 0) break;
-        row_sweep<T, BC, RPT, W>(z, r, rl, rr, prog_cu<T>(pr, tt), A, lane, warp, sl);
+        if constexpr (ADJ) row_sweep_T<T, RPT, W>(z, r, prog_cu<T>(pr, tt), A, lane, warp, sl);
+        else row_sweep<T, BC, RPT, W>(z, r, rl, rr, prog_cu<T>(pr, tt), A, lane, warp, sl);
     }
 
     // F -> coalesced side -> next level
@@ -1501,6 +1511,9 @@ __device__ __forceinline__ void strided_halos(const StridedCtx<T> &c, const T (&
     // by which time every reader is done with it
 }
 
+template <class T, int BC, int RPT>
+__device__ __forceinline__ void strided_solve(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT]);
+
 // One application of D on this thread's segment.  MODE as in seg_make_q;
 // halos l2, l1, r0, r1 as exchanged (MODE 0: l1 = s_{a-1}, r0 = s_{a+RPT}).
 template <class T, int BC, int RPT, int MODE>
@@ -1520,6 +1533,15 @@ __device__ __forceinline__ void strided_sweep(const StridedCtx<T> &c, const Axis
 #pragma unroll
         for (int k = 0; k < RPT; ++k) z[k] = 0;
     }
+    strided_solve<T, BC, RPT>(c, A, z);
+}
+
+// The solve of the difference form on this thread's segment of a strided
+// line of whole segments: z holds q on entry (zero in segments past the
+// line), e on exit (Dirichlet: e = 0 at both end nodes; periodic: images)
+template <class T, int BC, int RPT>
+__device__ __forceinline__ void strided_solve(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT])
+{
     const T d = c.d;
     const T dH = c.dpg[RPT / 2];
     T E1, ER2;
@@ -1542,6 +1564,26 @@ __device__ __forceinline__ void strided_sweep(const StridedCtx<T> &c, const Axis
     const T acc = d * eout + (c.full ? c.dpg[c.n - c.a - RPT] * Z : (T)0);
     seg_bwd_scan2<T, RPT>(z, d, dH, acc, ER2);
     if (BC == BC_DIRICHLET && c.full) seg_add_left2<T, RPT>(z, d, dH, Acoef * c.dpg[c.a]);
+}
+
+// One application of D^T (Dirichlet) on this thread's segment of a strided
+// line of whole segments (the transposed difference form of post_T): the
+// solve on the interior values, then t' and its second difference with the
+// neighbouring segments' e as halos.  hbuf: halo slot set (alternating).
+template <class T, int RPT>
+__device__ __forceinline__ void strided_sweep_T(const StridedCtx<T> &c, const AxisDev &A, T (&z)[RPT], int hbuf)
+{
+    const int kl = c.n - 1 - c.a;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) z[k] = (k < kl && (c.seg > 0 || k > 0)) ? z[k] : (T)0;   // interior rows only
+    strided_solve<T, BC_DIRICHLET, RPT>(c, A, z);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) z[k] = (k < kl && (c.seg > 0 || k > 0)) ? z[k] : (T)0;
+    T l2, l1, r0, r1;
+    strided_halos<T, BC_DIRICHLET, RPT>(c, z, l2, l1, r0, r1, hbuf);
+    const T c1 = A.cc1<T>(), c2 = A.cc2<T>();
+    if (c.seg == 0 || c.seg == c.Gd - 1) post_T<T, RPT, true>(z, l2, l1, r0, r1, c1, c2, c.a, c.n);
+    else post_T<T, RPT, false>(z, l2, l1, r0, r1, c1, c2, c.a, c.n);
 }
 
 // second differences r of u at points a-1 .. a+RPT of one strided line, from
@@ -1597,7 +1639,9 @@ __device__ __forceinline__ void strided_r_pair(const ProgParams &pr, int64_t lba
     }
 }
 
-template <class T, int BC, int RPT, bool HORNER>
+// KM: 0 powers D^p u, 1 Horner with several outputs, 2 powers (D^T)^p u
+// (Dirichlet; the adjoint step)
+template <class T, int BC, int RPT, int KM>
 __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgParams pr)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1632,9 +1676,35 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
     const int64_t lbase = valid ? (line % LS.inner) + (line / LS.inner) * LS.inner * (int64_t)n : 0;
     const int64_t st = LS.stride;
 
+    T z[RPT];
+    if constexpr (KM == 2) {
+        static_assert(BC == BC_DIRICHLET, "the transposed powers are for Dirichlet lines");
+        // the level value itself (pairs summed), then its powers of D^T
+        const T *H = reinterpret_cast<const T *>(pr.u_hi) + lbase, *L = reinterpret_cast<const T *>(pr.u_lo) + lbase;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            T v = 0;
+            if (io) {
+                v = H[(int64_t)(a + k) * st];
+                if constexpr (sizeof(T) == 4) v += L[(int64_t)(a + k) * st];
+            }
+            z[k] = v;
+        }
+        for (int p = 1; p <= pr.P; ++p) {
+            strided_sweep_T<T, RPT>(c, A, z, p & 1);
+            T *o = reinterpret_cast<T *>(pr.out[p - 1]);
+            if (o != nullptr && io) {
+                T *po = o + lbase + (int64_t)a * st;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) { *po = z[k]; po += st; }
+            }
+        }
+        if (c.K > 1) c.cl.sync();       // see the powers path below
+        return;
+    }
+
     // r = accurate second difference of u along the line (Dirichlet end
     // nodes use the neighbouring interior centre)
-    T z[RPT];
     T rl = 0, rr = 0;
     if (io) strided_r_pair<BC, RPT>(pr, lbase, st, a, n, z, rl, rr);
     else {
@@ -1646,7 +1716,7 @@ __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgP
         if (c.seg == c.Gd - 1) z[RPT - 1] = z[RPT - 2];
     }
 
-    if (!HORNER) {
+    if (KM == 0) {
         // powers; the first sweep starts from s = r
         for (int p = 1; p <= pr.P; ++p) {
             if (p == 1) {

@@ -338,6 +338,72 @@ def test_history_gradient_matches_central_difference():
     assert abs(fd - an) <= 1e-6 * abs(an)
 
 
+def adjoint_bound(tg, shape, rec, nu, P, beta):
+    """Mixed-precision error model of the adjoint recursion: 8 eps32
+    (1 + 1/(1-d)) 2P times sum_n |F^T mu^n| over the oracle's own states."""
+    nsteps = tg.shape[0]
+    size = int(np.prod(shape))
+    g = np.zeros((nsteps, size))
+    for n in range(nsteps):
+        np.add.at(g[n], rec, tg[n])
+    m2, m1 = np.zeros(shape), g[-1].reshape(shape)
+    Fsum = 0.0
+    for n in range(nsteps - 1, 0, -1):
+        F = oracle.FT(m1, nu, P, beta, "dirichlet")
+        Fsum += np.linalg.norm(F)
+        m2, m1 = m1, 2 * m1 - m2 + F + g[n - 1].reshape(shape)
+    Fsum += 0.5 * np.linalg.norm(oracle.FT(m1, nu, P, beta, "dirichlet"))
+    return model(nu, P) * Fsum
+
+
+@pytest.mark.parametrize("shape", [(128, 1024), (192, 2048)])
+def test_single_path_adjoint_mixed_matches_oracle(shape):
+    """Mixed-precision handles whose rows split over warps and whose columns
+    split into strided segments run F^T, traces and the adjoint on the
+    register kernels' transposed modes (not a one-problem batch: the
+    handle's own pass timers see the passes)."""
+    P, nsteps = 2, 6
+    ny, nx = shape
+    dt = 2.0 / (max(shape) - 1)
+    s = molt.Solver(shape, dt=dt, P=P, bc="dirichlet", prec="mixed")
+    nu, beta = s.nu, s.beta
+    rng = np.random.default_rng(41)
+    w = rng.normal(size=shape)
+    s.set_pass_timing(True)
+    got = s.apply_FT(torch.from_numpy(w).cuda()).cpu().numpy()
+    t = s.pass_times()
+    s.set_pass_timing(False)
+    assert t[0][1] == 1 and t[1][1] == 1, t
+    ref = oracle.FT(w, nu, P, beta, "dirichlet")
+    cond = np.linalg.norm(w) / np.linalg.norm(ref)
+    assert rel_l2(got, ref) <= 2 * model(nu, P) * max(cond, 1.0)
+    u0 = rng.normal(size=shape)
+    u0[0, :] = u0[-1, :] = 0
+    u0[:, 0] = u0[:, -1] = 0
+    rec = np.concatenate([rng.choice(ny * nx, size=7, replace=False), [5 * nx + 9, 5 * nx + 9]])
+    tr = s.traces(torch.from_numpy(u0).cuda(), rec, nsteps).cpu().numpy()
+    tref = oracle.traces(u0, nsteps, rec, nu, P, beta, "dirichlet")
+    assert np.abs(tr - tref).max() <= model(nu, P) * oracle_states(u0, nsteps, nu, P, beta)
+    tg = rng.normal(size=(nsteps, rec.size))
+    g = s.adjoint(rec, torch.from_numpy(tg)).cpu().numpy()
+    gref = oracle.adjoint(tg, shape, rec, nu, P, beta, "dirichlet")
+    assert np.linalg.norm(g - gref) <= adjoint_bound(tg, shape, rec, nu, P, beta)
+
+
+def test_single_path_FT_is_the_transpose_of_F():
+    """<F u, w> = <u, F^T w> with both sides from the mixed single path on the
+    adjoint workload's grid."""
+    shape = (1024, 1024)
+    s = molt.Solver(shape, dt=2.0 / 1023, P=2, bc="dirichlet", prec="mixed")
+    rng = np.random.default_rng(42)
+    u = torch.from_numpy(rng.normal(size=shape)).cuda()
+    w = torch.from_numpy(rng.normal(size=shape)).cuda()
+    lhs = float(torch.sum(s.apply_F(u) * w))
+    rhs = float(torch.sum(u * s.apply_FT(w)))
+    scale = float(torch.linalg.norm(u) * torch.linalg.norm(w))
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
 @pytest.mark.parametrize("shape", [(128, 256), (100, 129)])
 def test_single_handle_adjoint_matches_oracle(shape):
     """mol_apply_FT / mol_traces / mol_adjoint on a mol_create handle (a
