@@ -268,6 +268,7 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
         G.wshift = ilog2(G.W);
         AxisDev A = h->ax[axis];
         A.ls = line_stride(A.ms, G.W, h->tbytes);
+        G.dps = pass_smem_bytes(hp != nullptr, h->tbytes, G.W, A.ls, A.n, 1) <= h->smem_optin ? 1 : 0;
         e = hp ? launch_horner(h->tbytes, h->bc, axis == 0, A, G, *hp, s)
                : launch_powers(h->tbytes, h->bc, axis == 0, A, G, *pp, s);
     }

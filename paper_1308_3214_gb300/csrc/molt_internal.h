@@ -8,7 +8,8 @@
 namespace molt {
 
 constexpr int kMaxP = 5;            // highest order parameter P (order 2P)
-constexpr int64_t kMaxLine = 8192;  // longest line of the single-problem sweeps
+constexpr int64_t kMaxLine = 12288;  // longest line of the single-problem sweeps (two float64
+                                     // line buffers of one line fill most of shared memory)
 
 // Host constants of the scheme (molt_host.cu).
 double term_weight(int p, int m, double beta);     // weight of C^m D^{p-m} in the update
@@ -34,7 +35,7 @@ cudaError_t launch_from_f32(const float *f, double *x, int64_t N, cudaStream_t s
 cudaError_t configure_kernels();
 
 // Bytes of dynamic shared memory a pass needs.
-size_t pass_smem_bytes(bool horner, int tbytes, int W, int ls, int n);
+size_t pass_smem_bytes(bool horner, int tbytes, int W, int ls, int n, int dps = 1);
 
 // Line stride in shared memory for W lines of segment stride ms.
 int line_stride(int ms, int W, int tbytes);

@@ -82,6 +82,8 @@ struct PassGeom {
     int64_t nlines;  // number of lines
     int W;           // lines (warps) per CTA, a power of two <= 16
     int wshift;      // log2(W)
+    int dps;         // 1: the d^j table is copied to shared memory; 0 (long lines whose
+                     //    buffers leave no room): it is read from global memory
 };
 
 constexpr int MAXP = 6;     // P <= 5, Horner steps 0..P
@@ -223,7 +225,7 @@ __device__ __forceinline__ int spos(int j, const AxisDev &A)
 //   MODE 0: buf holds s already (first power of u; ends pre-duplicated).
 //   MODE 1: s = second difference of buf.
 //   MODE 2: s = second difference of buf + cu * r, r from rbuf.
-// dp points to the d^j table in shared memory.
+// dp points to the d^j table (shared memory, or global memory for long lines).
 // ---------------------------------------------------------------------------
 template <class T, int MODE, int BC>
 __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
@@ -360,17 +362,17 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
 // CTA helpers
 // ---------------------------------------------------------------------------
 // Shared-memory carve-out of a pass CTA: `arrays` line buffers of W lines,
-// the d^j table (n+1 values) and the W line base offsets.
+// the d^j table (n+1 values; none when dps == 0) and the W line base offsets.
 struct SmemLayout {
     size_t lines, dpow, lbase, total;
 };
 __host__ __device__ inline size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
-__host__ __device__ inline SmemLayout smem_layout(int arrays, int W, int ls, int n, size_t tsize)
+__host__ __device__ inline SmemLayout smem_layout(int arrays, int W, int ls, int n, size_t tsize, int dps = 1)
 {
     SmemLayout L;
     L.lines = 0;
     L.dpow = round16((size_t)arrays * W * ls * tsize);
-    L.lbase = L.dpow + round16((size_t)(n + 1) * tsize);
+    L.lbase = L.dpow + (dps ? round16((size_t)(n + 1) * tsize) : 0);
     L.total = L.lbase + round16((size_t)W * sizeof(int64_t));
     return L;
 }
@@ -459,9 +461,9 @@ __global__ void __launch_bounds__(512) k_powers(AxisDev A, PassGeom G, PowersPar
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.n, W = G.W;
-    const SmemLayout SL = smem_layout(1, W, A.ls, n, sizeof(T));
+    const SmemLayout SL = smem_layout(1, W, A.ls, n, sizeof(T), G.dps);
     T *lines = reinterpret_cast<T *>(smem_raw + SL.lines);
-    T *dp = reinterpret_cast<T *>(smem_raw + SL.dpow);
+    T *dps = reinterpret_cast<T *>(smem_raw + SL.dpow);
     int64_t *lbase = reinterpret_cast<int64_t *>(smem_raw + SL.lbase);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t L0 = (int64_t)blockIdx.x * W;
@@ -469,7 +471,9 @@ __global__ void __launch_bounds__(512) k_powers(AxisDev A, PassGeom G, PowersPar
     const int nl = rem < W ? (int)rem : W;
 
     const T *dpg = dpow_of<T>(A);
-    for (int j = threadIdx.x; j <= n; j += blockDim.x) dp[j] = dpg[j];
+    if (G.dps)
+        for (int j = threadIdx.x; j <= n; j += blockDim.x) dps[j] = dpg[j];
+    const T *dp = G.dps ? dps : dpg;
     if (threadIdx.x < W) lbase[threadIdx.x] = line_base(G, L0 + ((int)threadIdx.x < nl ? (int)threadIdx.x : nl - 1), n);
     __syncthreads();
 
@@ -531,10 +535,10 @@ __global__ void __launch_bounds__(512) k_horner(AxisDev A, PassGeom G, HornerPar
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.n, W = G.W;
-    const SmemLayout SL = smem_layout(2, W, A.ls, n, sizeof(T));
+    const SmemLayout SL = smem_layout(2, W, A.ls, n, sizeof(T), G.dps);
     T *lines = reinterpret_cast<T *>(smem_raw + SL.lines);
     T *rlines = lines + (size_t)W * A.ls;
-    T *dp = reinterpret_cast<T *>(smem_raw + SL.dpow);
+    T *dps = reinterpret_cast<T *>(smem_raw + SL.dpow);
     int64_t *lbase = reinterpret_cast<int64_t *>(smem_raw + SL.lbase);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t L0 = (int64_t)blockIdx.x * W;
@@ -542,7 +546,9 @@ __global__ void __launch_bounds__(512) k_horner(AxisDev A, PassGeom G, HornerPar
     const int nl = rem < W ? (int)rem : W;
 
     const T *dpg = dpow_of<T>(A);
-    for (int j = threadIdx.x; j <= n; j += blockDim.x) dp[j] = dpg[j];
+    if (G.dps)
+        for (int j = threadIdx.x; j <= n; j += blockDim.x) dps[j] = dpg[j];
+    const T *dp = G.dps ? dps : dpg;
     if (threadIdx.x < W) lbase[threadIdx.x] = line_base(G, L0 + ((int)threadIdx.x < nl ? (int)threadIdx.x : nl - 1), n);
     __syncthreads();
 

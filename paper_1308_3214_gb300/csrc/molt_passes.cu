@@ -56,9 +56,9 @@ int line_stride(int ms, int W, int tbytes)
     return base + (W <= 16 ? 16 / W : 1);
 }
 
-size_t pass_smem_bytes(bool horner, int tbytes, int W, int ls, int n)
+size_t pass_smem_bytes(bool horner, int tbytes, int W, int ls, int n, int dps)
 {
-    return smem_layout(horner ? 2 : 1, W, ls, n, (size_t)tbytes).total;
+    return smem_layout(horner ? 2 : 1, W, ls, n, (size_t)tbytes, dps).total;
 }
 
 template <class T, int BC, bool CONTIG>
@@ -84,7 +84,7 @@ cudaError_t configure_kernels()
 template <class T, int BC, bool CONTIG>
 static cudaError_t run_powers(const AxisDev &A, const PassGeom &G, const PowersParams &p, cudaStream_t s)
 {
-    const size_t smem = pass_smem_bytes(false, sizeof(T), G.W, A.ls, A.n);
+    const size_t smem = pass_smem_bytes(false, sizeof(T), G.W, A.ls, A.n, G.dps);
     const int64_t grid = (G.nlines + G.W - 1) / G.W;
     k_powers<T, BC, CONTIG><<<(unsigned)grid, 32 * G.W, smem, s>>>(A, G, p);
     return cudaGetLastError();
@@ -93,7 +93,7 @@ static cudaError_t run_powers(const AxisDev &A, const PassGeom &G, const PowersP
 template <class T, int BC, bool CONTIG>
 static cudaError_t run_horner(const AxisDev &A, const PassGeom &G, const HornerParams &p, cudaStream_t s)
 {
-    const size_t smem = pass_smem_bytes(true, sizeof(T), G.W, A.ls, A.n);
+    const size_t smem = pass_smem_bytes(true, sizeof(T), G.W, A.ls, A.n, G.dps);
     const int64_t grid = (G.nlines + G.W - 1) / G.W;
     k_horner<T, BC, CONTIG><<<(unsigned)grid, 32 * G.W, smem, s>>>(A, G, p);
     return cudaGetLastError();
