@@ -68,6 +68,11 @@ def _load():
         lib.orc_FT.argtypes = [dp, dp, I, lp, dp, I, I, I, D]
         lib.orc_traces.argtypes = [dp, L, I, lp, dp, I, lp, dp, I, I, I, D]
         lib.orc_adjoint.argtypes = [dp, L, I, lp, dp, I, lp, dp, I, I, I, D]
+        lib.orc_linv_line_bc.argtypes = [dp, dp, L, D, I, D, D]
+        lib.orc_D_line_bc.argtypes = [dp, dp, L, D, I, D, D]
+        lib.orc_F_bc.argtypes = [dp, dp, L, D, I, I, D, dp]
+        lib.orc_run_bc.argtypes = [dp, dp, L, L, D, I, I, D, dp]
+        lib.orc_bc_values.argtypes = [dp, I, dp]
         lib.orc_num_threads.restype = I
         _lib = lib
     return _lib
@@ -252,6 +257,55 @@ def run(uprev, ucur, nsteps: int, nu, P: int, beta: float, bc="dirichlet", quad:
     _load().orc_run(_dp(up), _dp(uc), int(nsteps), nd, shp, _dp(nus), int(quad), _bc(bc),
                     int(P), float(beta))
     return up, uc
+
+
+# ---------------------------------------------------------------------------
+# time-dependent Dirichlet data on a 1D line (Sec. 3.2)
+# ---------------------------------------------------------------------------
+def linv_line_bc(v, nu, gL: float, gR: float, quad: int = 2) -> np.ndarray:
+    """L^{-1} v corrected so that D v = v - L^{-1} v takes the values gL, gR
+    at the end nodes."""
+    v = _f64(v)
+    out = np.empty_like(v)
+    _load().orc_linv_line_bc(_dp(v), _dp(out), v.size, float(nu), int(quad), float(gL), float(gR))
+    return out
+
+
+def D_line_bc(v, nu, gL: float, gR: float, quad: int = 2) -> np.ndarray:
+    """D v with the end values gL, gR."""
+    v = _f64(v)
+    out = np.empty_like(v)
+    _load().orc_D_line_bc(_dp(v), _dp(out), v.size, float(nu), int(quad), float(gL), float(gR))
+    return out
+
+
+def F_bc(u, nu, P: int, beta: float, g, quad: int = 2) -> np.ndarray:
+    """F[u] = sum_p A_p D^p u on a 1D line, D^p u taking the end values
+    g[p] = (at a, at b), p = 1..P (g has P + 1 rows; row 0 is not used)."""
+    u = _f64(u)
+    gg = _f64(np.asarray(g, dtype=np.float64).reshape(P + 1, 2))
+    out = np.empty_like(u)
+    _load().orc_F_bc(_dp(u), _dp(out), u.size, float(nu), int(quad), int(P), float(beta), _dp(gg))
+    return out
+
+
+def bc_values(s, P: int) -> np.ndarray:
+    """Boundary values g[p, side] of D^p u, p = 0..P (row 0: the data itself),
+    from s[side, j] = (d_tt / (c alpha)^2)^j u_side, j = 0..P."""
+    ss = _f64(np.asarray(s, dtype=np.float64).reshape(2, P + 1))
+    g = np.empty((P + 1, 2))
+    _load().orc_bc_values(_dp(ss), int(P), _dp(g))
+    return g
+
+
+def run_bc(u0, nsteps: int, nu, P: int, beta: float, gam, quad: int = 2) -> np.ndarray:
+    """u^nsteps of a 1D line with Dirichlet data: gam[k, side, j] =
+    (d_tt / (c alpha)^2)^j u_side(t_k), k = 0..nsteps, j = 0..P."""
+    u0 = _f64(u0)
+    g = _f64(np.asarray(gam, dtype=np.float64).reshape(int(nsteps) + 1, 2, P + 1))
+    out = np.empty_like(u0)
+    _load().orc_run_bc(_dp(u0), _dp(out), int(nsteps), u0.size, float(nu), int(quad), int(P), float(beta), _dp(g))
+    return out
 
 
 def grid_spacing(n: int, length: float, bc) -> float:

@@ -110,8 +110,10 @@ static double sdiff(const double *v, long sv, long n, int bc, long c)
     return vat(v, sv, n, bc, c + 1) - 2.0 * vat(v, sv, n, bc, c) + vat(v, sv, n, bc, c - 1);
 }
 
-void orc_linv_line(const double *v, long sv, double *w, long sw, long n,
-                   double nu, int quad, int bc)
+/* gL, gR (Dirichlet): the values that D v = v - w must take at the end
+ * nodes (zero for homogeneous data, see orc_linv_line_bc). */
+static void linv_line_impl(const double *v, long sv, double *w, long sw, long n,
+                           double nu, int quad, int bc, double gL, double gR)
 {
     double c4[4];
     orc_weights(nu, quad, c4);
@@ -160,16 +162,22 @@ void orc_linv_line(const double *v, long sv, double *w, long sw, long n,
         A = IL[N] / (1.0 - mu);
         B = IR[0] / (1.0 - mu);
     } else {
-        /* w(a) = v(a), w(b) = v(b):
-         *   A + mu B = v_0 - I^R_0,   mu A + B = v_N - I^L_N  */
-        double r0 = vat(v, sv, n, bc, 0) - IR[0];
-        double r1 = vat(v, sv, n, bc, N) - IL[N];
+        /* w(a) = v(a) - gL, w(b) = v(b) - gR:
+         *   A + mu B = v_0 - gL - I^R_0,   mu A + B = v_N - gR - I^L_N  */
+        double r0 = vat(v, sv, n, bc, 0) - gL - IR[0];
+        double r1 = vat(v, sv, n, bc, N) - gR - IL[N];
         A = (r0 - mu * r1) / (1.0 - mu * mu);
         B = (r1 - mu * r0) / (1.0 - mu * mu);
     }
     for (long j = 0; j < n; ++j)
         w[j * sw] = IL[j] + IR[j] + A * pow(d, (double)j) + B * pow(d, (double)(N - j));
     free(JL); free(JR); free(IL); free(IR);
+}
+
+void orc_linv_line(const double *v, long sv, double *w, long sw, long n,
+                   double nu, int quad, int bc)
+{
+    linv_line_impl(v, sv, w, sw, n, nu, quad, bc, 0.0, 0.0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -602,6 +610,92 @@ void orc_adjoint(const double *tgrad, long nsteps, int nrec, const long *rec, do
 }
 
 /* Threads OpenMP would use (1 when built without OpenMP). */
+/* ------------------------------------------------------------------------ */
+/* Time-dependent Dirichlet data on a 1D line (Sec. 3.2): u(a, t) = u_L(t),  */
+/* u(b, t) = u_R(t).  As an operator on smooth functions D = 1 - L^{-1} =     */
+/* -(d_xx/alpha^2)(1 - d_xx/alpha^2)^{-1}, and in the limit x -> a the wave   */
+/* equation turns d_xx^j into (d_tt/c^2)^j.  With s_j = (d_tt/(c alpha)^2)^j  */
+/* u_L(t) (the data), the boundary value of D^p u expanded to the scheme's   */
+/* order is g_p = (-1)^p sum_{j=p}^{P} C(j-1, p-1) s_j (and the same at b).   */
+/* One application of D that must return e with e(a) = gL, e(b) = gR        */
+/* corrects L^{-1} to w(a) = v(a) - gL, w(b) = v(b) - gR.                      */
+/* ------------------------------------------------------------------------ */
+void orc_linv_line_bc(const double *v, double *w, long n, double nu, int quad, double gL, double gR)
+{
+    linv_line_impl(v, 1, w, 1, n, nu, quad, ORC_DIRICHLET, gL, gR);
+}
+
+void orc_D_line_bc(const double *v, double *e, long n, double nu, int quad, double gL, double gR)
+{
+    double *w = malloc(sizeof(double) * (size_t)n);
+    orc_linv_line_bc(v, w, n, nu, quad, gL, gR);
+    for (long j = 0; j < n; ++j) e[j] = v[j] - w[j];
+    free(w);
+}
+
+/* F = sum_{p=1}^P A_p D^p u with D^p u = D(D^{p-1} u) taking the boundary
+ * values g[2p] (at a) and g[2p + 1] (at b); g[0], g[1] (the data itself)
+ * are not used here. */
+void orc_F_bc(const double *u, double *F, long n, double nu, int quad, int P, double beta, const double *g)
+{
+    double A[16];
+    orc_Ap(P, beta, A);
+    double *v = malloc(sizeof(double) * (size_t)n), *e = malloc(sizeof(double) * (size_t)n);
+    memcpy(v, u, sizeof(double) * (size_t)n);
+    memset(F, 0, sizeof(double) * (size_t)n);
+    for (int p = 1; p <= P; ++p) {
+        orc_D_line_bc(v, e, n, nu, quad, g[2 * p], g[2 * p + 1]);
+        for (long j = 0; j < n; ++j) F[j] += A[p - 1] * e[j];
+        memcpy(v, e, sizeof(double) * (size_t)n);
+    }
+    free(v); free(e);
+}
+
+/* boundary values g[2p + side] (p = 1..P) of D^p u from the data
+ * s[side * (P + 1) + j] = (d_tt / (c alpha)^2)^j u_side, j = 0..P */
+void orc_bc_values(const double *s, int P, double *g)
+{
+    for (int side = 0; side < 2; ++side) {
+        g[side] = s[side * (P + 1)];
+        for (int p = 1; p <= P; ++p) {
+            double acc = 0.0;
+            for (int j = p; j <= P; ++j) acc += binom(j - 1, p - 1) * s[side * (P + 1) + j];
+            g[2 * p + side] = ((p & 1) ? -1.0 : 1.0) * acc;
+        }
+    }
+}
+
+/* u^0 -> u^{nsteps} with the data gam[(k * 2 + side) * (P + 1) + j] =
+ * (d_tt / (c alpha)^2)^j u_side(t_k), k = 0 .. nsteps: u^1 = u^0 + F[u^0]/2
+ * (zero initial velocity) and u^{k+1} = 2 u^k - u^{k-1} + F[u^k], F with
+ * the boundary values from the data at t_k; the end nodes of every new
+ * level take the data (j = 0) at its time. */
+void orc_run_bc(const double *u0, double *u_out, long nsteps, long n, double nu, int quad, int P, double beta,
+                const double *gam)
+{
+    const int Q = P + 1;
+    double *g = malloc(sizeof(double) * 2 * (size_t)Q);
+    double *up = malloc(sizeof(double) * (size_t)n), *uc = malloc(sizeof(double) * (size_t)n);
+    double *un = malloc(sizeof(double) * (size_t)n), *F = malloc(sizeof(double) * (size_t)n);
+    for (long k = 0; k < nsteps; ++k) {
+        orc_bc_values(gam + k * 2 * Q, P, g);
+        if (k == 0) {
+            memcpy(uc, u0, sizeof(double) * (size_t)n);
+            orc_F_bc(uc, F, n, nu, quad, P, beta, g);
+            for (long j = 0; j < n; ++j) un[j] = uc[j] + 0.5 * F[j];
+        } else {
+            orc_F_bc(uc, F, n, nu, quad, P, beta, g);
+            for (long j = 0; j < n; ++j) un[j] = 2.0 * uc[j] - up[j] + F[j];
+        }
+        un[0] = gam[((k + 1) * 2 + 0) * Q];
+        un[n - 1] = gam[((k + 1) * 2 + 1) * Q];
+        memcpy(up, uc, sizeof(double) * (size_t)n);
+        memcpy(uc, un, sizeof(double) * (size_t)n);
+    }
+    memcpy(u_out, nsteps > 0 ? uc : u0, sizeof(double) * (size_t)n);
+    free(g); free(up); free(uc); free(un); free(F);
+}
+
 #ifdef _OPENMP
 #include <omp.h>
 int orc_num_threads(void) { return omp_get_max_threads(); }
