@@ -189,6 +189,22 @@ mol_status mol_adjoint(mol_handle h, int nrec, const int64_t *rec, int64_t nstep
                        void *stream);
 
 /* Wait for the handle's work on the stream; reports device-side errors. */
+/* Time-dependent Dirichlet data on a 1D Dirichlet handle (Sec. 3.2):
+ * u(a, t) = u_L(t), u(b, t) = u_R(t), zero initial velocity.  u0: device,
+ * float64, the n points of u^0 (its end values the data at t_0); u_out:
+ * device, float64, receives u^nsteps.  data: HOST, float64,
+ * [nsteps + 1][2][P + 1]: data[k][side][m] = (d^2/dt^2 / c^2)^m u_side(t_k),
+ * t_k = k dt, side 0 = a, 1 = b (m = 0: the value itself).  The boundary
+ * values of D^p u come from the operator identity D = -(d_xx/alpha^2)
+ * (1 - d_xx/alpha^2)^{-1} with d_xx -> d_tt/c^2 at the ends (the inverse
+ * Lax-Wendroff limit of Sec. 3.2), expanded to the scheme's order:
+ * (-1)^p sum_{j=p..P} C(j-1, p-1) alpha^{-2j} data[k][side][j].  The end
+ * nodes of every new level take the data.  Runs on the shared-memory line
+ * kernels, one launch per step (no graph).  Errors: MOL_EINVAL for another
+ * grid or NULL pointers. */
+mol_status mol_solve_dirichlet(mol_handle h, const double *u0, int64_t nsteps, const double *data, double *u_out,
+                               void *stream);
+
 mol_status mol_sync(mol_handle h, void *stream);
 
 /* Number of kernel launches this handle issued so far (all entry points). */

@@ -232,7 +232,16 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
     if (st != MOL_OK) return st;
     int rpt = 0, S = 0, K = 0;
     cudaError_t e;
-    if (pr.mode == 2 || pr.mode == 3) {
+    const bool bcd = hp != nullptr && hp->bcd;      // boundary data: the shared-memory kernels carry it
+    if (bcd) {
+        PassGeom G = geom_of(h, axis);
+        G.W = choose_W(h, axis, true);
+        G.wshift = ilog2(G.W);
+        AxisDev A = h->ax[axis];
+        A.ls = line_stride(A.ms, G.W, h->tbytes);
+        G.dps = pass_smem_bytes(true, h->tbytes, G.W, A.ls, A.n, 1) <= h->smem_optin ? 1 : 0;
+        e = launch_horner(h->tbytes, h->bc, axis == 0, A, G, *hp, s);
+    } else if (pr.mode == 2 || pr.mode == 3) {
         // the transposed passes of the adjoint step (register kernels only;
         // single_adjoint checks that the grid has both plans)
         int W = 0;
@@ -1114,6 +1123,67 @@ mol_status mol_adjoint(mol_handle h, int nrec, const int64_t *rec, int64_t nstep
     if (st != MOL_OK) return st;
     if ((st = mol_batch_adjoint(b, nrec, rec, nsteps, tgrad, grad, stream)) != MOL_OK) h->err = mol_batch_last_error(b);
     return st;
+}
+
+mol_status mol_solve_dirichlet(mol_handle h, const double *u0, int64_t nsteps, const double *data, double *u_out,
+                               void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (h->ndim != 1 || h->bc != MOL_BC_DIRICHLET)
+        return fail(h, MOL_EINVAL, "time-dependent Dirichlet data is for 1D Dirichlet handles");
+    if (nsteps < 1) return fail(h, MOL_EINVAL, "nsteps must be >= 1");
+    if (!data) return fail(h, MOL_EINVAL, "data is NULL");
+    mol_status st;
+    if ((st = check_ptr(h, u0, "u0")) != MOL_OK || (st = check_ptr(h, u_out, "u_out")) != MOL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int P = h->P, Q = P + 1;
+    // binomials C(j - 1, p - 1) of the boundary values of D^p u (molt.h)
+    double binom[MAXP][MAXP] = {};
+    for (int j = 0; j < MAXP; ++j) {
+        binom[j][0] = 1.0;
+        for (int k = 1; k <= j; ++k) binom[j][k] = binom[j - 1][k - 1] + (k <= j - 1 ? binom[j - 1][k] : 0.0);
+    }
+    const double a2 = h->alpha * h->alpha;              // the data carries (d_tt / c^2)^m
+    const double *cu = h->xtpl.cu[0];
+    int ip = 0, ic = 1, in = 2;
+    if ((st = load_level(h, u0, h->lev[ic], s)) != MOL_OK) return st;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        // boundary values of D^p u at t_k from the data's time derivatives
+        double g[2][MAXP] = {};
+        for (int side = 0; side < 2; ++side) {
+            const double *dk = data + (k * 2 + side) * Q;
+            for (int p = 1; p <= P; ++p) {
+                double acc = 0.0, sc = 1.0;
+                for (int j = 1; j <= P; ++j) {
+                    sc /= a2;
+                    if (j >= p) acc += binom[j - 1][p - 1] * dk[j] * sc;
+                }
+                g[side][p] = (p & 1) ? -acc : acc;
+            }
+        }
+        HornerParams hp = h->xtpl;
+        const bool first = k == 0;
+        hp.ea = 1.0 + (first ? 0.0 : 1.0);
+        hp.eb = first ? 0.0 : -1.0;
+        hp.ec = first ? 0.5 : 1.0;
+        hp.u_hi = h->lev[ic].hi; hp.u_lo = h->lev[ic].lo;
+        hp.up_hi = h->lev[ip].hi; hp.up_lo = h->lev[ip].lo;
+        hp.un_hi = h->lev[in].hi; hp.un_lo = h->lev[in].lo;
+        hp.bcd = 1;
+        // the D application of Horner step t returns sum_{p >= t} cu_p D^{p-t+1} u
+        for (int t = 1; t <= P; ++t)
+            for (int side = 0; side < 2; ++side) {
+                double acc = 0.0;
+                for (int p = t; p <= P; ++p) acc += cu[p] * g[side][p - t + 1];
+                (side == 0 ? hp.bgL : hp.bgR)[t] = acc;
+            }
+        hp.bnew[0] = data[((k + 1) * 2 + 0) * Q];
+        hp.bnew[1] = data[((k + 1) * 2 + 1) * Q];
+        const double *b = h->coef_dev;
+        if ((st = run_horner(h, 0, hp, b + h->off_xc, b + h->off_xu, s)) != MOL_OK) return st;
+        const int t0 = ip; ip = ic; ic = in; in = t0;
+    }
+    return store_level(h, h->lev[ic], u_out, s);
 }
 
 mol_status mol_sync(mol_handle h, void *stream)

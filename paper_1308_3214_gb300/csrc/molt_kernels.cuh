@@ -109,6 +109,12 @@ struct HornerParams {
     const void *u_hi, *u_lo;
     const void *up_hi, *up_lo;
     void *un_hi, *un_lo;
+    // Time-dependent Dirichlet data (1D, Sec. 3.2; bcd = 1): the end values of
+    // the D application of Horner step t (bgL[t], bgR[t]) and of the new level
+    // (bnew); zero data is the homogeneous operator
+    int bcd;
+    double bgL[MAXP], bgR[MAXP];
+    double bnew[2];
 };
 
 // Coefficients and fields of a pass program.
@@ -227,9 +233,11 @@ __device__ __forceinline__ int spos(int j, const AxisDev &A)
 //   MODE 2: s = second difference of buf + cu * r, r from rbuf.
 // dp points to the d^j table (shared memory, or global memory for long lines).
 // ---------------------------------------------------------------------------
+// gL, gR (Dirichlet): the values D must take at the end nodes (zero for
+// homogeneous data)
 template <class T, int MODE, int BC>
 __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
-                        const T *__restrict__ dp, int lane)
+                        const T *__restrict__ dp, int lane, T gL = 0, T gR = 0)
 {
     const int n = A.n, m = A.m, ms = A.ms;
     const T d = A.cd<T>(), c1 = A.cc1<T>(), c2 = A.cc2<T>();
@@ -342,8 +350,8 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
     if (BC == BC_DIRICHLET) {
         const T ylast = __shfl_sync(0xffffffffu, y, Ld);  // y_{n-1} = zero-inflow e_{n-1}
         const T mu = A.cmu<T>(), inv = A.cinv<T>();
-        Acoef = (mu * ylast - e00) * inv;               // A'
-        Z = (mu * e00 - ylast) * inv;                   // B'
+        Acoef = (mu * ylast - e00) * inv + (gL - mu * gR) * inv;   // A': e_0 = gL
+        Z = (mu * e00 - ylast) * inv + (gR - mu * gL) * inv;       // B': e_{n-1} = gR
     } else {
         Z = d * e00 * A.cinv<T>();                         // d * e_n, e_n = e_0 over all images
     }
@@ -520,6 +528,12 @@ template <> struct LevelIO<float> {
         ((float *)p.un_hi)[i] = nh;
         ((float *)p.un_lo)[i] = nl;
     }
+    __device__ static void set(const HornerParams &p, int64_t i, double v)
+    {
+        const float h = __double2float_rn(v);
+        ((float *)p.un_hi)[i] = h;
+        ((float *)p.un_lo)[i] = __double2float_rn(v - (double)h);
+    }
 };
 template <> struct LevelIO<double> {
     __device__ static void combine(const HornerParams &p, int64_t i, double F)
@@ -528,6 +542,7 @@ template <> struct LevelIO<double> {
         if (p.eb != 0.0) v += p.eb * ((const double *)p.up_hi)[i];
         ((double *)p.un_hi)[i] = v;
     }
+    __device__ static void set(const HornerParams &p, int64_t i, double v) { ((double *)p.un_hi)[i] = v; }
 };
 
 template <class T, int BC, bool CONTIG>
@@ -576,13 +591,16 @@ __global__ void __launch_bounds__(512) k_horner(AxisDev A, PassGeom G, HornerPar
                     lines[si] = acc;
                 } else if (prm.epi == 0) {
                     reinterpret_cast<T *>(prm.out[o])[gi] = acc;
+                } else if (BC == BC_DIRICHLET && prm.bcd && (j == 0 || j == n - 1)) {
+                    LevelIO<T>::set(prm, gi, prm.bnew[j == 0 ? 0 : 1]);    // the data at the end nodes
                 } else {
                     LevelIO<T>::combine(prm, gi, acc);
                 }
             });
             __syncthreads();
             if (t > 0 && warp < nl)
-                sweep_D<T, 2, BC>(mine, rmine, (T)prm.cu[o][t], A, dp, lane);
+                sweep_D<T, 2, BC>(mine, rmine, (T)prm.cu[o][t], A, dp, lane, prm.bcd ? (T)prm.bgL[t] : (T)0,
+                                  prm.bcd ? (T)prm.bgR[t] : (T)0);
             __syncthreads();
         }
     }

@@ -33,7 +33,7 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
            "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times", "mol_batch_apply_FT",
            "mol_batch_traces", "mol_batch_adjoint", "mol_batch_update", "mol_autotune", "mol_get_tuning", "mol_set_tuning",
-           "mol_batch_autotune", "mol_batch_get_tuning", "mol_batch_set_tuning", "mol_apply_FT", "mol_traces", "mol_adjoint"]
+           "mol_batch_autotune", "mol_batch_get_tuning", "mol_batch_set_tuning", "mol_solve_dirichlet", "mol_apply_FT", "mol_traces", "mol_adjoint"]
 
 
 class MolError(RuntimeError):
@@ -117,6 +117,7 @@ def load_library(path: Path | None = None):
     lib.mol_adjoint.argtypes = [vp, I, ctypes.POINTER(i64), i64, vp, vp, vp]
     lib.mol_batch_get_tuning.argtypes = [vp, ctypes.POINTER(I), dp]
     lib.mol_batch_set_tuning.argtypes = [vp, I, I, I]
+    lib.mol_solve_dirichlet.argtypes = [vp, vp, i64, dp, vp, vp]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
@@ -290,6 +291,17 @@ class Solver:
         self._check(self.lib.mol_adjoint(self.h, rec.size, rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                          int(tg.shape[0]), ctypes.c_void_p(tg.data_ptr()),
                                          ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def solve_dirichlet(self, u0, nsteps: int, data, stream=None):
+        """u^nsteps of a 1D Dirichlet problem with time-dependent end data:
+        data[k, side, m] = (d_tt / c^2)^m u_side(t_k), k = 0..nsteps,
+        m = 0..P (host float64), zero initial velocity."""
+        d = np.ascontiguousarray(np.asarray(data, dtype=np.float64).reshape(int(nsteps) + 1, 2, self.P + 1))
+        out = self.empty()
+        self._check(self.lib.mol_solve_dirichlet(self.h, self._field(u0, "u0"), int(nsteps),
+                                                 d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 self._field(out, "u_out"), ctypes.c_void_p(_stream_ptr(stream))))
         return out
 
     def autotune(self, stream=None) -> dict:
