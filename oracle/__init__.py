@@ -73,6 +73,8 @@ def _load():
         lib.orc_F_bc.argtypes = [dp, dp, L, D, I, I, D, dp]
         lib.orc_run_bc.argtypes = [dp, dp, L, L, D, I, I, D, dp]
         lib.orc_bc_values.argtypes = [dp, I, dp]
+        lib.orc_C.argtypes = [dp, dp, I, lp, dp, I, I]
+        lib.orc_run_source.argtypes = [dp, dp, L, I, lp, dp, I, I, I, D, D, dp, dp]
         lib.orc_num_threads.restype = I
         _lib = lib
     return _lib
@@ -257,6 +259,32 @@ def run(uprev, ucur, nsteps: int, nu, P: int, beta: float, bc="dirichlet", quad:
     _load().orc_run(_dp(up), _dp(uc), int(nsteps), nd, shp, _dp(nus), int(quad), _bc(bc),
                     int(P), float(beta))
     return up, uc
+
+
+def C(v, nu, bc="dirichlet", quad: int = 2) -> np.ndarray:
+    """C[v] (eq. C_def_ADI): sum_g (prod_{a != g} L_a^{-1}) D_g v."""
+    v = _f64(v)
+    out = np.empty_like(v)
+    nd, shp = _shape(v)
+    _load().orc_C(_dp(v), _dp(out), nd, shp, _dp(_nu_arr(nu, nd)), int(quad), _bc(bc))
+    return out
+
+
+def run_source(u0, nsteps: int, nu, P: int, beta: float, sc: float, g, f, bc="dirichlet",
+               quad: int = 2) -> np.ndarray:
+    """u^nsteps with the source S = g(x) f(t) (Sec. 4.1; P = 1 or 2), zero
+    initial velocity; sc = (c dt)^2, f[k] = f(t_k), k = 0..nsteps."""
+    u0, g = _f64(u0), _f64(g)
+    ff = _f64(np.asarray(f, dtype=np.float64).reshape(-1))
+    if ff.size < int(nsteps) + 1:
+        raise ValueError("f needs nsteps + 1 values")
+    out = np.empty_like(u0)
+    nd, shp = _shape(u0)
+    st = _load().orc_run_source(_dp(u0), _dp(out), int(nsteps), nd, shp, _dp(_nu_arr(nu, nd)), int(quad), _bc(bc),
+                                int(P), float(beta), float(sc), _dp(g), _dp(ff))
+    if st != 0:
+        raise ValueError("source terms are defined for P = 1 and 2")
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -610,6 +610,55 @@ void orc_adjoint(const double *tgrad, long nsteps, int nrec, const long *rec, do
 }
 
 /* Threads OpenMP would use (1 when built without OpenMP). */
+/* C[v] (eq. C_def_ADI): sum over the axes g of D_g v smoothed by L^{-1} of
+ * the other axes */
+void orc_C(const double *v, double *out, int ndim, const long *shape, const double *nu, int quad, int bc)
+{
+    orc_ctx c = {ndim, shape, nu, quad, bc, total_size(ndim, shape), 0, 0};
+    applyC(&c, v, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Source terms (Sec. 4.1): (1/c^2) u_tt = lap u + S, S(x, t) = g(x) f(t).    */
+/* P = 1: u^{n+1} - 2u^n + u^{n-1} = F[u^n] + (c dt)^2 S^n.                    */
+/* P = 2 (the fourth-order scheme of Sec. 4.1): the Taylor terms of S up to   */
+/* dt^4, S_tt by the three-level difference and dt^4 c^4 lap S / 12 by        */
+/* -beta^2 (c dt)^2 C[S] / 12 (lap ~ -alpha^2 C):                             */
+/*   + (c dt)^2 (S^{n+1} + 10 S^n + S^{n-1}) / 12 - beta^2 (c dt)^2 C[S^n]/12. */
+/* Start (zero initial velocity): u^1 = u^0 + F[u^0]/2 + (the same source     */
+/* terms at n = 0)/2 with f(t_{-1}) = f(t_1) (exact for a source even about   */
+/* t_0).  sc = (c dt)^2; f[k] = f(t_k), k = 0..nsteps.  Returns 0, or 1 for   */
+/* P > 2 (the paper gives no higher-order source terms).                      */
+/* ------------------------------------------------------------------------ */
+int orc_run_source(const double *u0, double *u_out, long nsteps, int ndim, const long *shape, const double *nu,
+                   int quad, int bc, int P, double beta, double sc, const double *g, const double *f)
+{
+    if (P < 1 || P > 2) return 1;
+    long T = total_size(ndim, shape);
+    double *Cg = malloc(sizeof(double) * (size_t)T), *F = malloc(sizeof(double) * (size_t)T);
+    double *up = malloc(sizeof(double) * (size_t)T), *uc = malloc(sizeof(double) * (size_t)T);
+    double *un = malloc(sizeof(double) * (size_t)T);
+    orc_C(g, Cg, ndim, shape, nu, quad, bc);
+    memcpy(uc, u0, sizeof(double) * (size_t)T);
+    for (long k = 0; k < nsteps; ++k) {
+        const double fm = k > 0 ? f[k - 1] : f[1], f0 = f[k], fp = f[k + 1];
+        double a, b;
+        if (P == 1) { a = sc * f0; b = 0.0; }
+        else { a = sc * (fp + 10.0 * f0 + fm) / 12.0; b = -beta * beta * sc * f0 / 12.0; }
+        orc_F(uc, F, ndim, shape, nu, quad, bc, P, beta, NULL);
+        if (k == 0) {
+            for (long i = 0; i < T; ++i) un[i] = uc[i] + 0.5 * (F[i] + a * g[i] + b * Cg[i]);
+        } else {
+            for (long i = 0; i < T; ++i) un[i] = 2.0 * uc[i] - up[i] + F[i] + a * g[i] + b * Cg[i];
+        }
+        memcpy(up, uc, sizeof(double) * (size_t)T);
+        memcpy(uc, un, sizeof(double) * (size_t)T);
+    }
+    memcpy(u_out, uc, sizeof(double) * (size_t)T);
+    free(Cg); free(F); free(up); free(uc); free(un);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Time-dependent Dirichlet data on a 1D line (Sec. 3.2): u(a, t) = u_L(t),  */
 /* u(b, t) = u_R(t).  As an operator on smooth functions D = 1 - L^{-1} =     */
