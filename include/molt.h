@@ -205,6 +205,20 @@ mol_status mol_adjoint(mol_handle h, int nrec, const int64_t *rec, int64_t nstep
 mol_status mol_solve_dirichlet(mol_handle h, const double *u0, int64_t nsteps, const double *data, double *u_out,
                                void *stream);
 
+/* Source terms (Sec. 4.1): (1/c^2) u_tt = lap u + S with a separable source
+ * S(x, t) = g(x) f(t), zero initial velocity, P = 1 or 2.  P = 1 adds
+ * (c dt)^2 S^n to each step; P = 2 is the fourth-order scheme,
+ * + (c dt)^2 (S^{n+1} + 10 S^n + S^{n-1}) / 12 - beta^2 (c dt)^2 C[S^n] / 12,
+ * C the ADI operator of eq. C_def_ADI (the printed scale of the C[S] term is
+ * dimensionally inconsistent; this is the one the Taylor expansion gives).
+ * The start takes f(t_{-1}) = f(t_1).  u0, g: device float64 fields of the
+ * grid; u_out: device float64, receives u^nsteps; f: HOST float64,
+ * nsteps + 1 values f(t_k) = f(k dt).  Direct launches (no graph); C[g] is
+ * formed once per call with mol_apply_D (it uses the handle's levels).
+ * MOL_EINVAL for P > 2 or NULL pointers. */
+mol_status mol_solve_source(mol_handle h, const double *u0, int64_t nsteps, const double *g, const double *f,
+                            double *u_out, void *stream);
+
 mol_status mol_sync(mol_handle h, void *stream);
 
 /* Number of kernel launches this handle issued so far (all entry points). */

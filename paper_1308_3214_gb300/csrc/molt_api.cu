@@ -66,6 +66,8 @@ struct mol_ctx {
     mol_batch adj = nullptr;                   // one-problem batch for the adjoint entry points
     long long *irec = nullptr;                 // receivers (molt_recv.cuh layout), capacity irec_cap
     int nrec = 0, irec_cap = 0, nnode = 0;
+    double *srcbuf = nullptr;                  // mol_solve_source: C[g] and two temporaries (3 N)
+    float *src32 = nullptr;                    //   float32 copies of g and C[g] (mixed, 2 N)
     bool timing = false;                       // per-pass events (benchmarks)
     std::vector<cudaEvent_t> ev_pool;          // reusable events
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (axis, (start, stop))
@@ -1181,6 +1183,114 @@ mol_status mol_solve_dirichlet(mol_handle h, const double *u0, int64_t nsteps, c
         hp.bnew[1] = data[((k + 1) * 2 + 1) * Q];
         const double *b = h->coef_dev;
         if ((st = run_horner(h, 0, hp, b + h->off_xc, b + h->off_xu, s)) != MOL_OK) return st;
+        const int t0 = ip; ip = ic; ic = in; in = t0;
+    }
+    return store_level(h, h->lev[ic], u_out, s);
+}
+
+}  // extern "C"
+
+namespace {
+
+// out = a x + b y (float64; the one-time C[g] of mol_solve_source)
+__global__ void k_axpby(double *out, const double *x, const double *y, double a, double b, int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_to_f32(const double *x, float *y, int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
+// level += a g + b Cg: float32 pairs (the increment in float32, compensated
+// into the pair) or float64
+__global__ void k_add_source_pair(float *hi, float *lo, const float *g, const float *cg, float a, float b, int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float inc = __fadd_rn(__fmul_rn(a, g[i]), __fmul_rn(b, cg[i]));
+        float sh, se, nh, nl;
+        two_sum(hi[i], inc, sh, se);
+        two_sum(sh, __fadd_rn(lo[i], se), nh, nl);
+        hi[i] = nh;
+        lo[i] = nl;
+    }
+}
+
+__global__ void k_add_source_f64(double *x, const double *g, const double *cg, double a, double b, int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += a * g[i] + b * cg[i];
+}
+
+int grid_for(const mol_ctx *h) { return (int)std::min<int64_t>((h->N + 255) / 256, 8 * (int64_t)h->num_sms); }
+
+}  // namespace
+
+extern "C" {
+
+// Grids whose stepping runs on a one-problem batch (ragged 2D Dirichlet) run
+// this on the handle's own shared-memory kernels.
+mol_status mol_solve_source(mol_handle h, const double *u0, int64_t nsteps, const double *g, const double *f,
+                            double *u_out, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (h->P < 1 || h->P > 2) return fail(h, MOL_EINVAL, "source terms are defined for P = 1 and 2");
+    if (nsteps < 1) return fail(h, MOL_EINVAL, "nsteps must be >= 1");
+    if (!f) return fail(h, MOL_EINVAL, "f is NULL");
+    mol_status st;
+    if ((st = check_ptr(h, u0, "u0")) != MOL_OK || (st = check_ptr(h, g, "g")) != MOL_OK ||
+        (st = check_ptr(h, u_out, "u_out")) != MOL_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->N;
+    const int nb = grid_for(h);
+    if (!h->srcbuf && (st = dev_alloc(h, (void **)&h->srcbuf, sizeof(double) * 3 * (size_t)N)) != MOL_OK) return st;
+    if (h->prec == MOL_MIXED && !h->src32 &&
+        (st = dev_alloc(h, (void **)&h->src32, sizeof(float) * 2 * (size_t)N)) != MOL_OK)
+        return st;
+    double *Cg = h->srcbuf, *t1 = Cg + N, *t2 = t1 + N;
+    // C[g] = sum_gamma (prod_{a != gamma} (1 - D_a)) D_gamma g (eq. C_def_ADI, L^{-1} = 1 - D)
+    CK(cudaMemsetAsync(Cg, 0, sizeof(double) * (size_t)N, s), "clear");
+    for (int gam = 0; gam < h->ndim; ++gam) {
+        if ((st = mol_apply_D(h, g, t1, gam, 1, stream)) != MOL_OK) return st;
+        for (int a = 0; a < h->ndim; ++a) {
+            if (a == gam) continue;
+            if ((st = mol_apply_D(h, t1, t2, a, 1, stream)) != MOL_OK) return st;
+            k_axpby<<<nb, 256, 0, s>>>(t1, t1, t2, 1.0, -1.0, N);
+        }
+        k_axpby<<<nb, 256, 0, s>>>(Cg, Cg, t1, 1.0, 1.0, N);
+    }
+    CK(cudaGetLastError(), "source setup");
+    float *g32 = h->src32, *cg32 = g32 ? g32 + N : nullptr;
+    if (h->prec == MOL_MIXED) {
+        k_to_f32<<<nb, 256, 0, s>>>(g, g32, N);
+        k_to_f32<<<nb, 256, 0, s>>>(Cg, cg32, N);
+        CK(cudaGetLastError(), "source setup");
+    }
+    const double sc = h->c * h->c * h->dt * h->dt, b2 = h->beta * h->beta;
+    int ip = 0, ic = 1, in = 2;
+    if ((st = load_level(h, u0, h->lev[ic], s)) != MOL_OK) return st;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        const double fm = k > 0 ? f[k - 1] : f[1], f0 = f[k], fp = f[k + 1];
+        double a = h->P == 1 ? sc * f0 : sc * (fp + 10.0 * f0 + fm) / 12.0;
+        double b = h->P == 1 ? 0.0 : -b2 * sc * f0 / 12.0;
+        if (k == 0) {
+            if ((st = run_update(h, h->lev[ic], h->lev[ic], h->lev[in], 1.0, 0.0, 0.5, s)) != MOL_OK) return st;
+            a *= 0.5;
+            b *= 0.5;
+        } else if ((st = run_update(h, h->lev[ic], h->lev[ip], h->lev[in], 2.0, -1.0, 1.0, s)) != MOL_OK) {
+            return st;
+        }
+        if (h->prec == MOL_MIXED)
+            k_add_source_pair<<<nb, 256, 0, s>>>((float *)h->lev[in].hi, (float *)h->lev[in].lo, g32, cg32, (float)a,
+                                                 (float)b, N);
+        else
+            k_add_source_f64<<<nb, 256, 0, s>>>((double *)h->lev[in].hi, g, Cg, a, b, N);
+        CK(cudaGetLastError(), "source term");
+        h->launches++;
         const int t0 = ip; ip = ic; ic = in; in = t0;
     }
     return store_level(h, h->lev[ic], u_out, s);

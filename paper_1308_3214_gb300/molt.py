@@ -33,7 +33,7 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
            "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times", "mol_batch_apply_FT",
            "mol_batch_traces", "mol_batch_adjoint", "mol_batch_update", "mol_autotune", "mol_get_tuning", "mol_set_tuning",
-           "mol_batch_autotune", "mol_batch_get_tuning", "mol_batch_set_tuning", "mol_solve_dirichlet", "mol_apply_FT", "mol_traces", "mol_adjoint"]
+           "mol_batch_autotune", "mol_batch_get_tuning", "mol_batch_set_tuning", "mol_solve_dirichlet", "mol_solve_source", "mol_apply_FT", "mol_traces", "mol_adjoint"]
 
 
 class MolError(RuntimeError):
@@ -118,6 +118,7 @@ def load_library(path: Path | None = None):
     lib.mol_batch_get_tuning.argtypes = [vp, ctypes.POINTER(I), dp]
     lib.mol_batch_set_tuning.argtypes = [vp, I, I, I]
     lib.mol_solve_dirichlet.argtypes = [vp, vp, i64, dp, vp, vp]
+    lib.mol_solve_source.argtypes = [vp, vp, i64, vp, dp, vp, vp]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
@@ -302,6 +303,18 @@ class Solver:
         self._check(self.lib.mol_solve_dirichlet(self.h, self._field(u0, "u0"), int(nsteps),
                                                  d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                  self._field(out, "u_out"), ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def solve_source(self, u0, nsteps: int, g, f, stream=None):
+        """u^nsteps with the source S = g(x) f(t) (P = 1 or 2), zero initial
+        velocity: g a CUDA float64 field, f[k] = f(k dt), k = 0..nsteps."""
+        ff = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))
+        if ff.size < int(nsteps) + 1:
+            raise ValueError("f needs nsteps + 1 values")
+        out = self.empty()
+        self._check(self.lib.mol_solve_source(self.h, self._field(u0, "u0"), int(nsteps), self._field(g, "g"),
+                                              ff.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              self._field(out, "u_out"), ctypes.c_void_p(_stream_ptr(stream))))
         return out
 
     def autotune(self, stream=None) -> dict:
