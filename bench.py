@@ -71,6 +71,14 @@ def workload_spec(name: str) -> dict:
     if name == "batch":
         return dict(name="batch-512-dirichlet-n64..1024-P1..3-cfl0.5..4-gaussian", count=512, seed=1004,
                     steps_in_config=200, bc="dirichlet")
+    if name == "source":
+        n = 2048
+        return dict(name="source-2d-dirichlet-2048x2048-P2-cfl2-pointsource", shape=(n, n), P=2, cfl=2.0,
+                    bc="dirichlet", lo=(-1.0, -1.0), hi=(1.0, 1.0), h=2.0 / (n - 1))
+    if name == "dirichlet1d":
+        n = 10001
+        return dict(name="dirichlet1d-10001-P3-cfl2-standing-wave-data", shape=(n,), P=3, cfl=2.0, bc="dirichlet",
+                    lo=(0.0,), hi=(1.0,), h=1.0 / (n - 1))
     if name == "1d":
         n = 256
         L = 2 * math.pi
@@ -284,7 +292,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batch", "adjoint"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batch", "adjoint", "source", "dirichlet1d"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -308,6 +316,9 @@ def main():
         return
     if args.workload == "adjoint":
         main_adjoint(args, spec)
+        return
+    if args.workload in ("source", "dirichlet1d"):
+        main_extension(args, spec)
         return
     if args.impl == "reference":
         run_reference(args, spec)
@@ -696,6 +707,117 @@ def adjoint_problem(spec, seed_offset: int = 0):
     rec = np.array([iy * n + ix for iy, ix in workloads.receivers_2d(n, spec["nrec"], seed=1005 + seed_offset)],
                    dtype=np.int64)
     return u0, u_true, rec
+
+
+def extension_inputs(spec, nsteps: int):
+    """Inputs of the workloads of the NEXT rows: the point source of the
+    paper's Sec. 4.3 example on a 2048^2 grid (discrete delta at the centre,
+    f(t) = sin(4 pi t)(1 - exp(-(t/0.2)^2))), or the 1D standing wave
+    cos(3 pi x) cos(3 pi t) with its time-dependent end data."""
+    n = spec["shape"][0]
+    dt = spec["cfl"] * spec["h"]
+    t = dt * np.arange(nsteps + 1)
+    if spec["name"].startswith("source"):
+        g = np.zeros(spec["shape"])
+        g[n // 2, n // 2] = 1.0 / spec["h"] ** 2
+        f = np.sin(4 * np.pi * t) * (1.0 - np.exp(-(t / 0.2) ** 2))
+        return np.zeros(spec["shape"]), dt, g, f
+    P = spec["P"]
+    d = np.empty((nsteps + 1, 2, P + 1))
+    for m in range(P + 1):
+        fm = (-(3 * np.pi) ** 2) ** m * np.cos(3 * np.pi * t)
+        d[:, 0, m] = fm
+        d[:, 1, m] = np.cos(3 * np.pi) * fm
+    return np.cos(3 * np.pi * np.linspace(0.0, 1.0, n)), dt, None, d
+
+
+def main_extension(args, spec):
+    """The rows beyond the hot path (source terms, time-dependent Dirichlet
+    data): one solve call of K steps, inputs resident; per-pass events of a
+    second call; the oracle on a bounded sample."""
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    import torch
+    from paper_1308_3214_gb300 import molt
+    torch.cuda.set_device(0)
+    K = args.steps
+    u0h, dt, gh, data = extension_inputs(spec, K)
+    s = molt.Solver(spec["shape"], dt=dt, P=spec["P"], bc=spec["bc"], prec=args.prec, lo=list(spec["lo"]),
+                    hi=list(spec["hi"]))
+    u0 = torch.from_numpy(u0h).cuda()
+    g = torch.from_numpy(gh).cuda() if gh is not None else None
+
+    def call(nsteps):
+        if g is not None:
+            return s.solve_source(u0, nsteps, g, data[:nsteps + 1])
+        return s.solve_dirichlet(u0, nsteps, data[:nsteps + 1])
+
+    call(args.warmup)
+    torch.cuda.synchronize()
+    l0 = s.launches
+    bus = torch.cuda.get_device_properties(0).pci_bus_id
+    sampler = ClockSampler(bus).start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = call(K)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = s.launches - l0
+    s.set_pass_timing(True)
+    call(min(K, 100))
+    passes = s.pass_times()
+    s.set_pass_timing(False)
+    N = int(np.prod(spec["shape"]))
+    bpp = bytes_per_point(spec, args.prec)
+    dom = max(passes, key=lambda a: passes[a][0])
+    dom_ms = passes[dom][0] / passes[dom][1]
+    peak, peak_kind = read_peak()
+    achieved = bpp[dom] * N / (dom_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": N * K / (ms * 1e-3), "unit": METRIC, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": spec["name"], "shape": list(spec["shape"]), "P": spec["P"], "cfl": spec["cfl"],
+                       "prec": args.prec, "step": "one call of K steps (solve_source / solve_dirichlet, direct "
+                                                  "launches: per-step scalars)", "parallelism": "1 rank"},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                         "passes": {f"axis{a}": {"ms_per_launch": passes[a][0] / passes[a][1],
+                                                  "alg_bytes_per_point": bpp[a]} for a in passes}},
+            "clocks": clocks, "finite": bool(torch.isfinite(out).all())}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        beta = oracle.beta_max(spec["P"])
+        if gh is not None:
+            m = 257                                    # a bounded sample: the same problem on 257^2
+            hs = 2.0 / (m - 1)
+            dts = spec["cfl"] * hs
+            ks = 10
+            gs = np.zeros((m, m))
+            gs[m // 2, m // 2] = 1.0 / hs ** 2
+            ts = dts * np.arange(ks + 1)
+            fs = np.sin(4 * np.pi * ts) * (1.0 - np.exp(-(ts / 0.2) ** 2))
+            t0 = time.perf_counter()
+            oracle.run_source(np.zeros((m, m)), ks, beta / dts * hs, spec["P"], beta, dts ** 2, gs, fs)
+            el = time.perf_counter() - t0
+            sample = f"{ks} oracle steps of the point-source problem on {m}x{m} ({el:.1f} s)"
+            rate = m * m * ks / el
+        else:
+            ks = 20
+            gam = data[:ks + 1] / (beta / dt) ** (2 * np.arange(spec["P"] + 1))
+            t0 = time.perf_counter()
+            oracle.run_bc(u0h, ks, beta / dt * spec["h"], spec["P"], beta, gam)
+            el = time.perf_counter() - t0
+            sample = f"{ks} oracle steps of the same problem ({el:.2f} s)"
+            rate = N * ks / el
+        line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": sample}
+    s.close()
+    print(json.dumps(line), flush=True)
 
 
 def main_adjoint(args, spec):
