@@ -123,6 +123,33 @@ int pick_rpt_y(int n, int mode = 0)
 
 bool long_row(int nx) { return nx > 16 * 32; }
 
+// Order of the y-pass work list.  CTA b of G takes the items at b, b + G,
+// b + 2G, ... of the list.  The items are sorted by decreasing cost (the
+// serial segment length times the P + 1 phases of a column group: loads and
+// P sweeps) and dealt out in a snake: round k gives its G items to CTAs
+// 0..G-1 when k is even and G-1..0 when k is odd, so every CTA gets one item of
+// each cost class.  Items are independent, so the order changes no result.
+// A partial last round is dealt straight (CTAs 0..rem-1).
+std::vector<int2> order_y_items(const std::vector<BatchProb> &hp, const std::vector<int2> &it, int G)
+{
+    const int n = (int)it.size();
+    std::vector<int> cost(n), idx(n);
+    for (int i = 0; i < n; ++i) {
+        const BatchProb &pb = hp[it[i].x];
+        cost[i] = pick_rpt_y(pb.ay.n) * (pb.P + 1);
+        idx[i] = i;
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<int2> out(n);
+    for (int i = 0; i < n; ++i) {
+        const int k = i / G, j = i % G;
+        const bool full_round = (int64_t)(k + 1) * G <= n;
+        const int slot = (full_round && (k & 1)) ? G - 1 - j : j;
+        out[(int64_t)k * G + slot] = it[idx[i]];
+    }
+    return out;
+}
+
 // the problem table to the device, with its float32 copies refreshed
 cudaError_t upload_table(mol_batch_ctx *b)
 {
@@ -157,7 +184,7 @@ void set_y_segments(mol_batch_ctx *b)
 bool set_x_shape(mol_batch_ctx *b, int L, int W)
 {
     const int ctas = L == 0 ? 2 : 1;
-    const size_t bytes = batch_x_smem((size_t)b->tbytes, W, b->nbuf);
+    const size_t bytes = batch_x_smem((size_t)b->tbytes, W, b->nbuf, L == 1);
     if (W < 1 || W > 8 || bytes > (size_t)b->smem_blk || ctas * (bytes + 1024) > (size_t)b->smem_sm) return false;
     b->xW[L] = W;
     b->xsmem[L] = bytes;
@@ -556,6 +583,7 @@ mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, c
             for (int r = 0; r < pb.ay.n; ++r) rp[pb.row0 + r] = i;
             for (int c0 = 0; c0 < pb.ax.n; c0 += 32) it.push_back(make_int2(i, c0));
         }
+        it = order_y_items(b->hp, it, std::min(b->nitems_y, b->num_sms));
         for (int i = 0; i <= nprob; ++i) uo[i] = b->uoff[i];
         if ((st = balloc(b, (void **)&b->probs, sizeof(BatchProb) * nprob)) != MOL_OK) goto bad;
         if ((st = balloc(b, (void **)&b->row_prob, sizeof(int) * rp.size())) != MOL_OK) goto bad;

@@ -78,10 +78,12 @@ struct BatchPass {
     ProgParams pr;           // levels, ea / eb / ec, g[k] planes (internal layout)
 };
 
-template <class T>
+// field buffers of the one-warp x kernel: LARGE rows take 32-point segments,
+// the others at most 16 (a buffer holds a row in the padded segment layout)
+template <class T, bool LARGE>
 struct BatchX {
     static constexpr int VN = VecOf<T>::n;
-    static constexpr int RMAX = 32;                  // largest x segment
+    static constexpr int RMAX = LARGE ? 32 : 16;     // largest x segment
     static constexpr int LINE = 32 * (RMAX + VN);    // elements of one field buffer
 };
 
@@ -120,8 +122,8 @@ __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams 
     constexpr int VN = VecOf<T>::n;
     constexpr int NVL = RPT / VN;                    // vectors per lane of a full segment row
     constexpr bool pair = sizeof(T) == 4;
-    constexpr int LB = BatchX<T>::LINE;
-    static_assert(RPT % VN == 0 && RPT >= 4 && RPT <= BatchX<T>::RMAX, "segment length");
+    constexpr int LB = BatchX<T, (RPT > 16)>::LINE;
+    static_assert(RPT % VN == 0 && RPT >= 4 && RPT <= BatchX<T, true>::RMAX, "segment length");
     const AxisDev &A = pb.ax;
     const int n = A.n;
     const int64_t base = pb.off + (int64_t)row * pb.pitch;
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(256, LARGE ? 1 : 2) k_batch_x(BatchPass bp, in
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, W = blockDim.x >> 5;
     BatchProb *pbs = reinterpret_cast<BatchProb *>(smem_raw) + warp;
-    T *B = reinterpret_cast<T *>(smem_raw + (size_t)W * sizeof(BatchProb)) + (size_t)warp * nbuf * BatchX<T>::LINE;
+    T *B = reinterpret_cast<T *>(smem_raw + (size_t)W * sizeof(BatchProb)) + (size_t)warp * nbuf * BatchX<T, LARGE>::LINE;
     int cur = -1;
     for (int r = bp.row_begin + blockIdx.x * W + warp; r < bp.nitems; r += gridDim.x * W) {
         const int p = __ldg(bp.row_prob + r);
@@ -485,9 +487,10 @@ __device__ __forceinline__ void batch_row_split(const BatchProb &pb, const ProgP
 }
 
 // Rows [row_begin, nitems) of the list, one CTA of W warps per row (rows of
-// 32 (W-1) RPT < n <= 32 W RPT points)
+// 32 (W-1) RPT < n <= 32 W RPT points).  Float: ten CTAs per SM (96
+// registers, no spills; 20 warps in flight against 16 at eight CTAs).
 template <class T, int RPT, int W, bool ADJ>
-__global__ void __launch_bounds__(32 * W, sizeof(T) == 4 ? 8 : 4) k_batch_xs(BatchPass bp)
+__global__ void __launch_bounds__(32 * W, sizeof(T) == 4 ? 10 : 4) k_batch_xs(BatchPass bp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BatchProb &pb = *reinterpret_cast<BatchProb *>(smem_raw);
@@ -717,6 +720,26 @@ __device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams
     }
 }
 
+// L2 prefetch of the level rows that column group `item` reads (32 columns of
+// every row; both planes of a pair).  The internal layout makes each row's
+// piece 16-byte aligned: off is a multiple of 64, the pitch of 4, the first
+// column of 32; the piece is rounded up to whole 4-element vectors, which stay
+// inside the padded row.
+template <class T>
+__device__ __forceinline__ void prefetch_cols(const BatchPass &bp, int2 item)
+{
+    const BatchProb *q = bp.probs + item.x;
+    const int ny = __ldg(&q->ay.n), nx = __ldg(&q->ax.n), pitch = __ldg(&q->pitch);
+    const long long off = __ldg(&q->off);
+    const int w = min(32, nx - item.y);
+    const unsigned bytes = (unsigned)(((w + 3) & ~3) * (int)sizeof(T));
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+        const int64_t o = off + (int64_t)j * pitch + item.y;
+        prefetch_l2(reinterpret_cast<const T *>(bp.pr.u_hi) + o, bytes);
+        if (sizeof(T) == 4) prefetch_l2(reinterpret_cast<const T *>(bp.pr.u_lo) + o, bytes);
+    }
+}
+
 // ADJ: powers of D_y^T (the adjoint step) instead of D_y
 template <class T, bool ADJ>
 __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
@@ -742,6 +765,8 @@ __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
         const int2 item = bp.items[it];
         __syncthreads();                               // the previous item is done with pbs and the slots
         if (threadIdx.x < 32) warp_copy(&pbs, bp.probs + item.x, threadIdx.x);
+        // the CTA's next column group streams into L2 while this one sweeps
+        if (it + (int)gridDim.x < bp.nitems) prefetch_cols<T>(bp, bp.items[it + gridDim.x]);
         __syncthreads();
         switch (pbs.rpt_y) {
         case 4: batch_cols<T, 4, ADJ>(pbs, bp.pr, item.y, c, YL); break;
@@ -754,9 +779,10 @@ __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
 }
 
 inline size_t batch_y_smem(size_t tsize) { return strided_slot_bytes(kBatchYWarps, tsize) + 32 * tsize; }
-inline size_t batch_x_smem(size_t tsize, int W, int nbuf)
+inline size_t batch_x_smem(size_t tsize, int W, int nbuf, bool large)
 {
-    return (size_t)W * (sizeof(BatchProb) + (size_t)nbuf * 32 * (BatchX<float>::RMAX + 16 / tsize) * tsize);
+    const size_t rmax = large ? BatchX<float, true>::RMAX : BatchX<float, false>::RMAX;
+    return (size_t)W * (sizeof(BatchProb) + (size_t)nbuf * 32 * (rmax + 16 / tsize) * tsize);
 }
 // k_batch_xs: the problem, the exchange slots and nbuf fields of one row
 // (32 W segments of RPT + 16 / tsize elements)

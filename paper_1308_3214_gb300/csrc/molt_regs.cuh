@@ -1168,8 +1168,11 @@ __host__ __device__ constexpr size_t row_slots_bytes() { return (sizeof(RowSlots
 // ADJ (Dirichlet): the transposed Horner pass of the adjoint step,
 // F^T = sum_t (D_x^T)^t (f_t0 u + sum_k f_tk g_k) with g_k = (D_y^T)^{k+1} u;
 // u itself (pairs summed) takes the place of its second difference.
+// Four warps per row: seven CTAs per SM (72 registers, 31 KB of shared
+// memory each at RPT = 16 and three fields), so that the 2048 rows of a
+// 2048^2 grid run in two waves over the 152 SMs instead of two and a quarter.
 template <int BC, int RPT, int NB, int W, bool ADJ = false>
-__global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 6 : 4)) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr)
+__global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr)
 {
     static_assert(RPT % 4 == 0 && RPT >= 8, "segment length");
     static_assert(!ADJ || BC == BC_DIRICHLET, "the transposed pass is for Dirichlet rows");
@@ -1389,12 +1392,31 @@ __device__ __forceinline__ void strided_cta_consts(StridedCtx<T> &c)
 // overlap instead of adding up.
 constexpr int kXchKMax = 8, kXchSMax = 16;
 
-// causal exchange: y at a-1 (zero inflow) and the line's y_{n-1}
+// causal exchange: y at a-1 (zero inflow) and the line's y_{n-1}.  A line
+// inside one CTA (K = 1) needs one barrier: every warp combines the totals
+// itself, in the order the cluster path's warp 0 uses (the same values).
 template <class T, int RPT>
 __device__ __forceinline__ void strided_causal(const StridedCtx<T> &c, T E, T &yin, T &ytot)
 {
     c.sl.E[c.w * 32 + c.lane] = E;
     __syncthreads();
+    if (c.K == 1) {
+        T acc = 0, all = 0;
+#pragma unroll
+        for (int v0 = 0; v0 < kXchSMax; v0 += 4) {
+            T ev[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ev[i] = v0 + i < c.S ? c.sl.E[(v0 + i) * 32 + c.lane] : (T)0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (v0 + i < c.w) acc = c.dR * acc + ev[i];
+                if (v0 + i < c.S) all = ((v0 + i) < c.Gd ? c.dR : (T)1) * all + ev[i];
+            }
+        }
+        yin = acc;
+        ytot = all;
+        return;
+    }
     if (c.w == 0) {
         T acc = 0;
 #pragma unroll
@@ -1433,12 +1455,31 @@ __device__ __forceinline__ void strided_causal(const StridedCtx<T> &c, T E, T &y
     ytot = tot;
 }
 
-// anti-causal exchange: zero-inflow e just past the segment, and e_0
+// anti-causal exchange: zero-inflow e just past the segment, and e_0 (one
+// barrier for a line inside one CTA, as above)
 template <class T, int RPT>
 __device__ __forceinline__ void strided_anticausal(const StridedCtx<T> &c, T ER, T &eout, T &e0)
 {
     c.sl.ER[c.w * 32 + c.lane] = ER;
     __syncthreads();
+    if (c.K == 1) {
+        T acc = 0, all = 0;
+#pragma unroll
+        for (int v0 = kXchSMax - 1; v0 >= 0; v0 -= 4) {
+            T ev[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ev[i] = v0 - i < c.S ? c.sl.ER[(v0 - i) * 32 + c.lane] : (T)0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const T f = (v0 - i) < c.Gd ? c.dR : (T)1;
+                if (v0 - i > c.w && v0 - i < c.S) acc = f * acc + ev[i];
+                if (v0 - i < c.S) all = f * all + ev[i];
+            }
+        }
+        eout = acc;
+        e0 = all;
+        return;
+    }
     if (c.w == 0) {
         T acc = 0;
 #pragma unroll
