@@ -75,6 +75,11 @@ def _load():
         lib.orc_bc_values.argtypes = [dp, I, dp]
         lib.orc_C.argtypes = [dp, dp, I, lp, dp, I, I]
         lib.orc_run_source.argtypes = [dp, dp, L, I, lp, dp, I, I, I, D, D, dp, dp]
+        lib.orc_linv_obj.argtypes = [dp, L, dp, L, L, D, D, D, D]
+        geo = [L, L, D, D, lp, lp, dp, dp, lp, lp, dp, dp]
+        lib.orc_linv_axis_embed.argtypes = [dp, dp, I] + geo + [D]
+        lib.orc_F_embed.argtypes = [dp, dp] + geo + [D, I, D]
+        lib.orc_run_embed.argtypes = [dp, dp, L] + geo + [D, I, D]
         lib.orc_num_threads.restype = I
         _lib = lib
     return _lib
@@ -339,3 +344,64 @@ def run_bc(u0, nsteps: int, nu, P: int, beta: float, gam, quad: int = 2) -> np.n
 def grid_spacing(n: int, length: float, bc) -> float:
     """Dirichlet axes include both end nodes; periodic axes hold n points."""
     return length / (n - 1) if _bc(bc) == DIRICHLET else length / n
+
+
+# --------------------------------------------------------------------------
+# Embedded boundaries (Sec. 4.3): line objects and the 2D scheme on a domain
+# cut out of a grid.  ``g`` is a ``workloads.EmbeddedGrid``; fields have shape
+# (ny, nx) and vanish outside the domain.
+# --------------------------------------------------------------------------
+def linv_obj(v, h: float, da: float, db: float, alpha: float) -> np.ndarray:
+    """L^{-1} on one line object: m interior values at spacing h, boundary
+    points (zero data) at distance da before the first and db after the last."""
+    v = _f64(v)
+    w = np.empty_like(v)
+    _load().orc_linv_obj(_dp(v), 1, _dp(w), 1, v.size, h, da, db, alpha)
+    return w
+
+
+def _geo(g):
+    li = lambda a: np.ascontiguousarray(a, dtype=np.int64)
+    ld = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    keep = [li(g.r0), li(g.r1), ld(g.ra), ld(g.rb), li(g.c0), li(g.c1), ld(g.ca), ld(g.cb)]
+    lp = ctypes.POINTER(ctypes.c_long)
+    ptr = [a.ctypes.data_as(lp) if a.dtype == np.int64 else _dp(a) for a in keep]
+    return keep, [g.nx, g.ny, g.hx, g.hy] + ptr
+
+
+def _embedded_field(u, g):
+    u = _f64(u)
+    if u.shape != (g.ny, g.nx):
+        raise ValueError("field shape must be (ny, nx) of the grid")
+    return np.ascontiguousarray(np.where(g.mask, u, 0.0))
+
+
+def linv_axis_embed(v, axis: int, g, alpha: float) -> np.ndarray:
+    v = _embedded_field(v, g)
+    w = np.empty_like(v)
+    keep, args = _geo(g)
+    _load().orc_linv_axis_embed(_dp(v), _dp(w), axis, *args, alpha)
+    return w
+
+
+def D_axis_embed(v, axis: int, g, alpha: float) -> np.ndarray:
+    v = _embedded_field(v, g)
+    return v - linv_axis_embed(v, axis, g, alpha)
+
+
+def F_embed(u, g, alpha: float, P: int, beta: float) -> np.ndarray:
+    """F[u] of eq. (Full_2D) on the embedded domain (terms in Table 3 order)."""
+    u = _embedded_field(u, g)
+    F = np.empty_like(u)
+    keep, args = _geo(g)
+    _load().orc_F_embed(_dp(u), _dp(F), *args, alpha, P, beta)
+    return F
+
+
+def run_embed(u0, nsteps: int, g, alpha: float, P: int, beta: float) -> np.ndarray:
+    """u^{nsteps} from u^0 with zero initial velocity (start u^1 = u^0 + F/2)."""
+    u0 = _embedded_field(u0, g)
+    out = np.empty_like(u0)
+    keep, args = _geo(g)
+    _load().orc_run_embed(_dp(u0), _dp(out), nsteps, *args, alpha, P, beta)
+    return out

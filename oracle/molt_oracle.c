@@ -181,6 +181,117 @@ void orc_linv_line(const double *v, long sv, double *w, long sw, long n,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Embedded boundaries (Sec. 4.3): L^{-1} on a line object.  The line is the */
+/* part of a grid line inside the domain: m interior grid nodes x_1..x_m     */
+/* with spacing h, and two boundary points, x_0 = a at distance da before    */
+/* x_1 and x_{m+1} = b at distance db after x_m (0 < da, db), where the      */
+/* homogeneous Dirichlet data are zero.  The quadrature is the rule of the   */
+/* rectangular line written for arbitrary node positions: J^L on the cell    */
+/* [x_{j-1}, x_j] integrates the quadratic through x_{j-1}, x_j, x_{j+1}     */
+/* (x_{j-2}, x_{j-1}, x_j in the last cell), J^R on [x_j, x_{j+1}] the one   */
+/* through x_{j-1}, x_j, x_{j+1} (x_j, x_{j+1}, x_{j+2} in the first cell), */
+/* each exactly against the kernel; the recurrences decay by e^{-alpha dx}  */
+/* over each cell; A, B make w vanish at a and b.  With da = db = h this is  */
+/* orc_linv_line on the m + 2 nodes of a rectangular Dirichlet line.         */
+/* ------------------------------------------------------------------------ */
+
+/* out[i] = (alpha/2) int_0^len e^{-alpha s} l_i(s) ds for the Lagrange basis
+ * l_i of three nodes at coordinates ts[] (s = distance from the destination
+ * node into the cell), from int_0^len s^k e^{-alpha s} ds = M_k(alpha len) /
+ * alpha^{k+1}: l_i(s) = (s^2 - (ta + tb) s + ta tb) / ((t_i - ta)(t_i - tb)).
+ * The moments of short cells come from their power series (moment()), which
+ * is what keeps boundary points arbitrarily close to a grid node usable. */
+static void basis_weights(const double ts[3], double len, double alpha, double out[3])
+{
+    double nu = alpha * len;
+    double m0 = moment(0, nu) / alpha;
+    double m1 = moment(1, nu) / (alpha * alpha);
+    double m2 = moment(2, nu) / (alpha * alpha * alpha);
+    for (int i = 0; i < 3; ++i) {
+        double ta = ts[(i + 1) % 3], tb = ts[(i + 2) % 3];
+        double den = (ts[i] - ta) * (ts[i] - tb);
+        out[i] = 0.5 * alpha * (m2 - (ta + tb) * m1 + ta * tb * m0) / den;
+    }
+}
+
+void orc_linv_obj(const double *v, long sv, double *w, long sw, long m, double h, double da, double db,
+                  double alpha)
+{
+    long N = m + 1;                                   /* cells between the nodes 0..N */
+    double *x = malloc(sizeof(double) * (size_t)(N + 1));
+    double *u = malloc(sizeof(double) * (size_t)(N + 1));
+    double *JL = calloc((size_t)(N + 1), sizeof(double));
+    double *JR = calloc((size_t)(N + 1), sizeof(double));
+    double *IL = calloc((size_t)(N + 1), sizeof(double));
+    double *IR = calloc((size_t)(N + 1), sizeof(double));
+    x[0] = 0.0;
+    u[0] = 0.0;
+    for (long j = 1; j <= m; ++j) { x[j] = da + (double)(j - 1) * h; u[j] = v[(j - 1) * sv]; }
+    x[N] = x[m] + db;
+    u[N] = 0.0;
+    for (long j = 1; j <= N; ++j) {                   /* cell [x_{j-1}, x_j], destination x_j */
+        long c0 = (j + 1 <= N) ? j - 1 : j - 2;
+        double ts[3], wt[3];
+        for (int i = 0; i < 3; ++i) ts[i] = x[j] - x[c0 + i];
+        basis_weights(ts, x[j] - x[j - 1], alpha, wt);
+        JL[j] = wt[0] * u[c0] + wt[1] * u[c0 + 1] + wt[2] * u[c0 + 2];
+    }
+    for (long j = 0; j < N; ++j) {                    /* cell [x_j, x_{j+1}], destination x_j */
+        long c0 = (j - 1 >= 0) ? j - 1 : j;
+        double ts[3], wt[3];
+        for (int i = 0; i < 3; ++i) ts[i] = x[c0 + i] - x[j];
+        basis_weights(ts, x[j + 1] - x[j], alpha, wt);
+        JR[j] = wt[0] * u[c0] + wt[1] * u[c0 + 1] + wt[2] * u[c0 + 2];
+    }
+    IL[0] = 0.0;
+    for (long j = 1; j <= N; ++j) IL[j] = exp(-alpha * (x[j] - x[j - 1])) * IL[j - 1] + JL[j];
+    IR[N] = 0.0;
+    for (long j = N - 1; j >= 0; --j) IR[j] = exp(-alpha * (x[j + 1] - x[j])) * IR[j + 1] + JR[j];
+    double mu = exp(-alpha * (x[N] - x[0]));
+    double r0 = u[0] - IL[0] - IR[0];                 /* w(a) = 0 */
+    double r1 = u[N] - IL[N] - IR[N];                 /* w(b) = 0 */
+    double A = (r0 - mu * r1) / (1.0 - mu * mu);
+    double B = (r1 - mu * r0) / (1.0 - mu * mu);
+    for (long j = 1; j <= m; ++j)
+        w[(j - 1) * sw] = IL[j] + IR[j] + A * exp(-alpha * (x[j] - x[0])) + B * exp(-alpha * (x[N] - x[j]));
+    free(x); free(u); free(JL); free(JR); free(IL); free(IR);
+}
+
+/* A 2D domain embedded in an nx x ny grid (x fastest): row j holds the
+ * interior nodes i = r0[j] .. r1[j] (none when r0[j] > r1[j]) with the
+ * boundary points at distances ra[j] before r0[j] and rb[j] after r1[j];
+ * column i likewise holds the rows c0[i] .. c1[i] with gaps ca[i], cb[i].
+ * Nodes outside the domain hold zero. */
+typedef struct {
+    long nx, ny;
+    double hx, hy;
+    const long *r0, *r1, *c0, *c1;
+    const double *ra, *rb, *ca, *cb;
+} orc_geom;
+
+/* L_gamma^{-1} on every line object of one axis */
+static void linv_axis_obj(const orc_geom *g, const double *v, double *w, int axis, double alpha)
+{
+    long T = g->nx * g->ny;
+    memset(w, 0, sizeof(double) * (size_t)T);
+    if (axis == 0) {
+        #pragma omp parallel for schedule(static)
+        for (long j = 0; j < g->ny; ++j) {
+            if (g->r0[j] > g->r1[j]) continue;
+            long b = j * g->nx + g->r0[j];
+            orc_linv_obj(v + b, 1, w + b, 1, g->r1[j] - g->r0[j] + 1, g->hx, g->ra[j], g->rb[j], alpha);
+        }
+    } else {
+        #pragma omp parallel for schedule(static)
+        for (long i = 0; i < g->nx; ++i) {
+            if (g->c0[i] > g->c1[i]) continue;
+            long b = g->c0[i] * g->nx + i;
+            orc_linv_obj(v + b, g->nx, w + b, g->nx, g->c1[i] - g->c0[i] + 1, g->hy, g->ca[i], g->cb[i], alpha);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* (L^{-1})^T on one line: the statements of orc_linv_line transposed and     */
 /* executed in reverse order (each read x = v_j becomes vbar_j += xbar, each  */
 /* recurrence runs backwards).  Used by the adjoint of the time stepping; the */
@@ -405,16 +516,25 @@ typedef struct {
     int ndim; const long *shape; const double *nu; int quad; int bc; long total;
     long napplied;            /* number of applications of C or D (Table 3) */
     int transpose;            /* 1: every per-axis operator replaced by its transpose */
+    const orc_geom *geom;     /* 2D embedded domain (line objects), else NULL */
+    double alpha;             /* alpha of the line objects */
 } orc_ctx;
 
 static void Linv(orc_ctx *c, const double *v, double *w, int axis)
 {
-    if (c->transpose) orc_linv_axis_T(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
+    if (c->geom) linv_axis_obj(c->geom, v, w, axis, c->alpha);
+    else if (c->transpose) orc_linv_axis_T(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
     else orc_linv_axis(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
 }
 
 static void Dgam(orc_ctx *c, const double *v, double *w, int axis)
 {
+    if (c->geom) {
+        /* D_gamma = 1 - L_gamma^{-1} on the interior nodes (zero outside) */
+        linv_axis_obj(c->geom, v, w, axis, c->alpha);
+        for (long i = 0; i < c->total; ++i) w[i] = v[i] - w[i];
+        return;
+    }
     if (c->transpose) orc_D_axis_T(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
     else orc_D_axis(v, w, c->ndim, c->shape, axis, c->nu[axis], c->quad, c->bc);
 }
@@ -478,10 +598,8 @@ static void applyD(orc_ctx *c, const double *v, double *out)
  * p-1 by v_p = D[v_{p-1}] and v_k = C[v_k] (k < p); stage p costs p
  * applications.  *nops (if given) receives the number of applications.
  */
-static void F_impl(const double *u, double *F, int ndim, const long *shape, const double *nu, int quad,
-                   int bc, int P, double beta, long *nops, int transpose)
+static void F_core(orc_ctx c, const double *u, double *F, int P, double beta, long *nops)
 {
-    orc_ctx c = {ndim, shape, nu, quad, bc, total_size(ndim, shape), 0, transpose};
     long T = c.total;
     double **v = calloc((size_t)P + 1, sizeof(double *));
     for (int k = 1; k <= P; ++k) v[k] = malloc(sizeof(double) * (size_t)T);
@@ -505,6 +623,13 @@ static void F_impl(const double *u, double *F, int ndim, const long *shape, cons
     if (nops) *nops = c.napplied;
     for (int k = 1; k <= P; ++k) free(v[k]);
     free(v); free(tmp);
+}
+
+static void F_impl(const double *u, double *F, int ndim, const long *shape, const double *nu, int quad,
+                   int bc, int P, double beta, long *nops, int transpose)
+{
+    orc_ctx c = {ndim, shape, nu, quad, bc, total_size(ndim, shape), 0, transpose, NULL, 0.0};
+    F_core(c, u, F, P, beta, nops);
 }
 
 void orc_F(const double *u, double *F, int ndim, const long *shape,
@@ -614,7 +739,7 @@ void orc_adjoint(const double *tgrad, long nsteps, int nrec, const long *rec, do
  * the other axes */
 void orc_C(const double *v, double *out, int ndim, const long *shape, const double *nu, int quad, int bc)
 {
-    orc_ctx c = {ndim, shape, nu, quad, bc, total_size(ndim, shape), 0, 0};
+    orc_ctx c = {ndim, shape, nu, quad, bc, total_size(ndim, shape), 0, 0, NULL, 0.0};
     applyC(&c, v, out);
 }
 
@@ -743,6 +868,62 @@ void orc_run_bc(const double *u0, double *u_out, long nsteps, long n, double nu,
     }
     memcpy(u_out, nsteps > 0 ? uc : u0, sizeof(double) * (size_t)n);
     free(g); free(up); free(uc); free(un); free(F);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The 2D scheme of eq. (Full_2D) on an embedded domain (Sec. 4.3): C and D   */
+/* of eqs. (C_def_ADI), (D_def_ADI) built from the line-object operators,     */
+/* the terms in the order of Table 3 (on a domain that is not a rectangle the */
+/* x and y operators do not commute, so this order is part of the scheme).   */
+/* Geometry arrays as in orc_geom; alpha = beta / (c dt).                     */
+/* ------------------------------------------------------------------------ */
+static orc_geom make_geom(long nx, long ny, double hx, double hy, const long *r0, const long *r1,
+                          const double *ra, const double *rb, const long *c0, const long *c1,
+                          const double *ca, const double *cb)
+{
+    orc_geom g = {nx, ny, hx, hy, r0, r1, c0, c1, ra, rb, ca, cb};
+    return g;
+}
+
+void orc_linv_axis_embed(const double *v, double *w, int axis, long nx, long ny, double hx, double hy,
+                         const long *r0, const long *r1, const double *ra, const double *rb, const long *c0,
+                         const long *c1, const double *ca, const double *cb, double alpha)
+{
+    orc_geom g = make_geom(nx, ny, hx, hy, r0, r1, ra, rb, c0, c1, ca, cb);
+    linv_axis_obj(&g, v, w, axis, alpha);
+}
+
+void orc_F_embed(const double *u, double *F, long nx, long ny, double hx, double hy, const long *r0,
+                 const long *r1, const double *ra, const double *rb, const long *c0, const long *c1,
+                 const double *ca, const double *cb, double alpha, int P, double beta)
+{
+    orc_geom g = make_geom(nx, ny, hx, hy, r0, r1, ra, rb, c0, c1, ca, cb);
+    long shape[2] = {nx, ny};
+    double nu[2] = {alpha * hx, alpha * hy};
+    orc_ctx c = {2, shape, nu, 2, ORC_DIRICHLET, nx * ny, 0, 0, &g, alpha};
+    F_core(c, u, F, P, beta, NULL);
+}
+
+/* u^1 = u^0 + F[u^0]/2, then nsteps - 1 steps u^{n+1} = 2u^n - u^{n-1} + F[u^n];
+ * u_out = u^{nsteps} (u^0 when nsteps = 0) */
+void orc_run_embed(const double *u0, double *u_out, long nsteps, long nx, long ny, double hx, double hy,
+                   const long *r0, const long *r1, const double *ra, const double *rb, const long *c0,
+                   const long *c1, const double *ca, const double *cb, double alpha, int P, double beta)
+{
+    long T = nx * ny;
+    double *up = malloc(sizeof(double) * (size_t)T), *uc = malloc(sizeof(double) * (size_t)T);
+    double *F = malloc(sizeof(double) * (size_t)T);
+    memcpy(uc, u0, sizeof(double) * (size_t)T);
+    for (long k = 0; k < nsteps; ++k) {
+        orc_F_embed(uc, F, nx, ny, hx, hy, r0, r1, ra, rb, c0, c1, ca, cb, alpha, P, beta);
+        for (long i = 0; i < T; ++i) {
+            double un = (k == 0) ? uc[i] + 0.5 * F[i] : 2.0 * uc[i] - up[i] + F[i];
+            up[i] = uc[i];
+            uc[i] = un;
+        }
+    }
+    memcpy(u_out, uc, sizeof(double) * (size_t)T);
+    free(up); free(uc); free(F);
 }
 
 #ifdef _OPENMP

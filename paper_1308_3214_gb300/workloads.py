@@ -120,3 +120,124 @@ def receivers_2d(n: int = 1024, count: int = 64, seed: int = 1005) -> np.ndarray
 
 def random_field(shape, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).normal(size=shape)
+
+
+# --------------------------------------------------------------------------
+# Embedded domains (Sec. 4.3): a convex domain q(x, y) < 0 cut out of a grid
+# --------------------------------------------------------------------------
+@dataclass
+class EmbeddedGrid:
+    """A convex domain embedded in an nx x ny grid of spacing (hx, hy).
+
+    Node (i, j) sits at (x0 + i hx, y0 + j hy).  Row j holds the interior
+    nodes r0[j]..r1[j] (empty when r0 > r1), with the boundary points at
+    distances ra[j] before r0[j] and rb[j] after r1[j]; column i holds the
+    rows c0[i]..c1[i] with gaps ca[i], cb[i].  ``mask`` marks the interior
+    nodes, shape (ny, nx).
+    """
+    nx: int
+    ny: int
+    x0: float
+    y0: float
+    hx: float
+    hy: float
+    r0: np.ndarray
+    r1: np.ndarray
+    ra: np.ndarray
+    rb: np.ndarray
+    c0: np.ndarray
+    c1: np.ndarray
+    ca: np.ndarray
+    cb: np.ndarray
+    mask: np.ndarray
+
+    def coords(self):
+        x = self.x0 + self.hx * np.arange(self.nx)
+        y = self.y0 + self.hy * np.arange(self.ny)
+        return x, y
+
+
+def _roots(a: float, b: float, c: float):
+    """Real roots of a t^2 + b t + c (a > 0), or None."""
+    disc = b * b - 4.0 * a * c
+    if disc <= 0.0:
+        return None
+    s = np.sqrt(disc)
+    return (-b - s) / (2.0 * a), (-b + s) / (2.0 * a)
+
+
+def conic_grid(n: int, lo: float, hi: float, q) -> EmbeddedGrid:
+    """The domain q(x, y) = a x^2 + 2 b x y + c y^2 + d x + e y + f < 0 (a, c > 0,
+    ac > b^2: an ellipse) on the n x n grid of [lo, hi]^2 including both ends.
+
+    q = (a, b, c, d, e, f).  A node is interior when it lies strictly inside
+    both the row's and the column's chord, more than 1e-9 of a spacing from
+    either end; the gaps are the distances from the first and last interior
+    node to the chord's ends.
+    """
+    a, b, c, d, e, f = (float(t) for t in q)
+    h = (hi - lo) / (n - 1)
+    if a * lo * lo + 2 * b * lo * lo + c * lo * lo + d * lo + e * lo + f < 0 or any(
+            r is not None and (r[0] <= lo or r[1] >= hi)
+            for r in (_roots(a, 2 * b * y + d, c * y * y + e * y + f) for y in (lo, hi))):
+        raise ValueError("the domain must lie inside the grid")
+    xs = lo + h * np.arange(n)
+    eps = 1e-9 * h
+    rows = [_roots(a, 2 * b * y + d, c * y * y + e * y + f) for y in xs]     # x-chord of row y
+    cols = [_roots(c, 2 * b * x + e, a * x * x + d * x + f) for x in xs]     # y-chord of column x
+    mask = np.zeros((n, n), dtype=bool)
+    for j in range(n):
+        if rows[j] is None:
+            continue
+        xa, xb = rows[j]
+        for i in range(n):
+            if cols[i] is None:
+                continue
+            ya, yb = cols[i]
+            if xa + eps < xs[i] < xb - eps and ya + eps < xs[j] < yb - eps:
+                mask[j, i] = True
+
+    def lines(m, chords):
+        lo_i = np.full(n, 1, dtype=np.int64)
+        hi_i = np.zeros(n, dtype=np.int64)
+        ga = np.full(n, h)
+        gb = np.full(n, h)
+        for k in range(n):
+            idx = np.flatnonzero(m[k])
+            if idx.size == 0:
+                continue
+            if idx[-1] - idx[0] + 1 != idx.size:
+                raise ValueError("the domain's intersection with a grid line is not one interval")
+            ta, tb = chords[k]
+            lo_i[k], hi_i[k] = idx[0], idx[-1]
+            ga[k] = xs[idx[0]] - ta
+            gb[k] = tb - xs[idx[-1]]
+        return lo_i, hi_i, ga, gb
+
+    r0, r1, ra, rb = lines(mask, rows)
+    c0, c1, ca, cb = lines(mask.T, cols)
+    return EmbeddedGrid(n, n, lo, lo, h, h, r0, r1, ra, rb, c0, c1, ca, cb, mask)
+
+
+def ellipse_grid(n: int, half: float = 2.2) -> EmbeddedGrid:
+    """The ellipse ((x + y)/4)^2 + (x - y)^2 < 1 of Sec. 4.3 (principal axes on
+    the diagonals, semi-axes 2 sqrt 2 and 1/sqrt 2) in the grid of
+    [-half, half]^2 (it spans |x|, |y| <= sqrt(17)/2 = 2.06)."""
+    # (x + y)^2 / 16 + (x - y)^2 - 1 = (17/16)(x^2 + y^2) - (15/8) x y - 1
+    return conic_grid(n, -half, half, (17.0 / 16.0, -15.0 / 16.0, 17.0 / 16.0, 0.0, 0.0, -1.0))
+
+
+def disk_grid(n: int, radius: float = 1.0, half: float = 1.1) -> EmbeddedGrid:
+    """The disk x^2 + y^2 < radius^2 in the grid of [-half, half]^2."""
+    return conic_grid(n, -half, half, (1.0, 0.0, 1.0, 0.0, 0.0, -radius * radius))
+
+
+def gaussian_embedded(g: EmbeddedGrid, seed: int = 1006, width: float = 0.15) -> np.ndarray:
+    """Gaussian pulse with its centre drawn within 0.3 of the origin, zero
+    outside the domain."""
+    rng = np.random.default_rng(seed)
+    cx, cy = rng.uniform(-0.3, 0.3, size=2)
+    x, y = g.coords()
+    X, Y = np.meshgrid(x, y)
+    u = np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * width * width))
+    return np.where(g.mask, u, 0.0)
