@@ -79,6 +79,9 @@ def workload_spec(name: str) -> dict:
         n = 10001
         return dict(name="dirichlet1d-10001-P3-cfl2-standing-wave-data", shape=(n,), P=3, cfl=2.0, bc="dirichlet",
                     lo=(0.0,), hi=(1.0,), h=1.0 / (n - 1))
+    if name == "embedded":
+        n = 2048
+        return dict(name="embedded-ellipse-2048x2048-P2-cfl1-gaussian", n=n, P=2, cfl=1.0, bc="dirichlet")
     if name == "1d":
         n = 256
         L = 2 * math.pi
@@ -292,7 +295,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batch", "adjoint", "source", "dirichlet1d"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batch", "adjoint", "source", "dirichlet1d",
+                                                        "embedded"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -319,6 +323,9 @@ def main():
         return
     if args.workload in ("source", "dirichlet1d"):
         main_extension(args, spec)
+        return
+    if args.workload == "embedded":
+        main_embedded(args, spec)
         return
     if args.impl == "reference":
         run_reference(args, spec)
@@ -816,6 +823,120 @@ def main_extension(args, spec):
             rate = N * ks / el
         line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
                                 "sample": sample}
+    s.close()
+    print(json.dumps(line), flush=True)
+
+
+def embedded_bytes_per_point(P: int) -> float:
+    """Algorithmic bytes of the line-object sweeps per interior point and step:
+    C = 4 sweeps (D_x, L_y^{-1}, D_y, L_x^{-1} accumulated: 16 + 16 + 16 + 24 B),
+    D = 2 sweeps (L_y^{-1}, the subtraction from v: 16 + 24 B); Table 3 builds
+    1 + P(P-1)/2 C's and P - 1 D's per step."""
+    nC = 1 + P * (P - 1) // 2
+    return 88.0 * nC + 40.0 * (P - 1)
+
+
+def main_embedded(args, spec):
+    """The ellipse of Sec. 4.3 (embedded boundary, float64): one mol_embed_step
+    call of K steps with the levels resident; per-kind events of a second call;
+    the oracle on a bounded sample.  Points = interior nodes of the domain."""
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    n, P, cfl = spec["n"], spec["P"], spec["cfl"]
+    if args.impl == "reference":
+        import oracle
+        oracle.build()
+        m = 257
+        gs = workloads.ellipse_grid(m)
+        u0s = workloads.gaussian_embedded(gs, seed=1006, width=0.15)
+        beta = oracle.beta_max(P)
+        alpha = beta / (cfl * gs.hx)
+        oracle.run_embed(u0s, args.warmup, gs, alpha, P, beta)
+        t0 = time.perf_counter()
+        oracle.run_embed(u0s, args.steps, gs, alpha, P, beta)
+        el = time.perf_counter() - t0
+        value = gs.mask.sum() * args.steps / el
+        sample = f"the ellipse on {m}x{m} ({int(gs.mask.sum())} interior nodes), {args.steps} steps"
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": spec["name"], "sampled_shape": [m, m]},
+                "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import torch
+    from paper_1308_3214_gb300 import molt
+    torch.cuda.set_device(0)
+    g = workloads.ellipse_grid(n)
+    npts = int(g.mask.sum())
+    dt = cfl * g.hx
+    u0h = workloads.gaussian_embedded(g, seed=1006, width=0.15)
+    s = molt.EmbedSolver(g, dt=dt, P=P)
+    K = args.steps
+    up = torch.from_numpy(u0h).cuda()
+    uc = s.start(up)
+    s.step(up, uc, args.warmup)
+    torch.cuda.synchronize()
+    l0 = s.launches
+    bus = torch.cuda.get_device_properties(0).pci_bus_id
+    sampler = ClockSampler(bus).start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(up, uc, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = s.launches - l0
+    finite = bool(torch.isfinite(uc).all())
+    s.set_pass_timing(True)
+    kt = min(K, 50)
+    s.step(up, uc, kt)
+    kinds = s.pass_times()
+    s.set_pass_timing(False)
+    sweep_ms = kinds["x_sweep"][0] + kinds["y_sweep"][0]
+    sweep_launches = kinds["x_sweep"][1] + kinds["y_sweep"][1]
+    peak, peak_kind = read_peak()
+    bpp = embedded_bytes_per_point(P)
+    achieved = bpp * npts * kt / (sweep_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": npts * K / (ms * 1e-3), "unit": METRIC, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec["name"], "grid": [n, n], "interior_points": npts, "P": P, "cfl": cfl,
+                       "domain": "((x+y)/4)^2 + (x-y)^2 < 1 in [-2.2, 2.2]^2",
+                       "step": "mol_embed_step, K steps in one call, levels resident", "parallelism": "1 rank"},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                         "kernel": "k_obj_sweep (all line-object sweeps of a step; float64 recurrences)",
+                         "alg_bytes_per_point_step": bpp,
+                         "kinds_ms_per_step": {k: v[0] / kt for k, v in kinds.items()},
+                         "sweep_ms_per_launch": sweep_ms / max(sweep_launches, 1)},
+            "clocks": clocks, "finite": finite}
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        s.solve_host(u0h, K)
+        el = time.perf_counter() - t0
+        line["e2e"] = {"value": npts * K / el, "unit": METRIC, "h2d_bytes_per_step": 8 * n * n / K,
+                       "d2h_bytes_per_step": 8 * n * n / K, "note": "mol_embed_solve_host: u0 in, K steps, u out"}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        m = 257
+        gs = workloads.ellipse_grid(m)
+        u0s = workloads.gaussian_embedded(gs, seed=1006, width=0.15)
+        beta = oracle.beta_max(P)
+        ks = 20
+        t0 = time.perf_counter()
+        oracle.run_embed(u0s, ks, gs, beta / (cfl * gs.hx), P, beta)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": gs.mask.sum() * ks / el, "unit": METRIC, "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": f"{ks} oracle steps of the ellipse on {m}x{m} "
+                                                            f"({int(gs.mask.sum())} interior nodes, {el:.2f} s)"}
     s.close()
     print(json.dumps(line), flush=True)
 

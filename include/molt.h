@@ -346,6 +346,73 @@ mol_status mol_batch_set_tuning(mol_batch b, int x_warps_short, int x_warps_long
 mol_status mol_batch_set_pass_timing(mol_batch b, int enable);
 mol_status mol_batch_pass_times(mol_batch b, double total_ms[3], int64_t launches[3]);
 
+/* ------------------------------------------------------------------------
+ * Embedded boundaries (Sec. 4.3: the ADI lines as "line objects")
+ *
+ * A 2D domain cut out of an nx x ny grid of spacing (hx, hy), x fastest.
+ * Each grid line meets the domain in one interval: a line object made of the
+ * interior grid nodes of the line (row j: x indices row_lo[j] .. row_hi[j];
+ * none when row_lo[j] > row_hi[j]) and two boundary points off the grid, at
+ * distance row_gap_lo[j] > 0 before the first interior node and row_gap_hi[j]
+ * > 0 after the last; columns likewise (y indices col_lo[i] .. col_hi[i]).
+ * The boundary points carry homogeneous Dirichlet data.  Rows and columns
+ * must agree on which nodes are interior; a line object holds at most 2046
+ * interior nodes.  The geometry arrays are HOST arrays, read at creation.
+ *
+ * L_gamma^{-1} on a line object (Sec. 2 with the boundary points as the line's
+ * ends, Sec. 4.3): the increments integrate the quadratic through a node and
+ * its two neighbours (one node inward at the ends; the boundary points are
+ * nodes) exactly against the kernel over cells of their true length, the
+ * recurrences decay by e^{-alpha dx} per cell, and A, B make the result
+ * vanish at both boundary points.  The scheme is eq. (Full_2D) with C and D of
+ * eqs. (C_def_ADI), (D_def_ADI) built from these operators, its terms formed
+ * in the order of Table 3: on a curved domain the x and y operators do not
+ * commute, so the order is part of the scheme.  Float64 throughout.
+ *
+ * Fields: caller-owned device float64 arrays (ny, nx) that vanish outside the
+ * domain (outputs vanish there too).  The library owns its tables and work
+ * fields (P + 6 fields of nx ny doubles) and frees them in mol_embed_destroy.
+ * Calls are asynchronous on the given stream; errors are returned statuses
+ * (MOL_EINVAL arguments or geometry, MOL_EUNSTABLE beta above beta_max(P),
+ * MOL_ENOMEM, MOL_ECUDA), text via mol_embed_last_error.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t nx, ny;
+    double hx, hy;
+    const int64_t *row_lo, *row_hi;        /* ny entries */
+    const double *row_gap_lo, *row_gap_hi; /* ny entries */
+    const int64_t *col_lo, *col_hi;        /* nx entries */
+    const double *col_gap_lo, *col_gap_hi; /* nx entries */
+} mol_embed_geom;
+
+typedef struct mol_embed_ctx *mol_embed;
+
+/* alpha = beta / (c dt) (eq. L_def); beta <= 0 selects beta_max(P); P in 1..5. */
+mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double beta, int P, mol_embed *out);
+mol_status mol_embed_destroy(mol_embed e);
+/* Message of the last failed call on e (that of mol_last_error(NULL) if e is NULL). */
+const char *mol_embed_last_error(mol_embed e);
+
+/* w = L_gamma^{-1} v on every line object of axis 0 (x) or 1 (y). */
+mol_status mol_embed_linv(mol_embed e, const double *v, double *w, int axis, void *stream);
+/* F = F[u] (eq. Full_2D on the domain). */
+mol_status mol_embed_apply_F(mol_embed e, const double *u, double *F, void *stream);
+/* u1 = u0 + F[u0]/2 (zero initial velocity, Sec. 3.2). */
+mol_status mol_embed_start(mol_embed e, const double *u0, double *u1, void *stream);
+/* nsteps of u^{n+1} = 2 u^n - u^{n-1} + F[u^n]; (u_prev, u_cur) advance in place. */
+mol_status mol_embed_step(mol_embed e, double *u_prev, double *u_cur, int64_t nsteps, void *stream);
+/* End to end from HOST memory: u0 in, u^{nsteps} out (start, then steps).  Synchronous. */
+mol_status mol_embed_solve_host(mol_embed e, const double *u0, double *u_out, int64_t nsteps, void *stream);
+mol_status mol_embed_sync(mol_embed e, void *stream);
+int64_t mol_embed_launch_count(mol_embed e);
+/* Per-kind CUDA-event timing of the launches made while enabled: kind 0 =
+ * x line-object sweeps, 1 = y sweeps, 2 = transposes between the row and
+ * column layouts, 3 = the linear combinations of F and the level update.
+ * mol_embed_pass_times synchronizes, returns the totals since the last call
+ * and resets them. */
+mol_status mol_embed_set_pass_timing(mol_embed e, int enable);
+mol_status mol_embed_pass_times(mol_embed e, double total_ms[4], int64_t launches[4]);
+
 /*
  * F = F[u] in float64 (the operator of eq. update_P / Full_2D, as
  * mol_apply_F on a MOL_FP64 handle) WITHOUT ALLOCATING: no handle, no

@@ -33,7 +33,10 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
            "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times", "mol_batch_apply_FT",
            "mol_batch_traces", "mol_batch_adjoint", "mol_batch_update", "mol_autotune", "mol_get_tuning", "mol_set_tuning",
-           "mol_batch_autotune", "mol_batch_get_tuning", "mol_batch_set_tuning", "mol_solve_dirichlet", "mol_solve_source", "mol_apply_FT", "mol_traces", "mol_adjoint"]
+           "mol_batch_autotune", "mol_batch_get_tuning", "mol_batch_set_tuning", "mol_solve_dirichlet", "mol_solve_source", "mol_apply_FT", "mol_traces", "mol_adjoint",
+           "mol_embed_create", "mol_embed_destroy", "mol_embed_last_error", "mol_embed_linv", "mol_embed_apply_F",
+           "mol_embed_start", "mol_embed_step", "mol_embed_solve_host", "mol_embed_sync", "mol_embed_launch_count",
+           "mol_embed_set_pass_timing", "mol_embed_pass_times"]
 
 
 class MolError(RuntimeError):
@@ -45,6 +48,13 @@ class MolError(RuntimeError):
 class mol_grid(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3)]
+
+
+class mol_embed_geom(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("hx", ctypes.c_double), ("hy", ctypes.c_double),
+                ("row_lo", ctypes.c_void_p), ("row_hi", ctypes.c_void_p), ("row_gap_lo", ctypes.c_void_p),
+                ("row_gap_hi", ctypes.c_void_p), ("col_lo", ctypes.c_void_p), ("col_hi", ctypes.c_void_p),
+                ("col_gap_lo", ctypes.c_void_p), ("col_gap_hi", ctypes.c_void_p)]
 
 
 class mol_options(ctypes.Structure):
@@ -119,10 +129,25 @@ def load_library(path: Path | None = None):
     lib.mol_batch_set_tuning.argtypes = [vp, I, I, I]
     lib.mol_solve_dirichlet.argtypes = [vp, vp, i64, dp, vp, vp]
     lib.mol_solve_source.argtypes = [vp, vp, i64, vp, dp, vp, vp]
+    lib.mol_embed_create.argtypes = [ctypes.POINTER(mol_embed_geom), D, D, D, I, ctypes.POINTER(vp)]
+    lib.mol_embed_destroy.argtypes = [vp]
+    lib.mol_embed_last_error.argtypes = [vp]
+    lib.mol_embed_last_error.restype = ctypes.c_char_p
+    lib.mol_embed_linv.argtypes = [vp, vp, vp, I, vp]
+    lib.mol_embed_apply_F.argtypes = [vp, vp, vp, vp]
+    lib.mol_embed_start.argtypes = [vp, vp, vp, vp]
+    lib.mol_embed_step.argtypes = [vp, vp, vp, i64, vp]
+    lib.mol_embed_solve_host.argtypes = [vp, dp, dp, i64, vp]
+    lib.mol_embed_sync.argtypes = [vp, vp]
+    lib.mol_embed_launch_count.argtypes = [vp]
+    lib.mol_embed_launch_count.restype = i64
+    lib.mol_embed_set_pass_timing.argtypes = [vp, I]
+    lib.mol_embed_pass_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
     lib.mol_launch_count.restype = i64
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
-                        "mol_launch_count", "mol_batch_last_error", "mol_batch_launch_count"):
+                        "mol_launch_count", "mol_batch_last_error", "mol_batch_launch_count",
+                        "mol_embed_last_error", "mol_embed_launch_count"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -550,6 +575,119 @@ class BatchSolver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.mol_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class EmbedSolver:
+    """The 2D scheme on a domain embedded in a grid (Sec. 4.3), float64.
+
+    ``geom`` describes the line objects: any object with the attributes nx,
+    ny, hx, hy, r0, r1, ra, rb (rows: first / last interior x index, gaps
+    before / after them) and c0, c1, ca, cb (columns), as
+    ``workloads.EmbeddedGrid`` has.  Fields are contiguous CUDA float64
+    tensors of shape (ny, nx) that vanish outside the domain."""
+
+    def __init__(self, geom, dt: float, P: int, c: float = 1.0, beta: float = 0.0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libmolt needs a CUDA GPU")
+        self.lib = load_library()
+        self.shape = (int(geom.ny), int(geom.nx))
+        i64 = lambda a: np.ascontiguousarray(a, dtype=np.int64)
+        f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        arrs = [i64(geom.r0), i64(geom.r1), f64(geom.ra), f64(geom.rb),
+                i64(geom.c0), i64(geom.c1), f64(geom.ca), f64(geom.cb)]
+        g = mol_embed_geom(int(geom.nx), int(geom.ny), float(geom.hx), float(geom.hy),
+                           *[a.ctypes.data for a in arrs])
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        st = self.lib.mol_embed_create(ctypes.byref(g), float(c), float(dt), float(beta), int(P), ctypes.byref(h))
+        if st != MOL_OK:
+            raise MolError(st, self.lib.mol_last_error(None).decode())
+        self.h = h
+        self.P, self.dt, self.c = int(P), float(dt), float(c)
+
+    def _check(self, st: int):
+        if st != MOL_OK:
+            raise MolError(st, self.lib.mol_embed_last_error(self.h).decode())
+
+    def _field(self, t, name):
+        import torch
+        if (not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda
+                or tuple(t.shape) != self.shape or not t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous CUDA float64 tensor of shape {self.shape}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def empty(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+    def linv(self, v, axis: int, out=None, stream=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_embed_linv(self.h, self._field(v, "v"), self._field(out, "w"), int(axis),
+                                            ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def apply_F(self, u, out=None, stream=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_embed_apply_F(self.h, self._field(u, "u"), self._field(out, "F"),
+                                               ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def start(self, u0, out=None, stream=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mol_embed_start(self.h, self._field(u0, "u0"), self._field(out, "u1"),
+                                             ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def step(self, u_prev, u_cur, nsteps: int, stream=None):
+        self._check(self.lib.mol_embed_step(self.h, self._field(u_prev, "u_prev"), self._field(u_cur, "u_cur"),
+                                            int(nsteps), ctypes.c_void_p(_stream_ptr(stream))))
+
+    def solve_host(self, u0: np.ndarray, nsteps: int, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        if u0.shape != self.shape:
+            raise ValueError(f"u0 must have shape {self.shape}")
+        out = np.empty_like(u0) if out is None else out
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.mol_embed_solve_host(self.h, u0.ctypes.data_as(dp), out.ctypes.data_as(dp),
+                                                  int(nsteps), ctypes.c_void_p(_stream_ptr(stream))))
+        return out
+
+    def sync(self, stream=None):
+        self._check(self.lib.mol_embed_sync(self.h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def set_pass_timing(self, enable: bool = True):
+        self._check(self.lib.mol_embed_set_pass_timing(self.h, 1 if enable else 0))
+
+    def pass_times(self):
+        """{kind: (total ms, launches)} since the last call: x_sweep, y_sweep,
+        transpose, combine."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        self._check(self.lib.mol_embed_pass_times(self.h, ms, n))
+        names = ("x_sweep", "y_sweep", "transpose", "combine")
+        return {names[k]: (float(ms[k]), int(n[k])) for k in range(4)}
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.mol_embed_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mol_embed_destroy(self.h)
             self.h = None
 
     def __del__(self):

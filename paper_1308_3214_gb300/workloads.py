@@ -157,13 +157,15 @@ class EmbeddedGrid:
         return x, y
 
 
-def _roots(a: float, b: float, c: float):
-    """Real roots of a t^2 + b t + c (a > 0), or None."""
-    disc = b * b - 4.0 * a * c
-    if disc <= 0.0:
-        return None
-    s = np.sqrt(disc)
-    return (-b - s) / (2.0 * a), (-b + s) / (2.0 * a)
+def _chords(a: float, bl: np.ndarray, cl: np.ndarray):
+    """Roots t_lo < t_hi of a t^2 + bl t + cl (a > 0) for every entry; NaN where
+    the line misses the domain."""
+    disc = bl * bl - 4.0 * a * cl
+    ok = disc > 0.0
+    sq = np.sqrt(np.where(ok, disc, 0.0))
+    lo = np.where(ok, (-bl - sq) / (2.0 * a), np.nan)
+    hi = np.where(ok, (-bl + sq) / (2.0 * a), np.nan)
+    return lo, hi
 
 
 def conic_grid(n: int, lo: float, hi: float, q) -> EmbeddedGrid:
@@ -177,45 +179,29 @@ def conic_grid(n: int, lo: float, hi: float, q) -> EmbeddedGrid:
     """
     a, b, c, d, e, f = (float(t) for t in q)
     h = (hi - lo) / (n - 1)
-    if a * lo * lo + 2 * b * lo * lo + c * lo * lo + d * lo + e * lo + f < 0 or any(
-            r is not None and (r[0] <= lo or r[1] >= hi)
-            for r in (_roots(a, 2 * b * y + d, c * y * y + e * y + f) for y in (lo, hi))):
-        raise ValueError("the domain must lie inside the grid")
     xs = lo + h * np.arange(n)
     eps = 1e-9 * h
-    rows = [_roots(a, 2 * b * y + d, c * y * y + e * y + f) for y in xs]     # x-chord of row y
-    cols = [_roots(c, 2 * b * x + e, a * x * x + d * x + f) for x in xs]     # y-chord of column x
-    mask = np.zeros((n, n), dtype=bool)
-    for j in range(n):
-        if rows[j] is None:
-            continue
-        xa, xb = rows[j]
-        for i in range(n):
-            if cols[i] is None:
-                continue
-            ya, yb = cols[i]
-            if xa + eps < xs[i] < xb - eps and ya + eps < xs[j] < yb - eps:
-                mask[j, i] = True
+    rxa, rxb = _chords(a, 2 * b * xs + d, c * xs * xs + e * xs + f)      # x-chord of row y = xs[j]
+    cya, cyb = _chords(c, 2 * b * xs + e, a * xs * xs + d * xs + f)      # y-chord of column x = xs[i]
+    if (np.nanmin(rxa) <= lo or np.nanmax(rxb) >= hi or np.nanmin(cya) <= lo or np.nanmax(cyb) >= hi):
+        raise ValueError("the domain must lie inside the grid")
+    with np.errstate(invalid="ignore"):
+        in_row = (xs[None, :] > rxa[:, None] + eps) & (xs[None, :] < rxb[:, None] - eps)
+        in_col = (xs[:, None] > cya[None, :] + eps) & (xs[:, None] < cyb[None, :] - eps)
+    mask = in_row & in_col                                               # mask[j, i]: row j, column i
 
-    def lines(m, chords):
-        lo_i = np.full(n, 1, dtype=np.int64)
-        hi_i = np.zeros(n, dtype=np.int64)
-        ga = np.full(n, h)
-        gb = np.full(n, h)
-        for k in range(n):
-            idx = np.flatnonzero(m[k])
-            if idx.size == 0:
-                continue
-            if idx[-1] - idx[0] + 1 != idx.size:
-                raise ValueError("the domain's intersection with a grid line is not one interval")
-            ta, tb = chords[k]
-            lo_i[k], hi_i[k] = idx[0], idx[-1]
-            ga[k] = xs[idx[0]] - ta
-            gb[k] = tb - xs[idx[-1]]
-        return lo_i, hi_i, ga, gb
+    def lines(m, ta, tb):
+        cnt = m.sum(axis=1)
+        first = np.where(cnt > 0, m.argmax(axis=1), 1)
+        last = np.where(cnt > 0, n - 1 - m[:, ::-1].argmax(axis=1), 0)
+        if ((last - first + 1)[cnt > 0] != cnt[cnt > 0]).any():
+            raise ValueError("the domain's intersection with a grid line is not one interval")
+        ga = np.where(cnt > 0, xs[first] - ta, h)
+        gb = np.where(cnt > 0, tb - xs[last], h)
+        return first.astype(np.int64), last.astype(np.int64), ga, gb
 
-    r0, r1, ra, rb = lines(mask, rows)
-    c0, c1, ca, cb = lines(mask.T, cols)
+    r0, r1, ra, rb = lines(mask, rxa, rxb)
+    c0, c1, ca, cb = lines(mask.T, cya, cyb)
     return EmbeddedGrid(n, n, lo, lo, h, h, r0, r1, ra, rb, c0, c1, ca, cb, mask)
 
 

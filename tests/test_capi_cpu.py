@@ -4,6 +4,8 @@ import ctypes
 import re
 from pathlib import Path
 
+import numpy as np
+
 import pytest
 
 import oracle
@@ -94,3 +96,47 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.mol_step(None, None, None, 1, None) == molt.MOL_EINVAL
     assert lib.mol_destroy(None) == molt.MOL_EINVAL
     assert lib.mol_launch_count(None) == 0
+
+
+# --------------------------------------------------------------------------
+# embedded-boundary handles: the geometry is checked on the host, before any
+# device work
+# --------------------------------------------------------------------------
+def _embed_create(lib, g, P=2, beta=0.0):
+    i64 = lambda a: np.ascontiguousarray(a, dtype=np.int64)
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    arrs = [i64(g.r0), i64(g.r1), f64(g.ra), f64(g.rb), i64(g.c0), i64(g.c1), f64(g.ca), f64(g.cb)]
+    geom = molt.mol_embed_geom(g.nx, g.ny, g.hx, g.hy, *[a.ctypes.data for a in arrs])
+    h = ctypes.c_void_p()
+    st = lib.mol_embed_create(ctypes.byref(geom), 1.0, 0.01, beta, P, ctypes.byref(h))
+    return st, h
+
+
+def test_embed_create_rejects_bad_geometry_on_the_host(lib):
+    from paper_1308_3214_gb300 import workloads
+    g = workloads.ellipse_grid(41)
+    bad = workloads.ellipse_grid(41)
+    bad.ra = bad.ra.copy()
+    bad.ra[20] = 0.0                                     # a boundary point on the first interior node
+    assert _embed_create(lib, bad)[0] == molt.MOL_EINVAL
+    bad = workloads.ellipse_grid(41)
+    bad.r1 = bad.r1.copy()
+    bad.r1[20] += 1                                      # the row claims a node its column does not
+    st, h = _embed_create(lib, bad)
+    assert st == molt.MOL_EINVAL and not h.value
+    assert b"disagree" in lib.mol_last_error(None)
+    bad = workloads.ellipse_grid(41)
+    bad.c1 = bad.c1.copy()
+    bad.c1[20] = 41                                      # past the grid
+    assert _embed_create(lib, bad)[0] == molt.MOL_EINVAL
+    assert _embed_create(lib, g, P=0)[0] == molt.MOL_EINVAL
+    assert _embed_create(lib, g, P=2, beta=1.49)[0] == molt.MOL_EUNSTABLE
+    big = workloads.disk_grid(2301, radius=1.0, half=1.1)   # the middle row holds more than 2046 nodes
+    st, _ = _embed_create(lib, big)
+    assert st == molt.MOL_EINVAL and b"2046" in lib.mol_last_error(None)
+
+
+def test_embed_null_handle_calls_fail_cleanly(lib):
+    assert lib.mol_embed_step(None, None, None, 1, None) == molt.MOL_EINVAL
+    assert lib.mol_embed_destroy(None) == molt.MOL_OK
+    assert lib.mol_embed_launch_count(None) == 0

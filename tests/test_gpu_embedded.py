@@ -1,0 +1,131 @@
+"""GPU parity of the embedded-boundary path (Sec. 4.3) with the oracle.
+
+Float64 on both sides.  Tolerance: relative L2 1e-12, or 100 eps64 h / g_min
+when larger: the weights of a cell next to a boundary point at distance g
+from the first interior node carry a factor h / g (the quadratic through two
+nodes g apart), so two correct float64 evaluations of the same operator can
+differ by about that factor times the rounding unit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1308_3214_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS64 = np.finfo(np.float64).eps
+
+
+def _tol(g):
+    live_r, live_c = g.r0 <= g.r1, g.c0 <= g.c1
+    gmin = min(g.ra[live_r].min(), g.rb[live_r].min(), g.ca[live_c].min(), g.cb[live_c].min())
+    return max(1e-12, 100 * EPS64 * g.hx / gmin)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _solver(g, cfl, P):
+    from paper_1308_3214_gb300 import molt
+    return molt.EmbedSolver(g, dt=cfl * g.hx, P=P)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("shape", [("ellipse", 61), ("ellipse", 257), ("disk", 90)])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_linv_matches_oracle(shape, axis):
+    g = workloads.ellipse_grid(shape[1]) if shape[0] == "ellipse" else workloads.disk_grid(shape[1])
+    s = _solver(g, 1.7, 2)
+    alpha = oracle.beta_max(2) / (1.7 * g.hx)
+    v = workloads.random_field((g.ny, g.nx), 11 + axis) * g.mask
+    got = s.linv(_dev(v), axis).cpu().numpy()
+    ref = oracle.linv_axis_embed(v, axis, g, alpha)
+    assert _rel(got, ref) <= _tol(g)
+    assert not got[~g.mask].any()                      # nothing written outside the domain
+    s.close()
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+@pytest.mark.parametrize("cfl", [0.8, 3.0])
+def test_F_matches_oracle(P, cfl):
+    g = workloads.ellipse_grid(73)
+    s = _solver(g, cfl, P)
+    u = workloads.gaussian_embedded(g, seed=1006 + P, width=0.3)
+    got = s.apply_F(_dev(u)).cpu().numpy()
+    ref = oracle.F_embed(u, g, oracle.beta_max(P) / (cfl * g.hx), P, oracle.beta_max(P))
+    assert _rel(got, ref) <= _tol(g)
+    s.close()
+
+
+@pytest.mark.parametrize("nsteps", [1, 2, 3, 4, 12])
+def test_time_stepping_matches_oracle(nsteps):
+    """start, then nsteps - 1 steps in place: every rotation of the three
+    level buffers ends with (u^{n-1}, u^n) back in the caller's tensors."""
+    g = workloads.ellipse_grid(65)
+    P, cfl = 2, 1.5
+    s = _solver(g, cfl, P)
+    u0 = workloads.gaussian_embedded(g, seed=1006, width=0.25)
+    up = _dev(u0)
+    uc = s.start(up)
+    s.step(up, uc, nsteps - 1)
+    beta = oracle.beta_max(P)
+    alpha = beta / (cfl * g.hx)
+    ref_cur = oracle.run_embed(u0, nsteps, g, alpha, P, beta)
+    ref_prev = oracle.run_embed(u0, nsteps - 1, g, alpha, P, beta)
+    assert _rel(uc.cpu().numpy(), ref_cur) <= 10 * _tol(g)
+    assert _rel(up.cpu().numpy(), ref_prev) <= 10 * _tol(g)
+    s.close()
+
+
+def test_solve_host_matches_oracle_on_a_large_ellipse():
+    """801^2 grid (rows of up to 750 interior nodes): 3 steps from host memory."""
+    g = workloads.ellipse_grid(801)
+    P, cfl = 2, 2.0
+    s = _solver(g, cfl, P)
+    u0 = workloads.gaussian_embedded(g, seed=1006, width=0.15)
+    got = s.solve_host(u0, 3)
+    beta = oracle.beta_max(P)
+    ref = oracle.run_embed(u0, 3, g, beta / (cfl * g.hx), P, beta)
+    assert _rel(got, ref) <= 10 * _tol(g)
+    s.close()
+
+
+def test_longest_line_object():
+    """A disk whose middle row holds 2045 interior nodes (the kernel's limit is 2046)."""
+    g = workloads.disk_grid(2249, radius=1.0, half=1.1)
+    assert (g.r1 - g.r0 + 1).max() <= 2046 and (g.r1 - g.r0 + 1).max() > 2000
+    s = _solver(g, 1.0, 1)
+    v = workloads.random_field((g.ny, g.nx), 5) * g.mask
+    alpha = oracle.beta_max(1) / g.hx
+    for axis in (0, 1):
+        got = s.linv(_dev(v), axis).cpu().numpy()
+        assert _rel(got, oracle.linv_axis_embed(v, axis, g, alpha)) <= _tol(g)
+    s.close()
+
+
+@pytest.mark.parametrize("P", [1, 2])
+def test_disk_standing_mode_converges_on_the_gpu(P):
+    """J_0(k r) cos(k t) with J_0(k) = 0 on the unit disk: second-order
+    convergence at CFL 1 to t = 0.5, as the oracle shows."""
+    special = pytest.importorskip("scipy.special")
+    k = special.jn_zeros(0, 1)[0]
+    T = 0.5
+    errs = []
+    for n in (89, 177, 353):
+        g = workloads.disk_grid(n)
+        x, y = g.coords()
+        r = np.hypot(*np.meshgrid(x, y))
+        ns = int(round(T / g.hx))
+        s = _solver(g, T / ns / g.hx, P)
+        u = s.solve_host(np.where(g.mask, special.j0(k * r), 0.0), ns)
+        s.close()
+        ex = np.where(g.mask, special.j0(k * r) * np.cos(k * T), 0.0)
+        errs.append(np.sqrt(g.hx * g.hy * np.sum((u - ex) ** 2)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates.min() > 1.9, (errs, rates)
