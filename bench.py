@@ -50,6 +50,7 @@ KERNEL_SOURCES = {
     "batch": [CSRC / f for f in ("molt_kernels.cuh", "molt_regs.cuh", "molt_batch.cuh", "molt_batch.cu")],
 }
 FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_GFLOPS = 1250.0
 
 
 def workload_spec(name: str) -> dict:
@@ -635,7 +636,8 @@ def main_batch(args, spec):
     achieved = bpp_tot[dom_axis] / (dom_ms * 1e-3) / 1e9
     long_x = ("k_batch_xs (one CTA of two warps per row)" if tuning["x_warps"][1] == 0
               else "k_batch_x<LARGE> (one warp per row)")
-    kernel_name = {0: f"k_batch_x (x pass: Horner + level update; rows <= 512) + {long_x} for longer rows",
+    kernel_name = {0: f"k_batch_x (x pass: Horner + level update; rows <= 256) + k_batch_xs<8, 2> (rows of "
+                      f"257..512) + {long_x} for longer rows",
                    1: "k_batch_y (y pass: powers of D_y)"}[dom_axis]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": read_traffic(dom_axis, spec["name"], args.prec, "batch"),
@@ -900,9 +902,17 @@ def main_embedded(args, spec):
     s.set_pass_timing(False)
     sweep_ms = kinds["x_sweep"][0] + kinds["y_sweep"][0]
     sweep_launches = kinds["x_sweep"][1] + kinds["y_sweep"][1]
-    peak, peak_kind = read_peak()
+    hbm_peak, peak_kind = read_peak()
     bpp = embedded_bytes_per_point(P)
-    achieved = bpp * npts * kt / (sweep_ms * 1e-3) / 1e9
+    hbm_achieved = bpp * npts * kt / (sweep_ms * 1e-3) / 1e9
+    # float64 operations of the sweep per interior node (a node between grid
+    # nodes): two 3-point increments (2 x 5 flops), each recurrence's chunk
+    # reduction (FMA + multiply, 3 flops) and re-scan (FMA, 2 flops) in both
+    # directions (10), the homogeneous terms and the sum (9): 29 flops.  The
+    # peak is the nominal float64 rate of a GB300 (1.25 TFLOP/s): the sweeps
+    # are bound by the narrow float64 pipe, not by HBM.
+    flops = 29.0 * npts * sweep_launches
+    achieved = flops / (sweep_ms * 1e-3) / 1e9
     line = {"metric": METRIC, "value": npts * K / (ms * 1e-3), "unit": METRIC, "n_gpus": 1, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -910,10 +920,13 @@ def main_embedded(args, spec):
                        "domain": "((x+y)/4)^2 + (x-y)^2 < 1 in [-2.2, 2.2]^2",
                        "step": "mol_embed_step, K steps in one call, levels resident", "parallelism": "1 rank"},
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                         "peak_kind": "nominal float64 rate of a GB300 (no measured float64 peak on this pool)",
                          "kernel": "k_obj_sweep (all line-object sweeps of a step; float64 recurrences)",
-                         "alg_bytes_per_point_step": bpp,
+                         "flops_per_node_sweep": 29, "hbm": {"achieved_GBps": hbm_achieved, "peak": hbm_peak,
+                                                              "frac": hbm_achieved / hbm_peak,
+                                                              "alg_bytes_per_point_step": bpp},
                          "kinds_ms_per_step": {k: v[0] / kt for k, v in kinds.items()},
                          "sweep_ms_per_launch": sweep_ms / max(sweep_launches, 1)},
             "clocks": clocks, "finite": finite}

@@ -324,8 +324,10 @@ mol_status mol_batch_sync(mol_batch b, void *stream);
 int64_t mol_batch_launch_count(mol_batch b);
 
 /* Autotuner of a batch: times the x pass with 2, 4 and 8 warps per CTA for
- * each of its two launches (rows of <= 512 points; longer rows, which are
- * also timed split over the two warps of one CTA per row), then the y pass
+ * each of its one-warp-per-row launches (rows of <= 256 points; rows of more
+ * than 512 points, which are also timed split over the two warps of one CTA
+ * per row; rows of 257..512 points always run split, 8-point segments, when
+ * their buffers fit shared memory, else with the short rows), then the y pass
  * with each problem's segment length at the smallest RPT covering the column
  * with 16 warps or at twice that, on the batch's own workspace, and keeps
  * the fastest.  Synchronous; the caller's fields are not touched.

@@ -25,7 +25,8 @@ struct BLevel {
 struct mol_batch_ctx {
     int nprob = 0, prec = 0, tbytes = 8, Pmax = 1, quad = 2, use_graphs = 1;
     int64_t nrows = 0, total_int = 0;
-    int64_t rows_small = 0;             // rows of the problems with rows of <= 512 points come first
+    int64_t rows_small = 0;             // rows are ordered by length class: <= 256 points first,
+    int64_t rows_mid = 0;               //   then 257..512 (up to rows_mid), then 513..1024
     int nitems_y = 0;
     std::vector<int64_t> uoff;          // packed user layout: nprob + 1 prefix sums
     std::vector<BatchProb> hp;          // host copy of the problem table
@@ -52,11 +53,17 @@ struct mol_batch_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     std::string err;
-    int x_launches() const { return (rows_small > 0 ? 1 : 0) + (nrows > rows_small ? 1 : 0); }
+    int64_t one_warp_end() const { return xmid ? rows_small : rows_mid; }
+    int x_launches() const
+    {
+        return (one_warp_end() > 0 ? 1 : 0) + ((xmid && rows_mid > rows_small) ? 1 : 0) + (nrows > rows_mid ? 1 : 0);
+    }
     int smem_sm = 228 * 1024, smem_blk = 227 * 1024;
     int ymode = 0;                      // y segment rule: 0 smallest covering RPT, 1 twice that (<= 64)
     int xsplit = 1;                     // rows of > 512 points: 1 one CTA of two warps per row, 0 one warp
     size_t xs_smem = 0;                 // shared memory of the split-row kernel
+    int xmid = 1;                       // rows of 257..512 points: 1 one CTA of two warps per row (8-point
+    size_t xs8_smem = 0;                //   segments), 0 the one-warp kernel; its shared memory
     double tune_ms[2] = {0.0, 0.0};     // tuned x / y pass times
 };
 
@@ -121,7 +128,9 @@ int pick_rpt_y(int n, int mode = 0)
     return r;
 }
 
-bool long_row(int nx) { return nx > 16 * 32; }
+// length class of a row: 0 (<= 256 points), 1 (257..512), 2 (513..1024)
+int row_class(int nx) { return nx <= 256 ? 0 : (nx <= 512 ? 1 : 2); }
+bool long_row(int nx) { return row_class(nx) == 2; }
 
 // Order of the y-pass work list.  CTA b of G takes the items at b, b + G,
 // b + 2G, ... of the list.  The items are sorted by decreasing cost (the
@@ -163,8 +172,9 @@ cudaError_t upload_table(mol_batch_ctx *b)
 void set_x_segments(mol_batch_ctx *b)
 {
     for (BatchProb &pb : b->hp) {
-        if (!long_row(pb.ax.n)) continue;
-        pb.rpt_x = b->xsplit ? 16 : 32;
+        const int cls = row_class(pb.ax.n);
+        if (cls == 0) continue;
+        pb.rpt_x = cls == 2 ? (b->xsplit ? 16 : 32) : (b->xmid ? 8 : 16);
         const double nux = -std::log(pb.ax.d);
         for (int k = 0; k < 5; ++k) pb.ax.dm[k] = std::exp(-nux * (double)pb.rpt_x * (double)(1 << k));
     }
@@ -188,7 +198,7 @@ bool set_x_shape(mol_batch_ctx *b, int L, int W)
     if (W < 1 || W > 8 || bytes > (size_t)b->smem_blk || ctas * (bytes + 1024) > (size_t)b->smem_sm) return false;
     b->xW[L] = W;
     b->xsmem[L] = bytes;
-    const int64_t nr = L == 0 ? b->rows_small : b->nrows - b->rows_small;
+    const int64_t nr = L == 0 ? b->one_warp_end() : b->nrows - b->rows_mid;
     b->xgrid[L] = (int)std::max<int64_t>(1, std::min<int64_t>((nr + W - 1) / W, ctas * (int64_t)b->num_sms));
     return true;
 }
@@ -216,15 +226,21 @@ cudaError_t launch_pass_x(const mol_batch_ctx *b, BatchPass bp, cudaStream_t s)
 {
     // rows of short lines, then rows of long lines (each a persistent launch)
     bp.row_begin = 0;
-    bp.nitems = (int)b->rows_small;
+    bp.nitems = (int)b->one_warp_end();
     if (bp.nitems > 0) k_batch_x<T, false, ADJ><<<b->xgrid[0], 32 * b->xW[0], b->xsmem[0], s>>>(bp, b->nbuf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bp.row_begin = (int)b->rows_small;
+    if (b->xmid && b->rows_mid > b->rows_small) {
+        bp.row_begin = (int)b->rows_small;
+        bp.nitems = (int)b->rows_mid;
+        k_batch_xs<T, 8, 2, ADJ><<<(unsigned)(b->rows_mid - b->rows_small), 64, b->xs8_smem, s>>>(bp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    bp.row_begin = (int)b->rows_mid;
     bp.nitems = (int)b->nrows;
     if (bp.nitems > bp.row_begin) {
         if (b->xsplit)
-            k_batch_xs<T, 16, 2, ADJ><<<(unsigned)(b->nrows - b->rows_small), 64, b->xs_smem, s>>>(bp);
+            k_batch_xs<T, 16, 2, ADJ><<<(unsigned)(b->nrows - b->rows_mid), 64, b->xs_smem, s>>>(bp);
         else
             k_batch_x<T, true, ADJ><<<b->xgrid[1], 32 * b->xW[1], b->xsmem[1], s>>>(bp, b->nbuf);
     }
@@ -246,6 +262,9 @@ cudaError_t set_kernel_smem(const mol_batch_ctx *b)
     const void *sk[2] = {(const void *)k_batch_xs<T, 16, 2, false>, (const void *)k_batch_xs<T, 16, 2, true>};
     for (int adj = 0; adj < 2 && e == cudaSuccess; ++adj)
         e = cudaFuncSetAttribute(sk[adj], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xs_smem);
+    const void *mk[2] = {(const void *)k_batch_xs<T, 8, 2, false>, (const void *)k_batch_xs<T, 8, 2, true>};
+    for (int adj = 0; adj < 2 && e == cudaSuccess; ++adj)
+        e = cudaFuncSetAttribute(mk[adj], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->xs8_smem);
     return e;
 }
 
@@ -441,6 +460,7 @@ mol_status plan_batch(mol_batch_ctx *b, int nprob, const mol_grid *grids, const 
     b->uoff.assign(nprob + 1, 0);
     int64_t off = 0, rows = 0, items = 0;
     b->rows_small = 0;
+    b->rows_mid = 0;
     for (int i = 0; i < nprob; ++i) {
         const mol_grid &g = grids[i];
         const std::string who = "problem " + std::to_string(i) + ": ";
@@ -485,24 +505,28 @@ mol_status plan_batch(mol_batch_ctx *b, int nprob, const mol_grid *grids, const 
         b->Pmax = std::max(b->Pmax, P[i]);
         b->uoff[i + 1] = b->uoff[i] + (int64_t)nx * ny;
     }
-    // internal order: problems with rows of <= 512 points first, so that each
+    // internal order: problems by the length class of their rows, so that each
     // x-pass kernel takes one contiguous range of rows
-    for (int pass = 0; pass < 2; ++pass)
+    for (int pass = 0; pass < 3; ++pass) {
         for (int i = 0; i < nprob; ++i) {
             BatchProb &pb = b->hp[i];
-            if (long_row(pb.ax.n) != (pass == 1)) continue;
+            if (row_class(pb.ax.n) != pass) continue;
             pb.off = off;
             pb.row0 = (int)rows;
             off += ((int64_t)pb.ay.n * pb.pitch + 63) & ~(int64_t)63;
             rows += pb.ay.n;
-            if (pass == 0) b->rows_small = rows;
         }
+        if (pass == 0) b->rows_small = rows;
+        if (pass == 1) b->rows_mid = rows;
+    }
     if (rows > (1ll << 30) || items > (1ll << 30)) return bfail(nullptr, MOL_EINVAL, "batch too large");
     b->total_int = off;
     b->nrows = rows;
     b->nitems_y = (int)items;
     b->xs_smem = batch_xs_smem((size_t)b->tbytes, 16, 2, b->Pmax);
     b->xsplit = b->xs_smem <= (size_t)b->smem_blk ? 1 : 0;
+    b->xs8_smem = batch_xs_smem((size_t)b->tbytes, 8, 2, b->Pmax);
+    b->xmid = b->xs8_smem <= (size_t)b->smem_blk ? 1 : 0;
     set_x_segments(b);
     return MOL_OK;
 }
@@ -858,7 +882,7 @@ mol_status mol_batch_autotune(mol_batch b, void *stream)
         return upload_table(b);
     };
     for (int L = 0; L < 2; ++L) {
-        if ((L == 0 && b->rows_small == 0) || (L == 1 && b->nrows == b->rows_small)) continue;
+        if ((L == 0 && b->one_warp_end() == 0) || (L == 1 && b->nrows == b->rows_mid)) continue;
         int bestW = b->xW[L], bestSplit = b->xsplit;
         double best = 1e30;
         for (int W : {0, 2, 4, 8}) {

@@ -487,10 +487,11 @@ __device__ __forceinline__ void batch_row_split(const BatchProb &pb, const ProgP
 }
 
 // Rows [row_begin, nitems) of the list, one CTA of W warps per row (rows of
-// 32 (W-1) RPT < n <= 32 W RPT points).  Float: ten CTAs per SM (96
-// registers, no spills; 20 warps in flight against 16 at eight CTAs).
+// 32 (W-1) RPT < n <= 32 W RPT points).  Float: ten CTAs per SM at RPT = 16
+// (96 registers, no spills; 20 warps in flight against 16 at eight CTAs),
+// sixteen at RPT = 8 (64 registers).
 template <class T, int RPT, int W, bool ADJ>
-__global__ void __launch_bounds__(32 * W, sizeof(T) == 4 ? 10 : 4) k_batch_xs(BatchPass bp)
+__global__ void __launch_bounds__(32 * W, sizeof(T) == 4 ? (RPT <= 8 ? 16 : 10) : 4) k_batch_xs(BatchPass bp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BatchProb &pb = *reinterpret_cast<BatchProb *>(smem_raw);

@@ -14,10 +14,11 @@
 // and stencils that touch a boundary point take per-line weights computed on
 // the host in float64.
 //
-// The kernel: one warp per line object; the line's values and its two
-// partial sums sit in shared memory; each lane owns a chunk of consecutive
-// nodes, and both recurrences run as chunked scans of affine maps (a lane's
-// chunk maps the inflow y to P y + Q; a 5-step shuffle scan composes them).
+// The kernel: one warp per line object; the line's two partial sums sit in
+// shared memory (the increments overwrite the line's values in place); each
+// lane owns a chunk of consecutive nodes, and both recurrences run as
+// chunked scans of affine maps (a lane's chunk maps the inflow y to P y + Q;
+// a 5-step shuffle scan composes them).
 // Lines of the y axis are rows of the transposed field: the passes move
 // between the layouts with a tiled transpose.
 #include <algorithm>
@@ -71,15 +72,15 @@ __device__ __forceinline__ void affine_scan(double &p, double &q, int lane)
 
 // out[k] (interior node k of every line) = w = L^{-1} in (OBJ_LINV),
 // in - w (OBJ_D) or sub - w (OBJ_SUB); accum adds it to out instead.  slot:
-// shared-memory elements per line array (>= the longest line's m + 2).
+// shared-memory elements per line array (>= the longest line's m + 2; two
+// arrays per warp).
 __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep(ObjAxis ax, const ObjLine *lines, int nlines,
                                                              const double *__restrict__ in, double *out,
                                                              const double *sub, int mode, int accum, int slot)
 {
     extern __shared__ __align__(16) double sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double *U = sm + (size_t)warp * 3 * slot;
-    double *L = U + slot;
+    double *L = sm + (size_t)warp * 2 * slot;
     double *R = L + slot;
     const double d = ax.d;
     for (int li = blockIdx.x * kObjWarps + warp; li < nlines; li += gridDim.x * kObjWarps) {
@@ -88,26 +89,37 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep(ObjAxis ax, const 
         const long long base = ln.base;
         const double dA = ln.dA, dB = ln.dB;
         __syncwarp();
-        for (int k = lane; k <= N; k += 32) U[k] = (k >= 1 && k <= m) ? in[base + k - 1] : 0.0;
-        __syncwarp();
-        // increments; L[k] = J^L_k (k = 1..N, L[0] = 0), R[k] = J^R_k (k = 0..m, R[N] = 0)
-        for (int k = lane; k <= N; k += 32) {
-            double jl = 0.0, jr = 0.0;
-            if (k == 1) jl = ln.wl[2] * U[1] + ln.wl[3] * U[2];
-            else if (k == N) jl = ln.wr[0] * U[m] + ln.wr[1] * U[m - 1];
-            else if (k == m) jl = ln.wr[2] * U[m] + ln.wr[3] * U[m - 1];
-            else if (k > 1) jl = ax.uL[0] * U[k - 1] + ax.uL[1] * U[k] + ax.uL[2] * U[k + 1];
-            if (k == 0) jr = ln.wl[0] * U[1] + ln.wl[1] * U[2];
-            else if (k == 1) jr = ln.wl[4] * U[1] + ln.wl[5] * U[2];
-            else if (k == m) jr = ln.wr[4] * U[m] + ln.wr[5] * U[m - 1];
-            else if (k < m) jr = ax.uR[0] * U[k - 1] + ax.uR[1] * U[k] + ax.uR[2] * U[k + 1];
-            L[k] = jl;
-            R[k] = jr;
-        }
+        // the line's values into R (zero at the boundary points)
+        for (int k = lane; k <= N; k += 32) R[k] = (k >= 1 && k <= m) ? in[base + k - 1] : 0.0;
         __syncwarp();
         // chunk of nodes [k0, k1) of this lane
         const int s = (N + 1 + 31) / 32;
         const int k0 = min(lane * s, N + 1), k1 = min(k0 + s, N + 1);
+        // values the increments need from outside the lane's chunk, read before
+        // any lane overwrites R
+        const double u1 = R[1], u2 = R[2], um = R[m], um1 = R[m - 1];
+        double a = (k0 >= 1 && k0 <= N) ? R[k0 - 1] : 0.0;      // u_{k-1}
+        double b = (k0 <= N) ? R[k0] : 0.0;                     // u_k
+        const double after = (k1 <= N) ? R[k1] : 0.0;          // u_{k1}
+        __syncwarp();
+        // increments, in place: L[k] = J^L_k (L[0] = 0), R[k] = J^R_k (R[N] = 0)
+        for (int k = k0; k < k1; ++k) {
+            const double c = (k + 1 < k1) ? R[k + 1] : after;     // u_{k+1}, not yet overwritten
+            double jl = 0.0, jr = 0.0;
+            if (k == 1) jl = ln.wl[2] * u1 + ln.wl[3] * u2;
+            else if (k == N) jl = ln.wr[0] * um + ln.wr[1] * um1;
+            else if (k == m) jl = ln.wr[2] * um + ln.wr[3] * um1;
+            else if (k > 1) jl = ax.uL[0] * a + ax.uL[1] * b + ax.uL[2] * c;
+            if (k == 0) jr = ln.wl[0] * u1 + ln.wl[1] * u2;
+            else if (k == 1) jr = ln.wl[4] * u1 + ln.wl[5] * u2;
+            else if (k == m) jr = ln.wr[4] * um + ln.wr[5] * um1;
+            else if (k < m) jr = ax.uR[0] * a + ax.uR[1] * b + ax.uR[2] * c;
+            L[k] = jl;
+            R[k] = jr;
+            a = b;
+            b = c;
+        }
+        __syncwarp();
         // causal: I^L_k = e_k I^L_{k-1} + J^L_k, e_1 = dA, e_N = dB, else d
         {
             double p = 1.0, q = 0.0;
@@ -152,7 +164,7 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep(ObjAxis ax, const 
         for (int k = 1 + lane; k <= m; k += 32) {
             const double w = L[k] + R[k] + Acoef * dA * ax.dpow[k - 1] + Bcoef * dB * ax.dpow[m - k];
             double res = w;
-            if (mode == OBJ_D) res = U[k] - w;
+            if (mode == OBJ_D) res = in[base + k - 1] - w;
             else if (mode == OBJ_SUB) res = sub[base + k - 1] - w;
             double *o = out + base + k - 1;
             *o = accum ? *o + res : res;
@@ -601,7 +613,7 @@ mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double
     if (st == MOL_OK) {
         // line arrays sized for the longest line (even, for 16-byte alignment)
         e->slot = (int)((maxm + 2 + 1) & ~(int64_t)1);
-        e->smem = (int)(sizeof(double) * 3 * (size_t)e->slot * kObjWarps);
+        e->smem = (int)(sizeof(double) * 2 * (size_t)e->slot * kObjWarps);
         if ((ce = cudaFuncSetAttribute(k_obj_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem)) !=
             cudaSuccess)
             st = efail(e, MOL_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));

@@ -154,8 +154,10 @@ def test_batch_launches_and_pass_times():
     b.step(u, v, 3)
     b.sync()
     # two level conversions in, two out; per step one y pass and the x pass
-    # (one launch for rows of <= 512 points, one for longer rows)
-    x_launches = int(any(s[1] <= 512 for s in SHAPES)) + int(any(s[1] > 512 for s in SHAPES))
+    # (one launch per length class present: rows of <= 256 points, 257..512,
+    # longer rows)
+    x_launches = (int(any(s[1] <= 256 for s in SHAPES)) + int(any(256 < s[1] <= 512 for s in SHAPES))
+                  + int(any(s[1] > 512 for s in SHAPES)))
     assert b.launches - n0 == 4 + 3 * (1 + x_launches)
     b.set_pass_timing(True)
     b.step(u, v, 2)
