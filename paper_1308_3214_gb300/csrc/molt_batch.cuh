@@ -721,26 +721,6 @@ __device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams
     }
 }
 
-// L2 prefetch of the level rows that column group `item` reads (32 columns of
-// every row; both planes of a pair).  The internal layout makes each row's
-// piece 16-byte aligned: off is a multiple of 64, the pitch of 4, the first
-// column of 32; the piece is rounded up to whole 4-element vectors, which stay
-// inside the padded row.
-template <class T>
-__device__ __forceinline__ void prefetch_cols(const BatchPass &bp, int2 item)
-{
-    const BatchProb *q = bp.probs + item.x;
-    const int ny = __ldg(&q->ay.n), nx = __ldg(&q->ax.n), pitch = __ldg(&q->pitch);
-    const long long off = __ldg(&q->off);
-    const int w = min(32, nx - item.y);
-    const unsigned bytes = (unsigned)(((w + 3) & ~3) * (int)sizeof(T));
-    for (int j = threadIdx.x; j < ny; j += blockDim.x) {
-        const int64_t o = off + (int64_t)j * pitch + item.y;
-        prefetch_l2(reinterpret_cast<const T *>(bp.pr.u_hi) + o, bytes);
-        if (sizeof(T) == 4) prefetch_l2(reinterpret_cast<const T *>(bp.pr.u_lo) + o, bytes);
-    }
-}
-
 // ADJ: powers of D_y^T (the adjoint step) instead of D_y
 template <class T, bool ADJ>
 __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
@@ -766,8 +746,6 @@ __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
         const int2 item = bp.items[it];
         __syncthreads();                               // the previous item is done with pbs and the slots
         if (threadIdx.x < 32) warp_copy(&pbs, bp.probs + item.x, threadIdx.x);
-        // the CTA's next column group streams into L2 while this one sweeps
-        if (it + (int)gridDim.x < bp.nitems) prefetch_cols<T>(bp, bp.items[it + gridDim.x]);
         __syncthreads();
         switch (pbs.rpt_y) {
         case 4: batch_cols<T, 4, ADJ>(pbs, bp.pr, item.y, c, YL); break;
