@@ -373,7 +373,7 @@ mol_status mol_batch_pass_times(mol_batch b, double total_ms[3], int64_t launche
  *
  * Fields: caller-owned device float64 arrays (ny, nx) that vanish outside the
  * domain (outputs vanish there too).  The library owns its tables and work
- * fields (P + 6 fields of nx ny doubles) and frees them in mol_embed_destroy.
+ * fields (P + 4 fields of nx ny doubles) and frees them in mol_embed_destroy.
  * Calls are asynchronous on the given stream; errors are returned statuses
  * (MOL_EINVAL arguments or geometry, MOL_EUNSTABLE beta above beta_max(P),
  * MOL_ENOMEM, MOL_ECUDA), text via mol_embed_last_error.
@@ -408,12 +408,11 @@ mol_status mol_embed_solve_host(mol_embed e, const double *u0, double *u_out, in
 mol_status mol_embed_sync(mol_embed e, void *stream);
 int64_t mol_embed_launch_count(mol_embed e);
 /* Per-kind CUDA-event timing of the launches made while enabled: kind 0 =
- * x line-object sweeps, 1 = y sweeps, 2 = transposes between the row and
- * column layouts, 3 = the linear combinations of F and the level update.
- * mol_embed_pass_times synchronizes, returns the totals since the last call
- * and resets them. */
+ * x line-object sweeps, 1 = y sweeps, 2 = the linear combinations of F and
+ * the level update.  mol_embed_pass_times synchronizes, returns the totals
+ * since the last call and resets them. */
 mol_status mol_embed_set_pass_timing(mol_embed e, int enable);
-mol_status mol_embed_pass_times(mol_embed e, double total_ms[4], int64_t launches[4]);
+mol_status mol_embed_pass_times(mol_embed e, double total_ms[3], int64_t launches[3]);
 
 /*
  * F = F[u] in float64 (the operator of eq. update_P / Full_2D, as

@@ -19,8 +19,9 @@
 // lane owns a chunk of consecutive nodes, and both recurrences run as
 // chunked scans of affine maps (a lane's chunk maps the inflow y to P y + Q;
 // a 5-step shuffle scan composes them).
-// Lines of the y axis are rows of the transposed field: the passes move
-// between the layouts with a tiled transpose.
+// A line is read and written in place in the caller's layout: x lines with
+// stride 1, y lines with stride nx (the 4 warps of a CTA take 4 neighbouring
+// columns, which share the 32-byte sectors of each row).
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -45,6 +46,7 @@ struct ObjLine {
 };
 
 struct ObjAxis {
+    long long stride;   // element stride along the lines (1 for x, nx for y)
     double d;           // e^{-alpha h}
     double uL[3];       // uniform J^L_k weights on (u_{k-1}, u_k, u_{k+1})
     double uR[3];       // uniform J^R_k weights on (u_{k-1}, u_k, u_{k+1})
@@ -90,7 +92,8 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep(ObjAxis ax, const 
         const double dA = ln.dA, dB = ln.dB;
         __syncwarp();
         // the line's values into R (zero at the boundary points)
-        for (int k = lane; k <= N; k += 32) R[k] = (k >= 1 && k <= m) ? in[base + k - 1] : 0.0;
+        const long long st = ax.stride;
+        for (int k = lane; k <= N; k += 32) R[k] = (k >= 1 && k <= m) ? in[base + (k - 1) * st] : 0.0;
         __syncwarp();
         // chunk of nodes [k0, k1) of this lane
         const int s = (N + 1 + 31) / 32;
@@ -164,31 +167,11 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep(ObjAxis ax, const 
         for (int k = 1 + lane; k <= m; k += 32) {
             const double w = L[k] + R[k] + Acoef * dA * ax.dpow[k - 1] + Bcoef * dB * ax.dpow[m - k];
             double res = w;
-            if (mode == OBJ_D) res = in[base + k - 1] - w;
-            else if (mode == OBJ_SUB) res = sub[base + k - 1] - w;
-            double *o = out + base + k - 1;
+            const long long at = base + (k - 1) * st;
+            if (mode == OBJ_D) res = in[at] - w;
+            else if (mode == OBJ_SUB) res = sub[at] - w;
+            double *o = out + at;
             *o = accum ? *o + res : res;
-        }
-    }
-}
-
-// out (nx rows of ny) = in (ny rows of nx) transposed; accum adds
-__global__ void __launch_bounds__(256) k_obj_transpose(const double *__restrict__ in, double *out, int64_t ny,
-                                                      int64_t nx, int accum)
-{
-    __shared__ double tile[32][33];
-    const int64_t x0 = (int64_t)blockIdx.x * 32, y0 = (int64_t)blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t y = y0 + r, x = x0 + threadIdx.x;
-        tile[r][threadIdx.x] = (y < ny && x < nx) ? in[y * nx + x] : 0.0;
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t x = x0 + r, y = y0 + threadIdx.x;
-        if (x < nx && y < ny) {
-            double *o = out + x * ny + y;
-            const double v = tile[threadIdx.x][r];
-            *o = accum ? *o + v : v;
         }
     }
 }
@@ -304,18 +287,18 @@ struct mol_embed_ctx {
     double hx = 0, hy = 0, alpha = 0, beta = 0;
     int P = 1;
     std::vector<double> tw;             // weights of C^m D^{p-m}: tw[p * 8 + m]
-    ObjAxis ax[2]{};                    // x lines (rows), y lines (rows of the transposed field)
+    ObjAxis ax[2]{};                    // x lines (rows), y lines (columns)
     ObjLine *lines[2] = {nullptr, nullptr};
     int nlines[2] = {0, 0};
     double *dpow[2] = {nullptr, nullptr};
     double *V[kMaxP + 1] = {};          // V[1..P]: the Table 3 auxiliaries
-    double *tmp = nullptr, *t1 = nullptr, *aT = nullptr, *bT = nullptr, *lev = nullptr, *Fb = nullptr;
+    double *tmp = nullptr, *t1 = nullptr, *lev = nullptr, *Fb = nullptr;
     double *io[2] = {nullptr, nullptr}; // device copies of mol_embed_solve_host
     std::vector<void *> allocs;
     int smem = 0, grid = 1, slot = 2;     // sweep launch: shared memory, CTAs, elements per line array
     int64_t launches = 0;
     std::string err;
-    bool timing = false;                // per-kind CUDA events (0 x sweeps, 1 y sweeps, 2 transposes, 3 combines)
+    bool timing = false;                // per-kind CUDA events (0 x sweeps, 1 y sweeps, 2 combinations)
     std::vector<cudaEvent_t> ev_pool;
     struct Rec { int kind; cudaEvent_t a, b; };
     std::vector<Rec> recs;
@@ -389,7 +372,7 @@ struct Timed {
     }
 };
 
-// one sweep along axis a (0: rows of the field, 1: rows of the transposed field)
+// one sweep along axis a (0: the rows, 1: the columns of the field)
 mol_status sweep(mol_embed_ctx *e, int a, const double *in, double *out, int mode, int accum, const double *sub,
                  cudaStream_t s)
 {
@@ -403,22 +386,10 @@ mol_status sweep(mol_embed_ctx *e, int a, const double *in, double *out, int mod
     return MOL_OK;
 }
 
-// out = in^T; in has `rows` rows of `cols`
-mol_status transpose(mol_embed_ctx *e, const double *in, double *out, int64_t rows, int64_t cols, int accum,
-                     cudaStream_t s)
-{
-    dim3 g((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-    Timed t(e, 2, s);
-    k_obj_transpose<<<g, dim3(32, 8), 0, s>>>(in, out, rows, cols, accum);
-    ++e->launches;
-    ECK(cudaGetLastError(), "transpose");
-    return MOL_OK;
-}
-
 mol_status combine(mol_embed_ctx *e, const CombTerms &t, double *out, cudaStream_t s)
 {
     const int64_t blocks = std::min<int64_t>((e->N + 255) / 256, 4096);
-    Timed tm(e, 3, s);
+    Timed tm(e, 2, s);
     k_obj_combine<<<(unsigned)blocks, 256, 0, s>>>(t, out, e->N);
     ++e->launches;
     ECK(cudaGetLastError(), "combine");
@@ -431,27 +402,19 @@ mol_status combine(mol_embed_ctx *e, const CombTerms &t, double *out, cudaStream
         if (st_ != MOL_OK) return st_;         \
     } while (0)
 
-// axis-1 operator on a field in the normal layout: out = Op_y(v) (+ out)
-mol_status sweep_y(mol_embed_ctx *e, const double *v, double *out, int mode, int accum, cudaStream_t s)
-{
-    EST(transpose(e, v, e->aT, e->ny, e->nx, 0, s));
-    EST(sweep(e, 1, e->aT, e->bT, mode, 0, nullptr, s));
-    return transpose(e, e->bT, out, e->nx, e->ny, accum, s);
-}
-
 // out = C v = L_y^{-1} D_x v + L_x^{-1} D_y v   (eq. C_def_ADI)
 mol_status apply_C(mol_embed_ctx *e, const double *v, double *out, cudaStream_t s)
 {
     EST(sweep(e, 0, v, e->t1, OBJ_D, 0, nullptr, s));          // t1 = D_x v
-    EST(sweep_y(e, e->t1, out, OBJ_LINV, 0, s));               // out = L_y^{-1} t1
-    EST(sweep_y(e, v, e->t1, OBJ_D, 0, s));                    // t1 = D_y v
+    EST(sweep(e, 1, e->t1, out, OBJ_LINV, 0, nullptr, s));     // out = L_y^{-1} t1
+    EST(sweep(e, 1, v, e->t1, OBJ_D, 0, nullptr, s));          // t1 = D_y v
     return sweep(e, 0, e->t1, out, OBJ_LINV, 1, nullptr, s);   // out += L_x^{-1} t1
 }
 
 // out = D v = v - L_x^{-1} L_y^{-1} v   (eq. D_def_ADI)
 mol_status apply_Dadi(mol_embed_ctx *e, const double *v, double *out, cudaStream_t s)
 {
-    EST(sweep_y(e, v, e->t1, OBJ_LINV, 0, s));                 // t1 = L_y^{-1} v
+    EST(sweep(e, 1, v, e->t1, OBJ_LINV, 0, nullptr, s));       // t1 = L_y^{-1} v
     return sweep(e, 0, e->t1, out, OBJ_SUB, 0, v, s);          // out = v - L_x^{-1} t1
 }
 
@@ -565,6 +528,7 @@ mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double
     for (int a = 0; a < 2 && st == MOL_OK; ++a) {
         const double h = a == 0 ? e->hx : e->hy, alpha = e->alpha;
         ObjAxis &X = e->ax[a];
+        X.stride = a == 0 ? 1 : nx;
         X.d = std::exp(-alpha * h);
         double w[3];
         const double sL[3] = {h, 0.0, -h}, sR[3] = {-h, 0.0, h};
@@ -575,11 +539,14 @@ mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double
         std::vector<double> tab(kObjMaxM + 1);
         for (int k = 0; k <= kObjMaxM; ++k) tab[k] = std::exp(-alpha * h * (double)k);
         std::vector<ObjLine> ls;
-        const int64_t nl = a == 0 ? ny : nx, len = a == 0 ? nx : ny;
+        const int64_t nl = a == 0 ? ny : nx;
         const int64_t *lo = a == 0 ? g->row_lo : g->col_lo, *hi = a == 0 ? g->row_hi : g->col_hi;
         const double *ga = a == 0 ? g->row_gap_lo : g->col_gap_lo, *gb = a == 0 ? g->row_gap_hi : g->col_gap_hi;
-        for (int64_t l = 0; l < nl; ++l)
-            if (lo[l] <= hi[l]) ls.push_back(make_line(l * len + lo[l], (int)(hi[l] - lo[l] + 1), h, ga[l], gb[l], alpha));
+        for (int64_t l = 0; l < nl; ++l) {
+            if (lo[l] > hi[l]) continue;
+            const long long base = a == 0 ? l * nx + lo[l] : lo[l] * nx + l;   // first interior node
+            ls.push_back(make_line(base, (int)(hi[l] - lo[l] + 1), h, ga[l], gb[l], alpha));
+        }
         e->nlines[a] = (int)ls.size();
         if ((st = ealloc(e, (void **)&e->dpow[a], sizeof(double) * tab.size())) != MOL_OK) break;
         if ((ce = cudaMemcpy(e->dpow[a], tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -597,7 +564,7 @@ mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double
         }
     }
     const size_t plane = sizeof(double) * (size_t)e->N;
-    double **bufs[] = {&e->tmp, &e->t1, &e->aT, &e->bT, &e->lev, &e->Fb};
+    double **bufs[] = {&e->tmp, &e->t1, &e->lev, &e->Fb};
     for (double **b : bufs)
         if (st == MOL_OK) st = ealloc(e, (void **)b, plane);
     for (int k = 1; k <= P && st == MOL_OK; ++k) st = ealloc(e, (void **)&e->V[k], plane);
@@ -655,8 +622,7 @@ mol_status mol_embed_linv(mol_embed e, const double *v, double *w, int axis, voi
     if (v == w) return efail(e, MOL_EINVAL, "v and w must not overlap");
     cudaStream_t s = (cudaStream_t)stream;
     ECK(cudaMemsetAsync(w, 0, sizeof(double) * (size_t)e->N, s), "memset");
-    if (axis == 0) return sweep(e, 0, v, w, OBJ_LINV, 0, nullptr, s);
-    return sweep_y(e, v, w, OBJ_LINV, 0, s);
+    return sweep(e, axis, v, w, OBJ_LINV, 0, nullptr, s);
 }
 
 mol_status mol_embed_apply_F(mol_embed e, const double *u, double *F, void *stream)
@@ -743,11 +709,11 @@ mol_status mol_embed_set_pass_timing(mol_embed e, int enable)
     return MOL_OK;
 }
 
-mol_status mol_embed_pass_times(mol_embed e, double total_ms[4], int64_t launches[4])
+mol_status mol_embed_pass_times(mol_embed e, double total_ms[3], int64_t launches[3])
 {
     if (!e) return efail(nullptr, MOL_EINVAL, "handle is NULL");
     if (!total_ms || !launches) return efail(e, MOL_EINVAL, "output arrays must not be NULL");
-    for (int k = 0; k < 4; ++k) { total_ms[k] = 0.0; launches[k] = 0; }
+    for (int k = 0; k < 3; ++k) { total_ms[k] = 0.0; launches[k] = 0; }
     for (auto &r : e->recs) {
         float ms = 0.f;
         cudaError_t ce = cudaEventSynchronize(r.b);

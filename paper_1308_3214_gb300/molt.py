@@ -674,12 +674,12 @@ class EmbedSolver:
 
     def pass_times(self):
         """{kind: (total ms, launches)} since the last call: x_sweep, y_sweep,
-        transpose, combine."""
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_int64 * 4)()
+        combine."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
         self._check(self.lib.mol_embed_pass_times(self.h, ms, n))
-        names = ("x_sweep", "y_sweep", "transpose", "combine")
-        return {names[k]: (float(ms[k]), int(n[k])) for k in range(4)}
+        names = ("x_sweep", "y_sweep", "combine")
+        return {names[k]: (float(ms[k]), int(n[k])) for k in range(3)}
 
     @property
     def launches(self) -> int:
