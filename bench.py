@@ -236,6 +236,9 @@ def cpu_oracle_rate(spec: dict, budget_s: float, max_steps: int | None = None, m
     s = max(min_side, int(round(pts ** (1.0 / nd))))
     s = min(s, side)
     shape = (s,) * nd if pts < full else tuple(spec["shape"])
+    if max_steps is None and pts >= full:
+        # the whole field fits: spend the budget on steps of it (at most 50)
+        steps = int(max(3, min(50, rate * budget_s / (2.0 * full))))
     u0 = sample_field(spec, shape)
     u1 = oracle.start(u0, nu, P, beta, bc)
     t0 = time.perf_counter()
