@@ -911,11 +911,11 @@ def main_embedded(args, spec):
     hbm_achieved = bpp * npts * kt / (sweep_ms * 1e-3) / 1e9
     # float64 operations of the sweep per interior node (a node between grid
     # nodes): two 3-point increments (2 x 5 flops), each recurrence's chunk
-    # reduction (FMA + multiply, 3 flops) and re-scan (FMA, 2 flops) in both
-    # directions (10), the homogeneous terms and the sum (9): 29 flops.  The
+    # reduction (FMA, 2 flops) and re-scan (FMA, 2 flops) in both directions
+    # (8), the homogeneous terms and the sum (9): 27 flops.  The
     # peak is the nominal float64 rate of a GB300 (1.25 TFLOP/s): the sweeps
     # are bound by the narrow float64 pipe, not by HBM.
-    flops = 29.0 * npts * sweep_launches
+    flops = 27.0 * npts * sweep_launches
     achieved = flops / (sweep_ms * 1e-3) / 1e9
     line = {"metric": METRIC, "value": npts * K / (ms * 1e-3), "unit": METRIC, "n_gpus": 1, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -929,7 +929,7 @@ def main_embedded(args, spec):
                          "traffic": read_traffic(0, spec["name"], "fp64", "embed"),
                          "peak_kind": "nominal float64 rate of a GB300 (no measured float64 peak on this pool)",
                          "kernel": "k_obj_sweep (all line-object sweeps of a step; float64 recurrences)",
-                         "flops_per_node_sweep": 29, "hbm": {"achieved_GBps": hbm_achieved, "peak": hbm_peak,
+                         "flops_per_node_sweep": 27, "hbm": {"achieved_GBps": hbm_achieved, "peak": hbm_peak,
                                                               "frac": hbm_achieved / hbm_peak,
                                                               "alg_bytes_per_point_step": bpp},
                          "kinds_ms_per_step": {k: v[0] / kt for k, v in kinds.items()},

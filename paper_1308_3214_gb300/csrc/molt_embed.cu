@@ -40,6 +40,7 @@ struct ObjLine {
     int m;              // interior nodes
     int pad_;
     double dA, dB;      // e^{-alpha ga}, e^{-alpha gb}
+    double rA, rB;      // dA / d, dB / d (d = e^{-alpha h})
     double mu, inv;     // e^{-alpha (b - a)}, 1 / (1 - mu^2)
     double wl[6];       // J^R_0, J^L_1, J^R_1 as weights on (u_1, u_2)
     double wr[6];       // J^L_{m+1}, J^L_m, J^R_m as weights on (u_m, u_{m-1})
@@ -123,14 +124,17 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep(ObjAxis ax, const 
             b = c;
         }
         __syncwarp();
-        // causal: I^L_k = e_k I^L_{k-1} + J^L_k, e_1 = dA, e_N = dB, else d
+        // causal: I^L_k = e_k I^L_{k-1} + J^L_k, e_1 = dA, e_N = dB, else d; the
+        // chunk's decay is d^{k1-k0} with the end cells' factors swapped in
         {
-            double p = 1.0, q = 0.0;
+            double q = 0.0;
             for (int k = k0; k < k1; ++k) {
                 const double e = (k == 1) ? dA : (k == N ? dB : d);
                 q = e * q + L[k];
-                p = e * p;
             }
+            double p = ax.dpow[k1 - k0];
+            if (k0 <= 1 && 1 < k1) p *= ln.rA;
+            if (k0 <= N && N < k1) p *= ln.rB;
             affine_scan<true>(p, q, lane);
             double y = __shfl_up_sync(0xffffffffu, q, 1);
             y = (lane == 0) ? 0.0 : y;
@@ -141,14 +145,17 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep(ObjAxis ax, const 
             }
         }
         // anti-causal: I^R_k = f_k I^R_{k+1} + J^R_k, f_0 = dA, f_m = dB, else d
+        // (the chunk holding N passes no inflow on: every later chunk is empty)
         {
-            double p = 1.0, q = 0.0;
+            double q = 0.0;
             for (int k = k1 - 1; k >= k0; --k) {
                 const double f = (k == 0) ? dA : (k == m ? dB : d);
                 const double r = (k == N) ? 0.0 : R[k];
                 q = f * q + r;
-                p = f * p;
             }
+            double p = ax.dpow[k1 - k0];
+            if (k0 <= 0 && 0 < k1) p *= ln.rA;
+            if (k0 <= m && m < k1) p *= ln.rB;
             affine_scan<false>(p, q, lane);
             double y = __shfl_down_sync(0xffffffffu, q, 1);
             y = (lane == 31) ? 0.0 : y;
@@ -242,6 +249,8 @@ ObjLine make_line(long long base, int m, double h, double ga, double gb, double 
     const double xm1 = (m >= 2) ? xm - h : 0.0;           // node m - 1 (a itself when m = 1)
     L.dA = std::exp(-alpha * ga);
     L.dB = std::exp(-alpha * gb);
+    L.rA = std::exp(-alpha * (ga - h));
+    L.rB = std::exp(-alpha * (gb - h));
     L.mu = std::exp(-alpha * b);
     L.inv = 1.0 / (-std::expm1(-2.0 * alpha * b));
     double w[3];
