@@ -212,6 +212,58 @@ def dist_setup():
     return world, rank, local
 
 
+class RankGroup:
+    """One process per GPU (the env vars of torch.distributed.run).  With more
+    than one rank: a process group (NCCL on GPUs; gloo on the CPU, where the
+    tests drive this class), a barrier, and the reductions the JSON line needs:
+    the maximum of the ranks' times and the sum of their points.  With one
+    rank every call is the identity."""
+
+    def __init__(self, backend: str | None = None):
+        self.world, self.rank, self.local = dist_setup()
+        self.device = "cpu"
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = backend or ("nccl" if torch.cuda.is_available() else "gloo")
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+                self.device = "cuda"
+            else:
+                dist.init_process_group("gloo")
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def _reduce(self, x: float, op: str) -> float:
+        if self.world == 1:
+            return float(x)
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, "max")
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, "sum")
+
+    def close(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+def aggregate_rate(group: RankGroup, points: float, seconds: float) -> float:
+    """Whole-job rate: the points all ranks processed over the slowest rank's time."""
+    return group.sum(points) / group.max(seconds)
+
+
 def cpu_oracle_rate(spec: dict, budget_s: float, max_steps: int | None = None, min_side: int = 64):
     """Point-updates/s of the FP64 oracle on a bounded sample of the workload:
     the full field when one step fits the budget, else a smaller grid with the
@@ -339,27 +391,12 @@ def main():
     import torch
     from paper_1308_3214_gb300 import molt
 
-    world, rank, local = dist_setup()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+    group = RankGroup()
+    world, rank = group.world, group.rank
+    if world == 1:
         torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = group.barrier, group.max
 
     shape, P = spec["shape"], spec["P"]
     N = int(np.prod(shape))
@@ -416,8 +453,8 @@ def main():
     sampler = ClockSampler(bus).start()
     ms, launches, passes, ms_b = timed_steps(solver, args.steps, args.warmup)
     clocks = sampler.stop()
+    value = aggregate_rate(group, N * args.steps, ms * 1e-3)
     ms = max_over_ranks(ms)
-    value = world * N * args.steps / (ms * 1e-3)
 
     # roofline of the dominant pass
     bpp = bytes_per_point(spec, args.prec)
@@ -479,8 +516,9 @@ def main():
         for _ in range(calls):
             solver.solve_host(pin_in.numpy(), per_call, out=pin_out.numpy())
         torch.cuda.synchronize()
-        e2e_s = max_over_ranks(time.perf_counter() - t0)
-        line["e2e"] = {"value": world * N * per_call * calls / e2e_s, "unit": METRIC,
+        e2e_el = time.perf_counter() - t0
+        e2e_value = aggregate_rate(group, N * per_call * calls, e2e_el)
+        line["e2e"] = {"value": e2e_value, "unit": METRIC,
                        "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
                        "step": f"one mol_solve_host call: copy u0 in, start + {per_call - 1} steps, copy u out",
                        "time_steps_per_step": per_call}
@@ -493,9 +531,7 @@ def main():
     solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    group.close()
 
 
 # ---------------------------------------------------------------------------
@@ -559,26 +595,11 @@ def main_batch(args, spec):
 
     import torch
     from paper_1308_3214_gb300 import molt
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+    group = RankGroup()
+    if world == 1:
         torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = group.barrier, group.max
 
     probs, shapes, dts, Ps = batch_set(spec, rank)
     npts = sum(n * n for n, _ in shapes)
@@ -632,8 +653,8 @@ def main_batch(args, spec):
     sampler = ClockSampler(bus).start()
     ms, launches, passes, ms_b, _ = timed(b, args.steps, args.warmup)
     clocks = sampler.stop()
+    value = aggregate_rate(group, npts * args.steps, ms * 1e-3)
     ms = max_over_ranks(ms)
-    value = world * npts * args.steps / (ms * 1e-3)
     peak, peak_kind = read_peak()
     dom_axis = max(passes, key=lambda a: passes[a][0])
     dom_ms = passes[dom_axis][0] / passes[dom_axis][1]
@@ -689,8 +710,9 @@ def main_batch(args, spec):
         for _ in range(calls):
             b.solve_host(pin_in.numpy(), per_call, out=pin_out.numpy())
         torch.cuda.synchronize()
-        e2e_s = max_over_ranks(time.perf_counter() - t0)
-        line["e2e"] = {"value": world * npts * per_call * calls / e2e_s, "unit": METRIC,
+        e2e_el = time.perf_counter() - t0
+        e2e_value = aggregate_rate(group, npts * per_call * calls, e2e_el)
+        line["e2e"] = {"value": e2e_value, "unit": METRIC,
                        "h2d_bytes_per_step": 8 * npts, "d2h_bytes_per_step": 8 * npts,
                        "step": f"one mol_batch_solve_host call: copy u0 in, start + {per_call - 1} steps, copy u out",
                        "time_steps_per_step": per_call}
@@ -703,9 +725,7 @@ def main_batch(args, spec):
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    group.close()
 
 
 # ---------------------------------------------------------------------------
@@ -996,26 +1016,11 @@ def main_adjoint(args, spec):
 
     import torch
     from paper_1308_3214_gb300 import molt
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+    group = RankGroup()
+    if world == 1:
         torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier, max_over_ranks = group.barrier, group.max
 
     u0h, uth, rec = adjoint_problem(spec, 7919 * rank)
     N = args.steps                                   # adjoint steps timed
@@ -1043,7 +1048,8 @@ def main_adjoint(args, spec):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms_rank = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms_rank)
     launches = b.launches - l0
     # per-pass device times of the adjoint passes
     b.set_pass_timing(True)
@@ -1051,7 +1057,7 @@ def main_adjoint(args, spec):
     passes = b.pass_times()
     b.set_pass_timing(False)
     pts = n * n
-    value = world * pts * N / (ms * 1e-3)
+    value = aggregate_rate(group, pts * N, ms_rank * 1e-3)
     t = 4 if args.prec == "mixed" else 8
     bpp = {1: 8 + t * P, 0: t * P + 24}
     dom_axis = max(passes, key=lambda a: passes[a][0])
@@ -1110,8 +1116,8 @@ def main_adjoint(args, spec):
         for _ in range(calls):
             job()
         torch.cuda.synchronize()
-        el = max_over_ranks(time.perf_counter() - t0)
-        line["e2e"] = {"value": world * pts * nsteps * calls / el, "unit": METRIC,
+        el = time.perf_counter() - t0
+        line["e2e"] = {"value": aggregate_rate(group, pts * nsteps * calls, el), "unit": METRIC,
                        "h2d_bytes_per_step": 8 * pts, "d2h_bytes_per_step": 8 * pts + 8,
                        "step": f"one gradient: copy u0 in, {nsteps} forward steps with traces, loss, "
                                f"{nsteps} adjoint steps, copy the gradient out (counted as {nsteps} point-updates)",
@@ -1133,9 +1139,7 @@ def main_adjoint(args, spec):
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    group.close()
 
 
 def batch_accuracy(spec, probs, shapes, dts, Ps, make, molt, torch, sample: int = 6):
