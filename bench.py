@@ -1025,7 +1025,7 @@ def main_adjoint(args, spec):
     u0h, uth, rec = adjoint_problem(spec, 7919 * rank)
     N = args.steps                                   # adjoint steps timed
     b = molt.Solver((n, n), dt=dt, P=P, bc="dirichlet", prec=args.prec)
-    b.autotune()
+    tuning = b.autotune()
     u0 = torch.from_numpy(u0h).cuda()
     d = b.traces(torch.from_numpy(uth).cuda(), rec, max(N, nsteps))
     res = b.traces(u0, rec, max(N, nsteps)) - d
@@ -1079,7 +1079,7 @@ def main_adjoint(args, spec):
             "config": {"workload": spec["name"], "shape": [n, n], "P": P, "cfl": spec["cfl"], "receivers": int(rec.size),
                        "prec": args.prec, "step": "one adjoint step: mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n",
                        "l2": "no flush: per-step working set exceeds the 129 MB L2",
-                       "parallelism": f"{world} rank(s), each its own problem"},
+                       "parallelism": f"{world} rank(s), each its own problem", "tuning": tuning},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
     # gradient check and mixed-vs-fp64 comparison of the full workload gradient
     if rank == 0 and not args.no_accuracy:
