@@ -193,3 +193,28 @@ def test_ellipse_grid_is_consistent():
     X, Y = np.meshgrid(x, y)
     inside = ((X + Y) / 4) ** 2 + (X - Y) ** 2 < 1.0
     assert (g.mask <= inside).all() and (inside & ~g.mask).sum() == 0
+
+
+def test_disk_time_convergence_at_fixed_fine_grid():
+    """The same standing mode on a 201^2 grid (h = 0.011) with 4..16 steps to
+    t = 0.5 (CFL 11 down to 2.8): the second-order scheme converges at order
+    2 in dt; the fourth-order one starts at order 3 or more at the largest
+    steps and is 8 times or more as accurate, until both meet the spatial
+    error of the boundary cells."""
+    k = scipy_special.jn_zeros(0, 1)[0]
+    g = workloads.disk_grid(201)
+    x, y = g.coords()
+    r = np.hypot(*np.meshgrid(x, y))
+    u0 = np.where(g.mask, scipy_special.j0(k * r), 0.0)
+    T = 0.5
+    ex = np.where(g.mask, scipy_special.j0(k * r) * np.cos(k * T), 0.0)
+    errs = {}
+    for P in (1, 2):
+        beta = oracle.beta_max(P)
+        errs[P] = np.array([np.sqrt(g.hx * g.hy * np.sum(
+            (oracle.run_embed(u0, ns, g, beta / (T / ns), P, beta) - ex) ** 2)) for ns in (4, 8, 16)])
+    r1 = np.log2(errs[1][:-1] / errs[1][1:])
+    r2 = np.log2(errs[2][:-1] / errs[2][1:])
+    assert r1.min() > 1.9, (errs[1], r1)
+    assert r2[0] > 3.0, (errs[2], r2)
+    assert (errs[1] / errs[2]).min() > 8.0
