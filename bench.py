@@ -94,8 +94,10 @@ def workload_spec(name: str) -> dict:
 
 
 def bytes_per_point(spec: dict, prec: str) -> dict:
-    """Algorithmic HBM bytes per point and step of each pass:
-    every field read or written once per pass, levels as 8-byte pairs/doubles."""
+    """Algorithmic HBM bytes per point and step of each pass: every field read
+    or written once per pass, levels as 8-byte pairs/doubles (2D: the y pass
+    reads u and writes the P fields D_y^k u, the x pass reads them, u and
+    u^{n-1} and writes u^{n+1})."""
     P, nd = spec["P"], len(spec["shape"])
     t = 4 if prec == "mixed" else 8
     if nd == 1:

@@ -1,4 +1,4 @@
-"""Pins of the oracle's source terms (Sec. 4.1; readings in the design doc).
+"""Pins of the oracle's source terms (Sec. 4.1).
 
 * C in 1D is D, and in 2D it equals D_x v + D_y v - D_y D_x v - D_x D_y v
   (L^{-1} = 1 - D), composed here from the per-axis D;
@@ -7,7 +7,7 @@
 * the manufactured solution u = sin(pi x) sin(pi y) cos(w t) (source
   S = (2 pi^2 - w^2) sin(pi x) sin(pi y) cos(w t)) is reached at order 2 for
   P = 1 and 4 for P = 2 -- which fixes the sign and scale of the C[S] term
-  (the printed form does not reach fourth order, see the reading);
+  (the printed form does not reach fourth order);
 * P = 3 is refused (no higher-order source terms are given).
 """
 import numpy as np
