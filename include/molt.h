@@ -369,11 +369,12 @@ mol_status mol_batch_pass_times(mol_batch b, double total_ms[3], int64_t launche
  * vanish at both boundary points.  The scheme is eq. (Full_2D) with C and D of
  * eqs. (C_def_ADI), (D_def_ADI) built from these operators, its terms formed
  * in the order of Table 3: on a curved domain the x and y operators do not
- * commute, so the order is part of the scheme.  Float64 throughout.
+ * commute, so the order is part of the scheme.
  *
  * Fields: caller-owned device float64 arrays (ny, nx) that vanish outside the
  * domain (outputs vanish there too).  The library owns its tables and work
- * fields (P + 4 fields of nx ny doubles) and frees them in mol_embed_destroy.
+ * fields (P + 4 fields of nx ny doubles; mixed: P + 10 of floats) and frees
+ * them in mol_embed_destroy.
  * Calls are asynchronous on the given stream; errors are returned statuses
  * (MOL_EINVAL arguments or geometry, MOL_EUNSTABLE beta above beta_max(P),
  * MOL_ENOMEM, MOL_ECUDA), text via mol_embed_last_error.
@@ -389,8 +390,13 @@ typedef struct {
 
 typedef struct mol_embed_ctx *mol_embed;
 
-/* alpha = beta / (c dt) (eq. L_def); beta <= 0 selects beta_max(P); P in 1..5. */
-mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double beta, int P, mol_embed *out);
+/* alpha = beta / (c dt) (eq. L_def); beta <= 0 selects beta_max(P); P in 1..5.
+ * prec MOL_FP64: float64 sweeps.  MOL_MIXED: float32 sweeps in the difference
+ * form of D (the line object's rows 1 and N-1 with their own weights on the
+ * second divided differences of the end triples), the time levels as
+ * float32 pairs; the caller's fields stay float64 (converted once per call). */
+mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double beta, int P, mol_prec prec,
+                            mol_embed *out);
 mol_status mol_embed_destroy(mol_embed e);
 /* Message of the last failed call on e (that of mol_last_error(NULL) if e is NULL). */
 const char *mol_embed_last_error(mol_embed e);

@@ -73,6 +73,21 @@ __device__ __forceinline__ void affine_scan(double &p, double &q, int lane)
     }
 }
 
+template <bool FWD>
+__device__ __forceinline__ void affine_scan32(float &p, float &q, int lane)
+{
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const float pp = FWD ? __shfl_up_sync(0xffffffffu, p, k) : __shfl_down_sync(0xffffffffu, p, k);
+        const float qq = FWD ? __shfl_up_sync(0xffffffffu, q, k) : __shfl_down_sync(0xffffffffu, q, k);
+        const bool take = FWD ? lane >= k : lane + k < 32;
+        if (take) {
+            q = qq * p + q;
+            p = pp * p;
+        }
+    }
+}
+
 // out[k] (interior node k of every line) = w = L^{-1} in (OBJ_LINV),
 // in - w (OBJ_D) or sub - w (OBJ_SUB); accum adds it to out instead.  slot:
 // shared-memory elements per line array (>= the longest line's m + 2; two
@@ -201,6 +216,185 @@ __global__ void __launch_bounds__(256) k_obj_combine(CombTerms t, double *out, i
 }
 
 // ---------------------------------------------------------------------------
+// float32 sweeps: the difference form of D on a line object
+// ---------------------------------------------------------------------------
+// With g_k the decay of cell k (between x_{k-1} and x_k) and e = D v, the two
+// recurrences and the boundary terms give, at every interior node k = 1..N-1,
+//   T_k - g_{k+1} T_{k+1} = q_k,   T_k = (e_k - g_k e_{k-1}) / (1 - g_k^2),
+// with e = 0 at both boundary points; q_k is local in v and vanishes on
+// linear data, so it is a combination of second divided differences:
+//   q_k = ge s_{k-1} + gc s_k + ge s_{k+1} on the uniform interior
+//   (s_t = v_{t-1} - 2 v_t + v_{t+1}, the divided difference times h^2), and
+//   two per-line coefficients on rows 1 and N-1, whose end triples (a, x_1,
+//   x_2) and (x_{m-1}, x_m, b) have their own spacings.
+// The anti-causal recurrence gives T from T_N = 0, the causal one e from
+// e_0 = 0, and the homogeneous solutions A' e^{-alpha (x - a)} + B'
+// e^{-alpha (b - x)} restore e_N = 0.  D v then never subtracts two nearly
+// equal numbers, so float32 sweeps keep their accuracy (D v << v for smooth
+// fields); the input's second differences come from float32 pairs when the
+// input is a time level.
+struct ObjLineF {
+    long long base;     // element index of the first interior node
+    int m, pad_;
+    float dA, dB;       // decays of the end cells
+    float rA, rB;       // dA / d, dB / d
+    float cA, cB;       // 1 - dA^2, 1 - dB^2
+    float mu, inv;      // e^{-alpha (b - a)}, 1 / (1 - mu^2)
+    float g11, g12;     // row 1: q_1 = g11 s_1 + g12 s_2
+    float gNa, gNb;     // row N-1: q_m = gNa s_{m-1} + gNb s_m
+    float p1, q1;       // s_1 = p1 (v_2 - v_1) - q1 v_1 (v_2 = 0 when m = 1)
+    float pm, qm;       // s_m = pm (0 - v_m) - qm (v_m - v_{m-1})
+};
+
+struct ObjAxisF {
+    long long stride;
+    float d, c;         // e^{-alpha h}, 1 - d^2
+    float gc, ge;       // uniform rows
+    const float *dpow;  // d^k
+};
+
+enum : int { OBJF_D = 0, OBJF_LINV = 1, OBJF_BOTH = 2 };
+
+// MODE OBJF_D: out = D v; OBJF_LINV: out = v - D v (= L^{-1} v); OBJF_BOTH:
+// out = D v and out2 = v - D v.  accum adds to out.  PAIR: v is a float32
+// pair level (in = hi, lo = lo plane), else a float32 field.
+template <bool PAIR>
+__global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep32(ObjAxisF ax, const ObjLineF *lines, int nlines,
+                                                               const float *__restrict__ in, const float *__restrict__ lo,
+                                                               float *out, float *out2, int mode, int accum, int slot)
+{
+    extern __shared__ __align__(16) float smf[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *H = smf + (size_t)warp * 4 * slot;     // values (hi plane)
+    float *Lo = H + slot;                         // lo plane (PAIR)
+    float *S = Lo + slot;                         // second differences s_t
+    float *Q = S + slot;                          // q_k, then T_k, then e_k
+    const float d = ax.d, c = ax.c;
+    for (int li = blockIdx.x * kObjWarps + warp; li < nlines; li += gridDim.x * kObjWarps) {
+        const ObjLineF &ln = lines[li];
+        const int m = ln.m, N = m + 1;
+        const long long base = ln.base, st = ax.stride;
+        __syncwarp();
+        for (int k = lane; k <= N; k += 32) {
+            const bool in_line = k >= 1 && k <= m;
+            H[k] = in_line ? in[base + (k - 1) * st] : 0.f;
+            Lo[k] = (PAIR && in_line) ? lo[base + (k - 1) * st] : 0.f;
+        }
+        __syncwarp();
+        // second differences s_t, t = 1..m (end triples with their spacings)
+        for (int t = 1 + lane; t <= m; t += 32) {
+            float sv;
+            if (t == 1 || t == m) {
+                // differences of the pair values, then the end triple's weights
+                const float v1h = H[t], v1l = Lo[t];
+                const float dn = __fadd_rn(__fsub_rn(H[t + 1], v1h), __fsub_rn(Lo[t + 1], v1l));   // v_{t+1} - v_t
+                const float dp = __fadd_rn(__fsub_rn(v1h, H[t - 1]), __fsub_rn(v1l, Lo[t - 1]));   // v_t - v_{t-1}
+                if (t == 1) sv = ln.p1 * dn - ln.q1 * dp;
+                else sv = ln.pm * dn - ln.qm * dp;
+            } else {
+                sv = PAIR ? molt::sdiff_pair(H[t - 1], H[t], H[t + 1], Lo[t - 1], Lo[t], Lo[t + 1])
+                          : (H[t + 1] - H[t]) - (H[t] - H[t - 1]);
+            }
+            S[t] = sv;
+        }
+        __syncwarp();
+        for (int k = 1 + lane; k <= m; k += 32) {
+            float q;
+            if (k == 1) q = ln.g11 * S[1] + (m >= 2 ? ln.g12 * S[2] : 0.f);
+            else if (k == m) q = ln.gNa * S[m - 1] + ln.gNb * S[m];
+            else q = ax.ge * (S[k - 1] + S[k + 1]) + ax.gc * S[k];
+            Q[k] = q;
+        }
+        if (lane == 0) { Q[0] = 0.f; Q[N] = 0.f; }
+        __syncwarp();
+        const int s = (N + 1 + 31) / 32;
+        const int k0 = min(lane * s, N + 1), k1 = min(k0 + s, N + 1);
+        // anti-causal: T_k = q_k + g_{k+1} T_{k+1}, T_N = 0 (g_N = dB)
+        {
+            float qq = 0.f;
+            for (int k = k1 - 1; k >= k0; --k) {
+                const float g = (k == N - 1) ? ln.dB : d;
+                qq = (k == N) ? 0.f : g * qq + Q[k];
+            }
+            float p = ax.dpow[k1 - k0];
+            if (k0 <= N - 1 && N - 1 < k1) p *= ln.rB;
+            affine_scan32<false>(p, qq, lane);
+            float y = __shfl_down_sync(0xffffffffu, qq, 1);
+            y = (lane == 31) ? 0.f : y;
+            for (int k = k1 - 1; k >= k0; --k) {
+                const float g = (k == N - 1) ? ln.dB : d;
+                y = (k == N) ? 0.f : g * y + Q[k];
+                Q[k] = y;
+            }
+        }
+        __syncwarp();
+        // causal: e_k = g_k e_{k-1} + (1 - g_k^2) T_k, e_0 = 0 (g_1 = dA, g_N = dB)
+        {
+            float qq = 0.f;
+            for (int k = k0; k < k1; ++k) {
+                const float g = (k == 1) ? ln.dA : (k == N ? ln.dB : d);
+                const float cg = (k == 1) ? ln.cA : (k == N ? ln.cB : c);
+                qq = (k == 0) ? 0.f : g * qq + cg * Q[k];
+            }
+            float p = ax.dpow[k1 - k0];
+            if (k0 <= 1 && 1 < k1) p *= ln.rA;
+            if (k0 <= N && N < k1) p *= ln.rB;
+            affine_scan32<true>(p, qq, lane);
+            float y = __shfl_up_sync(0xffffffffu, qq, 1);
+            y = (lane == 0) ? 0.f : y;
+            for (int k = k0; k < k1; ++k) {
+                const float g = (k == 1) ? ln.dA : (k == N ? ln.dB : d);
+                const float cg = (k == 1) ? ln.cA : (k == N ? ln.cB : c);
+                y = (k == 0) ? 0.f : g * y + cg * Q[k];
+                Q[k] = y;
+            }
+        }
+        __syncwarp();
+        // e += A' e^{-alpha (x - a)} + B' e^{-alpha (b - x)} with e_0 = e_N = 0
+        const float Bp = -Q[N] * ln.inv, Ap = -Bp * ln.mu;
+        const float Ad = Ap * ln.dA, Bd = Bp * ln.dB;
+        for (int k = 1 + lane; k <= m; k += 32) {
+            const float e = Q[k] + Ad * ax.dpow[k - 1] + Bd * ax.dpow[m - k];
+            const float v = H[k] + Lo[k];
+            const long long at = base + (k - 1) * st;
+            const float r = (mode == OBJF_LINV) ? v - e : e;
+            out[at] = accum ? out[at] + r : r;
+            if (mode == OBJF_BOTH) out2[at] = v - e;
+        }
+    }
+}
+
+// out = sum_t c_t x_t in float32 (the partial sums of F)
+struct CombTermsF {
+    int n;
+    float c[kCombMax];
+    const float *x[kCombMax];
+};
+__global__ void __launch_bounds__(256) k_obj_combine32(CombTermsF t, float *out, int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int k = 0; k < t.n; ++k) v += t.c[k] * t.x[k][i];
+        out[i] = v;
+    }
+}
+
+// next level in pair arithmetic: (nh, nl) = a u + b up + c (F + sum_t c_t x_t)
+__global__ void __launch_bounds__(256) k_obj_level32(CombTermsF t, const float *uh, const float *ul, const float *ph,
+                                                     const float *pl, float a, float b, float cF, float *nh, float *nl,
+                                                     int64_t N)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        float F = 0.f;
+        for (int k = 0; k < t.n; ++k) F += t.c[k] * t.x[k][i];
+        float h, l;
+        molt::level_pair(uh[i], ul[i], b != 0.f ? ph[i] : 0.f, b != 0.f ? pl[i] : 0.f, F, a, b, cF, h, l);
+        nh[i] = h;
+        nl[i] = l;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host constants
 // ---------------------------------------------------------------------------
 // int_0^nu t^k e^{-t} dt, k = 0, 1, 2: the power series below 1 (the closed
@@ -287,6 +481,110 @@ ObjLine make_line(long long base, int m, double h, double ga, double gb, double 
     return L;
 }
 
+
+// Row k (1 <= k <= N-1) of the difference form as weights on the node
+// values v_0..v_N (beta, a dense vector): (v_k - g_k v_{k-1})/(1 - g_k^2) -
+// g_{k+1}(v_{k+1} - g_{k+1} v_k)/(1 - g_{k+1}^2) minus the same combination of
+// the increments, J^L_k - g_k J^R_{k-1} over (1 - g_k^2), ..., + J^R_k.  x: node
+// positions x_0..x_N; the increments use the quadrature rule of the line.
+std::vector<double> diff_row(const std::vector<double> &x, int k, double alpha)
+{
+    const int N = (int)x.size() - 1;
+    std::vector<double> b(N + 1, 0.0);
+    auto g = [&](int j) { return std::exp(-alpha * (x[j] - x[j - 1])); };   // decay of cell j
+    auto add_JL = [&](int j, double c) {   // c J^L_j: cell [x_{j-1}, x_j], destination x_j
+        const int c0 = (j + 1 <= N) ? j - 1 : j - 2;
+        double ts[3], w[3];
+        for (int i = 0; i < 3; ++i) ts[i] = x[j] - x[c0 + i];
+        obj_cell_weights(ts, x[j] - x[j - 1], alpha, w);
+        for (int i = 0; i < 3; ++i) b[c0 + i] += c * w[i];
+    };
+    auto add_JR = [&](int j, double c) {   // c J^R_j: cell [x_j, x_{j+1}], destination x_j
+        const int c0 = (j - 1 >= 0) ? j - 1 : j;
+        double ts[3], w[3];
+        for (int i = 0; i < 3; ++i) ts[i] = x[c0 + i] - x[j];
+        obj_cell_weights(ts, x[j + 1] - x[j], alpha, w);
+        for (int i = 0; i < 3; ++i) b[c0 + i] += c * w[i];
+    };
+    const double gk = g(k), gk1 = g(k + 1), ik = 1.0 / (1.0 - gk * gk), ik1 = 1.0 / (1.0 - gk1 * gk1);
+    b[k] += ik + gk1 * gk1 * ik1;
+    b[k - 1] -= gk * ik;
+    b[k + 1] -= gk1 * ik1;
+    add_JL(k, -ik);
+    add_JR(k - 1, gk * ik);
+    add_JL(k + 1, gk1 * ik1);
+    add_JR(k, -gk1 * gk1 * ik1);
+    add_JR(k, -1.0);
+    return b;
+}
+
+// weight of v_j in the second divided difference over the nodes t-1, t, t+1
+double ddiff_w(const std::vector<double> &x, int t, int j)
+{
+    const double a = x[t - 1], c = x[t], e = x[t + 1];
+    if (j == t - 1) return 2.0 / ((a - c) * (a - e));
+    if (j == t) return 2.0 / ((c - a) * (c - e));
+    return 2.0 / ((e - a) * (e - c));
+}
+
+// node positions of a line object (x_0 = a = 0)
+std::vector<double> obj_positions(int m, double h, double ga, double gb)
+{
+    std::vector<double> x(m + 2);
+    x[0] = 0.0;
+    for (int j = 1; j <= m; ++j) x[j] = ga + (double)(j - 1) * h;
+    x[m + 1] = x[m] + gb;
+    return x;
+}
+
+// the float32 constants of a line object.  The rows 1 and N-1 of the
+// difference form are computed in float64 from the increments and written
+// as weights on the second divided differences (scaled by h^2): a row
+// vanishes on linear data, so node 0 (node N) carries only s_1 (s_m), node
+// 3 (node N-3) only s_2 (s_{m-1}).
+ObjLineF make_line32(long long base, int m, double h, double ga, double gb, double alpha)
+{
+    ObjLineF L{};
+    L.base = base;
+    L.m = m;
+    const std::vector<double> x = obj_positions(m, h, ga, gb);
+    const int N = m + 1;
+    const double b = x[N];
+    L.dA = (float)std::exp(-alpha * ga);
+    L.dB = (float)std::exp(-alpha * gb);
+    L.rA = (float)std::exp(-alpha * (ga - h));
+    L.rB = (float)std::exp(-alpha * (gb - h));
+    L.cA = (float)(-std::expm1(-2.0 * alpha * ga));
+    L.cB = (float)(-std::expm1(-2.0 * alpha * gb));
+    L.mu = (float)std::exp(-alpha * b);
+    L.inv = (float)(1.0 / (-std::expm1(-2.0 * alpha * b)));
+    const double h2 = h * h;
+    // s_1 = h^2 divided difference over (x_0, x_1, x_2) = p1 (v_2 - v_1) - q1 (v_1 - v_0)
+    L.p1 = (float)(2.0 * h2 / ((x[2] - x[0]) * (x[2] - x[1])));
+    L.q1 = (float)(2.0 * h2 / ((x[2] - x[0]) * (x[1] - x[0])));
+    L.pm = (float)(2.0 * h2 / ((x[N] - x[m - 1]) * (x[N] - x[m])));
+    L.qm = (float)(2.0 * h2 / ((x[N] - x[m - 1]) * (x[m] - x[m - 1])));
+    const std::vector<double> b1 = diff_row(x, 1, alpha);
+    L.g11 = (float)(b1[0] / ddiff_w(x, 1, 0) / h2);
+    L.g12 = m >= 2 ? (float)(b1[3] / ddiff_w(x, 2, 3) / h2) : 0.f;
+    const std::vector<double> bm = diff_row(x, m, alpha);
+    L.gNb = (float)(bm[N] / ddiff_w(x, m, N) / h2);
+    L.gNa = m >= 2 ? (float)(bm[N - 3] / ddiff_w(x, m - 1, N - 3) / h2) : 0.f;
+    return L;
+}
+
+// the uniform rows: ge s_{k-1} + gc s_k + ge s_{k+1}, from a uniform line
+void uniform_rows32(double h, double alpha, float &gc, float &ge)
+{
+    const int m = 9, k = 5;
+    const std::vector<double> x = obj_positions(m, h, h, h);
+    const std::vector<double> bk = diff_row(x, k, alpha);
+    const double e = bk[k - 2] / ddiff_w(x, k - 1, k - 2);
+    const double c = (bk[k - 1] - e * ddiff_w(x, k - 1, k - 1)) / ddiff_w(x, k, k - 1);
+    ge = (float)(e / (h * h));
+    gc = (float)(c / (h * h));
+}
+
 }  // namespace
 
 using namespace molt;
@@ -308,6 +606,13 @@ struct mol_embed_ctx {
     int64_t launches = 0;
     std::string err;
     bool timing = false;                // per-kind CUDA events (0 x sweeps, 1 y sweeps, 2 combinations)
+    int prec = 0;                       // MOL_FP64 or MOL_MIXED (float32 sweeps, float32-pair levels)
+    ObjAxisF ax32[2]{};
+    ObjLineF *lines32[2] = {nullptr, nullptr};
+    float *dpow32[2] = {nullptr, nullptr};
+    float *V32[kMaxP + 1] = {};
+    float *tmp32 = nullptr, *t132 = nullptr, *t232 = nullptr, *Fb32 = nullptr;
+    float *lh[3] = {nullptr, nullptr, nullptr}, *ll[3] = {nullptr, nullptr, nullptr};   // pair levels
     std::vector<cudaEvent_t> ev_pool;
     struct Rec { int kind; cudaEvent_t a, b; };
     std::vector<Rec> recs;
@@ -459,6 +764,101 @@ mol_status run_update(mol_embed_ctx *e, const double *u, const double *up, doubl
     return MOL_OK;
 }
 
+// ---- float32 sweeps (MOL_MIXED) ----
+// one difference-form sweep along axis a; lo: the lo plane when in is a pair level
+mol_status sweep32(mol_embed_ctx *e, int a, const float *in, const float *lo, float *out, float *out2, int mode,
+                   int accum, cudaStream_t s)
+{
+    if (e->nlines[a] == 0) return MOL_OK;
+    const int grid = std::min(e->grid, (e->nlines[a] + kObjWarps - 1) / kObjWarps);
+    Timed t(e, a, s);
+    if (lo)
+        k_obj_sweep32<true><<<grid, 32 * kObjWarps, e->smem, s>>>(e->ax32[a], e->lines32[a], e->nlines[a], in, lo, out,
+                                                                  out2, mode, accum, e->slot);
+    else
+        k_obj_sweep32<false><<<grid, 32 * kObjWarps, e->smem, s>>>(e->ax32[a], e->lines32[a], e->nlines[a], in, nullptr,
+                                                                   out, out2, mode, accum, e->slot);
+    ++e->launches;
+    ECK(cudaGetLastError(), "line-object sweep (float32)");
+    return MOL_OK;
+}
+
+// out = C v (eq. C_def_ADI) with L^{-1} = 1 - D: D_x v - D_y D_x v + D_y v - D_x D_y v
+mol_status apply_C32(mol_embed_ctx *e, const float *v, const float *vlo, float *out, cudaStream_t s)
+{
+    EST(sweep32(e, 0, v, vlo, e->t132, nullptr, OBJF_D, 0, s));               // t1 = D_x v
+    EST(sweep32(e, 1, e->t132, nullptr, out, nullptr, OBJF_LINV, 0, s));      // out = L_y^{-1} t1
+    EST(sweep32(e, 1, v, vlo, e->t132, nullptr, OBJF_D, 0, s));               // t1 = D_y v
+    return sweep32(e, 0, e->t132, nullptr, out, nullptr, OBJF_LINV, 1, s);    // out += L_x^{-1} t1
+}
+
+// out = D v (eq. D_def_ADI) = v - L_x^{-1} L_y^{-1} v = D_y v + D_x (L_y^{-1} v)
+mol_status apply_D32(mol_embed_ctx *e, const float *v, float *out, cudaStream_t s)
+{
+    EST(sweep32(e, 1, v, nullptr, out, e->t232, OBJF_BOTH, 0, s));            // out = D_y v, t2 = L_y^{-1} v
+    return sweep32(e, 0, e->t232, nullptr, out, nullptr, OBJF_D, 1, s);       // out += D_x t2
+}
+
+mol_status combine32(mol_embed_ctx *e, const CombTermsF &t, float *out, cudaStream_t s)
+{
+    const int64_t blocks = std::min<int64_t>((e->N + 255) / 256, 4096);
+    Timed tm(e, 2, s);
+    k_obj_combine32<<<(unsigned)blocks, 256, 0, s>>>(t, out, e->N);
+    ++e->launches;
+    ECK(cudaGetLastError(), "combine (float32)");
+    return MOL_OK;
+}
+
+// F[u] of the pair level (uh, ul), Table 3 order as run_update.  With nh
+// set: (nh, nl) = ea u + eb up + ec F in pair arithmetic; else F (float32)
+// into F32.
+mol_status run_update32(mol_embed_ctx *e, const float *uh, const float *ul, const float *ph, const float *pl,
+                        float *nh, float *nl, float *F32, float ea, float eb, float ec, cudaStream_t s)
+{
+    const int P = e->P;
+    for (int p = 1; p <= P; ++p) {
+        if (p == 1) {
+            EST(apply_C32(e, uh, ul, e->V32[1], s));
+        } else {
+            EST(apply_D32(e, e->V32[p - 1], e->V32[p], s));
+            for (int k = 1; k < p; ++k) {
+                EST(apply_C32(e, e->V32[k], nullptr, e->tmp32, s));
+                std::swap(e->V32[k], e->tmp32);
+            }
+        }
+        CombTermsF t{};
+        if (p > 1) { t.c[t.n] = 1.f; t.x[t.n++] = e->Fb32; }
+        for (int k = 1; k <= p; ++k) {
+            t.c[t.n] = (float)e->tw[p * 8 + (p - k + 1)];
+            t.x[t.n++] = e->V32[k];
+        }
+        if (p < P || !nh) {
+            EST(combine32(e, t, p < P ? e->Fb32 : F32, s));
+        } else {
+            const int64_t blocks = std::min<int64_t>((e->N + 255) / 256, 4096);
+            Timed tm(e, 2, s);
+            k_obj_level32<<<(unsigned)blocks, 256, 0, s>>>(t, uh, ul, ph, pl, ea, eb, ec, nh, nl, e->N);
+            ++e->launches;
+            ECK(cudaGetLastError(), "level update (float32 pairs)");
+        }
+    }
+    return MOL_OK;
+}
+
+mol_status to_pair(mol_embed_ctx *e, const double *x, int k, cudaStream_t s)
+{
+    ECK(launch_to_pair(x, e->lh[k], e->ll[k], e->N, s), "level conversion");
+    ++e->launches;
+    return MOL_OK;
+}
+
+mol_status from_pair(mol_embed_ctx *e, int k, double *x, cudaStream_t s)
+{
+    ECK(launch_from_pair(e->lh[k], e->ll[k], x, e->N, s), "level conversion");
+    ++e->launches;
+    return MOL_OK;
+}
+
 mol_status check_dev(mol_embed_ctx *e, const void *p, const char *name)
 {
     if (!p) return efail(e, MOL_EINVAL, std::string(name) + " is NULL");
@@ -476,7 +876,8 @@ mol_status check_dev(mol_embed_ctx *e, const void *p, const char *name)
 
 extern "C" {
 
-mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double beta, int P, mol_embed *out)
+mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double beta, int P, mol_prec prec,
+                            mol_embed *out)
 {
     if (!out) return efail(nullptr, MOL_EINVAL, "out is NULL");
     *out = nullptr;
@@ -489,6 +890,7 @@ mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double
         !g->col_gap_lo || !g->col_gap_hi)
         return efail(nullptr, MOL_EINVAL, "geometry arrays must not be NULL");
     if (P < 1 || P > kMaxP) return efail(nullptr, MOL_EINVAL, "P must be in 1..5");
+    if (prec != MOL_FP64 && prec != MOL_MIXED) return efail(nullptr, MOL_EINVAL, "unknown precision");
     if (!(c > 0) || !(dt > 0) || !std::isfinite(c) || !std::isfinite(dt))
         return efail(nullptr, MOL_EINVAL, "c and dt must be positive");
     const double bmax = beta_max_of(P);
@@ -527,6 +929,7 @@ mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double
     e->hx = g->hx;
     e->hy = g->hy;
     e->P = P;
+    e->prec = prec;
     e->beta = beta;
     e->alpha = beta / (c * dt);                          // eq. L_def
     e->tw.assign(8 * 8, 0.0);
@@ -571,32 +974,73 @@ mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double
                 break;
             }
         }
-    }
-    const size_t plane = sizeof(double) * (size_t)e->N;
-    double **bufs[] = {&e->tmp, &e->t1, &e->lev, &e->Fb};
-    for (double **b : bufs)
-        if (st == MOL_OK) st = ealloc(e, (void **)b, plane);
-    for (int k = 1; k <= P && st == MOL_OK; ++k) st = ealloc(e, (void **)&e->V[k], plane);
-    if (st == MOL_OK) {
-        // every sweep writes only interior nodes: the work fields start at zero
-        for (void *p : e->allocs)
-            if (p != e->dpow[0] && p != e->dpow[1] && p != e->lines[0] && p != e->lines[1] &&
-                (ce = cudaMemset(p, 0, plane)) != cudaSuccess) {
-                st = efail(e, MOL_ECUDA, "memset");
+        if (prec == MOL_MIXED) {
+            // float32 constants of the difference form
+            ObjAxisF &Y = e->ax32[a];
+            Y.stride = X.stride;
+            Y.d = (float)X.d;
+            Y.c = (float)(-std::expm1(-2.0 * alpha * h));
+            uniform_rows32(h, alpha, Y.gc, Y.ge);
+            std::vector<float> tab32(tab.begin(), tab.end());
+            std::vector<ObjLineF> ls32;
+            for (int64_t l = 0; l < nl; ++l) {
+                if (lo[l] > hi[l]) continue;
+                const long long base = a == 0 ? l * nx + lo[l] : lo[l] * nx + l;
+                ls32.push_back(make_line32(base, (int)(hi[l] - lo[l] + 1), h, ga[l], gb[l], alpha));
+            }
+            if ((st = ealloc(e, (void **)&e->dpow32[a], sizeof(float) * tab32.size())) != MOL_OK) break;
+            if ((ce = cudaMemcpy(e->dpow32[a], tab32.data(), sizeof(float) * tab32.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+                st = efail(e, MOL_ECUDA, "table upload");
                 break;
             }
+            Y.dpow = e->dpow32[a];
+            if (!ls32.empty()) {
+                if ((st = ealloc(e, (void **)&e->lines32[a], sizeof(ObjLineF) * ls32.size())) != MOL_OK) break;
+                if ((ce = cudaMemcpy(e->lines32[a], ls32.data(), sizeof(ObjLineF) * ls32.size(),
+                                     cudaMemcpyHostToDevice)) != cudaSuccess) {
+                    st = efail(e, MOL_ECUDA, "line table upload");
+                    break;
+                }
+            }
+        }
+    }
+    // work fields; every sweep writes only interior nodes, so they start at zero
+    std::vector<std::pair<void **, size_t>> work;
+    const size_t plane = sizeof(double) * (size_t)e->N, plane32 = sizeof(float) * (size_t)e->N;
+    if (prec == MOL_FP64) {
+        for (double **b : {&e->tmp, &e->t1, &e->lev, &e->Fb}) work.push_back({(void **)b, plane});
+        for (int k = 1; k <= P; ++k) work.push_back({(void **)&e->V[k], plane});
+    } else {
+        for (float **b : {&e->tmp32, &e->t132, &e->t232, &e->Fb32}) work.push_back({(void **)b, plane32});
+        for (int k = 1; k <= P; ++k) work.push_back({(void **)&e->V32[k], plane32});
+        for (int k = 0; k < 3; ++k) {
+            work.push_back({(void **)&e->lh[k], plane32});
+            work.push_back({(void **)&e->ll[k], plane32});
+        }
+    }
+    for (auto &w : work) {
+        if (st != MOL_OK) break;
+        if ((st = ealloc(e, w.first, w.second)) != MOL_OK) break;
+        if ((ce = cudaMemset(*w.first, 0, w.second)) != cudaSuccess) st = efail(e, MOL_ECUDA, "memset");
     }
     if (st == MOL_OK) {
         // line arrays sized for the longest line (even, for 16-byte alignment)
         e->slot = (int)((maxm + 2 + 1) & ~(int64_t)1);
+        // float64: two line arrays of doubles; float32: four of floats (the same bytes)
         e->smem = (int)(sizeof(double) * 2 * (size_t)e->slot * kObjWarps);
-        if ((ce = cudaFuncSetAttribute(k_obj_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem)) !=
-            cudaSuccess)
+        const void *kf = prec == MOL_FP64 ? (const void *)k_obj_sweep : (const void *)k_obj_sweep32<true>;
+        if ((ce = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem)) != cudaSuccess ||
+            (prec == MOL_MIXED &&
+             (ce = cudaFuncSetAttribute(k_obj_sweep32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem)) !=
+                 cudaSuccess))
             st = efail(e, MOL_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));
         int dev = 0, sms = 152, per_sm = 1;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (st == MOL_OK &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_obj_sweep, 32 * kObjWarps, e->smem) != cudaSuccess) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prec == MOL_FP64 ? (const void *)k_obj_sweep
+                                                                                 : (const void *)k_obj_sweep32<true>,
+                                                          32 * kObjWarps, e->smem) != cudaSuccess) {
             cudaGetLastError();
             per_sm = 1;
         }
@@ -630,6 +1074,14 @@ mol_status mol_embed_linv(mol_embed e, const double *v, double *w, int axis, voi
     if (axis != 0 && axis != 1) return efail(e, MOL_EINVAL, "axis must be 0 (x) or 1 (y)");
     if (v == w) return efail(e, MOL_EINVAL, "v and w must not overlap");
     cudaStream_t s = (cudaStream_t)stream;
+    if (e->prec == MOL_MIXED) {
+        EST(to_pair(e, v, 0, s));
+        ECK(cudaMemsetAsync(e->t132, 0, sizeof(float) * (size_t)e->N, s), "memset");
+        EST(sweep32(e, axis, e->lh[0], e->ll[0], e->t132, nullptr, OBJF_LINV, 0, s));
+        ECK(launch_from_f32(e->t132, w, e->N, s), "conversion");
+        ++e->launches;
+        return MOL_OK;
+    }
     ECK(cudaMemsetAsync(w, 0, sizeof(double) * (size_t)e->N, s), "memset");
     return sweep(e, axis, v, w, OBJ_LINV, 0, nullptr, s);
 }
@@ -640,7 +1092,15 @@ mol_status mol_embed_apply_F(mol_embed e, const double *u, double *F, void *stre
     EST(check_dev(e, u, "u"));
     EST(check_dev(e, F, "F"));
     if (u == F) return efail(e, MOL_EINVAL, "u and F must not overlap");
-    return run_update(e, u, nullptr, F, 0.0, 0.0, 1.0, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e->prec == MOL_MIXED) {
+        EST(to_pair(e, u, 0, s));
+        EST(run_update32(e, e->lh[0], e->ll[0], nullptr, nullptr, nullptr, nullptr, e->t232, 0.f, 0.f, 1.f, s));
+        ECK(launch_from_f32(e->t232, F, e->N, s), "conversion");
+        ++e->launches;
+        return MOL_OK;
+    }
+    return run_update(e, u, nullptr, F, 0.0, 0.0, 1.0, s);
 }
 
 mol_status mol_embed_start(mol_embed e, const double *u0, double *u1, void *stream)
@@ -649,7 +1109,13 @@ mol_status mol_embed_start(mol_embed e, const double *u0, double *u1, void *stre
     EST(check_dev(e, u0, "u0"));
     EST(check_dev(e, u1, "u1"));
     if (u0 == u1) return efail(e, MOL_EINVAL, "u0 and u1 must not overlap");
-    return run_update(e, u0, nullptr, u1, 1.0, 0.0, 0.5, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e->prec == MOL_MIXED) {
+        EST(to_pair(e, u0, 0, s));
+        EST(run_update32(e, e->lh[0], e->ll[0], nullptr, nullptr, e->lh[1], e->ll[1], nullptr, 1.f, 0.f, 0.5f, s));
+        return from_pair(e, 1, u1, s);
+    }
+    return run_update(e, u0, nullptr, u1, 1.0, 0.0, 0.5, s);
 }
 
 mol_status mol_embed_step(mol_embed e, double *u_prev, double *u_cur, int64_t nsteps, void *stream)
@@ -660,6 +1126,24 @@ mol_status mol_embed_step(mol_embed e, double *u_prev, double *u_cur, int64_t ns
     if (u_prev == u_cur) return efail(e, MOL_EINVAL, "u_prev and u_cur must not overlap");
     if (nsteps < 0) return efail(e, MOL_EINVAL, "nsteps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
+    if (e->prec == MOL_MIXED) {
+        if (nsteps == 0) return MOL_OK;
+        // the levels as float32 pairs for the whole call (rotating through
+        // three internal pair levels), converted back at the end
+        EST(to_pair(e, u_prev, 0, s));
+        EST(to_pair(e, u_cur, 1, s));
+        int r[3] = {0, 1, 2};
+        for (int64_t k = 0; k < nsteps; ++k) {
+            EST(run_update32(e, e->lh[r[1]], e->ll[r[1]], e->lh[r[0]], e->ll[r[0]], e->lh[r[2]], e->ll[r[2]], nullptr,
+                             2.f, -1.f, 1.f, s));
+            const int t = r[0];
+            r[0] = r[1];
+            r[1] = r[2];
+            r[2] = t;
+        }
+        EST(from_pair(e, r[0], u_prev, s));
+        return from_pair(e, r[1], u_cur, s);
+    }
     double *b[3] = {u_prev, u_cur, e->lev};
     for (int64_t k = 0; k < nsteps; ++k) {
         EST(run_update(e, b[1], b[0], b[2], 2.0, -1.0, 1.0, s));
@@ -692,7 +1176,7 @@ mol_status mol_embed_solve_host(mol_embed e, const double *u0, double *u_out, in
         if (!e->io[k]) EST(ealloc(e, (void **)&e->io[k], bytes));
     ECK(cudaMemcpyAsync(e->io[0], u0, bytes, cudaMemcpyHostToDevice, s), "copy in");
     if (nsteps > 0) {
-        EST(run_update(e, e->io[0], nullptr, e->io[1], 1.0, 0.0, 0.5, s));
+        EST(mol_embed_start(e, e->io[0], e->io[1], stream));
         EST(mol_embed_step(e, e->io[0], e->io[1], nsteps - 1, stream));
         ECK(cudaMemcpyAsync(u_out, e->io[1], bytes, cudaMemcpyDeviceToHost, s), "copy out");
     } else {

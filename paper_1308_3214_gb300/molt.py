@@ -129,7 +129,7 @@ def load_library(path: Path | None = None):
     lib.mol_batch_set_tuning.argtypes = [vp, I, I, I]
     lib.mol_solve_dirichlet.argtypes = [vp, vp, i64, dp, vp, vp]
     lib.mol_solve_source.argtypes = [vp, vp, i64, vp, dp, vp, vp]
-    lib.mol_embed_create.argtypes = [ctypes.POINTER(mol_embed_geom), D, D, D, I, ctypes.POINTER(vp)]
+    lib.mol_embed_create.argtypes = [ctypes.POINTER(mol_embed_geom), D, D, D, I, I, ctypes.POINTER(vp)]
     lib.mol_embed_destroy.argtypes = [vp]
     lib.mol_embed_last_error.argtypes = [vp]
     lib.mol_embed_last_error.restype = ctypes.c_char_p
@@ -591,15 +591,17 @@ class BatchSolver:
 
 
 class EmbedSolver:
-    """The 2D scheme on a domain embedded in a grid (Sec. 4.3), float64.
+    """The 2D scheme on a domain embedded in a grid (Sec. 4.3).
 
     ``geom`` describes the line objects: any object with the attributes nx,
     ny, hx, hy, r0, r1, ra, rb (rows: first / last interior x index, gaps
     before / after them) and c0, c1, ca, cb (columns), as
     ``workloads.EmbeddedGrid`` has.  Fields are contiguous CUDA float64
-    tensors of shape (ny, nx) that vanish outside the domain."""
+    tensors of shape (ny, nx) that vanish outside the domain.  ``prec`` is
+    "fp64" (float64 sweeps) or "mixed" (float32 sweeps of the difference
+    form of D, time levels kept as float32 pairs inside the library)."""
 
-    def __init__(self, geom, dt: float, P: int, c: float = 1.0, beta: float = 0.0):
+    def __init__(self, geom, dt: float, P: int, c: float = 1.0, beta: float = 0.0, prec: str = "fp64"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libmolt needs a CUDA GPU")
@@ -613,11 +615,12 @@ class EmbedSolver:
                            *[a.ctypes.data for a in arrs])
         h = ctypes.c_void_p()
         torch.cuda.init()
-        st = self.lib.mol_embed_create(ctypes.byref(g), float(c), float(dt), float(beta), int(P), ctypes.byref(h))
+        st = self.lib.mol_embed_create(ctypes.byref(g), float(c), float(dt), float(beta), int(P), PREC[prec],
+                                       ctypes.byref(h))
         if st != MOL_OK:
             raise MolError(st, self.lib.mol_last_error(None).decode())
         self.h = h
-        self.P, self.dt, self.c = int(P), float(dt), float(c)
+        self.P, self.dt, self.c, self.prec = int(P), float(dt), float(c), prec
 
     def _check(self, st: int):
         if st != MOL_OK:

@@ -102,13 +102,13 @@ def test_null_handle_calls_fail_cleanly(lib):
 # embedded-boundary handles: the geometry is checked on the host, before any
 # device work
 # --------------------------------------------------------------------------
-def _embed_create(lib, g, P=2, beta=0.0):
+def _embed_create(lib, g, P=2, beta=0.0, prec=0):
     i64 = lambda a: np.ascontiguousarray(a, dtype=np.int64)
     f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
     arrs = [i64(g.r0), i64(g.r1), f64(g.ra), f64(g.rb), i64(g.c0), i64(g.c1), f64(g.ca), f64(g.cb)]
     geom = molt.mol_embed_geom(g.nx, g.ny, g.hx, g.hy, *[a.ctypes.data for a in arrs])
     h = ctypes.c_void_p()
-    st = lib.mol_embed_create(ctypes.byref(geom), 1.0, 0.01, beta, P, ctypes.byref(h))
+    st = lib.mol_embed_create(ctypes.byref(geom), 1.0, 0.01, beta, P, prec, ctypes.byref(h))
     return st, h
 
 
@@ -131,6 +131,7 @@ def test_embed_create_rejects_bad_geometry_on_the_host(lib):
     assert _embed_create(lib, bad)[0] == molt.MOL_EINVAL
     assert _embed_create(lib, g, P=0)[0] == molt.MOL_EINVAL
     assert _embed_create(lib, g, P=2, beta=1.49)[0] == molt.MOL_EUNSTABLE
+    assert _embed_create(lib, g, prec=7)[0] == molt.MOL_EINVAL
     big = workloads.disk_grid(2301, radius=1.0, half=1.1)   # the middle row holds more than 2046 nodes
     st, _ = _embed_create(lib, big)
     assert st == molt.MOL_EINVAL and b"2046" in lib.mol_last_error(None)
