@@ -868,19 +868,24 @@ def main_extension(args, spec):
     print(json.dumps(line), flush=True)
 
 
-def embedded_bytes_per_point(P: int) -> float:
-    """Algorithmic bytes of the line-object sweeps per interior point and step:
-    C = 4 sweeps (D_x, L_y^{-1}, D_y, L_x^{-1} accumulated: 16 + 16 + 16 + 24 B),
-    D = 2 sweeps (L_y^{-1}, the subtraction from v: 16 + 24 B); Table 3 builds
-    1 + P(P-1)/2 C's and P - 1 D's per step."""
+def embedded_bytes_per_point(P: int, prec: str = "fp64") -> float:
+    """Algorithmic bytes of the line-object sweeps per interior point and step.
+    float64: C = 4 sweeps (D_x, L_y^{-1}, D_y, L_x^{-1} accumulated: 16 + 16 +
+    16 + 24 B), D = 2 sweeps (L_y^{-1}, the subtraction from v: 16 + 24 B).
+    float32: C of the pair level (8 B in) 12 + 8 + 12 + 12 B, C of a float32
+    field 8 + 8 + 8 + 12 B, D (D_y v and L_y^{-1} v in one sweep, then D_x
+    accumulated) 12 + 12 B.  Table 3 builds 1 + P(P-1)/2 C's (the first on the
+    level) and P - 1 D's per step."""
     nC = 1 + P * (P - 1) // 2
+    if prec == "mixed":
+        return 44.0 + 36.0 * (nC - 1) + 24.0 * (P - 1)
     return 88.0 * nC + 40.0 * (P - 1)
 
 
 def main_embedded(args, spec):
-    """The ellipse of Sec. 4.3 (embedded boundary, float64): one mol_embed_step
-    call of K steps with the levels resident; per-kind events of a second call;
-    the oracle on a bounded sample.  Points = interior nodes of the domain."""
+    """The ellipse of Sec. 4.3 (embedded boundary): one mol_embed_step call of
+    K steps with the levels resident; per-kind events of a second call; the
+    oracle on a bounded sample.  Points = interior nodes of the domain."""
     world, rank, local = dist_setup()
     if rank != 0:
         return
@@ -915,7 +920,7 @@ def main_embedded(args, spec):
     npts = int(g.mask.sum())
     dt = cfl * g.hx
     u0h = workloads.gaussian_embedded(g, seed=1006, width=0.15)
-    s = molt.EmbedSolver(g, dt=dt, P=P)
+    s = molt.EmbedSolver(g, dt=dt, P=P, prec=args.prec)
     K = args.steps
     up = torch.from_numpy(u0h).cuda()
     uc = s.start(up)
@@ -942,33 +947,46 @@ def main_embedded(args, spec):
     sweep_ms = kinds["x_sweep"][0] + kinds["y_sweep"][0]
     sweep_launches = kinds["x_sweep"][1] + kinds["y_sweep"][1]
     hbm_peak, peak_kind = read_peak()
-    bpp = embedded_bytes_per_point(P)
+    bpp = embedded_bytes_per_point(P, args.prec)
     hbm_achieved = bpp * npts * kt / (sweep_ms * 1e-3) / 1e9
-    # float64 operations of the sweep per interior node (a node between grid
-    # nodes): two 3-point increments (2 x 5 flops), each recurrence's chunk
-    # reduction (FMA, 2 flops) and re-scan (FMA, 2 flops) in both directions
-    # (8), the homogeneous terms and the sum (9): 27 flops.  The
-    # peak is the nominal float64 rate of a GB300 (1.25 TFLOP/s): the sweeps
-    # are bound by the narrow float64 pipe, not by HBM.
-    flops = 27.0 * npts * sweep_launches
-    achieved = flops / (sweep_ms * 1e-3) / 1e9
+    kinds_ms = {k: v[0] / kt for k, v in kinds.items()}
+    if args.prec == "fp64":
+        # float64 operations of the sweep per interior node (a node between
+        # grid nodes): two 3-point increments (2 x 5 flops), each recurrence's
+        # chunk reduction (FMA, 2 flops) and re-scan (FMA, 2 flops) in both
+        # directions (8), the homogeneous terms and the sum (9): 27 flops.  The
+        # peak is the nominal float64 rate of a GB300 (1.25 TFLOP/s): the
+        # sweeps are bound by the narrow float64 pipe, not by HBM.
+        flops = 27.0 * npts * sweep_launches
+        achieved = flops / (sweep_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": achieved / FP64_PEAK_GFLOPS,
+                    "traffic": read_traffic(0, spec["name"], "fp64", "embed"),
+                    "peak_kind": "nominal float64 rate of a GB300 (no measured float64 peak on this pool)",
+                    "kernel": "k_obj_sweep (all line-object sweeps of a step; float64 recurrences)",
+                    "flops_per_node_sweep": 27, "hbm": {"achieved_GBps": hbm_achieved, "peak": hbm_peak,
+                                                         "frac": hbm_achieved / hbm_peak,
+                                                         "alg_bytes_per_point_step": bpp}}
+    else:
+        # float32 sweeps: at the HBM copy rate the algorithmic bytes take less
+        # time than their float32 arithmetic at the nominal rate, so HBM is the
+        # roofline; one warp per line object leaves the sweeps latency bound
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_achieved / hbm_peak,
+                    "traffic": read_traffic(0, spec["name"], "mixed", "embed"),
+                    "peak_kind": peak_kind,
+                    "kernel": "k_obj_sweep32 (all line-object sweeps of a step; float32 difference form)",
+                    "alg_bytes_per_point_step": bpp}
+    roofline["kinds_ms_per_step"] = kinds_ms
+    roofline["sweep_ms_per_launch"] = sweep_ms / max(sweep_launches, 1)
     line = {"metric": METRIC, "value": npts * K / (ms * 1e-3), "unit": METRIC, "n_gpus": 1, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": spec["name"], "grid": [n, n], "interior_points": npts, "P": P, "cfl": cfl,
                        "domain": "((x+y)/4)^2 + (x-y)^2 < 1 in [-2.2, 2.2]^2",
+                       "levels": "f32 hi+lo pairs" if args.prec == "mixed" else "f64",
                        "step": "mol_embed_step, K steps in one call, levels resident", "parallelism": "1 rank"},
-            "gpu_launches": launches,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_PEAK_GFLOPS,
-                         "traffic": read_traffic(0, spec["name"], "fp64", "embed"),
-                         "peak_kind": "nominal float64 rate of a GB300 (no measured float64 peak on this pool)",
-                         "kernel": "k_obj_sweep (all line-object sweeps of a step; float64 recurrences)",
-                         "flops_per_node_sweep": 27, "hbm": {"achieved_GBps": hbm_achieved, "peak": hbm_peak,
-                                                              "frac": hbm_achieved / hbm_peak,
-                                                              "alg_bytes_per_point_step": bpp},
-                         "kinds_ms_per_step": {k: v[0] / kt for k, v in kinds.items()},
-                         "sweep_ms_per_launch": sweep_ms / max(sweep_launches, 1)},
+            "gpu_launches": launches, "roofline": roofline,
             "clocks": clocks, "finite": finite}
     if not args.no_e2e:
         t0 = time.perf_counter()
@@ -976,6 +994,20 @@ def main_embedded(args, spec):
         el = time.perf_counter() - t0
         line["e2e"] = {"value": npts * K / el, "unit": METRIC, "h2d_bytes_per_step": 8 * n * n / K,
                        "d2h_bytes_per_step": 8 * n * n / K, "note": "mol_embed_solve_host: u0 in, K steps, u out"}
+    if not args.no_fp64_compare and args.prec == "mixed":
+        s64 = molt.EmbedSolver(g, dt=dt, P=P, prec="fp64")
+        vp = torch.from_numpy(u0h).cuda()
+        vc = s64.start(vp)
+        s64.step(vp, vc, 3)
+        k64 = max(3, K // 4)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s64.step(vp, vc, k64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        line["fp64_path"] = {"value": npts * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64}
+        s64.close()
     if not args.no_cpu_baseline:
         import oracle
         oracle.build()

@@ -34,6 +34,8 @@ namespace {
 
 constexpr int kObjMaxM = 2046;             // interior nodes of a line object at most
 constexpr int kObjWarps = 4;               // line objects (warps) per CTA
+constexpr int kObjThreads32 = 128;         // threads per line object in the float32 sweep
+constexpr int kObjCpb[2] = {1, 4};         // float32 sweep: line objects per CTA, contiguous / strided axis
 
 struct ObjLine {
     long long base;     // element index of the first interior node
@@ -258,31 +260,72 @@ enum : int { OBJF_D = 0, OBJF_LINV = 1, OBJF_BOTH = 2 };
 // MODE OBJF_D: out = D v; OBJF_LINV: out = v - D v (= L^{-1} v); OBJF_BOTH:
 // out = D v and out2 = v - D v.  accum adds to out.  PAIR: v is a float32
 // pair level (in = hi, lo = lo plane), else a float32 field.
-template <bool PAIR>
-__global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep32(ObjAxisF ax, const ObjLineF *lines, int nlines,
-                                                               const float *__restrict__ in, const float *__restrict__ lo,
-                                                               float *out, float *out2, int mode, int accum, int slot)
+// A CTA takes CPB consecutive line objects at a time, kObjThreads32 threads
+// per line.  Loads and stores run over grid positions along the lines, the
+// CPB lines interleaved, so that on the strided axis (consecutive lines =
+// adjacent columns) a row's CPB values are read and written together.  In the
+// recurrences each thread reduces a chunk of its group's line, the chunk maps
+// are composed over the lanes of a warp (shuffles) and over the group's warps
+// (their totals in shared memory), and each chunk is re-run from its carry.
+// slot: elements per line array (>= m + 2), four arrays per line.
+template <bool PAIR, int CPB>
+__global__ void __launch_bounds__(kObjThreads32 * CPB) k_obj_sweep32(ObjAxisF ax, const ObjLineF *lines, int nlines,
+                                                                    const float *__restrict__ in,
+                                                                    const float *__restrict__ lo, float *out,
+                                                                    float *out2, int mode, int accum, int slot)
 {
+    constexpr int NW = kObjThreads32 / 32, NT = kObjThreads32 * CPB;
     extern __shared__ __align__(16) float smf[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *H = smf + (size_t)warp * 4 * slot;     // values (hi plane)
-    float *Lo = H + slot;                         // lo plane (PAIR)
-    float *S = Lo + slot;                         // second differences s_t
-    float *Q = S + slot;                          // q_k, then T_k, then e_k
+    __shared__ float2 totA[CPB][NW], totC[CPB][NW];   // warp totals of the two recurrences
+    __shared__ long long l_base[CPB], l_pos[CPB];      // first interior node: element, position on the line's axis
+    __shared__ int l_m[CPB];
+    __shared__ float l_Ad[CPB], l_Bd[CPB];
+    const int tid = threadIdx.x;
+    const int grp = tid / kObjThreads32, gt = tid % kObjThreads32, warp = gt >> 5, lane = gt & 31;
+    const int ij = tid % CPB, ii = tid / CPB;           // interleaved load/store mapping: line, position
+    const long long st = ax.stride;
     const float d = ax.d, c = ax.c;
-    for (int li = blockIdx.x * kObjWarps + warp; li < nlines; li += gridDim.x * kObjWarps) {
-        const ObjLineF &ln = lines[li];
-        const int m = ln.m, N = m + 1;
-        const long long base = ln.base, st = ax.stride;
-        __syncwarp();
-        for (int k = lane; k <= N; k += 32) {
-            const bool in_line = k >= 1 && k <= m;
-            H[k] = in_line ? in[base + (k - 1) * st] : 0.f;
-            Lo[k] = (PAIR && in_line) ? lo[base + (k - 1) * st] : 0.f;
+    for (int gb = blockIdx.x * CPB; gb < nlines; gb += gridDim.x * CPB) {
+        __syncthreads();
+        if (tid < CPB) {
+            const int li = gb + tid;
+            const bool ok = li < nlines;
+            l_m[tid] = ok ? lines[li].m : 0;
+            l_base[tid] = ok ? lines[li].base : 0;
+            l_pos[tid] = (ok && CPB > 1) ? lines[li].base / st : 0;
         }
-        __syncwarp();
+        __syncthreads();
+        long long p_lo = l_pos[0], p_hi = l_pos[0] + l_m[0] - 1;
+#pragma unroll
+        for (int j = 1; j < CPB; ++j)
+            if (l_m[j] > 0) {
+                p_lo = min(p_lo, l_pos[j]);
+                p_hi = max(p_hi, l_pos[j] + l_m[j] - 1);
+            }
+        {
+            const int mj = l_m[ij];
+            const long long bj = l_base[ij], pj = l_pos[ij];
+            float *Hj = smf + (size_t)ij * 4 * slot, *Lj = Hj + slot;
+            for (long long r = p_lo + ii; r <= p_hi; r += NT / CPB) {
+                const long long k = r - pj + 1;
+                if (k >= 1 && k <= mj) {
+                    Hj[k] = in[bj + (k - 1) * st];
+                    Lj[k] = PAIR ? lo[bj + (k - 1) * st] : 0.f;
+                }
+            }
+            if (ii == 0) { Hj[0] = 0.f; Lj[0] = 0.f; Hj[mj + 1] = 0.f; Lj[mj + 1] = 0.f; }
+        }
+        __syncthreads();
+        // the recurrences of line grp
+        const int li = gb + grp;
+        const int m = l_m[grp], N = m + 1;
+        float *H = smf + (size_t)grp * 4 * slot;
+        float *Lo = H + slot;        // lo plane (PAIR)
+        float *S = Lo + slot;        // second differences s_t
+        float *Q = S + slot;         // q_k, then T_k, then e_k
+        const ObjLineF &ln = lines[li < nlines ? li : 0];
         // second differences s_t, t = 1..m (end triples with their spacings)
-        for (int t = 1 + lane; t <= m; t += 32) {
+        for (int t = 1 + gt; t <= m; t += kObjThreads32) {
             float sv;
             if (t == 1 || t == m) {
                 // differences of the pair values, then the end triple's weights
@@ -297,19 +340,20 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep32(ObjAxisF ax, con
             }
             S[t] = sv;
         }
-        __syncwarp();
-        for (int k = 1 + lane; k <= m; k += 32) {
+        __syncthreads();
+        for (int k = 1 + gt; k <= m; k += kObjThreads32) {
             float q;
             if (k == 1) q = ln.g11 * S[1] + (m >= 2 ? ln.g12 * S[2] : 0.f);
             else if (k == m) q = ln.gNa * S[m - 1] + ln.gNb * S[m];
             else q = ax.ge * (S[k - 1] + S[k + 1]) + ax.gc * S[k];
             Q[k] = q;
         }
-        if (lane == 0) { Q[0] = 0.f; Q[N] = 0.f; }
-        __syncwarp();
-        const int s = (N + 1 + 31) / 32;
-        const int k0 = min(lane * s, N + 1), k1 = min(k0 + s, N + 1);
-        // anti-causal: T_k = q_k + g_{k+1} T_{k+1}, T_N = 0 (g_N = dB)
+        if (gt == 0) { Q[0] = 0.f; Q[N] = 0.f; }
+        __syncthreads();
+        const int s = (N + kObjThreads32) / kObjThreads32;      // ceil((N + 1) / threads)
+        const int k0 = m > 0 ? min(gt * s, N + 1) : 0, k1 = m > 0 ? min(k0 + s, N + 1) : 0;
+        // anti-causal: T_k = q_k + g_{k+1} T_{k+1}, T_N = 0 (g_N = dB); a
+        // thread's chunk reads and writes only its own entries of Q
         {
             float qq = 0.f;
             for (int k = k1 - 1; k >= k0; --k) {
@@ -319,15 +363,18 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep32(ObjAxisF ax, con
             float p = ax.dpow[k1 - k0];
             if (k0 <= N - 1 && N - 1 < k1) p *= ln.rB;
             affine_scan32<false>(p, qq, lane);
-            float y = __shfl_down_sync(0xffffffffu, qq, 1);
-            y = (lane == 31) ? 0.f : y;
+            if (lane == 0) totA[grp][warp] = make_float2(p, qq);
+            __syncthreads();
+            float yin = 0.f;                                     // carry from the warps to the right
+            for (int w = NW - 1; w > warp; --w) yin = totA[grp][w].x * yin + totA[grp][w].y;
+            const float pn = __shfl_down_sync(0xffffffffu, p, 1), qn = __shfl_down_sync(0xffffffffu, qq, 1);
+            float y = (lane == 31) ? yin : pn * yin + qn;
             for (int k = k1 - 1; k >= k0; --k) {
                 const float g = (k == N - 1) ? ln.dB : d;
                 y = (k == N) ? 0.f : g * y + Q[k];
                 Q[k] = y;
             }
         }
-        __syncwarp();
         // causal: e_k = g_k e_{k-1} + (1 - g_k^2) T_k, e_0 = 0 (g_1 = dA, g_N = dB)
         {
             float qq = 0.f;
@@ -340,8 +387,12 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep32(ObjAxisF ax, con
             if (k0 <= 1 && 1 < k1) p *= ln.rA;
             if (k0 <= N && N < k1) p *= ln.rB;
             affine_scan32<true>(p, qq, lane);
-            float y = __shfl_up_sync(0xffffffffu, qq, 1);
-            y = (lane == 0) ? 0.f : y;
+            if (lane == 31) totC[grp][warp] = make_float2(p, qq);
+            __syncthreads();
+            float yin = 0.f;                                     // carry from the warps to the left
+            for (int w = 0; w < warp; ++w) yin = totC[grp][w].x * yin + totC[grp][w].y;
+            const float pp = __shfl_up_sync(0xffffffffu, p, 1), qp = __shfl_up_sync(0xffffffffu, qq, 1);
+            float y = (lane == 0) ? yin : pp * yin + qp;
             for (int k = k0; k < k1; ++k) {
                 const float g = (k == 1) ? ln.dA : (k == N ? ln.dB : d);
                 const float cg = (k == 1) ? ln.cA : (k == N ? ln.cB : c);
@@ -349,17 +400,31 @@ __global__ void __launch_bounds__(32 * kObjWarps) k_obj_sweep32(ObjAxisF ax, con
                 Q[k] = y;
             }
         }
-        __syncwarp();
+        __syncthreads();
         // e += A' e^{-alpha (x - a)} + B' e^{-alpha (b - x)} with e_0 = e_N = 0
-        const float Bp = -Q[N] * ln.inv, Ap = -Bp * ln.mu;
-        const float Ad = Ap * ln.dA, Bd = Bp * ln.dB;
-        for (int k = 1 + lane; k <= m; k += 32) {
-            const float e = Q[k] + Ad * ax.dpow[k - 1] + Bd * ax.dpow[m - k];
-            const float v = H[k] + Lo[k];
-            const long long at = base + (k - 1) * st;
-            const float r = (mode == OBJF_LINV) ? v - e : e;
-            out[at] = accum ? out[at] + r : r;
-            if (mode == OBJF_BOTH) out2[at] = v - e;
+        if (gt == 0 && m > 0) {
+            const float Bp = -Q[N] * ln.inv, Ap = -Bp * ln.mu;
+            l_Ad[grp] = Ap * ln.dA;
+            l_Bd[grp] = Bp * ln.dB;
+        }
+        __syncthreads();
+        {
+            const int mj = l_m[ij];
+            const long long bj = l_base[ij], pj = l_pos[ij];
+            const float *Hj = smf + (size_t)ij * 4 * slot, *Lj = Hj + slot, *Qj = Hj + 3 * slot;
+            const float Ad = l_Ad[ij], Bd = l_Bd[ij];
+            for (long long r = p_lo + ii; r <= p_hi; r += NT / CPB) {
+                const long long kk = r - pj + 1;
+                if (kk >= 1 && kk <= mj) {
+                    const int k = (int)kk;
+                    const float e = Qj[k] + Ad * ax.dpow[k - 1] + Bd * ax.dpow[mj - k];
+                    const float v = Hj[k] + Lj[k];
+                    const long long at = bj + (k - 1) * st;
+                    const float rr = (mode == OBJF_LINV) ? v - e : e;
+                    out[at] = accum ? out[at] + rr : rr;
+                    if (mode == OBJF_BOTH) out2[at] = v - e;
+                }
+            }
         }
     }
 }
@@ -603,6 +668,7 @@ struct mol_embed_ctx {
     double *io[2] = {nullptr, nullptr}; // device copies of mol_embed_solve_host
     std::vector<void *> allocs;
     int smem = 0, grid = 1, slot = 2;     // sweep launch: shared memory, CTAs, elements per line array
+    int smem32[2] = {0, 0}, grid32[2] = {1, 1};   // float32 sweep launch per axis
     int64_t launches = 0;
     std::string err;
     bool timing = false;                // per-kind CUDA events (0 x sweeps, 1 y sweeps, 2 combinations)
@@ -770,14 +836,20 @@ mol_status sweep32(mol_embed_ctx *e, int a, const float *in, const float *lo, fl
                    int accum, cudaStream_t s)
 {
     if (e->nlines[a] == 0) return MOL_OK;
-    const int grid = std::min(e->grid, (e->nlines[a] + kObjWarps - 1) / kObjWarps);
+    const int cpb = kObjCpb[a];
+    const int grid = std::min(e->grid32[a], (e->nlines[a] + cpb - 1) / cpb);
     Timed t(e, a, s);
-    if (lo)
-        k_obj_sweep32<true><<<grid, 32 * kObjWarps, e->smem, s>>>(e->ax32[a], e->lines32[a], e->nlines[a], in, lo, out,
-                                                                  out2, mode, accum, e->slot);
-    else
-        k_obj_sweep32<false><<<grid, 32 * kObjWarps, e->smem, s>>>(e->ax32[a], e->lines32[a], e->nlines[a], in, nullptr,
-                                                                   out, out2, mode, accum, e->slot);
+    auto launch = [&](auto kern) {
+        kern<<<grid, kObjThreads32 * cpb, e->smem32[a], s>>>(e->ax32[a], e->lines32[a], e->nlines[a], in, lo, out,
+                                                             out2, mode, accum, e->slot);
+    };
+    if (cpb == 1) {
+        if (lo) launch(k_obj_sweep32<true, 1>);
+        else launch(k_obj_sweep32<false, 1>);
+    } else {
+        if (lo) launch(k_obj_sweep32<true, kObjCpb[1]>);
+        else launch(k_obj_sweep32<false, kObjCpb[1]>);
+    }
     ++e->launches;
     ECK(cudaGetLastError(), "line-object sweep (float32)");
     return MOL_OK;
@@ -1027,22 +1099,39 @@ mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double
     if (st == MOL_OK) {
         // line arrays sized for the longest line (even, for 16-byte alignment)
         e->slot = (int)((maxm + 2 + 1) & ~(int64_t)1);
-        // float64: two line arrays of doubles; float32: four of floats (the same bytes)
-        e->smem = (int)(sizeof(double) * 2 * (size_t)e->slot * kObjWarps);
-        const void *kf = prec == MOL_FP64 ? (const void *)k_obj_sweep : (const void *)k_obj_sweep32<true>;
-        if ((ce = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem)) != cudaSuccess ||
-            (prec == MOL_MIXED &&
-             (ce = cudaFuncSetAttribute(k_obj_sweep32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem)) !=
-                 cudaSuccess))
-            st = efail(e, MOL_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));
+        // float64: two line arrays of doubles per warp; float32: four arrays of
+        // floats per line
         int dev = 0, sms = 152, per_sm = 1;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (st == MOL_OK &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prec == MOL_FP64 ? (const void *)k_obj_sweep
-                                                                                 : (const void *)k_obj_sweep32<true>,
-                                                          32 * kObjWarps, e->smem) != cudaSuccess) {
-            cudaGetLastError();
-            per_sm = 1;
+        if (prec == MOL_FP64) {
+            e->smem = (int)(sizeof(double) * 2 * (size_t)e->slot * kObjWarps);
+            if ((ce = cudaFuncSetAttribute(k_obj_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem)) !=
+                cudaSuccess)
+                st = efail(e, MOL_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));
+            if (st == MOL_OK && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_obj_sweep, 32 * kObjWarps,
+                                                                              e->smem) != cudaSuccess) {
+                cudaGetLastError();
+                per_sm = 1;
+            }
+        } else {
+            const void *kf[2][2] = {{(const void *)k_obj_sweep32<true, 1>, (const void *)k_obj_sweep32<false, 1>},
+                                    {(const void *)k_obj_sweep32<true, kObjCpb[1]>,
+                                     (const void *)k_obj_sweep32<false, kObjCpb[1]>}};
+            for (int a = 0; a < 2 && st == MOL_OK; ++a) {
+                e->smem32[a] = (int)(sizeof(float) * 4 * (size_t)e->slot * kObjCpb[a]);
+                for (int v = 0; v < 2 && st == MOL_OK; ++v)
+                    if ((ce = cudaFuncSetAttribute(kf[a][v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   e->smem32[a])) != cudaSuccess)
+                        st = efail(e, MOL_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(ce));
+                int ps = 1;
+                if (st == MOL_OK && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kf[a][0], kObjThreads32 *
+                                                                                  kObjCpb[a], e->smem32[a]) !=
+                                        cudaSuccess) {
+                    cudaGetLastError();
+                    ps = 1;
+                }
+                e->grid32[a] = std::max(1, sms) * std::max(1, ps);
+            }
         }
         e->grid = std::max(1, sms) * std::max(1, per_sm);
     }
