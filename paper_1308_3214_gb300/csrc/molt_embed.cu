@@ -435,27 +435,39 @@ struct CombTermsF {
     float c[kCombMax];
     const float *x[kCombMax];
 };
-__global__ void __launch_bounds__(256) k_obj_combine32(CombTermsF t, float *out, int64_t N)
+// Both kernels below touch the interior nodes only, row by row (the line
+// objects of the contiguous axis): outside the domain every field stays zero.
+__global__ void __launch_bounds__(256) k_obj_combine32(CombTermsF t, const ObjLineF *rows, int nrows, float *out)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        float v = 0.f;
-        for (int k = 0; k < t.n; ++k) v += t.c[k] * t.x[k][i];
-        out[i] = v;
+    for (int li = blockIdx.x; li < nrows; li += gridDim.x) {
+        const long long base = rows[li].base;
+        const int m = rows[li].m;
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const long long i = base + k;
+            float v = 0.f;
+            for (int j = 0; j < t.n; ++j) v += t.c[j] * t.x[j][i];
+            out[i] = v;
+        }
     }
 }
 
 // next level in pair arithmetic: (nh, nl) = a u + b up + c (F + sum_t c_t x_t)
-__global__ void __launch_bounds__(256) k_obj_level32(CombTermsF t, const float *uh, const float *ul, const float *ph,
-                                                     const float *pl, float a, float b, float cF, float *nh, float *nl,
-                                                     int64_t N)
+__global__ void __launch_bounds__(256) k_obj_level32(CombTermsF t, const ObjLineF *rows, int nrows, const float *uh,
+                                                     const float *ul, const float *ph, const float *pl, float a,
+                                                     float b, float cF, float *nh, float *nl)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        float F = 0.f;
-        for (int k = 0; k < t.n; ++k) F += t.c[k] * t.x[k][i];
-        float h, l;
-        molt::level_pair(uh[i], ul[i], b != 0.f ? ph[i] : 0.f, b != 0.f ? pl[i] : 0.f, F, a, b, cF, h, l);
-        nh[i] = h;
-        nl[i] = l;
+    for (int li = blockIdx.x; li < nrows; li += gridDim.x) {
+        const long long base = rows[li].base;
+        const int m = rows[li].m;
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const long long i = base + k;
+            float F = 0.f;
+            for (int j = 0; j < t.n; ++j) F += t.c[j] * t.x[j][i];
+            float h, l;
+            molt::level_pair(uh[i], ul[i], b != 0.f ? ph[i] : 0.f, b != 0.f ? pl[i] : 0.f, F, a, b, cF, h, l);
+            nh[i] = h;
+            nl[i] = l;
+        }
     }
 }
 
@@ -873,9 +885,9 @@ mol_status apply_D32(mol_embed_ctx *e, const float *v, float *out, cudaStream_t 
 
 mol_status combine32(mol_embed_ctx *e, const CombTermsF &t, float *out, cudaStream_t s)
 {
-    const int64_t blocks = std::min<int64_t>((e->N + 255) / 256, 4096);
+    if (e->nlines[0] == 0) return MOL_OK;
     Timed tm(e, 2, s);
-    k_obj_combine32<<<(unsigned)blocks, 256, 0, s>>>(t, out, e->N);
+    k_obj_combine32<<<std::min(e->nlines[0], e->grid32[0]), 256, 0, s>>>(t, e->lines32[0], e->nlines[0], out);
     ++e->launches;
     ECK(cudaGetLastError(), "combine (float32)");
     return MOL_OK;
@@ -907,9 +919,10 @@ mol_status run_update32(mol_embed_ctx *e, const float *uh, const float *ul, cons
         if (p < P || !nh) {
             EST(combine32(e, t, p < P ? e->Fb32 : F32, s));
         } else {
-            const int64_t blocks = std::min<int64_t>((e->N + 255) / 256, 4096);
+            if (e->nlines[0] == 0) continue;
             Timed tm(e, 2, s);
-            k_obj_level32<<<(unsigned)blocks, 256, 0, s>>>(t, uh, ul, ph, pl, ea, eb, ec, nh, nl, e->N);
+            k_obj_level32<<<std::min(e->nlines[0], e->grid32[0]), 256, 0, s>>>(t, e->lines32[0], e->nlines[0], uh, ul,
+                                                                                ph, pl, ea, eb, ec, nh, nl);
             ++e->launches;
             ECK(cudaGetLastError(), "level update (float32 pairs)");
         }
