@@ -259,3 +259,26 @@ def test_mixed_disk_standing_mode_matches_fp64_error(P):
         s.close()
         errs.append(np.sqrt(g.hx * g.hy * np.sum((u - ex) ** 2)))
     assert abs(errs[1] - errs[0]) <= 0.01 * errs[0], errs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_ellipse_matches_oracle(prec):
+    """The timed workload itself: the ellipse on the 2048^2 grid (1,359,906
+    interior nodes, lines of up to 903), P = 2, CFL 1, three steps from host
+    memory in the launch configuration the benchmark uses."""
+    g = workloads.ellipse_grid(2048)
+    P, cfl = 2, 1.0
+    s = molt_solver(g, cfl, P, prec)
+    u0 = workloads.gaussian_embedded(g, seed=1006, width=0.15)
+    got = s.solve_host(u0, 3)
+    beta = oracle.beta_max(P)
+    alpha = beta / (cfl * g.hx)
+    ref = oracle.run_embed(u0, 3, g, alpha, P, beta)
+    tol = 10 * _tol(g) if prec == "fp64" else _step_tol(g, u0, 3, alpha, P, beta, cfl, ref)
+    assert _rel(got, ref) <= tol, (_rel(got, ref), tol)
+    assert not got[~g.mask].any()
+    s.close()
+
+
+def molt_solver(g, cfl, P, prec):
+    return _solver(g, cfl, P) if prec == "fp64" else _mixed(g, cfl, P)
