@@ -543,6 +543,15 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle",
                                 "sample": f"{ssteps} oracle steps on a {'x'.join(map(str, sshape))} grid "
                                           f"({sdt:.1f} s), same CFL, P, boundary"}
+        import oracle
+        oracle.set_threads(1)
+        try:
+            r1, s1, k1, t1, _ = cpu_oracle_rate(spec, budget_s=5.0)
+        finally:
+            oracle.set_threads(cores)
+        line["cpu_baseline"]["single_thread"] = {
+            "value": r1, "unit": METRIC, "cores": 1,
+            "sample": f"{k1} oracle steps on a {'x'.join(map(str, s1))} grid ({t1:.1f} s)"}
     solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -81,6 +81,7 @@ def _load():
         lib.orc_F_embed.argtypes = [dp, dp] + geo + [D, I, D]
         lib.orc_run_embed.argtypes = [dp, dp, L] + geo + [D, I, D]
         lib.orc_num_threads.restype = I
+        lib.orc_set_threads.argtypes = [I]
         _lib = lib
     return _lib
 
@@ -113,6 +114,11 @@ def _bc(bc) -> int:
 
 def num_threads() -> int:
     return _load().orc_num_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (timing only)."""
+    _load().orc_set_threads(int(n))
 
 
 def weights(nu: float, quad: int = 2):

@@ -929,6 +929,10 @@ void orc_run_embed(const double *u0, double *u_out, long nsteps, long nx, long n
 #ifdef _OPENMP
 #include <omp.h>
 int orc_num_threads(void) { return omp_get_max_threads(); }
+/* threads of the parallel loops that follow (timing only; results do not
+   depend on it: every loop is over independent lines) */
+void orc_set_threads(int n) { if (n > 0) omp_set_num_threads(n); }
 #else
 int orc_num_threads(void) { return 1; }
+void orc_set_threads(int n) { (void)n; }
 #endif

@@ -447,3 +447,22 @@ def test_table2_errors_reproduced(row):
     P, dt, err = int(row[0]), float(row[1]), float(row[2])
     ours = _table2_error(P, dt, TABLE2_BETA[P])
     assert ours == pytest.approx(err, rel=0.01)
+
+
+def test_thread_count_does_not_change_the_oracle():
+    """The oracle's parallel loops run over independent lines, so one thread
+    and all threads give bitwise the same steps (the single-thread timing of
+    the benchmark measures the same computation)."""
+    from paper_1308_3214_gb300 import workloads
+    n0 = oracle.num_threads()
+    u = workloads.gaussian_2d(96, seed=1002, ny=80)
+    beta = oracle.beta_max(3)
+    try:
+        oracle.set_threads(1)
+        one = oracle.run(u, u, 4, beta / 2.0, 3, beta, "dirichlet")
+        oracle.set_threads(max(n0, 2))
+        many = oracle.run(u, u, 4, beta / 2.0, 3, beta, "dirichlet")
+    finally:
+        oracle.set_threads(n0)
+    for a, b in zip(one, many):
+        assert np.array_equal(a, b)
