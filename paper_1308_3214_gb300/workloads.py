@@ -183,7 +183,11 @@ def conic_grid(n: int, lo: float, hi: float, q) -> EmbeddedGrid:
     eps = 1e-9 * h
     rxa, rxb = _chords(a, 2 * b * xs + d, c * xs * xs + e * xs + f)      # x-chord of row y = xs[j]
     cya, cyb = _chords(c, 2 * b * xs + e, a * xs * xs + d * xs + f)      # y-chord of column x = xs[i]
-    if (np.nanmin(rxa) <= lo or np.nanmax(rxb) >= hi or np.nanmin(cya) <= lo or np.nanmax(cyb) >= hi):
+    def outside(t, beyond):
+        t = t[np.isfinite(t)]                      # rows or columns that meet the domain
+        return t.size > 0 and bool(beyond(t).any())
+    if (outside(rxa, lambda t: t <= lo) or outside(rxb, lambda t: t >= hi) or outside(cya, lambda t: t <= lo)
+            or outside(cyb, lambda t: t >= hi)):
         raise ValueError("the domain must lie inside the grid")
     with np.errstate(invalid="ignore"):
         in_row = (xs[None, :] > rxa[:, None] + eps) & (xs[None, :] < rxb[:, None] - eps)

@@ -282,3 +282,32 @@ def test_full_size_ellipse_matches_oracle(prec):
 
 def molt_solver(g, cfl, P, prec):
     return _solver(g, cfl, P) if prec == "fp64" else _mixed(g, cfl, P)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_degenerate_domains(prec):
+    """A disk around one grid node (every line object has m = 1) and a disk
+    between the nodes (no interior node: no line, nothing to do)."""
+    from paper_1308_3214_gb300 import molt
+    g = workloads.disk_grid(11, radius=0.15, half=1.1)
+    assert g.mask.sum() == 1
+    P, cfl = 2, 1.0
+    beta = oracle.beta_max(P)
+    alpha = beta / (cfl * g.hx)
+    s = molt.EmbedSolver(g, dt=cfl * g.hx, P=P, prec=prec)
+    u0 = np.where(g.mask, 0.7, 0.0)
+    for axis in (0, 1):
+        got = s.linv(_dev(u0), axis).cpu().numpy()
+        ref = oracle.linv_axis_embed(u0, axis, g, alpha)
+        assert abs(got - ref).max() <= (1e-12 if prec == "fp64" else 1e-6)
+    got = s.solve_host(u0, 5)
+    ref = oracle.run_embed(u0, 5, g, alpha, P, beta)
+    assert abs(got - ref).max() <= (1e-12 if prec == "fp64" else 1e-6)
+    s.close()
+    g = workloads.disk_grid(10, radius=0.05, half=1.1)
+    assert not g.mask.any()
+    s = molt.EmbedSolver(g, dt=cfl * g.hx, P=P, prec=prec)
+    z = np.zeros((g.ny, g.nx))
+    assert not s.solve_host(z, 3).any()
+    assert not s.apply_F(_dev(z)).cpu().numpy().any()
+    s.close()
