@@ -518,6 +518,10 @@ def main():
 
     if rank == 0 and not args.no_accuracy and len(shape) == 2:
         line["accuracy"] = accuracy_check(spec, make, molt, torch)
+    elif rank == 0 and not args.no_accuracy and len(shape) == 3 and spec["bc"] == "periodic":
+        line["accuracy"] = accuracy_check_3d(spec, make, torch, dt)
+    elif rank == 0 and not args.no_accuracy and len(shape) == 1 and spec["bc"] == "periodic":
+        line["accuracy"] = accuracy_check_1d(spec, make, torch, dt)
 
     if not args.no_e2e:
         calls, per_call = 3, max(1, min(spec["steps_in_config"], args.steps))
@@ -1270,6 +1274,73 @@ def accuracy_check(spec, make, molt, torch):
             "equal_l2": bool(abs(e_m - e_d) <= 0.05 * e_d),
             "rel_l2_mixed_vs_fp64": float(np.linalg.norm(out["mixed"] - out["fp64"]) / np.linalg.norm(out["fp64"])),
             "reference": f"fp64 on {nf}x{nf}, dt/2, {2 * nsteps} steps, shared nodes"}
+
+
+def accuracy_check_3d(spec, make, torch, dt):
+    """Mixed vs FP64 at equal L2 error (3D periodic): both paths run the
+    workload's step count from the Fourier field; E_X = rel L2 against the
+    exact solution sum_m a_m cos(k_m . x + phi_m) cos(|k_m| t) (c = 1, zero
+    initial velocity)."""
+    n = spec["shape"][0]
+    nsteps = spec["steps_in_config"]
+    u0, modes = workloads.fourier_3d(n, seed=1003)
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = make(prec)
+        up = torch.from_numpy(u0).cuda()
+        uc = s.start(up)
+        s.step(up, uc, nsteps - 1)
+        out[prec] = uc.cpu().numpy()
+        s.close()
+    t = nsteps * dt
+    x = workloads.axis_coords(n, 0.0, 2 * np.pi, "periodic")
+    exact = np.zeros((n, n, n))
+    for kx, ky, kz, amp, ph in modes:
+        w = np.sqrt(kx * kx + ky * ky + kz * kz)
+        e = (amp * np.cos(w * t)) * np.exp(1j * ph) * (np.exp(1j * kz * x)[:, None, None]
+                                                       * np.exp(1j * ky * x)[None, :, None]
+                                                       * np.exp(1j * kx * x)[None, None, :])
+        exact += e.real
+    nr = np.linalg.norm(exact)
+    e_m = float(np.linalg.norm(out["mixed"] - exact) / nr)
+    e_d = float(np.linalg.norm(out["fp64"] - exact) / nr)
+    return {"steps": nsteps, "t": t, "E_mixed": e_m, "E_fp64": e_d,
+            "equal_l2": bool(abs(e_m - e_d) <= 0.05 * e_d),
+            "rel_l2_mixed_vs_fp64": float(np.linalg.norm(out["mixed"] - out["fp64"]) / np.linalg.norm(out["fp64"])),
+            "reference": "exact solution sum_m a_m cos(k_m . x + phi_m) cos(|k_m| t) of the 16 modes"}
+
+
+def accuracy_check_1d(spec, make, torch, dt):
+    """The 1D periodic configuration over its step count: mixed and FP64
+    against the exact solution (each Fourier mode times cos(k t); c = 1, zero
+    initial velocity) and against the FP64 oracle's own run."""
+    import oracle
+    oracle.build()
+    n, P = spec["shape"][0], spec["P"]
+    nsteps = spec["steps_in_config"]
+    rng = np.random.default_rng(1001)                    # the coefficients of workloads.fourier_1d
+    a, b = rng.normal(size=8), rng.normal(size=8)
+    u0 = spec["field"]()
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = make(prec)
+        up = torch.from_numpy(u0).cuda()
+        uc = s.start(up)
+        s.step(up, uc, nsteps - 1)
+        out[prec] = uc.cpu().numpy()
+        s.close()
+    t = nsteps * dt
+    x = workloads.axis_coords(n, 0.0, 2 * np.pi, "periodic")
+    exact = sum((a[k - 1] * np.cos(k * x) + b[k - 1] * np.sin(k * x)) * np.cos(k * t) for k in range(1, 9))
+    beta = oracle.beta_max(P)
+    nu = beta / spec["cfl"]
+    u1 = oracle.start(u0, nu, P, beta, "periodic")
+    _, ref = oracle.run(u0, u1, nsteps - 1, nu, P, beta, "periodic")
+    rel = lambda v, r: float(np.linalg.norm(v - r) / np.linalg.norm(r))
+    e_m, e_d = rel(out["mixed"], exact), rel(out["fp64"], exact)
+    return {"steps": nsteps, "t": t, "E_mixed": e_m, "E_fp64": e_d, "equal_l2": bool(abs(e_m - e_d) <= 0.05 * e_d),
+            "rel_l2_fp64_vs_oracle": rel(out["fp64"], ref), "rel_l2_mixed_vs_oracle": rel(out["mixed"], ref),
+            "reference": "exact solution sum_k (a_k cos kx + b_k sin kx) cos(k t), and the oracle's run"}
 
 
 if __name__ == "__main__":
