@@ -884,14 +884,15 @@ def main_extension(args, spec):
 def embedded_bytes_per_point(P: int, prec: str = "fp64") -> float:
     """Algorithmic bytes of the line-object sweeps per interior point and step.
     float64: C = 4 sweeps (D_x, L_y^{-1}, D_y, L_x^{-1} accumulated: 16 + 16 +
-    16 + 24 B), D = 2 sweeps (L_y^{-1}, the subtraction from v: 16 + 24 B).
-    float32: C of the pair level (8 B in) 12 + 8 + 12 + 12 B, C of a float32
-    field 8 + 8 + 8 + 12 B, D (D_y v and L_y^{-1} v in one sweep, then D_x
-    accumulated) 12 + 12 B.  Table 3 builds 1 + P(P-1)/2 C's (the first on the
-    level) and P - 1 D's per step."""
+    16 + 24 B), D = 2 sweeps (L_y^{-1}, the subtraction from v: 16 + 24 B);
+    Table 3 builds 1 + P(P-1)/2 C's and P - 1 D's per step.
+    float32: C of the pair level (8 B in) 12 + 8 + 12 + 12 B; D (D_y v and
+    L_y^{-1} v in one sweep that also keeps D_y v for the C of the same field,
+    then D_x accumulated) 16 + 12 B; the C of that field, its D_y v already
+    formed, 8 + 8 + 12 B; any other C of a float32 field 8 + 8 + 8 + 12 B."""
     nC = 1 + P * (P - 1) // 2
     if prec == "mixed":
-        return 44.0 + 36.0 * (nC - 1) + 24.0 * (P - 1)
+        return 44.0 + (P - 1) * (28.0 + 28.0) + (nC - 1 - (P - 1)) * 36.0
     return 88.0 * nC + 40.0 * (P - 1)
 
 

@@ -258,7 +258,7 @@ struct ObjAxisF {
 enum : int { OBJF_D = 0, OBJF_LINV = 1, OBJF_BOTH = 2 };
 
 // MODE OBJF_D: out = D v; OBJF_LINV: out = v - D v (= L^{-1} v); OBJF_BOTH:
-// out = D v and out2 = v - D v.  accum adds to out.  PAIR: v is a float32
+// out = D v and out2 = v - D v (and out3 = D v when given).  accum adds to out.  PAIR: v is a float32
 // pair level (in = hi, lo = lo plane), else a float32 field.
 // A CTA takes CPB consecutive line objects at a time, kObjThreads32 threads
 // per line.  Loads and stores run over grid positions along the lines, the
@@ -272,7 +272,8 @@ template <bool PAIR, int CPB>
 __global__ void __launch_bounds__(kObjThreads32 * CPB) k_obj_sweep32(ObjAxisF ax, const ObjLineF *lines, int nlines,
                                                                     const float *__restrict__ in,
                                                                     const float *__restrict__ lo, float *out,
-                                                                    float *out2, int mode, int accum, int slot)
+                                                                    float *out2, float *out3, int mode, int accum,
+                                                                    int slot)
 {
     constexpr int NW = kObjThreads32 / 32, NT = kObjThreads32 * CPB;
     extern __shared__ __align__(16) float smf[];
@@ -422,7 +423,10 @@ __global__ void __launch_bounds__(kObjThreads32 * CPB) k_obj_sweep32(ObjAxisF ax
                     const long long at = bj + (k - 1) * st;
                     const float rr = (mode == OBJF_LINV) ? v - e : e;
                     out[at] = accum ? out[at] + rr : rr;
-                    if (mode == OBJF_BOTH) out2[at] = v - e;
+                    if (mode == OBJF_BOTH) {
+                        out2[at] = v - e;
+                        if (out3) out3[at] = e;
+                    }
                 }
             }
         }
@@ -689,7 +693,7 @@ struct mol_embed_ctx {
     ObjLineF *lines32[2] = {nullptr, nullptr};
     float *dpow32[2] = {nullptr, nullptr};
     float *V32[kMaxP + 1] = {};
-    float *tmp32 = nullptr, *t132 = nullptr, *t232 = nullptr, *Fb32 = nullptr;
+    float *tmp32 = nullptr, *t132 = nullptr, *t232 = nullptr, *t332 = nullptr, *Fb32 = nullptr;
     float *lh[3] = {nullptr, nullptr, nullptr}, *ll[3] = {nullptr, nullptr, nullptr};   // pair levels
     std::vector<cudaEvent_t> ev_pool;
     struct Rec { int kind; cudaEvent_t a, b; };
@@ -845,7 +849,7 @@ mol_status run_update(mol_embed_ctx *e, const double *u, const double *up, doubl
 // ---- float32 sweeps (MOL_MIXED) ----
 // one difference-form sweep along axis a; lo: the lo plane when in is a pair level
 mol_status sweep32(mol_embed_ctx *e, int a, const float *in, const float *lo, float *out, float *out2, int mode,
-                   int accum, cudaStream_t s)
+                   int accum, cudaStream_t s, float *out3 = nullptr)
 {
     if (e->nlines[a] == 0) return MOL_OK;
     const int cpb = kObjCpb[a];
@@ -853,7 +857,7 @@ mol_status sweep32(mol_embed_ctx *e, int a, const float *in, const float *lo, fl
     Timed t(e, a, s);
     auto launch = [&](auto kern) {
         kern<<<grid, kObjThreads32 * cpb, e->smem32[a], s>>>(e->ax32[a], e->lines32[a], e->nlines[a], in, lo, out,
-                                                             out2, mode, accum, e->slot);
+                                                             out2, out3, mode, accum, e->slot);
     };
     if (cpb == 1) {
         if (lo) launch(k_obj_sweep32<true, 1>);
@@ -867,19 +871,25 @@ mol_status sweep32(mol_embed_ctx *e, int a, const float *in, const float *lo, fl
     return MOL_OK;
 }
 
-// out = C v (eq. C_def_ADI) with L^{-1} = 1 - D: D_x v - D_y D_x v + D_y v - D_x D_y v
-mol_status apply_C32(mol_embed_ctx *e, const float *v, const float *vlo, float *out, cudaStream_t s)
+// out = C v (eq. C_def_ADI) with L^{-1} = 1 - D: D_x v - D_y D_x v + D_y v - D_x D_y v.
+// dyv: D_y v when an earlier sweep has formed it, else null.
+mol_status apply_C32(mol_embed_ctx *e, const float *v, const float *vlo, float *out, cudaStream_t s,
+                     const float *dyv = nullptr)
 {
     EST(sweep32(e, 0, v, vlo, e->t132, nullptr, OBJF_D, 0, s));               // t1 = D_x v
     EST(sweep32(e, 1, e->t132, nullptr, out, nullptr, OBJF_LINV, 0, s));      // out = L_y^{-1} t1
-    EST(sweep32(e, 1, v, vlo, e->t132, nullptr, OBJF_D, 0, s));               // t1 = D_y v
-    return sweep32(e, 0, e->t132, nullptr, out, nullptr, OBJF_LINV, 1, s);    // out += L_x^{-1} t1
+    if (!dyv) {
+        EST(sweep32(e, 1, v, vlo, e->t132, nullptr, OBJF_D, 0, s));           // t1 = D_y v
+        dyv = e->t132;
+    }
+    return sweep32(e, 0, dyv, nullptr, out, nullptr, OBJF_LINV, 1, s);       // out += L_x^{-1} D_y v
 }
 
-// out = D v (eq. D_def_ADI) = v - L_x^{-1} L_y^{-1} v = D_y v + D_x (L_y^{-1} v)
-mol_status apply_D32(mol_embed_ctx *e, const float *v, float *out, cudaStream_t s)
+// out = D v (eq. D_def_ADI) = v - L_x^{-1} L_y^{-1} v = D_y v + D_x (L_y^{-1} v); dyv, when
+// given, receives D_y v as well
+mol_status apply_D32(mol_embed_ctx *e, const float *v, float *out, cudaStream_t s, float *dyv = nullptr)
 {
-    EST(sweep32(e, 1, v, nullptr, out, e->t232, OBJF_BOTH, 0, s));            // out = D_y v, t2 = L_y^{-1} v
+    EST(sweep32(e, 1, v, nullptr, out, e->t232, OBJF_BOTH, 0, s, dyv));       // out = D_y v, t2 = L_y^{-1} v
     return sweep32(e, 0, e->t232, nullptr, out, nullptr, OBJF_D, 1, s);       // out += D_x t2
 }
 
@@ -904,9 +914,10 @@ mol_status run_update32(mol_embed_ctx *e, const float *uh, const float *ul, cons
         if (p == 1) {
             EST(apply_C32(e, uh, ul, e->V32[1], s));
         } else {
-            EST(apply_D32(e, e->V32[p - 1], e->V32[p], s));
+            // D_y V_{p-1} serves both D V_{p-1} and C V_{p-1}: formed once
+            EST(apply_D32(e, e->V32[p - 1], e->V32[p], s, e->t332));
             for (int k = 1; k < p; ++k) {
-                EST(apply_C32(e, e->V32[k], nullptr, e->tmp32, s));
+                EST(apply_C32(e, e->V32[k], nullptr, e->tmp32, s, k == p - 1 ? e->t332 : nullptr));
                 std::swap(e->V32[k], e->tmp32);
             }
         }
@@ -1097,7 +1108,7 @@ mol_status mol_embed_create(const mol_embed_geom *g, double c, double dt, double
         for (double **b : {&e->tmp, &e->t1, &e->lev, &e->Fb}) work.push_back({(void **)b, plane});
         for (int k = 1; k <= P; ++k) work.push_back({(void **)&e->V[k], plane});
     } else {
-        for (float **b : {&e->tmp32, &e->t132, &e->t232, &e->Fb32}) work.push_back({(void **)b, plane32});
+        for (float **b : {&e->tmp32, &e->t132, &e->t232, &e->t332, &e->Fb32}) work.push_back({(void **)b, plane32});
         for (int k = 1; k <= P; ++k) work.push_back({(void **)&e->V32[k], plane32});
         for (int k = 0; k < 3; ++k) {
             work.push_back({(void **)&e->lh[k], plane32});
