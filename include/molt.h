@@ -373,7 +373,7 @@ mol_status mol_batch_pass_times(mol_batch b, double total_ms[3], int64_t launche
  *
  * Fields: caller-owned device float64 arrays (ny, nx) that vanish outside the
  * domain (outputs vanish there too).  The library owns its tables and work
- * fields (P + 4 fields of nx ny doubles; mixed: P + 10 of floats) and frees
+ * fields (P + 4 fields of nx ny doubles; mixed: P + 11 of floats) and frees
  * them in mol_embed_destroy.
  * Calls are asynchronous on the given stream; errors are returned statuses
  * (MOL_EINVAL arguments or geometry, MOL_EUNSTABLE beta above beta_max(P),

@@ -258,8 +258,9 @@ struct ObjAxisF {
 enum : int { OBJF_D = 0, OBJF_LINV = 1, OBJF_BOTH = 2 };
 
 // MODE OBJF_D: out = D v; OBJF_LINV: out = v - D v (= L^{-1} v); OBJF_BOTH:
-// out = D v and out2 = v - D v (and out3 = D v when given).  accum adds to out.  PAIR: v is a float32
-// pair level (in = hi, lo = lo plane), else a float32 field.
+// out = D v and out2 = v - D v (and out3 = D v when given).  accum adds to
+// out.  PAIR: v is a float32 pair level (in = hi, lo = lo plane), else a
+// float32 field.
 // A CTA takes CPB consecutive line objects at a time, kObjThreads32 threads
 // per line.  Loads and stores run over grid positions along the lines, the
 // CPB lines interleaved, so that on the strided axis (consecutive lines =
