@@ -91,3 +91,36 @@ def test_higher_orders_are_refused():
     z = torch.zeros((33, 33), dtype=torch.float64, device="cuda")
     with pytest.raises(molt.MolError):
         s.solve_source(z, 2, z, np.zeros(3))
+
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_point_source_matches_oracle(prec):
+    """The timed source workload: [-1, 1]^2 on 2048 x 2048 nodes, P = 2,
+    CFL 2, the discrete delta 1/h^2 at the centre node times
+    f(t) = sin(4 pi t)(1 - exp(-(t/0.2)^2)), four steps from rest.  Mixed:
+    the stepping error model, 8 eps32 (1 + 1/(1 - d)) 2P sum_k |delta_k| /
+    |u_M| with delta_k the oracle's own increment of step k (F plus the
+    source terms; twice the first, half of which the start applies)."""
+    n, P, M = 2048, 2, 4
+    h = 2.0 / (n - 1)
+    dt = 2.0 * h
+    t = dt * np.arange(M + 1)
+    g = np.zeros((n, n))
+    g[n // 2, n // 2] = 1.0 / h ** 2
+    f = np.sin(4 * np.pi * t) * (1.0 - np.exp(-(t / 0.2) ** 2))
+    got, nu = gpu_source((n, n), [-1.0, -1.0], [1.0, 1.0], dt, P, prec, g, f, M)
+    beta = oracle.beta_max(P)
+    traj = [np.zeros((n, n))] + [oracle.run_source(np.zeros((n, n)), m, nu, P, beta, dt ** 2, g, f[:m + 1])
+                                 for m in range(1, M + 1)]
+    ref = traj[M]
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    if prec == "fp64":
+        assert err <= 1e-12
+    else:
+        d = np.exp(-max(nu))
+        inc = 2 * np.linalg.norm(traj[1] - traj[0])
+        inc += sum(np.linalg.norm(traj[k] - 2 * traj[k - 1] + traj[k - 2]) for k in range(2, M + 1))
+        assert err <= 8 * EPS32 * (1 + 1 / (1 - d)) * 2 * P * inc / np.linalg.norm(ref), err
