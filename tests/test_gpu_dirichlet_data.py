@@ -97,3 +97,38 @@ def test_rejects_other_grids():
     s = molt.Solver((16, 16), dt=0.01, P=1, bc="dirichlet", prec="fp64")
     with pytest.raises(molt.MolError):
         s.solve_dirichlet(torch.zeros((16, 16), dtype=torch.float64, device="cuda"), 2, np.zeros((3, 2, 2)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_standing_wave_matches_oracle(prec):
+    """The timed 1D workload: 10001 points, P = 3, CFL 2, the standing wave
+    cos(3 pi x) cos(3 pi t) with its end data, 20 steps.  float64: the bound
+    above.  Mixed: the stepping error model, 8 eps32 (1 + 1/(1 - d)) 2P
+    sum_k |delta_k| / |u_M| with delta_k the oracle's own increment of step k
+    (twice the first, half of which the start applies); the end values equal
+    the data exactly in float64, to the float32 pairs' 48 bits in mixed."""
+    n, P, M = 10001, 3, 20
+    h = 1.0 / (n - 1)
+    dt = 2.0 * h
+    x = np.linspace(0, 1, n)
+    u0 = np.cos(K * np.pi * x)
+    d = data_for(M, P, dt)
+    s = molt.Solver((n,), dt=dt, P=P, bc="dirichlet", prec=prec, lo=[0.0], hi=[1.0])
+    got = s.solve_dirichlet(torch.from_numpy(u0).cuda(), M, d).cpu().numpy()
+    alpha, nu = s.alpha, s.nu[0]
+    s.close()
+    gam = d / alpha ** (2 * np.arange(P + 1))
+    beta = oracle.beta_max(P)
+    traj = [u0] + [oracle.run_bc(u0, m, nu, P, beta, gam[:m + 1]) for m in range(1, M + 1)]
+    ref = traj[M]
+    if prec == "fp64":
+        assert np.linalg.norm(got - ref) <= 4 * 2.0 ** -52 * M / (1 - np.exp(-nu)) * np.linalg.norm(u0)
+    else:
+        inc = 2 * np.linalg.norm(traj[1] - traj[0])
+        inc += sum(np.linalg.norm(traj[k] - 2 * traj[k - 1] + traj[k - 2]) for k in range(2, M + 1))
+        tol = 8 * 2.0 ** -24 * (1 + 1 / (1 - np.exp(-nu))) * 2 * P * inc / np.linalg.norm(ref)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol, (np.linalg.norm(got - ref) / np.linalg.norm(ref), tol)
+    if prec == "fp64":
+        assert got[0] == d[-1, 0, 0] and got[-1] == d[-1, 1, 0]
+    else:                                   # levels held as float32 pairs: about 48 bits
+        assert abs(got[0] - d[-1, 0, 0]) <= 2.0 ** -46 and abs(got[-1] - d[-1, 1, 0]) <= 2.0 ** -46
