@@ -922,8 +922,13 @@ mol_status run_update32(mol_embed_ctx *e, const float *uh, const float *ul, cons
                 std::swap(e->V32[k], e->tmp32);
             }
         }
+        // F's partial sum.  The terms of stage 1 are tw_11 C u alone, and C u
+        // is still in tmp32 after stage 2 (whose only C swaps V_1 out), so
+        // with P > 1 they join the sum of stage 2 instead of a pass of their own
+        if (p == 1 && P > 1) continue;
         CombTermsF t{};
-        if (p > 1) { t.c[t.n] = 1.f; t.x[t.n++] = e->Fb32; }
+        if (p == 2) { t.c[t.n] = (float)e->tw[1 * 8 + 1]; t.x[t.n++] = e->tmp32; }
+        if (p > 2) { t.c[t.n] = 1.f; t.x[t.n++] = e->Fb32; }
         for (int k = 1; k <= p; ++k) {
             t.c[t.n] = (float)e->tw[p * 8 + (p - k + 1)];
             t.x[t.n++] = e->V32[k];
