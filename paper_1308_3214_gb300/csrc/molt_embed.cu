@@ -831,9 +831,13 @@ mol_status run_update(mol_embed_ctx *e, const double *u, const double *up, doubl
                 std::swap(e->V[k], e->tmp);
             }
         }
+        // the stage-1 term tw_11 C u is still in tmp after stage 2 (whose only C
+        // swaps V_1 out): with P > 1 it joins stage 2's sum, no pass of its own
+        if (p == 1 && P > 1) continue;
         CombTerms t{};
         const bool last = p == P;
-        if (p > 1) { t.c[t.n] = last ? ec : 1.0; t.x[t.n++] = e->Fb; }
+        if (p == 2) { t.c[t.n] = (last ? ec : 1.0) * e->tw[1 * 8 + 1]; t.x[t.n++] = e->tmp; }
+        if (p > 2) { t.c[t.n] = last ? ec : 1.0; t.x[t.n++] = e->Fb; }
         for (int k = 1; k <= p; ++k) {
             t.c[t.n] = (last ? ec : 1.0) * e->tw[p * 8 + (p - k + 1)];
             t.x[t.n++] = e->V[k];
