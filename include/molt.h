@@ -440,7 +440,8 @@ mol_status mol_embed_pass_times(mol_embed e, double total_ms[3], int64_t launche
  *
  * Set-up: the first call on each device (with that device current) looks
  * up the array's address and sets the kernels' shared-memory limits; make
- * that first call before any stream capture.
+ * that first call before any stream capture.  First calls from several host
+ * threads are serialised by a lock inside the library.
  *
  * Concurrency: the array is shared by all calls on a device.  Calls that
  * overlap in time on one device (different streams, or threads without
@@ -448,9 +449,11 @@ mol_status mol_embed_pass_times(mol_embed e, double total_ms[3], int64_t launche
  *
  * grid, c, dt, beta (<= 0 selects beta_max(P)), P, bc and quad_order (1 or
  * 2) mean what they mean for mol_create; u, F: device float64 fields of the
- * grid's size that may not overlap; stream: the CUDA stream (NULL = legacy
- * default).  Errors: MOL_EINVAL (arguments, size), MOL_EUNSTABLE (beta),
- * MOL_ECUDA (launch); text via mol_last_error(NULL).
+ * grid's size, both on the CURRENT device (the kernels run there), whose
+ * byte ranges must not intersect; stream: a stream of the current device
+ * (NULL = legacy default).  Errors: MOL_EINVAL (arguments, size, a field on
+ * another device, overlapping fields), MOL_EUNSTABLE (beta), MOL_ECUDA
+ * (launch); text via mol_last_error(NULL).
  */
 mol_status mol_apply_F_noalloc(const mol_grid *grid, double c, double dt, double beta, int P, mol_bc bc,
                                int quad_order, const double *u, double *F, void *stream);

@@ -2,6 +2,7 @@
 // CUDA-graph time loop.  See include/molt.h for the contract.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -583,6 +584,15 @@ mol_status check_ptr(mol_ctx *h, const void *p, const char *name)
     return MOL_OK;
 }
 
+// Rows split over two warps where the row length allows it (faster than one
+// warp per row on every measured grid; mol_autotune may still choose
+// otherwise).  Needs h->xtpl filled.
+void default_rows_split(mol_ctx *h)
+{
+    int r = 0;
+    if (h->ndim >= 2 && regs_rows_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, 2, &r)) h->tune_rows_warps = 2;
+}
+
 }  // namespace
 
 void molt::set_global_error(const std::string &msg) { g_err = msg; }
@@ -726,13 +736,7 @@ mol_status mol_create(const mol_grid *grid, double c, double dt, double beta, in
         for (int k = 0; k < ninter; ++k)
             if ((st = dev_alloc(h, &h->inter[k], (size_t)h->tbytes * h->N)) != MOL_OK) goto bad;
     }
-    {
-        // rows split over two warps where the row length allows it (faster
-        // than one warp per row on every measured grid; mol_autotune may
-        // still choose otherwise)
-        int r = 0;
-        if (h->ndim >= 2 && regs_rows_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, 2, &r)) h->tune_rows_warps = 2;
-    }
+    default_rows_split(h);
     if (h->ndim == 2 && bc == MOL_BC_DIRICHLET && h->n[0] <= 1024 && h->n[1] <= 1024) {
         int r = 0, S = 0, K = 0;
         const bool xreg = regs_res_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, &r) ||
@@ -1355,13 +1359,20 @@ constexpr int kNoallocCoefMax = 288;   // >= the 258 table entries of 3D, P = 5;
 std::atomic<double *> g_noalloc_ptr[kNoallocMaxDevices];
 int g_noalloc_sms[kNoallocMaxDevices];
 int g_noalloc_smem[kNoallocMaxDevices];
+std::mutex g_noalloc_setup_mutex;      // first calls on one device from several host threads
 
 // Resolve the array's device address once per device (with that device
-// current) and give the pass kernels their shared-memory limits.
+// current) and give the pass kernels their shared-memory limits.  The
+// per-device values are written under the mutex and published by the
+// release store of the pointer; later calls only read them.
 mol_status noalloc_setup(int dev, double **out)
 {
     if (dev < 0 || dev >= kNoallocMaxDevices) return fail(nullptr, MOL_EINVAL, "device ordinal out of range");
     double *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lock(g_noalloc_setup_mutex);
+        p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    }
     if (!p) {
         void *q = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
@@ -1503,11 +1514,25 @@ extern "C" mol_status mol_apply_F_noalloc(const mol_grid *grid, double c, double
                                              std::to_string(kNoallocScratchBytes));
     mol_status st;
     if ((st = check_ptr(nullptr, u, "u")) != MOL_OK || (st = check_ptr(nullptr, F, "F")) != MOL_OK) return st;
-    if (u == F) return fail(nullptr, MOL_EINVAL, "u and F must not overlap");
+    {
+        const uintptr_t ub = (uintptr_t)u, fb = (uintptr_t)F, nb = (uintptr_t)N * sizeof(double);
+        if (ub < fb + nb && fb < ub + nb) return fail(nullptr, MOL_EINVAL, "u and F must not overlap");
+    }
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    // the kernels run on the current device: both fields must live there
+    for (const void *p : {(const void *)u, (const void *)F}) {
+        cudaPointerAttributes at{};
+        if ((e = cudaPointerGetAttributes(&at, p)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(nullptr, MOL_EINVAL, "u / F: not a CUDA pointer");
+        }
+        if (at.type == cudaMemoryTypeDevice && at.device != dev)
+            return fail(nullptr, MOL_EINVAL, "u and F must be on the current device (" + std::to_string(dev) +
+                                                 "); one is on device " + std::to_string(at.device));
+    }
     double *scratch = nullptr;
     if ((st = noalloc_setup(dev, &scratch)) != MOL_OK) return st;
 
@@ -1551,6 +1576,7 @@ extern "C" mol_status mol_apply_F_noalloc(const mol_grid *grid, double c, double
     FPoly f;
     if (!expand_fixed(ndim, P, beta, f)) return fail(nullptr, MOL_EINVAL, "coefficient expansion failed");
     fill_tables(ndim, P, [&f](int i, int j, int k) { return f.c[fidx(i, j, k)]; }, h.xtpl, h.ytpl);
+    default_rows_split(&h);                           // as mol_create (float64: one warp per row either way)
     // flattened like flatten(): per output o and Horner term t, the ng field
     // weights, then the weights of u
     double flat[2 * kNoallocCoefMax];

@@ -181,16 +181,24 @@ def apply_F_noalloc(u, out, dt: float, P: int, bc: str = "dirichlet", c: float =
     allocation.  u and out: contiguous CUDA float64 tensors of one shape
     (nz, ny, nx); the library's static scratch bounds the grid size."""
     import torch
-    lib = load_library()
     for t, name in ((u, "u"), (out, "out")):
-        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+    if u.device != out.device:
+        raise ValueError(f"u ({u.device}) and out ({out.device}) must be on the same CUDA device")
+    for t, name in ((u, "u"), (out, "out")):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
             raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
     if tuple(u.shape) != tuple(out.shape):
         raise ValueError("u and out must have the same shape")
+    lib = load_library()
     g = make_grid(u.shape, lo, hi)
-    st = lib.mol_apply_F_noalloc(ctypes.byref(g), float(c), float(dt), float(beta), int(P), BC[bc],
-                                 int(quad_order), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                 ctypes.c_void_p(_stream_ptr(stream)))
+    with torch.cuda.device(u.device):           # the library launches on the current device
+        if stream is not None and stream.device != u.device:
+            raise ValueError(f"stream is on {stream.device}, the fields on {u.device}")
+        st = lib.mol_apply_F_noalloc(ctypes.byref(g), float(c), float(dt), float(beta), int(P), BC[bc],
+                                     int(quad_order), ctypes.c_void_p(u.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream)))
     if st != MOL_OK:
         raise MolError(st, lib.mol_last_error(None).decode())
     return out

@@ -240,20 +240,71 @@ def test_bad_pointer_rejected():
 # ---------------------------------------------------------------------------
 # full-size workloads, in the launch configuration the benchmark times
 # ---------------------------------------------------------------------------
+_FULL2D = {}
+
+
+def _full2d_reference(s, P):
+    """u0, u1 and the oracle's u3 of the 2048^2 workload (computed once)."""
+    if not _FULL2D:
+        n = 2048
+        u0 = workloads.gaussian_2d(n, seed=1002)
+        u1 = oracle.start(u0, s.nu, P, s.beta, "dirichlet")
+        _, rc = oracle.run(u0, u1, 2, s.nu, P, s.beta, "dirichlet")
+        _FULL2D.update(u0=u0, u1=u1, rc=rc)
+    return _FULL2D["u0"], _FULL2D["u1"], _FULL2D["rc"]
+
+
+# tunings: the handle's defaults, the autotuner's own pick, and each launch
+# variant the autotuner has kept on this grid (rows of the x pass over 2 or 4
+# warps; 64-row float32 strided segments over 4 warps per CTA, so each
+# 2048-row column runs in a cluster of 8 CTAs)
+TUNINGS_2D = [None, "auto", dict(res_warps=4, strided_rpt=0, strided_warps=4, rows_warps=4),
+              dict(res_warps=4, strided_rpt=0, strided_warps=4, rows_warps=2),
+              dict(res_warps=2, strided_rpt=32, strided_warps=8, rows_warps=8)]
+
+
 @pytest.mark.slow
+@pytest.mark.parametrize("tuning", TUNINGS_2D, ids=["default", "auto", "rows4-cl8", "rows2-cl8", "rows8-rpt32"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_full_size_2d_gaussian_two_steps(prec):
+def test_full_size_2d_gaussian_two_steps(prec, tuning):
+    """The benchmark's 2048^2 workload, two steps, in every launch
+    configuration the benchmark may time."""
     n, P, cfl = 2048, 3, 2.0
     h = 1.0 / (n - 1)
     dt = cfl * h
     s = make((n, n), dt, P, "dirichlet", prec)
-    u0 = workloads.gaussian_2d(n, seed=1002)
-    u1 = oracle.start(u0, s.nu, P, s.beta, "dirichlet")
+    if tuning == "auto":
+        s.autotune()
+    elif tuning is not None:
+        if prec == "fp64" and tuning["rows_warps"]:
+            pytest.skip("the row split is a float32 kernel")
+        s.set_tuning(**tuning)
+        assert s.tuning()["strided_warps"] == tuning["strided_warps"]
+    u0, u1, rc = _full2d_reference(s, P)
     up, uc = dev(u0), dev(u1)
     s.step(up, uc, 2)
-    _, rc = oracle.run(u0, u1, 2, s.nu, P, s.beta, "dirichlet")
     err = rel_l2(uc.cpu().numpy(), rc)
-    assert err <= (1e-12 if prec == "fp64" else 1e-8), err
+    assert err <= (1e-12 if prec == "fp64" else 1e-8), (err, s.tuning())
+    s.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("rpt,warps", [(0, 4), (0, 8), (32, 8)])
+def test_full_size_2d_strided_powers(rpt, warps):
+    """D_y^p, p = 1..3, on the 2048^2 grid with the float32 strided pass in
+    each segmenting the tuner offers (64-row segments over 4 warps: clusters
+    of 8 CTAs per 2048-row column; over 8 warps: clusters of 4; 32-row
+    segments over 8 warps: clusters of 8)."""
+    n = 2048
+    s = make((n, n), 2.0 / (n - 1), 3, "dirichlet", "mixed")
+    s.set_tuning(res_warps=4, strided_rpt=rpt, strided_warps=warps, rows_warps=4)
+    v = field((n, n), 61, "dirichlet")
+    vd = dev(v)
+    for power in (1, 2, 3):
+        got = s.apply_D(vd, 1, power).cpu().numpy()
+        ref = oracle.D_axis(v, 1, s.nu[1], "dirichlet", 2, power=power)
+        assert rel_l2(got, ref) <= tol_for("mixed", s, power), (power, rel_l2(got, ref))
+    s.close()
 
 
 @pytest.mark.slow

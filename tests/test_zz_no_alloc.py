@@ -78,6 +78,8 @@ CASES = [
     ((1000,), 4, "periodic"),
     ((256, 192), 3, "dirichlet"),        # register kernels on both axes
     ((250, 300), 2, "periodic"),         # ragged lines: shared-memory kernels
+    ((250, 300), 2, "dirichlet"),        # ragged Dirichlet: shared-memory kernels here, the handle runs
+                                         # the same F as a batch of one
     ((32, 36, 40), 2, "periodic"),
     ((64, 64, 64), 3, "dirichlet"),
     ((1024, 1280), 3, "dirichlet"),      # 2D close to the scratch limit
@@ -128,6 +130,37 @@ def test_reuse_across_shapes():
     for o, r in zip(outs, refs):
         l2, mx = rel(o, r)
         assert l2 <= 1e-12 and mx <= 1e-12, (l2, mx)
+
+
+def test_fields_on_different_devices_rejected_before_the_library():
+    """The binding refuses fields on two devices before it loads or calls
+    the library (a launch on the wrong device would read another GPU's
+    memory)."""
+    u = torch.zeros((8, 8), dtype=torch.float64)
+    o = torch.empty((8, 8), dtype=torch.float64, device="meta")
+    with pytest.raises(ValueError, match="same CUDA device"):
+        molt.apply_F_noalloc(u, o, dt=0.1, P=1)
+
+
+@pytest.mark.gpu
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2, reason="needs two GPUs")
+def test_field_on_another_device_rejected():
+    """Through the C ABI: a field on device 1 while device 0 is current."""
+    torch.cuda.set_device(0)
+    u = torch.zeros((64, 64), dtype=torch.float64, device="cuda:1")
+    o = torch.empty((64, 64), dtype=torch.float64, device="cuda:0")
+    st = call_raw((64, 64), 2, u=ctypes.c_void_p(u.data_ptr()), F=ctypes.c_void_p(o.data_ptr()))
+    assert st == molt.MOL_EINVAL
+    assert "current device" in molt.load_library().mol_last_error(None).decode()
+
+
+@pytest.mark.gpu
+def test_overlapping_fields_rejected():
+    """F starting inside u (not the same pointer) is refused."""
+    buf = torch.zeros(64 * 64 + 64, dtype=torch.float64, device="cuda")
+    st = call_raw((64, 64), 2, u=ctypes.c_void_p(buf.data_ptr()), F=ctypes.c_void_p(buf.data_ptr() + 8 * 64))
+    assert st == molt.MOL_EINVAL
+    assert "overlap" in molt.load_library().mol_last_error(None).decode()
 
 
 @pytest.mark.gpu
