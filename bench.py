@@ -375,7 +375,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512, help="problems of the batch workload (profiling)")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch variants instead of the autotuner (profiling): res_warps,strided_rpt,"
-                         "strided_warps,rows_warps for a single problem; x_warps_short,x_warps_long,y_rule for "
+                         "strided_warps,rows_warps[,rows_persist] for a single problem; x_warps_short,x_warps_long,y_rule for "
                          "the batch")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -478,7 +478,9 @@ def main():
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
     peak, peak_kind = read_peak()
     if tuning.get("rows_warps", 0) > 0:
-        xk = f"k_contig_rows (x: one row per CTA of {tuning['rows_warps']} warps; Horner + level update)"
+        how = ("persistent CTAs, next row prefetched into L2" if tuning.get("rows_persist") else "one CTA per row")
+        xk = (f"k_contig_rows (x: each row over {tuning['rows_warps']} warps of a CTA, {how}; "
+              "Horner + level update)")
     else:
         xk = "k_contig_res / k_contig (x: one row per warp; Horner + level update)"
     kernel_name = {0: xk,

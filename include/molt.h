@@ -153,7 +153,8 @@ mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t
 /*
  * Autotuner: times the launch variants that change something for this grid
  * -- the float32 x pass with one warp per row (1, 2 or 4 warps per CTA) or
- * each row split over 2 or 4 warps (rows of 32 W RPT points, RPT 16 or 32),
+ * each row split over 2, 4 or 8 warps (rows of 32 W RPT points), one CTA per
+ * row or persistent CTAs that prefetch their next row (MOL_TUNE_ROWS_PERSIST),
  * the strided segment length (64 or 32 points per thread for float32 sweeps)
  * and the segments per CTA at most (8 or 4, hence the cluster size) -- on the
  * handle's own workspace (a few steps each, CUDA events, minimum of 3
@@ -174,6 +175,32 @@ mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int stri
  * most, out[3] = warps per row (0 = one); *ms_per_step (may be NULL) = the
  * tuned step time (0 before tuning). */
 mol_status mol_get_tuning(mol_handle h, int out[4], double *ms_per_step);
+
+/* The full set of launch choices, by index (later indices may be added; a
+ * caller passes how many it knows):
+ *   MOL_TUNE_RES_WARPS .. MOL_TUNE_ROWS_WARPS: as mol_set_tuning;
+ *   MOL_TUNE_ROWS_PERSIST: 1 = the row-split x pass runs persistent CTAs
+ *     (as many as fit on the device) that walk the rows and prefetch the
+ *     next row's fields into L2 while they work on the current one; 0 = one
+ *     CTA per row;
+ *   MOL_TUNE_STRIDED_NB: 1 (default) = the float32 strided powers pass
+ *     exchanges once per sweep between neighbouring segments wherever the
+ *     decay over one segment makes that exact to below 2^-30 (d^(RPT-1) <=
+ *     2^-30); 0 = the full-carry pass (three exchanges per sweep) always.
+ * mol_set_tuning_ex takes count >= 4 values (indices past count keep their
+ * setting); mol_get_tuning_ex fills count values.  MOL_EINVAL on a value out
+ * of range, a count out of range or a choice that does not fit the grid. */
+enum {
+    MOL_TUNE_RES_WARPS = 0,
+    MOL_TUNE_STRIDED_RPT = 1,
+    MOL_TUNE_STRIDED_WARPS = 2,
+    MOL_TUNE_ROWS_WARPS = 3,
+    MOL_TUNE_ROWS_PERSIST = 4,
+    MOL_TUNE_STRIDED_NB = 5,
+    MOL_TUNE_COUNT = 6
+};
+mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count);
+mol_status mol_get_tuning_ex(mol_handle h, int *vals, int count, double *ms_per_step);
 
 /*
  * Adjoint on a single-problem handle (2D Dirichlet, at most 1024 points per

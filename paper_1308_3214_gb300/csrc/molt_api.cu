@@ -59,6 +59,9 @@ struct mol_ctx {
     // strided segment length (0 = default) and segments per CTA at most
     int tune_res_warps = 2, tune_strided_rpt = 0, tune_strided_warps = 8;
     int tune_rows_warps = 0;                   // > 0: the x pass splits each row over this many warps
+    int tune_rows_persist = 0;                 // row-split x pass: persistent CTAs with next-row L2 prefetch
+    int tune_strided_nb = 1;                   // float32 strided powers: one neighbour exchange per sweep
+                                               // where that is exact to rounding
     double tune_ms = 0.0;                      // step time of the chosen configuration
     // 2D Dirichlet grids (n <= 1024 per axis) whose lines the register
     // kernels cannot split into whole segments run on the batched kernels
@@ -252,7 +255,9 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
             for (int w : {h->tune_rows_warps, 4, 2, 8})
                 if (w > 0 && regs_rows_plan(h->tbytes, n, pr.ng, w, &rpt)) { W = w; break; }
             if (W == 0) return fail(h, MOL_EINVAL, "no register plan for the transposed x pass");
-            e = launch_rows(h->bc, rpt, pr.ng, W, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
+            LineSet L = lineset_of(h, 0);
+            L.persist_sms = h->tune_rows_persist ? h->num_sms : 0;
+            e = launch_rows(h->bc, rpt, pr.ng, W, regs_axis(h, 0, rpt), L, pr, s);
         } else {
             if (!regs_strided_plan(h->tbytes, h->bc, n, &rpt, &S, &K, h->tune_strided_rpt, h->tune_strided_warps))
                 return fail(h, MOL_EINVAL, "no register plan for the transposed y pass");
@@ -263,7 +268,9 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
         }
     } else if (axis == 0 && pr.mode == 1 && pr.nout == 1 && h->tune_rows_warps > 0 &&
         regs_rows_plan(h->tbytes, n, pr.ng, h->tune_rows_warps, &rpt)) {
-        e = launch_rows(h->bc, rpt, pr.ng, h->tune_rows_warps, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
+        LineSet L = lineset_of(h, 0);
+        L.persist_sms = h->tune_rows_persist ? h->num_sms : 0;
+        e = launch_rows(h->bc, rpt, pr.ng, h->tune_rows_warps, regs_axis(h, 0, rpt), L, pr, s);
     } else if (axis == 0 && pr.mode == 1 && pr.nout == 1 && regs_res_plan(h->tbytes, n, pr.ng, &rpt)) {
         e = launch_res(h->bc, rpt, pr.ng, h->tune_res_warps, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
     } else if (axis == 0 && regs_contig_plan(h->tbytes, h->bc, n, &rpt)) {
@@ -273,7 +280,11 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
         LineSet L = lineset_of(h, axis);
         L.S = S;
         L.K = K;
-        e = launch_strided(h->tbytes, h->bc, rpt, regs_axis(h, axis, rpt), L, pr, s);
+        const AxisDev A = regs_axis(h, axis, rpt);
+        if (h->tbytes == 4 && pr.mode == 0 && h->tune_strided_nb && regs_strided_nb_plan(A.d, n, rpt))
+            e = launch_strided_nb(h->bc, rpt, A, L, pr, s);
+        else
+            e = launch_strided(h->tbytes, h->bc, rpt, A, L, pr, s);
     } else {
         PassGeom G = geom_of(h, axis);
         G.W = choose_W(h, axis, hp != nullptr);
@@ -926,16 +937,33 @@ mol_status mol_autotune(mol_handle h, void *stream)
     bool strided = false;
     for (int a = 1; a < h->ndim; ++a) strided |= regs_strided_plan(h->tbytes, h->bc, (int)h->n[a], &r0, &S0, &K0);
     // x variants: one warp per row with 1, 2 or 4 warps per CTA (code 1, 2, 4),
-    // or each row split over 2 or 4 warps (code -2, -4)
+    // or each row split over 2, 4 or 8 warps, one CTA per row (code -2, -4,
+    // -8) or persistent CTAs (code -102, -104, -108)
     std::vector<int> warps_c = res ? std::vector<int>{1, 2, 4} : std::vector<int>{h->tune_res_warps};
     if (h->ndim >= 2) {
         for (int W : {2, 4, 8})
-            if (regs_rows_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, W, &dummy)) warps_c.push_back(-W);
+            if (regs_rows_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, W, &dummy)) {
+                warps_c.push_back(-W);
+                warps_c.push_back(-100 - W);
+            }
     }
-    std::vector<std::pair<int, int>> str_c = {{h->tune_strided_rpt, h->tune_strided_warps}};
+    // strided variants: segment length code, segments per CTA at most, and
+    // (float32) the neighbour-exchange kernel where it applies (code + 100)
+    std::vector<std::pair<int, int>> str_c = {{h->tune_strided_rpt + 100 * h->tune_strided_nb, h->tune_strided_warps}};
     if (strided) {
-        str_c = {{0, 8}, {0, 4}};
-        if (h->tbytes == 4) { str_c.push_back({32, 8}); str_c.push_back({32, 4}); }
+        std::vector<std::pair<int, int>> base = {{0, 8}, {0, 4}};
+        if (h->tbytes == 4) { base.push_back({32, 8}); base.push_back({32, 4}); }
+        str_c.clear();
+        for (auto &b : base) {
+            bool nb = false;
+            for (int a = 1; a < h->ndim && h->tbytes == 4; ++a) {
+                int rr = 0, SS = 0, KK = 0;
+                if (regs_strided_plan(h->tbytes, h->bc, (int)h->n[a], &rr, &SS, &KK, b.first, b.second))
+                    nb |= regs_strided_nb_plan(h->ax[a].d, (int)h->n[a], rr);
+            }
+            if (nb) str_c.push_back({b.first + 100, b.second});
+            str_c.push_back(b);
+        }
     }
     for (int k = 0; k < 3; ++k) {
         const size_t bytes = (size_t)h->tbytes * h->N;
@@ -950,17 +978,20 @@ mol_status mol_autotune(mol_handle h, void *stream)
     const int64_t launches0 = h->launches;
     double best = 1e30;
     int bw = h->tune_res_warps, br = h->tune_strided_rpt, bsw = h->tune_strided_warps, brw = h->tune_rows_warps;
+    int bpe = h->tune_rows_persist, bnb = h->tune_strided_nb;
     mol_status st = MOL_OK;
     for (int w : warps_c) {
         for (auto &sc : str_c) {
             int rr = 0, SS = 0, KK = 0;
             bool ok = true;
             for (int a = 1; a < h->ndim && strided; ++a)
-                ok &= regs_strided_plan(h->tbytes, h->bc, (int)h->n[a], &rr, &SS, &KK, sc.first, sc.second);
+                ok &= regs_strided_plan(h->tbytes, h->bc, (int)h->n[a], &rr, &SS, &KK, sc.first % 100, sc.second);
             if (!ok) continue;
             h->tune_res_warps = w > 0 ? w : h->tune_res_warps;
-            h->tune_rows_warps = w < 0 ? -w : 0;
-            h->tune_strided_rpt = sc.first;
+            h->tune_rows_warps = w < 0 ? (-w) % 100 : 0;
+            h->tune_rows_persist = w < -100 ? 1 : 0;
+            h->tune_strided_rpt = sc.first % 100;
+            h->tune_strided_nb = sc.first >= 100 ? 1 : 0;
             h->tune_strided_warps = sc.second;
             // 2 warm-up steps, then the minimum of 3 timings of 3 steps
             double t = 1e30;
@@ -980,7 +1011,15 @@ mol_status mol_autotune(mol_handle h, void *stream)
                 }
             }
             if (st != MOL_OK) break;
-            if (t < best) { best = t; bw = h->tune_res_warps; brw = h->tune_rows_warps; br = sc.first; bsw = sc.second; }
+            if (t < best) {
+                best = t;
+                bw = h->tune_res_warps;
+                brw = h->tune_rows_warps;
+                bpe = h->tune_rows_persist;
+                bnb = h->tune_strided_nb;
+                br = sc.first % 100;
+                bsw = sc.second;
+            }
         }
         if (st != MOL_OK) break;
     }
@@ -990,6 +1029,8 @@ mol_status mol_autotune(mol_handle h, void *stream)
     h->launches = launches0;
     h->tune_res_warps = bw;
     h->tune_rows_warps = brw;
+    h->tune_rows_persist = bpe;
+    h->tune_strided_nb = bnb;
     h->tune_strided_rpt = br;
     h->tune_strided_warps = bsw;
     h->tune_ms = best < 1e30 ? best : 0.0;
@@ -1028,6 +1069,35 @@ mol_status mol_get_tuning(mol_handle h, int out[4], double *ms_per_step)
     out[1] = h->tune_strided_rpt;
     out[2] = h->tune_strided_warps;
     out[3] = h->tune_rows_warps;
+    if (ms_per_step) *ms_per_step = h->tune_ms;
+    return MOL_OK;
+}
+
+mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count)
+{
+    if (!h || !vals) return fail(h, MOL_EINVAL, "NULL argument");
+    if (count < 4 || count > MOL_TUNE_COUNT)
+        return fail(h, MOL_EINVAL, "count must be in 4.." + std::to_string(MOL_TUNE_COUNT));
+    if (count > MOL_TUNE_ROWS_PERSIST && vals[MOL_TUNE_ROWS_PERSIST] != 0 && vals[MOL_TUNE_ROWS_PERSIST] != 1)
+        return fail(h, MOL_EINVAL, "rows_persist must be 0 or 1");
+    if (count > MOL_TUNE_STRIDED_NB && vals[MOL_TUNE_STRIDED_NB] != 0 && vals[MOL_TUNE_STRIDED_NB] != 1)
+        return fail(h, MOL_EINVAL, "strided_nb must be 0 or 1");
+    mol_status st = mol_set_tuning(h, vals[MOL_TUNE_RES_WARPS], vals[MOL_TUNE_STRIDED_RPT],
+                                   vals[MOL_TUNE_STRIDED_WARPS], vals[MOL_TUNE_ROWS_WARPS]);
+    if (st != MOL_OK) return st;
+    if (count > MOL_TUNE_ROWS_PERSIST) h->tune_rows_persist = vals[MOL_TUNE_ROWS_PERSIST];
+    if (count > MOL_TUNE_STRIDED_NB) h->tune_strided_nb = vals[MOL_TUNE_STRIDED_NB];
+    return MOL_OK;
+}
+
+mol_status mol_get_tuning_ex(mol_handle h, int *vals, int count, double *ms_per_step)
+{
+    if (!h || !vals) return fail(h, MOL_EINVAL, "NULL argument");
+    if (count < 1 || count > MOL_TUNE_COUNT)
+        return fail(h, MOL_EINVAL, "count must be in 1.." + std::to_string(MOL_TUNE_COUNT));
+    const int all[MOL_TUNE_COUNT] = {h->tune_res_warps, h->tune_strided_rpt, h->tune_strided_warps,
+                                     h->tune_rows_warps, h->tune_rows_persist, h->tune_strided_nb};
+    for (int i = 0; i < count; ++i) vals[i] = all[i];
     if (ms_per_step) *ms_per_step = h->tune_ms;
     return MOL_OK;
 }

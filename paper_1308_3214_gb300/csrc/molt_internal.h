@@ -52,6 +52,11 @@ cudaError_t launch_contig(int tbytes, int bc, int rpt, const AxisDev &A, const L
 cudaError_t launch_strided(int tbytes, int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
                            cudaStream_t s);
 cudaError_t configure_regs_kernels();
+// The strided powers pass with one neighbour exchange per sweep (float32):
+// true when a line of n points with segments of rpt points and decay d is
+// computed by it exactly to well below float32 rounding (molt_strided_nb.cuh).
+bool regs_strided_nb_plan(double d, int n, int rpt);
+cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s);
 bool regs_res_plan(int tbytes, int n, int ng, int *rpt);
 bool regs_rows_plan(int tbytes, int n, int ng, int W, int *rpt);
 cudaError_t launch_rows(int bc, int rpt, int ng, int W, const AxisDev &A, const LineSet &L, const ProgParams &p,

@@ -173,6 +173,7 @@ struct LineSet {
     int64_t inner;    // product of the extents before the axis
     int64_t nlines;
     int S, K;         // strided: segments per CTA (warps) and CTAs per line
+    int persist_sms;  // row-split x pass: > 0 runs persistent CTAs on this many SMs
 };
 
 // ---------------------------------------------------------------------------

@@ -1,6 +1,8 @@
 // molt_regs.cu -- instantiation and launch of the register-resident pass kernels.
+#include <algorithm>
 #include "molt_internal.h"
 #include "molt_regs.cuh"
+#include "molt_strided_nb.cuh"
 
 namespace molt {
 
@@ -30,16 +32,38 @@ cudaError_t attr_res()
 template <int RPT, int NB, int W>
 size_t rows_smem() { return row_slots_bytes<float, W>() + (size_t)NB * 32 * W * ContigStage<float, RPT>::SST * sizeof(float); }
 
+// Grid of the row-split pass: one CTA per row, or as many persistent CTAs as
+// fit on L.persist_sms SMs (occupancy of the kernel, looked up once).
+template <class K>
+unsigned rows_grid(K kernel, int W, size_t smem, const LineSet &L, int &occ_cache)
+{
+    if (L.persist_sms <= 0) return (unsigned)L.nlines;
+    if (occ_cache <= 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 32 * W, smem) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        occ_cache = occ;
+    }
+    return (unsigned)std::min<int64_t>(L.nlines, (int64_t)occ_cache * L.persist_sms);
+}
+
 template <int BC, int RPT, int NB, int W>
 cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
 {
+    const size_t smem = rows_smem<RPT, NB, W>();
     if constexpr (BC == BC_DIRICHLET) {
         if (p.mode == 3) {                            // the transposed Horner pass
-            k_contig_rows<BC, RPT, NB, W, true><<<(unsigned)L.nlines, 32 * W, rows_smem<RPT, NB, W>(), s>>>(A, L, p);
+            static int occ_adj = 0;
+            const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W, true>, W, smem, L, occ_adj);
+            k_contig_rows<BC, RPT, NB, W, true><<<g, 32 * W, smem, s>>>(A, L, p);
             return cudaGetLastError();
         }
     }
-    k_contig_rows<BC, RPT, NB, W><<<(unsigned)L.nlines, 32 * W, rows_smem<RPT, NB, W>(), s>>>(A, L, p);
+    static int occ = 0;
+    const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W>, W, smem, L, occ);
+    k_contig_rows<BC, RPT, NB, W><<<g, 32 * W, smem, s>>>(A, L, p);
     return cudaGetLastError();
 }
 
@@ -98,6 +122,24 @@ cudaError_t run_strided(const AxisDev &A, const LineSet &L, const ProgParams &p,
     return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, 0>, A, L, p);
 }
 
+template <int BC, int RPT>
+cudaError_t run_strided_nb(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1);
+    cfg.blockDim = dim3(32 * L.S, 1, 1);
+    cfg.dynamicSmemBytes = strided_nb_smem(L.S);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = (unsigned)L.K;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = L.K > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_strided_nb<BC, RPT>, A, L, p, strided_nb_consts(A.d, RPT));
+}
+
 template <class T, int BC, int RPT>
 cudaError_t attr_contig()
 {
@@ -151,6 +193,21 @@ bool regs_strided_plan(int tbytes, int, int n, int *rpt, int *S, int *K, int pre
     *S = (G + k - 1) / k;
     *K = k;
     return true;
+}
+
+bool regs_strided_nb_plan(double d, int n, int rpt)
+{
+    return (rpt == kStridedRptF || rpt == kStridedRptF2) && strided_nb_exact(d, n, rpt);
+}
+
+cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+{
+    if (p.mode != 0 || !regs_strided_nb_plan(A.d, A.n, rpt)) return cudaErrorInvalidValue;
+    if (rpt == kStridedRptF)
+        return bc == BC_PERIODIC ? run_strided_nb<BC_PERIODIC, kStridedRptF>(A, L, p, s)
+                                 : run_strided_nb<BC_DIRICHLET, kStridedRptF>(A, L, p, s);
+    return bc == BC_PERIODIC ? run_strided_nb<BC_PERIODIC, kStridedRptF2>(A, L, p, s)
+                             : run_strided_nb<BC_DIRICHLET, kStridedRptF2>(A, L, p, s);
 }
 
 size_t regs_strided_smem(int tbytes, int S, int rpt, bool horner)

@@ -1186,10 +1186,13 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_conti
     T *B = reinterpret_cast<T *>(smem_raw + row_slots_bytes<T, W>());
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int n = A.n;                                // == NT * RPT
-    const int64_t row = blockIdx.x;
-    if (row >= LS.nlines) return;
-    const int64_t base = row * (int64_t)n;
     const int ng = pr.ng;
+    // one row per CTA, or (gridDim.x < rows) persistent CTAs that walk the
+    // rows with a stride of the grid and stream the next row into L2 while
+    // they work on this one, so that DRAM stays busy through the sweeps
+    for (int64_t row = blockIdx.x; row < LS.nlines; row += gridDim.x) {
+    if (row != (int64_t)blockIdx.x) __syncthreads();  // the previous row is done with the buffers and slots
+    const int64_t base = row * (int64_t)n;
     if (t == 0) {
         const unsigned bytes = (unsigned)n * 4u;
         prefetch_l2((const float *)pr.u_hi + base, bytes);
@@ -1197,6 +1200,17 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_conti
         if (pr.feb != 0.f) {
             prefetch_l2((const float *)pr.up_hi + base, bytes);
             prefetch_l2((const float *)pr.up_lo + base, bytes);
+        }
+        const int64_t nx = row + gridDim.x;
+        if (nx < LS.nlines) {
+            const int64_t nb = nx * (int64_t)n;
+            prefetch_l2((const float *)pr.u_hi + nb, bytes);
+            prefetch_l2((const float *)pr.u_lo + nb, bytes);
+            for (int k = 0; k < ng; ++k) prefetch_l2(reinterpret_cast<const float *>(pr.g[k]) + nb, bytes);
+            if (pr.feb != 0.f) {
+                prefetch_l2((const float *)pr.up_hi + nb, bytes);
+                prefetch_l2((const float *)pr.up_lo + nb, bytes);
+            }
         }
     }
     auto copy_field = [&](int k) {
@@ -1328,6 +1342,7 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_conti
             NL[v] = nl;
         }
     }
+    }   // rows
 }
 
 // ---------------------------------------------------------------------------

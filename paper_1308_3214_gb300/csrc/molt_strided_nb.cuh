@@ -1,0 +1,217 @@
+// molt_strided_nb.cuh -- strided-axis powers D^p u (float32 sweeps) with one
+// exchange per sweep between neighbouring segments (sm_103a).
+//
+// Layout as k_strided: lane = one of 32 neighbouring lines (every global
+// access coalesced), warp = a segment of RPT consecutive points of those
+// lines, the segments of a line over the warps of a CTA and the CTAs of a
+// thread-block cluster.
+//
+// The operator (Sec. 2, the two recurrences of L^{-1} in the difference form
+// of D): e = anti-causal(causal(q)) plus the boundary terms A d^j + B d^{n-1-j}.
+// The causal and anti-causal recurrences decay by d = e^{-nu} per point, so a
+// value RPT points away enters a segment's results multiplied by d^RPT.  When
+// d^{RPT-1} <= 2^-30 (far below float32 rounding) every inflow a segment needs
+// comes from its two neighbours alone:
+//   * each segment runs both halves of its causal recurrence with zero inflow
+//     and publishes four numbers: E = y0 at its last point, y0 at the one
+//     before, and the zero-inflow anti-causal sums ER0 = sum_k d^k y0_k,
+//     ER1 = sum_{k>=1} d^(k-1) y0_k;
+//   * after ONE barrier it reads E, y0 of its left neighbour (its causal
+//     inflow) and ER0, ER1 of its right neighbour, which with its own E give
+//     the right neighbour's first two values e_{a+RPT}, e_{a+RPT+1} exactly to
+//     the truncation (the right inflow is linear in E: ER = ER0 + G E);
+//   * it corrects its causal values for the inflow (y_k += yin d^(k+1)), runs
+//     the anti-causal recurrence from e_{a+RPT}, and forms the halos of the
+//     next sweep (its left neighbour's last two e values follow from E, y0 and
+//     its own first e value) without a second exchange.
+// The Dirichlet coefficients reduce to A = -e_0 / (1 - mu^2) and
+// B = -y_{n-1} / (1 - mu^2) (mu = d^{n-1} <= d^{2 RPT - 1} is negligible), so
+// only the two end segments apply them; periodic images reduce to the wrapped
+// neighbour.  The full-carry kernel (k_strided, three exchanges per sweep)
+// serves every other decay.
+#pragma once
+#include "molt_regs.cuh"
+
+namespace molt {
+
+// Constants of the neighbour exchange, float32 copies of float64 values:
+// G = d sum_{j<RPT} d^2j, G1 = d^2 sum_{j<RPT-1} d^2j, GH = d sum_{j<H} d^2j,
+// dH = d^H, dH1 = d^(H-1) with H = RPT/2.
+struct NbConsts {
+    float G, G1, GH, dH, dH1;
+};
+
+// True when the neighbour exchange is exact to well below float32 rounding
+// for a line of n points with segments of rpt points and decay d.
+inline bool strided_nb_exact(double d, int n, int rpt)
+{
+    if (rpt < 4 || n % rpt != 0 || n / rpt < 2) return false;
+    return std::pow(d, (double)(rpt - 1)) <= std::ldexp(1.0, -30);
+}
+
+inline NbConsts strided_nb_consts(double d, int rpt)
+{
+    const int H = rpt / 2;
+    double g = 0.0, g1 = 0.0, gh = 0.0, p = 1.0;
+    for (int j = 0; j < rpt; ++j) {
+        if (j < rpt - 1) g1 += p;
+        if (j < H) gh += p;
+        g += p;
+        p *= d * d;
+    }
+    NbConsts c;
+    c.G = (float)(d * g);
+    c.G1 = (float)(d * d * g1);
+    c.GH = (float)(d * gh);
+    c.dH = (float)std::pow(d, (double)H);
+    c.dH1 = (float)std::pow(d, (double)(H - 1));
+    return c;
+}
+
+__host__ __device__ inline size_t strided_nb_smem(int S) { return (size_t)2 * S * 4 * 32 * sizeof(float); }
+
+// KM: 0 = powers D^p u, p = 1..P, into pr.out[p-1] (r = second difference of
+// the pair level u formed here).  Launch: grid (column groups, K), clusters
+// of K CTAs along y, S warps per CTA, strided_nb_smem(S) bytes.
+template <int BC, int RPT>
+__global__ void __launch_bounds__(256, 2) k_strided_nb(AxisDev A, LineSet LS, ProgParams pr, NbConsts nc)
+{
+    static_assert(RPT % 2 == 0 && RPT >= 8, "segment length");
+    constexpr int H = RPT / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *slots = reinterpret_cast<float *>(smem_raw);          // [2][S][4][32]
+    cg::cluster_group cl = cg::this_cluster();
+    const int S = LS.S, K = LS.K;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int krank = K > 1 ? (int)cl.block_rank() : 0;
+    const int n = A.n, Gd = n / RPT;
+    const int seg = krank * S + w, a = seg * RPT;
+    const bool full = seg < Gd;
+    const float d = A.fd, c1 = A.fc1, c2 = A.fc2, inv = A.finv;
+
+    const int64_t line = (int64_t)blockIdx.x * 32 + lane;
+    const bool valid = line < LS.nlines;
+    const bool io = valid && full;
+    const int64_t lbase = valid ? (line % LS.inner) + (line / LS.inner) * LS.inner * (int64_t)n : 0;
+    const int64_t st = LS.stride;
+
+    // neighbouring segments: periodic lines wrap, Dirichlet ends have none
+    int sl = seg - 1, sr = seg + 1;
+    if (BC == BC_PERIODIC) {
+        if (sl < 0) sl = Gd - 1;
+        if (sr >= Gd) sr = 0;
+    }
+    const bool hasL = full && sl >= 0, hasR = full && sr < Gd;
+    const bool left_end = BC == BC_DIRICHLET && seg == 0, right_end = BC == BC_DIRICHLET && seg == Gd - 1;
+    auto slot = [&](int buf, int sg) -> const float * {
+        const float *p = slots + ((size_t)buf * S + sg % S) * 128;
+        return K > 1 ? cl.map_shared_rank(p, sg / S) : p;
+    };
+
+    // r = accurate second difference of u along the line (Dirichlet end
+    // nodes take the neighbouring interior centre)
+    float z[RPT];
+    float rl = 0.f, rr = 0.f;
+    if (io) strided_r_pair<BC, RPT>(pr, lbase, st, a, n, z, rl, rr);
+    else {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0.f;
+    }
+    if (BC == BC_DIRICHLET) {
+        if (left_end) z[0] = z[1];
+        if (right_end) z[RPT - 1] = z[RPT - 2];
+    }
+    float hl2 = 0.f, hl1 = rl, hr0 = rr, hr1 = 0.f;   // sweep 1 (z = s): s at a-1 and a+RPT
+
+    for (int p = 1; p <= pr.P; ++p) {
+        float zl2 = hl2, zl1 = hl1, zr0 = hr0, zr1 = hr1;
+        if (p == 1) {
+            if (BC == BC_DIRICHLET) end_ghosts<float, RPT, 0>(z, left_end, right_end, zl2, zl1, zr0, zr1);
+            seg_make_q<float, RPT, 0>(z, zl2, zl1, zr0, zr1, [](int) { return 0.f; }, 0.f, c1, c2);
+        } else {
+            if (BC == BC_DIRICHLET) end_ghosts<float, RPT, 1>(z, left_end, right_end, zl2, zl1, zr0, zr1);
+            seg_make_q<float, RPT, 1>(z, zl2, zl1, zr0, zr1, [](int) { return 0.f; }, 0.f, c1, c2);
+        }
+        if (BC == BC_DIRICHLET) end_zero<float, RPT>(z, left_end, right_end);
+        if (!full) {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) z[k] = 0.f;
+        }
+
+        // both halves of the causal recurrence with zero inflow; ERb and the
+        // chain-A part of ER1 on the way
+        float ya = z[0], yb = z[H], ra1 = 0.f, rb = yb, pw = 1.f;
+#pragma unroll
+        for (int k = 1; k < H; ++k) {
+            ya = d * ya + z[k];
+            yb = d * yb + z[H + k];
+            z[k] = ya;
+            z[H + k] = yb;
+            const float pbk = pw * d;     // chain A weighs y_k by d^(k-1), chain B by d^k
+            ra1 += pw * ya;
+            rb += pbk * yb;
+            pw = pbk;
+        }
+        const float E1 = ya;                                // zero-inflow y at H-1
+        const float E = yb + E1 * nc.dH;                    // ... at RPT-1
+        const float Y2 = z[RPT - 2] + E1 * nc.dH1;          // ... at RPT-2
+        const float ER1 = ra1 + nc.dH1 * (rb + E1 * nc.GH);
+        const float ER0 = z[0] + d * ER1;
+
+        float *mine = slots + ((size_t)(p & 1) * S + w) * 128;
+        mine[lane] = E;
+        mine[32 + lane] = Y2;
+        mine[64 + lane] = ER0;
+        mine[96 + lane] = ER1;
+        if (K > 1) cl.sync();
+        else __syncthreads();
+        float EL = 0.f, Y2L = 0.f, ER0R = 0.f, ER1R = 0.f;
+        if (hasL) {
+            const float *q = slot(p & 1, sl);
+            EL = q[lane];
+            Y2L = q[32 + lane];
+        }
+        if (hasR) {
+            const float *q = slot(p & 1, sr);
+            ER0R = q[64 + lane];
+            ER1R = q[96 + lane];
+        }
+
+        // true causal values: chain A from the left neighbour's y at a-1,
+        // chain B from the corrected y at H-1
+        const float cB = E1 + EL * nc.dH;
+        float pk = d;
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            z[k] += EL * pk;
+            z[H + k] += cB * pk;
+            pk *= d;
+        }
+        const float ER2 = rb + cB * nc.GH;                  // sum_j d^j y_{H+j}
+        const float eout = hasR ? ER0R + nc.G * E : 0.f;    // e at a+RPT
+        const float er1 = hasR ? ER1R + nc.G1 * E : 0.f;    // e at a+RPT+1
+        float acc = d * eout;
+        if (right_end) acc -= z[RPT - 1] * inv;             // B' d^{n-1-j} through the inflow
+        seg_bwd_scan2<float, RPT>(z, d, nc.dH, acc, ER2);
+        if (left_end) seg_add_left2<float, RPT>(z, d, nc.dH, -z[0] * inv);
+
+        // halos of the next sweep: e at a-1, a-2 from the left neighbour's
+        // last causal values and this segment's first e; e at a+RPT, a+RPT+1
+        hl1 = hasL ? EL + d * z[0] : 0.f;
+        hl2 = hasL ? Y2L + d * hl1 : 0.f;
+        hr0 = eout;
+        hr1 = er1;
+
+        float *o = reinterpret_cast<float *>(pr.out[p - 1]);
+        if (o != nullptr && io) {
+            float *po = o + lbase + (int64_t)a * st;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) { *po = z[k]; po += st; }
+        }
+    }
+    // peers read this CTA's slots after the last exchange: no CTA of the
+    // cluster exits before every one of them is past those reads
+    if (K > 1) cl.sync();
+}
+
+}  // namespace molt

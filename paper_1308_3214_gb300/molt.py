@@ -33,6 +33,7 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_batch_offsets", "mol_batch_apply_F", "mol_batch_start", "mol_batch_step", "mol_batch_solve_host", "mol_batch_sync",
            "mol_batch_launch_count", "mol_batch_set_pass_timing", "mol_batch_pass_times", "mol_batch_apply_FT",
            "mol_batch_traces", "mol_batch_adjoint", "mol_batch_update", "mol_autotune", "mol_get_tuning", "mol_set_tuning",
+           "mol_get_tuning_ex", "mol_set_tuning_ex",
            "mol_batch_autotune", "mol_batch_get_tuning", "mol_batch_set_tuning", "mol_solve_dirichlet", "mol_solve_source", "mol_apply_FT", "mol_traces", "mol_adjoint",
            "mol_embed_create", "mol_embed_destroy", "mol_embed_last_error", "mol_embed_linv", "mol_embed_apply_F",
            "mol_embed_start", "mol_embed_step", "mol_embed_solve_host", "mol_embed_sync", "mol_embed_launch_count",
@@ -121,6 +122,8 @@ def load_library(path: Path | None = None):
     lib.mol_autotune.argtypes = [vp, vp]
     lib.mol_get_tuning.argtypes = [vp, ctypes.POINTER(I), dp]
     lib.mol_set_tuning.argtypes = [vp, I, I, I, I]
+    lib.mol_get_tuning_ex.argtypes = [vp, ctypes.POINTER(I), I, dp]
+    lib.mol_set_tuning_ex.argtypes = [vp, ctypes.POINTER(I), I]
     lib.mol_batch_autotune.argtypes = [vp, vp]
     lib.mol_apply_FT.argtypes = [vp, vp, vp, vp]
     lib.mol_traces.argtypes = [vp, vp, I, ctypes.POINTER(i64), i64, vp, vp]
@@ -355,16 +358,27 @@ class Solver:
         self._check(self.lib.mol_autotune(self.h, ctypes.c_void_p(_stream_ptr(stream))))
         return self.tuning()
 
-    def set_tuning(self, res_warps: int = 2, strided_rpt: int = 0, strided_warps: int = 8, rows_warps: int = 0):
-        self._check(self.lib.mol_set_tuning(self.h, int(res_warps), int(strided_rpt), int(strided_warps),
-                                            int(rows_warps)))
+    TUNING_KEYS = ("res_warps", "strided_rpt", "strided_warps", "rows_warps", "rows_persist", "strided_nb")
+
+    def set_tuning(self, res_warps: int = 2, strided_rpt: int = 0, strided_warps: int = 8, rows_warps: int = 0,
+                   rows_persist: int | None = None, strided_nb: int | None = None):
+        """Launch choices by hand (mol_set_tuning_ex); rows_persist and
+        strided_nb None keep the handle's settings."""
+        cur = self.tuning()
+        vals = [int(res_warps), int(strided_rpt), int(strided_warps), int(rows_warps),
+                int(cur["rows_persist"] if rows_persist is None else rows_persist),
+                int(cur["strided_nb"] if strided_nb is None else strided_nb)]
+        arr = (ctypes.c_int * len(vals))(*vals)
+        self._check(self.lib.mol_set_tuning_ex(self.h, arr, len(vals)))
 
     def tuning(self) -> dict:
-        out = (ctypes.c_int * 4)()
+        n = len(self.TUNING_KEYS)
+        out = (ctypes.c_int * n)()
         ms = ctypes.c_double()
-        self._check(self.lib.mol_get_tuning(self.h, out, ctypes.byref(ms)))
-        return {"res_warps": out[0], "strided_rpt": out[1], "strided_warps": out[2], "rows_warps": out[3],
-                "ms_per_step": ms.value}
+        self._check(self.lib.mol_get_tuning_ex(self.h, out, n, ctypes.byref(ms)))
+        d = {k: out[i] for i, k in enumerate(self.TUNING_KEYS)}
+        d["ms_per_step"] = ms.value
+        return d
 
     def sync(self, stream=None):
         self._check(self.lib.mol_sync(self.h, ctypes.c_void_p(_stream_ptr(stream))))

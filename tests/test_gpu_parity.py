@@ -449,3 +449,29 @@ def test_rows_split_over_warps_match_oracle(shape, W, bc, P):
         a, b = b, 2 * b - a + F
     tol = 8 * EPS32 * (1 + 1 / (1 - max(s.d))) * 2 * P * Fsum / np.linalg.norm(rc)
     assert rel_l2(uc.cpu().numpy(), rc) <= tol
+
+
+# ---------------------------------------------------------------------------
+# float32 strided powers with one neighbour exchange per sweep: used where
+# the decay over one segment, d^(RPT-1), is below 2^-30; the full-carry
+# kernel elsewhere.  Both choices against the oracle, over decays on either
+# side of that limit.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(2048, 96), (256, 64), (128, 160)])
+@pytest.mark.parametrize("cfl", [0.5, 2.0, 3.5, 8.0])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("rpt,warps", [(0, 4), (0, 8), (32, 8)])
+def test_strided_neighbour_exchange_matches_oracle(shape, cfl, bc, rpt, warps):
+    n = shape[0]
+    h = spacing(n, bc)
+    s = make(shape, cfl * h, 3, bc, "mixed")
+    v = field(shape, 70, bc)
+    vd = dev(v)
+    refs = [oracle.D_axis(v, 1, s.nu[1], bc, 2, power=p) for p in (1, 2, 3)]
+    for nb in (1, 0):
+        s.set_tuning(res_warps=2, strided_rpt=rpt, strided_warps=warps, rows_warps=0, strided_nb=nb)
+        assert s.tuning()["strided_nb"] == nb
+        for p, ref in zip((1, 2, 3), refs):
+            got = s.apply_D(vd, 1, p).cpu().numpy()
+            assert rel_l2(got, ref) <= tol_for("mixed", s, p), (nb, p, rel_l2(got, ref))
+    s.close()
