@@ -186,7 +186,14 @@ mol_status mol_get_tuning(mol_handle h, int out[4], double *ms_per_step);
  *   MOL_TUNE_STRIDED_NB: 1 (default) = the float32 strided powers pass
  *     exchanges once per sweep between neighbouring segments wherever the
  *     decay over one segment makes that exact to below 2^-30 (d^(RPT-1) <=
- *     2^-30); 0 = the full-carry pass (three exchanges per sweep) always.
+ *     2^-30); 0 = the full-carry pass (three exchanges per sweep) always;
+ *   MOL_TUNE_STRIDED_STAGE: how that pass moves its tiles: 0 direct
+ *     coalesced loads and stores from registers; 1 the pair level's tile (the
+ *     CTA's rows plus halos, 32 lines) copied into shared memory by TMA tensor
+ *     loads on an mbarrier; 2 (default) each output power staged in shared
+ *     memory and written by TMA tensor stores; 3 both.  Grids whose 32-line
+ *     groups would straddle an outer slice (inner extent not a multiple of 32)
+ *     take 0.
  * mol_set_tuning_ex takes count >= 4 values (indices past count keep their
  * setting); mol_get_tuning_ex fills count values.  MOL_EINVAL on a value out
  * of range, a count out of range or a choice that does not fit the grid. */
@@ -197,7 +204,8 @@ enum {
     MOL_TUNE_ROWS_WARPS = 3,
     MOL_TUNE_ROWS_PERSIST = 4,
     MOL_TUNE_STRIDED_NB = 5,
-    MOL_TUNE_COUNT = 6
+    MOL_TUNE_STRIDED_STAGE = 6,
+    MOL_TUNE_COUNT = 7
 };
 mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count);
 mol_status mol_get_tuning_ex(mol_handle h, int *vals, int count, double *ms_per_step);
@@ -246,6 +254,11 @@ mol_status mol_solve_dirichlet(mol_handle h, const double *u0, int64_t nsteps, c
 mol_status mol_solve_source(mol_handle h, const double *u0, int64_t nsteps, const double *g, const double *f,
                             double *u_out, void *stream);
 
+/* Synchronize the stream and report device-side failures: MOL_ECUDA for a
+ * CUDA error, MOL_ETIMEOUT when a bounded wait inside a kernel (the strided
+ * pass's tile-copy barrier, MOL_TUNE_STRIDED_STAGE 1 or 3) gave up since the
+ * last mol_sync -- the results computed since then are not valid.  The wait
+ * limit is about two seconds, far beyond any healthy copy. */
 mol_status mol_sync(mol_handle h, void *stream);
 
 /* Number of kernel launches this handle issued so far (all entry points). */

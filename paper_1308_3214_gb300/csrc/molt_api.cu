@@ -62,6 +62,7 @@ struct mol_ctx {
     int tune_rows_persist = 0;                 // row-split x pass: persistent CTAs with next-row L2 prefetch
     int tune_strided_nb = 1;                   // float32 strided powers: one neighbour exchange per sweep
                                                // where that is exact to rounding
+    int tune_strided_stage = 2;                // ... its tiles: 0 direct, 1 TMA loads, 2 TMA stores, 3 both
     double tune_ms = 0.0;                      // step time of the chosen configuration
     // 2D Dirichlet grids (n <= 1024 per axis) whose lines the register
     // kernels cannot split into whole segments run on the batched kernels
@@ -282,7 +283,7 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
         L.K = K;
         const AxisDev A = regs_axis(h, axis, rpt);
         if (h->tbytes == 4 && pr.mode == 0 && h->tune_strided_nb && regs_strided_nb_plan(A.d, n, rpt))
-            e = launch_strided_nb(h->bc, rpt, A, L, pr, s);
+            e = launch_strided_nb(h->bc, rpt, A, L, pr, s, h->tune_strided_stage);
         else
             e = launch_strided(h->tbytes, h->bc, rpt, A, L, pr, s);
     } else {
@@ -949,7 +950,8 @@ mol_status mol_autotune(mol_handle h, void *stream)
     }
     // strided variants: segment length code, segments per CTA at most, and
     // (float32) the neighbour-exchange kernel where it applies (code + 100)
-    std::vector<std::pair<int, int>> str_c = {{h->tune_strided_rpt + 100 * h->tune_strided_nb, h->tune_strided_warps}};
+    std::vector<std::pair<int, int>> str_c = {
+        {h->tune_strided_rpt + 100 * h->tune_strided_nb + 1000 * h->tune_strided_stage, h->tune_strided_warps}};
     if (strided) {
         std::vector<std::pair<int, int>> base = {{0, 8}, {0, 4}};
         if (h->tbytes == 4) { base.push_back({32, 8}); base.push_back({32, 4}); }
@@ -961,7 +963,8 @@ mol_status mol_autotune(mol_handle h, void *stream)
                 if (regs_strided_plan(h->tbytes, h->bc, (int)h->n[a], &rr, &SS, &KK, b.first, b.second))
                     nb |= regs_strided_nb_plan(h->ax[a].d, (int)h->n[a], rr);
             }
-            if (nb) str_c.push_back({b.first + 100, b.second});
+            if (nb)
+                for (int stg = 0; stg < 4; ++stg) str_c.push_back({b.first + 100 + 1000 * stg, b.second});
             str_c.push_back(b);
         }
     }
@@ -978,7 +981,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
     const int64_t launches0 = h->launches;
     double best = 1e30;
     int bw = h->tune_res_warps, br = h->tune_strided_rpt, bsw = h->tune_strided_warps, brw = h->tune_rows_warps;
-    int bpe = h->tune_rows_persist, bnb = h->tune_strided_nb;
+    int bpe = h->tune_rows_persist, bnb = h->tune_strided_nb, bst = h->tune_strided_stage;
     mol_status st = MOL_OK;
     for (int w : warps_c) {
         for (auto &sc : str_c) {
@@ -991,7 +994,8 @@ mol_status mol_autotune(mol_handle h, void *stream)
             h->tune_rows_warps = w < 0 ? (-w) % 100 : 0;
             h->tune_rows_persist = w < -100 ? 1 : 0;
             h->tune_strided_rpt = sc.first % 100;
-            h->tune_strided_nb = sc.first >= 100 ? 1 : 0;
+            h->tune_strided_nb = (sc.first / 100) % 10;
+            h->tune_strided_stage = sc.first / 1000;
             h->tune_strided_warps = sc.second;
             // 2 warm-up steps, then the minimum of 3 timings of 3 steps
             double t = 1e30;
@@ -1017,6 +1021,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
                 brw = h->tune_rows_warps;
                 bpe = h->tune_rows_persist;
                 bnb = h->tune_strided_nb;
+                bst = h->tune_strided_stage;
                 br = sc.first % 100;
                 bsw = sc.second;
             }
@@ -1031,6 +1036,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
     h->tune_rows_warps = brw;
     h->tune_rows_persist = bpe;
     h->tune_strided_nb = bnb;
+    h->tune_strided_stage = bst;
     h->tune_strided_rpt = br;
     h->tune_strided_warps = bsw;
     h->tune_ms = best < 1e30 ? best : 0.0;
@@ -1082,11 +1088,15 @@ mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count)
         return fail(h, MOL_EINVAL, "rows_persist must be 0 or 1");
     if (count > MOL_TUNE_STRIDED_NB && vals[MOL_TUNE_STRIDED_NB] != 0 && vals[MOL_TUNE_STRIDED_NB] != 1)
         return fail(h, MOL_EINVAL, "strided_nb must be 0 or 1");
+    if (count > MOL_TUNE_STRIDED_STAGE && (vals[MOL_TUNE_STRIDED_STAGE] < 0 || vals[MOL_TUNE_STRIDED_STAGE] > 3))
+        return fail(h, MOL_EINVAL, "strided_stage must be 0, 1, 2 or 3");
     mol_status st = mol_set_tuning(h, vals[MOL_TUNE_RES_WARPS], vals[MOL_TUNE_STRIDED_RPT],
                                    vals[MOL_TUNE_STRIDED_WARPS], vals[MOL_TUNE_ROWS_WARPS]);
     if (st != MOL_OK) return st;
     if (count > MOL_TUNE_ROWS_PERSIST) h->tune_rows_persist = vals[MOL_TUNE_ROWS_PERSIST];
     if (count > MOL_TUNE_STRIDED_NB) h->tune_strided_nb = vals[MOL_TUNE_STRIDED_NB];
+    if (count > MOL_TUNE_STRIDED_STAGE) h->tune_strided_stage = vals[MOL_TUNE_STRIDED_STAGE];
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     return MOL_OK;
 }
 
@@ -1096,7 +1106,8 @@ mol_status mol_get_tuning_ex(mol_handle h, int *vals, int count, double *ms_per_
     if (count < 1 || count > MOL_TUNE_COUNT)
         return fail(h, MOL_EINVAL, "count must be in 1.." + std::to_string(MOL_TUNE_COUNT));
     const int all[MOL_TUNE_COUNT] = {h->tune_res_warps, h->tune_strided_rpt, h->tune_strided_warps,
-                                     h->tune_rows_warps, h->tune_rows_persist, h->tune_strided_nb};
+                                     h->tune_rows_warps, h->tune_rows_persist, h->tune_strided_nb,
+                                     h->tune_strided_stage};
     for (int i = 0; i < count; ++i) vals[i] = all[i];
     if (ms_per_step) *ms_per_step = h->tune_ms;
     return MOL_OK;
@@ -1375,6 +1386,11 @@ mol_status mol_sync(mol_handle h, void *stream)
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
     CK(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
     CK(cudaGetLastError(), "device error");
+    const int to = regs_timeout_take((cudaStream_t)stream);
+    if (to < 0) return fail(h, MOL_ECUDA, "reading the device wait flag failed");
+    if (to > 0)
+        return fail(h, MOL_ETIMEOUT, "a bounded device wait (tile copy barrier) gave up; the results since the last "
+                                     "mol_sync are not valid");
     return MOL_OK;
 }
 

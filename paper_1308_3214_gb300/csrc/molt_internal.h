@@ -56,7 +56,14 @@ cudaError_t configure_regs_kernels();
 // true when a line of n points with segments of rpt points and decay d is
 // computed by it exactly to well below float32 rounding (molt_strided_nb.cuh).
 bool regs_strided_nb_plan(double d, int n, int rpt);
-cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s);
+// stage: 0 direct loads and stores, 1 the pair level's tile through TMA into
+// shared memory, 2 each output power staged in shared memory and written by
+// TMA tensor stores, 3 both
+cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s,
+                              int stage = 0);
+// 1 if a bounded wait of a register kernel gave up since the last call (and
+// clears it), 0 if not, -1 if the flag could not be read; synchronizes s.
+int regs_timeout_take(cudaStream_t s);
 bool regs_res_plan(int tbytes, int n, int ng, int *rpt);
 bool regs_rows_plan(int tbytes, int n, int ng, int W, int *rpt);
 cudaError_t launch_rows(int bc, int rpt, int ng, int W, const AxisDev &A, const LineSet &L, const ProgParams &p,

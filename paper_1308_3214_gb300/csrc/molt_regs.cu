@@ -122,13 +122,87 @@ cudaError_t run_strided(const AxisDev &A, const LineSet &L, const ProgParams &p,
     return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, 0>, A, L, p);
 }
 
-template <int BC, int RPT>
-cudaError_t run_strided_nb(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+// cuTensorMapEncodeTiled from the driver (through the runtime, so that the
+// library links no driver stub)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn()
 {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3D view {inner, n, outer} of a float32 field (the strided axis is the
+// middle one), boxes of {32, box_rows, 1}; zeros outside the field.
+bool encode_field_map(CUtensorMap *m, const void *ptr, const LineSet &L, int n, int box_rows)
+{
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn || ptr == nullptr || ((uintptr_t)ptr & 15) != 0 || L.inner % 32 != 0 || box_rows < 1 || box_rows > 256)
+        return false;
+    const cuuint64_t inner = (cuuint64_t)L.inner, outer = (cuuint64_t)(L.nlines / L.inner);
+    const cuuint64_t dims[3] = {inner, (cuuint64_t)n, outer};
+    const cuuint64_t strides[2] = {inner * 4, inner * (cuuint64_t)n * 4};
+    const cuuint32_t box[3] = {32, (cuuint32_t)box_rows, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(ptr), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BC, int RPT, int STAGE>
+cudaError_t launch_nb_stage(const cudaLaunchConfig_t &cfg, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                            const TmaMaps &tm)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_strided_nb<BC, RPT, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return cudaLaunchKernelEx(&cfg, k_strided_nb<BC, RPT, STAGE>, A, L, p, strided_nb_consts(A.d, RPT), tm);
+}
+
+template <int BC, int RPT>
+cudaError_t run_strided_nb(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s, int stage)
+{
+    TmaMaps tm{};
+    if (stage != 0) {
+        // tensor maps of this launch's fields; any that cannot be made (a
+        // grid whose line groups straddle an outer slice, an unaligned
+        // pointer, no driver entry point) fall back to direct loads / stores
+        const int in_rows = L.S * RPT + 4;
+        tm.nbox = (in_rows + 255) / 256;
+        tm.box_rows = (in_rows + tm.nbox - 1) / tm.nbox;
+        const int out_box = L.S * RPT > 256 ? 256 : L.S * RPT;
+        bool ok = true;
+        if (stage & 1)
+            ok = encode_field_map(&tm.in_hi, p.u_hi, L, A.n, tm.box_rows) &&
+                 encode_field_map(&tm.in_lo, p.u_lo, L, A.n, tm.box_rows);
+        if ((stage & 2) && ok) {
+            if (p.P > kMaxTmaOut) ok = false;
+            for (int k = 0; k < p.P && ok; ++k)
+                if (p.out[k] != nullptr) ok = encode_field_map(&tm.out[k], p.out[k], L, A.n, out_box);
+        }
+        if (!ok) stage = 0;
+    }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1);
     cfg.blockDim = dim3(32 * L.S, 1, 1);
-    cfg.dynamicSmemBytes = strided_nb_smem(L.S);
+    cfg.dynamicSmemBytes = strided_nb_smem(L.S, RPT, stage, tm.nbox, tm.box_rows);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -137,7 +211,12 @@ cudaError_t run_strided_nb(const AxisDev &A, const LineSet &L, const ProgParams 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = L.K > 1 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_strided_nb<BC, RPT>, A, L, p, strided_nb_consts(A.d, RPT));
+    switch (stage) {
+    case 1: return launch_nb_stage<BC, RPT, 1>(cfg, A, L, p, tm);
+    case 2: return launch_nb_stage<BC, RPT, 2>(cfg, A, L, p, tm);
+    case 3: return launch_nb_stage<BC, RPT, 3>(cfg, A, L, p, tm);
+    default: return launch_nb_stage<BC, RPT, 0>(cfg, A, L, p, tm);
+    }
 }
 
 template <class T, int BC, int RPT>
@@ -200,14 +279,27 @@ bool regs_strided_nb_plan(double d, int n, int rpt)
     return (rpt == kStridedRptF || rpt == kStridedRptF2) && strided_nb_exact(d, n, rpt);
 }
 
-cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s,
+                              int stage)
 {
-    if (p.mode != 0 || !regs_strided_nb_plan(A.d, A.n, rpt)) return cudaErrorInvalidValue;
+    if (p.mode != 0 || !regs_strided_nb_plan(A.d, A.n, rpt) || stage < 0 || stage > 3) return cudaErrorInvalidValue;
     if (rpt == kStridedRptF)
-        return bc == BC_PERIODIC ? run_strided_nb<BC_PERIODIC, kStridedRptF>(A, L, p, s)
-                                 : run_strided_nb<BC_DIRICHLET, kStridedRptF>(A, L, p, s);
-    return bc == BC_PERIODIC ? run_strided_nb<BC_PERIODIC, kStridedRptF2>(A, L, p, s)
-                             : run_strided_nb<BC_DIRICHLET, kStridedRptF2>(A, L, p, s);
+        return bc == BC_PERIODIC ? run_strided_nb<BC_PERIODIC, kStridedRptF>(A, L, p, s, stage)
+                                 : run_strided_nb<BC_DIRICHLET, kStridedRptF>(A, L, p, s, stage);
+    return bc == BC_PERIODIC ? run_strided_nb<BC_PERIODIC, kStridedRptF2>(A, L, p, s, stage)
+                             : run_strided_nb<BC_DIRICHLET, kStridedRptF2>(A, L, p, s, stage);
+}
+
+int regs_timeout_take(cudaStream_t s)
+{
+    int v = 0, zero = 0;
+    if (cudaMemcpyFromSymbolAsync(&v, g_molt_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return -1;
+    if (v != 0 && cudaMemcpyToSymbolAsync(g_molt_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return -1;
+    if (v != 0) cudaStreamSynchronize(s);
+    return v;
 }
 
 size_t regs_strided_smem(int tbytes, int S, int rpt, bool horner)

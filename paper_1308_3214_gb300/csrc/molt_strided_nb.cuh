@@ -31,6 +31,7 @@
 // serves every other decay.
 #pragma once
 #include "molt_regs.cuh"
+#include "molt_tma.cuh"
 
 namespace molt {
 
@@ -68,13 +69,26 @@ inline NbConsts strided_nb_consts(double d, int rpt)
     return c;
 }
 
-__host__ __device__ inline size_t strided_nb_smem(int S) { return (size_t)2 * S * 4 * 32 * sizeof(float); }
+// Shared memory of one CTA: the exchange slots [2][S][4][32], then (STAGE
+// != 0) the tile barrier and the tile: the pair level's rows a0-2 .. a0+S RPT+1
+// of the CTA's 32 lines (STAGE & 1; nbox boxes of box_rows rows for hi and for
+// lo), or only the output rows a0 .. a0+S RPT-1 (STAGE == 2).  STAGE & 2
+// stages each output power in the tile and writes it with one tensor store.
+__host__ __device__ inline size_t strided_nb_slot_bytes(int S) { return (size_t)2 * S * 4 * 32 * sizeof(float); }
+__host__ __device__ inline size_t strided_nb_tile_off(int S) { return (strided_nb_slot_bytes(S) + 8 + 127) & ~(size_t)127; }
+__host__ __device__ inline size_t strided_nb_smem(int S, int rpt = 0, int stage = 0, int nbox = 0, int box_rows = 0)
+{
+    if (stage == 0) return strided_nb_slot_bytes(S);
+    const size_t out_rows = (size_t)S * rpt, in_rows = (stage & 1) ? (size_t)2 * nbox * box_rows : 0;
+    return strided_nb_tile_off(S) + (in_rows > out_rows ? in_rows : out_rows) * 32 * sizeof(float);
+}
 
 // KM: 0 = powers D^p u, p = 1..P, into pr.out[p-1] (r = second difference of
 // the pair level u formed here).  Launch: grid (column groups, K), clusters
 // of K CTAs along y, S warps per CTA, strided_nb_smem(S) bytes.
-template <int BC, int RPT>
-__global__ void __launch_bounds__(256, 2) k_strided_nb(AxisDev A, LineSet LS, ProgParams pr, NbConsts nc)
+template <int BC, int RPT, int STAGE>
+__global__ void __launch_bounds__(256, 2) k_strided_nb(AxisDev A, LineSet LS, ProgParams pr, NbConsts nc,
+                                                      const __grid_constant__ TmaMaps tm)
 {
     static_assert(RPT % 2 == 0 && RPT >= 8, "segment length");
     constexpr int H = RPT / 2;
@@ -108,14 +122,71 @@ __global__ void __launch_bounds__(256, 2) k_strided_nb(AxisDev A, LineSet LS, Pr
         return K > 1 ? cl.map_shared_rank(p, sg / S) : p;
     };
 
+    // tile of the CTA's lines: 32 lines from column x0 of outer slice z0
+    const int64_t line0 = (int64_t)blockIdx.x * 32;
+    const int x0 = (int)(line0 % LS.inner), z0 = (int)(line0 / LS.inner);
+    const int a0 = krank * S * RPT;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + strided_nb_slot_bytes(S));
+    float *tile = reinterpret_cast<float *>(smem_raw + strided_nb_tile_off(S));
+    if constexpr (STAGE & 1) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, (uint32_t)(2 * tm.nbox * tm.box_rows * 32 * sizeof(float)));
+            for (int b = 0; b < tm.nbox; ++b) {
+                tma_load_3d(tile + (size_t)b * tm.box_rows * 32, &tm.in_hi, x0, a0 - 2 + b * tm.box_rows, z0, bar);
+                tma_load_3d(tile + (size_t)(tm.nbox + b) * tm.box_rows * 32, &tm.in_lo, x0, a0 - 2 + b * tm.box_rows,
+                            z0, bar);
+            }
+        }
+        __syncthreads();                                   // the barrier is initialised before anyone waits on it
+    }
+
     // r = accurate second difference of u along the line (Dirichlet end
     // nodes take the neighbouring interior centre)
     float z[RPT];
     float rl = 0.f, rr = 0.f;
-    if (io) strided_r_pair<BC, RPT>(pr, lbase, st, a, n, z, rl, rr);
-    else {
+    if constexpr (STAGE & 1) {
+        mbar_wait_or_flag(bar, 0);
+        // tile row of line point j: j - (a0 - 2); rows outside the line came
+        // in as zeros: periodic lines take their wrapped rows from global
+        // memory, Dirichlet ends replace the values that used them
+        const float *Th = tile + (size_t)(w * RPT) * 32 + lane;
+        const float *Tl = tile + (size_t)(tm.nbox * tm.box_rows + w * RPT) * 32 + lane;
+        float hm = Th[0], lm = Tl[0], h0 = Th[32], l0 = Tl[32];
+        if (BC == BC_PERIODIC && io && seg == 0) {
+            const float *Hp = (const float *)pr.u_hi + lbase, *Lp = (const float *)pr.u_lo + lbase;
+            hm = Hp[(int64_t)(n - 2) * st];
+            lm = Lp[(int64_t)(n - 2) * st];
+            h0 = Hp[(int64_t)(n - 1) * st];
+            l0 = Lp[(int64_t)(n - 1) * st];
+        }
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) z[k] = 0.f;
+        for (int k = 0; k <= RPT + 1; ++k) {
+            float hp = Th[(k + 2) * 32], lp = Tl[(k + 2) * 32];
+            if (BC == BC_PERIODIC && k >= RPT && io && seg == Gd - 1) {
+                const float *Hp = (const float *)pr.u_hi + lbase, *Lp = (const float *)pr.u_lo + lbase;
+                hp = Hp[(int64_t)(k - RPT) * st];
+                lp = Lp[(int64_t)(k - RPT) * st];
+            }
+            const float v = sdiff_pair(hm, h0, hp, lm, l0, lp);   // centre a + k - 1
+            if (k == 0) rl = v;
+            else if (k == RPT + 1) rr = v;
+            else z[k - 1] = v;
+            hm = h0;
+            h0 = hp;
+            lm = l0;
+            l0 = lp;
+        }
+        if (!io) {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) z[k] = 0.f;
+        }
+    } else {
+        if (io) strided_r_pair<BC, RPT>(pr, lbase, st, a, n, z, rl, rr);
+        else {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) z[k] = 0.f;
+        }
     }
     if (BC == BC_DIRICHLET) {
         if (left_end) z[0] = z[1];
@@ -203,11 +274,31 @@ __global__ void __launch_bounds__(256, 2) k_strided_nb(AxisDev A, LineSet LS, Pr
         hr1 = er1;
 
         float *o = reinterpret_cast<float *>(pr.out[p - 1]);
-        if (o != nullptr && io) {
+        if constexpr (STAGE & 2) {
+            if (o != nullptr) {
+                // the previous power's store has read the tile before it is
+                // written again; then one tensor store per box
+                if (threadIdx.x == 0) tma_store_wait_read();
+                __syncthreads();
+                float *T = tile + (size_t)(w * RPT) * 32 + lane;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) T[k * 32] = z[k];
+                fence_proxy_async();
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    const int orows = S * RPT, ob = orows > 256 ? 256 : orows;
+                    for (int y = 0; y < orows; y += ob) tma_store_3d(&tm.out[p - 1], x0, a0 + y, z0, tile + (size_t)y * 32);
+                    tma_store_commit();
+                }
+            }
+        } else if (o != nullptr && io) {
             float *po = o + lbase + (int64_t)a * st;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) { *po = z[k]; po += st; }
         }
+    }
+    if constexpr (STAGE & 2) {
+        if (threadIdx.x == 0) tma_store_wait_all();    // the tile outlives the stores that read it
     }
     // peers read this CTA's slots after the last exchange: no CTA of the
     // cluster exits before every one of them is past those reads

@@ -475,3 +475,27 @@ def test_strided_neighbour_exchange_matches_oracle(shape, cfl, bc, rpt, warps):
             got = s.apply_D(vd, 1, p).cpu().numpy()
             assert rel_l2(got, ref) <= tol_for("mixed", s, p), (nb, p, rel_l2(got, ref))
     s.close()
+
+
+@pytest.mark.parametrize("shape", [(2048, 96), (256, 64), (128, 32, 64)])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("stage", [1, 2, 3])
+@pytest.mark.parametrize("rpt,warps", [(0, 4), (0, 8), (32, 8)])
+def test_strided_tma_staging_matches_oracle(shape, bc, stage, rpt, warps):
+    """The neighbour-exchange strided pass with its tiles moved by TMA
+    (tensor loads of the pair level, tensor stores of the powers, or both)
+    equals the oracle's D^p, and mol_sync reports no timed-out wait."""
+    n = shape[0]                         # the strided axis: y in 2D, z in 3D
+    h = spacing(n, bc)
+    s = make(shape, 1.5 * h, 3, bc, "mixed")
+    v = field(shape, 80, bc)
+    vd = dev(v)
+    axis = 1 if len(shape) == 2 else 2
+    s.set_tuning(res_warps=2, strided_rpt=rpt, strided_warps=warps, rows_warps=0, strided_nb=1, strided_stage=stage)
+    assert s.tuning()["strided_stage"] == stage
+    for p in (1, 2, 3):
+        got = s.apply_D(vd, axis, p).cpu().numpy()
+        ref = oracle.D_axis(v, axis, s.nu[axis], bc, 2, power=p)
+        assert rel_l2(got, ref) <= tol_for("mixed", s, p), (p, rel_l2(got, ref))
+    s.sync()
+    s.close()
