@@ -254,6 +254,56 @@ mol_status mol_solve_dirichlet(mol_handle h, const double *u0, int64_t nsteps, c
 mol_status mol_solve_source(mol_handle h, const double *u0, int64_t nsteps, const double *g, const double *f,
                             double *u_out, void *stream);
 
+/*
+ * Robustness (no counterpart in the paper).
+ *
+ * mol_field_norm: *norm = the discrete L2 norm (prod_a h_a * sum u^2)^(1/2) of
+ * a device float64 field of the handle's grid (NaN or Inf propagate).
+ * Synchronous on the stream.
+ *
+ * mol_step_checked: mol_step plus an instability check: the norm of u_cur is
+ * taken before and after; MOL_EUNSTABLE if the field is no longer finite or
+ * its norm grew by more than growth_limit (> 0) times (an A-stable run at
+ * beta <= beta_max stays bounded, Sec. 3.1).  The fields hold the advanced
+ * levels either way.  Synchronous.
+ *
+ * mol_checkpoint_write / mol_checkpoint_read: save and restore a run's state
+ * -- the two levels u^{n-1}, u^n (device float64, caller-owned) and the step
+ * index -- in a file with a header naming the problem (grid, c, dt, beta, P,
+ * boundary condition, precision, quadrature) and a hash of the data.  Reading
+ * refuses (MOL_EINVAL, with the reason) a file written for another problem, a
+ * truncated file or data that do not match their hash.  Synchronous; the
+ * stream orders the copies.
+ */
+mol_status mol_field_norm(mol_handle h, const double *u, double *norm, void *stream);
+mol_status mol_step_checked(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps, double growth_limit,
+                            void *stream);
+mol_status mol_checkpoint_write(mol_handle h, const char *path, const double *u_prev, const double *u_cur,
+                                int64_t step, void *stream);
+mol_status mol_checkpoint_read(mol_handle h, const char *path, double *u_prev, double *u_cur, int64_t *step,
+                               void *stream);
+
+/*
+ * Test hooks (no counterpart in the paper).
+ *
+ * mol_wait_selftest: launches one CTA whose bounded wait (the same code as the
+ * tile-copy barriers) cannot succeed, with a limit of limit_cycles SM cycles
+ * (1 .. 2^40), and synchronizes.  Returns MOL_ETIMEOUT when the wait gave up
+ * and raised the device flag, as it must; the GPU context stays usable.
+ *
+ * mol_debug_fail_alloc(after): the next `after` device allocations of the
+ * library succeed and every one after them fails as if the device were full
+ * (MOL_ENOMEM from the creating call, with everything it had allocated freed);
+ * after < 0 switches the injection off.  Process-wide.
+ *
+ * mol_debug_allow_unstable(on): with on != 0, mol_create accepts beta above
+ * beta_max(P) (to exercise the instability check); 0 restores the refusal.
+ * Process-wide.
+ */
+mol_status mol_wait_selftest(int64_t limit_cycles, void *stream);
+void mol_debug_fail_alloc(int64_t after);
+void mol_debug_allow_unstable(int on);
+
 /* Synchronize the stream and report device-side failures: MOL_ECUDA for a
  * CUDA error, MOL_ETIMEOUT when a bounded wait inside a kernel (the strided
  * pass's tile-copy barrier, MOL_TUNE_STRIDED_STAGE 1 or 3) gave up since the

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "molt.h"
 #include "molt_internal.h"
 #include "molt_recv.cuh"
@@ -73,6 +75,7 @@ struct mol_ctx {
     int nrec = 0, irec_cap = 0, nnode = 0;
     double *srcbuf = nullptr;                  // mol_solve_source: C[g] and two temporaries (3 N)
     float *src32 = nullptr;                    //   float32 copies of g and C[g] (mixed, 2 N)
+    double *norm_acc = nullptr;                // mol_field_norm: one double of device scratch
     bool timing = false;                       // per-pass events (benchmarks)
     std::vector<cudaEvent_t> ev_pool;          // reusable events
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;  // (axis, (start, stop))
@@ -82,6 +85,15 @@ struct mol_ctx {
 namespace {
 
 thread_local std::string g_err;
+
+// NVTX range for the lifetime of a scope (shows in Nsight timelines; no cost
+// without a tool attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 mol_status fail(mol_ctx *h, mol_status st, const std::string &msg)
 {
@@ -113,6 +125,8 @@ int ilog2(int W)
 // ---------------------------------------------------------------------------
 mol_status dev_alloc(mol_ctx *h, void **p, size_t bytes)
 {
+    if (alloc_injected_failure())
+        return fail(h, MOL_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -233,6 +247,8 @@ LineSet lineset_of(const mol_ctx *h, int axis)
 mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersParams *pp, const HornerParams *hp,
                        cudaStream_t s)
 {
+    static const char *const kPassNames[3] = {"pass x", "pass y", "pass z"};
+    NvtxRange nvtx_(kPassNames[axis < 0 || axis > 2 ? 0 : axis]);
     const int n = (int)h->n[axis];
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     mol_status st = timing_begin(h, s, &e0, &e1);
@@ -658,7 +674,7 @@ mol_status mol_create(const mol_grid *grid, double c, double dt, double beta, in
     }
     const double bmax = beta_max_of(P);
     if (beta <= 0) beta = bmax;
-    if (beta > bmax * (1.0 + 1e-12))
+    if (beta > bmax * (1.0 + 1e-12) && !unstable_allowed())
         return fail(nullptr, MOL_EUNSTABLE, "beta above beta_max(P): the scheme is not A-stable");
 
     h = new mol_ctx();
@@ -793,6 +809,7 @@ mol_status mol_get_params(mol_handle h, double out[8])
 
 mol_status mol_apply_D(mol_handle h, const double *v, double *outp, int axis, int power, void *stream)
 {
+    NvtxRange nvtx_("mol_apply_D");
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
     if (axis < 0 || axis >= h->ndim) return fail(h, MOL_EINVAL, "axis out of range");
     if (power < 1 || power > MAXG) return fail(h, MOL_EINVAL, "power must be in 1..8");
@@ -818,6 +835,7 @@ mol_status mol_apply_D(mol_handle h, const double *v, double *outp, int axis, in
 
 mol_status mol_apply_F(mol_handle h, const double *u, double *F, void *stream)
 {
+    NvtxRange nvtx_("mol_apply_F");
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
     if (h->batch) {
         const mol_status st0 = mol_batch_apply_F(h->batch, u, F, stream);
@@ -841,6 +859,7 @@ mol_status mol_apply_F(mol_handle h, const double *u, double *F, void *stream)
 
 mol_status mol_start(mol_handle h, const double *u0, double *u1, void *stream)
 {
+    NvtxRange nvtx_("mol_start");
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
     if (h->batch) {
         const mol_status st0 = mol_batch_start(h->batch, u0, u1, stream);
@@ -864,6 +883,7 @@ mol_status mol_start(mol_handle h, const double *u0, double *u1, void *stream)
 
 mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps, void *stream)
 {
+    NvtxRange nvtx_("mol_step");
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
     if (h->batch) {
         const mol_status st0 = mol_batch_step(h->batch, u_prev, u_cur, nsteps, stream);
@@ -898,6 +918,7 @@ mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps,
 
 mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t nsteps, void *stream)
 {
+    NvtxRange nvtx_("mol_solve_host");
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
     if (h->batch) {
         const mol_status st0 = mol_batch_solve_host(h->batch, u0, u_out, nsteps, stream);
@@ -920,6 +941,7 @@ mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t
 
 mol_status mol_autotune(mol_handle h, void *stream)
 {
+    NvtxRange nvtx_("mol_autotune");
     if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
     if (h->batch) {
         const mol_status st0 = mol_batch_autotune(h->batch, stream);
@@ -1581,7 +1603,7 @@ extern "C" mol_status mol_apply_F_noalloc(const mol_grid *grid, double c, double
     }
     const double bmax = beta_max_of(P);
     if (beta <= 0) beta = bmax;
-    if (beta > bmax * (1.0 + 1e-12))
+    if (beta > bmax * (1.0 + 1e-12) && !unstable_allowed())
         return fail(nullptr, MOL_EUNSTABLE, "beta above beta_max(P): the scheme is not A-stable");
 
     // scratch layout (doubles, every part 256-byte aligned): Horner tables,
@@ -1704,3 +1726,186 @@ extern "C" mol_status mol_apply_F_noalloc(const mol_grid *grid, double c, double
     if (st != MOL_OK) g_err = h.err;
     return st;
 }
+
+// ===========================================================================
+// Robustness: field norm and checked stepping, checkpoint files, the device
+// wait self-test (no counterpart in the paper)
+// ===========================================================================
+namespace {
+
+// sum of squares of x[0..N) into *acc (block partial sums, one atomic add
+// per block); NaN and Inf propagate into the sum
+__global__ void k_sumsq(const double *x, int64_t N, double *acc)
+{
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        s += x[i] * x[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(acc, s);
+    }
+}
+
+mol_status field_norm(mol_ctx *h, const double *u, double *norm, cudaStream_t s)
+{
+    if (!h->norm_acc) {
+        mol_status st = dev_alloc(h, (void **)&h->norm_acc, sizeof(double));
+        if (st != MOL_OK) return st;
+    }
+    CK(cudaMemsetAsync(h->norm_acc, 0, sizeof(double), s), "memset");
+    const int64_t blocks = std::min<int64_t>((h->N + 255) / 256, 4 * (int64_t)h->num_sms);
+    k_sumsq<<<(unsigned)blocks, 256, 0, s>>>(u, h->N, h->norm_acc);
+    CK(cudaGetLastError(), "norm launch");
+    double ss = 0.0;
+    CK(cudaMemcpyAsync(&ss, h->norm_acc, sizeof(double), cudaMemcpyDeviceToHost, s), "norm copy");
+    CK(cudaStreamSynchronize(s), "stream synchronize");
+    double vol = 1.0;
+    for (int a = 0; a < h->ndim; ++a) vol *= h->h[a];
+    *norm = std::sqrt(vol * ss);
+    return MOL_OK;
+}
+
+// Checkpoint file: a fixed header that names the problem, the step index,
+// then u^{n-1} and u^n (float64, x fastest) and an FNV-1a hash of them.
+constexpr char kCkpMagic[8] = {'M', 'O', 'L', 'T', 'C', 'K', 'P', '1'};
+struct CkpHeader {
+    char magic[8];
+    int32_t ndim, P, bc, prec, quad;
+    int32_t pad;
+    int64_t n[3];
+    double lo[3], hi[3], c, dt, beta;
+    int64_t step;
+};
+
+uint64_t fnv1a(const void *p, size_t bytes, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < bytes; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+CkpHeader header_of(const mol_ctx *h, int64_t step)
+{
+    CkpHeader hd{};
+    std::memcpy(hd.magic, kCkpMagic, 8);
+    hd.ndim = h->ndim;
+    hd.P = h->P;
+    hd.bc = (int32_t)h->bc;
+    hd.prec = (int32_t)h->prec;
+    hd.quad = h->opt.quad_order;
+    for (int a = 0; a < 3; ++a) { hd.n[a] = h->n[a]; hd.lo[a] = h->lo[a]; hd.hi[a] = h->hi[a]; }
+    hd.c = h->c;
+    hd.dt = h->dt;
+    hd.beta = h->beta;
+    hd.step = step;
+    return hd;
+}
+
+}  // namespace
+
+extern "C" {
+
+mol_status mol_field_norm(mol_handle h, const double *u, double *norm, void *stream)
+{
+    if (!h || !norm) return fail(h, MOL_EINVAL, "NULL argument");
+    mol_status st = check_ptr(h, u, "u");
+    if (st != MOL_OK) return st;
+    NvtxRange r("mol_field_norm");
+    return field_norm(h, u, norm, (cudaStream_t)stream);
+}
+
+mol_status mol_step_checked(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps, double growth_limit,
+                            void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    if (!(growth_limit > 0) || !std::isfinite(growth_limit)) return fail(h, MOL_EINVAL, "growth_limit must be > 0");
+    mol_status st;
+    if ((st = check_ptr(h, u_cur, "u_cur")) != MOL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double n0 = 0.0, n1 = 0.0;
+    if ((st = field_norm(h, u_cur, &n0, s)) != MOL_OK) return st;
+    if ((st = mol_step(h, u_prev, u_cur, nsteps, stream)) != MOL_OK) return st;
+    if ((st = field_norm(h, u_cur, &n1, s)) != MOL_OK) return st;
+    if (!std::isfinite(n1))
+        return fail(h, MOL_EUNSTABLE, "the field is no longer finite after " + std::to_string(nsteps) + " steps");
+    if (n1 > growth_limit * std::max(n0, 1e-300))
+        return fail(h, MOL_EUNSTABLE, "the field norm grew from " + std::to_string(n0) + " to " + std::to_string(n1) +
+                                          " in " + std::to_string(nsteps) + " steps (limit x" +
+                                          std::to_string(growth_limit) + ")");
+    return MOL_OK;
+}
+
+mol_status mol_checkpoint_write(mol_handle h, const char *path, const double *u_prev, const double *u_cur, int64_t step,
+                                void *stream)
+{
+    if (!h || !path) return fail(h, MOL_EINVAL, "NULL argument");
+    mol_status st;
+    if ((st = check_ptr(h, u_prev, "u_prev")) != MOL_OK || (st = check_ptr(h, u_cur, "u_cur")) != MOL_OK) return st;
+    NvtxRange r("mol_checkpoint_write");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> buf(2 * (size_t)h->N);
+    CK(cudaMemcpyAsync(buf.data(), u_prev, sizeof(double) * h->N, cudaMemcpyDeviceToHost, s), "copy u_prev");
+    CK(cudaMemcpyAsync(buf.data() + h->N, u_cur, sizeof(double) * h->N, cudaMemcpyDeviceToHost, s), "copy u_cur");
+    CK(cudaStreamSynchronize(s), "stream synchronize");
+    const CkpHeader hd = header_of(h, step);
+    const uint64_t sum = fnv1a(buf.data(), sizeof(double) * buf.size());
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(h, MOL_EINVAL, std::string("cannot open ") + path + " for writing");
+    bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1 && std::fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size() &&
+              std::fwrite(&sum, sizeof sum, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MOL_OK : fail(h, MOL_EINVAL, std::string("writing ") + path + " failed");
+}
+
+mol_status mol_checkpoint_read(mol_handle h, const char *path, double *u_prev, double *u_cur, int64_t *step,
+                               void *stream)
+{
+    if (!h || !path || !step) return fail(h, MOL_EINVAL, "NULL argument");
+    mol_status st;
+    if ((st = check_ptr(h, u_prev, "u_prev")) != MOL_OK || (st = check_ptr(h, u_cur, "u_cur")) != MOL_OK) return st;
+    NvtxRange r("mol_checkpoint_read");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(h, MOL_EINVAL, std::string("cannot open ") + path);
+    CkpHeader hd{};
+    std::vector<double> buf(2 * (size_t)h->N);
+    uint64_t sum = 0;
+    const bool ok = std::fread(&hd, sizeof hd, 1, f) == 1 && std::fread(buf.data(), sizeof(double), buf.size(), f) == buf.size() &&
+                    std::fread(&sum, sizeof sum, 1, f) == 1;
+    std::fclose(f);
+    if (!ok) return fail(h, MOL_EINVAL, std::string(path) + ": truncated or not a checkpoint of this grid");
+    CkpHeader want = header_of(h, hd.step);
+    if (std::memcmp(&hd, &want, sizeof hd) != 0)
+        return fail(h, MOL_EINVAL, std::string(path) + ": written for another problem (grid, c, dt, beta, P, boundary, "
+                                                       "precision or quadrature differ)");
+    if (fnv1a(buf.data(), sizeof(double) * buf.size()) != sum)
+        return fail(h, MOL_EINVAL, std::string(path) + ": the field data do not match their checksum");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(u_prev, buf.data(), sizeof(double) * h->N, cudaMemcpyHostToDevice, s), "copy u_prev");
+    CK(cudaMemcpyAsync(u_cur, buf.data() + h->N, sizeof(double) * h->N, cudaMemcpyHostToDevice, s), "copy u_cur");
+    CK(cudaStreamSynchronize(s), "stream synchronize");
+    *step = hd.step;
+    return MOL_OK;
+}
+
+mol_status mol_wait_selftest(int64_t limit_cycles, void *stream)
+{
+    if (limit_cycles < 1 || limit_cycles > (int64_t)1 << 40)
+        return fail(nullptr, MOL_EINVAL, "limit_cycles must be in 1..2^40");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_wait_selftest((long long)limit_cycles, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "self-test launch");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(nullptr, e, "stream synchronize");
+    const int to = regs_timeout_take(s);
+    if (to < 0) return fail(nullptr, MOL_ECUDA, "reading the device wait flag failed");
+    if (to > 0) return fail(nullptr, MOL_ETIMEOUT, "the bounded device wait gave up, as it must");
+    return MOL_OK;
+}
+
+}  // extern "C"

@@ -89,6 +89,8 @@ mol_status bcuda(mol_batch_ctx *b, cudaError_t e, const char *what)
 
 mol_status balloc(mol_batch_ctx *b, void **p, size_t bytes)
 {
+    if (alloc_injected_failure())
+        return bfail(b, MOL_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -718,6 +718,8 @@ mol_status efail(mol_embed_ctx *e, mol_status st, const std::string &msg)
 
 mol_status ealloc(mol_embed_ctx *e, void **p, size_t bytes)
 {
+    if (alloc_injected_failure())
+        return efail(e, MOL_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
     cudaError_t r = cudaMalloc(p, bytes);
     if (r != cudaSuccess) {
         cudaGetLastError();

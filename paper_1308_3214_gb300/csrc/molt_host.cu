@@ -2,6 +2,7 @@
 // problem and the batched entry points: the update weights and beta_max
 // (Sec. 3), the expansion of F in the per-axis D_gamma (Sec. 4), and the
 // per-axis constants of the difference form of D.
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -183,4 +184,25 @@ void axis_constants(double nu, int64_t n, int bc, int quad, AxisDev &A)
     axis_mirror(A);
 }
 
+// ---------------------------------------------------------------------------
+// Test hooks (host only): injected allocation failure, unstable beta
+// ---------------------------------------------------------------------------
+static std::atomic<long long> g_alloc_budget{-1};
+static std::atomic<int> g_allow_unstable{0};
+
+bool alloc_injected_failure()
+{
+    long long b = g_alloc_budget.load();
+    while (b >= 0) {
+        if (b == 0) return true;
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) return false;
+    }
+    return false;
+}
+
+bool unstable_allowed() { return g_allow_unstable.load() != 0; }
+
 }  // namespace molt
+
+extern "C" void mol_debug_fail_alloc(int64_t after) { molt::g_alloc_budget.store(after < 0 ? -1 : (long long)after); }
+extern "C" void mol_debug_allow_unstable(int on) { molt::g_allow_unstable.store(on ? 1 : 0); }

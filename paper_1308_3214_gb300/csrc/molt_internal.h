@@ -31,6 +31,12 @@ cudaError_t launch_to_pair(const double *x, float *hi, float *lo, int64_t N, cud
 cudaError_t launch_from_pair(const float *hi, const float *lo, double *x, int64_t N, cudaStream_t s);
 cudaError_t launch_from_f32(const float *f, double *x, int64_t N, cudaStream_t s);
 
+// Test hooks (molt_host.cu; set through mol_debug_fail_alloc /
+// mol_debug_allow_unstable): true when the next device allocation is to fail
+// as if the device were full; true when beta above beta_max is accepted.
+bool alloc_injected_failure();
+bool unstable_allowed();
+
 // Allow every pass kernel the largest dynamic shared-memory carve-out.
 cudaError_t configure_kernels();
 
@@ -64,6 +70,8 @@ cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &
 // 1 if a bounded wait of a register kernel gave up since the last call (and
 // clears it), 0 if not, -1 if the flag could not be read; synchronizes s.
 int regs_timeout_take(cudaStream_t s);
+// A kernel whose bounded wait cannot succeed (mol_wait_selftest).
+cudaError_t launch_wait_selftest(long long limit_cycles, cudaStream_t s);
 bool regs_res_plan(int tbytes, int n, int ng, int *rpt);
 bool regs_rows_plan(int tbytes, int n, int ng, int W, int *rpt);
 cudaError_t launch_rows(int bc, int rpt, int ng, int W, const AxisDev &A, const LineSet &L, const ProgParams &p,

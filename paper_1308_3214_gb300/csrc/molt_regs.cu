@@ -290,6 +290,25 @@ cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &
                              : run_strided_nb<BC_DIRICHLET, kStridedRptF2>(A, L, p, s, stage);
 }
 
+// One CTA waits on a barrier that is never completed (two arrivals expected,
+// one made), bounded by `limit` cycles: the timeout path of every bounded
+// wait, without a copy in flight.
+__global__ void k_wait_selftest(long long limit)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 2);
+    __syncthreads();
+    if (threadIdx.x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0, limit) && threadIdx.x == 0) atomicExch(&g_molt_timeout, 1);
+}
+
+cudaError_t launch_wait_selftest(long long limit_cycles, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(limit_cycles);
+    return cudaGetLastError();
+}
+
 int regs_timeout_take(cudaStream_t s)
 {
     int v = 0, zero = 0;

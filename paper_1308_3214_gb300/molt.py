@@ -37,7 +37,9 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_batch_autotune", "mol_batch_get_tuning", "mol_batch_set_tuning", "mol_solve_dirichlet", "mol_solve_source", "mol_apply_FT", "mol_traces", "mol_adjoint",
            "mol_embed_create", "mol_embed_destroy", "mol_embed_last_error", "mol_embed_linv", "mol_embed_apply_F",
            "mol_embed_start", "mol_embed_step", "mol_embed_solve_host", "mol_embed_sync", "mol_embed_launch_count",
-           "mol_embed_set_pass_timing", "mol_embed_pass_times"]
+           "mol_embed_set_pass_timing", "mol_embed_pass_times", "mol_field_norm", "mol_step_checked",
+           "mol_checkpoint_write", "mol_checkpoint_read", "mol_wait_selftest", "mol_debug_fail_alloc",
+           "mol_debug_allow_unstable"]
 
 
 class MolError(RuntimeError):
@@ -147,10 +149,20 @@ def load_library(path: Path | None = None):
     lib.mol_embed_set_pass_timing.argtypes = [vp, I]
     lib.mol_embed_pass_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
     lib.mol_launch_count.restype = i64
+    lib.mol_field_norm.argtypes = [vp, vp, dp, vp]
+    lib.mol_step_checked.argtypes = [vp, vp, vp, i64, D, vp]
+    lib.mol_checkpoint_write.argtypes = [vp, ctypes.c_char_p, vp, vp, i64, vp]
+    lib.mol_checkpoint_read.argtypes = [vp, ctypes.c_char_p, vp, vp, ctypes.POINTER(i64), vp]
+    lib.mol_wait_selftest.argtypes = [i64, vp]
+    lib.mol_debug_fail_alloc.argtypes = [i64]
+    lib.mol_debug_fail_alloc.restype = None
+    lib.mol_debug_allow_unstable.argtypes = [I]
+    lib.mol_debug_allow_unstable.restype = None
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
                         "mol_launch_count", "mol_batch_last_error", "mol_batch_launch_count",
-                        "mol_embed_last_error", "mol_embed_launch_count"):
+                        "mol_embed_last_error", "mol_embed_launch_count", "mol_debug_fail_alloc",
+                        "mol_debug_allow_unstable"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -385,6 +397,33 @@ class Solver:
 
     def sync(self, stream=None):
         self._check(self.lib.mol_sync(self.h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def norm(self, u, stream=None) -> float:
+        """Discrete L2 norm of a field of this grid (synchronous)."""
+        out = ctypes.c_double()
+        self._check(self.lib.mol_field_norm(self.h, self._field(u, "u"), ctypes.byref(out),
+                                            ctypes.c_void_p(_stream_ptr(stream))))
+        return out.value
+
+    def step_checked(self, u_prev, u_cur, nsteps: int, growth_limit: float = 1e3, stream=None):
+        """step() that raises MolError(MOL_EUNSTABLE) if the field stops being
+        finite or its norm grows by more than growth_limit times."""
+        self._check(self.lib.mol_step_checked(self.h, self._field(u_prev, "u_prev"), self._field(u_cur, "u_cur"),
+                                              int(nsteps), float(growth_limit), ctypes.c_void_p(_stream_ptr(stream))))
+
+    def checkpoint_write(self, path, u_prev, u_cur, step: int, stream=None):
+        """Save (u^{n-1}, u^n, n) with a header naming this problem."""
+        self._check(self.lib.mol_checkpoint_write(self.h, str(path).encode(), self._field(u_prev, "u_prev"),
+                                                  self._field(u_cur, "u_cur"), int(step),
+                                                  ctypes.c_void_p(_stream_ptr(stream))))
+
+    def checkpoint_read(self, path, u_prev, u_cur, stream=None) -> int:
+        """Restore the levels from a checkpoint of this problem; returns n."""
+        step = ctypes.c_int64()
+        self._check(self.lib.mol_checkpoint_read(self.h, str(path).encode(), self._field(u_prev, "u_prev"),
+                                                 self._field(u_cur, "u_cur"), ctypes.byref(step),
+                                                 ctypes.c_void_p(_stream_ptr(stream))))
+        return step.value
 
     def set_pass_timing(self, enable: bool = True):
         self._check(self.lib.mol_set_pass_timing(self.h, 1 if enable else 0))

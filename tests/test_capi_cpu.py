@@ -141,3 +141,15 @@ def test_embed_null_handle_calls_fail_cleanly(lib):
     assert lib.mol_embed_step(None, None, None, 1, None) == molt.MOL_EINVAL
     assert lib.mol_embed_destroy(None) == molt.MOL_OK
     assert lib.mol_embed_launch_count(None) == 0
+
+
+def test_robustness_calls_refuse_bad_arguments_on_the_host(lib):
+    """Host-side checks of the robustness entry points (no GPU needed)."""
+    assert lib.mol_field_norm(None, None, None, None) == molt.MOL_EINVAL
+    assert lib.mol_step_checked(None, None, None, 1, 10.0, None) == molt.MOL_EINVAL
+    assert lib.mol_checkpoint_write(None, b"x", None, None, 0, None) == molt.MOL_EINVAL
+    assert lib.mol_checkpoint_read(None, b"x", None, None, None, None) == molt.MOL_EINVAL
+    for limit in (0, -1, 1 << 41):
+        assert lib.mol_wait_selftest(limit, None) == molt.MOL_EINVAL
+    lib.mol_debug_fail_alloc(-1)          # the hooks are plain host switches
+    lib.mol_debug_allow_unstable(0)
