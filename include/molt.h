@@ -255,6 +255,34 @@ mol_status mol_solve_source(mol_handle h, const double *u0, int64_t nsteps, cons
                             double *u_out, void *stream);
 
 /*
+ * Gradient of a loss of the whole field history by checkpoint-and-recompute
+ * (the paper has no adjoint; the discrete adjoint of the implemented forward
+ * map, as mol_adjoint).
+ *
+ * J = sum_{n=0}^{nsteps} phi_n(u^n) over the forward run from u0 with zero
+ * initial velocity (u^1 = u^0 + F u^0 / 2).  grad_fn(n, u_n, g_n, stream,
+ * user) is called on the host for n = nsteps .. 0 (each n once, in that
+ * order); u_n (device, float64, the grid's layout; packed for a batch) holds
+ * u^n and must not be written; the function writes dphi_n/du^n into g_n
+ * (device, float64, same layout) with work ordered on `stream` and returns 0,
+ * or returns 1 when phi_n is absent (g_n is then not read); any other return
+ * value aborts the call with MOL_EINVAL.
+ *
+ * The adjoint states obey mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n
+ * (n = N .. 1, mu^{N+1} = mu^{N+2} = 0) and grad = mu^1 + F^T mu^1 / 2 -
+ * mu^2 + g^0.  g^n needs u^n in reverse order: the forward pass keeps
+ * (u^{c-1}, u^c) at c = 1, 1 + K, 1 + 2K, ... (K = checkpoint_every >= 1) and
+ * the backward pass recomputes one segment of at most K states at a time
+ * from its checkpoint on the device, holding 2 ceil(N/K) + K + 4 fields
+ * (allocated for the call and freed before it returns).  grad: device,
+ * float64.  Synchronous.  Errors: MOL_EINVAL (arguments, callback failure),
+ * MOL_ENOMEM, MOL_ECUDA.
+ */
+typedef int (*mol_grad_fn)(int64_t n, const double *u_n, double *g_n, void *stream, void *user);
+mol_status mol_adjoint_history(mol_handle h, const double *u0, int64_t nsteps, int64_t checkpoint_every,
+                               mol_grad_fn grad_fn, void *user, double *grad, void *stream);
+
+/*
  * Robustness (no counterpart in the paper).
  *
  * mol_field_norm: *norm = the discrete L2 norm (prod_a h_a * sum u^2)^(1/2) of
@@ -405,6 +433,11 @@ mol_status mol_batch_traces(mol_batch b, const double *u0, int nrec, const int64
 /* grad (device, packed) = dJ/du^0 given tgrad (device, nsteps * nrec). */
 mol_status mol_batch_adjoint(mol_batch b, int nrec, const int64_t *rec, int64_t nsteps, const double *tgrad,
                              double *grad, void *stream);
+
+/* mol_adjoint_history for a batch (fields packed; grad_fn sees packed u_n
+ * and writes packed g_n). */
+mol_status mol_batch_adjoint_history(mol_batch b, const double *u0, int64_t nsteps, int64_t checkpoint_every,
+                                     mol_grad_fn grad_fn, void *user, double *grad, void *stream);
 
 /* End-to-end from HOST memory, as mol_solve_host: packed u0 (host float64)
  * in, u^{nsteps} of every problem out (host float64, packed).  Synchronous. */

@@ -1909,3 +1909,75 @@ mol_status mol_wait_selftest(int64_t limit_cycles, void *stream)
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// History gradient (checkpoint-and-recompute) on a single-problem handle
+// ===========================================================================
+namespace {
+
+mol_status hist_fail(void *c, mol_status st, const char *msg) { return fail((mol_ctx *)c, st, msg); }
+
+mol_status hist_start(void *c, const double *u0, double *u1, cudaStream_t s)
+{
+    return mol_start((mol_ctx *)c, u0, u1, (void *)s);
+}
+
+mol_status hist_step(void *c, double *prev, double *cur, int64_t n, cudaStream_t s)
+{
+    return mol_step((mol_ctx *)c, prev, cur, n, (void *)s);
+}
+
+// m steps on the handle's levels, each new level written out once
+mol_status hist_step_emit(void *c, const double *prev, const double *cur, int64_t m, double *states, cudaStream_t s)
+{
+    mol_ctx *h = (mol_ctx *)c;
+    mol_status st;
+    if ((st = load_level(h, prev, h->lev[0], s)) != MOL_OK) return st;
+    if ((st = load_level(h, cur, h->lev[1], s)) != MOL_OK) return st;
+    for (int64_t j = 0; j < m; ++j) {
+        const int k = (int)(j % 3);
+        if ((st = run_update(h, h->lev[(k + 1) % 3], h->lev[k], h->lev[(k + 2) % 3], 2.0, -1.0, 1.0, s)) != MOL_OK)
+            return st;
+        if ((st = store_level(h, h->lev[(k + 2) % 3], states + (size_t)j * h->N, s)) != MOL_OK) return st;
+    }
+    return MOL_OK;
+}
+
+mol_status hist_update_T(void *c, const double *u, const double *up, double *un, double ea, double eb, double ec,
+                         const double *add, cudaStream_t s)
+{
+    mol_ctx *h = (mol_ctx *)c;
+    mol_status st;
+    if ((st = load_level(h, u, h->lev[0], s)) != MOL_OK) return st;
+    if ((st = load_level(h, up, h->lev[1], s)) != MOL_OK) return st;
+    if ((st = run_update_T(h, h->lev[0], h->lev[1], h->lev[2], ea, eb, ec, s)) != MOL_OK) return st;
+    if ((st = store_level(h, h->lev[2], un, s)) != MOL_OK) return st;
+    if (add) {
+        const int nb = grid_for(h);
+        k_axpby<<<nb, 256, 0, s>>>(un, un, add, 1.0, 1.0, h->N);
+        CK(cudaGetLastError(), "gradient injection");
+        h->launches++;
+    }
+    return MOL_OK;
+}
+
+}  // namespace
+
+extern "C" mol_status mol_adjoint_history(mol_handle h, const double *u0, int64_t nsteps, int64_t checkpoint_every,
+                                          mol_grad_fn grad_fn, void *user, double *grad, void *stream)
+{
+    if (!h) return fail(nullptr, MOL_EINVAL, "handle is NULL");
+    NvtxRange nvtx_("mol_adjoint_history");
+    if (!single_adjoint(h)) {
+        mol_batch b = nullptr;
+        mol_status st = adjoint_batch(h, &b);
+        if (st != MOL_OK) return st;
+        st = mol_batch_adjoint_history(b, u0, nsteps, checkpoint_every, grad_fn, user, grad, stream);
+        if (st != MOL_OK) h->err = mol_batch_last_error(b);
+        return st;
+    }
+    mol_status st;
+    if ((st = check_ptr(h, u0, "u0")) != MOL_OK || (st = check_ptr(h, grad, "grad")) != MOL_OK) return st;
+    HistoryOps o{h, h->N, hist_start, hist_step, hist_step_emit, hist_update_T, hist_fail};
+    return history_gradient_run(o, u0, nsteps, checkpoint_every, grad_fn, user, grad, (cudaStream_t)stream);
+}

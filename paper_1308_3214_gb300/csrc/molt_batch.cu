@@ -981,4 +981,54 @@ mol_status mol_batch_pass_times(mol_batch b, double total_ms[3], int64_t launche
     return MOL_OK;
 }
 
+
+// history gradient (checkpoint-and-recompute) over the batch's packed fields
+namespace {
+
+mol_status bh_fail(void *c, mol_status st, const char *msg) { return bfail((mol_batch_ctx *)c, st, msg); }
+
+mol_status bh_start(void *c, const double *u0, double *u1, cudaStream_t s)
+{
+    return mol_batch_start((mol_batch_ctx *)c, u0, u1, (void *)s);
+}
+
+mol_status bh_step(void *c, double *prev, double *cur, int64_t n, cudaStream_t s)
+{
+    return mol_batch_step((mol_batch_ctx *)c, prev, cur, n, (void *)s);
+}
+
+mol_status bh_step_emit(void *c, const double *prev, const double *cur, int64_t m, double *states, cudaStream_t s)
+{
+    mol_batch_ctx *b = (mol_batch_ctx *)c;
+    mol_status st;
+    if ((st = pack(b, prev, b->lev[0], s)) != MOL_OK) return st;
+    if ((st = pack(b, cur, b->lev[1], s)) != MOL_OK) return st;
+    const int64_t N = b->uoff[b->nprob];
+    for (int64_t j = 0; j < m; ++j) {
+        const int k = (int)(j % 3);
+        if ((st = run_update(b, b->lev[(k + 1) % 3], b->lev[k], b->lev[(k + 2) % 3], 2.0, -1.0, 1.0, s)) != MOL_OK)
+            return st;
+        if ((st = unpack(b, b->lev[(k + 2) % 3], states + (size_t)j * N, s)) != MOL_OK) return st;
+    }
+    return MOL_OK;
+}
+
+mol_status bh_update_T(void *c, const double *u, const double *up, double *un, double ea, double eb, double ec,
+                       const double *add, cudaStream_t s)
+{
+    return mol_batch_update((mol_batch_ctx *)c, u, up, un, ea, eb, ec, 1, add, (void *)s);
+}
+
+}  // namespace
+
+mol_status mol_batch_adjoint_history(mol_batch b, const double *u0, int64_t nsteps, int64_t checkpoint_every,
+                                     mol_grad_fn grad_fn, void *user, double *grad, void *stream)
+{
+    if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
+    mol_status st;
+    if ((st = bcheck_ptr(b, u0, "u0")) != MOL_OK || (st = bcheck_ptr(b, grad, "grad")) != MOL_OK) return st;
+    HistoryOps o{b, b->uoff[b->nprob], bh_start, bh_step, bh_step_emit, bh_update_T, bh_fail};
+    return history_gradient_run(o, u0, nsteps, checkpoint_every, grad_fn, user, grad, (cudaStream_t)stream);
+}
+
 }  // extern "C"

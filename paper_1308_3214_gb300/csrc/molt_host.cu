@@ -2,8 +2,10 @@
 // problem and the batched entry points: the update weights and beta_max
 // (Sec. 3), the expansion of F in the per-axis D_gamma (Sec. 4), and the
 // per-axis constants of the difference form of D.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "molt_internal.h"
@@ -182,6 +184,72 @@ void axis_constants(double nu, int64_t n, int bc, int quad, AxisDev &A)
     }
     for (int k = 0; k < 5; ++k) A.dm[k] = std::exp(-nu * (double)A.m * (double)(1 << k));
     axis_mirror(A);
+}
+
+// ---------------------------------------------------------------------------
+// History gradient by checkpoint-and-recompute (the adjoint of the forward
+// map u^0 -> (u^0 .. u^N); see mol_adjoint_history in molt.h)
+// ---------------------------------------------------------------------------
+bool alloc_injected_failure();
+
+mol_status history_gradient_run(const HistoryOps &o, const double *u0, int64_t N, int64_t K, mol_grad_fn fn,
+                                void *user, double *grad, cudaStream_t s)
+{
+    if (N < 1 || K < 1 || !fn) return o.fail(o.ctx, MOL_EINVAL, "need nsteps >= 1, checkpoint_every >= 1, grad_fn");
+    const int64_t nck = (N - 1) / K + 1;                   // checkpoints at c = 1 + i K <= N
+    const int64_t seg = std::min<int64_t>(K, N);
+    const size_t fb = sizeof(double) * (size_t)o.N;
+    const size_t total = fb * (size_t)(2 * nck + seg + 4);
+    double *buf = nullptr;
+    if (alloc_injected_failure()) return o.fail(o.ctx, MOL_ENOMEM, "history workspace allocation failed (injected)");
+    cudaError_t e = cudaMalloc(&buf, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return o.fail(o.ctx, MOL_ENOMEM, ("history workspace of " + std::to_string(total) + " bytes").c_str());
+    }
+    auto ck = [&](int64_t i, int which) { return buf + (size_t)(2 * i + which) * o.N; };
+    double *states = buf + (size_t)(2 * nck) * o.N;
+    double *mu[3] = {states + (size_t)seg * o.N, states + (size_t)(seg + 1) * o.N, states + (size_t)(seg + 2) * o.N};
+    double *g = states + (size_t)(seg + 3) * o.N;
+    mol_status st = MOL_OK;
+    auto cuda_ok = [&](cudaError_t r, const char *what) {
+        if (r == cudaSuccess) return true;
+        st = o.fail(o.ctx, MOL_ECUDA, (std::string(what) + ": " + cudaGetErrorString(r)).c_str());
+        return false;
+    };
+    // forward: (u^{c-1}, u^c) at every checkpoint
+    if (cuda_ok(cudaMemcpyAsync(ck(0, 0), u0, fb, cudaMemcpyDeviceToDevice, s), "copy u0"))
+        st = o.start(o.ctx, u0, ck(0, 1), s);
+    for (int64_t i = 1; i < nck && st == MOL_OK; ++i) {
+        if (!cuda_ok(cudaMemcpyAsync(ck(i, 0), ck(i - 1, 0), 2 * fb, cudaMemcpyDeviceToDevice, s), "copy checkpoint"))
+            break;
+        st = o.step(o.ctx, ck(i, 0), ck(i, 1), K, s);
+    }
+    // backward: recompute each segment's states, then run the adjoint through them
+    int i0 = 0, i1 = 1, i2 = 2;                             // mu^n, mu^{n+1}, mu^{n+2}
+    if (st == MOL_OK && cuda_ok(cudaMemsetAsync(mu[i1], 0, fb, s), "clear") &&
+        cuda_ok(cudaMemsetAsync(mu[i2], 0, fb, s), "clear")) {
+        for (int64_t i = nck - 1; i >= 0 && st == MOL_OK; --i) {
+            const int64_t c = 1 + i * K, last = std::min(c + K - 1, N), m = last - c;
+            if (!cuda_ok(cudaMemcpyAsync(states, ck(i, 1), fb, cudaMemcpyDeviceToDevice, s), "copy state")) break;
+            if (m > 0 && (st = o.step_emit(o.ctx, ck(i, 0), ck(i, 1), m, states + o.N, s)) != MOL_OK) break;
+            for (int64_t j = m; j >= 0 && st == MOL_OK; --j) {
+                const int r = fn(c + j, states + (size_t)j * o.N, g, (void *)s, user);
+                if (r != 0 && r != 1) { st = o.fail(o.ctx, MOL_EINVAL, "grad_fn returned an error"); break; }
+                st = o.update_T(o.ctx, mu[i1], mu[i2], mu[i0], 2.0, -1.0, 1.0, r == 0 ? g : nullptr, s);
+                const int t = i2; i2 = i1; i1 = i0; i0 = t;
+            }
+        }
+    }
+    if (st == MOL_OK) {
+        const int r = fn(0, u0, g, (void *)s, user);
+        if (r != 0 && r != 1) st = o.fail(o.ctx, MOL_EINVAL, "grad_fn returned an error");
+        else st = o.update_T(o.ctx, mu[i1], mu[i2], grad, 1.0, -1.0, 0.5, r == 0 ? g : nullptr, s);
+    }
+    if (st == MOL_OK) cuda_ok(cudaStreamSynchronize(s), "stream synchronize");
+    else cudaStreamSynchronize(s);
+    cudaFree(buf);
+    return st;
 }
 
 // ---------------------------------------------------------------------------

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <string>
 #include <vector>
+#include "molt.h"
 #include "molt_kernels.cuh"
 
 namespace molt {
@@ -36,6 +37,23 @@ cudaError_t launch_from_f32(const float *f, double *x, int64_t N, cudaStream_t s
 // as if the device were full; true when beta above beta_max is accepted.
 bool alloc_injected_failure();
 bool unstable_allowed();
+
+// Checkpoint-and-recompute history gradient (molt_host.cu), shared by the
+// single-problem and batch handles through their own field operations.
+struct HistoryOps {
+    void *ctx;
+    int64_t N;                                                  // doubles per field
+    mol_status (*start)(void *, const double *u0, double *u1, cudaStream_t);
+    mol_status (*step)(void *, double *prev, double *cur, int64_t nsteps, cudaStream_t);
+    // m steps from (prev, cur), unchanged; the new levels into states[0..m)
+    mol_status (*step_emit)(void *, const double *prev, const double *cur, int64_t m, double *states, cudaStream_t);
+    // un = ea u + eb up + ec F^T u (+ add)
+    mol_status (*update_T)(void *, const double *u, const double *up, double *un, double ea, double eb, double ec,
+                           const double *add, cudaStream_t);
+    mol_status (*fail)(void *, mol_status, const char *);
+};
+mol_status history_gradient_run(const HistoryOps &o, const double *u0, int64_t nsteps, int64_t K, mol_grad_fn fn,
+                                void *user, double *grad, cudaStream_t s);
 
 // Allow every pass kernel the largest dynamic shared-memory carve-out.
 cudaError_t configure_kernels();

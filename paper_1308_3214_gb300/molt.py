@@ -39,7 +39,7 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_embed_start", "mol_embed_step", "mol_embed_solve_host", "mol_embed_sync", "mol_embed_launch_count",
            "mol_embed_set_pass_timing", "mol_embed_pass_times", "mol_field_norm", "mol_step_checked",
            "mol_checkpoint_write", "mol_checkpoint_read", "mol_wait_selftest", "mol_debug_fail_alloc",
-           "mol_debug_allow_unstable"]
+           "mol_debug_allow_unstable", "mol_adjoint_history", "mol_batch_adjoint_history"]
 
 
 class MolError(RuntimeError):
@@ -158,6 +158,8 @@ def load_library(path: Path | None = None):
     lib.mol_debug_fail_alloc.restype = None
     lib.mol_debug_allow_unstable.argtypes = [I]
     lib.mol_debug_allow_unstable.restype = None
+    lib.mol_adjoint_history.argtypes = [vp, vp, i64, i64, GRAD_FN, vp, vp, vp]
+    lib.mol_batch_adjoint_history.argtypes = [vp, vp, i64, i64, GRAD_FN, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
                         "mol_launch_count", "mol_batch_last_error", "mol_batch_launch_count",
@@ -802,42 +804,58 @@ def receiver_traces(u0, solver: "BatchSolver", rec, nsteps: int):
     return _RT.apply(u0, solver, rec, nsteps)
 
 
-def history_gradient(solver: "BatchSolver", u0, nsteps: int, grad_fn, checkpoint_every: int = 40):
-    """dJ/du^0 for J = sum_{n=0}^{nsteps} phi_n(u^n) over the forward run from
-    u0 (zero initial velocity), given grad_fn(n, u_n) -> dphi_n/du^n (a packed
-    tensor, or None where phi_n is absent).
+GRAD_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_void_p)
 
-    The adjoint states obey mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n
-    (n = N..1, mu^{N+1} = mu^{N+2} = 0) and dJ/du^0 = mu^1 + F^T mu^1 / 2 -
-    mu^2 + g^0, with g^n = grad_fn(n, u^n).  g^n needs the forward state u^n
-    in reverse order: the forward pass keeps (u^{c-1}, u^c) at c = 1, 1+K,
-    1+2K, ... (K = checkpoint_every) and the backward pass recomputes one
-    segment of K states at a time from its checkpoint, holding about
-    2 N/K + K fields instead of N."""
-    K = max(1, int(checkpoint_every))
-    N = int(nsteps)
-    up = u0.detach().clone()
-    uc = solver.start(up)
-    ckpt = {}                                  # c -> (u^{c-1}, u^c)
-    c = 1
-    while True:
-        ckpt[c] = (up.clone(), uc.clone())
-        if c + K > N:
-            break
-        solver.step(up, uc, K)
-        c += K
-    mu1, mu2 = solver.empty().zero_(), solver.empty().zero_()   # mu^{n+1}, mu^{n+2}
-    for c in sorted(ckpt, reverse=True):
-        a, bb = ckpt[c][0].clone(), ckpt[c][1].clone()
-        states = [bb.clone()]                  # u^c .. u^{min(c+K-1, N)}
-        for _ in range(min(c + K - 1, N) - c):
-            solver.step(a, bb, 1)
-            states.append(bb.clone())
-        for j in range(len(states) - 1, -1, -1):
-            n = c + j
-            g = grad_fn(n, states[j])
-            mu0 = solver.update(mu1, mu2, 2.0, -1.0, 1.0, transpose=True, add=g)
-            mu1, mu2 = mu0, mu1
-        del states
-    g0 = grad_fn(0, u0.detach())
-    return solver.update(mu1, mu2, 1.0, -1.0, 0.5, transpose=True, add=g0)
+
+class _DeviceView:
+    """A float64 device buffer of the library, seen by torch without a copy."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+def history_gradient(solver, u0, nsteps: int, grad_fn, checkpoint_every: int = 40, stream=None):
+    """dJ/du^0 for J = sum_{n=0}^{nsteps} phi_n(u^n) over the forward run from
+    u0 (zero initial velocity), given grad_fn(n, u_n) -> dphi_n/du^n (a tensor
+    of u0's shape, or None where phi_n is absent).
+
+    Runs mol_adjoint_history (Solver) or mol_batch_adjoint_history
+    (BatchSolver, packed fields): the forward pass keeps (u^{c-1}, u^c) every
+    K = checkpoint_every steps on the device, the backward pass recomputes one
+    segment of at most K states at a time and runs the adjoint recursion
+    mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n through it.  grad_fn is
+    called for n = nsteps .. 0; u_n is the library's buffer (do not write it)."""
+    import torch
+    lib = load_library()
+    if not isinstance(u0, torch.Tensor) or u0.dtype != torch.float64 or not u0.is_cuda or not u0.is_contiguous():
+        raise TypeError("u0 must be a contiguous CUDA float64 tensor")
+    shape = tuple(u0.shape)
+    errors = []
+
+    def cb(n, u_ptr, g_ptr, _stream, _user):
+        try:
+            u = torch.as_tensor(_DeviceView(u_ptr, shape), device=u0.device)
+            g = grad_fn(int(n), u)
+            if g is None:
+                return 1
+            torch.as_tensor(_DeviceView(g_ptr, shape), device=u0.device).copy_(g.reshape(shape))
+            return 0
+        except Exception as e:                     # reported after the call returns
+            errors.append(e)
+            return 2
+
+    c_cb = GRAD_FN(cb)
+    grad = torch.empty_like(u0)
+    sp = ctypes.c_void_p(_stream_ptr(stream))
+    if isinstance(solver, BatchSolver):
+        st = lib.mol_batch_adjoint_history(solver.h, ctypes.c_void_p(u0.data_ptr()), int(nsteps),
+                                           int(checkpoint_every), c_cb, None, ctypes.c_void_p(grad.data_ptr()), sp)
+    else:
+        st = lib.mol_adjoint_history(solver.h, ctypes.c_void_p(u0.data_ptr()), int(nsteps), int(checkpoint_every),
+                                     c_cb, None, ctypes.c_void_p(grad.data_ptr()), sp)
+    if errors:
+        raise errors[0]
+    solver._check(st)
+    return grad

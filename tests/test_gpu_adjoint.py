@@ -431,3 +431,80 @@ def test_single_handle_adjoint_matches_oracle(shape):
     t = molt.receiver_traces(u, s, rec, nsteps)
     (0.5 * (t ** 2).sum()).backward()
     assert torch.equal(u.grad, s.adjoint(rec, t.detach()))
+
+
+# ---------------------------------------------------------------------------
+# history gradient through mol_adjoint_history on single-problem handles
+# ---------------------------------------------------------------------------
+def test_single_handle_history_gradient_matches_oracle():
+    """float64 handle (its adjoint runs on a one-problem batch): J = sum_n
+    sum_i w_i (u^n_i)^4 / 4 against the oracle's forward states and F^T."""
+    shape, P, nsteps = (96, 128), 2, 7
+    dt = 2.0 / (max(shape) - 1)
+    s = molt.Solver(shape, dt=dt, P=P, bc="dirichlet", prec="fp64")
+    nu, beta = s.nu, s.beta
+    rng = np.random.default_rng(51)
+    u0 = rng.normal(size=shape)
+    u0[0, :] = u0[-1, :] = 0
+    u0[:, 0] = u0[:, -1] = 0
+    w = rng.uniform(0.5, 1.5, size=shape)
+    wd = torch.from_numpy(w).cuda()
+    got = molt.history_gradient(s, torch.from_numpy(u0).cuda(), nsteps, lambda n, u: wd * u ** 3,
+                                checkpoint_every=3).cpu().numpy()
+    states = [u0, oracle.start(u0, nu, P, beta, "dirichlet")]
+    for _ in range(nsteps - 1):
+        states.append(oracle.step(states[-2], states[-1], nu, P, beta, "dirichlet"))
+    g = [w * st ** 3 for st in states]
+    m1, m2 = np.zeros(shape), np.zeros(shape)
+    for n in range(nsteps, 0, -1):
+        m1, m2 = 2 * m1 - m2 + oracle.FT(m1, nu, P, beta, "dirichlet") + g[n], m1
+    ref = m1 + 0.5 * oracle.FT(m1, nu, P, beta, "dirichlet") - m2 + g[0]
+    assert rel_l2(got, ref) <= 1e-12
+    s.close()
+
+
+def test_single_path_history_gradient_equals_trace_adjoint():
+    """Mixed handle on the register kernels' transposed modes: with
+    g^n = R^T (trace residual) the checkpointed driver reproduces mol_adjoint
+    (to float32 rounding of the injection) and is bitwise the same for every
+    checkpoint interval."""
+    shape, P, nsteps = (128, 1024), 2, 10
+    s = molt.Solver(shape, dt=2.0 / 1023, P=P, bc="dirichlet", prec="mixed")
+    rng = np.random.default_rng(52)
+    u0 = rng.normal(size=shape)
+    u0[0, :] = u0[-1, :] = 0
+    u0[:, 0] = u0[:, -1] = 0
+    u0 = torch.from_numpy(u0).cuda()
+    rec = rng.choice(shape[0] * shape[1], size=9, replace=False)
+    d = torch.from_numpy(rng.normal(size=(nsteps, rec.size))).cuda()
+    res = s.traces(u0, rec, nsteps) - d
+    ref = s.adjoint(rec, res)
+    rec_t = torch.from_numpy(rec).cuda()
+
+    def g(n, u):
+        if n == 0:
+            return None
+        out = torch.zeros(u.numel(), dtype=torch.float64, device="cuda")
+        out.index_put_((rec_t,), res[n - 1], accumulate=True)
+        return out.view(shape)
+
+    outs = [molt.history_gradient(s, u0, nsteps, g, checkpoint_every=K) for K in (1, 4, nsteps)]
+    for o in outs:
+        assert float(torch.linalg.norm(o - ref) / torch.linalg.norm(ref)) <= 1e-6
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
+    s.close()
+
+
+def test_history_gradient_callback_errors_surface():
+    shape = (64, 64)
+    s = molt.Solver(shape, dt=2.0 / 63, P=1, bc="dirichlet", prec="fp64")
+    u0 = torch.zeros(shape, dtype=torch.float64, device="cuda")
+
+    def bad(n, u):
+        raise ValueError("boom")
+
+    with pytest.raises(ValueError, match="boom"):
+        molt.history_gradient(s, u0, 3, bad, checkpoint_every=2)
+    # the handle keeps working
+    assert torch.isfinite(s.apply_F(u0)).all()
+    s.close()
