@@ -46,7 +46,8 @@ PEAKS_FILE = ROOT / "MEASURED_PEAKS.json"
 TRAFFIC_FILE = ROOT / "profiles" / "ncu_traffic.json"
 CSRC = ROOT / "paper_1308_3214_gb300" / "csrc"
 KERNEL_SOURCES = {
-    "single": [CSRC / f for f in ("molt_kernels.cuh", "molt_regs.cuh", "molt_passes.cu", "molt_regs.cu", "molt_api.cu")],
+    "single": [CSRC / f for f in ("molt_kernels.cuh", "molt_regs.cuh", "molt_strided_nb.cuh", "molt_tma.cuh",
+                                  "molt_passes.cu", "molt_regs.cu", "molt_api.cu")],
     "batch": [CSRC / f for f in ("molt_kernels.cuh", "molt_regs.cuh", "molt_batch.cuh", "molt_batch.cu")],
     "embed": [CSRC / "molt_embed.cu"],
 }
@@ -94,17 +95,32 @@ def workload_spec(name: str) -> dict:
 
 
 def bytes_per_point(spec: dict, prec: str) -> dict:
-    """Algorithmic HBM bytes per point and step of each pass: every field read
-    or written once per pass, levels as 8-byte pairs/doubles (2D: the y pass
-    reads u and writes the P fields D_y^k u, the x pass reads them, u and
-    u^{n-1} and writes u^{n+1})."""
+    """Algorithmic HBM bytes per point and step of each pass, the per-unit
+    figures of the path's plan (one pass per axis, every field read or written
+    once per pass, levels as 8-byte pairs / doubles, staged fields in the
+    sweep precision): 2D y pass: u in, the P + 1 stage combinations out
+    (8 + t (P + 1)); 2D x pass: those in, u, u^{n-1} in, u^{n+1} out
+    (t (P + 1) + 24); 3D: z 8 + t P, y t P + 8 + t (P + 1), x t (P + 1) + 24.
+    The roofline's `achieved` uses these."""
     P, nd = spec["P"], len(spec["shape"])
     t = 4 if prec == "mixed" else 8
     if nd == 1:
         return {0: 24}
     if nd == 2:
-        return {1: 8 + t * P, 0: t * P + 24}
+        return {1: 8 + t * (P + 1), 0: t * (P + 1) + 24}
     return {2: 8 + t * P, 1: t * P + 8 + t * (P + 1), 0: t * (P + 1) + 24}
+
+
+def bytes_per_point_design(spec: dict, prec: str) -> dict:
+    """The bytes these kernels move: in 2D the y pass writes the P powers
+    D_y^k u (not P + 1 combinations) and the x pass reads them and takes the
+    u term from the pair level it reads anyway (y 8 + t P, x t P + 24);
+    otherwise as bytes_per_point."""
+    P, nd = spec["P"], len(spec["shape"])
+    t = 4 if prec == "mixed" else 8
+    if nd == 2:
+        return {1: 8 + t * P, 0: t * P + 24}
+    return bytes_per_point(spec, prec)
 
 
 def kernel_sha(family: str = "single") -> str:
@@ -352,8 +368,13 @@ def run_reference(args, spec):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": spec["name"], "sampled_shape": list(shape)},
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+            "data": "synthetic",
+            "config": {"workload": spec["name"], "shape": list(spec["shape"]), "P": P, "cfl": spec["cfl"], "bc": bc,
+                       "beta": beta, "prec": "fp64", "levels": "f64",
+                       "l2": "host run (the oracle on the CPU cores; no GPU cache)",
+                       "parallelism": f"{cores} OpenMP threads over lines", "tuning": None},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample,
+                             "sampled_shape": list(shape)},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -372,6 +393,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="2D default: leave out the batched sub-measurement")
     ap.add_argument("--batch-count", type=int, default=512, help="problems of the batch workload (profiling)")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch variants instead of the autotuner (profiling): res_warps,strided_rpt,"
@@ -472,6 +494,7 @@ def main():
 
     # roofline of the dominant pass
     bpp = bytes_per_point(spec, args.prec)
+    bpd = bytes_per_point_design(spec, args.prec)
     dom_axis = max(passes, key=lambda a: passes[a][0])
     dom_ms = passes[dom_axis][0] / passes[dom_axis][1]
     alg_bytes = bpp[dom_axis] * N
@@ -492,7 +515,13 @@ def main():
                 "alg_bytes_per_launch": alg_bytes,
                 "passes": {f"axis{a}": {"ms_per_launch": passes[a][0] / passes[a][1],
                                          "alg_GBps": bpp[a] * N / (passes[a][0] / passes[a][1] * 1e-3) / 1e9,
-                                         "alg_bytes_per_point": bpp[a]} for a in passes},
+                                         "frac": bpp[a] * N / (passes[a][0] / passes[a][1] * 1e-3) / 1e9 / peak,
+                                         "alg_bytes_per_point": bpp[a],
+                                         "moved_bytes_per_point": bpd[a],
+                                         "moved_frac": bpd[a] * N / (passes[a][0] / passes[a][1] * 1e-3) / 1e9 / peak}
+                           for a in passes},
+                "bytes_note": ("achieved counts the plan's per-point bytes (2D: P + 1 staged fields); "
+                               "moved_* count what these kernels move (2D: P fields)"),
                 "step_alg_GBps": sum(bpp.values()) * N * args.steps / (ms * 1e-3) / 1e9,
                 "kernel_timing": (f"per-pass CUDA events over a second region of min(steps, 100) steps, "
                                   f"enqueued behind a spin kernel so that they run back to back "
@@ -526,7 +555,7 @@ def main():
         line["accuracy"] = accuracy_check_1d(spec, make, torch, dt)
 
     if not args.no_e2e:
-        calls, per_call = 3, max(1, min(spec["steps_in_config"], args.steps))
+        calls, per_call = 2, spec["steps_in_config"]          # the configuration's whole run per call
         pin_in = torch.empty(shape, dtype=torch.float64, pin_memory=True)
         pin_out = torch.empty(shape, dtype=torch.float64, pin_memory=True)
         pin_in.numpy()[...] = u0_host
@@ -543,6 +572,9 @@ def main():
                        "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
                        "step": f"one mol_solve_host call: copy u0 in, start + {per_call - 1} steps, copy u out",
                        "time_steps_per_step": per_call}
+
+    if len(shape) == 2 and args.prec == "mixed" and not args.no_batch:
+        line["batch"] = batch_summary(args, group)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, sshape, ssteps, sdt, cores = cpu_oracle_rate(spec, budget_s=20.0)
@@ -597,6 +629,68 @@ def batch_oracle_rate(probs, dts, budget_s: float, steps: int = 2):
     return pts / t_all, used, steps, t_all, oracle.num_threads()
 
 
+def batch_summary(args, group):
+    """The 512-problem batched workload measured inside the default run: the
+    mixed path through mol_batch_step (CUDA-graph loop), per-pass roofline
+    fractions against the measured HBM peak (plan bytes 8 + 4 (P_i + 1) for
+    the y pass and 4 (P_i + 1) + 24 for the x pass per point, and the bytes
+    the batch kernels move), and the float64 path on the same batch."""
+    import torch
+    from paper_1308_3214_gb300 import molt
+    spec = workload_spec("batch")
+    probs, shapes, dts, Ps = batch_set(spec, group.rank)
+    npts = sum(n * n for n, _ in shapes)
+    plan = {1: sum(n * n * (8 + 4 * (P + 1)) for (n, _), P in zip(shapes, Ps)),
+            0: sum(n * n * (4 * (P + 1) + 24) for (n, _), P in zip(shapes, Ps))}
+    moved = {1: sum(n * n * (8 + 4 * P) for (n, _), P in zip(shapes, Ps)),
+             0: sum(n * n * (4 * P + 24) for (n, _), P in zip(shapes, Ps))}
+    steps = max(10, min(args.steps, 40))
+    peak, _ = read_peak()
+
+    def run(prec, k):
+        b = molt.BatchSolver(shapes, dt=dts, P=Ps, prec=prec)
+        tun = b.autotune()
+        u0 = b.pack([p.u0 for p in probs])
+        up = u0.clone()
+        uc = b.start(up)
+        b.step(up, uc, 3)
+        torch.cuda.synchronize()
+        group.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(up, uc, k)
+        e1.record()
+        torch.cuda.synchronize()
+        group.barrier()
+        ms = e0.elapsed_time(e1)
+        b.set_pass_timing(True)
+        hold_stream()
+        b.step(up, uc, k)
+        torch.cuda.synchronize()
+        passes = b.pass_times()
+        b.set_pass_timing(False)
+        out = uc.clone()
+        b.close()
+        return ms, passes, tun, out
+
+    ms, passes, tun, u_mixed = run("mixed", steps)
+    out = {"workload": spec["name"], "problems": len(shapes), "points_per_step": npts, "steps": steps,
+           "value": aggregate_rate(group, npts * steps, ms * 1e-3), "unit": METRIC,
+           "ms_per_step": group.max(ms) / steps, "tuning": tun, "passes": {}}
+    for a in passes:
+        t = passes[a][0] / passes[a][1] * 1e-3
+        out["passes"][f"axis{a}"] = {
+            "ms_per_launch": t * 1e3, "frac": plan[a] / t / 1e9 / peak, "alg_bytes": plan[a],
+            "moved_frac": moved[a] / t / 1e9 / peak, "moved_bytes": moved[a],
+            "traffic": read_traffic(a, spec["name"], "mixed", "batch")}
+    if group.rank == 0 and not args.no_fp64_compare:
+        k64 = max(3, steps // 4)
+        ms64, p64, _, _ = run("fp64", k64)
+        out["fp64_path"] = {"value": npts * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
+                            "passes_ms_per_launch": {f"axis{a}": p64[a][0] / p64[a][1] for a in p64}}
+    return out
+
+
 def main_batch(args, spec):
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -634,8 +728,12 @@ def main_batch(args, spec):
     probs, shapes, dts, Ps = batch_set(spec, rank)
     npts = sum(n * n for n, _ in shapes)
     t = 4 if args.prec == "mixed" else 8
-    bpp_tot = {1: sum(n * n * (8 + t * P) for (n, _), P in zip(shapes, Ps)),
-               0: sum(n * n * (t * P + 24) for (n, _), P in zip(shapes, Ps))}
+    # plan bytes (P + 1 staged fields per problem; `achieved`) and the bytes
+    # the batch kernels move (P powers)
+    bpp_tot = {1: sum(n * n * (8 + t * (P + 1)) for (n, _), P in zip(shapes, Ps)),
+               0: sum(n * n * (t * (P + 1) + 24) for (n, _), P in zip(shapes, Ps))}
+    moved_tot = {1: sum(n * n * (8 + t * P) for (n, _), P in zip(shapes, Ps)),
+                 0: sum(n * n * (t * P + 24) for (n, _), P in zip(shapes, Ps))}
 
     def make(prec, **kw):
         return molt.BatchSolver(shapes, dt=dts, P=Ps, prec=prec, **kw)
@@ -700,7 +798,9 @@ def main_batch(args, spec):
                 "alg_bytes_per_launch": bpp_tot[dom_axis],
                 "passes": {f"axis{a}": {"ms_per_launch": passes[a][0] / passes[a][1],
                                          "alg_GBps": bpp_tot[a] / (passes[a][0] / passes[a][1] * 1e-3) / 1e9,
-                                         "alg_bytes": bpp_tot[a]} for a in passes},
+                                         "alg_bytes": bpp_tot[a], "moved_bytes": moved_tot[a],
+                                         "moved_frac": moved_tot[a] / (passes[a][0] / passes[a][1] * 1e-3) / 1e9
+                                         / peak} for a in passes},
                 "step_alg_GBps": sum(bpp_tot.values()) * args.steps / (ms * 1e-3) / 1e9,
                 "kernel_timing": (f"per-pass CUDA events over a second region of {args.steps} steps "
                                   f"(graphs off, {ms_b / args.steps:.4f} ms/step)")}
