@@ -25,6 +25,54 @@ __global__ void k_from_f32(const float *__restrict__ f, double *__restrict__ x, 
         x[i] = (double)f[i];
 }
 
+// float64 <-> float32 conversions by integer operations on the IEEE-754
+// encodings (round to nearest, ties to even, as the standard defines it):
+// GB300 runs float64 conversions on its narrow float64 pipe, so the pair
+// conversions below keep one float64 add per point.  Infinities, NaNs and
+// float32 subnormal inputs of the widening take the hardware conversion.
+__device__ __forceinline__ float d2f_rn_bits(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned s = (unsigned)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned long long m = b & 0xfffffffffffffull;
+    if (e == 0x7ff) return __double2float_rn(v);
+    const int fe = e - 896;                                  // float32 biased exponent of the value
+    unsigned long long q, rem, half;
+    if (fe >= 1) {
+        if (fe >= 255) return __uint_as_float(s | 0x7f800000u);
+        q = ((unsigned long long)fe << 23) | (m >> 29);      // exponent and 23 mantissa bits; a carry
+        rem = m & ((1ull << 29) - 1);                        // from rounding moves into the exponent
+        half = 1ull << 28;
+    } else {
+        if (e == 0) return __uint_as_float(s);               // float64 zero or subnormal -> +-0
+        const int sh = 30 - fe;                              // subnormal result in units of 2^-149
+        if (sh > 63) return __uint_as_float(s);
+        const unsigned long long M = m | (1ull << 52);
+        q = M >> sh;
+        rem = M & ((1ull << sh) - 1);
+        half = 1ull << (sh - 1);
+    }
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    return __uint_as_float(s | (unsigned)q);
+}
+
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    const unsigned long long s = (unsigned long long)(b >> 31) << 63;
+    if (e == 0) return m == 0 ? __longlong_as_double((long long)s) : (double)f;
+    if (e == 0xffu) return (double)f;
+    return __longlong_as_double((long long)(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29)));
+}
+
+__device__ __forceinline__ void split_pair(double v, float &h, float &l)
+{
+    h = d2f_rn_bits(v);
+    l = d2f_rn_bits(v - f2d_bits(h));
+}
+
 // The same conversions four points per thread (two 16-byte float64 loads or
 // stores, one 16-byte float32 store or load per plane), for 16-byte aligned
 // fields; the last N % 4 points by the scalar form.
@@ -35,23 +83,19 @@ __global__ void k_to_pair4(const double *__restrict__ x, float *__restrict__ hi,
         const double2 a = reinterpret_cast<const double2 *>(x)[2 * i];
         const double2 b = reinterpret_cast<const double2 *>(x)[2 * i + 1];
         float4 h, l;
-        h.x = __double2float_rn(a.x);
-        h.y = __double2float_rn(a.y);
-        h.z = __double2float_rn(b.x);
-        h.w = __double2float_rn(b.y);
-        l.x = __double2float_rn(a.x - (double)h.x);
-        l.y = __double2float_rn(a.y - (double)h.y);
-        l.z = __double2float_rn(b.x - (double)h.z);
-        l.w = __double2float_rn(b.y - (double)h.w);
+        split_pair(a.x, h.x, l.x);
+        split_pair(a.y, h.y, l.y);
+        split_pair(b.x, h.z, l.z);
+        split_pair(b.y, h.w, l.w);
         reinterpret_cast<float4 *>(hi)[i] = h;
         reinterpret_cast<float4 *>(lo)[i] = l;
     }
     const int64_t t = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < N) {
-        const double v = x[t];
-        const float h = __double2float_rn(v);
+        float h, l;
+        split_pair(x[t], h, l);
         hi[t] = h;
-        lo[t] = __double2float_rn(v - (double)h);
+        lo[t] = l;
     }
 }
 
@@ -61,11 +105,13 @@ __global__ void k_from_pair4(const float *__restrict__ hi, const float *__restri
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
         const float4 h = reinterpret_cast<const float4 *>(hi)[i];
         const float4 l = reinterpret_cast<const float4 *>(lo)[i];
-        reinterpret_cast<double2 *>(x)[2 * i] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
-        reinterpret_cast<double2 *>(x)[2 * i + 1] = make_double2((double)h.z + (double)l.z, (double)h.w + (double)l.w);
+        reinterpret_cast<double2 *>(x)[2 * i] =
+            make_double2(f2d_bits(h.x) + f2d_bits(l.x), f2d_bits(h.y) + f2d_bits(l.y));
+        reinterpret_cast<double2 *>(x)[2 * i + 1] =
+            make_double2(f2d_bits(h.z) + f2d_bits(l.z), f2d_bits(h.w) + f2d_bits(l.w));
     }
     const int64_t t = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < N) x[t] = (double)hi[t] + (double)lo[t];
+    if (t < N) x[t] = f2d_bits(hi[t]) + f2d_bits(lo[t]);
 }
 
 static int elementwise_grid(int64_t N)
