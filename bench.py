@@ -85,6 +85,9 @@ def workload_spec(name: str) -> dict:
     if name == "embedded":
         n = 2048
         return dict(name="embedded-ellipse-2048x2048-P2-cfl1-gaussian", n=n, P=2, cfl=1.0, bc="dirichlet")
+    if name == "toeplitz":
+        n = 2048
+        return dict(name="toeplitz-experiment-2048x2048-chunk32-d0.5395", shape=(n, n), d=math.exp(-1.234290745253055 / 2))
     if name == "1d":
         n = 256
         L = 2 * math.pi
@@ -386,7 +389,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batch", "adjoint", "source", "dirichlet1d",
-                                                        "embedded"])
+                                                        "embedded", "toeplitz"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -417,6 +420,9 @@ def main():
         return
     if args.workload == "embedded":
         main_embedded(args, spec)
+        return
+    if args.workload == "toeplitz":
+        main_toeplitz(args, spec)
         return
     if args.impl == "reference":
         run_reference(args, spec)
@@ -689,6 +695,34 @@ def batch_summary(args, group):
         out["fp64_path"] = {"value": npts * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
                             "passes_ms_per_launch": {f"axis{a}": p64[a][0] / p64[a][1] for a in p64}}
     return out
+
+
+def main_toeplitz(args, spec):
+    """The chunk-local causal recurrence of a strided sweep at the 2D
+    workload's size and decay (d = e^(-beta_max(3)/2)): the in-register scan
+    against the 32 x 32 Toeplitz product on the tensor cores.  Not the
+    solver's step: a measurement of a design alternative."""
+    from paper_1308_3214_gb300 import molt
+    if args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "a kernel design experiment: no reference arm"}))
+        return
+    n = spec["shape"][0]
+    t_scan, t_tc, diff = molt.toeplitz_experiment(n, n, spec["d"], reps=max(args.steps, 10))
+    peak, _ = read_peak()
+    bytes_ = 8 * n * n
+    flops_tc = 3 * 2 * (24 * 16 * 8 * 8) * (n // 32) * (n // 32)   # issued MMA work: 72 m16n8k8 per tile
+    line = {"metric": "chunk recurrences/s", "value": n * n / (t_scan * 1e-3), "unit": "points/s", "n_gpus": 1,
+            "steps": max(args.steps, 10), "warmup": 3, "ms_per_step": t_scan, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded uniform)",
+            "config": {"workload": spec["name"], "shape": [n, n], "d": spec["d"], "chunk": 32},
+            "scan": {"ms_per_launch": t_scan, "GBps": bytes_ / (t_scan * 1e-3) / 1e9,
+                     "frac_hbm": bytes_ / (t_scan * 1e-3) / 1e9 / peak},
+            "tensor_core_toeplitz": {"ms_per_launch": t_tc, "GBps": bytes_ / (t_tc * 1e-3) / 1e9,
+                                     "frac_hbm": bytes_ / (t_tc * 1e-3) / 1e9 / peak,
+                                     "mma_tflops_issued": flops_tc / (t_tc * 1e-3) / 1e12,
+                                     "max_rel_diff_vs_scan": diff},
+            "gpu_launches": 2 * (max(args.steps, 10) + 3)}
+    print(json.dumps(line), flush=True)
 
 
 def main_batch(args, spec):

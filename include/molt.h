@@ -332,6 +332,22 @@ mol_status mol_wait_selftest(int64_t limit_cycles, void *stream);
 void mol_debug_fail_alloc(int64_t after);
 void mol_debug_allow_unstable(int on);
 
+/*
+ * Measurement of a design alternative (the paper has no counterpart): the
+ * chunk-local causal recurrence of a strided sweep, y_i = d y_{i-1} + q_i on
+ * 32-point chunks with zero inflow (Sec. 2), over an nrows x ncols float32
+ * field (multiples of 32; chunks along the rows, seeded uniform q), computed
+ * [0] by the in-register scan of the pass kernels and [1] as the product with
+ * the 32 x 32 lower-triangular Toeplitz matrix d^(i-j) on the tensor cores
+ * (mma.sync m16n8k8 TF32, operands split into head and tail: three products).
+ * ms_per_launch[v] = mean CUDA-event time of `reps` launches of variant v
+ * after three warm-ups; *max_rel_diff = max |y_1 - y_0| / max |y_1|.
+ * Allocates and frees its own buffers; synchronous.  MOL_EINVAL for sizes
+ * that are not multiples of 32, d outside (0, 1) or reps < 1.
+ */
+mol_status mol_toeplitz_experiment(int nrows, int ncols, double d, int reps, double ms_per_launch[2],
+                                   double *max_rel_diff, void *stream);
+
 /* Synchronize the stream and report device-side failures: MOL_ECUDA for a
  * CUDA error, MOL_ETIMEOUT when a bounded wait inside a kernel (the strided
  * pass's tile-copy barrier, MOL_TUNE_STRIDED_STAGE 1 or 3) gave up since the

@@ -19,7 +19,8 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libmolt.so"
-SOURCES = ["molt_passes.cu", "molt_regs.cu", "molt_api.cu", "molt_host.cu", "molt_batch.cu", "molt_embed.cu"]
+SOURCES = ["molt_passes.cu", "molt_regs.cu", "molt_api.cu", "molt_host.cu", "molt_batch.cu", "molt_embed.cu",
+           "molt_toeplitz.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -39,7 +39,8 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_embed_start", "mol_embed_step", "mol_embed_solve_host", "mol_embed_sync", "mol_embed_launch_count",
            "mol_embed_set_pass_timing", "mol_embed_pass_times", "mol_field_norm", "mol_step_checked",
            "mol_checkpoint_write", "mol_checkpoint_read", "mol_wait_selftest", "mol_debug_fail_alloc",
-           "mol_debug_allow_unstable", "mol_adjoint_history", "mol_batch_adjoint_history"]
+           "mol_debug_allow_unstable", "mol_adjoint_history", "mol_batch_adjoint_history",
+           "mol_toeplitz_experiment"]
 
 
 class MolError(RuntimeError):
@@ -159,6 +160,7 @@ def load_library(path: Path | None = None):
     lib.mol_debug_allow_unstable.argtypes = [I]
     lib.mol_debug_allow_unstable.restype = None
     lib.mol_adjoint_history.argtypes = [vp, vp, i64, i64, GRAD_FN, vp, vp, vp]
+    lib.mol_toeplitz_experiment.argtypes = [I, I, D, I, dp, dp, vp]
     lib.mol_batch_adjoint_history.argtypes = [vp, vp, i64, i64, GRAD_FN, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("mol_default_options", "mol_last_error", "mol_beta_max", "mol_max_line",
@@ -859,3 +861,15 @@ def history_gradient(solver, u0, nsteps: int, grad_fn, checkpoint_every: int = 4
         raise errors[0]
     solver._check(st)
     return grad
+
+
+def toeplitz_experiment(nrows: int = 2048, ncols: int = 2048, d: float = 0.5395, reps: int = 50, stream=None):
+    """mol_toeplitz_experiment: (scan ms, tensor-core ms, max relative difference)."""
+    lib = load_library()
+    ms = (ctypes.c_double * 2)()
+    diff = ctypes.c_double()
+    st = lib.mol_toeplitz_experiment(int(nrows), int(ncols), float(d), int(reps), ms, ctypes.byref(diff),
+                                     ctypes.c_void_p(_stream_ptr(stream)))
+    if st != MOL_OK:
+        raise MolError(st, lib.mol_last_error(None).decode())
+    return ms[0], ms[1], diff.value

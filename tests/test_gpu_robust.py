@@ -145,3 +145,17 @@ def test_checkpoint_round_trip_and_refusals(tmp_path):
     with mk(P=3) as other:                                   # another problem
         with pytest.raises(molt.MolError, match="another problem"):
             other.checkpoint_read(path, torch.zeros_like(up), torch.zeros_like(uc))
+
+
+@pytest.mark.parametrize("d", [0.05, 0.5395, 0.9])
+def test_toeplitz_experiment_variants_agree(d):
+    """The tensor-core Toeplitz product and the scan give the same chunk
+    recurrence (three TF32 products keep float32 accuracy)."""
+    t_scan, t_tc, diff = molt.toeplitz_experiment(256, 512, d, reps=3)
+    assert t_scan > 0 and t_tc > 0
+    assert diff <= 2e-6, diff
+
+
+def test_toeplitz_experiment_rejects_bad_sizes():
+    assert lib().mol_toeplitz_experiment(100, 64, 0.5, 1, (ctypes.c_double * 2)(), ctypes.byref(ctypes.c_double()),
+                                         None) == molt.MOL_EINVAL
