@@ -193,7 +193,12 @@ mol_status mol_get_tuning(mol_handle h, int out[4], double *ms_per_step);
  *     loads on an mbarrier; 2 (default) each output power staged in shared
  *     memory and written by TMA tensor stores; 3 both.  Grids whose 32-line
  *     groups would straddle an outer slice (inner extent not a multiple of 32)
- *     take 0.
+ *     take 0;
+ *   MOL_TUNE_ROWS_NB: 1 (default) = the row-split x pass with two warps per
+ *     row exchanges once per sweep between neighbouring segments where the
+ *     dropped inflows are below 1/8 of a float32 unit in the last place
+ *     (d^(RPT-1) <= 2^-27); 0 = the full carries (scans over the warp and a
+ *     combine over the warps, three barriers per sweep).
  * mol_set_tuning_ex takes count >= 4 values (indices past count keep their
  * setting); mol_get_tuning_ex fills count values.  MOL_EINVAL on a value out
  * of range, a count out of range or a choice that does not fit the grid. */
@@ -205,7 +210,8 @@ enum {
     MOL_TUNE_ROWS_PERSIST = 4,
     MOL_TUNE_STRIDED_NB = 5,
     MOL_TUNE_STRIDED_STAGE = 6,
-    MOL_TUNE_COUNT = 7
+    MOL_TUNE_ROWS_NB = 7,
+    MOL_TUNE_COUNT = 8
 };
 mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count);
 mol_status mol_get_tuning_ex(mol_handle h, int *vals, int count, double *ms_per_step);

@@ -62,6 +62,8 @@ struct mol_ctx {
     int tune_res_warps = 2, tune_strided_rpt = 0, tune_strided_warps = 8;
     int tune_rows_warps = 0;                   // > 0: the x pass splits each row over this many warps
     int tune_rows_persist = 0;                 // row-split x pass: persistent CTAs with next-row L2 prefetch
+    int tune_rows_nb = 1;                      // row-split x pass: one neighbour exchange per sweep where
+                                               // exact to rounding (two warps per row)
     int tune_strided_nb = 1;                   // float32 strided powers: one neighbour exchange per sweep
                                                // where that is exact to rounding
     int tune_strided_stage = 2;                // ... its tiles: 0 direct, 1 TMA loads, 2 TMA stores, 3 both
@@ -274,6 +276,7 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
             if (W == 0) return fail(h, MOL_EINVAL, "no register plan for the transposed x pass");
             LineSet L = lineset_of(h, 0);
             L.persist_sms = h->tune_rows_persist ? h->num_sms : 0;
+            L.rows_nb = 0;                                      // the transposed pass keeps the full carries
             e = launch_rows(h->bc, rpt, pr.ng, W, regs_axis(h, 0, rpt), L, pr, s);
         } else {
             if (!regs_strided_plan(h->tbytes, h->bc, n, &rpt, &S, &K, h->tune_strided_rpt, h->tune_strided_warps))
@@ -287,6 +290,7 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
         regs_rows_plan(h->tbytes, n, pr.ng, h->tune_rows_warps, &rpt)) {
         LineSet L = lineset_of(h, 0);
         L.persist_sms = h->tune_rows_persist ? h->num_sms : 0;
+        L.rows_nb = h->tune_rows_nb;
         e = launch_rows(h->bc, rpt, pr.ng, h->tune_rows_warps, regs_axis(h, 0, rpt), L, pr, s);
     } else if (axis == 0 && pr.mode == 1 && pr.nout == 1 && regs_res_plan(h->tbytes, n, pr.ng, &rpt)) {
         e = launch_res(h->bc, rpt, pr.ng, h->tune_res_warps, regs_axis(h, 0, rpt), lineset_of(h, 0), pr, s);
@@ -968,6 +972,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
             if (regs_rows_plan(h->tbytes, (int)h->n[0], h->xtpl.ng, W, &dummy)) {
                 warps_c.push_back(-W);
                 warps_c.push_back(-100 - W);
+                if (rows_nb_plan(h->ax[0].d, (int)h->n[0], dummy, W)) warps_c.push_back(-200 - W);
             }
     }
     // strided variants: segment length code, segments per CTA at most, and
@@ -1003,7 +1008,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
     const int64_t launches0 = h->launches;
     double best = 1e30;
     int bw = h->tune_res_warps, br = h->tune_strided_rpt, bsw = h->tune_strided_warps, brw = h->tune_rows_warps;
-    int bpe = h->tune_rows_persist, bnb = h->tune_strided_nb, bst = h->tune_strided_stage;
+    int bpe = h->tune_rows_persist, bnb = h->tune_strided_nb, bst = h->tune_strided_stage, brn = h->tune_rows_nb;
     mol_status st = MOL_OK;
     for (int w : warps_c) {
         for (auto &sc : str_c) {
@@ -1014,7 +1019,8 @@ mol_status mol_autotune(mol_handle h, void *stream)
             if (!ok) continue;
             h->tune_res_warps = w > 0 ? w : h->tune_res_warps;
             h->tune_rows_warps = w < 0 ? (-w) % 100 : 0;
-            h->tune_rows_persist = w < -100 ? 1 : 0;
+            h->tune_rows_persist = (w < -100 && w > -200) ? 1 : 0;
+            h->tune_rows_nb = w < -200 ? 1 : 0;
             h->tune_strided_rpt = sc.first % 100;
             h->tune_strided_nb = (sc.first / 100) % 10;
             h->tune_strided_stage = sc.first / 1000;
@@ -1042,6 +1048,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
                 bw = h->tune_res_warps;
                 brw = h->tune_rows_warps;
                 bpe = h->tune_rows_persist;
+                brn = h->tune_rows_nb;
                 bnb = h->tune_strided_nb;
                 bst = h->tune_strided_stage;
                 br = sc.first % 100;
@@ -1057,6 +1064,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
     h->tune_res_warps = bw;
     h->tune_rows_warps = brw;
     h->tune_rows_persist = bpe;
+    h->tune_rows_nb = brn;
     h->tune_strided_nb = bnb;
     h->tune_strided_stage = bst;
     h->tune_strided_rpt = br;
@@ -1112,12 +1120,15 @@ mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count)
         return fail(h, MOL_EINVAL, "strided_nb must be 0 or 1");
     if (count > MOL_TUNE_STRIDED_STAGE && (vals[MOL_TUNE_STRIDED_STAGE] < 0 || vals[MOL_TUNE_STRIDED_STAGE] > 3))
         return fail(h, MOL_EINVAL, "strided_stage must be 0, 1, 2 or 3");
+    if (count > MOL_TUNE_ROWS_NB && vals[MOL_TUNE_ROWS_NB] != 0 && vals[MOL_TUNE_ROWS_NB] != 1)
+        return fail(h, MOL_EINVAL, "rows_nb must be 0 or 1");
     mol_status st = mol_set_tuning(h, vals[MOL_TUNE_RES_WARPS], vals[MOL_TUNE_STRIDED_RPT],
                                    vals[MOL_TUNE_STRIDED_WARPS], vals[MOL_TUNE_ROWS_WARPS]);
     if (st != MOL_OK) return st;
     if (count > MOL_TUNE_ROWS_PERSIST) h->tune_rows_persist = vals[MOL_TUNE_ROWS_PERSIST];
     if (count > MOL_TUNE_STRIDED_NB) h->tune_strided_nb = vals[MOL_TUNE_STRIDED_NB];
     if (count > MOL_TUNE_STRIDED_STAGE) h->tune_strided_stage = vals[MOL_TUNE_STRIDED_STAGE];
+    if (count > MOL_TUNE_ROWS_NB) h->tune_rows_nb = vals[MOL_TUNE_ROWS_NB];
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     return MOL_OK;
 }
@@ -1129,7 +1140,7 @@ mol_status mol_get_tuning_ex(mol_handle h, int *vals, int count, double *ms_per_
         return fail(h, MOL_EINVAL, "count must be in 1.." + std::to_string(MOL_TUNE_COUNT));
     const int all[MOL_TUNE_COUNT] = {h->tune_res_warps, h->tune_strided_rpt, h->tune_strided_warps,
                                      h->tune_rows_warps, h->tune_rows_persist, h->tune_strided_nb,
-                                     h->tune_strided_stage};
+                                     h->tune_strided_stage, h->tune_rows_nb};
     for (int i = 0; i < count; ++i) vals[i] = all[i];
     if (ms_per_step) *ms_per_step = h->tune_ms;
     return MOL_OK;

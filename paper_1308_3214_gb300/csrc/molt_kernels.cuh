@@ -174,6 +174,7 @@ struct LineSet {
     int64_t nlines;
     int S, K;         // strided: segments per CTA (warps) and CTAs per line
     int persist_sms;  // row-split x pass: > 0 runs persistent CTAs on this many SMs
+    int rows_nb;      // row-split x pass: 1 = one neighbour exchange per sweep where exact to rounding
 };
 
 // ---------------------------------------------------------------------------

@@ -53,17 +53,26 @@ template <int BC, int RPT, int NB, int W>
 cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
 {
     const size_t smem = rows_smem<RPT, NB, W>();
+    const NbConsts nc = strided_nb_consts(A.d, RPT);
     if constexpr (BC == BC_DIRICHLET) {
         if (p.mode == 3) {                            // the transposed Horner pass
             static int occ_adj = 0;
             const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W, true>, W, smem, L, occ_adj);
-            k_contig_rows<BC, RPT, NB, W, true><<<g, 32 * W, smem, s>>>(A, L, p);
+            k_contig_rows<BC, RPT, NB, W, true><<<g, 32 * W, smem, s>>>(A, L, p, nc);
+            return cudaGetLastError();
+        }
+    }
+    if constexpr (W == 2) {
+        if (L.rows_nb && rows_nb_plan(A.d, A.n, RPT, W)) {   // one neighbour exchange per sweep
+            static int occ_nb = 0;
+            const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W, false, true>, W, smem, L, occ_nb);
+            k_contig_rows<BC, RPT, NB, W, false, true><<<g, 32 * W, smem, s>>>(A, L, p, nc);
             return cudaGetLastError();
         }
     }
     static int occ = 0;
     const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W>, W, smem, L, occ);
-    k_contig_rows<BC, RPT, NB, W><<<g, 32 * W, smem, s>>>(A, L, p);
+    k_contig_rows<BC, RPT, NB, W><<<g, 32 * W, smem, s>>>(A, L, p, nc);
     return cudaGetLastError();
 }
 
@@ -83,6 +92,14 @@ cudaError_t attr_rows()
                                      (int)rows_smem<RPT, NB, W>());
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W, true>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    }
+    if constexpr (W == 2) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W, false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem<RPT, NB, W>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W, false, true>,
                                      cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     }
     return e;
@@ -272,6 +289,11 @@ bool regs_strided_plan(int tbytes, int, int n, int *rpt, int *S, int *K, int pre
     *S = (G + k - 1) / k;
     *K = k;
     return true;
+}
+
+bool rows_nb_plan(double d, int n, int rpt, int W)
+{
+    return W == 2 && n == 32 * W * rpt && rpt >= 16 && strided_nb_exact(d, n, rpt, 27);
 }
 
 bool regs_strided_nb_plan(double d, int n, int rpt)

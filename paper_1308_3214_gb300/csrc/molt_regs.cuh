@@ -976,6 +976,43 @@ __global__ void __launch_bounds__(128) k_contig_res(AxisDev A, LineSet LS, ProgP
 // ---------------------------------------------------------------------------
 // contiguous axis, float32 Horner pass, one row per CTA of W warps
 // ---------------------------------------------------------------------------
+// one neighbour exchange per sweep (molt_strided_nb.cuh explains the algebra)
+// ---------------------------------------------------------------------------
+// Constants of the neighbour exchange, float32 copies of float64 values:
+// G = d sum_{j<RPT} d^2j, G1 = d^2 sum_{j<RPT-1} d^2j, GH = d sum_{j<H} d^2j,
+// dH = d^H, dH1 = d^(H-1) with H = RPT/2.
+struct NbConsts {
+    float G, G1, GH, dH, dH1;
+};
+
+// True when the neighbour exchange is exact to well below float32 rounding
+// for a line of n points with segments of rpt points and decay d.
+inline bool strided_nb_exact(double d, int n, int rpt, int log2_limit = 30)
+{
+    if (rpt < 4 || n % rpt != 0 || n / rpt < 2) return false;
+    return std::pow(d, (double)(rpt - 1)) <= std::ldexp(1.0, -log2_limit);
+}
+
+inline NbConsts strided_nb_consts(double d, int rpt)
+{
+    const int H = rpt / 2;
+    double g = 0.0, g1 = 0.0, gh = 0.0, p = 1.0;
+    for (int j = 0; j < rpt; ++j) {
+        if (j < rpt - 1) g1 += p;
+        if (j < H) gh += p;
+        g += p;
+        p *= d * d;
+    }
+    NbConsts c;
+    c.G = (float)(d * g);
+    c.G1 = (float)(d * d * g1);
+    c.GH = (float)(d * gh);
+    c.dH = (float)std::pow(d, (double)H);
+    c.dH1 = (float)std::pow(d, (double)(H - 1));
+    return c;
+}
+
+// ---------------------------------------------------------------------------
 // A row of n = 32 W RPT points is split over the W warps of a CTA: warp w holds
 // points [32 w RPT, 32 (w+1) RPT), lane = segment of RPT points.  Each warp
 // runs the single-warp sweep on its part; halos and the causal and anti-causal
@@ -990,6 +1027,8 @@ struct RowSlots {
     T tc[W];         // per warp: zero-inflow causal total (y at its last point)
     T ta[W];         // per warp: zero-inflow anti-causal total (e at its first point)
     T yl;            // y_{n-1} of the row with zero inflow
+    T nb[2][W][4];   // neighbour exchange: per warp its last lane's E, y0(RPT-2) and its
+                     // first lane's ER0, ER1 (two sets, alternating by sweep)
 };
 
 // Neighbours of the thread's segment: z at a-2, a-1 (left) and a+RPT,
@@ -1136,6 +1175,92 @@ __device__ __forceinline__ void row_sweep(T (&z)[RPT], const T (&r)[RPT], T rl, 
     row_solve<T, BC, RPT, W, RAG>(z, A, lane, warp, sl);
 }
 
+// One application of D (MODE 2: s = the second difference of z plus cu r) on
+// a row split over W warps with ONE neighbour exchange: the algebra of
+// k_strided_nb (molt_strided_nb.cuh) with the neighbours at lane -+ 1 by
+// shuffles and across warps through the slots, one CTA barrier.  For rows
+// with d^(RPT-1) <= 2^-27 (the dropped inflows below 1/8 of a float32 unit in
+// the last place).  hl2, hl1, hr0, hr1: z at a-2, a-1, a+RPT, a+RPT+1 on
+// entry; e there on exit (the caller adds the next Horner term to both).
+template <int BC, int RPT, int W>
+__device__ __forceinline__ void row_sweep_nb(float (&z)[RPT], const float (&r)[RPT], float rl, float rr, float cu,
+                                             const AxisDev &A, const NbConsts &nc, int lane, int warp,
+                                             RowSlots<float, W> &sl, int buf, float &hl2, float &hl1, float &hr0,
+                                             float &hr1)
+{
+    constexpr int H = RPT / 2;
+    constexpr int NSEG = 32 * W;
+    const int seg = warp * 32 + lane;
+    const bool left_end = BC == BC_DIRICHLET && seg == 0, right_end = BC == BC_DIRICHLET && seg == NSEG - 1;
+    const float d = A.fd, c1 = A.fc1, c2 = A.fc2, inv = A.finv;
+    float zl2 = hl2, zl1 = hl1, zr0 = hr0, zr1 = hr1;
+    if (BC == BC_DIRICHLET) end_ghosts<float, RPT, 2>(z, left_end, right_end, zl2, zl1, zr0, zr1);
+    seg_make_q<float, RPT, 2>(z, zl2, zl1, zr0, zr1, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : r[k]); }, cu,
+                              c1, c2);
+    if (BC == BC_DIRICHLET) end_zero<float, RPT>(z, left_end, right_end);
+
+    // both halves of the causal recurrence with zero inflow
+    float ya = z[0], yb = z[H], ra1 = 0.f, rb = yb, pw = 1.f;
+#pragma unroll
+    for (int k = 1; k < H; ++k) {
+        ya = d * ya + z[k];
+        yb = d * yb + z[H + k];
+        z[k] = ya;
+        z[H + k] = yb;
+        const float pbk = pw * d;
+        ra1 += pw * ya;
+        rb += pbk * yb;
+        pw = pbk;
+    }
+    const float E1 = ya;
+    const float E = yb + E1 * nc.dH;
+    const float Y2 = z[RPT - 2] + E1 * nc.dH1;
+    const float ER1 = ra1 + nc.dH1 * (rb + E1 * nc.GH);
+    const float ER0 = z[0] + d * ER1;
+
+    // the exchange: lane -+ 1 by shuffles, the neighbouring warps' end lanes
+    // through the slots
+    __syncwarp();
+    float EL = __shfl_up_sync(0xffffffffu, E, 1), Y2L = __shfl_up_sync(0xffffffffu, Y2, 1);
+    float ER0R = __shfl_down_sync(0xffffffffu, ER0, 1), ER1R = __shfl_down_sync(0xffffffffu, ER1, 1);
+    if (lane == 31) { sl.nb[buf][warp][0] = E; sl.nb[buf][warp][1] = Y2; }
+    if (lane == 0) { sl.nb[buf][warp][2] = ER0; sl.nb[buf][warp][3] = ER1; }
+    __syncthreads();
+    if (lane == 0) {
+        const int wl = warp > 0 ? warp - 1 : W - 1;
+        EL = sl.nb[buf][wl][0];
+        Y2L = sl.nb[buf][wl][1];
+    }
+    if (lane == 31) {
+        const int wr = warp < W - 1 ? warp + 1 : 0;
+        ER0R = sl.nb[buf][wr][2];
+        ER1R = sl.nb[buf][wr][3];
+    }
+    const bool hasL = !left_end, hasR = !right_end;
+    if (!hasL) { EL = 0.f; Y2L = 0.f; }
+    if (!hasR) { ER0R = 0.f; ER1R = 0.f; }
+
+    const float cB = E1 + EL * nc.dH;
+    float pk = d;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        z[k] += EL * pk;
+        z[H + k] += cB * pk;
+        pk *= d;
+    }
+    const float ER2 = rb + cB * nc.GH;
+    const float eout = hasR ? ER0R + nc.G * E : 0.f;
+    const float er1 = hasR ? ER1R + nc.G1 * E : 0.f;
+    float acc = d * eout;
+    if (right_end) acc -= z[RPT - 1] * inv;
+    seg_bwd_scan2<float, RPT>(z, d, nc.dH, acc, ER2);
+    if (left_end) seg_add_left2<float, RPT>(z, d, nc.dH, -z[0] * inv);
+    hl1 = hasL ? EL + d * z[0] : 0.f;
+    hl2 = hasL ? Y2L + d * hl1 : 0.f;
+    hr0 = eout;
+    hr1 = er1;
+}
+
 // D^T (z + cu u) on a Dirichlet row split over W warps (the transposed
 // difference form of post_T; any n with 32 (W-1) RPT < n <= 32 W RPT)
 template <class T, int RPT, int W>
@@ -1171,8 +1296,9 @@ __host__ __device__ constexpr size_t row_slots_bytes() { return (sizeof(RowSlots
 // Four warps per row: seven CTAs per SM (72 registers, 31 KB of shared
 // memory each at RPT = 16 and three fields), so that the 2048 rows of a
 // 2048^2 grid run in two waves over the 152 SMs instead of two and a quarter.
-template <int BC, int RPT, int NB, int W, bool ADJ = false>
-__global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr)
+template <int BC, int RPT, int NB, int W, bool ADJ = false, bool NBX = false>
+__global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr,
+                                                                                       NbConsts nc)
 {
     static_assert(RPT % 4 == 0 && RPT >= 8, "segment length");
     static_assert(!ADJ || BC == BC_DIRICHLET, "the transposed pass is for Dirichlet rows");
@@ -1286,6 +1412,22 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_conti
     T z[RPT];
 #pragma unroll
     for (int k = 0; k < RPT; ++k) z[k] = 0;
+    // NBX: z's halos ride along (the sweeps form e's, each Horner term adds
+    // the fields' values there); positions a-2, a-1, a+RPT, a+RPT+1
+    float hz[4] = {0.f, 0.f, 0.f, 0.f};
+    int hpos[4] = {0, 0, 0, 0};
+    bool hin[4] = {false, false, false, false};
+    if constexpr (NBX) {
+        const int a = t * RPT;
+        const int g[4] = {a - 2, a - 1, a + RPT, a + RPT + 1};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int gi = g[i];
+            if (BC == BC_PERIODIC) gi = gi < 0 ? gi + n : (gi >= n ? gi - n : gi);
+            hin[i] = gi >= 0 && gi < n;
+            hpos[i] = hin[i] ? St::pos(gi) : 0;
+        }
+    }
     for (int tt = pr.P; tt >= 0; --tt) {
         for (int k = 0; k < ng; ++k) {
             const T c = prog_coef<T>(pr, (size_t)tt * ng + k);
@@ -1299,9 +1441,16 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_conti
                 z[4 * q + 2] += c * y.z;
                 z[4 * q + 3] += c * y.w;
             }
+            if constexpr (NBX) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) hz[i] += hin[i] ? c * B[k * LINE + hpos[i]] : 0.f;
+            }
         }
         if (tt == 0) break;
         if constexpr (ADJ) row_sweep_T<T, RPT, W>(z, r, prog_cu<T>(pr, tt), A, lane, warp, sl);
+        else if constexpr (NBX)
+            row_sweep_nb<BC, RPT, W>(z, r, rl, rr, prog_cu<T>(pr, tt), A, nc, lane, warp, sl, tt & 1, hz[0], hz[1],
+                                     hz[2], hz[3]);
         else row_sweep<T, BC, RPT, W>(z, r, rl, rr, prog_cu<T>(pr, tt), A, lane, warp, sl);
     }
 

@@ -35,40 +35,6 @@
 
 namespace molt {
 
-// Constants of the neighbour exchange, float32 copies of float64 values:
-// G = d sum_{j<RPT} d^2j, G1 = d^2 sum_{j<RPT-1} d^2j, GH = d sum_{j<H} d^2j,
-// dH = d^H, dH1 = d^(H-1) with H = RPT/2.
-struct NbConsts {
-    float G, G1, GH, dH, dH1;
-};
-
-// True when the neighbour exchange is exact to well below float32 rounding
-// for a line of n points with segments of rpt points and decay d.
-inline bool strided_nb_exact(double d, int n, int rpt)
-{
-    if (rpt < 4 || n % rpt != 0 || n / rpt < 2) return false;
-    return std::pow(d, (double)(rpt - 1)) <= std::ldexp(1.0, -30);
-}
-
-inline NbConsts strided_nb_consts(double d, int rpt)
-{
-    const int H = rpt / 2;
-    double g = 0.0, g1 = 0.0, gh = 0.0, p = 1.0;
-    for (int j = 0; j < rpt; ++j) {
-        if (j < rpt - 1) g1 += p;
-        if (j < H) gh += p;
-        g += p;
-        p *= d * d;
-    }
-    NbConsts c;
-    c.G = (float)(d * g);
-    c.G1 = (float)(d * d * g1);
-    c.GH = (float)(d * gh);
-    c.dH = (float)std::pow(d, (double)H);
-    c.dH1 = (float)std::pow(d, (double)(H - 1));
-    return c;
-}
-
 // Shared memory of one CTA: the exchange slots [2][S][4][32], then (STAGE
 // != 0) the tile barrier and the tile: the pair level's rows a0-2 .. a0+S RPT+1
 // of the CTA's 32 lines (STAGE & 1; nbox boxes of box_rows rows for hi and for

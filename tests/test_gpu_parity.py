@@ -499,3 +499,36 @@ def test_strided_tma_staging_matches_oracle(shape, bc, stage, rpt, warps):
         assert rel_l2(got, ref) <= tol_for("mixed", s, p), (p, rel_l2(got, ref))
     s.sync()
     s.close()
+
+
+@pytest.mark.parametrize("shape", [(40, 2048), (24, 1024)])
+@pytest.mark.parametrize("cfl", [0.5, 2.0, 3.0])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("P", [1, 3])
+@pytest.mark.parametrize("rows_nb", [1, 0])
+def test_rows_neighbour_exchange_matches_oracle(shape, cfl, bc, P, rows_nb):
+    """The x pass over two warps per row with one neighbour exchange per
+    sweep (where d^(RPT-1) <= 2^-27; the full carries otherwise): F and a few
+    steps against the oracle."""
+    nx = shape[1]
+    dt = cfl * spacing(nx, bc)
+    s = make(shape, dt, P, bc, "mixed")
+    s.set_tuning(res_warps=2, strided_rpt=0, strided_warps=8, rows_warps=2, rows_nb=rows_nb)
+    assert s.tuning()["rows_nb"] == rows_nb
+    u = field(shape, 90, bc)
+    ref = oracle.F(u, s.nu, P, s.beta, bc)
+    assert rel_l2(s.apply_F(dev(u)).cpu().numpy(), ref) <= tol_for("mixed", s, 2 * P)
+    u0 = smooth_field(shape, 91, bc) + 0.05 * field(shape, 92, bc)
+    u1 = oracle.start(u0, s.nu, P, s.beta, bc)
+    up, uc = dev(u0), dev(u1)
+    nsteps = 5
+    s.step(up, uc, nsteps)
+    rp, rc = oracle.run(u0, u1, nsteps, s.nu, P, s.beta, bc)
+    Fsum, a, b = 0.0, u0, u1
+    for _ in range(nsteps):
+        F = oracle.F(b, s.nu, P, s.beta, bc)
+        Fsum += np.linalg.norm(F)
+        a, b = b, 2 * b - a + F
+    tol = 8 * EPS32 * (1 + 1 / (1 - max(s.d))) * 2 * P * Fsum / np.linalg.norm(rc)
+    assert rel_l2(uc.cpu().numpy(), rc) <= tol
+    s.close()
