@@ -194,11 +194,12 @@ mol_status mol_get_tuning(mol_handle h, int out[4], double *ms_per_step);
  *     memory and written by TMA tensor stores; 3 both.  Grids whose 32-line
  *     groups would straddle an outer slice (inner extent not a multiple of 32)
  *     take 0;
- *   MOL_TUNE_ROWS_NB: 1 (default) = the row-split x pass with two warps per
- *     row exchanges once per sweep between neighbouring segments where the
- *     dropped inflows are below 1/8 of a float32 unit in the last place
- *     (d^(RPT-1) <= 2^-27); 0 = the full carries (scans over the warp and a
- *     combine over the warps, three barriers per sweep).
+ *   MOL_TUNE_ROWS_NB: 1 (default) = the row-split x pass exchanges once per
+ *     sweep between neighbouring segments where the dropped inflows are below
+ *     1/8 of a float32 unit in the last place: two warps per row with the two
+ *     neighbours (d^(RPT-1) <= 2^-27) or four warps per row with two on each
+ *     side (d^(2 RPT - 1) <= 2^-27); 0 = the full carries (scans over the
+ *     warp and a combine over the warps, three barriers per sweep).
  * mol_set_tuning_ex takes count >= 4 values (indices past count keep their
  * setting); mol_get_tuning_ex fills count values.  MOL_EINVAL on a value out
  * of range, a count out of range or a choice that does not fit the grid. */

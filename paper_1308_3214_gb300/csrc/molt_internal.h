@@ -80,8 +80,9 @@ cudaError_t configure_regs_kernels();
 // true when a line of n points with segments of rpt points and decay d is
 // computed by it exactly to well below float32 rounding (molt_strided_nb.cuh).
 bool regs_strided_nb_plan(double d, int n, int rpt);
-// The row-split x pass with one neighbour exchange per sweep (W = 2 warps per
-// row; dropped inflows d^(RPT-1) <= 2^-27, below 1/8 of a float32 ulp).
+// The row-split x pass with one neighbour exchange per sweep: W = 2 warps per
+// row with one hop (dropped inflows d^(RPT-1) <= 2^-27, below 1/8 of a float32
+// ulp) or W = 4 with two hops (d^(2 RPT - 1) <= 2^-27).
 bool rows_nb_plan(double d, int n, int rpt, int W);
 // stage: 0 direct loads and stores, 1 the pair level's tile through TMA into
 // shared memory, 2 each output power staged in shared memory and written by

@@ -1,5 +1,6 @@
 // molt_regs.cu -- instantiation and launch of the register-resident pass kernels.
 #include <algorithm>
+#include <cmath>
 #include "molt_internal.h"
 #include "molt_regs.cuh"
 #include "molt_strided_nb.cuh"
@@ -62,7 +63,7 @@ cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cu
             return cudaGetLastError();
         }
     }
-    if constexpr (W == 2) {
+    if constexpr (W == 2 || W == 4) {
         if (L.rows_nb && rows_nb_plan(A.d, A.n, RPT, W)) {   // one neighbour exchange per sweep
             static int occ_nb = 0;
             const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W, false, true>, W, smem, L, occ_nb);
@@ -94,7 +95,7 @@ cudaError_t attr_rows()
             e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W, true>,
                                      cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     }
-    if constexpr (W == 2) {
+    if constexpr (W == 2 || W == 4) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W, false, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem<RPT, NB, W>());
@@ -293,7 +294,10 @@ bool regs_strided_plan(int tbytes, int, int n, int *rpt, int *S, int *K, int pre
 
 bool rows_nb_plan(double d, int n, int rpt, int W)
 {
-    return W == 2 && n == 32 * W * rpt && rpt >= 16 && strided_nb_exact(d, n, rpt, 27);
+    if (n != 32 * W * rpt || rpt < 16) return false;
+    if (W == 2) return std::pow(d, (double)(rpt - 1)) <= std::ldexp(1.0, -27);          // one hop
+    if (W == 4) return std::pow(d, (double)(2 * rpt - 1)) <= std::ldexp(1.0, -27);      // two hops
+    return false;
 }
 
 bool regs_strided_nb_plan(double d, int n, int rpt)

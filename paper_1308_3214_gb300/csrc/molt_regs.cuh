@@ -983,6 +983,7 @@ __global__ void __launch_bounds__(128) k_contig_res(AxisDev A, LineSet LS, ProgP
 // dH = d^H, dH1 = d^(H-1) with H = RPT/2.
 struct NbConsts {
     float G, G1, GH, dH, dH1;
+    float dR, dR1, dR2, dRp1;   // d^RPT, d^(RPT-1), d^(RPT-2), d^(RPT+1) (two-hop exchange)
 };
 
 // True when the neighbour exchange is exact to well below float32 rounding
@@ -1009,6 +1010,10 @@ inline NbConsts strided_nb_consts(double d, int rpt)
     c.GH = (float)(d * gh);
     c.dH = (float)std::pow(d, (double)H);
     c.dH1 = (float)std::pow(d, (double)(H - 1));
+    c.dR = (float)std::pow(d, (double)rpt);
+    c.dR1 = (float)std::pow(d, (double)(rpt - 1));
+    c.dR2 = (float)std::pow(d, (double)(rpt - 2));
+    c.dRp1 = (float)std::pow(d, (double)(rpt + 1));
     return c;
 }
 
@@ -1027,8 +1032,9 @@ struct RowSlots {
     T tc[W];         // per warp: zero-inflow causal total (y at its last point)
     T ta[W];         // per warp: zero-inflow anti-causal total (e at its first point)
     T yl;            // y_{n-1} of the row with zero inflow
-    T nb[2][W][4];   // neighbour exchange: per warp its last lane's E, y0(RPT-2) and its
-                     // first lane's ER0, ER1 (two sets, alternating by sweep)
+    T nb[2][W][8];   // neighbour exchange, per warp (two sets, alternating by sweep): lane 31's
+                     // E, y0(RPT-2); lane 0's ER0, ER1; two hops also lane 30's E, lane 0's E,
+                     // lane 1's ER0
 };
 
 // Neighbours of the thread's segment: z at a-2, a-1 (left) and a+RPT,
@@ -1261,6 +1267,116 @@ __device__ __forceinline__ void row_sweep_nb(float (&z)[RPT], const float (&r)[R
     hr1 = er1;
 }
 
+// Two hops (segments of 16 points, where d^RPT is not yet negligible but
+// d^(2 RPT - 1) <= 2^-27): the inflows from l-1, l-2 and l+1, l+2, the
+// Dirichlet corrections reaching into the second segment from each end.
+// Same interface as row_sweep_nb.
+template <int BC, int RPT, int W>
+__device__ __forceinline__ void row_sweep_nb2(float (&z)[RPT], const float (&r)[RPT], float rl, float rr, float cu,
+                                              const AxisDev &A, const NbConsts &nc, int lane, int warp,
+                                              RowSlots<float, W> &sl, int buf, float &hl2, float &hl1, float &hr0,
+                                              float &hr1)
+{
+    constexpr int H = RPT / 2;
+    constexpr int NSEG = 32 * W;
+    constexpr bool DIR = BC == BC_DIRICHLET;
+    const int seg = warp * 32 + lane;
+    const bool left_end = DIR && seg == 0, right_end = DIR && seg == NSEG - 1;
+    const float d = A.fd, c1 = A.fc1, c2 = A.fc2, inv = A.finv;
+    float zl2 = hl2, zl1 = hl1, zr0 = hr0, zr1 = hr1;
+    if (DIR) end_ghosts<float, RPT, 2>(z, left_end, right_end, zl2, zl1, zr0, zr1);
+    seg_make_q<float, RPT, 2>(z, zl2, zl1, zr0, zr1, [&](int k) { return k < 0 ? rl : (k >= RPT ? rr : r[k]); }, cu,
+                              c1, c2);
+    if (DIR) end_zero<float, RPT>(z, left_end, right_end);
+
+    float ya = z[0], yb = z[H], ra1 = 0.f, rb = yb, pw = 1.f;
+#pragma unroll
+    for (int k = 1; k < H; ++k) {
+        ya = d * ya + z[k];
+        yb = d * yb + z[H + k];
+        z[k] = ya;
+        z[H + k] = yb;
+        const float pbk = pw * d;
+        ra1 += pw * ya;
+        rb += pbk * yb;
+        pw = pbk;
+    }
+    const float E1 = ya;
+    const float E = yb + E1 * nc.dH;
+    const float Y2 = z[RPT - 2] + E1 * nc.dH1;
+    const float ER1 = ra1 + nc.dH1 * (rb + E1 * nc.GH);
+    const float ER0 = z[0] + d * ER1;
+
+    __syncwarp();
+    constexpr unsigned F = 0xffffffffu;
+    float EL = __shfl_up_sync(F, E, 1), EL2 = __shfl_up_sync(F, E, 2), Y2L = __shfl_up_sync(F, Y2, 1);
+    const float ER0L = __shfl_up_sync(F, ER0, 1);
+    float ER = __shfl_down_sync(F, E, 1), ER0R = __shfl_down_sync(F, ER0, 1), ER1R = __shfl_down_sync(F, ER1, 1);
+    float ER0R2 = __shfl_down_sync(F, ER0, 2);
+    float *mine = sl.nb[buf][warp];
+    if (lane == 31) { mine[0] = E; mine[1] = Y2; }
+    if (lane == 30) mine[4] = E;
+    if (lane == 0) { mine[2] = ER0; mine[3] = ER1; mine[5] = E; }
+    if (lane == 1) mine[6] = ER0;
+    __syncthreads();
+    const float *prev = sl.nb[buf][warp > 0 ? warp - 1 : W - 1], *next = sl.nb[buf][warp < W - 1 ? warp + 1 : 0];
+    if (lane == 0) { EL = prev[0]; Y2L = prev[1]; EL2 = prev[4]; }
+    if (lane == 1) EL2 = prev[0];
+    if (lane == 31) { ER = next[5]; ER0R = next[2]; ER1R = next[3]; ER0R2 = next[6]; }
+    if (lane == 30) ER0R2 = next[2];
+    const bool hasL = !(DIR && seg < 1), hasL2 = !(DIR && seg < 2);
+    const bool hasR = !(DIR && seg > NSEG - 2), hasR2 = !(DIR && seg > NSEG - 3);
+    EL = hasL ? EL : 0.f;
+    Y2L = hasL ? Y2L : 0.f;
+    EL2 = hasL2 ? EL2 : 0.f;
+
+    const float yin = EL + nc.dR * EL2;                     // causal value at a-1
+    const float cB = E1 + yin * nc.dH;
+    float pk = d;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        z[k] += yin * pk;
+        z[H + k] += cB * pk;
+        pk *= d;
+    }
+    const float Cl = E + nc.dR * EL;                        // causal value at a+RPT-1
+    const float ER2n = hasR2 ? ER0R2 + nc.G * ER : 0.f;      // anti-causal sum of segment l+2
+    float eout = hasR ? ER0R + nc.G * Cl + nc.dR * ER2n : 0.f;
+    float er1 = hasR ? ER1R + nc.G1 * Cl + nc.dR1 * ER2n : 0.f;
+    float acc = d * eout;
+    if (DIR && seg == NSEG - 1) {
+        acc -= z[RPT - 1] * inv;                               // B' = -y_{n-1} / (1 - mu^2)
+    } else if (DIR && seg == NSEG - 2) {
+        const float Bc = -(ER + nc.dR * E) * inv;             // y_{n-1} from the last segment's E
+        acc += Bc * nc.dR;
+        eout += Bc * nc.dR1;
+        er1 += Bc * nc.dR2;
+    }
+    const float ER2 = rb + cB * nc.GH;
+    seg_bwd_scan2<float, RPT>(z, d, nc.dH, acc, ER2);
+    float Ac = 0.f;
+    if (DIR && seg == 0) {
+        Ac = -z[0] * inv;                                       // A' = -e_0 / (1 - mu^2)
+        seg_add_left2<float, RPT>(z, d, nc.dH, Ac);
+    } else if (DIR && seg == 1) {
+        Ac = -(ER0L + nc.dR * (ER0 + nc.G * EL)) * inv;        // e_0 from the first segment's sums
+        seg_add_left2<float, RPT>(z, d, nc.dH, Ac * nc.dR);
+    }
+    if (DIR && seg == 1) {
+        hl1 = yin + d * (z[0] - Ac * nc.dR) + Ac * nc.dR1;
+        hl2 = Y2L + d * (hl1 - Ac * nc.dR1) + Ac * nc.dR2;
+    } else {
+        hl1 = hasL ? yin + d * z[0] : 0.f;
+        hl2 = hasL ? Y2L + EL2 * nc.dR1 + d * hl1 : 0.f;
+    }
+    hr0 = eout;
+    hr1 = er1;
+    if (DIR && seg == 0) {
+        hr0 += Ac * nc.dR;
+        hr1 += Ac * nc.dRp1;
+    }
+}
+
 // D^T (z + cu u) on a Dirichlet row split over W warps (the transposed
 // difference form of post_T; any n with 32 (W-1) RPT < n <= 32 W RPT)
 template <class T, int RPT, int W>
@@ -1448,9 +1564,12 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_conti
         }
         if (tt == 0) break;
         if constexpr (ADJ) row_sweep_T<T, RPT, W>(z, r, prog_cu<T>(pr, tt), A, lane, warp, sl);
-        else if constexpr (NBX)
+        else if constexpr (NBX && W == 2)
             row_sweep_nb<BC, RPT, W>(z, r, rl, rr, prog_cu<T>(pr, tt), A, nc, lane, warp, sl, tt & 1, hz[0], hz[1],
                                      hz[2], hz[3]);
+        else if constexpr (NBX)
+            row_sweep_nb2<BC, RPT, W>(z, r, rl, rr, prog_cu<T>(pr, tt), A, nc, lane, warp, sl, tt & 1, hz[0], hz[1],
+                                      hz[2], hz[3]);
         else row_sweep<T, BC, RPT, W>(z, r, rl, rr, prog_cu<T>(pr, tt), A, lane, warp, sl);
     }
 

@@ -501,19 +501,20 @@ def test_strided_tma_staging_matches_oracle(shape, bc, stage, rpt, warps):
     s.close()
 
 
-@pytest.mark.parametrize("shape", [(40, 2048), (24, 1024)])
+@pytest.mark.parametrize("shape,W", [((40, 2048), 2), ((24, 1024), 2), ((40, 2048), 4), ((16, 4096), 4)])
 @pytest.mark.parametrize("cfl", [0.5, 2.0, 3.0])
 @pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
 @pytest.mark.parametrize("P", [1, 3])
 @pytest.mark.parametrize("rows_nb", [1, 0])
-def test_rows_neighbour_exchange_matches_oracle(shape, cfl, bc, P, rows_nb):
-    """The x pass over two warps per row with one neighbour exchange per
-    sweep (where d^(RPT-1) <= 2^-27; the full carries otherwise): F and a few
-    steps against the oracle."""
+def test_rows_neighbour_exchange_matches_oracle(shape, W, cfl, bc, P, rows_nb):
+    """The x pass over W warps per row with one neighbour exchange per sweep
+    (two warps: the neighbours, where d^(RPT-1) <= 2^-27; four warps: two on
+    each side, where d^(2 RPT - 1) <= 2^-27; the full carries otherwise): F
+    and a few steps against the oracle."""
     nx = shape[1]
     dt = cfl * spacing(nx, bc)
     s = make(shape, dt, P, bc, "mixed")
-    s.set_tuning(res_warps=2, strided_rpt=0, strided_warps=8, rows_warps=2, rows_nb=rows_nb)
+    s.set_tuning(res_warps=2, strided_rpt=0, strided_warps=8, rows_warps=W, rows_nb=rows_nb)
     assert s.tuning()["rows_nb"] == rows_nb
     u = field(shape, 90, bc)
     ref = oracle.F(u, s.nu, P, s.beta, bc)
