@@ -1277,7 +1277,9 @@ def main_adjoint(args, spec):
             "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": spec["name"], "shape": [n, n], "P": P, "cfl": spec["cfl"], "receivers": int(rec.size),
                        "prec": args.prec, "step": "one adjoint step: mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n",
-                       "l2": "no flush: per-step working set exceeds the 129 MB L2",
+                       "l2": "no flush, and the per-step working set (3 adjoint levels as f32 pairs + P power "
+                             "fields, about 40 MB at 1024^2) fits in the 129 MB L2: steps run back to back inside "
+                             "one mol_adjoint call, so HBM fractions of this line are not DRAM-bound figures",
                        "parallelism": f"{world} rank(s), each its own problem", "tuning": tuning},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
     # gradient check and mixed-vs-fp64 comparison of the full workload gradient
@@ -1321,6 +1323,33 @@ def main_adjoint(args, spec):
                        "step": f"one gradient: copy u0 in, {nsteps} forward steps with traces, loss, "
                                f"{nsteps} adjoint steps, copy the gradient out (counted as {nsteps} point-updates)",
                        "time_steps_per_step": nsteps}
+    if rank == 0 and not args.no_e2e:
+        # the same gradient through checkpoint-and-recompute (mol_adjoint_history,
+        # K = 40): the loss's g^n injected by a callback as a dense field
+        K = 40
+        rec_t = torch.from_numpy(rec).cuda()
+        res_all = res[:nsteps]
+
+        def gfun(step, u):
+            if step == 0:
+                return None
+            g = torch.zeros(pts, dtype=torch.float64, device="cuda")
+            g.index_put_((rec_t,), res_all[step - 1], accumulate=True)
+            return g.view(n, n)
+
+        hist = molt.history_gradient(b, u0, nsteps, gfun, checkpoint_every=K)      # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = molt.history_gradient(b, u0, nsteps, gfun, checkpoint_every=K)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        ref = b.adjoint(rec, res_all)
+        line["history"] = {"value": pts * nsteps / el, "unit": METRIC, "checkpoint_every": K, "steps": nsteps,
+                           "seconds": el, "fields_held": 2 * ((nsteps - 1) // K + 1) + min(K, nsteps) + 4,
+                           "rel_l2_vs_trace_adjoint": float(torch.linalg.norm(hist - ref) / torch.linalg.norm(ref)),
+                           "step": f"one gradient of the trace misfit through mol_adjoint_history: {nsteps} forward "
+                                   f"steps keeping (u^(c-1), u^c) every {K}, each segment recomputed on the device, "
+                                   f"{nsteps} adjoint steps with g^n from a host callback"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
