@@ -400,8 +400,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512, help="problems of the batch workload (profiling)")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch variants instead of the autotuner (profiling): res_warps,strided_rpt,"
-                         "strided_warps,rows_warps[,rows_persist] for a single problem; x_warps_short,x_warps_long,y_rule for "
-                         "the batch")
+                         "strided_warps,rows_warps[,rows_persist,strided_nb,strided_stage,rows_nb] for a single "
+                         "problem; x_warps_short,x_warps_long,y_rule for the batch")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -512,9 +512,15 @@ def main():
               "Horner + level update)")
     else:
         xk = "k_contig_res / k_contig (x: one row per warp; Horner + level update)"
-    kernel_name = {0: xk,
-                   1: "k_strided (y: powers of D_y)" if len(shape) == 2 else "k_strided (y: Horner, P+1 outputs)",
-                   2: "k_strided (z: powers of D_z)"}[dom_axis]
+    nbt = tuning.get("strided_nb", 0)
+    stg = {0: "direct loads and stores", 1: "TMA tile loads", 2: "TMA tensor stores",
+           3: "TMA loads and stores"}[tuning.get("strided_stage", 0)]
+    pk = (f"k_strided_nb ({{}}: powers of D_{{}}, one neighbour exchange per sweep, {stg})" if nbt
+          else "k_strided ({}: powers of D_{})")
+    yk = ("k_strided_nb_h (y: Horner, P+1 outputs, one neighbour exchange per sweep"
+          + (", fields staged in shared memory)" if nbt == 2 else ")") if nbt
+          else "k_strided (y: Horner, P+1 outputs)")
+    kernel_name = {0: xk, 1: pk.format("y", "y") if len(shape) == 2 else yk, 2: pk.format("z", "z")}[dom_axis]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": read_traffic(dom_axis, spec["name"], args.prec),
                 "kernel": kernel_name, "peak_kind": f"{peak_kind} hbm_gbs (copy)",

@@ -183,10 +183,14 @@ mol_status mol_get_tuning(mol_handle h, int out[4], double *ms_per_step);
  *     (as many as fit on the device) that walk the rows and prefetch the
  *     next row's fields into L2 while they work on the current one; 0 = one
  *     CTA per row;
- *   MOL_TUNE_STRIDED_NB: 1 (default) = the float32 strided powers pass
- *     exchanges once per sweep between neighbouring segments wherever the
- *     decay over one segment makes that exact to below 2^-30 (d^(RPT-1) <=
- *     2^-30); 0 = the full-carry pass (three exchanges per sweep) always;
+ *   MOL_TUNE_STRIDED_NB: 1 (default) = the float32 strided passes (powers,
+ *     and the Horner pass of 3D grids) exchange once per sweep between
+ *     neighbouring segments wherever the decay over one segment makes that
+ *     exact to below 2^-30 (d^(RPT-1) <= 2^-30); 2 = the same, and the
+ *     Horner pass stages the CTA's rows of its input fields in shared memory
+ *     once instead of reading them from global memory for every output and
+ *     power (where two CTAs per SM still fit; else as 1); 0 = the full-carry
+ *     passes (three exchanges per sweep) always;
  *   MOL_TUNE_STRIDED_STAGE: how that pass moves its tiles: 0 direct
  *     coalesced loads and stores from registers; 1 the pair level's tile (the
  *     CTA's rows plus halos, 32 lines) copied into shared memory by TMA tensor

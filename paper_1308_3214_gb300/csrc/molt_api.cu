@@ -64,8 +64,9 @@ struct mol_ctx {
     int tune_rows_persist = 0;                 // row-split x pass: persistent CTAs with next-row L2 prefetch
     int tune_rows_nb = 1;                      // row-split x pass: one neighbour exchange per sweep where
                                                // exact to rounding (two warps per row)
-    int tune_strided_nb = 1;                   // float32 strided powers: one neighbour exchange per sweep
-                                               // where that is exact to rounding
+    int tune_strided_nb = 1;                   // float32 strided passes: one neighbour exchange per sweep
+                                               // where that is exact to rounding (2: the Horner pass
+                                               // also stages its input fields in shared memory)
     int tune_strided_stage = 2;                // ... its tiles: 0 direct, 1 TMA loads, 2 TMA stores, 3 both
     double tune_ms = 0.0;                      // step time of the chosen configuration
     // 2D Dirichlet grids (n <= 1024 per axis) whose lines the register
@@ -304,6 +305,8 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
         const AxisDev A = regs_axis(h, axis, rpt);
         if (h->tbytes == 4 && pr.mode == 0 && h->tune_strided_nb && regs_strided_nb_plan(A.d, n, rpt))
             e = launch_strided_nb(h->bc, rpt, A, L, pr, s, h->tune_strided_stage);
+        else if (h->tbytes == 4 && pr.mode == 1 && h->tune_strided_nb && regs_strided_nb_plan(A.d, n, rpt))
+            e = launch_strided_nb_h(h->bc, rpt, A, L, pr, s, h->tune_strided_nb == 2);
         else
             e = launch_strided(h->tbytes, h->bc, rpt, A, L, pr, s);
     } else {
@@ -992,6 +995,8 @@ mol_status mol_autotune(mol_handle h, void *stream)
             }
             if (nb)
                 for (int stg = 0; stg < 4; ++stg) str_c.push_back({b.first + 100 + 1000 * stg, b.second});
+            if (nb && h->ndim == 3)               // the y Horner pass with its fields staged
+                for (int stg : {0, 2}) str_c.push_back({b.first + 200 + 1000 * stg, b.second});
             str_c.push_back(b);
         }
     }
@@ -1116,8 +1121,8 @@ mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count)
         return fail(h, MOL_EINVAL, "count must be in 4.." + std::to_string(MOL_TUNE_COUNT));
     if (count > MOL_TUNE_ROWS_PERSIST && vals[MOL_TUNE_ROWS_PERSIST] != 0 && vals[MOL_TUNE_ROWS_PERSIST] != 1)
         return fail(h, MOL_EINVAL, "rows_persist must be 0 or 1");
-    if (count > MOL_TUNE_STRIDED_NB && vals[MOL_TUNE_STRIDED_NB] != 0 && vals[MOL_TUNE_STRIDED_NB] != 1)
-        return fail(h, MOL_EINVAL, "strided_nb must be 0 or 1");
+    if (count > MOL_TUNE_STRIDED_NB && (vals[MOL_TUNE_STRIDED_NB] < 0 || vals[MOL_TUNE_STRIDED_NB] > 2))
+        return fail(h, MOL_EINVAL, "strided_nb must be 0, 1 or 2");
     if (count > MOL_TUNE_STRIDED_STAGE && (vals[MOL_TUNE_STRIDED_STAGE] < 0 || vals[MOL_TUNE_STRIDED_STAGE] > 3))
         return fail(h, MOL_EINVAL, "strided_stage must be 0, 1, 2 or 3");
     if (count > MOL_TUNE_ROWS_NB && vals[MOL_TUNE_ROWS_NB] != 0 && vals[MOL_TUNE_ROWS_NB] != 1)

@@ -89,6 +89,11 @@ bool rows_nb_plan(double d, int n, int rpt, int W);
 // TMA tensor stores, 3 both
 cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s,
                               int stage = 0);
+// The strided Horner pass (several outputs, float32) with one neighbour
+// exchange per sweep, under the same condition on d; gtile: the g fields'
+// rows staged in shared memory once per CTA (where two CTAs per SM still fit).
+cudaError_t launch_strided_nb_h(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                                cudaStream_t s, bool gtile);
 // 1 if a bounded wait of a register kernel gave up since the last call (and
 // clears it), 0 if not, -1 if the flag could not be read; synchronizes s.
 int regs_timeout_take(cudaStream_t s);

@@ -237,6 +237,51 @@ cudaError_t run_strided_nb(const AxisDev &A, const LineSet &L, const ProgParams 
     }
 }
 
+template <int BC, int RPT, bool GT>
+cudaError_t run_strided_nb_h(const AxisDev &A, const LineSet &L, const ProgParams &p, const TmaGMaps &tg, size_t smem,
+                             cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_strided_nb_h<BC, RPT, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1);
+    cfg.blockDim = dim3(32 * L.S, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr1[1];
+    attr1[0].id = cudaLaunchAttributeClusterDimension;
+    attr1[0].val.clusterDim.x = 1;
+    attr1[0].val.clusterDim.y = (unsigned)L.K;
+    attr1[0].val.clusterDim.z = 1;
+    cfg.attrs = attr1;
+    cfg.numAttrs = L.K > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_strided_nb_h<BC, RPT, GT>, A, L, p, strided_nb_consts(A.d, RPT), tg);
+}
+
+template <int BC, int RPT>
+cudaError_t run_strided_nb_h_any(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s, bool gt)
+{
+    TmaGMaps tg{};
+    if (gt) {
+        // the staged tiles only with a tensor map for every field and while
+        // two CTAs per SM still fit; else the fields are read from global
+        const int in_rows = L.S * RPT + 4;
+        tg.nbox = (in_rows + 255) / 256;
+        tg.box_rows = (in_rows + tg.nbox - 1) / tg.nbox;
+        const size_t smem = strided_nb_h_smem(L.S, RPT, p.ng, true, tg.nbox * tg.box_rows);
+        bool ok = p.ng >= 1 && p.ng <= kMaxTmaG && smem <= 110 * 1024;
+        for (int q = 0; q < p.ng && ok; ++q) ok = encode_field_map(&tg.g[q], p.g[q], L, A.n, tg.box_rows);
+        if (ok) return run_strided_nb_h<BC, RPT, true>(A, L, p, tg, smem, s);
+        tg = TmaGMaps{};
+    }
+    return run_strided_nb_h<BC, RPT, false>(A, L, p, tg, strided_nb_h_smem(L.S, RPT, p.ng, false), s);
+}
+
 template <class T, int BC, int RPT>
 cudaError_t attr_contig()
 {
@@ -314,6 +359,19 @@ cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &
                                  : run_strided_nb<BC_DIRICHLET, kStridedRptF>(A, L, p, s, stage);
     return bc == BC_PERIODIC ? run_strided_nb<BC_PERIODIC, kStridedRptF2>(A, L, p, s, stage)
                              : run_strided_nb<BC_DIRICHLET, kStridedRptF2>(A, L, p, s, stage);
+}
+
+cudaError_t launch_strided_nb_h(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
+                                cudaStream_t s, bool gtile)
+{
+    if (p.mode != 1 || p.ng < 0 || p.ng > MAXG || p.nout < 1 || p.nout > MAXG || p.P < 1 ||
+        !regs_strided_nb_plan(A.d, A.n, rpt))
+        return cudaErrorInvalidValue;
+    if (rpt == kStridedRptF)
+        return bc == BC_PERIODIC ? run_strided_nb_h_any<BC_PERIODIC, kStridedRptF>(A, L, p, s, gtile)
+                                 : run_strided_nb_h_any<BC_DIRICHLET, kStridedRptF>(A, L, p, s, gtile);
+    return bc == BC_PERIODIC ? run_strided_nb_h_any<BC_PERIODIC, kStridedRptF2>(A, L, p, s, gtile)
+                             : run_strided_nb_h_any<BC_DIRICHLET, kStridedRptF2>(A, L, p, s, gtile);
 }
 
 // One CTA waits on a barrier that is never completed (two arrivals expected,

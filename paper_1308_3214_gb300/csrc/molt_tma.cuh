@@ -102,4 +102,13 @@ struct TmaMaps {
     int nbox;       // boxes per tile
 };
 
+// Tensor maps of the input fields of a strided Horner pass (the same 3D view
+// and boxes), for its tiles staged in shared memory.
+constexpr int kMaxTmaG = 5;
+struct TmaGMaps {
+    CUtensorMap g[kMaxTmaG];
+    int box_rows;   // rows of one box
+    int nbox;       // boxes per field
+};
+
 }  // namespace molt

@@ -307,6 +307,11 @@ def test_full_size_2d_strided_powers(rpt, warps):
     s.close()
 
 
+TUNINGS_3D = [None, "auto", dict(res_warps=2, strided_rpt=32, strided_warps=8, rows_warps=0, strided_nb=2),
+              dict(res_warps=2, strided_rpt=0, strided_warps=4, rows_warps=0, strided_nb=1, strided_stage=0),
+              dict(res_warps=2, strided_rpt=0, strided_warps=8, rows_warps=0, strided_nb=0)]
+
+
 @pytest.mark.slow
 def test_full_size_3d_fourier_one_step():
     n, P, cfl = 256, 2, 1.5
@@ -320,8 +325,18 @@ def test_full_size_3d_fourier_one_step():
     assert rel_l2(got, ref) <= 1e-12, rel_l2(got, ref)
     s64.close()
     smx = molt.Solver((n, n, n), dt=dt, P=P, bc="periodic", prec="mixed", **box)
-    got = smx.apply_F(dev(u0)).cpu().numpy()
-    assert rel_l2(got, ref) <= tol_for("mixed", smx, 2 * P), rel_l2(got, ref)
+    ud = dev(u0)
+    for tuning in TUNINGS_3D:
+        # every launch configuration the 3D benchmark may time: the default,
+        # the tuner's pick, the neighbour-exchange y Horner pass with and
+        # without its fields staged in shared memory, the full-carry passes
+        if tuning == "auto":
+            smx.autotune()
+        elif tuning is not None:
+            smx.set_tuning(**tuning)
+        got = smx.apply_F(ud).cpu().numpy()
+        assert rel_l2(got, ref) <= tol_for("mixed", smx, 2 * P), (tuning, rel_l2(got, ref))
+    smx.close()
 
 
 # ---------------------------------------------------------------------------
@@ -498,6 +513,52 @@ def test_strided_tma_staging_matches_oracle(shape, bc, stage, rpt, warps):
         ref = oracle.D_axis(v, axis, s.nu[axis], bc, 2, power=p)
         assert rel_l2(got, ref) <= tol_for("mixed", s, p), (p, rel_l2(got, ref))
     s.sync()
+    s.close()
+
+
+# The 3D y pass (Horner in D_y with P+1 outputs) with one neighbour exchange
+# per sweep, its fields read from global memory (strided_nb 1) or staged in
+# shared memory (2), against the oracle's F and steps; decays on either side
+# of the exchange's limit (where it does not hold the full-carry pass runs),
+# lines in one CTA and over a 2-CTA cluster, x extents that are not a multiple
+# of the 32-line group.
+@pytest.mark.parametrize("shape", [(64, 128, 64), (40, 256, 32), (96, 64, 48)])
+@pytest.mark.parametrize("cfl", [0.5, 3.0])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("P", [1, 3])
+@pytest.mark.parametrize("rpt,warps", [(0, 8), (32, 8), (32, 4)])
+def test_strided_horner_neighbour_exchange_matches_oracle(shape, cfl, bc, P, rpt, warps):
+    s = make(shape, cfl * spacing(shape[1], bc), P, bc, "mixed")
+    u = field(shape, 90, bc)
+    ud = dev(u)
+    ref = oracle.F(u, s.nu, P, s.beta, bc)
+    for nb in (2, 1, 0):
+        s.set_tuning(res_warps=2, strided_rpt=rpt, strided_warps=warps, rows_warps=0, strided_nb=nb)
+        assert s.tuning()["strided_nb"] == nb
+        got = s.apply_F(ud).cpu().numpy()
+        assert rel_l2(got, ref) <= tol_for("mixed", s, 2 * P), (nb, rel_l2(got, ref))
+    s.sync()
+    s.close()
+
+
+def test_strided_horner_neighbour_exchange_steps():
+    """Six steps of a 3D Dirichlet problem with the staged neighbour-exchange
+    y pass follow the oracle's time stepping."""
+    shape, P, bc, nsteps = (64, 128, 64), 2, "dirichlet", 6
+    s = make(shape, 1.0 * spacing(shape[1], bc), P, bc, "mixed")
+    s.set_tuning(res_warps=2, strided_rpt=32, strided_warps=8, rows_warps=0, strided_nb=2)
+    u0 = smooth_field(shape, 91, bc) + 0.05 * field(shape, 92, bc)
+    u1 = oracle.start(u0, s.nu, P, s.beta, bc)
+    up, uc = dev(u0), dev(u1)
+    s.step(up, uc, nsteps)
+    rp, rc = oracle.run(u0, u1, nsteps, s.nu, P, s.beta, bc)
+    Fsum, a, b = 0.0, u0, u1
+    for _ in range(nsteps):
+        F = oracle.F(b, s.nu, P, s.beta, bc)
+        Fsum += np.linalg.norm(F)
+        a, b = b, 2 * b - a + F
+    tol = 8 * EPS32 * (1 + 1 / (1 - max(s.d))) * 2 * P * Fsum / np.linalg.norm(rc)
+    assert rel_l2(uc.cpu().numpy(), rc) <= tol
     s.close()
 
 
