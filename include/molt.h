@@ -203,7 +203,13 @@ mol_status mol_get_tuning(mol_handle h, int out[4], double *ms_per_step);
  *     1/8 of a float32 unit in the last place: two warps per row with the two
  *     neighbours (d^(RPT-1) <= 2^-27) or four warps per row with two on each
  *     side (d^(2 RPT - 1) <= 2^-27); 0 = the full carries (scans over the
- *     warp and a combine over the warps, three barriers per sweep).
+ *     warp and a combine over the warps, three barriers per sweep);
+ *   MOL_TUNE_PDL: 1 = the register-resident pass kernels are launched as
+ *     programmatic dependents of the kernel before them in the stream (their
+ *     CTAs are scheduled while it finishes and wait for its completion before
+ *     touching memory); 0 (default) = ordinary stream order.  Bitwise the
+ *     same results; measured 2 % (2D) to 4 % (3D) slower per step, the
+ *     waiting CTAs holding SM slots through the previous pass's last wave.
  * mol_set_tuning_ex takes count >= 4 values (indices past count keep their
  * setting); mol_get_tuning_ex fills count values.  MOL_EINVAL on a value out
  * of range, a count out of range or a choice that does not fit the grid. */
@@ -216,7 +222,8 @@ enum {
     MOL_TUNE_STRIDED_NB = 5,
     MOL_TUNE_STRIDED_STAGE = 6,
     MOL_TUNE_ROWS_NB = 7,
-    MOL_TUNE_COUNT = 8
+    MOL_TUNE_PDL = 8,
+    MOL_TUNE_COUNT = 9
 };
 mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count);
 mol_status mol_get_tuning_ex(mol_handle h, int *vals, int count, double *ms_per_step);

@@ -68,6 +68,8 @@ struct mol_ctx {
                                                // where that is exact to rounding (2: the Horner pass
                                                // also stages its input fields in shared memory)
     int tune_strided_stage = 2;                // ... its tiles: 0 direct, 1 TMA loads, 2 TMA stores, 3 both
+    int tune_pdl = 0;                          // register pass kernels as programmatic dependent launches
+                                               // (measured slower on the 2D and 3D steps: off)
     double tune_ms = 0.0;                      // step time of the chosen configuration
     // 2D Dirichlet grids (n <= 1024 per axis) whose lines the register
     // kernels cannot split into whole segments run on the batched kernels
@@ -242,6 +244,7 @@ LineSet lineset_of(const mol_ctx *h, int axis)
     L.inner = G.inner;
     L.nlines = G.nlines;
     L.S = L.K = 1;
+    L.pdl = h->tune_pdl;
     return L;
 }
 
@@ -1127,6 +1130,8 @@ mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count)
         return fail(h, MOL_EINVAL, "strided_stage must be 0, 1, 2 or 3");
     if (count > MOL_TUNE_ROWS_NB && vals[MOL_TUNE_ROWS_NB] != 0 && vals[MOL_TUNE_ROWS_NB] != 1)
         return fail(h, MOL_EINVAL, "rows_nb must be 0 or 1");
+    if (count > MOL_TUNE_PDL && vals[MOL_TUNE_PDL] != 0 && vals[MOL_TUNE_PDL] != 1)
+        return fail(h, MOL_EINVAL, "pdl must be 0 or 1");
     mol_status st = mol_set_tuning(h, vals[MOL_TUNE_RES_WARPS], vals[MOL_TUNE_STRIDED_RPT],
                                    vals[MOL_TUNE_STRIDED_WARPS], vals[MOL_TUNE_ROWS_WARPS]);
     if (st != MOL_OK) return st;
@@ -1134,6 +1139,7 @@ mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count)
     if (count > MOL_TUNE_STRIDED_NB) h->tune_strided_nb = vals[MOL_TUNE_STRIDED_NB];
     if (count > MOL_TUNE_STRIDED_STAGE) h->tune_strided_stage = vals[MOL_TUNE_STRIDED_STAGE];
     if (count > MOL_TUNE_ROWS_NB) h->tune_rows_nb = vals[MOL_TUNE_ROWS_NB];
+    if (count > MOL_TUNE_PDL) h->tune_pdl = vals[MOL_TUNE_PDL];
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     return MOL_OK;
 }
@@ -1145,7 +1151,7 @@ mol_status mol_get_tuning_ex(mol_handle h, int *vals, int count, double *ms_per_
         return fail(h, MOL_EINVAL, "count must be in 1.." + std::to_string(MOL_TUNE_COUNT));
     const int all[MOL_TUNE_COUNT] = {h->tune_res_warps, h->tune_strided_rpt, h->tune_strided_warps,
                                      h->tune_rows_warps, h->tune_rows_persist, h->tune_strided_nb,
-                                     h->tune_strided_stage, h->tune_rows_nb};
+                                     h->tune_strided_stage, h->tune_rows_nb, h->tune_pdl};
     for (int i = 0; i < count; ++i) vals[i] = all[i];
     if (ms_per_step) *ms_per_step = h->tune_ms;
     return MOL_OK;

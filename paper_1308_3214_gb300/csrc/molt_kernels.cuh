@@ -175,7 +175,19 @@ struct LineSet {
     int S, K;         // strided: segments per CTA (warps) and CTAs per line
     int persist_sms;  // row-split x pass: > 0 runs persistent CTAs on this many SMs
     int rows_nb;      // row-split x pass: 1 = one neighbour exchange per sweep where exact to rounding
+    int pdl;          // 1 = launched as a programmatic dependent of the previous kernel in the stream
 };
+
+// Programmatic dependent launch: a kernel launched with that attribute may be
+// scheduled while its predecessor in the stream is still running; it waits
+// here for the predecessor's completion (and its memory) before it touches
+// global memory, and lets its own successor be scheduled once all of its CTAs
+// have started.  Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // ---------------------------------------------------------------------------
 // float32 pair ("hi + lo") arithmetic for the time levels.  The __f*_rn

@@ -1,6 +1,7 @@
 // molt_regs.cu -- instantiation and launch of the register-resident pass kernels.
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include "molt_internal.h"
 #include "molt_regs.cuh"
 #include "molt_strided_nb.cuh"
@@ -8,6 +9,39 @@
 namespace molt {
 
 namespace {
+
+// Launch with the launch attributes of a pass: a cluster of cluster_y CTAs
+// along y (> 1), and (L.pdl) programmatic dependent launch, under which the
+// kernel's CTAs may be scheduled while the previous kernel in the stream
+// finishes (every pass kernel waits for it in pdl_enter before touching
+// global memory).
+template <class... KArgs, class... Args>
+cudaError_t launch_pass(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                        const LineSet &L, int cluster_y, Args &&...args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    if (cluster_y > 1) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = 1;
+        attr[na].val.clusterDim.y = (unsigned)cluster_y;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (L.pdl) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 constexpr int kContigWarps = 4;
 constexpr int kResWarpsMax = 4;
@@ -19,8 +53,8 @@ template <int BC, int RPT, int NB>
 cudaError_t run_res(int warps, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
 {
     const int64_t grid = (L.nlines + warps - 1) / warps;
-    k_contig_res<BC, RPT, NB><<<(unsigned)grid, 32 * warps, res_smem<RPT, NB>(warps), s>>>(A, L, p);
-    return cudaGetLastError();
+    return launch_pass(k_contig_res<BC, RPT, NB>, dim3((unsigned)grid), dim3(32 * warps), res_smem<RPT, NB>(warps), s, L,
+                       1, A, L, p);
 }
 
 template <int BC, int RPT, int NB>
@@ -59,22 +93,20 @@ cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cu
         if (p.mode == 3) {                            // the transposed Horner pass
             static int occ_adj = 0;
             const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W, true>, W, smem, L, occ_adj);
-            k_contig_rows<BC, RPT, NB, W, true><<<g, 32 * W, smem, s>>>(A, L, p, nc);
-            return cudaGetLastError();
+            return launch_pass(k_contig_rows<BC, RPT, NB, W, true>, dim3(g), dim3(32 * W), smem, s, L, 1, A, L, p, nc);
         }
     }
     if constexpr (W == 2 || W == 4) {
         if (L.rows_nb && rows_nb_plan(A.d, A.n, RPT, W)) {   // one neighbour exchange per sweep
             static int occ_nb = 0;
             const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W, false, true>, W, smem, L, occ_nb);
-            k_contig_rows<BC, RPT, NB, W, false, true><<<g, 32 * W, smem, s>>>(A, L, p, nc);
-            return cudaGetLastError();
+            return launch_pass(k_contig_rows<BC, RPT, NB, W, false, true>, dim3(g), dim3(32 * W), smem, s, L, 1, A, L,
+                               p, nc);
         }
     }
     static int occ = 0;
     const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W>, W, smem, L, occ);
-    k_contig_rows<BC, RPT, NB, W><<<g, 32 * W, smem, s>>>(A, L, p, nc);
-    return cudaGetLastError();
+    return launch_pass(k_contig_rows<BC, RPT, NB, W>, dim3(g), dim3(32 * W), smem, s, L, 1, A, L, p, nc);
 }
 
 template <int BC, int RPT, int NB, int W>
@@ -113,8 +145,8 @@ template <class T, int BC, int RPT>
 cudaError_t run_contig(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
 {
     const int64_t grid = (L.nlines + kContigWarps - 1) / kContigWarps;
-    k_contig<T, BC, RPT, kContigWarps><<<(unsigned)grid, 32 * kContigWarps, contig_smem<T, RPT>(), s>>>(A, L, p);
-    return cudaGetLastError();
+    return launch_pass(k_contig<T, BC, RPT, kContigWarps>, dim3((unsigned)grid), dim3(32 * kContigWarps),
+                       contig_smem<T, RPT>(), s, L, 1, A, L, p);
 }
 
 template <class T, int BC, int RPT>
@@ -122,22 +154,11 @@ cudaError_t run_strided(const AxisDev &A, const LineSet &L, const ProgParams &p,
 {
     size_t smem = strided_slot_bytes(L.S, sizeof(T));
     if (p.mode == 1) smem += (size_t)L.S * RPT * 32 * sizeof(T);
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1);
-    cfg.blockDim = dim3(32 * L.S, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = (unsigned)L.K;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = L.K > 1 ? 1 : 0;
-    if (p.mode == 1) return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, 1>, A, L, p);
+    const dim3 grid((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1), block(32 * L.S, 1, 1);
+    if (p.mode == 1) return launch_pass(k_strided<T, BC, RPT, 1>, grid, block, smem, s, L, L.K, A, L, p);
     if constexpr (BC == BC_DIRICHLET)
-        if (p.mode == 2) return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, 2>, A, L, p);
-    return cudaLaunchKernelEx(&cfg, k_strided<T, BC, RPT, 0>, A, L, p);
+        if (p.mode == 2) return launch_pass(k_strided<T, BC, RPT, 2>, grid, block, smem, s, L, L.K, A, L, p);
+    return launch_pass(k_strided<T, BC, RPT, 0>, grid, block, smem, s, L, L.K, A, L, p);
 }
 
 // cuTensorMapEncodeTiled from the driver (through the runtime, so that the
@@ -181,8 +202,8 @@ bool encode_field_map(CUtensorMap *m, const void *ptr, const LineSet &L, int n, 
 }
 
 template <int BC, int RPT, int STAGE>
-cudaError_t launch_nb_stage(const cudaLaunchConfig_t &cfg, const AxisDev &A, const LineSet &L, const ProgParams &p,
-                            const TmaMaps &tm)
+cudaError_t launch_nb_stage(const AxisDev &A, const LineSet &L, const ProgParams &p, const TmaMaps &tm, size_t smem,
+                            cudaStream_t s)
 {
     static bool attr = false;
     if (!attr) {
@@ -191,7 +212,8 @@ cudaError_t launch_nb_stage(const cudaLaunchConfig_t &cfg, const AxisDev &A, con
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    return cudaLaunchKernelEx(&cfg, k_strided_nb<BC, RPT, STAGE>, A, L, p, strided_nb_consts(A.d, RPT), tm);
+    return launch_pass(k_strided_nb<BC, RPT, STAGE>, dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1),
+                       dim3(32 * L.S, 1, 1), smem, s, L, L.K, A, L, p, strided_nb_consts(A.d, RPT), tm);
 }
 
 template <int BC, int RPT>
@@ -217,23 +239,12 @@ cudaError_t run_strided_nb(const AxisDev &A, const LineSet &L, const ProgParams 
         }
         if (!ok) stage = 0;
     }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1);
-    cfg.blockDim = dim3(32 * L.S, 1, 1);
-    cfg.dynamicSmemBytes = strided_nb_smem(L.S, RPT, stage, tm.nbox, tm.box_rows);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = (unsigned)L.K;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = L.K > 1 ? 1 : 0;
+    const size_t smem = strided_nb_smem(L.S, RPT, stage, tm.nbox, tm.box_rows);
     switch (stage) {
-    case 1: return launch_nb_stage<BC, RPT, 1>(cfg, A, L, p, tm);
-    case 2: return launch_nb_stage<BC, RPT, 2>(cfg, A, L, p, tm);
-    case 3: return launch_nb_stage<BC, RPT, 3>(cfg, A, L, p, tm);
-    default: return launch_nb_stage<BC, RPT, 0>(cfg, A, L, p, tm);
+    case 1: return launch_nb_stage<BC, RPT, 1>(A, L, p, tm, smem, s);
+    case 2: return launch_nb_stage<BC, RPT, 2>(A, L, p, tm, smem, s);
+    case 3: return launch_nb_stage<BC, RPT, 3>(A, L, p, tm, smem, s);
+    default: return launch_nb_stage<BC, RPT, 0>(A, L, p, tm, smem, s);
     }
 }
 
@@ -248,19 +259,8 @@ cudaError_t run_strided_nb_h(const AxisDev &A, const LineSet &L, const ProgParam
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1);
-    cfg.blockDim = dim3(32 * L.S, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr1[1];
-    attr1[0].id = cudaLaunchAttributeClusterDimension;
-    attr1[0].val.clusterDim.x = 1;
-    attr1[0].val.clusterDim.y = (unsigned)L.K;
-    attr1[0].val.clusterDim.z = 1;
-    cfg.attrs = attr1;
-    cfg.numAttrs = L.K > 1 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_strided_nb_h<BC, RPT, GT>, A, L, p, strided_nb_consts(A.d, RPT), tg);
+    return launch_pass(k_strided_nb_h<BC, RPT, GT>, dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1),
+                       dim3(32 * L.S, 1, 1), smem, s, L, L.K, A, L, p, strided_nb_consts(A.d, RPT), tg);
 }
 
 template <int BC, int RPT>

@@ -726,6 +726,7 @@ __device__ __forceinline__ void contig_r(T (&z)[RPT], T *stage, T *rline, const 
 template <class T, int BC, int RPT, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS, 3) k_contig(AxisDev A, LineSet LS, ProgParams pr)
 {
+    pdl_enter();
     static_assert(RPT >= 4 && RPT % VecOf<T>::n == 0, "segment length");
     using St = ContigStage<T, RPT>;
     using V = typename VecOf<T>::type;
@@ -836,6 +837,7 @@ __device__ __forceinline__ float4 sdiff4(const float4 &h, const float4 &l, float
 template <int BC, int RPT, int NB>
 __global__ void __launch_bounds__(128) k_contig_res(AxisDev A, LineSet LS, ProgParams pr)
 {
+    pdl_enter();
     static_assert(RPT % 4 == 0 && RPT >= 8, "segment length");
     using T = float;
     using St = ContigStage<T, RPT>;
@@ -1416,6 +1418,7 @@ template <int BC, int RPT, int NB, int W, bool ADJ = false, bool NBX = false>
 __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_contig_rows(AxisDev A, LineSet LS, ProgParams pr,
                                                                                        NbConsts nc)
 {
+    pdl_enter();
     static_assert(RPT % 4 == 0 && RPT >= 8, "segment length");
     static_assert(!ADJ || BC == BC_DIRICHLET, "the transposed pass is for Dirichlet rows");
     using T = float;
@@ -1968,6 +1971,7 @@ __device__ __forceinline__ void strided_r_pair(const ProgParams &pr, int64_t lba
 template <class T, int BC, int RPT, int KM>
 __global__ void __launch_bounds__(256, 2) k_strided(AxisDev A, LineSet LS, ProgParams pr)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StridedCtx<T> c{cg::this_cluster()};
     c.S = LS.S;

@@ -180,6 +180,7 @@ template <int BC, int RPT, int STAGE>
 __global__ void __launch_bounds__(256, 2) k_strided_nb(AxisDev A, LineSet LS, ProgParams pr, NbConsts nc,
                                                       const __grid_constant__ TmaMaps tm)
 {
+    pdl_enter();
     static_assert(RPT % 2 == 0 && RPT >= 8, "segment length");
     constexpr int H = RPT / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -422,6 +423,7 @@ template <int BC, int RPT, bool GT>
 __global__ void __launch_bounds__(256, 2) k_strided_nb_h(AxisDev A, LineSet LS, ProgParams pr, NbConsts nc,
                                                         const __grid_constant__ TmaGMaps tg)
 {
+    pdl_enter();
     static_assert(RPT % 2 == 0 && RPT >= 8, "segment length");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *slots = reinterpret_cast<float *>(smem_raw);          // [2][S][4][32]

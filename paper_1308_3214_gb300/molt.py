@@ -375,20 +375,21 @@ class Solver:
         return self.tuning()
 
     TUNING_KEYS = ("res_warps", "strided_rpt", "strided_warps", "rows_warps", "rows_persist", "strided_nb",
-                   "strided_stage", "rows_nb")
+                   "strided_stage", "rows_nb", "pdl")
 
     def set_tuning(self, res_warps: int = 2, strided_rpt: int = 0, strided_warps: int = 8, rows_warps: int = 0,
                    rows_persist: int | None = None, strided_nb: int | None = None,
-                   strided_stage: int | None = None, rows_nb: int | None = None):
+                   strided_stage: int | None = None, rows_nb: int | None = None, pdl: int | None = None):
         """Launch choices by hand (mol_set_tuning_ex); rows_persist,
-        strided_nb, strided_stage and rows_nb None keep the handle's
+        strided_nb, strided_stage, rows_nb and pdl None keep the handle's
         settings."""
         cur = self.tuning()
         vals = [int(res_warps), int(strided_rpt), int(strided_warps), int(rows_warps),
                 int(cur["rows_persist"] if rows_persist is None else rows_persist),
                 int(cur["strided_nb"] if strided_nb is None else strided_nb),
                 int(cur["strided_stage"] if strided_stage is None else strided_stage),
-                int(cur["rows_nb"] if rows_nb is None else rows_nb)]
+                int(cur["rows_nb"] if rows_nb is None else rows_nb),
+                int(cur["pdl"] if pdl is None else pdl)]
         arr = (ctypes.c_int * len(vals))(*vals)
         self._check(self.lib.mol_set_tuning_ex(self.h, arr, len(vals)))
 

@@ -396,6 +396,30 @@ def test_register_kernels_F_and_steps(shape, P, bc, prec):
     assert rel_l2(uc.cpu().numpy(), rc) <= tol
 
 
+@pytest.mark.parametrize("shape, P, bc", [((256, 2048), 3, "dirichlet"), ((64, 128, 96), 2, "periodic"),
+                                          ((512, 256), 2, "periodic")])
+def test_programmatic_dependent_launch_is_bitwise_neutral(shape, P, bc):
+    """The passes launched as programmatic dependents of the kernel before
+    them (each waits for its predecessor before touching memory) give the
+    same bits as ordinary stream order, through graphs and direct launches;
+    and they match the oracle."""
+    s = make(shape, 1.5 * spacing(shape[1], bc), P, bc, "mixed")
+    u0 = smooth_field(shape, 61, bc) + 0.05 * field(shape, 62, bc)
+    u1 = oracle.start(u0, s.nu, P, s.beta, bc)
+    out = {}
+    for pdl in (1, 0):
+        s.set_tuning(res_warps=2, strided_rpt=0, strided_warps=8, rows_warps=0, pdl=pdl)
+        assert s.tuning()["pdl"] == pdl
+        up, uc = dev(u0), dev(u1)
+        s.step(up, uc, 7)
+        out[pdl] = (up.clone(), uc.clone(), s.apply_F(dev(u0)))
+    for a, b in zip(out[1], out[0]):
+        assert torch.equal(a, b)
+    ref = oracle.F(u0, s.nu, P, s.beta, bc)
+    assert rel_l2(out[1][2].cpu().numpy(), ref) <= tol_for("mixed", s, 2 * P)
+    s.close()
+
+
 # ---------------------------------------------------------------------------
 # autotuner
 # ---------------------------------------------------------------------------
