@@ -1442,6 +1442,8 @@ __global__ void __launch_bounds__(32 * W, W == 2 ? 8 : (W == 4 ? 7 : 4)) k_conti
         const unsigned bytes = (unsigned)n * 4u;
         prefetch_l2((const float *)pr.u_hi + base, bytes);
         prefetch_l2((const float *)pr.u_lo + base, bytes);
+        // field 0 is copied only once r has left its buffer: into L2 now
+        if (ng > 0) prefetch_l2(reinterpret_cast<const float *>(pr.g[0]) + base, bytes);
         if (pr.feb != 0.f) {
             prefetch_l2((const float *)pr.up_hi + base, bytes);
             prefetch_l2((const float *)pr.up_lo + base, bytes);
