@@ -490,13 +490,16 @@ int64_t mol_batch_launch_count(mol_batch b);
  * the fastest.  Synchronous; the caller's fields are not touched.
  * mol_batch_get_tuning: out[0], out[1] = warps per CTA of the two x launches
  * (out[1] = 0: the long rows run split, one CTA of two warps per row),
- * out[2] = y segment rule (0 smallest, 1 doubled); ms (may be NULL) = the
- * tuned x and y pass times. */
+ * out[2] = y rule: bit 0 the segment length (0 smallest, 1 doubled), bit 1
+ * set = full carries in every column; clear (the default) = the float32 y
+ * pass exchanges once per sweep between neighbouring segments in the
+ * problems where the decay over a segment is below 2^-30 and a column has
+ * more than two segments; ms (may be NULL) = the tuned x and y pass times. */
 mol_status mol_batch_autotune(mol_batch b, void *stream);
 mol_status mol_batch_get_tuning(mol_batch b, int out[3], double ms[2]);
 /* Sets the launch variants by hand, in the encoding of mol_batch_get_tuning:
  * x_warps_short, x_warps_long in {2, 4, 8} (x_warps_long 0: split long
- * rows), y_rule in {0, 1}.  MOL_EINVAL (nothing changed) for a value outside
+ * rows), y_rule in {0, 1, 2, 3}.  MOL_EINVAL (nothing changed) for a value outside
  * those sets or one whose buffers exceed shared memory.  Synchronous. */
 mol_status mol_batch_set_tuning(mol_batch b, int x_warps_short, int x_warps_long, int y_rule);
 

@@ -59,7 +59,9 @@ struct mol_batch_ctx {
         return (one_warp_end() > 0 ? 1 : 0) + ((xmid && rows_mid > rows_small) ? 1 : 0) + (nrows > rows_mid ? 1 : 0);
     }
     int smem_sm = 228 * 1024, smem_blk = 227 * 1024;
-    int ymode = 0;                      // y segment rule: 0 smallest covering RPT, 1 twice that (<= 64)
+    int ymode = 0;                      // y segment rule: bit 0: 0 smallest covering RPT, 1 twice that
+                                        // (<= 64); bit 1: full carries even where the neighbour exchange
+                                        // is exact
     int xsplit = 1;                     // rows of > 512 points: 1 one CTA of two warps per row, 0 one warp
     size_t xs_smem = 0;                 // shared memory of the split-row kernel
     int xmid = 1;                       // rows of 257..512 points: 1 one CTA of two warps per row (8-point
@@ -122,12 +124,36 @@ int pick_rpt_x(int n)
     while (32 * r < n) r *= 2;
     return r;
 }
+// mode bit 0: twice the smallest covering segment length (<= 64)
 int pick_rpt_y(int n, int mode = 0)
 {
     int r = 4;
     while (kBatchYWarps * r < n) r *= 2;
-    if (mode == 1 && r < 64) r *= 2;
+    if ((mode & 1) && r < 64) r *= 2;
     return r;
+}
+
+// The neighbour-exchange y pass of one problem (batch_cols_nb): on where the
+// decay over a segment is below float32 rounding, d^(RPT-1) <= 2^-30, and the
+// column has more than two segments; the constants of its segment length and
+// of its ragged last segment.
+void set_y_nb(BatchProb &pb, bool allow)
+{
+    const int R = pb.rpt_y, n = pb.ay.n;
+    const double d = pb.ay.d;
+    pb.ynb = (allow && R >= 4 && (n + R - 1) / R > 2 && std::pow(d, (double)(R - 1)) <= std::ldexp(1.0, -30)) ? 1 : 0;
+    pb.nby = strided_nb_consts(d, R);
+    const int kl = (n - 1) % R;
+    double gl = 0.0, g1l = 0.0;
+    for (int k = 0; k <= kl; ++k) {
+        gl += std::pow(d, 2.0 * k + 1.0);
+        if (k >= 1) g1l += std::pow(d, 2.0 * k);
+    }
+    pb.nbGL = (float)gl;
+    pb.nbG1L = (float)g1l;
+    pb.nbdk = (float)std::pow(d, (double)kl);
+    pb.nbdk1 = kl >= 1 ? (float)std::pow(d, (double)(kl - 1)) : 0.f;
+    pb.nbdkp = (float)std::pow(d, (double)(kl + 1));
 }
 
 // length class of a row: 0 (<= 256 points), 1 (257..512), 2 (513..1024)
@@ -189,6 +215,7 @@ void set_y_segments(mol_batch_ctx *b)
         pb.rpt_y = pick_rpt_y(pb.ay.n, b->ymode);
         const double nuy = -std::log(pb.ay.d);
         for (int k = 0; k < 5; ++k) pb.ay.dm[k] = std::exp(-nuy * (double)pb.rpt_y * (double)(1 << k));
+        set_y_nb(pb, b->tbytes == 4 && !(b->ymode & 2));
     }
 }
 
@@ -494,6 +521,7 @@ mol_status plan_batch(mol_batch_ctx *b, int nprob, const mol_grid *grids, const 
             pb.ax.dm[k] = std::exp(-nux * (double)pb.rpt_x * (double)(1 << k));
             pb.ay.dm[k] = std::exp(-nuy * (double)pb.rpt_y * (double)(1 << k));
         }
+        set_y_nb(pb, b->tbytes == 4);
         pb.P = P[i];
         pb.pitch = (nx + 3) & ~3;
         items += (nx + 31) / 32;
@@ -908,7 +936,7 @@ mol_status mol_batch_autotune(mol_batch b, void *stream)
     }
     int bestY = b->ymode;
     double besty = 1e30;
-    for (int mode : {0, 1}) {
+    for (int mode : {0, 1, 2}) {
         b->ymode = mode;
         set_y_segments(b);
         BCK(upload(), "table upload");
@@ -928,8 +956,8 @@ mol_status mol_batch_set_tuning(mol_batch b, int x_warps_short, int x_warps_long
 {
     if (!b) return bfail(nullptr, MOL_EINVAL, "handle is NULL");
     auto okW = [](int W) { return W == 2 || W == 4 || W == 8; };
-    if (!okW(x_warps_short) || !(okW(x_warps_long) || x_warps_long == 0) || (y_rule != 0 && y_rule != 1))
-        return bfail(b, MOL_EINVAL, "x warps must be 2, 4 or 8 (0: split long rows) and the y rule 0 or 1");
+    if (!okW(x_warps_short) || !(okW(x_warps_long) || x_warps_long == 0) || y_rule < 0 || y_rule > 3)
+        return bfail(b, MOL_EINVAL, "x warps must be 2, 4 or 8 (0: split long rows) and the y rule 0..3");
     if (x_warps_long == 0 && b->xs_smem > (size_t)b->smem_blk)
         return bfail(b, MOL_EINVAL, "split-row buffers exceed shared memory");
     const int oldW[2] = {b->xW[0], b->xW[1]};

@@ -44,6 +44,14 @@ struct BatchProb {
     double coef[BMAXP + 1][BMAXP];   // x Horner weights of g_k, t = 0..P, k < P
     float cu32[BMAXP + 1];           // float32 copies (batch_mirror)
     float coef32[BMAXP + 1][BMAXP];
+    // y pass with one neighbour exchange per sweep (float32; batch_cols_nb):
+    // ynb = 1 where exact to rounding; the constants of rpt_y and of the
+    // ragged last segment (its last point at kl = (ny - 1) mod rpt_y)
+    NbConsts nby;
+    float nbGL, nbG1L;               // sum_{k<=kl} d^(2k+1), sum_{1<=k<=kl} d^(2k)
+    float nbdk, nbdk1, nbdkp;        // d^kl, d^(kl-1) (0 when kl = 0), d^(kl+1)
+    int ynb;
+    int pad2_;
 
     template <class T> __device__ T ccu(int t) const
     {
@@ -133,6 +141,8 @@ __device__ __forceinline__ void batch_row(const BatchProb &pb, const ProgParams 
         const unsigned bytes = (unsigned)(nvec * 16);    // whole 16-byte vectors inside the pitch
         prefetch_l2(reinterpret_cast<const T *>(pr.u_hi) + base, bytes);
         if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.u_lo) + base, bytes);
+        // field 0 is copied only once r has left its buffer: into L2 now
+        if (ng > 0) prefetch_l2(reinterpret_cast<const T *>(pr.g[0]) + base, bytes);
         if (pr.feb != 0.f) {
             prefetch_l2(reinterpret_cast<const T *>(pr.up_hi) + base, bytes);
             if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.up_lo) + base, bytes);
@@ -336,6 +346,7 @@ __device__ __forceinline__ void batch_row_split(const BatchProb &pb, const ProgP
         const unsigned bytes = (unsigned)(nvec * 16);
         prefetch_l2(reinterpret_cast<const T *>(pr.u_hi) + base, bytes);
         if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.u_lo) + base, bytes);
+        if (ng > 0) prefetch_l2(reinterpret_cast<const T *>(pr.g[0]) + base, bytes);   // copied after r
         if (pr.feb != 0.f) {
             prefetch_l2(reinterpret_cast<const T *>(pr.up_hi) + base, bytes);
             if (pair) prefetch_l2(reinterpret_cast<const T *>(pr.up_lo) + base, bytes);
@@ -721,6 +732,193 @@ __device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams
     }
 }
 
+// The powers D_y^p u of one group of 32 columns with ONE exchange per sweep
+// between neighbouring segments (the algebra of k_strided_nb: each segment
+// runs its causal recurrence with zero inflow, publishes E, y0(RPT-2), ER0,
+// ER1, and after one barrier corrects itself from its neighbours' numbers),
+// for columns of any length: the last segment holds the line's last point
+// at kl and is ragged (zeros past it; with kl = 0 the segment before it is
+// ragged too, so that it never reads past the line).  The right boundary
+// term B' = -y_{n-1} / (1 - mu^2) of the Dirichlet line enters at the last
+// point; the last segment also publishes its zero-inflow y at kl, so that its
+// left neighbour forms B' (linear in its own E) and takes the term into its
+// inflow.  Valid when d^(RPT-1) <= 2^-30 and the line has more than two
+// segments (ynb, set on the host).  Float32 only.
+template <int RPT>
+__device__ __forceinline__ void batch_cols_nb(const BatchProb &pb, const ProgParams &pr, int col0, int w, int lane,
+                                              float *slots)
+{
+    constexpr int H = RPT / 2;
+    constexpr int S = kBatchYWarps;
+    constexpr bool TWO = RPT >= 8;                  // two-chain recurrences on the full segments
+    const AxisDev &A = pb.ay;
+    const NbConsts &nc = pb.nby;
+    const int n = A.n, Gd = (n + RPT - 1) / RPT, Ld = Gd - 1;
+    const int seg = w, a = seg * RPT;
+    const bool full = seg < Gd;
+    const int kl = n - 1 - a;
+    const bool rag = full && kl <= RPT;
+    const bool left_end = seg == 0, last = seg == Ld;
+    const bool hasL = full && seg > 0, hasR = full && seg < Ld, rlast = seg == Ld - 1;
+    const int col = col0 + lane;
+    const bool io = full && col < pb.ax.n;
+    const int64_t lbase = pb.off + (io ? col : 0);
+    const int64_t st = pb.pitch;
+    const float d = A.fd, c1 = A.fc1, c2 = A.fc2, inv = A.finv;
+
+    float z[RPT];
+    float rl = 0.f, rr = 0.f;
+    if (io) {
+        if (rag) bcol_r_rag<RPT>(pr, lbase, st, a, n, z, rl, rr);
+        else strided_r_pair<BC_DIRICHLET, RPT>(pr, lbase, st, a, n, z, rl, rr);
+    } else {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = 0.f;
+    }
+    if (seg == 0) z[0] = z[1];                      // Dirichlet: the end node takes the interior centre
+    float hl2 = 0.f, hl1 = rl, hr0 = rr, hr1 = 0.f;  // sweep 1 (z = s): s at a-1 and a+RPT
+    auto noR = [](int) { return 0.f; };
+
+    for (int p = 1; p <= pb.P; ++p) {
+        float zl2 = hl2, zl1 = hl1, zr0 = hr0, zr1 = hr1;
+        if (p == 1) {
+            end_ghosts<float, RPT, 0>(z, left_end, false, zl2, zl1, zr0, zr1);
+            if (rag) seg_make_q<float, RPT, 0, true>(z, zl2, zl1, zr0, zr1, noR, 0.f, c1, c2, kl);
+            else seg_make_q<float, RPT, 0, false>(z, zl2, zl1, zr0, zr1, noR, 0.f, c1, c2);
+        } else {
+            end_ghosts<float, RPT, 1>(z, left_end, false, zl2, zl1, zr0, zr1);
+            if (rag) seg_make_q<float, RPT, 1, true>(z, zl2, zl1, zr0, zr1, noR, 0.f, c1, c2, kl);
+            else seg_make_q<float, RPT, 1, false>(z, zl2, zl1, zr0, zr1, noR, 0.f, c1, c2);
+        }
+        end_zero<float, RPT>(z, left_end, false);
+        if (!full) {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) z[k] = 0.f;
+        }
+
+        // the causal recurrence with zero inflow (ragged segments: one chain,
+        // zero past the last point); E, Y2 = zero-inflow y at RPT-1, RPT-2
+        float E1 = 0.f, rb = 0.f, ER1 = 0.f, YL0 = 0.f, E, Y2;
+        if (TWO && !rag) {
+            float ya = z[0], yb = z[H], ra1 = 0.f, pw = 1.f;
+            rb = yb;
+#pragma unroll
+            for (int k = 1; k < H; ++k) {
+                ya = d * ya + z[k];
+                yb = d * yb + z[H + k];
+                z[k] = ya;
+                z[H + k] = yb;
+                const float pbk = pw * d;            // chain A weighs y_k by d^(k-1), chain B by d^k
+                ra1 += pw * ya;
+                rb += pbk * yb;
+                pw = pbk;
+            }
+            E1 = ya;
+            E = yb + E1 * nc.dH;
+            Y2 = z[RPT - 2] + E1 * nc.dH1;
+            ER1 = ra1 + nc.dH1 * (rb + E1 * nc.GH);
+        } else {
+            float y = 0.f, pw = 1.f;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                y = d * y + z[k];
+                const float yo = (!rag || k <= kl) ? y : 0.f;
+                YL0 = (k == kl) ? y : YL0;
+                z[k] = yo;
+                if (k > 0) {
+                    ER1 += pw * yo;
+                    pw *= d;
+                }
+            }
+            E = z[RPT - 1];
+            Y2 = z[RPT - 2];
+        }
+        const float ER0 = z[0] + d * ER1;
+
+        float *mine = slots + ((size_t)(p & 1) * S + seg) * 160;
+        mine[lane] = E;
+        mine[32 + lane] = Y2;
+        mine[64 + lane] = ER0;
+        mine[96 + lane] = ER1;
+        mine[128 + lane] = YL0;
+        __syncthreads();
+        float EL = 0.f, Y2L = 0.f, ER0R = 0.f, ER1R = 0.f, YLR = 0.f;
+        if (hasL) {
+            const float *q = slots + ((size_t)(p & 1) * S + seg - 1) * 160;
+            EL = q[lane];
+            Y2L = q[32 + lane];
+        }
+        if (hasR) {
+            const float *q = slots + ((size_t)(p & 1) * S + seg + 1) * 160;
+            ER0R = q[64 + lane];
+            ER1R = q[96 + lane];
+            YLR = q[128 + lane];
+        }
+
+        // true causal values: chain A from the left neighbour's y at a-1,
+        // chain B from the corrected y at H-1
+        float ER2 = 0.f;
+        if (TWO && !rag) {
+            const float cB = E1 + EL * nc.dH;
+            float pk = d;
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                z[k] += EL * pk;
+                z[H + k] += cB * pk;
+                pk *= d;
+            }
+            ER2 = rb + cB * nc.GH;                   // sum_j d^j y_{H+j}
+        } else {
+            float pk = d;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (!rag || k <= kl) z[k] += EL * pk;
+                pk *= d;
+            }
+        }
+
+        // the right inflow: e at a+RPT and a+RPT+1, with the line's B' term
+        // when the right neighbour holds the last point
+        float eout = 0.f, er1 = 0.f;
+        if (hasR) {
+            if (rlast) {
+                const float Bp = -(YLR + E * pb.nbdkp) * inv;
+                eout = ER0R + pb.nbGL * E + Bp * pb.nbdk;
+                er1 = ER1R + pb.nbG1L * E + Bp * pb.nbdk1;
+            } else {
+                eout = ER0R + nc.G * E;
+                er1 = ER1R + nc.G1 * E;
+            }
+        }
+        const float acc = d * eout;
+        if (TWO && !rag) {
+            seg_bwd_scan2<float, RPT>(z, d, nc.dH, acc, ER2);
+        } else {
+            const float Zr = last ? -(YL0 + EL * pb.nbdkp) * inv : 0.f;   // B' at the last point
+            seg_bwd_scan<float, RPT, true>(z, d, acc, rag ? kl : RPT, Zr);
+        }
+        if (left_end) {
+            if (TWO && !rag) seg_add_left2<float, RPT>(z, d, nc.dH, -z[0] * inv);
+            else seg_add_left<float, RPT>(z, d, -z[0] * inv);
+        }
+
+        // halos of the next sweep
+        hl1 = hasL ? EL + d * z[0] : 0.f;
+        hl2 = hasL ? Y2L + d * hl1 : 0.f;
+        hr0 = eout;
+        hr1 = er1;
+
+        if (io) {
+            float *po = reinterpret_cast<float *>(pr.out[p - 1]) + lbase + (int64_t)a * st;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (k <= kl) *po = z[k];
+                po += st;
+            }
+        }
+    }
+}
+
 // ADJ: powers of D_y^T (the adjoint step) instead of D_y
 template <class T, bool ADJ>
 __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
@@ -747,6 +945,19 @@ __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
         __syncthreads();                               // the previous item is done with pbs and the slots
         if (threadIdx.x < 32) warp_copy(&pbs, bp.probs + item.x, threadIdx.x);
         __syncthreads();
+        if constexpr (sizeof(T) == 4 && !ADJ) {
+            if (pbs.ynb) {
+                float *slots = reinterpret_cast<float *>(smem_raw);
+                switch (pbs.rpt_y) {
+                case 4: batch_cols_nb<4>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
+                case 8: batch_cols_nb<8>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
+                case 16: batch_cols_nb<16>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
+                case 32: batch_cols_nb<32>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
+                default: batch_cols_nb<64>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
+                }
+                continue;
+            }
+        }
         switch (pbs.rpt_y) {
         case 4: batch_cols<T, 4, ADJ>(pbs, bp.pr, item.y, c, YL); break;
         case 8: batch_cols<T, 8, ADJ>(pbs, bp.pr, item.y, c, YL); break;
@@ -757,7 +968,12 @@ __global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
     }
 }
 
-inline size_t batch_y_smem(size_t tsize) { return strided_slot_bytes(kBatchYWarps, tsize) + 32 * tsize; }
+inline size_t batch_y_smem(size_t tsize)
+{
+    const size_t full = strided_slot_bytes(kBatchYWarps, tsize) + 32 * tsize;
+    const size_t nb = (size_t)2 * kBatchYWarps * 5 * 32 * sizeof(float);   // batch_cols_nb's slots
+    return full > nb ? full : nb;
+}
 inline size_t batch_x_smem(size_t tsize, int W, int nbuf, bool large)
 {
     const size_t rmax = large ? BatchX<float, true>::RMAX : BatchX<float, false>::RMAX;

@@ -618,7 +618,9 @@ class BatchSolver:
 
     def set_tuning(self, x_warps=(8, 8), y_rule: int = 0):
         """Launch variants by hand: x_warps = (short rows, long rows; 0 = long
-        rows split over two warps of one CTA), y_rule 0 or 1."""
+        rows split over two warps of one CTA), y_rule 0..3 (bit 0: doubled
+        y segments; bit 1: full carries even where the y pass's neighbour
+        exchange is exact)."""
         self._check(self.lib.mol_batch_set_tuning(self.h, int(x_warps[0]), int(x_warps[1]), int(y_rule)))
 
     def tuning(self) -> dict:

@@ -203,9 +203,60 @@ def test_batch_full_size_512_problems_sampled():
         assert rel_l2(res["mixed"][i], res["fp64"][i]) <= mixed_tol((nu, nu), 2 * p.P), i
 
 
+# The y pass with one neighbour exchange per sweep: columns whose last point
+# falls at every kind of place in its segment (kl = 0, where the segment
+# before the last is ragged too; kl = 1; kl = RPT - 1; in between), every
+# segment length 4..64, decays on both sides of the exchange's limit
+# d^(RPT-1) <= 2^-30 (where it does not hold the column takes the full
+# carries), against the oracle with the exchange on (y rule 0, 1) and off
+# (2, 3).
+NB_SHAPES = [(577, 40), (578, 33), (640, 64), (1024, 20), (600, 70), (520, 36), (257, 50), (258, 40),
+             (300, 64), (512, 31), (129, 45), (130, 64), (200, 17), (256, 40), (65, 40), (100, 64),
+             (33, 40), (64, 64)]
+NB_CFL = [0.4, 0.9, 0.3, 1.5, 3.5]
+
+
+def rpt_y(ny, rule):
+    r = 4
+    while 16 * r < ny:
+        r *= 2
+    return min(64, 2 * r) if (rule & 1) and r < 64 else r
+
+
+@pytest.mark.parametrize("rule", [0, 1, 2, 3])
+def test_batch_y_neighbour_exchange_matches_oracle(rule):
+    shapes = NB_SHAPES
+    Ps = [1 + i % 3 for i in range(len(shapes))]
+    cfls = [NB_CFL[i % len(NB_CFL)] for i in range(len(shapes))]
+    dts, specs = [], []
+    for (ny, nx), P, cfl in zip(shapes, Ps, cfls):
+        hy = 1.0 / (ny - 1)
+        dt = cfl * hy
+        beta = oracle.beta_max(P)
+        nu = (beta / dt / (nx - 1), beta / dt / (ny - 1))
+        dts.append(dt)
+        specs.append((P, dt, beta, nu))
+    b = molt.BatchSolver(shapes, dt=dts, P=Ps, prec="mixed")
+    b.set_tuning((4, 0), rule)
+    assert b.tuning()["y_rule"] == rule
+    # the exchange applies to a good share of the problems, ragged ends of
+    # every kind among them
+    nb = [math.exp(-nu[1]) ** (rpt_y(ny, rule) - 1) <= 2.0 ** -30 and (ny + rpt_y(ny, rule) - 1) // rpt_y(ny, rule) > 2
+          for (ny, nx), (P, dt, beta, nu) in zip(shapes, specs)]
+    kls = {(ny - 1) % rpt_y(ny, rule) for (ny, nx), on in zip(shapes, nb) if on}
+    assert sum(nb) >= 8 and 0 in kls and any(0 < k < 8 for k in kls)
+    us = [rough_field(s, 700 + i) for i, s in enumerate(shapes)]
+    got = b.unpack(b.apply_F(b.pack(us)))
+    for i, (u, g, (P, dt, beta, nu)) in enumerate(zip(us, got, specs)):
+        ref = oracle.F(u, nu, P, beta, "dirichlet")
+        err = rel_l2(g.cpu().numpy(), ref)
+        assert err <= mixed_tol(nu, 2 * P), (i, shapes[i], P, nb[i], err)
+    b.close()
+
+
 def test_batch_set_tuning_rejects_bad_choices():
     b, _ = make_batch(SHAPES[:3], "mixed")
-    for bad in (((3, 8), 0), ((8, 1), 0), ((8, 8), 2), ((0, 8), 0)):
+    for bad in (((3, 8), 0), ((8, 1), 0), ((8, 8), 4), ((8, 8), -1), ((0, 8), 0)):
         with pytest.raises(molt.MolError):
             b.set_tuning(*bad)
 
@@ -213,7 +264,7 @@ def test_batch_set_tuning_rejects_bad_choices():
 def test_batch_autotune_choice_keeps_parity():
     b, specs = make_batch(SHAPES, "mixed")
     tun = b.autotune()
-    assert tun["x_warps"][0] in (2, 4, 8) and tun["x_warps"][1] in (0, 2, 4, 8) and tun["y_rule"] in (0, 1)
+    assert tun["x_warps"][0] in (2, 4, 8) and tun["x_warps"][1] in (0, 2, 4, 8) and tun["y_rule"] in (0, 1, 2)
     assert tun["x_ms"] > 0 and tun["y_ms"] > 0
     us = [rough_field(s, 900 + i) for i, s in enumerate(SHAPES)]
     got = b.unpack(b.apply_F(b.pack(us)))
