@@ -42,11 +42,15 @@ struct mol_batch_ctx {
     int nrec = 0, irec_cap = 0;          //   nodes, the node groups' starts and the receivers by node
     int nnode = 0;
     void *inter[BMAXP] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    int xW[2] = {8, 8}, xgrid[2] = {1, 1}, ygrid = 1, nbuf = 1, cgrid = 1;
+    int xW[2] = {8, 8}, xgrid[2] = {1, 1}, nbuf = 1, cgrid = 1;
+    int ycls_begin[4] = {0, 0, 0, 0};   // y work list: the items of clusters of 1, 2, 4, 8 CTAs
+    int ycls_count[4] = {0, 0, 0, 0};
     size_t xsmem[2] = {0, 0}, ysmem = 0;
     int num_sms = 152;
     std::vector<void *> allocs;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t ys[3] = {nullptr, nullptr, nullptr};   // y pass: side streams of the cluster-size classes
+    cudaEvent_t yev[4] = {nullptr, nullptr, nullptr, nullptr};   // their fork and joins
     cudaGraphExec_t gexec = nullptr;
     int64_t launches = 0;
     bool timing = false;
@@ -54,14 +58,20 @@ struct mol_batch_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     std::string err;
     int64_t one_warp_end() const { return xmid ? rows_small : rows_mid; }
+    int y_launches() const
+    {
+        int n = 0;
+        for (int k = 0; k < 4; ++k) n += ycls_count[k] > 0 ? 1 : 0;
+        return n;
+    }
     int x_launches() const
     {
         return (one_warp_end() > 0 ? 1 : 0) + ((xmid && rows_mid > rows_small) ? 1 : 0) + (nrows > rows_mid ? 1 : 0);
     }
     int smem_sm = 228 * 1024, smem_blk = 227 * 1024;
-    int ymode = 0;                      // y segment rule: bit 0: 0 smallest covering RPT, 1 twice that
-                                        // (<= 64); bit 1: full carries even where the neighbour exchange
-                                        // is exact
+    int ymode = 0;                      // y rule: bit 0: 0 the fewest CTAs per column group, 1 twice as
+                                        // many (shorter segments); bit 1: full carries even where the
+                                        // neighbour exchange is exact
     int xsplit = 1;                     // rows of > 512 points: 1 one CTA of two warps per row, 0 one warp
     size_t xs_smem = 0;                 // shared memory of the split-row kernel
     int xmid = 1;                       // rows of 257..512 points: 1 one CTA of two warps per row (8-point
@@ -113,6 +123,14 @@ void bfree_all(mol_batch_ctx *b)
     b->gexec = nullptr;
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     b->cap_stream = nullptr;
+    for (int k = 0; k < 3; ++k) {
+        if (b->ys[k]) cudaStreamDestroy(b->ys[k]);
+        b->ys[k] = nullptr;
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (b->yev[k]) cudaEventDestroy(b->yev[k]);
+        b->yev[k] = nullptr;
+    }
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
 }
@@ -124,13 +142,18 @@ int pick_rpt_x(int n)
     while (32 * r < n) r *= 2;
     return r;
 }
-// mode bit 0: twice the smallest covering segment length (<= 64)
-int pick_rpt_y(int n, int mode = 0)
+// y pass of a column of n points: K CTAs of kBatchYSeg warps (K a power of
+// two, the fewest whose segments of at most 64 (float32) / 32 (float64)
+// points cover the column; mode bit 0: twice as many, up to 8) and the
+// segment length R (a power of two >= 4 with kBatchYSeg K R >= n)
+void pick_y(int n, int mode, int tbytes, int &K, int &R)
 {
-    int r = 4;
-    while (kBatchYWarps * r < n) r *= 2;
-    if ((mode & 1) && r < 64) r *= 2;
-    return r;
+    const int rmax = tbytes == 4 ? 64 : 32;
+    K = 1;
+    while (kBatchYSeg * K * rmax < n) K *= 2;
+    if ((mode & 1) && K < 8) K *= 2;
+    R = 4;
+    while (kBatchYSeg * K * R < n) R *= 2;
 }
 
 // The neighbour-exchange y pass of one problem (batch_cols_nb): on where the
@@ -158,31 +181,29 @@ void set_y_nb(BatchProb &pb, bool allow)
 
 // length class of a row: 0 (<= 256 points), 1 (257..512), 2 (513..1024)
 int row_class(int nx) { return nx <= 256 ? 0 : (nx <= 512 ? 1 : 2); }
-bool long_row(int nx) { return row_class(nx) == 2; }
 
-// Order of the y-pass work list.  CTA b of G takes the items at b, b + G,
-// b + 2G, ... of the list.  The items are sorted by decreasing cost (the
-// serial segment length times the P + 1 phases of a column group: loads and
-// P sweeps) and dealt out in a snake: round k gives its G items to CTAs
-// 0..G-1 when k is even and G-1..0 when k is odd, so every CTA gets one item of
-// each cost class.  Items are independent, so the order changes no result.
-// A partial last round is dealt straight (CTAs 0..rem-1).
-std::vector<int2> order_y_items(const std::vector<BatchProb> &hp, const std::vector<int2> &it, int G)
+// The y-pass work list: one item (problem, first column) per group of 32
+// columns, grouped by the cluster size of its problem (one launch per size),
+// and within a group by decreasing cost (the segment length times the P + 1
+// phases of a column group: loads and P sweeps), so that the long items
+// start first.  Items are independent, so the order changes no result.
+std::vector<int2> y_work_list(mol_batch_ctx *b)
 {
-    const int n = (int)it.size();
-    std::vector<int> cost(n), idx(n);
-    for (int i = 0; i < n; ++i) {
-        const BatchProb &pb = hp[it[i].x];
-        cost[i] = pick_rpt_y(pb.ay.n) * (pb.P + 1);
-        idx[i] = i;
-    }
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    std::vector<int2> out(n);
-    for (int i = 0; i < n; ++i) {
-        const int k = i / G, j = i % G;
-        const bool full_round = (int64_t)(k + 1) * G <= n;
-        const int slot = (full_round && (k & 1)) ? G - 1 - j : j;
-        out[(int64_t)k * G + slot] = it[idx[i]];
+    std::vector<int2> out;
+    out.reserve(b->nitems_y);
+    for (int k = 0; k < 4; ++k) {
+        std::vector<std::pair<int, int2>> cls;
+        for (int i = 0; i < b->nprob; ++i) {
+            const BatchProb &pb = b->hp[i];
+            if (pb.ky != (1 << k)) continue;
+            for (int c0 = 0; c0 < pb.ax.n; c0 += 32) cls.push_back({pb.rpt_y * (pb.P + 1), make_int2(i, c0)});
+        }
+        std::stable_sort(cls.begin(), cls.end(), [](const std::pair<int, int2> &a, const std::pair<int, int2> &c) {
+            return a.first > c.first;
+        });
+        b->ycls_begin[k] = (int)out.size();
+        b->ycls_count[k] = (int)cls.size();
+        for (auto &c : cls) out.push_back(c.second);
     }
     return out;
 }
@@ -209,14 +230,24 @@ void set_x_segments(mol_batch_ctx *b)
 }
 
 // per-problem y-pass segment constants for the current rule
-void set_y_segments(mol_batch_ctx *b)
+void set_y_problems(mol_batch_ctx *b)
 {
     for (BatchProb &pb : b->hp) {
-        pb.rpt_y = pick_rpt_y(pb.ay.n, b->ymode);
+        pick_y(pb.ay.n, b->ymode, b->tbytes, pb.ky, pb.rpt_y);
         const double nuy = -std::log(pb.ay.d);
         for (int k = 0; k < 5; ++k) pb.ay.dm[k] = std::exp(-nuy * (double)pb.rpt_y * (double)(1 << k));
         set_y_nb(pb, b->tbytes == 4 && !(b->ymode & 2));
     }
+}
+
+// ... and the work list grouped by the new cluster sizes (synchronous)
+cudaError_t set_y_segments(mol_batch_ctx *b)
+{
+    set_y_problems(b);
+    const std::vector<int2> it = y_work_list(b);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(b->items, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice);
+    return e;
 }
 
 // x-pass launch shape L (0: rows of <= 512 points, 1: longer rows) for W warps per CTA
@@ -245,11 +276,63 @@ cudaEvent_t btake_event(mol_batch_ctx *b)
 }
 
 template <class T, bool ADJ>
-cudaError_t launch_pass_y(const mol_batch_ctx *b, const BatchPass &bp, cudaStream_t s)
+cudaError_t launch_y_class(const mol_batch_ctx *b, BatchPass bp, int k, cudaStream_t s)
 {
-    k_batch_y<T, ADJ><<<b->ygrid, 32 * kBatchYWarps, b->ysmem, s>>>(bp);
-    return cudaGetLastError();
+    const unsigned K = 1u << k;
+    bp.items += b->ycls_begin[k];
+    bp.nitems = b->ycls_count[k];
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)b->ycls_count[k], K, 1);
+    cfg.blockDim = dim3(32 * kBatchYSeg, 1, 1);
+    cfg.dynamicSmemBytes = b->ysmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = K;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = K > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_batch_y<T, ADJ>, bp);
 }
+
+// One launch per cluster size (a cluster of K CTAs per item of that size).
+// The classes are independent: the one with the most CTAs runs on s, the
+// others on side streams forked from s and joined back into it, so that the
+// few long-latency CTAs of the short-column classes overlap the large class
+// instead of running after it.
+template <class T, bool ADJ>
+cudaError_t launch_pass_y(mol_batch_ctx *b, const BatchPass &bp, cudaStream_t s)
+{
+    int main_k = -1, nside = 0;
+    for (int k = 0; k < 4; ++k)
+        if (b->ycls_count[k] > 0 && (main_k < 0 || (int64_t)b->ycls_count[k] << k >
+                                                       (int64_t)b->ycls_count[main_k] << main_k))
+            main_k = k;
+    if (main_k < 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4; ++k) nside += (k != main_k && b->ycls_count[k] > 0) ? 1 : 0;
+    if (nside > 0) {
+        for (int j = 0; j < 3 && e == cudaSuccess; ++j)
+            if (!b->ys[j]) e = cudaStreamCreateWithFlags(&b->ys[j], cudaStreamNonBlocking);
+        for (int j = 0; j < 4 && e == cudaSuccess; ++j)
+            if (!b->yev[j]) e = cudaEventCreateWithFlags(&b->yev[j], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(b->yev[0], s);
+        int j = 0;
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            if (k == main_k || b->ycls_count[k] == 0) continue;
+            e = cudaStreamWaitEvent(b->ys[j], b->yev[0], 0);
+            if (e == cudaSuccess) e = launch_y_class<T, ADJ>(b, bp, k, b->ys[j]);
+            if (e == cudaSuccess) e = cudaEventRecord(b->yev[1 + j], b->ys[j]);
+            ++j;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_y_class<T, ADJ>(b, bp, main_k, s);
+    for (int j = 0; j < nside && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s, b->yev[1 + j], 0);
+    return e;
+}
+
 template <class T, bool ADJ>
 cudaError_t launch_pass_x(const mol_batch_ctx *b, BatchPass bp, cudaStream_t s)
 {
@@ -317,7 +400,7 @@ mol_status run_pass(mol_batch_ctx *b, int axis, const BatchPass &bp, cudaStream_
         else e = b->tbytes == 4 ? launch_pass_x<float, false>(b, bp, s) : launch_pass_x<double, false>(b, bp, s);
     }
     if (e != cudaSuccess) return bcuda(b, e, "batched pass launch");
-    b->launches += (axis == 1) ? 1 : b->x_launches();
+    b->launches += (axis == 1) ? b->y_launches() : b->x_launches();
     if (b->timing) {
         BCK(cudaEventRecord(e1, s), "event record");
         b->ev_used.push_back({axis, {e0, e1}});
@@ -516,7 +599,7 @@ mol_status plan_batch(mol_batch_ctx *b, int nprob, const mol_grid *grids, const 
         axis_constants(nux, nx, BC_DIRICHLET, quad, pb.ax);
         axis_constants(nuy, ny, BC_DIRICHLET, quad, pb.ay);
         pb.rpt_x = pick_rpt_x(nx);
-        pb.rpt_y = pick_rpt_y(ny);
+        pick_y(ny, 0, b->tbytes, pb.ky, pb.rpt_y);
         for (int k = 0; k < 5; ++k) {
             pb.ax.dm[k] = std::exp(-nux * (double)pb.rpt_x * (double)(1 << k));
             pb.ay.dm[k] = std::exp(-nuy * (double)pb.rpt_y * (double)(1 << k));
@@ -629,15 +712,12 @@ mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, c
     }
     {
         std::vector<int> rp(b->nrows);
-        std::vector<int2> it;
-        it.reserve(b->nitems_y);
         std::vector<long long> uo(nprob + 1);
         for (int i = 0; i < nprob; ++i) {
             const BatchProb &pb = b->hp[i];
             for (int r = 0; r < pb.ay.n; ++r) rp[pb.row0 + r] = i;
-            for (int c0 = 0; c0 < pb.ax.n; c0 += 32) it.push_back(make_int2(i, c0));
         }
-        it = order_y_items(b->hp, it, std::min(b->nitems_y, b->num_sms));
+        const std::vector<int2> it = y_work_list(b);
         for (int i = 0; i <= nprob; ++i) uo[i] = b->uoff[i];
         if ((st = balloc(b, (void **)&b->probs, sizeof(BatchProb) * nprob)) != MOL_OK) goto bad;
         if ((st = balloc(b, (void **)&b->row_prob, sizeof(int) * rp.size())) != MOL_OK) goto bad;
@@ -669,7 +749,7 @@ mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, c
     }
     {
         // launch shapes: x pass W warps per CTA with two CTAs per SM when the
-        // field buffers allow it; y pass one 16-warp CTA per SM
+        // field buffers allow it; y pass clusters of 4-warp CTAs per column group
         b->nbuf = b->Pmax;
         b->smem_sm = smem_sm;
         b->smem_blk = smem_blk;
@@ -678,7 +758,6 @@ mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, c
             while (W > 1 && !set_x_shape(b, L, W)) --W;
             if (!set_x_shape(b, L, W)) { st = bfail(b, MOL_EINVAL, "x-pass buffers exceed shared memory"); goto bad; }
         }
-        b->ygrid = std::min(b->nitems_y, b->num_sms);
         b->ysmem = batch_y_smem((size_t)b->tbytes);
         b->cgrid = (int)std::min<int64_t>((b->nrows + 7) / 8, 8 * (int64_t)b->num_sms);
         e = b->tbytes == 4 ? set_kernel_smem<float>(b) : set_kernel_smem<double>(b);
@@ -751,7 +830,7 @@ mol_status mol_batch_step(mol_batch b, double *u_prev, double *u_cur, int64_t ns
         if ((st = build_graph(b)) != MOL_OK) return st;
         for (; done + 3 <= nsteps; done += 3) {
             BCK(cudaGraphLaunch(b->gexec, s), "graph launch");
-            b->launches += 3 * (1 + b->x_launches());
+            b->launches += 3 * (b->y_launches() + b->x_launches());
         }
     }
     for (; done < nsteps; ++done) {
@@ -938,13 +1017,13 @@ mol_status mol_batch_autotune(mol_batch b, void *stream)
     double besty = 1e30;
     for (int mode : {0, 1, 2}) {
         b->ymode = mode;
-        set_y_segments(b);
+        BCK(set_y_segments(b), "y work list upload");
         BCK(upload(), "table upload");
         if ((st = batch_pass_ms(b, s, t)) != MOL_OK) return st;
         if (t[1] < besty) { besty = t[1]; bestY = mode; }
     }
     b->ymode = bestY;
-    set_y_segments(b);
+    BCK(set_y_segments(b), "y work list upload");
     BCK(upload(), "table upload");
     b->tune_ms[1] = besty;
     b->launches = launches0;
@@ -969,7 +1048,7 @@ mol_status mol_batch_set_tuning(mol_batch b, int x_warps_short, int x_warps_long
     b->xsplit = x_warps_long == 0 ? 1 : 0;
     b->ymode = y_rule;
     set_x_segments(b);
-    set_y_segments(b);
+    BCK(set_y_segments(b), "y work list upload");
     BCK(cudaDeviceSynchronize(), "synchronise before the table upload");
     BCK(upload_table(b), "table upload");
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }

@@ -28,7 +28,8 @@
 namespace molt {
 
 constexpr int BMAXP = 5;            // highest P of a batched problem
-constexpr int kBatchYWarps = 16;    // segments per column group in the y pass
+constexpr int kBatchYSeg = 4;       // y pass: warps (segments) per CTA; a column group takes a
+                                    // cluster of ky such CTAs
 constexpr int kBatchDpowPad = 64;   // table entries past d^n (read, multiplied by zero, by the exchange)
 constexpr int kBatchMaxN = 1024;    // longest line of a batched problem
 
@@ -51,7 +52,7 @@ struct BatchProb {
     float nbGL, nbG1L;               // sum_{k<=kl} d^(2k+1), sum_{1<=k<=kl} d^(2k)
     float nbdk, nbdk1, nbdkp;        // d^kl, d^(kl-1) (0 when kl = 0), d^(kl+1)
     int ynb;
-    int pad2_;
+    int ky;                          // y pass: CTAs (of kBatchYSeg warps) per column group
 
     template <class T> __device__ T ccu(int t) const
     {
@@ -582,7 +583,7 @@ __device__ __forceinline__ void bsolve(const StridedCtx<T> &c, const AxisDev &A,
     if (rag && kl < RPT) YL[c.lane] = ylast;
     T eout, e00;
     strided_anticausal<T, RPT>(c, ER, eout, e00);      // its barrier publishes YL
-    const T yl = YL[c.lane];
+    const T yl = peer_of(c, YL, (c.Gd - 1) / c.S)[c.lane];   // written by the CTA holding the last point
     const T mu = A.cmu<T>(), inv = A.cinv<T>();
     const T Acoef = (mu * yl - e00) * inv;
     const T Z = (mu * e00 - yl) * inv;
@@ -746,19 +747,23 @@ __device__ __forceinline__ void batch_cols(const BatchProb &pb, const ProgParams
 // segments (ynb, set on the host).  Float32 only.
 template <int RPT>
 __device__ __forceinline__ void batch_cols_nb(const BatchProb &pb, const ProgParams &pr, int col0, int w, int lane,
-                                              float *slots)
+                                              float *slots, int S, int K, int krank, cg::cluster_group &cl)
 {
     constexpr int H = RPT / 2;
-    constexpr int S = kBatchYWarps;
     constexpr bool TWO = RPT >= 8;                  // two-chain recurrences on the full segments
     const AxisDev &A = pb.ay;
     const NbConsts &nc = pb.nby;
     const int n = A.n, Gd = (n + RPT - 1) / RPT, Ld = Gd - 1;
-    const int seg = w, a = seg * RPT;
+    const int seg = krank * S + w, a = seg * RPT;
     const bool full = seg < Gd;
     const int kl = n - 1 - a;
     const bool rag = full && kl <= RPT;
     const bool left_end = seg == 0, last = seg == Ld;
+    // a segment's slots ([2][S][5][32] per CTA), in its CTA of the cluster
+    auto slot = [&](int buf, int sg) -> float * {
+        float *q = slots + ((size_t)buf * S + sg % S) * 160;
+        return K > 1 ? cl.map_shared_rank(q, sg / S) : q;
+    };
     const bool hasL = full && seg > 0, hasR = full && seg < Ld, rlast = seg == Ld - 1;
     const int col = col0 + lane;
     const bool io = full && col < pb.ax.n;
@@ -835,21 +840,22 @@ __device__ __forceinline__ void batch_cols_nb(const BatchProb &pb, const ProgPar
         }
         const float ER0 = z[0] + d * ER1;
 
-        float *mine = slots + ((size_t)(p & 1) * S + seg) * 160;
+        float *mine = slots + ((size_t)(p & 1) * S + w) * 160;
         mine[lane] = E;
         mine[32 + lane] = Y2;
         mine[64 + lane] = ER0;
         mine[96 + lane] = ER1;
         mine[128 + lane] = YL0;
-        __syncthreads();
+        if (K > 1) cl.sync();
+        else __syncthreads();
         float EL = 0.f, Y2L = 0.f, ER0R = 0.f, ER1R = 0.f, YLR = 0.f;
         if (hasL) {
-            const float *q = slots + ((size_t)(p & 1) * S + seg - 1) * 160;
+            const float *q = slot(p & 1, seg - 1);
             EL = q[lane];
             Y2L = q[32 + lane];
         }
         if (hasR) {
-            const float *q = slots + ((size_t)(p & 1) * S + seg + 1) * 160;
+            const float *q = slot(p & 1, seg + 1);
             ER0R = q[64 + lane];
             ER1R = q[96 + lane];
             YLR = q[128 + lane];
@@ -919,59 +925,72 @@ __device__ __forceinline__ void batch_cols_nb(const BatchProb &pb, const ProgPar
     }
 }
 
-// ADJ: powers of D_y^T (the adjoint step) instead of D_y
+// One column group (32 neighbouring columns of one problem, the work-list
+// item of blockIdx.x) per cluster of ky = gridDim.y CTAs of kBatchYSeg warps;
+// warp w of cluster rank k owns segment k kBatchYSeg + w of rpt_y rows.  The
+// launch takes the items of one cluster size; small CTAs (four per SM at 128
+// registers) let the loads of some column groups overlap the sweeps of
+// others.  Float32 forward passes exchange once per sweep between
+// neighbouring segments where that is exact (batch_cols_nb), the others
+// carry through every segment (batch_cols).
+// ADJ: powers of D_y^T (the adjoint step) instead of D_y.
 template <class T, bool ADJ>
-__global__ void __launch_bounds__(32 * kBatchYWarps, 1) k_batch_y(BatchPass bp)
+__global__ void __launch_bounds__(32 * kBatchYSeg, sizeof(T) == 4 ? 4 : 2) k_batch_y(BatchPass bp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(16) BatchProb pbs;
-    StridedCtx<T> c{cg::this_cluster()};
-    c.S = kBatchYWarps;
-    c.K = 1;
-    c.krank = 0;
+    cg::cluster_group cl = cg::this_cluster();
+    const int2 item = bp.items[blockIdx.x];
+    // the problem's constants are read where they are used (through L1): a
+    // copy of the whole table entry would cost each short-lived CTA a round trip
+    const BatchProb &pbs = bp.probs[item.x];
+    const int K = (int)gridDim.y;
+    StridedCtx<T> c{cl};
+    c.S = kBatchYSeg;
+    c.K = K;
+    c.krank = K > 1 ? (int)cl.block_rank() : 0;
     c.w = threadIdx.x >> 5;
     c.lane = threadIdx.x & 31;
-    c.seg = c.w;
-    {
+    c.seg = c.krank * c.S + c.w;
+    bool done = false;
+    if constexpr (sizeof(T) == 4 && !ADJ) {
+        if (pbs.ynb) {
+            float *slots = reinterpret_cast<float *>(smem_raw);
+            switch (pbs.rpt_y) {
+            case 4: batch_cols_nb<4>(pbs, bp.pr, item.y, c.w, c.lane, slots, c.S, K, c.krank, cl); break;
+            case 8: batch_cols_nb<8>(pbs, bp.pr, item.y, c.w, c.lane, slots, c.S, K, c.krank, cl); break;
+            case 16: batch_cols_nb<16>(pbs, bp.pr, item.y, c.w, c.lane, slots, c.S, K, c.krank, cl); break;
+            case 32: batch_cols_nb<32>(pbs, bp.pr, item.y, c.w, c.lane, slots, c.S, K, c.krank, cl); break;
+            default: batch_cols_nb<64>(pbs, bp.pr, item.y, c.w, c.lane, slots, c.S, K, c.krank, cl); break;
+            }
+            done = true;
+        }
+    }
+    if (!done) {
         T *p = reinterpret_cast<T *>(smem_raw);
         c.sl.E = p;
         c.sl.ER = p + c.S * 32;
         c.sl.H = p + 2 * c.S * 32;
         c.sl.Tot = p + 10 * c.S * 32;
-    }
-    T *YL = reinterpret_cast<T *>(smem_raw + strided_slot_bytes(kBatchYWarps, sizeof(T)));
-    for (int it = blockIdx.x; it < bp.nitems; it += gridDim.x) {
-        const int2 item = bp.items[it];
-        __syncthreads();                               // the previous item is done with pbs and the slots
-        if (threadIdx.x < 32) warp_copy(&pbs, bp.probs + item.x, threadIdx.x);
-        __syncthreads();
-        if constexpr (sizeof(T) == 4 && !ADJ) {
-            if (pbs.ynb) {
-                float *slots = reinterpret_cast<float *>(smem_raw);
-                switch (pbs.rpt_y) {
-                case 4: batch_cols_nb<4>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
-                case 8: batch_cols_nb<8>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
-                case 16: batch_cols_nb<16>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
-                case 32: batch_cols_nb<32>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
-                default: batch_cols_nb<64>(pbs, bp.pr, item.y, c.w, c.lane, slots); break;
-                }
-                continue;
-            }
-        }
+        T *YL = reinterpret_cast<T *>(smem_raw + strided_slot_bytes(c.S, sizeof(T)));
         switch (pbs.rpt_y) {
         case 4: batch_cols<T, 4, ADJ>(pbs, bp.pr, item.y, c, YL); break;
         case 8: batch_cols<T, 8, ADJ>(pbs, bp.pr, item.y, c, YL); break;
         case 16: batch_cols<T, 16, ADJ>(pbs, bp.pr, item.y, c, YL); break;
         case 32: batch_cols<T, 32, ADJ>(pbs, bp.pr, item.y, c, YL); break;
-        default: batch_cols<T, 64, ADJ>(pbs, bp.pr, item.y, c, YL); break;
+        default:
+            if constexpr (sizeof(T) == 4) batch_cols<T, 64, ADJ>(pbs, bp.pr, item.y, c, YL);
+            break;
         }
     }
+    // peers read this CTA's shared memory after the last exchange: no CTA
+    // of the cluster exits before all of them are past those reads
+    if (K > 1) cl.sync();
 }
 
 inline size_t batch_y_smem(size_t tsize)
 {
-    const size_t full = strided_slot_bytes(kBatchYWarps, tsize) + 32 * tsize;
-    const size_t nb = (size_t)2 * kBatchYWarps * 5 * 32 * sizeof(float);   // batch_cols_nb's slots
+    const size_t full = strided_slot_bytes(kBatchYSeg, tsize) + 32 * tsize;
+    const size_t nb = (size_t)2 * kBatchYSeg * 5 * 32 * sizeof(float);   // batch_cols_nb's slots
     return full > nb ? full : nb;
 }
 inline size_t batch_x_smem(size_t tsize, int W, int nbuf, bool large)

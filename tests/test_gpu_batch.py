@@ -153,12 +153,15 @@ def test_batch_launches_and_pass_times():
     n0 = b.launches
     b.step(u, v, 3)
     b.sync()
-    # two level conversions in, two out; per step one y pass and the x pass
-    # (one launch per length class present: rows of <= 256 points, 257..512,
-    # longer rows)
+    # two level conversions in, two out; per step the y pass (one launch per
+    # cluster size present: columns of <= 256 points on one 4-warp CTA,
+    # 257..512 on two, longer on four) and the x pass (one launch per length
+    # class present: rows of <= 256 points, 257..512, longer rows)
+    y_launches = (int(any(s[0] <= 256 for s in SHAPES)) + int(any(256 < s[0] <= 512 for s in SHAPES))
+                  + int(any(s[0] > 512 for s in SHAPES)))
     x_launches = (int(any(s[1] <= 256 for s in SHAPES)) + int(any(256 < s[1] <= 512 for s in SHAPES))
                   + int(any(s[1] > 512 for s in SHAPES)))
-    assert b.launches - n0 == 4 + 3 * (1 + x_launches)
+    assert b.launches - n0 == 4 + 3 * (y_launches + x_launches)
     b.set_pass_timing(True)
     b.step(u, v, 2)
     t = b.pass_times()
