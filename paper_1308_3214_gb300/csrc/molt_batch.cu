@@ -51,6 +51,7 @@ struct mol_batch_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t ys[3] = {nullptr, nullptr, nullptr};   // y pass: side streams of the cluster-size classes
     cudaEvent_t yev[4] = {nullptr, nullptr, nullptr, nullptr};   // their fork and joins
+    cudaEvent_t xev[3] = {nullptr, nullptr, nullptr};            // x pass: fork and joins of its classes
     cudaGraphExec_t gexec = nullptr;
     int64_t launches = 0;
     bool timing = false;
@@ -130,6 +131,10 @@ void bfree_all(mol_batch_ctx *b)
     for (int k = 0; k < 4; ++k) {
         if (b->yev[k]) cudaEventDestroy(b->yev[k]);
         b->yev[k] = nullptr;
+    }
+    for (int k = 0; k < 3; ++k) {
+        if (b->xev[k]) cudaEventDestroy(b->xev[k]);
+        b->xev[k] = nullptr;
     }
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
@@ -333,30 +338,56 @@ cudaError_t launch_pass_y(mol_batch_ctx *b, const BatchPass &bp, cudaStream_t s)
     return e;
 }
 
+// The x pass: rows of short lines (one warp per row, persistent), rows of
+// 257..512 points and longer rows (one CTA per row, or persistent warps),
+// one launch per length class.  The classes are independent: the long rows
+// (most of the work) run on s, the others on side streams forked from s and
+// joined back into it, so that their launches overlap instead of queueing.
 template <class T, bool ADJ>
-cudaError_t launch_pass_x(const mol_batch_ctx *b, BatchPass bp, cudaStream_t s)
+cudaError_t launch_pass_x(mol_batch_ctx *b, BatchPass bp, cudaStream_t s)
 {
-    // rows of short lines, then rows of long lines (each a persistent launch)
-    bp.row_begin = 0;
-    bp.nitems = (int)b->one_warp_end();
-    if (bp.nitems > 0) k_batch_x<T, false, ADJ><<<b->xgrid[0], 32 * b->xW[0], b->xsmem[0], s>>>(bp, b->nbuf);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (b->xmid && b->rows_mid > b->rows_small) {
-        bp.row_begin = (int)b->rows_small;
-        bp.nitems = (int)b->rows_mid;
-        k_batch_xs<T, 8, 2, ADJ><<<(unsigned)(b->rows_mid - b->rows_small), 64, b->xs8_smem, s>>>(bp);
+    const bool c0 = b->one_warp_end() > 0, c1 = b->xmid && b->rows_mid > b->rows_small, c2 = b->nrows > b->rows_mid;
+    const int nside = (c0 ? 1 : 0) + (c1 ? 1 : 0);
+    cudaError_t e = cudaSuccess;
+    cudaStream_t side[2] = {s, s};
+    if (c2 && nside > 0) {
+        for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+            if (!b->ys[j]) e = cudaStreamCreateWithFlags(&b->ys[j], cudaStreamNonBlocking);
+        for (int j = 0; j < 3 && e == cudaSuccess; ++j)
+            if (!b->xev[j]) e = cudaEventCreateWithFlags(&b->xev[j], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(b->xev[0], s);
+        for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+            e = cudaStreamWaitEvent(b->ys[j], b->xev[0], 0);
+            side[j] = b->ys[j];
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (c0) {
+        bp.row_begin = 0;
+        bp.nitems = (int)b->one_warp_end();
+        k_batch_x<T, false, ADJ><<<b->xgrid[0], 32 * b->xW[0], b->xsmem[0], side[0]>>>(bp, b->nbuf);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    bp.row_begin = (int)b->rows_mid;
-    bp.nitems = (int)b->nrows;
-    if (bp.nitems > bp.row_begin) {
+    if (c1) {
+        bp.row_begin = (int)b->rows_small;
+        bp.nitems = (int)b->rows_mid;
+        k_batch_xs<T, 8, 2, ADJ><<<(unsigned)(b->rows_mid - b->rows_small), 64, b->xs8_smem, side[1]>>>(bp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (c2) {
+        bp.row_begin = (int)b->rows_mid;
+        bp.nitems = (int)b->nrows;
         if (b->xsplit)
             k_batch_xs<T, 16, 2, ADJ><<<(unsigned)(b->nrows - b->rows_mid), 64, b->xs_smem, s>>>(bp);
         else
             k_batch_x<T, true, ADJ><<<b->xgrid[1], 32 * b->xW[1], b->xsmem[1], s>>>(bp, b->nbuf);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (nside > 0) {
+            for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(b->xev[1 + j], side[j]);
+            for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s, b->xev[1 + j], 0);
+        }
     }
-    return cudaGetLastError();
+    return e;
 }
 
 template <class T>
