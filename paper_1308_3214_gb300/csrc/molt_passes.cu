@@ -177,12 +177,22 @@ cudaError_t configure_kernels()
     return cudaSuccess;
 }
 
+// Threads of a shared-memory pass CTA: one warp per line for the sweeps; a
+// contiguous-axis grid of one CTA (a single line or a few) takes 512 threads,
+// so that its loads, stores and per-point phases run over 16 warps while the
+// sweeps stay on the lines' own warps.
+template <bool CONTIG>
+static int pass_threads(const PassGeom &G)
+{
+    return (CONTIG && G.nlines <= G.W && G.W < 16) ? 512 : 32 * G.W;
+}
+
 template <class T, int BC, bool CONTIG>
 static cudaError_t run_powers(const AxisDev &A, const PassGeom &G, const PowersParams &p, cudaStream_t s)
 {
     const size_t smem = pass_smem_bytes(false, sizeof(T), G.W, A.ls, A.n, G.dps);
     const int64_t grid = (G.nlines + G.W - 1) / G.W;
-    k_powers<T, BC, CONTIG><<<(unsigned)grid, 32 * G.W, smem, s>>>(A, G, p);
+    k_powers<T, BC, CONTIG><<<(unsigned)grid, pass_threads<CONTIG>(G), smem, s>>>(A, G, p);
     return cudaGetLastError();
 }
 
@@ -191,7 +201,7 @@ static cudaError_t run_horner(const AxisDev &A, const PassGeom &G, const HornerP
 {
     const size_t smem = pass_smem_bytes(true, sizeof(T), G.W, A.ls, A.n, G.dps);
     const int64_t grid = (G.nlines + G.W - 1) / G.W;
-    k_horner<T, BC, CONTIG><<<(unsigned)grid, 32 * G.W, smem, s>>>(A, G, p);
+    k_horner<T, BC, CONTIG><<<(unsigned)grid, pass_threads<CONTIG>(G), smem, s>>>(A, G, p);
     return cudaGetLastError();
 }
 
