@@ -248,6 +248,32 @@ LineSet lineset_of(const mol_ctx *h, int axis)
     return L;
 }
 
+// Launch shape of a shared-memory pass: W lines per CTA, one warp each; a
+// single long contiguous line (1D) is swept by the whole CTA instead,
+// kCtaLineThreads segments of m points (their constants replace the warp's).
+void smem_pass_geom(const mol_ctx *h, int axis, bool horner, PassGeom &G, AxisDev &A)
+{
+    const int n = (int)h->n[axis];
+    G = geom_of(h, axis);
+    G.W = choose_W(h, axis, horner);
+    G.wshift = ilog2(G.W);
+    A = h->ax[axis];
+    A.ls = line_stride(A.ms, G.W, h->tbytes);
+    if (axis == 0 && G.nlines == 1 && n >= 1024) {
+        G.W = 1;
+        G.wshift = 0;
+        G.cta = 1;
+        A.m = (n + kCtaLineThreads - 1) / kCtaLineThreads;
+        A.ms = (A.m % 2 == 0) ? A.m + 1 : A.m;
+        A.mmagic = (unsigned)(((1ull << 32) + (unsigned long long)A.m - 1) / (unsigned long long)A.m);
+        const double nu = -std::log(A.d);
+        for (int k = 0; k < 5; ++k) A.dm[k] = std::exp(-nu * (double)A.m * (double)(1 << k));
+        axis_mirror(A);
+        A.ls = kCtaLineThreads * A.ms;
+    }
+    G.dps = pass_smem_bytes(horner, h->tbytes, G.W, A.ls, A.n, 1) <= h->smem_optin ? 1 : 0;
+}
+
 // Launch one pass program: the register-resident kernel when the line length
 // and boundary condition allow it, else the shared-memory kernels.
 mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersParams *pp, const HornerParams *hp,
@@ -263,12 +289,9 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
     cudaError_t e;
     const bool bcd = hp != nullptr && hp->bcd;      // boundary data: the shared-memory kernels carry it
     if (bcd) {
-        PassGeom G = geom_of(h, axis);
-        G.W = choose_W(h, axis, true);
-        G.wshift = ilog2(G.W);
-        AxisDev A = h->ax[axis];
-        A.ls = line_stride(A.ms, G.W, h->tbytes);
-        G.dps = pass_smem_bytes(true, h->tbytes, G.W, A.ls, A.n, 1) <= h->smem_optin ? 1 : 0;
+        PassGeom G;
+        AxisDev A;
+        smem_pass_geom(h, axis, true, G, A);
         e = launch_horner(h->tbytes, h->bc, axis == 0, A, G, *hp, s);
     } else if (pr.mode == 2 || pr.mode == 3) {
         // the transposed passes of the adjoint step (register kernels only;
@@ -313,12 +336,9 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
         else
             e = launch_strided(h->tbytes, h->bc, rpt, A, L, pr, s);
     } else {
-        PassGeom G = geom_of(h, axis);
-        G.W = choose_W(h, axis, hp != nullptr);
-        G.wshift = ilog2(G.W);
-        AxisDev A = h->ax[axis];
-        A.ls = line_stride(A.ms, G.W, h->tbytes);
-        G.dps = pass_smem_bytes(hp != nullptr, h->tbytes, G.W, A.ls, A.n, 1) <= h->smem_optin ? 1 : 0;
+        PassGeom G;
+        AxisDev A;
+        smem_pass_geom(h, axis, hp != nullptr, G, A);
         e = hp ? launch_horner(h->tbytes, h->bc, axis == 0, A, G, *hp, s)
                : launch_powers(h->tbytes, h->bc, axis == 0, A, G, *pp, s);
     }

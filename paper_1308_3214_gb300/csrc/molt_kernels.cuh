@@ -84,7 +84,11 @@ struct PassGeom {
     int wshift;      // log2(W)
     int dps;         // 1: the d^j table is copied to shared memory; 0 (long lines whose
                      //    buffers leave no room): it is read from global memory
+    int cta;         // 1: one line per CTA of kCtaLineThreads threads, each owning a segment
+                     //    (A.m, A.ms, A.dm describe those segments): sweep_D_cta
 };
+
+constexpr int kCtaLineThreads = 512;   // threads (segments) of a line swept by a whole CTA
 
 constexpr int MAXP = 6;     // P <= 5, Horner steps 0..P
 constexpr int MAXG = 8;     // input fields of a Horner pass
@@ -380,13 +384,168 @@ __device__ void sweep_D(T *buf, const T *rbuf, T cu, const AxisDev &A,
     __syncwarp();
 }
 
+// The same sweep with the line split over the kCtaLineThreads threads of the
+// CTA (thread t owns points t m .. t m + m - 1): the chunk carries combine
+// over the lanes of a warp by shuffles, as in sweep_D, then over the warps
+// through their totals in shared memory (the warps before the last one
+// holding data are full, so a warp spans d^(32 m)).  Every thread of the CTA
+// calls it; the line's n >= 32 m.
+// scratch: 2 kCtaLineThreads / 32 + 3 elements of shared memory.
+template <class T, int MODE, int BC>
+__device__ void sweep_D_cta(T *buf, const T *rbuf, T cu, const AxisDev &A, const T *__restrict__ dp, T *scratch,
+                            T gL = 0, T gR = 0)
+{
+    constexpr int NWC = kCtaLineThreads / 32;
+    T *s_tc = scratch, *s_ta = scratch + NWC, *s_bc = scratch + 2 * NWC;
+    const int tt = threadIdx.x, lane = tt & 31, warp = tt >> 5;
+    const int n = A.n, m = A.m, ms = A.ms;
+    const T d = A.cd<T>(), c1 = A.cc1<T>(), c2 = A.cc2<T>();
+    const int a = tt * m;
+    const int b = min(a + m, n);
+    const int cnt = b > a ? b - a : 0;
+    T *seg = buf + tt * ms;
+    const T *rseg = rbuf + tt * ms;
+    const T D32 = A.cdm<T>(4) * A.cdm<T>(4);          // d^(32 m): across one full warp
+
+    // ---- halo values from neighbouring segments (other warps' too), read
+    // before any write ----
+    T h_l2 = 0, h_l1 = 0, h_r0 = 0, h_r1 = 0;
+    if (cnt > 0) {
+        h_l1 = buf[spos<BC>(a - 1, A)];
+        h_r0 = buf[spos<BC>(b, A)];
+        if (MODE != 0) {
+            h_l2 = buf[spos<BC>(a - 2, A)];
+            h_r1 = buf[spos<BC>(b + 1, A)];
+        }
+    }
+    __syncthreads();
+
+    // ---- q_j and the causal reduction of this segment (as sweep_D) ----
+    T E = 0;
+    if (cnt > 0) {
+        T sm1, s0, z0 = 0, zp1 = 0;
+        if (MODE == 0) {
+            sm1 = h_l1;
+            s0 = seg[0];
+        } else {
+            T zm1 = h_l1;
+            z0 = seg[0];
+            zp1 = cnt > 1 ? seg[1] : h_r0;
+            sm1 = (z0 - zm1) - (zm1 - h_l2);
+            s0 = (zp1 - z0) - (z0 - zm1);
+            if (MODE == 2) {
+                sm1 += cu * rbuf[spos<BC>(a - 1, A)];
+                s0 += cu * rseg[0];
+            }
+        }
+        for (int k = 0; k < cnt; ++k) {
+            const int j = a + k;
+            T sp1;
+            if (MODE == 0) {
+                sp1 = (k + 1 < cnt) ? seg[k + 1] : h_r0;
+            } else {
+                T zp2 = (k + 2 < cnt) ? seg[k + 2] : (k + 2 == cnt ? h_r0 : h_r1);
+                sp1 = (zp2 - zp1) - (zp1 - z0);
+                if (MODE == 2) sp1 += cu * ((k + 1 < cnt) ? rseg[k + 1] : rbuf[spos<BC>(b, A)]);
+                z0 = zp1;
+                zp1 = zp2;
+            }
+            T q;
+            if (BC == BC_DIRICHLET) {
+                T sl = (j - 1 < 1) ? s0 : sm1;
+                T sr = (j + 1 > n - 2) ? s0 : sp1;
+                q = (j == 0 || j == n - 1) ? (T)0 : c1 * s0 + c2 * (sl + sr);
+            } else {
+                q = c1 * s0 + c2 * (sm1 + sp1);
+            }
+            seg[k] = q;
+            E = d * E + q;
+            sm1 = s0;
+            s0 = sp1;
+        }
+    }
+
+    // ---- causal carries: y at a-1, over the lanes, then over the warps ----
+    __syncwarp();
+    T x = E;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        T y = __shfl_up_sync(0xffffffffu, x, 1 << k);
+        if (lane >= (1 << k)) x += A.cdm<T>(k) * y;
+    }
+    T excl = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) excl = 0;
+    if (lane == 31) s_tc[warp] = x;
+    __syncthreads();
+    {
+        T win = 0;                                          // y just before this warp
+        for (int w = 0; w < warp; ++w) win = D32 * win + s_tc[w];
+        excl += dp[lane * m] * win;
+    }
+    const int Ld = (n - 1) / m;        // last thread holding data
+    T y = excl;
+    if (BC == BC_PERIODIC) {
+        if (tt == Ld) s_bc[0] = dp[cnt] * excl + E;        // zero-inflow y_{n-1}
+        __syncthreads();
+        const T y_m1 = s_bc[0] * A.cinv<T>();              // y_{-1} over all images
+        if (cnt > 0) y += dp[a] * y_m1;
+    }
+
+    // ---- causal scan of the segment; anti-causal reduction ----
+    T ER = 0, pw = 1;
+    for (int k = 0; k < cnt; ++k) {
+        y = d * y + seg[k];
+        seg[k] = y;
+        ER += pw * y;
+        pw *= d;
+    }
+
+    // ---- anti-causal carries: e at b, over the lanes, then over the warps ----
+    __syncwarp();
+    T xb = ER;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        T t2 = __shfl_down_sync(0xffffffffu, xb, 1 << k);
+        if (lane + (1 << k) < 32) xb += A.cdm<T>(k) * t2;
+    }
+    T exclb = __shfl_down_sync(0xffffffffu, xb, 1);
+    if (lane == 31) exclb = 0;
+    if (lane == 0) s_ta[warp] = xb;
+    if (BC == BC_DIRICHLET && tt == Ld) s_bc[1] = y;       // y_{n-1} = zero-inflow e_{n-1}
+    __syncthreads();
+    T wout = 0;                                             // e at the first point after this warp
+    for (int w = NWC - 1; w > warp; --w) wout = D32 * wout + s_ta[w];
+    exclb += dp[(31 - lane) * m] * wout;
+    if (tt == 0) s_bc[2] = xb + D32 * wout;                // zero-inflow e_0
+    __syncthreads();
+    const T e00 = s_bc[2];
+    T Z, Acoef = 0;
+    if (BC == BC_DIRICHLET) {
+        const T ylast = s_bc[1];
+        const T mu = A.cmu<T>(), inv = A.cinv<T>();
+        Acoef = (mu * ylast - e00) * inv + (gL - mu * gR) * inv;   // A': e_0 = gL
+        Z = (mu * e00 - ylast) * inv + (gR - mu * gL) * inv;       // B': e_{n-1} = gR
+    } else {
+        Z = d * e00 * A.cinv<T>();                         // d * e_n, e_n = e_0 over all images
+    }
+    T acc = d * exclb + (cnt > 0 ? dp[n - b] * Z : (T)0);
+    for (int k = cnt - 1; k >= 0; --k) {
+        T e = acc + seg[k];
+        acc = d * e;
+        if (BC == BC_DIRICHLET) e += Acoef * dp[a + k];
+        seg[k] = e;
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // CTA helpers
 // ---------------------------------------------------------------------------
 // Shared-memory carve-out of a pass CTA: `arrays` line buffers of W lines,
-// the d^j table (n+1 values; none when dps == 0) and the W line base offsets.
+// the d^j table (n+1 values; none when dps == 0), the W line base offsets and
+// the carry scratch of sweep_D_cta.
 struct SmemLayout {
-    size_t lines, dpow, lbase, total;
+    size_t lines, dpow, lbase, scratch, total;
 };
 __host__ __device__ inline size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline SmemLayout smem_layout(int arrays, int W, int ls, int n, size_t tsize, int dps = 1)
@@ -395,7 +554,8 @@ __host__ __device__ inline SmemLayout smem_layout(int arrays, int W, int ls, int
     L.lines = 0;
     L.dpow = round16((size_t)arrays * W * ls * tsize);
     L.lbase = L.dpow + (dps ? round16((size_t)(n + 1) * tsize) : 0);
-    L.total = L.lbase + round16((size_t)W * sizeof(int64_t));
+    L.scratch = L.lbase + round16((size_t)W * sizeof(int64_t));
+    L.total = L.scratch + round16((size_t)(2 * kCtaLineThreads / 32 + 3) * tsize);
     return L;
 }
 __device__ __forceinline__ int64_t line_base(const PassGeom &G, int64_t L, int n)
@@ -508,7 +668,11 @@ __global__ void __launch_bounds__(512) k_powers(AxisDev A, PassGeom G, PowersPar
 
     T *mine = lines + (size_t)warp * A.ls;
     for (int p = 1; p <= prm.P; ++p) {
-        if (warp < nl) {
+        if (G.cta) {
+            T *scr = reinterpret_cast<T *>(smem_raw + SL.scratch);
+            if (p == 1) sweep_D_cta<T, 0, BC>(lines, lines, (T)0, A, dp, scr);
+            else sweep_D_cta<T, 1, BC>(lines, lines, (T)0, A, dp, scr);
+        } else if (warp < nl) {
             if (p == 1) sweep_D<T, 0, BC>(mine, mine, (T)0, A, dp, lane);
             else sweep_D<T, 1, BC>(mine, mine, (T)0, A, dp, lane);
         }
@@ -612,7 +776,11 @@ __global__ void __launch_bounds__(512) k_horner(AxisDev A, PassGeom G, HornerPar
                 }
             });
             __syncthreads();
-            if (t > 0 && warp < nl)
+            if (t > 0 && G.cta)
+                sweep_D_cta<T, 2, BC>(lines, rlines, (T)prm.cu[o][t], A, dp,
+                                      reinterpret_cast<T *>(smem_raw + SL.scratch), prm.bcd ? (T)prm.bgL[t] : (T)0,
+                                      prm.bcd ? (T)prm.bgR[t] : (T)0);
+            else if (t > 0 && warp < nl)
                 sweep_D<T, 2, BC>(mine, rmine, (T)prm.cu[o][t], A, dp, lane, prm.bcd ? (T)prm.bgL[t] : (T)0,
                                   prm.bcd ? (T)prm.bgR[t] : (T)0);
             __syncthreads();

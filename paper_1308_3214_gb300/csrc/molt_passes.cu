@@ -184,7 +184,7 @@ cudaError_t configure_kernels()
 template <bool CONTIG>
 static int pass_threads(const PassGeom &G)
 {
-    return (CONTIG && G.nlines <= G.W && G.W < 16) ? 512 : 32 * G.W;
+    return (G.cta || (CONTIG && G.nlines <= G.W && G.W < 16)) ? kCtaLineThreads : 32 * G.W;
 }
 
 template <class T, int BC, bool CONTIG>
