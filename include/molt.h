@@ -396,9 +396,11 @@ mol_status mol_pass_times(mol_handle h, double total_ms[3], int64_t launches[3])
  * Batches of independent 2D problems
  *
  * Many Dirichlet problems of uneven size stepped together: every pass runs
- * all problems in one persistent launch over a flat work list (rows for
- * the x pass, groups of 32 columns for the y pass), and mol_batch_step
- * captures its time loop in a CUDA graph.  Problem i has its own grid
+ * all problems in a few launches over flat work lists (the x pass one per
+ * row-length class, over the rows; the y pass one per cluster size, a
+ * cluster of CTAs per group of 32 columns), the launches of a pass running
+ * concurrently on streams forked from the caller's and joined back into it;
+ * mol_batch_step captures its time loop in a CUDA graph.  Problem i has its own grid
  * (ndim = 2, 3 <= n <= 1024 per axis), c, dt, beta and P; all share the
  * boundary condition (homogeneous Dirichlet only) and the precision.  Each
  * problem follows the same scheme as a single mol_create handle (eq.
@@ -485,9 +487,9 @@ int64_t mol_batch_launch_count(mol_batch b);
  * than 512 points, which are also timed split over the two warps of one CTA
  * per row; rows of 257..512 points always run split, 8-point segments, when
  * their buffers fit shared memory, else with the short rows), then the y pass
- * with each problem's segment length at the smallest RPT covering the column
- * with 16 warps or at twice that, on the batch's own workspace, and keeps
- * the fastest.  Synchronous; the caller's fields are not touched.
+ * with each problem's columns on the fewest 4-warp CTAs whose segments cover
+ * them, on twice as many, and with full carries only, on the batch's own
+ * workspace, and keeps the fastest.  Synchronous; the caller's fields are not touched.
  * mol_batch_get_tuning: out[0], out[1] = warps per CTA of the two x launches
  * (out[1] = 0: the long rows run split, one CTA of two warps per row),
  * out[2] = y rule: bit 0 the segment length (0 smallest, 1 doubled), bit 1

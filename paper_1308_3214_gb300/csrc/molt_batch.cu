@@ -1,6 +1,7 @@
 // molt_batch.cu -- the batched C ABI (mol_batch_* in include/molt.h): many
-// independent 2D Dirichlet problems of uneven size stepped together, one
-// persistent launch per pass, the time loop captured in a CUDA graph.
+// independent 2D Dirichlet problems of uneven size stepped together, a few
+// concurrent launches per pass over flat work lists, the time loop captured
+// in a CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -140,7 +141,7 @@ void bfree_all(mol_batch_ctx *b)
     b->allocs.clear();
 }
 
-// segment lengths: x pass 32 lanes x rpt >= nx; y pass 16 warps x rpt >= ny
+// segment lengths: x pass 32 lanes x rpt >= nx (pick_y below for the y pass)
 int pick_rpt_x(int n)
 {
     int r = 4;

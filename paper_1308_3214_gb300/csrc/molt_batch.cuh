@@ -5,17 +5,19 @@
 // the per-axis D_gamma): a y pass forming g_k = D_y^{k+1} u (k < P_i), then an
 // x pass evaluating F = sum_t D_x^t (f_t0 u + sum_k f_t,k+1 g_k) by Horner's
 // rule with the level combination u^{n+1} = ea u^n + eb u^{n-1} + ec F fused
-// in (eq. update_P).  Each pass runs every problem in ONE persistent launch
-// over a flat work list:
+// in (eq. update_P).  Each pass runs every problem in a few launches over
+// flat work lists:
 //
 //  * x pass: one warp per row; the rows of all problems form the list (the
 //    problem of a row is looked up, its constants copied to shared memory).
 //    A lane owns a segment of RPT_i points, RPT_i the smallest of 4..32 with
 //    32 RPT_i >= nx_i, so short rows keep most lanes busy; the row's input
 //    fields are copied once into shared memory with cp.async.
-//  * y pass: one CTA of 16 warps per group of 32 neighbouring columns (lane =
-//    column, warp = segment of RPT_i rows, RPT_i the smallest of 4..64 with
-//    16 RPT_i >= ny_i); carries cross the segments through shared memory.
+//  * y pass: a cluster of K_i CTAs of kBatchYSeg warps per group of 32
+//    neighbouring columns (lane = column, warp = segment of RPT_i rows,
+//    kBatchYSeg K_i RPT_i >= ny_i), one launch per cluster size; carries cross
+//    the segments through shared and distributed shared memory, or one
+//    neighbour exchange per sweep where that is exact (batch_cols_nb).
 //
 // Line lengths are arbitrary: the segment routines' RAG variants handle the
 // last point anywhere in a segment.  Fields live in an internal layout whose
