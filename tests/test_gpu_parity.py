@@ -420,6 +420,43 @@ def test_programmatic_dependent_launch_is_bitwise_neutral(shape, P, bc):
     s.close()
 
 
+# A single contiguous line of >= 1024 points whose length no register kernel
+# takes is swept by the whole CTA (512 segments, carries over lanes and warps):
+# powers, F and steps against the oracle, both boundary conditions, lengths
+# that leave the last segments partly or wholly empty.
+@pytest.mark.parametrize("n", [1024, 1500, 3001, 5119])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_single_long_line_cta_sweep_matches_oracle(n, bc, prec):
+    P = 3
+    s = make((n,), 1.3 * spacing(n, bc), P, bc, prec)
+    v = field((n,), 95, bc)
+    vd = dev(v)
+    for power in (1, 2, 3):
+        got = s.apply_D(vd, 0, power).cpu().numpy()
+        ref = oracle.D_axis(v, 0, s.nu[0], bc, 2, power=power)
+        assert rel_l2(got, ref) <= tol_for(prec, s, power, cond_of(v, ref)), (power, rel_l2(got, ref))
+    got = s.apply_F(vd).cpu().numpy()
+    ref = oracle.F(v, s.nu, P, s.beta, bc)
+    assert rel_l2(got, ref) <= tol_for(prec, s, 2 * P), rel_l2(got, ref)
+    u0 = smooth_field((n,), 96, bc) + 0.05 * field((n,), 97, bc)
+    u1 = oracle.start(u0, s.nu, P, s.beta, bc)
+    up, uc = dev(u0), dev(u1)
+    nsteps = 8
+    s.step(up, uc, nsteps)
+    rp, rc = oracle.run(u0, u1, nsteps, s.nu, P, s.beta, bc)
+    tol = 1e-12
+    if prec == "mixed":
+        Fsum, a, b = 0.0, u0, u1
+        for _ in range(nsteps):
+            F = oracle.F(b, s.nu, P, s.beta, bc)
+            Fsum += np.linalg.norm(F)
+            a, b = b, 2 * b - a + F
+        tol = 8 * EPS32 * (1 + 1 / (1 - max(s.d))) * 2 * P * Fsum / np.linalg.norm(rc)
+    assert rel_l2(uc.cpu().numpy(), rc) <= tol
+    s.close()
+
+
 # ---------------------------------------------------------------------------
 # autotuner
 # ---------------------------------------------------------------------------
