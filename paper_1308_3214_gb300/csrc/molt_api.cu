@@ -311,7 +311,11 @@ mol_status run_program(mol_ctx *h, int axis, const ProgParams &pr, const PowersP
             LineSet L = lineset_of(h, axis);
             L.S = S;
             L.K = K;
-            e = launch_strided(h->tbytes, h->bc, rpt, regs_axis(h, axis, rpt), L, pr, s);
+            const AxisDev A = regs_axis(h, axis, rpt);
+            if (h->tbytes == 4 && h->tune_strided_nb && regs_strided_nb_plan(A.d, n, rpt))
+                e = launch_strided_nb_T(rpt, A, L, pr, s);
+            else
+                e = launch_strided(h->tbytes, h->bc, rpt, A, L, pr, s);
         }
     } else if (axis == 0 && pr.mode == 1 && pr.nout == 1 && h->tune_rows_warps > 0 &&
         regs_rows_plan(h->tbytes, n, pr.ng, h->tune_rows_warps, &rpt)) {

@@ -94,6 +94,9 @@ cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &
 // rows staged in shared memory once per CTA (where two CTAs per SM still fit).
 cudaError_t launch_strided_nb_h(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
                                 cudaStream_t s, bool gtile);
+// The transposed strided powers (the adjoint step's y pass, Dirichlet,
+// float32) with one neighbour exchange per sweep, under the same condition.
+cudaError_t launch_strided_nb_T(int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s);
 // 1 if a bounded wait of a register kernel gave up since the last call (and
 // clears it), 0 if not, -1 if the flag could not be read; synchronizes s.
 int regs_timeout_take(cudaStream_t s);

@@ -361,6 +361,24 @@ cudaError_t launch_strided_nb(int bc, int rpt, const AxisDev &A, const LineSet &
                              : run_strided_nb<BC_DIRICHLET, kStridedRptF2>(A, L, p, s, stage);
 }
 
+cudaError_t launch_strided_nb_T(int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
+{
+    if (p.mode != 2 || p.P < 1 || !regs_strided_nb_plan(A.d, A.n, rpt)) return cudaErrorInvalidValue;
+    auto run = [&](auto kernel, int R) -> cudaError_t {
+        static bool attr[2] = {false, false};
+        bool &done = attr[R == kStridedRptF ? 0 : 1];
+        if (!done) {
+            const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (e != cudaSuccess) return e;
+            done = true;
+        }
+        return launch_pass(kernel, dim3((unsigned)((L.nlines + 31) / 32), (unsigned)L.K, 1), dim3(32 * L.S, 1, 1),
+                           strided_nb_slot_bytes(L.S), s, L, L.K, A, L, p, strided_nb_consts(A.d, R));
+    };
+    if (rpt == kStridedRptF) return run(k_strided_nb_T<kStridedRptF>, kStridedRptF);
+    return run(k_strided_nb_T<kStridedRptF2>, kStridedRptF2);
+}
+
 cudaError_t launch_strided_nb_h(int bc, int rpt, const AxisDev &A, const LineSet &L, const ProgParams &p,
                                 cudaStream_t s, bool gtile)
 {

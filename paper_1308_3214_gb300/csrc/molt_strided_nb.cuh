@@ -103,8 +103,10 @@ struct NbXch {
 
 // One application of D on a segment with one neighbour exchange (the algebra
 // above; the powers kernel below carries the same steps inline, where they
-// compile to fewer registers).  MODE as seg_make_q: 0 z holds s (the first power: hl1 = s at a-1,
-// hr0 = s at a+RPT), 1 s = second difference of z, 2 the same plus cu r.
+// compile to fewer registers).  MODE as seg_make_q: 0 z holds s (the first
+// power: hl1 = s at a-1, hr0 = s at a+RPT), 1 s = second difference of z, 2
+// the same plus cu r; 3 z holds q itself (the solve alone: the transposed
+// operator).
 // hl2, hl1, hr0, hr1: z at a-2, a-1, a+RPT, a+RPT+1 on entry, e there on exit.
 // xch(E, Y2, ER0, ER1, EL, Y2L, ER0R, ER1R) publishes this segment's four
 // numbers, waits for the neighbours' and returns theirs (zeros where there is
@@ -116,10 +118,12 @@ __device__ __forceinline__ void strided_sweep_nb(float (&z)[RPT], RF r, float cu
 {
     constexpr int H = RPT / 2;
     const float d = A.fd, c1 = A.fc1, c2 = A.fc2, inv = A.finv;
-    float zl2 = hl2, zl1 = hl1, zr0 = hr0, zr1 = hr1;
-    if (BC == BC_DIRICHLET) end_ghosts<float, RPT, MODE>(z, left_end, right_end, zl2, zl1, zr0, zr1);
-    seg_make_q<float, RPT, MODE>(z, zl2, zl1, zr0, zr1, r, cu, c1, c2);
-    if (BC == BC_DIRICHLET) end_zero<float, RPT>(z, left_end, right_end);
+    if constexpr (MODE != 3) {
+        float zl2 = hl2, zl1 = hl1, zr0 = hr0, zr1 = hr1;
+        if (BC == BC_DIRICHLET) end_ghosts<float, RPT, MODE>(z, left_end, right_end, zl2, zl1, zr0, zr1);
+        seg_make_q<float, RPT, MODE>(z, zl2, zl1, zr0, zr1, r, cu, c1, c2);
+        if (BC == BC_DIRICHLET) end_zero<float, RPT>(z, left_end, right_end);
+    }
     if (!full) {
 #pragma unroll
         for (int k = 0; k < RPT; ++k) z[k] = 0.f;
@@ -533,6 +537,66 @@ __global__ void __launch_bounds__(256, 2) k_strided_nb_h(AxisDev A, LineSet LS, 
         float *ob = reinterpret_cast<float *>(pr.out[o]);
         if (io) {
             float *po = ob + lbase + (int64_t)a * st;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) { *po = z[k]; po += st; }
+        }
+    }
+    if (K > 1) cl.sync();       // peers may still read this CTA's slots
+}
+
+// Powers of the transposed operator, (D^T)^p u for p = 1..P (Dirichlet lines,
+// the adjoint step's y pass), with one neighbour exchange per sweep: D^T w =
+// Delta^T C^T S w (post_T), where S, the solve of the difference form, is
+// the same recurrence pair with its Dirichlet terms (strided_sweep_nb, MODE 3,
+// on w with its end values dropped) and the halos of e that post_T needs are
+// the exchange's.  u = the level's pair summed.  Launch as k_strided_nb.
+template <int RPT>
+__global__ void __launch_bounds__(256, 2) k_strided_nb_T(AxisDev A, LineSet LS, ProgParams pr, NbConsts nc)
+{
+    static_assert(RPT % 2 == 0 && RPT >= 8, "segment length");
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *slots = reinterpret_cast<float *>(smem_raw);          // [2][S][4][32]
+    cg::cluster_group cl = cg::this_cluster();
+    const int S = LS.S, K = LS.K;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int krank = K > 1 ? (int)cl.block_rank() : 0;
+    const int n = A.n, Gd = n / RPT;
+    const int seg = krank * S + w, a = seg * RPT;
+    const bool full = seg < Gd;
+    const int64_t line = (int64_t)blockIdx.x * 32 + lane;
+    const bool valid = line < LS.nlines;
+    const bool io = valid && full;
+    const int64_t lbase = valid ? (line % LS.inner) + (line / LS.inner) * LS.inner * (int64_t)n : 0;
+    const int64_t st = LS.stride;
+    NbXch<BC_DIRICHLET> xch(slots, cl, S, K, w, lane, seg, Gd);
+    const bool left_end = seg == 0, right_end = seg == Gd - 1;
+    const float c1 = A.fc1, c2 = A.fc2;
+
+    float z[RPT];
+    {
+        const float *H = reinterpret_cast<const float *>(pr.u_hi) + lbase;
+        const float *L = reinterpret_cast<const float *>(pr.u_lo) + lbase;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = io ? H[(int64_t)(a + k) * st] + L[(int64_t)(a + k) * st] : 0.f;
+    }
+    const auto no_r = [](int) { return 0.f; };
+    const int kl = n - 1 - a;
+    for (int p = 1; p <= pr.P; ++p) {
+        // interior rows only, the solve with one exchange, interior rows only
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = (k < kl && (seg > 0 || k > 0)) ? z[k] : 0.f;
+        float hl2 = 0.f, hl1 = 0.f, hr0 = 0.f, hr1 = 0.f;
+        xch.buf = p & 1;
+        strided_sweep_nb<BC_DIRICHLET, RPT, 3>(z, no_r, 0.f, A, nc, full, left_end, right_end, xch.hasL, xch.hasR,
+                                               xch, hl2, hl1, hr0, hr1);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) z[k] = (k < kl && (seg > 0 || k > 0)) ? z[k] : 0.f;
+        if (left_end || right_end) post_T<float, RPT, true>(z, hl2, hl1, hr0, hr1, c1, c2, a, n);
+        else post_T<float, RPT, false>(z, hl2, hl1, hr0, hr1, c1, c2, a, n);
+        float *o = reinterpret_cast<float *>(pr.out[p - 1]);
+        if (o != nullptr && io) {
+            float *po = o + lbase + (int64_t)a * st;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) { *po = z[k]; po += st; }
         }

@@ -356,16 +356,20 @@ def adjoint_bound(tg, shape, rec, nu, P, beta):
     return model(nu, P) * Fsum
 
 
-@pytest.mark.parametrize("shape", [(128, 1024), (192, 2048)])
-def test_single_path_adjoint_mixed_matches_oracle(shape):
+@pytest.mark.parametrize("shape", [(128, 1024), (192, 2048), (256, 1024)])
+@pytest.mark.parametrize("strided_nb", [1, 0])
+def test_single_path_adjoint_mixed_matches_oracle(shape, strided_nb):
     """Mixed-precision handles whose rows split over warps and whose columns
     split into strided segments run F^T, traces and the adjoint on the
     register kernels' transposed modes (not a one-problem batch: the
-    handle's own pass timers see the passes)."""
+    handle's own pass timers see the passes); the transposed y pass with one
+    neighbour exchange per sweep (strided_nb 1) or the full carries (0)."""
     P, nsteps = 2, 6
     ny, nx = shape
     dt = 2.0 / (max(shape) - 1)
     s = molt.Solver(shape, dt=dt, P=P, bc="dirichlet", prec="mixed")
+    cur = s.tuning()
+    s.set_tuning(cur["res_warps"], cur["strided_rpt"], cur["strided_warps"], cur["rows_warps"], strided_nb=strided_nb)
     nu, beta = s.nu, s.beta
     rng = np.random.default_rng(41)
     w = rng.normal(size=shape)
