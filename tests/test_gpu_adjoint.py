@@ -394,6 +394,25 @@ def test_single_path_adjoint_mixed_matches_oracle(shape, strided_nb):
     assert np.linalg.norm(g - gref) <= adjoint_bound(tg, shape, rec, nu, P, beta)
 
 
+@pytest.mark.parametrize("rpt,warps", [(32, 4), (32, 8), (0, 4)])
+def test_transposed_y_pass_over_clusters_matches_oracle(rpt, warps):
+    """F^T of a mixed handle whose 1024-point columns span a cluster of CTAs
+    (8, 4 or 4 CTAs per column group), the transposed y pass with one
+    neighbour exchange per sweep and with the full carries."""
+    shape, P = (1024, 512), 2
+    s = molt.Solver(shape, dt=2.0 / 1023, P=P, bc="dirichlet", prec="mixed")
+    rng = np.random.default_rng(43)
+    w = rng.normal(size=shape)
+    ref = oracle.FT(w, s.nu, P, s.beta, "dirichlet")
+    cond = np.linalg.norm(w) / np.linalg.norm(ref)
+    wd = torch.from_numpy(w).cuda()
+    for nb in (1, 0):
+        s.set_tuning(res_warps=2, strided_rpt=rpt, strided_warps=warps, rows_warps=0, strided_nb=nb)
+        got = s.apply_FT(wd).cpu().numpy()
+        assert rel_l2(got, ref) <= 2 * model(s.nu, P) * max(cond, 1.0), (nb, rel_l2(got, ref))
+    s.close()
+
+
 def test_single_path_FT_is_the_transpose_of_F():
     """<F u, w> = <u, F^T w> with both sides from the mixed single path on the
     adjoint workload's grid."""
