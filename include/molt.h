@@ -322,6 +322,16 @@ mol_status mol_adjoint_history(mol_handle h, const double *u0, int64_t nsteps, i
  * stream orders the copies.
  */
 mol_status mol_field_norm(mol_handle h, const double *u, double *norm, void *stream);
+
+/* The level conversions of the mixed path (MOL_MIXED keeps each time level
+ * as a pair of float32 planes, hi + lo): mol_pair_split sets hi[i] = x[i]
+ * rounded to float32 (to nearest, ties to even) and lo[i] = (x[i] - hi[i])
+ * rounded to float32; mol_pair_join sets x[i] = hi[i] + lo[i] evaluated in
+ * float64.  n elements of caller-owned device memory (x float64, hi and lo
+ * float32; 16-byte aligned buffers take the vectorised kernels); asynchronous
+ * on the stream.  MOL_EINVAL for a NULL pointer or n < 0. */
+mol_status mol_pair_split(const double *x, float *hi, float *lo, int64_t n, void *stream);
+mol_status mol_pair_join(const float *hi, const float *lo, double *x, int64_t n, void *stream);
 mol_status mol_step_checked(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps, double growth_limit,
                             void *stream);
 mol_status mol_checkpoint_write(mol_handle h, const char *path, const double *u_prev, const double *u_cur,

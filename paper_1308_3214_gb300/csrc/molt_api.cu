@@ -1867,6 +1867,22 @@ mol_status mol_field_norm(mol_handle h, const double *u, double *norm, void *str
     return field_norm(h, u, norm, (cudaStream_t)stream);
 }
 
+mol_status mol_pair_split(const double *x, float *hi, float *lo, int64_t n, void *stream)
+{
+    if (!x || !hi || !lo || n < 0) return fail(nullptr, MOL_EINVAL, "NULL pointer or n < 0");
+    if (n == 0) return MOL_OK;
+    const cudaError_t e = launch_to_pair(x, hi, lo, n, (cudaStream_t)stream);
+    return e == cudaSuccess ? MOL_OK : cuda_fail(nullptr, e, "pair split");
+}
+
+mol_status mol_pair_join(const float *hi, const float *lo, double *x, int64_t n, void *stream)
+{
+    if (!x || !hi || !lo || n < 0) return fail(nullptr, MOL_EINVAL, "NULL pointer or n < 0");
+    if (n == 0) return MOL_OK;
+    const cudaError_t e = launch_from_pair(hi, lo, x, n, (cudaStream_t)stream);
+    return e == cudaSuccess ? MOL_OK : cuda_fail(nullptr, e, "pair join");
+}
+
 mol_status mol_step_checked(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps, double growth_limit,
                             void *stream)
 {

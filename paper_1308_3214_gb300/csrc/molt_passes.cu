@@ -67,10 +67,28 @@ __device__ __forceinline__ double f2d_bits(float f)
     return __longlong_as_double((long long)(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29)));
 }
 
+// The common case in 32-bit integer operations: a value whose float32
+// rounding is a normal number or overflows to infinity (biased float64
+// exponent 897 .. 1150); the rest takes d2f_rn_bits.  hw, lw: the high and
+// low words of the encoding; the float32 mantissa is the top 23 of the 52
+// mantissa bits, rounded by the 29 below them.
+__device__ __forceinline__ float d2f_rn_fast(double v)
+{
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+    const unsigned e = (hw >> 20) & 0x7ffu;
+    if (e - 897u <= 1150u - 897u) {
+        unsigned q = ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
+        const unsigned rem = lw & 0x1fffffffu;
+        q += (rem > 0x10000000u || (rem == 0x10000000u && (q & 1u))) ? 1u : 0u;   // a carry moves into the exponent
+        return __uint_as_float((hw & 0x80000000u) | q);
+    }
+    return d2f_rn_bits(v);
+}
+
 __device__ __forceinline__ void split_pair(double v, float &h, float &l)
 {
-    h = d2f_rn_bits(v);
-    l = d2f_rn_bits(v - f2d_bits(h));
+    h = d2f_rn_fast(v);
+    l = d2f_rn_fast(v - f2d_bits(h));
 }
 
 // The same conversions four points per thread (two 16-byte float64 loads or

@@ -40,7 +40,7 @@ EXPORTS = ["mol_default_options", "mol_create", "mol_destroy", "mol_last_error",
            "mol_embed_set_pass_timing", "mol_embed_pass_times", "mol_field_norm", "mol_step_checked",
            "mol_checkpoint_write", "mol_checkpoint_read", "mol_wait_selftest", "mol_debug_fail_alloc",
            "mol_debug_allow_unstable", "mol_adjoint_history", "mol_batch_adjoint_history",
-           "mol_toeplitz_experiment"]
+           "mol_toeplitz_experiment", "mol_pair_split", "mol_pair_join"]
 
 
 class MolError(RuntimeError):
@@ -151,6 +151,8 @@ def load_library(path: Path | None = None):
     lib.mol_embed_pass_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
     lib.mol_launch_count.restype = i64
     lib.mol_field_norm.argtypes = [vp, vp, dp, vp]
+    lib.mol_pair_split.argtypes = [vp, vp, vp, i64, vp]
+    lib.mol_pair_join.argtypes = [vp, vp, vp, i64, vp]
     lib.mol_step_checked.argtypes = [vp, vp, vp, i64, D, vp]
     lib.mol_checkpoint_write.argtypes = [vp, ctypes.c_char_p, vp, vp, i64, vp]
     lib.mol_checkpoint_read.argtypes = [vp, ctypes.c_char_p, vp, vp, ctypes.POINTER(i64), vp]
@@ -218,6 +220,45 @@ def apply_F_noalloc(u, out, dt: float, P: int, bc: str = "dirichlet", c: float =
         st = lib.mol_apply_F_noalloc(ctypes.byref(g), float(c), float(dt), float(beta), int(P), BC[bc],
                                      int(quad_order), ctypes.c_void_p(u.data_ptr()),
                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream)))
+    if st != MOL_OK:
+        raise MolError(st, lib.mol_last_error(None).decode())
+    return out
+
+
+def _pair_args(x, hi, lo):
+    import torch
+    for t, name, dt in ((x, "x", torch.float64), (hi, "hi", torch.float32), (lo, "lo", torch.float32)):
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous CUDA {dt} tensor")
+    if not (x.numel() == hi.numel() == lo.numel()) or not (x.device == hi.device == lo.device):
+        raise ValueError("x, hi and lo must have the same size and device")
+
+
+def pair_split(x, hi=None, lo=None, stream=None):
+    """(hi, lo) float32 planes with hi = x rounded to float32 and lo = x - hi
+    rounded (mol_pair_split: the mixed path's level conversion)."""
+    import torch
+    hi = torch.empty(x.shape, dtype=torch.float32, device=x.device) if hi is None else hi
+    lo = torch.empty(x.shape, dtype=torch.float32, device=x.device) if lo is None else lo
+    _pair_args(x, hi, lo)
+    lib = load_library()
+    with torch.cuda.device(x.device):
+        st = lib.mol_pair_split(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(hi.data_ptr()),
+                                ctypes.c_void_p(lo.data_ptr()), x.numel(), ctypes.c_void_p(_stream_ptr(stream)))
+    if st != MOL_OK:
+        raise MolError(st, lib.mol_last_error(None).decode())
+    return hi, lo
+
+
+def pair_join(hi, lo, out=None, stream=None):
+    """x = hi + lo in float64 (mol_pair_join)."""
+    import torch
+    out = torch.empty(hi.shape, dtype=torch.float64, device=hi.device) if out is None else out
+    _pair_args(out, hi, lo)
+    lib = load_library()
+    with torch.cuda.device(hi.device):
+        st = lib.mol_pair_join(ctypes.c_void_p(hi.data_ptr()), ctypes.c_void_p(lo.data_ptr()),
+                               ctypes.c_void_p(out.data_ptr()), hi.numel(), ctypes.c_void_p(_stream_ptr(stream)))
     if st != MOL_OK:
         raise MolError(st, lib.mol_last_error(None).decode())
     return out
