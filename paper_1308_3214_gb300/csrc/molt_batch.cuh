@@ -1034,15 +1034,11 @@ __global__ void k_batch_pack(const BatchProb *probs, const int *row_prob, const 
 #pragma unroll
             for (int c = 0; c < 4; ++c) v[c] = (j + c < nx) ? __ldg(src + j + c) : 0.0;
             if constexpr (sizeof(T) == 4) {
-                float4 h, l;
-                h.x = __double2float_rn(v[0]);
-                h.y = __double2float_rn(v[1]);
-                h.z = __double2float_rn(v[2]);
-                h.w = __double2float_rn(v[3]);
-                l.x = __double2float_rn(v[0] - (double)h.x);
-                l.y = __double2float_rn(v[1] - (double)h.y);
-                l.z = __double2float_rn(v[2] - (double)h.z);
-                l.w = __double2float_rn(v[3] - (double)h.w);
+                float4 h, l;                         // the pair split of the single-problem levels
+                split_pair(v[0], h.x, l.x);
+                split_pair(v[1], h.y, l.y);
+                split_pair(v[2], h.z, l.z);
+                split_pair(v[3], h.w, l.w);
                 *reinterpret_cast<float4 *>(hi + dst + j) = h;
                 *reinterpret_cast<float4 *>(lo + dst + j) = l;
             } else {

@@ -212,6 +212,72 @@ __device__ __forceinline__ float sdiff_pair(float hm, float h0, float hp, float 
     return __fadd_rn(dh, dl);
 }
 
+// float64 <-> float32 conversions by integer operations on the IEEE-754
+// encodings (round to nearest, ties to even, as the standard defines it):
+// GB300 runs float64 conversions on its narrow float64 pipe, so the pair
+// conversions below keep one float64 add per point.  Infinities, NaNs and
+// float32 subnormal inputs of the widening take the hardware conversion.
+__device__ __forceinline__ float d2f_rn_bits(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned s = (unsigned)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned long long m = b & 0xfffffffffffffull;
+    if (e == 0x7ff) return __double2float_rn(v);
+    const int fe = e - 896;                                  // float32 biased exponent of the value
+    unsigned long long q, rem, half;
+    if (fe >= 1) {
+        if (fe >= 255) return __uint_as_float(s | 0x7f800000u);
+        q = ((unsigned long long)fe << 23) | (m >> 29);      // exponent and 23 mantissa bits; a carry
+        rem = m & ((1ull << 29) - 1);                        // from rounding moves into the exponent
+        half = 1ull << 28;
+    } else {
+        if (e == 0) return __uint_as_float(s);               // float64 zero or subnormal -> +-0
+        const int sh = 30 - fe;                              // subnormal result in units of 2^-149
+        if (sh > 63) return __uint_as_float(s);
+        const unsigned long long M = m | (1ull << 52);
+        q = M >> sh;
+        rem = M & ((1ull << sh) - 1);
+        half = 1ull << (sh - 1);
+    }
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    return __uint_as_float(s | (unsigned)q);
+}
+
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    const unsigned long long s = (unsigned long long)(b >> 31) << 63;
+    if (e == 0) return m == 0 ? __longlong_as_double((long long)s) : (double)f;
+    if (e == 0xffu) return (double)f;
+    return __longlong_as_double((long long)(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29)));
+}
+
+// The common case in 32-bit integer operations: a value whose float32
+// rounding is a normal number or overflows to infinity (biased float64
+// exponent 897 .. 1150); the rest takes d2f_rn_bits.  hw, lw: the high and
+// low words of the encoding; the float32 mantissa is the top 23 of the 52
+// mantissa bits, rounded by the 29 below them.
+__device__ __forceinline__ float d2f_rn_fast(double v)
+{
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+    const unsigned e = (hw >> 20) & 0x7ffu;
+    if (e - 897u <= 1150u - 897u) {
+        unsigned q = ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
+        const unsigned rem = lw & 0x1fffffffu;
+        q += (rem > 0x10000000u || (rem == 0x10000000u && (q & 1u))) ? 1u : 0u;   // a carry moves into the exponent
+        return __uint_as_float((hw & 0x80000000u) | q);
+    }
+    return d2f_rn_bits(v);
+}
+
+__device__ __forceinline__ void split_pair(double v, float &h, float &l)
+{
+    h = d2f_rn_fast(v);
+    l = d2f_rn_fast(v - f2d_bits(h));
+}
+
 // u_next = a u + b up + c F with a, b, c in {0, +-1, 2, 0.5} (exact scalings)
 __device__ __forceinline__ void level_pair(float uh, float ul, float ph, float pl, float F,
                                            float a, float b, float c, float &nh, float &nl)
