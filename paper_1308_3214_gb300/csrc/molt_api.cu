@@ -55,7 +55,7 @@ struct mol_ctx {
     int num_sms = 152;
     size_t smem_optin = 227 * 1024;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};   // graphs of kGraphSteps[k] steps
     int64_t launches = 0;
     // launch choices (mol_autotune): warps per CTA of the resident x pass,
     // strided segment length (0 = default) and segments per CTA at most
@@ -99,6 +99,16 @@ struct NvtxRange {
     NvtxRange(const NvtxRange &) = delete;
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
+
+constexpr int kGraphSteps[4] = {1, 2, 3, 9};
+
+void drop_graphs(mol_ctx *h)
+{
+    for (cudaGraphExec_t &g : h->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
 
 mol_status fail(mol_ctx *h, mol_status st, const std::string &msg)
 {
@@ -150,8 +160,7 @@ void free_all(mol_ctx *h)
     h->ev_used.clear();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
+    drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->cap_stream = nullptr;
     for (void *p : h->allocs) cudaFree(p);
@@ -615,23 +624,27 @@ mol_status store_level(mol_ctx *h, const Level &L, double *x, cudaStream_t s)
 int passes_per_step(const mol_ctx *h) { return h->ndim; }
 
 // Capture three steps (one full rotation of the three level buffers) as a graph.
-mol_status build_graph(mol_ctx *h)
+// Graph k holds kGraphSteps[k] time steps from the first level buffer
+// rotation (lev[0] = u^{n-1}, lev[1] = u^n); 3 and 9 steps return to it, 1 and
+// 2 end a call's run.  Captured lazily, dropped whenever a launch choice
+// changes.
+mol_status build_graph(mol_ctx *h, int k)
 {
-    if (h->gexec) return MOL_OK;
+    if (h->gexec[k]) return MOL_OK;
     if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream create");
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
     const int64_t before = h->launches;
     mol_status st = MOL_OK;
-    for (int k = 0; k < 3 && st == MOL_OK; ++k)
-        st = run_update(h, h->lev[(k + 1) % 3], h->lev[k % 3], h->lev[(k + 2) % 3], 2.0, -1.0, 1.0, h->cap_stream);
+    for (int j = 0; j < kGraphSteps[k] && st == MOL_OK; ++j)
+        st = run_update(h, h->lev[(j + 1) % 3], h->lev[j % 3], h->lev[(j + 2) % 3], 2.0, -1.0, 1.0, h->cap_stream);
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     h->launches = before;
     if (st != MOL_OK) { if (g) cudaGraphDestroy(g); return st; }
     if (e != cudaSuccess) return cuda_fail(h, e, "graph capture end");
-    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    e = cudaGraphInstantiate(&h->gexec[k], g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "graph instantiate"); }
+    if (e != cudaSuccess) { h->gexec[k] = nullptr; return cuda_fail(h, e, "graph instantiate"); }
     return MOL_OK;
 }
 
@@ -933,11 +946,15 @@ mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps,
     if ((st = load_level(h, u_prev, h->lev[0], s)) != MOL_OK) return st;
     if ((st = load_level(h, u_cur, h->lev[1], s)) != MOL_OK) return st;
     int64_t done = 0;
-    if (h->opt.use_graphs && !h->timing && nsteps >= 3) {
-        if ((st = build_graph(h)) != MOL_OK) return st;
-        for (; done + 3 <= nsteps; done += 3) {
-            CK(cudaGraphLaunch(h->gexec, s), "graph launch");
-            h->launches += 3 * passes_per_step(h);
+    if (h->opt.use_graphs && !h->timing) {
+        // whole rotations by graphs of 9 and 3 steps, the rest by a graph of 1 or 2
+        while (done < nsteps) {
+            const int64_t left = nsteps - done;
+            const int k = left >= 9 ? 3 : (left >= 3 ? 2 : (int)left - 1);
+            if ((st = build_graph(h, k)) != MOL_OK) return st;
+            CK(cudaGraphLaunch(h->gexec[k], s), "graph launch");
+            h->launches += kGraphSteps[k] * passes_per_step(h);
+            done += kGraphSteps[k];
         }
     }
     for (; done < nsteps; ++done) {
@@ -1102,7 +1119,7 @@ mol_status mol_autotune(mol_handle h, void *stream)
     h->tune_strided_rpt = br;
     h->tune_strided_warps = bsw;
     h->tune_ms = best < 1e30 ? best : 0.0;
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // rebuilt with the choice
+    drop_graphs(h);                                      // rebuilt with the choice
     return st;
 }
 
@@ -1126,7 +1143,7 @@ mol_status mol_set_tuning(mol_handle h, int res_warps, int strided_rpt, int stri
     h->tune_rows_warps = rows_warps;
     h->tune_strided_rpt = strided_rpt;
     h->tune_strided_warps = strided_warps;
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    drop_graphs(h);
     return MOL_OK;
 }
 
@@ -1164,7 +1181,7 @@ mol_status mol_set_tuning_ex(mol_handle h, const int *vals, int count)
     if (count > MOL_TUNE_STRIDED_STAGE) h->tune_strided_stage = vals[MOL_TUNE_STRIDED_STAGE];
     if (count > MOL_TUNE_ROWS_NB) h->tune_rows_nb = vals[MOL_TUNE_ROWS_NB];
     if (count > MOL_TUNE_PDL) h->tune_pdl = vals[MOL_TUNE_PDL];
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    drop_graphs(h);
     return MOL_OK;
 }
 

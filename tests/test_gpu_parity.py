@@ -197,16 +197,20 @@ def test_time_stepping_matches_oracle(shape, P, bc, nsteps, dt, prec):
     assert rel_l2(up.cpu().numpy(), rp) <= tol
 
 
-def test_graph_and_direct_launches_agree_bitwise():
+@pytest.mark.parametrize("nsteps", [1, 2, 3, 4, 9, 17, 20])
+def test_graph_and_direct_launches_agree_bitwise(nsteps):
+    """The time loop through its graphs (9, 3, then 1 or 2 steps) and through
+    direct launches give the same bits, both levels."""
     shape, P = (40, 50), 3
     u0 = smooth_field(shape, 9, "dirichlet")
     outs = []
     for graphs in (True, False):
         s = make(shape, 0.02, P, "dirichlet", "mixed", use_graphs=graphs)
         up, uc = dev(u0), s.start(dev(u0))
-        s.step(up, uc, 17)
-        outs.append(uc.cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
+        s.step(up, uc, nsteps)
+        s.step(up, uc, nsteps)             # a second call reuses the graphs
+        outs.append((up.cpu().numpy(), uc.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
 def test_launch_count_reports_kernels():
