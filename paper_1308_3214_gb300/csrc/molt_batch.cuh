@@ -1013,12 +1013,13 @@ inline size_t batch_xs_smem(size_t tsize, int RPT, int W, int nbuf)
 // internal layout (padded rows; float32 pairs or float64)
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_batch_pack(const BatchProb *probs, const int *row_prob, const long long *uoff, int nrows,
+__global__ void __launch_bounds__(256, 8) k_batch_pack(const BatchProb *probs, const int *row_prob, const long long *uoff, int nrows,
                              const double *__restrict__ x, T *__restrict__ hi, T *__restrict__ lo)
 {
-    // a lane converts 4 consecutive points (the internal row starts 16-byte
-    // aligned and its pitch is a multiple of 4): 4 loads in flight, 16-byte
-    // stores
+    // a warp converts a row 128 points at a time, lane + 32 c for c = 0..3:
+    // every load and store instruction of the warp covers one contiguous
+    // span (256 bytes of float64, 128 of float32), whatever the alignment of
+    // the packed row; the padding of the internal row is written as zeros
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int r = gw; r < nrows; r += nw) {
@@ -1029,29 +1030,32 @@ __global__ void k_batch_pack(const BatchProb *probs, const int *row_prob, const 
         const double *src = x + __ldg(uoff + p) + (int64_t)row * nx;
         const int64_t dst = __ldg(&pb->off) + (int64_t)row * pitch;
 #pragma unroll 2
-        for (int j = 4 * lane; j < pitch; j += 128) {
+        for (int j0 = lane; j0 < pitch; j0 += 128) {
             double v[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = (j + c < nx) ? __ldg(src + j + c) : 0.0;
-            if constexpr (sizeof(T) == 4) {
-                float4 h, l;                         // the pair split of the single-problem levels
-                split_pair(v[0], h.x, l.x);
-                split_pair(v[1], h.y, l.y);
-                split_pair(v[2], h.z, l.z);
-                split_pair(v[3], h.w, l.w);
-                *reinterpret_cast<float4 *>(hi + dst + j) = h;
-                *reinterpret_cast<float4 *>(lo + dst + j) = l;
-            } else {
-                *reinterpret_cast<double2 *>(hi + dst + j) = make_double2(v[0], v[1]);
-                *reinterpret_cast<double2 *>(hi + dst + j + 2) = make_double2(v[2], v[3]);
+            for (int c = 0; c < 4; ++c) v[c] = (j0 + 32 * c < nx) ? __ldg(src + j0 + 32 * c) : 0.0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = j0 + 32 * c;
+                if (j < pitch) {
+                    if constexpr (sizeof(T) == 4) {
+                        float h, l;                  // the pair split of the single-problem levels
+                        split_pair(v[c], h, l);
+                        hi[dst + j] = h;
+                        lo[dst + j] = l;
+                    } else {
+                        hi[dst + j] = v[c];
+                    }
+                }
             }
         }
     }
 }
 
-// x = level (+ add, a packed field, when given)
+// x = level (+ add, a packed field, when given); the same warp-per-row
+// traversal as k_batch_pack
 template <class T>
-__global__ void k_batch_unpack(const BatchProb *probs, const int *row_prob, const long long *uoff, int nrows,
+__global__ void __launch_bounds__(256, 8) k_batch_unpack(const BatchProb *probs, const int *row_prob, const long long *uoff, int nrows,
                                const T *__restrict__ hi, const T *__restrict__ lo, double *__restrict__ x,
                                const double *__restrict__ add)
 {
@@ -1065,31 +1069,21 @@ __global__ void k_batch_unpack(const BatchProb *probs, const int *row_prob, cons
         const int64_t u0 = __ldg(uoff + p) + (int64_t)row * nx;
         double *dstp = x + u0;
         const int64_t src = __ldg(&pb->off) + (int64_t)row * pitch;
-#pragma unroll 2
-        for (int j = 4 * lane; j < nx; j += 128) {
+        for (int j0 = lane; j0 < nx; j0 += 128) {
             double v[4];
-            if constexpr (sizeof(T) == 4) {
-                const float4 h = __ldg(reinterpret_cast<const float4 *>(hi + src + j));
-                const float4 l = __ldg(reinterpret_cast<const float4 *>(lo + src + j));
-                v[0] = (double)h.x + (double)l.x;
-                v[1] = (double)h.y + (double)l.y;
-                v[2] = (double)h.z + (double)l.z;
-                v[3] = (double)h.w + (double)l.w;
-            } else {
-                const double2 a = __ldg(reinterpret_cast<const double2 *>(hi + src + j));
-                const double2 b = __ldg(reinterpret_cast<const double2 *>(hi + src + j + 2));
-                v[0] = a.x;
-                v[1] = a.y;
-                v[2] = b.x;
-                v[3] = b.y;
-            }
-            if (add) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) v[c] += (j + c < nx) ? __ldg(add + u0 + j + c) : 0.0;
+            for (int c = 0; c < 4; ++c) {
+                const int j = j0 + 32 * c;
+                v[c] = 0.0;
+                if (j < nx) {
+                    if constexpr (sizeof(T) == 4) v[c] = join_pair(__ldg(hi + src + j), __ldg(lo + src + j));
+                    else v[c] = __ldg(hi + src + j);
+                    if (add) v[c] += __ldg(add + u0 + j);
+                }
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                if (j + c < nx) dstp[j + c] = v[c];
+                if (j0 + 32 * c < nx) dstp[j0 + 32 * c] = v[c];
         }
     }
 }

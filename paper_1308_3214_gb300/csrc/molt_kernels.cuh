@@ -244,14 +244,24 @@ __device__ __forceinline__ float d2f_rn_bits(double v)
     return __uint_as_float(s | (unsigned)q);
 }
 
+// float64 encoding of a finite float32 encoding b: a normal value moves its
+// exponent and mantissa over; a subnormal m 2^-149 with leading bit p becomes
+// a normal float64 of exponent p - 149
+__device__ __forceinline__ unsigned long long f2d_enc(unsigned b)
+{
+    const unsigned long long s = (unsigned long long)(b >> 31) << 63;
+    const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    if (e != 0u) return s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    if (m == 0u) return s;
+    const int p = 31 - __clz((int)m);
+    return s | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+}
+
 __device__ __forceinline__ double f2d_bits(float f)
 {
     const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-    const unsigned long long s = (unsigned long long)(b >> 31) << 63;
-    if (e == 0) return m == 0 ? __longlong_as_double((long long)s) : (double)f;
-    if (e == 0xffu) return (double)f;
-    return __longlong_as_double((long long)(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29)));
+    if (((b >> 23) & 0xffu) == 0xffu) return (double)f;
+    return __longlong_as_double((long long)f2d_enc(b));
 }
 
 // The common case in 32-bit integer operations: a value whose float32
@@ -272,10 +282,120 @@ __device__ __forceinline__ float d2f_rn_fast(double v)
     return d2f_rn_bits(v);
 }
 
+// RN32(R 2^k) for an integer 0 < R < 2^29, k = e - 1075 with e the biased
+// float64 exponent of a value in the float32 normal range (897 <= e): a
+// normal result takes the top 24 bits of R, rounded to nearest even by those
+// below; a subnormal one the bits of R at or above 2^-149.
+__device__ __forceinline__ unsigned rn32_scaled(unsigned R, unsigned e)
+{
+    const int nb = 32 - __clz((int)R);                  // bit length of R
+    const int bl = (int)e + nb - 949;                    // biased float32 exponent of the result
+    unsigned q, s;
+    if (bl >= 1) {
+        if (nb <= 24) return ((unsigned)(bl - 1) << 23) + (R << (24 - nb));
+        s = (unsigned)(nb - 24);
+        q = ((unsigned)(bl - 1) << 23) + (R >> s);       // a carry from rounding moves into the exponent
+    } else {
+        const int t = (int)e - 926;                      // R 2^k in units of 2^-149 is R 2^t
+        if (t >= 0) return R << t;
+        if (t <= -30) return 0u;                         // below half the smallest subnormal
+        s = (unsigned)(-t);
+        q = R >> s;
+    }
+    const unsigned rem = R & ((1u << s) - 1u), half = 1u << (s - 1u);
+    return q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+}
+
+// v -> (h, l) = (RN32(v), RN32(v - h)), the float32 pair of a float64 value,
+// in integer operations on the encoding for every |v| below 2^127 (biased
+// float64 exponent e < 1150); v - h is exact in float64.
+//  - h a normal float32 (897 <= e): h takes the top 23 mantissa bits rounded
+//    by the 29 below them (rem), and v - h is +-R units of the last place of
+//    v with R = rem (rounded down) or 2^29 - rem (rounded up, the sign of l
+//    then opposite to that of v);
+//  - below (e < 897): h is a subnormal or zero, |v - h| <= 2^-150 rounds to
+//    a zero carrying the sign of v - h (+0 where v = h).
+// Larger values, infinities and NaNs go through the float64 subtraction.
 __device__ __forceinline__ void split_pair(double v, float &h, float &l)
 {
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+    const unsigned e = (hw >> 20) & 0x7ffu;
+    const unsigned sv = hw & 0x80000000u;
+    if (e - 897u <= 1149u - 897u) {
+        const unsigned q = ((e - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
+        const unsigned rem = lw & 0x1fffffffu;
+        const bool up = rem > 0x10000000u || (rem == 0x10000000u && (q & 1u));
+        h = __uint_as_float(sv | (q + (up ? 1u : 0u)));
+        const unsigned R = up ? 0x20000000u - rem : rem;
+        l = R == 0u ? 0.0f : __uint_as_float((up ? sv ^ 0x80000000u : sv) | rn32_scaled(R, e));
+        return;
+    }
+    if (e < 897u) {
+        const unsigned long long m = ((unsigned long long)(hw & 0xfffffu) << 32) | lw;
+        if (e == 0u) {                                   // float64 zero or subnormal: h = +-0
+            h = __uint_as_float(sv);
+            l = __uint_as_float(m == 0ull ? 0u : sv);
+            return;
+        }
+        const unsigned sh = 926u - e;                    // >= 30: the value in units of 2^-149 is M 2^-sh
+        const unsigned long long M = m | (1ull << 52);
+        unsigned q = 0u;
+        bool up = false, exact = false;
+        if (sh <= 63u) {
+            q = (unsigned)(M >> sh);
+            const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);
+            up = rem > half || (rem == half && (q & 1u));
+            exact = rem == 0ull;
+        }
+        h = __uint_as_float(sv | (q + (up ? 1u : 0u)));  // a carry gives the smallest normal
+        l = __uint_as_float(exact ? 0u : (up ? sv ^ 0x80000000u : sv));
+        return;
+    }
     h = d2f_rn_fast(v);
     l = d2f_rn_fast(v - f2d_bits(h));
+}
+
+// RN64(h + l) for a float32 pair, in integer operations where
+//  - l is a zero and h finite: the sum is h (a zero of sign sign(h) & sign(l)
+//    where h is a zero too);
+//  - h and l are normal, l no larger than h and every bit of l at or above
+//    2^-32 ulp(h) (always so for a pair from split_pair of a value in the
+//    float32 normal range): the sum is formed in a 64-bit integer in units of
+//    2^-32 ulp(h), below 2^57, and rounded to 53 bits to nearest even.
+// Other pairs go through the float64 addition.
+__device__ __forceinline__ double join_pair(float h, float l)
+{
+    const unsigned hb = __float_as_uint(h), lb = __float_as_uint(l);
+    const unsigned eh = (hb >> 23) & 0xffu, el = (lb >> 23) & 0xffu, la = lb & 0x7fffffffu;
+    if (la == 0u && eh != 0xffu) {
+        if ((hb & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)(hb & lb) << 32));
+        return __longlong_as_double((long long)f2d_enc(hb));
+    }
+    const unsigned d = eh - el;                          // exponent gap (wraps when l is larger)
+    const unsigned ml = (lb & 0x7fffffu) | 0x800000u;
+    const bool fast = eh - 1u <= 253u && el - 1u <= 253u &&
+                      (d <= 32u || (d < 56u && (ml & ((1u << (d - 32u)) - 1u)) == 0u));
+    if (!fast) return f2d_bits(h) + f2d_bits(l);
+    const unsigned long long H = (unsigned long long)((hb & 0x7fffffu) | 0x800000u) << 32;
+    const unsigned long long L = d <= 32u ? (unsigned long long)ml << (32u - d) : (unsigned long long)(ml >> (d - 32u));
+    unsigned long long sg = (unsigned long long)(hb >> 31) << 63, S;
+    if (((hb ^ lb) >> 31) == 0u) {
+        S = H + L;
+    } else if (H >= L) {
+        S = H - L;
+    } else {
+        S = L - H;
+        sg ^= 1ull << 63;
+    }
+    if (S == 0ull) return 0.0;                           // h + (-h) = +0
+    const int nb = 64 - __clzll((long long)S);           // <= 57
+    const unsigned long long top = (unsigned long long)(eh + (unsigned)nb + 839u) << 52;   // biased exponent - 1
+    if (nb <= 53) return __longlong_as_double((long long)(sg | (top + (S << (53 - nb)))));
+    const int s = nb - 53;
+    unsigned long long q = S >> s;
+    const unsigned long long rem = S & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+    return __longlong_as_double((long long)(sg | (top + q)));  // a carry moves into the exponent
 }
 
 // u_next = a u + b up + c F with a, b, c in {0, +-1, 2, 0.5} (exact scalings)

@@ -6,17 +6,17 @@ namespace molt {
 __global__ void k_to_pair(const double *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo, int64_t N)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = x[i];
-        float h = __double2float_rn(v);
+        float h, l;
+        split_pair(x[i], h, l);
         hi[i] = h;
-        lo[i] = __double2float_rn(v - (double)h);
+        lo[i] = l;
     }
 }
 
 __global__ void k_from_pair(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ x, int64_t N)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = (double)hi[i] + (double)lo[i];
+        x[i] = join_pair(hi[i], lo[i]);
 }
 
 __global__ void k_from_f32(const float *__restrict__ f, double *__restrict__ x, int64_t N)
@@ -58,12 +58,12 @@ __global__ void k_from_pair4(const float *__restrict__ hi, const float *__restri
         const float4 h = reinterpret_cast<const float4 *>(hi)[i];
         const float4 l = reinterpret_cast<const float4 *>(lo)[i];
         reinterpret_cast<double2 *>(x)[2 * i] =
-            make_double2(f2d_bits(h.x) + f2d_bits(l.x), f2d_bits(h.y) + f2d_bits(l.y));
+            make_double2(join_pair(h.x, l.x), join_pair(h.y, l.y));
         reinterpret_cast<double2 *>(x)[2 * i + 1] =
-            make_double2(f2d_bits(h.z) + f2d_bits(l.z), f2d_bits(h.w) + f2d_bits(l.w));
+            make_double2(join_pair(h.z, l.z), join_pair(h.w, l.w));
     }
     const int64_t t = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < N) x[t] = f2d_bits(hi[t]) + f2d_bits(lo[t]);
+    if (t < N) x[t] = join_pair(hi[t], lo[t]);
 }
 
 static int elementwise_grid(int64_t N)

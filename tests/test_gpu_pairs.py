@@ -4,8 +4,9 @@ addition (through torch), over magnitudes that cover every branch of the
 integer rounding: float32-normal results (ties, carries into the exponent,
 the largest finite values), results that overflow to infinity, float32
 subnormal results and underflow to zero, float64 subnormal inputs, signed
-zeros, infinities and NaNs; both the 16-byte vectorised kernels and the
-scalar ones (an unaligned view), and ragged lengths."""
+zeros, infinities and NaNs, low parts far below the high part; both the
+16-byte vectorised kernels and the scalar ones (an unaligned view), and
+ragged lengths."""
 import numpy as np
 import pytest
 
@@ -34,6 +35,13 @@ def inputs(n, seed):
     # exact ties of the float32 rounding: a float32 value plus half its ulp
     h = rng.uniform(1.0, 2.0, size=n // 8).astype(np.float32).astype(np.float64)
     x[: n // 8] = h + np.ldexp(1.0, -24) * np.sign(rng.uniform(-1, 1, size=n // 8))
+    # values a few units of the last float64 place away from a float32: small
+    # residuals, whose low part has few bits and lies far below the high part
+    k = n // 8
+    h = np.ldexp(rng.uniform(-2.0, 2.0, size=k), rng.integers(-140, 120, size=k)).astype(np.float32).astype(np.float64)
+    x[k: 2 * k] = h + np.ldexp(rng.integers(-1000, 1000, size=k).astype(np.float64), np.frexp(h)[1] - 53)
+    # magnitudes below the float32 normal range down to float64 subnormals
+    x[2 * k: 3 * k] = np.ldexp(rng.uniform(-2.0, 2.0, size=k), rng.integers(-1080, -100, size=k))
     return np.concatenate([x, special_values()])
 
 
@@ -68,6 +76,22 @@ def test_pair_conversions_bitwise(n):
     out = torch.empty(x.numel() + 1, dtype=torch.float64, device="cuda")[1:]
     molt.pair_join(hi, lo, out)
     assert same_bits(out, hi.double() + lo.double())
+
+
+def test_pair_join_arbitrary_pairs():
+    """mol_pair_join on pairs that no split produced: random encodings, and
+    normal pairs with every exponent gap from 0 to 60 in either order."""
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    bits = rng.integers(0, 1 << 32, size=(2, n), dtype=np.uint64).astype(np.uint32)
+    hi = torch.from_numpy(bits[0].view(np.float32).copy()).cuda()
+    lo = torch.from_numpy(bits[1].view(np.float32).copy()).cuda()
+    assert same_bits(molt.pair_join(hi, lo), hi.double() + lo.double())
+    e = rng.integers(-100, 100, size=n)
+    h = np.ldexp(rng.uniform(-2.0, 2.0, size=n), e).astype(np.float32)
+    l = np.ldexp(rng.uniform(-2.0, 2.0, size=n), e - rng.integers(-4, 61, size=n)).astype(np.float32)
+    hi, lo = torch.from_numpy(h).cuda(), torch.from_numpy(l).cuda()
+    assert same_bits(molt.pair_join(hi, lo), hi.double() + lo.double())
 
 
 def test_pair_conversions_reject_bad_arguments():
