@@ -280,6 +280,12 @@ class RankGroup:
             dist.destroy_process_group()
 
 
+TIMED_REGION = ("one call of the public API (mol_step / the solve or adjoint call) over the K timed steps, "
+                "level conversions in and out included; CUDA events on the launch stream, the call enqueued "
+                "behind a bounded spin kernel so that the host's enqueue latency is not device time (e2e "
+                "includes it)")
+
+
 def hold_stream(ms: float = 60.0):
     """Keep the current stream busy for about `ms` (torch's bounded spin
     kernel) so that the launches enqueued next run back to back: per-pass
@@ -467,6 +473,7 @@ def main():
         l0 = s.launches
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
+        hold_stream()
         ev0.record()
         s.step(up, uc, nsteps)
         ev1.record()
@@ -546,6 +553,7 @@ def main():
             "config": {"workload": spec["name"], "shape": list(shape), "P": P, "cfl": spec["cfl"],
                        "bc": spec["bc"], "beta": solver.beta, "prec": args.prec,
                        "levels": "f32 hi+lo pairs" if args.prec == "mixed" else "f64",
+                       "timed_region": TIMED_REGION,
                        "l2": "no flush: per-step working set (3 levels + intermediate fields) exceeds the 129 MB L2",
                        "parallelism": f"{world} independent replica(s)", "tuning": tuning},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
@@ -669,6 +677,7 @@ def batch_summary(args, group):
         torch.cuda.synchronize()
         group.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hold_stream()
         e0.record()
         b.step(up, uc, k)
         e1.record()
@@ -796,6 +805,7 @@ def main_batch(args, spec):
         torch.cuda.synchronize()
         l0 = bs.launches
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hold_stream()
         e0.record()
         bs.step(up, uc, nsteps)
         e1.record()
@@ -852,6 +862,7 @@ def main_batch(args, spec):
                        "n_range": [min(n for n, _ in shapes), max(n for n, _ in shapes)],
                        "P_counts": {str(k): Ps.count(k) for k in (1, 2, 3)}, "prec": args.prec,
                        "levels": "f32 hi+lo pairs" if args.prec == "mixed" else "f64",
+                       "timed_region": TIMED_REGION,
                        "l2": "no flush: per-step working set (3 levels + intermediate fields) exceeds the 129 MB L2",
                        "parallelism": f"{world} rank(s), each its own {len(shapes)} problems", "tuning": tuning},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
@@ -962,6 +973,7 @@ def main_extension(args, spec):
     bus = torch.cuda.get_device_properties(0).pci_bus_id
     sampler = ClockSampler(bus).start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hold_stream()
     e0.record()
     out = call(K)
     e1.record()
@@ -984,7 +996,8 @@ def main_extension(args, spec):
             "vs_baseline": None, "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": spec["name"], "shape": list(spec["shape"]), "P": spec["P"], "cfl": spec["cfl"],
                        "prec": args.prec, "step": "one call of K steps (solve_source / solve_dirichlet, direct "
-                                                  "launches: per-step scalars)", "parallelism": "1 rank"},
+                                                  "launches: per-step scalars)", "parallelism": "1 rank",
+                       "timed_region": TIMED_REGION},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
@@ -1087,6 +1100,7 @@ def main_embedded(args, spec):
     sampler = ClockSampler(bus).start()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hold_stream()
     e0.record(stream)
     s.step(up, uc, K)
     e1.record(stream)
@@ -1141,7 +1155,8 @@ def main_embedded(args, spec):
             "config": {"workload": spec["name"], "grid": [n, n], "interior_points": npts, "P": P, "cfl": cfl,
                        "domain": "((x+y)/4)^2 + (x-y)^2 < 1 in [-2.2, 2.2]^2",
                        "levels": "f32 hi+lo pairs" if args.prec == "mixed" else "f64",
-                       "step": "mol_embed_step, K steps in one call, levels resident", "parallelism": "1 rank"},
+                       "step": "mol_embed_step, K steps in one call, levels resident", "parallelism": "1 rank",
+                       "timed_region": TIMED_REGION},
             "gpu_launches": launches, "roofline": roofline,
             "clocks": clocks, "finite": finite}
     if not args.no_e2e:
@@ -1245,6 +1260,7 @@ def main_adjoint(args, spec):
         bus = None
     sampler = ClockSampler(bus).start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hold_stream()
     e0.record()
     grad = b.adjoint(rec, res[:N])
     e1.record()
@@ -1283,6 +1299,7 @@ def main_adjoint(args, spec):
             "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": spec["name"], "shape": [n, n], "P": P, "cfl": spec["cfl"], "receivers": int(rec.size),
                        "prec": args.prec, "step": "one adjoint step: mu^n = 2 mu^{n+1} - mu^{n+2} + F^T mu^{n+1} + g^n",
+                       "timed_region": TIMED_REGION,
                        "l2": "no flush, and the per-step working set (3 adjoint levels as f32 pairs + P power "
                              "fields, about 40 MB at 1024^2) fits in the 129 MB L2: steps run back to back inside "
                              "one mol_adjoint call, so HBM fractions of this line are not DRAM-bound figures",
