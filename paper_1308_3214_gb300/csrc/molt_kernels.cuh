@@ -212,11 +212,13 @@ __device__ __forceinline__ float sdiff_pair(float hm, float h0, float hp, float 
     return __fadd_rn(dh, dl);
 }
 
+// --- level conversions (begin) ---
 // float64 <-> float32 conversions by integer operations on the IEEE-754
 // encodings (round to nearest, ties to even, as the standard defines it):
-// GB300 runs float64 conversions on its narrow float64 pipe, so the pair
-// conversions below keep one float64 add per point.  Infinities, NaNs and
-// float32 subnormal inputs of the widening take the hardware conversion.
+// GB300 runs float64 arithmetic and conversions on its narrow float64 pipe
+// (about one lane-operation per SM and clock), so the pair conversions below
+// take none on their common paths.  Infinities and NaNs take the hardware
+// conversion.
 __device__ __forceinline__ float d2f_rn_bits(double v)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
@@ -397,6 +399,8 @@ __device__ __forceinline__ double join_pair(float h, float l)
     q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
     return __longlong_as_double((long long)(sg | (top + q)));  // a carry moves into the exponent
 }
+
+// --- level conversions (end) ---
 
 // u_next = a u + b up + c F with a, b, c in {0, +-1, 2, 0.5} (exact scalings)
 __device__ __forceinline__ void level_pair(float uh, float ul, float ph, float pl, float F,
