@@ -380,6 +380,7 @@ def run_reference(args, spec):
             "data": "synthetic",
             "config": {"workload": spec["name"], "shape": list(spec["shape"]), "P": P, "cfl": spec["cfl"], "bc": bc,
                        "beta": beta, "prec": "fp64", "levels": "f64",
+                       "timed_region": "host wall clock over the K oracle steps of the sample",
                        "l2": "host run (the oracle on the CPU cores; no GPU cache)",
                        "parallelism": f"{cores} OpenMP threads over lines", "tuning": None},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample,
@@ -760,7 +761,13 @@ def main_batch(args, spec):
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * npts / value,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": spec["name"], "points_per_step": npts},
+                "data": "synthetic",
+                "config": {"workload": spec["name"], "problems": len(shapes), "points_per_step": npts,
+                           "n_range": [min(n for n, _ in shapes), max(n for n, _ in shapes)],
+                           "P_counts": {str(k): Ps.count(k) for k in (1, 2, 3)}, "prec": "fp64", "levels": "f64",
+                           "timed_region": "host wall clock over each step's oracle sample",
+                           "l2": "host run (the oracle on the CPU cores; no GPU cache)",
+                           "parallelism": f"{cores} OpenMP threads over lines", "tuning": None},
                 "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
                 "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
