@@ -621,6 +621,35 @@ mol_status store_level(mol_ctx *h, const Level &L, double *x, cudaStream_t s)
     return MOL_OK;
 }
 
+// the two levels of a time-stepping call, in and out: one launch each way
+// on the mixed path (two when a field is not 16-byte aligned)
+mol_status load_levels(mol_ctx *h, const double *x0, const Level &L0, const double *x1, const Level &L1,
+                       cudaStream_t s)
+{
+    if (h->prec != MOL_MIXED) {
+        mol_status st = load_level(h, x0, L0, s);
+        return st != MOL_OK ? st : load_level(h, x1, L1, s);
+    }
+    CK(launch_to_pair2(x0, (float *)L0.hi, (float *)L0.lo, x1, (float *)L1.hi, (float *)L1.lo, h->N, s),
+       "level conversion");
+    h->launches += (((uintptr_t)x0 | (uintptr_t)L0.hi | (uintptr_t)L0.lo | (uintptr_t)x1 | (uintptr_t)L1.hi |
+                     (uintptr_t)L1.lo) & 15) ? 2 : 1;
+    return MOL_OK;
+}
+
+mol_status store_levels(mol_ctx *h, const Level &L0, double *x0, const Level &L1, double *x1, cudaStream_t s)
+{
+    if (h->prec != MOL_MIXED) {
+        mol_status st = store_level(h, L0, x0, s);
+        return st != MOL_OK ? st : store_level(h, L1, x1, s);
+    }
+    CK(launch_from_pair2((const float *)L0.hi, (const float *)L0.lo, x0, (const float *)L1.hi, (const float *)L1.lo,
+                         x1, h->N, s), "level conversion");
+    h->launches += (((uintptr_t)x0 | (uintptr_t)L0.hi | (uintptr_t)L0.lo | (uintptr_t)x1 | (uintptr_t)L1.hi |
+                     (uintptr_t)L1.lo) & 15) ? 2 : 1;
+    return MOL_OK;
+}
+
 int passes_per_step(const mol_ctx *h) { return h->ndim; }
 
 // Capture three steps (one full rotation of the three level buffers) as a graph.
@@ -943,8 +972,7 @@ mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps,
     if (u_prev == u_cur) return fail(h, MOL_EINVAL, "u_prev and u_cur must not overlap");
     if (nsteps == 0) return MOL_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = load_level(h, u_prev, h->lev[0], s)) != MOL_OK) return st;
-    if ((st = load_level(h, u_cur, h->lev[1], s)) != MOL_OK) return st;
+    if ((st = load_levels(h, u_prev, h->lev[0], u_cur, h->lev[1], s)) != MOL_OK) return st;
     int64_t done = 0;
     if (h->opt.use_graphs && !h->timing) {
         // whole rotations by graphs of 9 and 3 steps, the rest by a graph of 1 or 2
@@ -963,8 +991,7 @@ mol_status mol_step(mol_handle h, double *u_prev, double *u_cur, int64_t nsteps,
             return st;
     }
     const int k = (int)(nsteps % 3);
-    if ((st = store_level(h, h->lev[k], u_prev, s)) != MOL_OK) return st;
-    return store_level(h, h->lev[(k + 1) % 3], u_cur, s);
+    return store_levels(h, h->lev[k], u_prev, h->lev[(k + 1) % 3], u_cur, s);
 }
 
 mol_status mol_solve_host(mol_handle h, const double *u0, double *u_out, int64_t nsteps, void *stream)
@@ -2011,8 +2038,7 @@ mol_status hist_step_emit(void *c, const double *prev, const double *cur, int64_
 {
     mol_ctx *h = (mol_ctx *)c;
     mol_status st;
-    if ((st = load_level(h, prev, h->lev[0], s)) != MOL_OK) return st;
-    if ((st = load_level(h, cur, h->lev[1], s)) != MOL_OK) return st;
+    if ((st = load_levels(h, prev, h->lev[0], cur, h->lev[1], s)) != MOL_OK) return st;
     for (int64_t j = 0; j < m; ++j) {
         const int k = (int)(j % 3);
         if ((st = run_update(h, h->lev[(k + 1) % 3], h->lev[k], h->lev[(k + 2) % 3], 2.0, -1.0, 1.0, s)) != MOL_OK)
@@ -2027,8 +2053,7 @@ mol_status hist_update_T(void *c, const double *u, const double *up, double *un,
 {
     mol_ctx *h = (mol_ctx *)c;
     mol_status st;
-    if ((st = load_level(h, u, h->lev[0], s)) != MOL_OK) return st;
-    if ((st = load_level(h, up, h->lev[1], s)) != MOL_OK) return st;
+    if ((st = load_levels(h, u, h->lev[0], up, h->lev[1], s)) != MOL_OK) return st;
     if ((st = run_update_T(h, h->lev[0], h->lev[1], h->lev[2], ea, eb, ec, s)) != MOL_OK) return st;
     if ((st = store_level(h, h->lev[2], un, s)) != MOL_OK) return st;
     if (add) {

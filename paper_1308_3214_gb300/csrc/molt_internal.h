@@ -30,6 +30,11 @@ cudaError_t launch_horner(int tbytes, int bc, bool contig, const AxisDev &A, con
                           const HornerParams &p, cudaStream_t s);
 cudaError_t launch_to_pair(const double *x, float *hi, float *lo, int64_t N, cudaStream_t s);
 cudaError_t launch_from_pair(const float *hi, const float *lo, double *x, int64_t N, cudaStream_t s);
+// two levels in one launch where every field is 16-byte aligned, else two
+cudaError_t launch_to_pair2(const double *x0, float *hi0, float *lo0, const double *x1, float *hi1, float *lo1,
+                            int64_t N, cudaStream_t s);
+cudaError_t launch_from_pair2(const float *hi0, const float *lo0, double *x0, const float *hi1, const float *lo1,
+                              double *x1, int64_t N, cudaStream_t s);
 cudaError_t launch_from_f32(const float *f, double *x, int64_t N, cudaStream_t s);
 
 // Test hooks (molt_host.cu; set through mol_debug_fail_alloc /

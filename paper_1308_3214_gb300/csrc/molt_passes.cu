@@ -28,7 +28,8 @@ __global__ void k_from_f32(const float *__restrict__ f, double *__restrict__ x, 
 // The same conversions four points per thread (two 16-byte float64 loads or
 // stores, one 16-byte float32 store or load per plane), for 16-byte aligned
 // fields; the last N % 4 points by the scalar form.
-__global__ void k_to_pair4(const double *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo, int64_t N)
+__device__ __forceinline__ void to_pair4(const double *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo,
+                                         int64_t N)
 {
     const int64_t n4 = N >> 2;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
@@ -51,7 +52,8 @@ __global__ void k_to_pair4(const double *__restrict__ x, float *__restrict__ hi,
     }
 }
 
-__global__ void k_from_pair4(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ x, int64_t N)
+__device__ __forceinline__ void from_pair4(const float *__restrict__ hi, const float *__restrict__ lo,
+                                           double *__restrict__ x, int64_t N)
 {
     const int64_t n4 = N >> 2;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
@@ -64,6 +66,37 @@ __global__ void k_from_pair4(const float *__restrict__ hi, const float *__restri
     }
     const int64_t t = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < N) x[t] = join_pair(hi[t], lo[t]);
+}
+
+__global__ void k_to_pair4(const double *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo, int64_t N)
+{
+    to_pair4(x, hi, lo, N);
+}
+
+__global__ void k_from_pair4(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ x, int64_t N)
+{
+    from_pair4(hi, lo, x, N);
+}
+
+// Two levels in one launch (blockIdx.y = the level): the two conversions at
+// each end of a time-stepping call share one launch's ramp and tail.
+struct PairFields2 {
+    const double *x[2];
+    double *xo[2];
+    float *hi[2];
+    float *lo[2];
+};
+
+__global__ void k_to_pair4_2(const PairFields2 f, int64_t N)
+{
+    const bool k = blockIdx.y != 0;                // selects, so that f stays in the parameter space
+    to_pair4(k ? f.x[1] : f.x[0], k ? f.hi[1] : f.hi[0], k ? f.lo[1] : f.lo[0], N);
+}
+
+__global__ void k_from_pair4_2(const PairFields2 f, int64_t N)
+{
+    const bool k = blockIdx.y != 0;
+    from_pair4(k ? f.hi[1] : f.hi[0], k ? f.lo[1] : f.lo[0], k ? f.xo[1] : f.xo[0], N);
 }
 
 static int elementwise_grid(int64_t N)
@@ -89,6 +122,31 @@ cudaError_t launch_from_pair(const float *hi, const float *lo, double *x, int64_
     else k_from_pair<<<elementwise_grid(N), 256, 0, s>>>(hi, lo, x, N);
     return cudaGetLastError();
 }
+cudaError_t launch_to_pair2(const double *x0, float *hi0, float *lo0, const double *x1, float *hi1, float *lo1,
+                            int64_t N, cudaStream_t s)
+{
+    if (!(aligned16(x0, hi0, lo0) && aligned16(x1, hi1, lo1))) {
+        cudaError_t e = launch_to_pair(x0, hi0, lo0, N, s);
+        return e != cudaSuccess ? e : launch_to_pair(x1, hi1, lo1, N, s);
+    }
+    const PairFields2 f = {{x0, x1}, {nullptr, nullptr}, {hi0, hi1}, {lo0, lo1}};
+    k_to_pair4_2<<<dim3(elementwise_grid((N + 3) / 4), 2), 256, 0, s>>>(f, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_pair2(const float *hi0, const float *lo0, double *x0, const float *hi1, const float *lo1,
+                              double *x1, int64_t N, cudaStream_t s)
+{
+    if (!(aligned16(x0, hi0, lo0) && aligned16(x1, hi1, lo1))) {
+        cudaError_t e = launch_from_pair(hi0, lo0, x0, N, s);
+        return e != cudaSuccess ? e : launch_from_pair(hi1, lo1, x1, N, s);
+    }
+    const PairFields2 f = {{nullptr, nullptr}, {x0, x1}, {const_cast<float *>(hi0), const_cast<float *>(hi1)},
+                           {const_cast<float *>(lo0), const_cast<float *>(lo1)}};
+    k_from_pair4_2<<<dim3(elementwise_grid((N + 3) / 4), 2), 256, 0, s>>>(f, N);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_from_f32(const float *f, double *x, int64_t N, cudaStream_t s)
 {
     k_from_f32<<<elementwise_grid(N), 256, 0, s>>>(f, x, N);

@@ -214,12 +214,20 @@ def test_graph_and_direct_launches_agree_bitwise(nsteps):
 
 
 def test_launch_count_reports_kernels():
+    # a small Dirichlet grid runs as a batch of one: 2 conversions in (one
+    # per level), 2 passes per step, 2 conversions out
     s = make((32, 40), 0.02, 2, "dirichlet", "mixed")
     u = dev(field((32, 40), 1, "dirichlet"))
     before = s.launches
     s.step(u.clone(), u.clone(), 6)
-    # 2 conversions in, 2 passes per step, 2 conversions out
     assert s.launches - before == 2 + 2 * 6 + 2
+    # the single-problem kernels: one conversion launch in for both levels,
+    # 2 passes per step, one out
+    s = make((32, 64), 0.02, 2, "periodic", "mixed")
+    u = dev(field((32, 64), 1, "periodic"))
+    before = s.launches
+    s.step(u.clone(), u.clone(), 6)
+    assert s.launches - before == 1 + 2 * 6 + 1
 
 
 def test_solve_host_matches_device_path():
