@@ -74,7 +74,12 @@ typedef struct {
 typedef struct {
     int quad_order;     /* 2 (default): quadratic local interpolant; 1: linear */
     int lines_per_block;/* 0 = automatic; else 1, 2, 4, 8 or 16 lines per CTA    */
-    int use_graphs;     /* 1 (default): replay the time loop as a CUDA graph    */
+    int use_graphs;     /* 1 (default): replay the time loop as a CUDA graph;
+                         * 0: direct launches; 2 (batches): graphs with the
+                         * passes of all problems joined at every step (1 runs
+                         * the launches of a batch's size classes as
+                         * independent chains where each class's y and x
+                         * launches cover the same problems)                 */
 } mol_options;
 
 typedef struct mol_ctx *mol_handle;

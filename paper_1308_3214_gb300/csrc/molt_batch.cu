@@ -79,6 +79,8 @@ struct mol_batch_ctx {
     int xmid = 1;                       // rows of 257..512 points: 1 one CTA of two warps per row (8-point
     size_t xs8_smem = 0;                //   segments), 0 the one-warp kernel; its shared memory
     double tune_ms[2] = {0.0, 0.0};     // tuned x / y pass times
+    int chains = 1;                     // graphs: the y / x launch pairs as independent chains where
+                                        // they pair up (chain_plan)
 };
 
 namespace {
@@ -339,19 +341,53 @@ cudaError_t launch_pass_y(mol_batch_ctx *b, const BatchPass &bp, cudaStream_t s)
     return e;
 }
 
-// The x pass: rows of short lines (one warp per row, persistent), rows of
-// 257..512 points and longer rows (one CTA per row, or persistent warps),
-// one launch per length class.  The classes are independent: the long rows
-// (most of the work) run on s, the others on side streams forked from s and
-// joined back into it, so that their launches overlap instead of queueing.
+// One launch of the x pass per row group: g = 0 the rows of short lines
+// (one warp per row, persistent), 1 rows of 257..512 points (one CTA of two
+// warps per row, when their buffers fit), 2 longer rows (one CTA per row, or
+// persistent warps).
+template <class T, bool ADJ>
+cudaError_t launch_x_group(const mol_batch_ctx *b, BatchPass bp, int g, cudaStream_t s)
+{
+    if (g == 0) {
+        bp.row_begin = 0;
+        bp.nitems = (int)b->one_warp_end();
+        k_batch_x<T, false, ADJ><<<b->xgrid[0], 32 * b->xW[0], b->xsmem[0], s>>>(bp, b->nbuf);
+    } else if (g == 1) {
+        bp.row_begin = (int)b->rows_small;
+        bp.nitems = (int)b->rows_mid;
+        k_batch_xs<T, 8, 2, ADJ><<<(unsigned)(b->rows_mid - b->rows_small), 64, b->xs8_smem, s>>>(bp);
+    } else {
+        bp.row_begin = (int)b->rows_mid;
+        bp.nitems = (int)b->nrows;
+        if (b->xsplit)
+            k_batch_xs<T, 16, 2, ADJ><<<(unsigned)(b->nrows - b->rows_mid), 64, b->xs_smem, s>>>(bp);
+        else
+            k_batch_x<T, true, ADJ><<<b->xgrid[1], 32 * b->xW[1], b->xsmem[1], s>>>(bp, b->nbuf);
+    }
+    return cudaGetLastError();
+}
+
+// the row groups present
+void x_groups(const mol_batch_ctx *b, bool c[3])
+{
+    c[0] = b->one_warp_end() > 0;
+    c[1] = b->xmid && b->rows_mid > b->rows_small;
+    c[2] = b->nrows > b->rows_mid;
+}
+
+// The x pass: one launch per row group.  The groups are independent: the
+// long rows (most of the work) run on s, the others on side streams forked
+// from s and joined back into it, so that their launches overlap instead of
+// queueing.
 template <class T, bool ADJ>
 cudaError_t launch_pass_x(mol_batch_ctx *b, BatchPass bp, cudaStream_t s)
 {
-    const bool c0 = b->one_warp_end() > 0, c1 = b->xmid && b->rows_mid > b->rows_small, c2 = b->nrows > b->rows_mid;
-    const int nside = (c0 ? 1 : 0) + (c1 ? 1 : 0);
+    bool c[3];
+    x_groups(b, c);
+    const int nside = (c[0] ? 1 : 0) + (c[1] ? 1 : 0);
     cudaError_t e = cudaSuccess;
     cudaStream_t side[2] = {s, s};
-    if (c2 && nside > 0) {
+    if (c[2] && nside > 0) {
         for (int j = 0; j < 2 && e == cudaSuccess; ++j)
             if (!b->ys[j]) e = cudaStreamCreateWithFlags(&b->ys[j], cudaStreamNonBlocking);
         for (int j = 0; j < 3 && e == cudaSuccess; ++j)
@@ -363,30 +399,11 @@ cudaError_t launch_pass_x(mol_batch_ctx *b, BatchPass bp, cudaStream_t s)
         }
         if (e != cudaSuccess) return e;
     }
-    if (c0) {
-        bp.row_begin = 0;
-        bp.nitems = (int)b->one_warp_end();
-        k_batch_x<T, false, ADJ><<<b->xgrid[0], 32 * b->xW[0], b->xsmem[0], side[0]>>>(bp, b->nbuf);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (c1) {
-        bp.row_begin = (int)b->rows_small;
-        bp.nitems = (int)b->rows_mid;
-        k_batch_xs<T, 8, 2, ADJ><<<(unsigned)(b->rows_mid - b->rows_small), 64, b->xs8_smem, side[1]>>>(bp);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (c2) {
-        bp.row_begin = (int)b->rows_mid;
-        bp.nitems = (int)b->nrows;
-        if (b->xsplit)
-            k_batch_xs<T, 16, 2, ADJ><<<(unsigned)(b->nrows - b->rows_mid), 64, b->xs_smem, s>>>(bp);
-        else
-            k_batch_x<T, true, ADJ><<<b->xgrid[1], 32 * b->xW[1], b->xsmem[1], s>>>(bp, b->nbuf);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (nside > 0) {
-            for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(b->xev[1 + j], side[j]);
-            for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s, b->xev[1 + j], 0);
-        }
+    for (int g = 0; g < 3 && e == cudaSuccess; ++g)
+        if (c[g]) e = launch_x_group<T, ADJ>(b, bp, g, g == 2 ? s : side[g]);
+    if (e == cudaSuccess && c[2] && nside > 0) {
+        for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(b->xev[1 + j], side[j]);
+        for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s, b->xev[1 + j], 0);
     }
     return e;
 }
@@ -440,11 +457,11 @@ mol_status run_pass(mol_batch_ctx *b, int axis, const BatchPass &bp, cudaStream_
     return MOL_OK;
 }
 
-// un = ea u + eb up + ec F[u] (adj: F^T[u]) for every problem: y pass, then x pass
-mol_status run_update(mol_batch_ctx *b, const BLevel &u, const BLevel &up, const BLevel &un, double ea, double eb,
-                      double ec, cudaStream_t s, bool adj = false)
+// the two passes of un = ea u + eb up + ec F[u]
+void update_passes(const mol_batch_ctx *b, const BLevel &u, const BLevel &up, const BLevel &un, double ea, double eb,
+                   double ec, BatchPass &y, BatchPass &x)
 {
-    BatchPass y{};
+    y = BatchPass{};
     y.probs = b->probs;
     y.row_prob = b->row_prob;
     y.items = b->items;
@@ -452,9 +469,7 @@ mol_status run_update(mol_batch_ctx *b, const BLevel &u, const BLevel &up, const
     y.pr.u_hi = u.hi;
     y.pr.u_lo = u.lo;
     for (int k = 0; k < b->Pmax; ++k) y.pr.out[k] = b->inter[k];
-    mol_status st = run_pass(b, 1, y, s, adj);
-    if (st != MOL_OK) return st;
-    BatchPass x = y;
+    x = y;
     x.nitems = (int)b->nrows;
     for (int k = 0; k < b->Pmax; ++k) { x.pr.g[k] = b->inter[k]; x.pr.out[k] = nullptr; }
     x.pr.up_hi = up.hi;
@@ -467,6 +482,16 @@ mol_status run_update(mol_batch_ctx *b, const BLevel &u, const BLevel &up, const
     x.pr.fea = (float)ea;
     x.pr.feb = (float)eb;
     x.pr.fec = (float)ec;
+}
+
+// un = ea u + eb up + ec F[u] (adj: F^T[u]) for every problem: y pass, then x pass
+mol_status run_update(mol_batch_ctx *b, const BLevel &u, const BLevel &up, const BLevel &un, double ea, double eb,
+                      double ec, cudaStream_t s, bool adj = false)
+{
+    BatchPass y, x;
+    update_passes(b, u, up, un, ea, eb, ec, y, x);
+    mol_status st = run_pass(b, 1, y, s, adj);
+    if (st != MOL_OK) return st;
     return run_pass(b, 0, x, s, adj);
 }
 
@@ -565,16 +590,83 @@ mol_status zero_level(mol_batch_ctx *b, const BLevel &L, cudaStream_t s)
     return MOL_OK;
 }
 
+// Chains of the time loop.  A problem's y pass runs in the launch of its
+// cluster size and its x pass in the launch of its row group; where these
+// pair up one to one (every problem of a y launch in the same x launch and
+// back; so for square problems), each pair (y launch, then x launch, step
+// after step) touches only its own problems' fields and runs as a chain of
+// its own, joined with the others only at the end of the graph: the short
+// problems' launches fill the ramps and tails of the long ones' instead of
+// waiting at every pass.  ych / xch: the pairs; false where they do not
+// pair up or there is only one.
+bool chain_plan(const mol_batch_ctx *b, int ych[3], int xch[3], int &nch)
+{
+    int x2y[3] = {-1, -1, -1}, y2x[4] = {-1, -1, -1, -1};
+    for (const BatchProb &pb : b->hp) {
+        int xg = row_class(pb.ax.n);
+        if (xg == 1 && !b->xmid) xg = 0;
+        int yk = 0;
+        while ((1 << yk) < pb.ky) ++yk;
+        if (yk > 3 || (1 << yk) != pb.ky) return false;
+        if (x2y[xg] < 0) x2y[xg] = yk;
+        else if (x2y[xg] != yk) return false;
+        if (y2x[yk] < 0) y2x[yk] = xg;
+        else if (y2x[yk] != xg) return false;
+    }
+    nch = 0;
+    for (int g = 0; g < 3; ++g)
+        if (x2y[g] >= 0) {
+            ych[nch] = x2y[g];
+            xch[nch] = g;
+            ++nch;
+        }
+    return nch > 1;
+}
+
+// three time steps captured as chains (see chain_plan)
+template <class T>
+mol_status capture_chains(mol_batch_ctx *b, const int ych[3], const int xch[3], int nch)
+{
+    cudaStream_t cs[3] = {b->cap_stream, nullptr, nullptr};
+    for (int c = 1; c < nch; ++c) {
+        if (!b->ys[c - 1]) BCK(cudaStreamCreateWithFlags(&b->ys[c - 1], cudaStreamNonBlocking), "stream create");
+        cs[c] = b->ys[c - 1];
+    }
+    for (int j = 0; j < 4; ++j)
+        if (!b->yev[j]) BCK(cudaEventCreateWithFlags(&b->yev[j], cudaEventDisableTiming), "event create");
+    BCK(cudaEventRecord(b->yev[0], cs[0]), "event record");
+    for (int c = 1; c < nch; ++c) BCK(cudaStreamWaitEvent(cs[c], b->yev[0], 0), "stream wait");
+    for (int k = 0; k < 3; ++k) {
+        BatchPass y, x;
+        update_passes(b, b->lev[(k + 1) % 3], b->lev[k % 3], b->lev[(k + 2) % 3], 2.0, -1.0, 1.0, y, x);
+        for (int c = 0; c < nch; ++c) {
+            BCK((launch_y_class<T, false>(b, y, ych[c], cs[c])), "batched pass launch");
+            BCK((launch_x_group<T, false>(b, x, xch[c], cs[c])), "batched pass launch");
+        }
+    }
+    for (int c = 1; c < nch; ++c) {
+        BCK(cudaEventRecord(b->yev[c], cs[c]), "event record");
+        BCK(cudaStreamWaitEvent(cs[0], b->yev[c], 0), "stream wait");
+    }
+    return MOL_OK;
+}
+
 mol_status build_graph(mol_batch_ctx *b)
 {
     if (b->gexec) return MOL_OK;
     if (!b->cap_stream) BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream create");
+    int ych[3], xch[3], nch = 0;
+    const bool chains = b->chains && chain_plan(b, ych, xch, nch);
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
     const int64_t before = b->launches;
     mol_status st = MOL_OK;
-    for (int k = 0; k < 3 && st == MOL_OK; ++k)
-        st = run_update(b, b->lev[(k + 1) % 3], b->lev[k % 3], b->lev[(k + 2) % 3], 2.0, -1.0, 1.0, b->cap_stream);
+    if (chains) {
+        st = b->tbytes == 4 ? capture_chains<float>(b, ych, xch, nch) : capture_chains<double>(b, ych, xch, nch);
+    } else {
+        for (int k = 0; k < 3 && st == MOL_OK; ++k)
+            st = run_update(b, b->lev[(k + 1) % 3], b->lev[k % 3], b->lev[(k + 2) % 3], 2.0, -1.0, 1.0, b->cap_stream);
+    }
     cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
     b->launches = before;
     if (st != MOL_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -699,7 +791,8 @@ mol_status mol_batch_create(int nprob, const mol_grid *grids, const double *c, c
     b->prec = prec;
     b->tbytes = prec == MOL_MIXED ? 4 : 8;
     b->quad = o.quad_order;
-    b->use_graphs = o.use_graphs;
+    b->use_graphs = o.use_graphs ? 1 : 0;
+    b->chains = o.use_graphs == 1 ? 1 : 0;
     mol_status st = plan_batch(b, nprob, grids, c, dt, beta, P, o.quad_order);
     if (st != MOL_OK) { delete b; return st; }
 

@@ -513,10 +513,13 @@ class BatchSolver:
     value per problem or a scalar for all; ``lo`` / ``hi``: per-problem
     (y, x) pairs or None for the unit square.  Fields are PACKED: one flat
     CUDA float64 tensor holding every problem's (ny, nx) array in turn;
-    ``pack`` / ``unpack`` convert."""
+    ``pack`` / ``unpack`` convert.  ``chains``: in the graph time loop,
+    run the launches of each size class as an independent chain where the
+    classes' y and x launches cover the same problems (False: join every
+    pass of all problems at every step)."""
 
     def __init__(self, shapes, dt, P, c=1.0, beta=0.0, prec: str = "mixed", lo=None, hi=None,
-                 quad_order: int = 2, use_graphs: bool = True):
+                 quad_order: int = 2, use_graphs: bool = True, chains: bool = True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libmolt needs a CUDA GPU")
@@ -541,7 +544,7 @@ class BatchSolver:
         cs = (ctypes.c_double * n)(*self.c)
         bs = (ctypes.c_double * n)(*betas)
         Ps = (ctypes.c_int * n)(*self.P)
-        opt = mol_options(int(quad_order), 0, 1 if use_graphs else 0)
+        opt = mol_options(int(quad_order), 0, (1 if chains else 2) if use_graphs else 0)
         h = ctypes.c_void_p()
         torch.cuda.init()
         st = self.lib.mol_batch_create(n, grids, cs, dts, bs, Ps, BC["dirichlet"], PREC[prec], ctypes.byref(opt),

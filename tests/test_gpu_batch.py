@@ -131,6 +131,30 @@ def test_batch_start_and_steps_match_oracle(prec):
         assert rel_l2(gp[i].cpu().numpy(), rp) <= tol, (i, "u_prev")
 
 
+# square problems of every size class: each class's y launch (cluster size)
+# and x launch (row group) cover the same problems, so the graph runs the
+# classes as independent chains
+CHAIN_SHAPES = [(64, 64), (200, 200), (130, 130), (300, 300), (450, 450), (600, 600), (1000, 1000)]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("nsteps", [3, 7])
+def test_batch_chained_graph_agrees_bitwise(prec, nsteps):
+    outs = []
+    for graphs, chains in ((True, True), (True, False), (False, True)):
+        b, _ = make_batch(CHAIN_SHAPES, prec, use_graphs=graphs, chains=chains)
+        u0s = [smooth_field(s, 650 + i) for i, s in enumerate(CHAIN_SHAPES)]
+        up = b.pack(u0s)
+        uc = b.start(up)
+        b.step(up, uc, nsteps)
+        b.step(up, uc, nsteps)             # a second call replays the graph
+        torch.cuda.synchronize()
+        outs.append((up.cpu().numpy(), uc.cpu().numpy()))
+        b.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0][0], o[0]) and np.array_equal(outs[0][1], o[1])
+
+
 def test_batch_graph_and_direct_agree_bitwise():
     shapes = SHAPES[:8]
     outs = []
