@@ -84,6 +84,48 @@ unsigned rows_grid(K kernel, int W, size_t smem, const LineSet &L, int &occ_cach
     return (unsigned)std::min<int64_t>(L.nlines, (int64_t)occ_cache * L.persist_sms);
 }
 
+// Dynamic shared memory of a one-CTA-per-row launch: the row's buffers,
+// padded where one CTA per SM fewer than the kernel's occupancy occ leaves
+// fuller waves.  With k CTAs per SM the nrows CTAs take nrows / (SMs k)
+// waves, the last one partly empty; k = occ - 1 is taken where it raises the
+// filled fraction of the waves by more than 0.05 (2048 rows of two warps on
+// 152 SMs: 8 per SM fill 84 % of two waves, 7 fill 96 %), and the padding
+// leaves no room for a (k+1)-th CTA: (k+1) (smem + reserved) > the SM's
+// shared memory.
+template <class K>
+size_t rows_launch_smem(K kernel, int W, size_t base, int64_t nrows, int &occ_cache)
+{
+    static int dev_c = -1, sms = 0, smem_sm = 0, resv = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return base; }
+    if (dev != dev_c) {
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return base;
+        }
+        dev_c = dev;
+    }
+    if (occ_cache <= 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 32 * W, base) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        occ_cache = occ;
+    }
+    const int occ = occ_cache;
+    if (occ < 2 || sms < 1) return base;
+    auto fill = [&](int k) {
+        const double w = (double)nrows / ((double)sms * (double)k);
+        return w / std::ceil(w);
+    };
+    if (fill(occ - 1) <= fill(occ) + 0.05) return base;
+    const size_t pad = ((size_t)smem_sm / (size_t)occ - (size_t)resv + 16 + 15) & ~(size_t)15;
+    return pad > base ? pad : base;
+}
+
 template <int BC, int RPT, int NB, int W>
 cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cudaStream_t s)
 {
@@ -98,15 +140,19 @@ cudaError_t run_rows(const AxisDev &A, const LineSet &L, const ProgParams &p, cu
     }
     if constexpr (W == 2 || W == 4) {
         if (L.rows_nb && rows_nb_plan(A.d, A.n, RPT, W)) {   // one neighbour exchange per sweep
-            static int occ_nb = 0;
+            static int occ_nb = 0, occ_nb_pad = 0;
             const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W, false, true>, W, smem, L, occ_nb);
-            return launch_pass(k_contig_rows<BC, RPT, NB, W, false, true>, dim3(g), dim3(32 * W), smem, s, L, 1, A, L,
+            const size_t sm = L.persist_sms > 0 ? smem
+                                                : rows_launch_smem(k_contig_rows<BC, RPT, NB, W, false, true>, W, smem,
+                                                                   L.nlines, occ_nb_pad);
+            return launch_pass(k_contig_rows<BC, RPT, NB, W, false, true>, dim3(g), dim3(32 * W), sm, s, L, 1, A, L,
                                p, nc);
         }
     }
-    static int occ = 0;
+    static int occ = 0, occ_pad = 0;
     const unsigned g = rows_grid(k_contig_rows<BC, RPT, NB, W>, W, smem, L, occ);
-    return launch_pass(k_contig_rows<BC, RPT, NB, W>, dim3(g), dim3(32 * W), smem, s, L, 1, A, L, p, nc);
+    const size_t sm = L.persist_sms > 0 ? smem : rows_launch_smem(k_contig_rows<BC, RPT, NB, W>, W, smem, L.nlines, occ_pad);
+    return launch_pass(k_contig_rows<BC, RPT, NB, W>, dim3(g), dim3(32 * W), sm, s, L, 1, A, L, p, nc);
 }
 
 template <int BC, int RPT, int NB, int W>
@@ -114,8 +160,9 @@ cudaError_t attr_rows()
 {
     // the largest shared-memory carveout: the CTAs per SM are then limited
     // by registers and the row's buffers, not by the default split with L1
+    // (up to the per-CTA maximum: a launch may pad its buffers, rows_launch_smem)
     cudaError_t e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rows_smem<RPT, NB, W>());
+                                         227 * 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
@@ -130,7 +177,7 @@ cudaError_t attr_rows()
     if constexpr (W == 2 || W == 4) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W, false, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem<RPT, NB, W>());
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_contig_rows<BC, RPT, NB, W, false, true>,
                                      cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
